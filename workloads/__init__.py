@@ -1,0 +1,202 @@
+"""Seeded synthetic inputs for HSS compression.
+
+This module only builds input matrices, point clouds and orderings; it holds
+none of the compression, product, factorization or solve arithmetic.  The CPU
+oracle and the GPU path both take their inputs from here, and nothing here
+imports either of them.
+
+Matrix families (stand-ins for the paper's application matrices, Section 4.1):
+
+* ``toeplitz_inv_distance``  a_ij = 1/(1+|i-j|), a_ii = 10.
+* ``simple_toeplitz``        the paper's SimpleToeplitz: a_ii = n^2, a_ij = i-j.
+* ``gaussian_kernel``        K_ij = exp(-|x_i-x_j|^2/(2h^2)) + lambda*delta_ij on
+                             points uniform in the unit cube.
+* ``bem_like``               a_ij = 1/(4*pi*|x_i-x_j|), a_ii = sqrt(n) on points
+                             uniform on the unit sphere.
+* ``random_hss``             a dense matrix assembled from random HSS generators
+                             with prescribed ranks (known-rank test input).
+
+Point clouds are put in recursive-coordinate-bisection order whose splits match
+the cluster tree's bisection (left part = floor(s/2) points), so that the
+off-diagonal blocks of the tree are the far-field blocks.
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+try:  # torch is only needed for the chunked on-device generators
+    import torch
+except ImportError:  # pragma: no cover
+    torch = None
+
+
+# ---------------------------------------------------------------- point clouds
+def points_unit_cube(n: int, seed: int) -> np.ndarray:
+    """n points uniform in [0,1]^3 (float64, shape n x 3)."""
+    return np.random.default_rng(seed).random((n, 3))
+
+
+def points_unit_sphere(n: int, seed: int) -> np.ndarray:
+    """n points uniform on the unit sphere (normalised Gaussian vectors)."""
+    g = np.random.default_rng(seed).standard_normal((n, 3))
+    return g / np.linalg.norm(g, axis=1, keepdims=True)
+
+
+def rcb_order(points: np.ndarray, leaf_size: int) -> np.ndarray:
+    """Recursive coordinate bisection permutation.
+
+    A range of s > leaf_size points is sorted (stably) along the longest axis
+    of its bounding box and split into floor(s/2) and s - floor(s/2) points,
+    the same split the cluster tree uses, down to ranges of <= leaf_size.
+    """
+    n = points.shape[0]
+    perm = np.arange(n)
+    stack = [(0, n)]
+    while stack:
+        lo, hi = stack.pop()
+        s = hi - lo
+        if s <= leaf_size:
+            continue
+        sub = points[perm[lo:hi]]
+        axis = int(np.argmax(sub.max(axis=0) - sub.min(axis=0)))
+        order = np.argsort(sub[:, axis], kind="stable")
+        perm[lo:hi] = perm[lo:hi][order]
+        mid = lo + s // 2
+        stack.append((lo, mid))
+        stack.append((mid, hi))
+    return perm
+
+
+# ------------------------------------------------------------ dense matrices
+def _dev(device):
+    if torch is None:
+        raise RuntimeError("torch is required for the chunked generators")
+    return torch.device(device)
+
+
+def toeplitz_inv_distance(n: int, dtype=np.float64, device="cpu"):
+    """a_ij = 1/(1+|i-j|) off the diagonal, a_ii = 10 (row-major n x n)."""
+    dev = _dev(device)
+    i = torch.arange(n, device=dev, dtype=torch.float64)
+    a = 1.0 / (1.0 + (i[:, None] - i[None, :]).abs())
+    a.diagonal().fill_(10.0)
+    return a.to(_tdtype(dtype))
+
+
+def simple_toeplitz(n: int, dtype=np.float64, device="cpu"):
+    """The paper's SimpleToeplitz matrix: a_ii = n^2, a_ij = i - j."""
+    dev = _dev(device)
+    i = torch.arange(n, device=dev, dtype=torch.float64)
+    a = i[:, None] - i[None, :]
+    a.diagonal().fill_(float(n) * n)
+    return a.to(_tdtype(dtype))
+
+
+def _tdtype(dtype):
+    if dtype in (np.float32, "float32", "f32") or dtype == torch.float32:
+        return torch.float32
+    return torch.float64
+
+
+def _chunked_kernel(points: np.ndarray, fn, dtype, device, chunk=4096):
+    dev = _dev(device)
+    x = torch.as_tensor(points, dtype=torch.float64, device=dev)
+    n = x.shape[0]
+    out = torch.empty((n, n), dtype=_tdtype(dtype), device=dev)
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        d2 = ((x[r0:r1, None, :] - x[None, :, :]) ** 2).sum(-1)
+        blk = fn(d2, r0, r1)
+        out[r0:r1] = blk.to(out.dtype)
+    return out
+
+
+def gaussian_kernel(points: np.ndarray, h: float, lam: float, dtype=np.float32, device="cpu"):
+    """K_ij = exp(-|x_i-x_j|^2 / (2 h^2)) + lam * delta_ij (computed in FP64)."""
+    def fn(d2, r0, r1):
+        k = torch.exp(-d2 / (2.0 * h * h))
+        idx = torch.arange(r0, r1, device=k.device)
+        k[idx - r0, idx] += lam
+        return k
+    return _chunked_kernel(points, fn, dtype, device)
+
+
+def bem_like(points: np.ndarray, dtype=np.float32, device="cpu"):
+    """a_ij = 1/(4 pi |x_i-x_j|) for i != j, a_ii = sqrt(n) (computed in FP64)."""
+    n = points.shape[0]
+    diag = math.sqrt(n)
+
+    def fn(d2, r0, r1):
+        idx = torch.arange(r0, r1, device=d2.device)
+        d2[idx - r0, idx] = 1.0
+        k = 1.0 / (4.0 * math.pi * torch.sqrt(d2))
+        k[idx - r0, idx] = diag
+        return k
+    return _chunked_kernel(points, fn, dtype, device)
+
+
+# ------------------------------------------------ known-rank random HSS input
+def bisection_intervals(n: int, leaf_size: int):
+    """Cluster tree by bisection, as nested tuples (lo, hi, left, right).
+
+    Input-side copy of the tree rule (left child gets floor(s/2) indices, a
+    range of <= leaf_size indices is a leaf); used only to lay out the random
+    generators of ``random_hss``.
+    """
+    def rec(lo, hi):
+        s = hi - lo
+        if s <= leaf_size:
+            return (lo, hi, None, None)
+        mid = lo + s // 2
+        return (lo, hi, rec(lo, mid), rec(mid, hi))
+    return rec(0, n)
+
+
+def random_hss(n: int, leaf_size: int, rank: int, seed: int, diag_shift: float = 0.0):
+    """Dense n x n matrix whose every off-diagonal Hankel block has rank `rank`.
+
+    Random Gaussian generators are drawn at every node: D at the leaves, U and
+    V (size m x rank, m = leaf size or 2*rank) at every non-root node, B12 and
+    B21 (rank x rank) at every non-leaf.  The dense matrix is assembled from
+    the nested bases U^big = diag(U^big_1, U^big_2) U.  Returns (A, info) where
+    info maps (lo, hi) of every non-root node to its row/column rank.
+    """
+    rng = np.random.default_rng(seed)
+    A = np.zeros((n, n))
+    ranks = {}
+
+    def rec(node, is_root):
+        lo, hi, left, right = node
+        if left is None:
+            m = hi - lo
+            A[lo:hi, lo:hi] = rng.standard_normal((m, m)) + diag_shift * np.eye(m)
+            k = min(rank, m)
+            ub = rng.standard_normal((m, k))
+            vb = rng.standard_normal((m, k))
+        else:
+            u1, v1 = rec(left, False)
+            u2, v2 = rec(right, False)
+            l0, l1 = left[0], left[1]
+            r0, r1 = right[0], right[1]
+            b12 = rng.standard_normal((u1.shape[1], v2.shape[1]))
+            b21 = rng.standard_normal((u2.shape[1], v1.shape[1]))
+            A[l0:l1, r0:r1] = u1 @ b12 @ v2.T
+            A[r0:r1, l0:l1] = u2 @ b21 @ v1.T
+            if is_root:
+                return None, None
+            m = u1.shape[1] + u2.shape[1]
+            k = min(rank, m)
+            ut = rng.standard_normal((m, k))
+            vt = rng.standard_normal((m, k))
+            ub = np.vstack([u1 @ ut[: u1.shape[1]], u2 @ ut[u1.shape[1]:]])
+            vb = np.vstack([v1 @ vt[: v1.shape[1]], v2 @ vt[v1.shape[1]:]])
+        ranks[(lo, hi)] = ub.shape[1]
+        return ub, vb
+
+    root = bisection_intervals(n, leaf_size)
+    if root[2] is None:
+        A[:, :] = rng.standard_normal((n, n)) + diag_shift * np.eye(n)
+    else:
+        rec(root, True)
+    return A, ranks
