@@ -1,0 +1,334 @@
+"""Benchmark: randomized HSS compression on the GB300 (one JSON line on rank 0).
+
+A step is one full hss_compress of the workload (fused sampling, batched FP64
+ID level by level, generator extraction, adaptive re-sampling), with the input
+matrix already resident in HBM; the handle is destroyed after each step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--mode native|tf32|bf16x2|bf16x3] [--impl ours|reference]
+
+Workloads (synthetic, seeded; stand-ins for the paper's application matrices):
+  gauss20k    FP32 Gaussian kernel, n=20000, h=0.2, lambda=1, points uniform in
+              the unit cube in RCB order, leaf 256, rtol 1e-4, d0=128, step 64
+              (default)
+  toeplitz2k  FP64 Toeplitz a_ij = 1/(1+|i-j|), a_ii = 10, n=2000, leaf 128,
+              rtol 1e-6, d0=64, step 32
+  bem60k      FP32 a_ij = 1/(4 pi |x_i-x_j|), a_ii = sqrt(n), n=60000 points
+              on the unit sphere in RCB order, leaf 512, rtol 1e-6, d0=256,
+              step 128
+
+--impl reference times the CPU oracle (FP64 numpy/scipy, the reference
+implementation written from the paper) on the host cores, on the same
+workload, metric and unit.  Multi-GPU runs are independent replicas (the
+method has no data-path exchange on one matrix): each rank compresses its own
+copy; the value is the whole job's seconds per compression.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "gauss20k": dict(family="gaussian_kernel", n=20000, leaf=256, rtol=1e-4, d0=128, step=64,
+                     dtype="f32", seed=1002, h=0.2, lam=1.0),
+    "toeplitz2k": dict(family="toeplitz_inv_distance", n=2000, leaf=128, rtol=1e-6, d0=64,
+                       step=32, dtype="f64", seed=1001),
+    "bem60k": dict(family="bem_like_sphere", n=60000, leaf=512, rtol=1e-6, d0=256, step=128,
+                   dtype="f32", seed=1003),
+}
+
+METRIC = "HSS compress s"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 and FP32 FMA throughput on this GB300 (own probe: 152 SMs, ~2 FP64 and
+# 128 FP32 FMA per clock per SM at ~1.97 GHz)
+FP64_PEAK_TFLOPS = 1.20
+FP32_SIMT_PEAK_TFLOPS = 69.7
+
+
+def make_matrix(wl, device):
+    import workloads as W
+    fam = wl["family"]
+    dt = np.float32 if wl["dtype"] == "f32" else np.float64
+    if fam == "toeplitz_inv_distance":
+        return W.toeplitz_inv_distance(wl["n"], dtype=dt, device=device)
+    if fam == "gaussian_kernel":
+        pts = W.points_unit_cube(wl["n"], wl["seed"])
+        pts = pts[W.rcb_order(pts, wl["leaf"])]
+        return W.gaussian_kernel(pts, wl["h"], wl["lam"], dtype=dt, device=device)
+    if fam == "bem_like_sphere":
+        pts = W.points_unit_sphere(wl["n"], wl["seed"])
+        pts = pts[W.rcb_order(pts, wl["leaf"])]
+        return W.bem_like(pts, dtype=dt, device=device)
+    raise ValueError(fam)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args, wl):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__ as g
+    g.build()
+    import paper_1503_05464_gb300 as P
+
+    A = make_matrix(wl, dev).contiguous()
+    torch.cuda.synchronize()
+    opts = P.hss_default_opts(leaf_size=wl["leaf"], rtol=wl["rtol"], d0=wl["d0"],
+                              d_step=wl["step"], seed=wl["seed"] + 1, sample_mode=args.mode)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        h = P.hss_compress(A, opts, stream=stream)
+        info = P.hss_info(h)
+        h.close()
+        return info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    infos = []
+    l0 = P.hss.hss_kernel_launches()
+    with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = P.hss.hss_kernel_launches() - l0
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+
+    # end to end through the public API from pinned host memory
+    A_host = A.cpu().pin_memory()
+    A_dev = torch.empty_like(A)
+    ranks_bytes = 0
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        A_dev.copy_(A_host, non_blocking=True)
+        h = P.hss_compress(A_dev, opts, stream=stream)
+        rk = P.hss_node_ranks(h)
+        ranks_bytes = 16 * len(rk)
+        h.close()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    info = infos[-1]
+    d2h = info["bytes_d2h"] + ranks_bytes
+
+    # roofline of the dominant kernel family
+    s_ms = statistics.mean(i["ms_sample"] for i in infos)
+    id_ms = statistics.mean(i["ms_id"] for i in infos)
+    peaks = {}
+    if os.path.exists(MEASURED_PEAKS):
+        peaks = json.load(open(MEASURED_PEAKS))
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    n = wl["n"]
+    esz = 4 if wl["dtype"] == "f32" else 8
+    id_tflops = info["flops_id"] / (id_ms * 1e-3) / 1e12 if id_ms > 0 else 0.0
+    samp_tflops = info["flops_sample"] / (s_ms * 1e-3) / 1e12 if s_ms > 0 else 0.0
+    samp_gbs = info["passes"] * n * n * esz / (s_ms * 1e-3) / 1e9 if s_ms > 0 else 0.0
+    samp_peak = FP64_PEAK_TFLOPS if wl["dtype"] == "f64" else FP32_SIMT_PEAK_TFLOPS
+    phases = {
+        "id_cpqr_fp64": {"ms": id_ms, "bound": "alu", "achieved": id_tflops,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": id_tflops / FP64_PEAK_TFLOPS},
+        "fused_sampling": {"ms": s_ms, "bound": "alu" if args.mode == "native" else "tensor",
+                           "achieved": samp_tflops, "peak": samp_peak, "unit": "TFLOP/s",
+                           "frac": samp_tflops / samp_peak, "hbm_gbs": samp_gbs,
+                           "hbm_frac": samp_gbs / hbm},
+    }
+    dom = max(phases, key=lambda k: phases[k]["ms"])
+    roof = dict(phases[dom])
+    roof.pop("ms")
+    roof.pop("hbm_gbs", None)
+    roof.pop("hbm_frac", None)
+    roof["kernel"] = dom
+    roof["traffic"] = None
+    value = ms / 1e3 / (args.steps * world) if world > 1 else ms / 1e3 / args.steps
+    out = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32": "f32", "f64": "f64"}[wl["dtype"]] + "+f64-id",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "leaf": wl["leaf"], "rtol": wl["rtol"],
+                   "d0": wl["d0"], "d_step": wl["step"], "sample_mode": args.mode,
+                   "family": wl["family"], "l2": "input larger than L2 (no flush needed)"},
+        "roofline": roof,
+        "phases": phases,
+        "hss": {"passes": info["passes"], "d_final": info["d_final"],
+                "max_rank": max(info["max_rank_r"], info["max_rank_c"]),
+                "bytes_hss": info["bytes_hss"], "levels": info["levels"]},
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": n * n * esz,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+    }
+    clocks = clk.summary()
+    if clocks:
+        out["clocks"] = clocks
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, A.cpu().numpy())
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _threads():
+    n = os.cpu_count() or 1
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            n = max(i.get("num_threads", n) for i in info)
+    except Exception:
+        pass
+    return n
+
+
+def cpu_baseline(wl, A_np):
+    """The oracle, as it stands, on the host cores: one full compression."""
+    from oracle import hss_oracle as O
+    A64 = np.asarray(A_np, dtype=np.float64)
+    t0 = time.perf_counter()
+    O.compress(A64, wl["rtol"], leaf_size=wl["leaf"], d0=wl["d0"], d_step=wl["step"],
+               seed=wl["seed"] + 1)
+    t = time.perf_counter() - t0
+    return {"value": t, "unit": "s", "cores": _threads(), "kind": "oracle",
+            "sample": f"one full FP64 oracle compression of {wl['family']} n={wl['n']}"}
+
+
+def run_reference(args, wl):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads  # noqa: F401
+    from oracle import hss_oracle as O
+    A = make_matrix(wl, "cpu").numpy().astype(np.float64)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.compress(A, wl["rtol"], leaf_size=wl["leaf"], d0=wl["d0"], d_step=wl["step"],
+                   seed=wl["seed"] + 1)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    v = sum(times) / len(times)
+    out = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": args.workload, "n": wl["n"], "leaf": wl["leaf"],
+                      "rtol": wl["rtol"], "family": wl["family"]},
+           "cpu_baseline": {"value": v, "unit": "s", "cores": _threads(), "kind": "oracle",
+                            "sample": f"full FP64 oracle compression of {wl['family']} n={wl['n']} per step"},
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="gauss20k", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="native", choices=["native", "tf32", "bf16x2", "bf16x3"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.steps is None:
+        args.steps = 3 if args.impl == "reference" else 10
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

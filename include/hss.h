@@ -1,0 +1,225 @@
+/*
+ * hss.h -- C ABI of the GB300 randomized HSS compression library.
+ *
+ * The method is randomized Hierarchically Semi-Separable (HSS) compression of
+ * a dense n x n matrix (Rouet, Li, Ghysels, Napov, arXiv:1503.05464):
+ *   - HSS representation and cluster tree ............ Section 2.1, Fig. 1
+ *   - randomized compression ......................... Section 2.2, Algorithm 1
+ *   - interpolative decomposition (truncated CPQR) ... Section 2.2, Section 3.1
+ *   - adaptive sampling (late notification) .......... Section 3.2, Algorithm 5
+ *   - HSS matrix-vector product ...................... Section 2.3, Algorithm 2
+ *   - ULV-like factorization ......................... Section 2.4, Algorithm 3
+ *   - solution with the ULV factors .................. Section 2.5, Algorithm 4
+ *
+ * Conventions for every entry point:
+ *   - Matrix and vector pointers are DEVICE pointers owned by the caller,
+ *     unless a parameter says "host".  Dense matrices are row-major with a
+ *     leading dimension (elements between consecutive rows) >= the row length.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is stream-ordered; entry points that must read results
+ *     back (hss_compress reads ranks to size its storage) synchronize `stream`.
+ *   - Errors are returned as hss_status codes; no exception or abort crosses
+ *     the ABI.  A handle keeps a message for its last error
+ *     (hss_last_error); calls without a handle keep a thread-local message
+ *     readable with hss_last_error(NULL).
+ *   - Device memory that a handle needs is allocated by the library with
+ *     stream-ordered cudaMallocAsync and released by hss_destroy.
+ */
+#ifndef HSS_H
+#define HSS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hss_s* hss_t;
+
+typedef enum {
+  HSS_OK = 0,
+  HSS_ERR_INVALID = 1,   /* bad argument (size, pointer, leading dimension, option) */
+  HSS_ERR_OOM = 2,       /* device allocation failed */
+  HSS_ERR_CUDA = 3,      /* a CUDA call or kernel launch failed */
+  HSS_ERR_RANK_CAP = 4,  /* adaptive sampling reached d_max before every node compressed */
+  HSS_ERR_SINGULAR = 5,  /* zero pivot in the root LU of the ULV factorization */
+  HSS_ERR_TIMEOUT = 6,   /* a device-side wait gave up after its iteration limit */
+  HSS_ERR_STATE = 7      /* call out of order (e.g. hss_solve before hss_factor) */
+} hss_status;
+
+typedef enum { HSS_F32 = 0, HSS_F64 = 1 } hss_dtype;
+
+/* Arithmetic of the sampling products S^r = A R and S^c = A^T R (step 2 of
+ * the compression algorithm, Section 2.2).  R is bfloat16-exact, so the
+ * split modes only split A.  For HSS_F64 inputs only NATIVE is accepted. */
+typedef enum {
+  HSS_SAMPLE_NATIVE = 0, /* FP32 (or FP64) fused multiply-add, no tensor cores  */
+  HSS_SAMPLE_TF32 = 1,   /* A rounded to TF32, tensor cores, FP32 accumulation */
+  HSS_SAMPLE_BF16X2 = 2, /* A = hi + lo (two bfloat16 terms), FP32 accumulation */
+  HSS_SAMPLE_BF16X3 = 3  /* A = hi + mid + lo (three bfloat16 terms)            */
+} hss_sample_mode;
+
+/* Compression options (Section 2.2, Section 3.2). */
+typedef struct {
+  int32_t leaf_size;     /* cluster tree: bisect [lo,hi) while hi-lo > leaf_size  */
+  double rtol;           /* ID stops at the first |R_ii| <= max(rtol |R_11|, atol) */
+  double atol;           /* absolute floor of that test (0 = relative only)      */
+  int32_t d0;            /* initial number of random sample columns              */
+  int32_t d_step;        /* columns added when a node's rank is too large         */
+  int32_t d_max;         /* cap on the sample count (0 = n)                      */
+  int32_t oversample_p;  /* a node fails iff d < m and rank > d - oversample_p    */
+  int32_t sample_mode;   /* hss_sample_mode                                      */
+  uint64_t seed;         /* seed of the counter-based Gaussian generator of R    */
+} hss_opts;
+
+/* Statistics of a handle (Table 3's columns: max rank, factor sizes, time). */
+typedef struct {
+  int64_t n;
+  int32_t nodes, leaves, levels;
+  int32_t max_rank_r, max_rank_c;   /* largest U / V generator rank            */
+  int32_t d_final;                  /* sample count at the end of compression  */
+  int32_t passes;                   /* adaptive passes (1 = no restart)        */
+  int64_t bytes_hss;                /* device bytes of D, B, E, permutations   */
+  int64_t bytes_ulv;                /* device bytes of the ULV factors         */
+  double ms_compress;               /* wall time of hss_compress              */
+  double ms_sample;                 /* device time in the fused sampling kernel */
+  double ms_id;                     /* device time in the batched ID kernel    */
+  double ms_levels;                 /* host-measured time of the level loop    */
+  double flops_sample;              /* 4 n^2 d summed over passes              */
+  double flops_id;                  /* sum over IDs of 4 d m k (FP64)          */
+  int32_t factored;                 /* 1 after hss_factor                      */
+  int64_t launches;                 /* kernels launched by hss_compress        */
+  int64_t bytes_d2h;                /* bytes read back to the host (ranks)     */
+} hss_info_t;
+
+/* Fills *opts with defaults: leaf_size 128, rtol 1e-6, atol 0, d0 64,
+ * d_step 32, d_max 0 (= n), oversample_p 10, NATIVE sampling, seed 0. */
+hss_status hss_default_opts(hss_opts* opts);
+
+/*
+ * hss_compress -- randomized HSS compression (Algorithm 1 with Algorithm 5's
+ * late-notification adaptive sampling, processed level by level).
+ *   A      device, n x n row-major, leading dimension lda >= n, dtype
+ *          HSS_F32 or HSS_F64.  Borrowed for the call only: D and B blocks
+ *          are copied out, the caller may free A afterwards.
+ *   opts   host; NULL = hss_default_opts.
+ *   out    host; receives a new handle (NULL on error).
+ * Errors: INVALID (n < 1, lda < n, bad options), OOM, CUDA, RANK_CAP (the
+ * handle is still returned in *out with the nodes that did compress, and
+ * must be destroyed).  Synchronizes `stream`.
+ */
+hss_status hss_compress(const void* A, int64_t n, int64_t lda, hss_dtype dtype,
+                        const hss_opts* opts, void* stream, hss_t* out);
+
+/*
+ * hss_matvec -- B = H X with the compressed form (Algorithm 2).
+ *   X  device, n x nrhs row-major, ldx >= nrhs, the handle's dtype.
+ *   B  device, n x nrhs row-major, ldb >= nrhs; must not overlap X.
+ * Errors: INVALID, OOM, CUDA.  Stream-ordered.
+ */
+hss_status hss_matvec(hss_t h, const void* X, int64_t ldx, int64_t nrhs,
+                      void* B, int64_t ldb, void* stream);
+
+/*
+ * hss_factor -- ULV-like factorization of the compressed form (Algorithm 3),
+ * in FP64 whatever the handle's dtype.  Errors: SINGULAR (zero pivot in the
+ * root LU), OOM, CUDA.  Synchronizes `stream`.
+ */
+hss_status hss_factor(hss_t h, void* stream);
+
+/*
+ * hss_solve -- X = H^{-1} B with the ULV factors (Algorithm 4).
+ *   B  device, n x nrhs row-major, ldb >= nrhs, the handle's dtype.
+ *   X  device, n x nrhs row-major, ldx >= nrhs (may equal B when ldx == ldb).
+ * Errors: STATE (no hss_factor yet), INVALID, OOM, CUDA.  Stream-ordered.
+ */
+hss_status hss_solve(hss_t h, const void* B, int64_t ldb, int64_t nrhs,
+                     void* X, int64_t ldx, void* stream);
+
+/* hss_info -- statistics of the handle into *info (host). */
+hss_status hss_info(hss_t h, hss_info_t* info);
+
+/*
+ * hss_node_ranks -- per-node ranks, nodes numbered breadth-first (root 0,
+ * children of a node are consecutive).  lo, hi, kr, kc are host arrays of
+ * `cap` entries (any may be NULL); entry i gets node i's interval [lo, hi)
+ * and its row / column rank (-1 for the root).  Returns the node count in
+ * *count.  Errors: INVALID (cap smaller than the node count).
+ */
+hss_status hss_node_ranks(hss_t h, int32_t* lo, int32_t* hi, int32_t* kr,
+                          int32_t* kc, int32_t cap, int32_t* count);
+
+/* hss_kernel_launches -- number of CUDA kernels this library has launched in
+ * the calling process so far (all threads, all handles). */
+int64_t hss_kernel_launches(void);
+
+/* hss_destroy -- frees every device buffer of the handle (NULL is a no-op). */
+void hss_destroy(hss_t h);
+
+/* hss_last_error -- message of the last failed call on h (NULL: the calling
+ * thread's last failed call that had no handle).  Never NULL. */
+const char* hss_last_error(hss_t h);
+
+/* ---------------------------------------------------------------------------
+ * Step-level entry points.  They run single steps of the compression on
+ * caller buffers; hss_compress runs the same kernels.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * hss_random_gaussian -- columns [c0, c1) of the n x d random matrix R of
+ * Section 2.2.  R[i, j] is a standard Gaussian from the splitmix64 sequence
+ * (outputs 2q+1 and 2q+2 for q = i*2^32 + j, Box-Muller in FP64) rounded to
+ * the nearest bfloat16, stored as dtype.
+ *   R  device, row-major, ldr >= c1; row i, column j at R[i*ldr + j].
+ * Errors: INVALID, CUDA.  Stream-ordered.
+ */
+hss_status hss_random_gaussian(uint64_t seed, int64_t n, int64_t c0, int64_t c1,
+                               void* R, int64_t ldr, hss_dtype dtype, void* stream);
+
+/*
+ * hss_sample -- fused sampling (Section 2.2, step 2): for columns [c0, c1)
+ *   Sr[:, c] = (A - D) R[:, c],   Sc[:, c] = (A - D)^T R[:, c],
+ * reading every tile of A from device memory once for both products.  D is
+ * the block diagonal of the leaf blocks A(I_t, I_t) of the cluster tree given
+ * by `leaf_starts` (host, nleaf+1 increasing offsets, leaf_starts[0] = 0,
+ * leaf_starts[nleaf] = n); nleaf = 0 means no masking (D = 0).  With the
+ * mask, Sr(I_t, :) is Algorithm 1's S^r_loc = S^r(I_t,:) - D_t R(I_t,:).
+ *   A  device n x n row-major (lda);  R, Sr, Sc device n x ld row-major with
+ *   ldr / lds >= c1.  mode: hss_sample_mode (NATIVE only for HSS_F64).
+ * Errors: INVALID, OOM (scratch for the partial sums), CUDA.  Stream-ordered.
+ */
+hss_status hss_sample(const void* A, int64_t n, int64_t lda, hss_dtype dtype,
+                      const void* R, int64_t ldr, int64_t c0, int64_t c1,
+                      void* Sr, void* Sc, int64_t lds,
+                      const int64_t* leaf_starts, int32_t nleaf, int32_t mode,
+                      void* stream);
+
+/*
+ * hss_id_batched -- interpolative decompositions [X, J] = ID(Y_b, eps) of a
+ * batch of matrices by truncated column-pivoted QR in FP64 (Section 2.2,
+ * Section 3.1): the factorization of Y_b (d_b x m_b) stops at the first i
+ * with |R_ii| <= max(rtol |R_11|, atol), k_b = i (min(d_b, m_b) if none).
+ *   Yt     device array (count entries) of device pointers; Y_b is stored
+ *          TRANSPOSED, as m_b rows of d_b values: column j of Y_b is the
+ *          contiguous row Yt[b] + j*ldy[b].  dtype of the values: dtype.
+ *   m, d, ldy   device int32 arrays (count entries).
+ *   perm   device array of device int32 pointers, m_b entries each: on return
+ *          perm[b][0..k) = J (pivot order), perm[b][k..m) = the other
+ *          columns in increasing order.
+ *   E      device array of device double pointers; E_b is written as a dense
+ *          (m_b - k_b) x k_b row-major matrix (ld = k_b), so each buffer
+ *          needs m_b * min(d_b, m_b) doubles at most.  E = (R1^{-1} R2)^T,
+ *          so that X^T = Pi [I; E] with Pi the permutation `perm`.
+ *   k      device int32 array (count): the ranks.
+ * Errors: INVALID, OOM, CUDA.  Stream-ordered.
+ */
+hss_status hss_id_batched(int32_t count, const void* const* Yt, const int32_t* m,
+                          const int32_t* d, const int32_t* ldy, hss_dtype dtype,
+                          double rtol, double atol, int32_t* const* perm,
+                          double* const* E, int32_t* k, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSS_H */

@@ -374,6 +374,23 @@ def _process_node(A, R, Sr, Sc, nodes, data, nd, d, rtol, atol, p):
     me.state = COMPRESSED
 
 
+def leaf_local_samples(A, R, nodes):
+    """Algorithm 1's leaf samples for every leaf, stacked in index order:
+    S^r_loc(I_t,:) = S^r(I_t,:) - D_t R(I_t,:) and S^c_loc = S^c(I_t,:) - D_t^T R(I_t,:)
+    with S^r = A R, S^c = A^T R (Section 2.2)."""
+    A = np.asarray(A, dtype=np.float64)
+    R = np.asarray(R, dtype=np.float64)
+    Sr = A @ R
+    Sc = A.T @ R
+    for nd in nodes:
+        if nd.is_leaf:
+            I = slice(nd.lo, nd.hi)
+            D = A[I, I]
+            Sr[I] -= D @ R[I]
+            Sc[I] -= D.T @ R[I]
+    return Sr, Sc
+
+
 # ------------------------------------------------------ dense reconstruction
 
 

@@ -1,0 +1,133 @@
+// Internal declarations shared by the CUDA translation units of libhss.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/hss.h"
+
+namespace hss {
+
+// ------------------------------------------------------------------ errors
+struct Err {
+  hss_status st = HSS_OK;
+  std::string msg;
+};
+
+#define HSS_CUDA_TRY(expr)                                                    \
+  do {                                                                        \
+    cudaError_t e_ = (expr);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      return ::hss::fail(HSS_ERR_CUDA, std::string(#expr) + ": " +           \
+                                           cudaGetErrorString(e_));           \
+    }                                                                         \
+  } while (0)
+
+#define HSS_TRY(expr)                                                         \
+  do {                                                                        \
+    ::hss::Err e_ = (expr);                                                   \
+    if (e_.st != HSS_OK) return e_;                                           \
+  } while (0)
+
+inline Err fail(hss_status st, const std::string& m) { return Err{st, m}; }
+inline Err ok() { return Err{}; }
+// Counts the launch (see hss_kernel_launches) and checks for a launch error.
+Err check_launch(const char* what);
+int64_t launches_so_far();
+
+// Stream-ordered device allocation (cudaMallocAsync); null for 0 bytes.
+Err dalloc(void** p, size_t bytes, cudaStream_t s);
+void dfree(void* p, cudaStream_t s);
+
+template <typename T>
+inline Err dalloc_t(T** p, size_t count, cudaStream_t s) {
+  return dalloc(reinterpret_cast<void**>(p), count * sizeof(T), s);
+}
+
+// ----------------------------------------------------------- random matrix
+// R[i, j] for j in [c0, c1), row-major with ldr (Section 2.2).
+template <typename T>
+Err launch_random_gaussian(uint64_t seed, int64_t n, int64_t c0, int64_t c1, T* R,
+                           int64_t ldr, cudaStream_t s);
+
+// ---------------------------------------------------------- fused sampling
+// Sr[:, c0:c1] = (A - Dleaf) R[:, c0:c1], Sc[:, c0:c1] = (A - Dleaf)^T R.
+// leaf_of: device int32 array of n leaf ids (nullptr = no mask).
+struct SampleScratch {
+  void* part = nullptr;     // partial column sums, one slab per row panel
+  size_t bytes = 0;
+};
+template <typename T>
+Err launch_sample(const T* A, int64_t n, int64_t lda, const T* R, int64_t ldr,
+                  int64_t c0, int64_t c1, T* Sr, T* Sc, int64_t lds,
+                  const int32_t* leaf_of, int mode, SampleScratch* scratch,
+                  cudaStream_t s, float* ms_out);
+size_t sample_scratch_bytes(int64_t n, int64_t ncols, int mode, bool f64);
+
+// ------------------------------------------------------- batched FP64 ID
+// One item: Y stored transposed (m rows of d values, row j = column j of Y).
+struct IdItem {
+  const void* Yt;   // m x ldy (dtype of the launch)
+  int32_t m, d, ldy;
+  int32_t* perm;    // m entries
+  double* E;        // (m - k) x k row-major, ld = k
+  int32_t* k;       // rank out
+  double* work;     // m * d doubles of scratch
+  double* norms;    // 2 * m doubles of scratch
+};
+// max_d: largest d of the batch (shared-memory size of the reflector).
+Err launch_id_batched(const IdItem* items_dev, int count, bool f64, double rtol,
+                      double atol, int max_d, cudaStream_t s);
+
+// --------------------------------------------- batched gathered GEMM
+// out[j][c] = (X ? X[xrow(j)][c] : 0) + sign * sum_l Mat(j,l) * Z[zrow(l)][c]
+// for j < rows, c in [c0, c1).  Row sources are two-part: row r < split comes
+// from p0 + r*ld0, else from p1 + (r-split)*ld1; an optional int32 map is
+// applied first (row = map[j]).  Mat is double or T, normal (M[j*ldm+l]) or
+// transposed (M[l*ldm+j]).
+template <typename T>
+struct RowSrc {
+  const T* p0 = nullptr;
+  const T* p1 = nullptr;
+  int64_t ld0 = 0, ld1 = 0;
+  int32_t split = 0x7fffffff;
+  const int32_t* map = nullptr;
+};
+template <typename T>
+struct GemmItem {
+  T* out;
+  int64_t ldo;
+  int32_t rows, inner;   // j < rows, l < inner
+  int32_t c0, c1;
+  RowSrc<T> X;           // X.p0 == nullptr: no X term
+  RowSrc<T> Z;
+  const void* M;         // T or double (see m_is_f64)
+  int64_t ldm;
+  int32_t m_trans;       // 0: M[j*ldm+l], 1: M[l*ldm+j]
+  int32_t m_is_f64;
+  T sign;
+};
+template <typename T>
+Err launch_gemm_batched(const std::vector<GemmItem<T>>& items, cudaStream_t s,
+                        void* scratch_dev, size_t scratch_bytes);
+
+// ------------------------------------------------------------- gathers
+// out[j][l] = A[rows[j]][cols[l]] for a batch of blocks.
+template <typename T>
+struct GatherItem {
+  T* out;                // rows x cols, row-major, ld = cols
+  const int32_t* rows;
+  const int32_t* cols;
+  int32_t nr, nc;
+};
+template <typename T>
+Err launch_gather_batched(const T* A, int64_t lda, const std::vector<GatherItem<T>>& items,
+                          cudaStream_t s, void* scratch_dev, size_t scratch_bytes);
+
+// map[j] = base[idx[j]]  (skeleton index sets I^r_tau = I(J))
+Err launch_index_compose(int32_t* out, const int32_t* base, const int32_t* idx, int count,
+                         cudaStream_t s);
+
+}  // namespace hss

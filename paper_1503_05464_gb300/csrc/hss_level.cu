@@ -1,0 +1,217 @@
+// Batched level kernels of the tree traversals (Algorithms 1, 2): every node
+// of a tree level is one item of a single launch.
+//
+//  * gemm_batched: out[j][c] = X[xrow(j)][c] + sign * sum_l Mat(j,l) Z[zrow(l)][c]
+//    covers Algorithm 1's merges S_nu - B R_nu, the row selections
+//    S_tau = S_loc(J,:), the basis products V^T R = R(J) + E^T R(rest), and
+//    Algorithm 2's products.  Rows of X and Z may come through an index map
+//    and from two stacked sources (the two children of a node).
+//  * gather_batched: B = A(I^r, I^c) submatrix extraction (Section 2.2: with
+//    an ID basis, B_{nu1,nu2} = A(I^r_nu1, I^c_nu2)).
+#include "hss_internal.cuh"
+
+#include <algorithm>
+
+namespace hss {
+
+namespace {
+
+constexpr int G_TM = 64, G_TN = 64, G_TK = 16, G_THREADS = 256;
+
+template <typename T>
+__device__ __forceinline__ const T* src_row(const RowSrc<T>& s, int r) {
+  if (s.map) r = s.map[r];
+  return r < s.split ? s.p0 + (int64_t)r * s.ld0 : s.p1 + (int64_t)(r - s.split) * s.ld1;
+}
+
+template <typename T>
+__device__ __forceinline__ T mat_at(const GemmItem<T>& it, int j, int l) {
+  int64_t off = it.m_trans ? (int64_t)l * it.ldm + j : (int64_t)j * it.ldm + l;
+  return it.m_is_f64 ? (T)(reinterpret_cast<const double*>(it.M)[off])
+                     : reinterpret_cast<const T*>(it.M)[off];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(G_THREADS)
+gemm_batched_kernel(const GemmItem<T>* __restrict__ items, const int* __restrict__ tile_start,
+                    int nitems) {
+  __shared__ T Ms[G_TM][G_TK + 1];
+  __shared__ T Zs[G_TK][G_TN];
+  // locate the item of this tile (binary search in the tile prefix)
+  int lo = 0, hi = nitems - 1;
+  const int b = blockIdx.x;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (tile_start[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const GemmItem<T> it = items[lo];
+  const int local = b - tile_start[lo];
+  const int ncol = it.c1 - it.c0;
+  const int tiles_c = (ncol + G_TN - 1) / G_TN;
+  const int tr = local / tiles_c, tc = local - tr * tiles_c;
+  const int j0 = tr * G_TM, cb = it.c0 + tc * G_TN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[a][q] = T(0);
+
+  for (int l0 = 0; l0 < it.inner; l0 += G_TK) {
+    __syncthreads();
+    for (int e = tid; e < G_TM * G_TK; e += G_THREADS) {
+      int r = e / G_TK, l = e - r * G_TK;
+      int j = j0 + r, ll = l0 + l;
+      Ms[r][l] = (j < it.rows && ll < it.inner) ? mat_at(it, j, ll) : T(0);
+    }
+    for (int e = tid; e < G_TK * G_TN; e += G_THREADS) {
+      int l = e / G_TN, c = e - l * G_TN;
+      int ll = l0 + l, cc = cb + c;
+      T v = T(0);
+      if (ll < it.inner && cc < it.c1) v = src_row(it.Z, ll)[cc];
+      Zs[l][c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < G_TK; ++l) {
+      T a[4], z[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = Ms[ty * 4 + r][l];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) z[c] = Zs[l][tx * 4 + c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], z[c], acc[r][c]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    int j = j0 + ty * 4 + r;
+    if (j >= it.rows) continue;
+    const T* xr = it.X.p0 ? src_row(it.X, j) : nullptr;
+    T* o = it.out + (int64_t)j * it.ldo;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int cc = cb + tx * 4 + c;
+      if (cc >= it.c1) continue;
+      T v = it.sign * acc[r][c];
+      if (xr) v += xr[cc];
+      o[cc] = v;
+    }
+  }
+}
+
+template <typename T>
+__global__ void gather_batched_kernel(const T* __restrict__ A, int64_t lda,
+                                      const GatherItem<T>* __restrict__ items,
+                                      const int64_t* __restrict__ start, int nitems,
+                                      int64_t total) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  int lo = 0, hi = nitems - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  const GatherItem<T> it = items[lo];
+  int64_t e = t - start[lo];
+  int j = (int)(e / it.nc), l = (int)(e - (int64_t)j * it.nc);
+  it.out[e] = A[(int64_t)it.rows[j] * lda + it.cols[l]];
+}
+
+__global__ void index_compose_kernel(int32_t* out, const int32_t* base, const int32_t* idx,
+                                     int count) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) out[t] = base[idx[t]];
+}
+
+}  // namespace
+
+template <typename T>
+Err launch_gemm_batched(const std::vector<GemmItem<T>>& items, cudaStream_t s,
+                        void* scratch_dev, size_t scratch_bytes) {
+  std::vector<GemmItem<T>> live;
+  std::vector<int> starts;
+  int tiles = 0;
+  for (const auto& it : items) {
+    if (it.rows <= 0 || it.c1 <= it.c0) continue;
+    int tr = (it.rows + G_TM - 1) / G_TM, tc = (it.c1 - it.c0 + G_TN - 1) / G_TN;
+    live.push_back(it);
+    starts.push_back(tiles);
+    tiles += tr * tc;
+  }
+  if (live.empty()) return ok();
+  size_t bi = live.size() * sizeof(GemmItem<T>);
+  size_t bs = starts.size() * sizeof(int);
+  size_t off = (bi + 255) & ~size_t(255);
+  void* buf = scratch_dev;
+  bool own = false;
+  if (!buf || scratch_bytes < off + bs) {
+    HSS_TRY(dalloc(&buf, off + bs, s));
+    own = true;
+  }
+  HSS_CUDA_TRY(cudaMemcpyAsync(buf, live.data(), bi, cudaMemcpyHostToDevice, s));
+  HSS_CUDA_TRY(cudaMemcpyAsync((char*)buf + off, starts.data(), bs, cudaMemcpyHostToDevice, s));
+  gemm_batched_kernel<T><<<tiles, G_THREADS, 0, s>>>(
+      reinterpret_cast<const GemmItem<T>*>(buf), reinterpret_cast<const int*>((char*)buf + off),
+      (int)live.size());
+  Err e = check_launch("gemm_batched_kernel");
+  if (own) dfree(buf, s);
+  return e;
+}
+
+template <typename T>
+Err launch_gather_batched(const T* A, int64_t lda, const std::vector<GatherItem<T>>& items,
+                          cudaStream_t s, void* scratch_dev, size_t scratch_bytes) {
+  std::vector<GatherItem<T>> live;
+  std::vector<int64_t> starts;
+  int64_t total = 0;
+  for (const auto& it : items) {
+    if (it.nr <= 0 || it.nc <= 0) continue;
+    live.push_back(it);
+    starts.push_back(total);
+    total += (int64_t)it.nr * it.nc;
+  }
+  if (live.empty()) return ok();
+  size_t bi = live.size() * sizeof(GatherItem<T>);
+  size_t bs = starts.size() * sizeof(int64_t);
+  size_t off = (bi + 255) & ~size_t(255);
+  void* buf = scratch_dev;
+  bool own = false;
+  if (!buf || scratch_bytes < off + bs) {
+    HSS_TRY(dalloc(&buf, off + bs, s));
+    own = true;
+  }
+  HSS_CUDA_TRY(cudaMemcpyAsync(buf, live.data(), bi, cudaMemcpyHostToDevice, s));
+  HSS_CUDA_TRY(cudaMemcpyAsync((char*)buf + off, starts.data(), bs, cudaMemcpyHostToDevice, s));
+  gather_batched_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+      A, lda, reinterpret_cast<const GatherItem<T>*>(buf),
+      reinterpret_cast<const int64_t*>((char*)buf + off), (int)live.size(), total);
+  Err e = check_launch("gather_batched_kernel");
+  if (own) dfree(buf, s);
+  return e;
+}
+
+Err launch_index_compose(int32_t* out, const int32_t* base, const int32_t* idx, int count,
+                         cudaStream_t s) {
+  if (count <= 0) return ok();
+  index_compose_kernel<<<(count + 255) / 256, 256, 0, s>>>(out, base, idx, count);
+  return check_launch("index_compose_kernel");
+}
+
+template Err launch_gemm_batched<float>(const std::vector<GemmItem<float>>&, cudaStream_t, void*,
+                                        size_t);
+template Err launch_gemm_batched<double>(const std::vector<GemmItem<double>>&, cudaStream_t,
+                                         void*, size_t);
+template Err launch_gather_batched<float>(const float*, int64_t,
+                                          const std::vector<GatherItem<float>>&, cudaStream_t,
+                                          void*, size_t);
+template Err launch_gather_batched<double>(const double*, int64_t,
+                                           const std::vector<GatherItem<double>>&, cudaStream_t,
+                                           void*, size_t);
+
+}  // namespace hss

@@ -1,0 +1,217 @@
+// Fused sampling S^r = (A - D) R, S^c = (A - D)^T R (Section 2.2, step 2 of
+// the compression; Algorithm 1's leaf samples S^r(I,:) - D R(I,:)).
+//
+// One pass over A serves both products: a CTA owns a panel of BM rows and a
+// chunk of DC sample columns and walks every column tile of A once.  The row
+// sample of its panel is complete when the walk ends (accumulated on chip);
+// the column sample of each tile is a partial sum over the panel's rows and is
+// written to a slab of partial sums, which a second kernel reduces over the
+// panels in a fixed order (deterministic: no floating-point atomics).
+// Entries with leaf(i) == leaf(j) are masked to zero while A is staged, which
+// subtracts the leaf diagonal blocks D exactly (no cancellation).
+#include "hss_internal.cuh"
+
+#include <cuda_bf16.h>
+
+namespace hss {
+
+namespace {
+
+constexpr int S_BM = 128;   // panel rows
+constexpr int S_BK = 32;    // column tile of A
+constexpr int S_DC = 64;    // sample columns per CTA
+constexpr int S_THREADS = 256;
+
+// SIMT (FP32 or FP64 FMA) fused sampling.  Thread (ty, tx) of a 16 x 16 grid
+// owns an 8 x 4 block of the row sample and a 2 x 4 block of each column
+// tile's partial column sample.
+template <typename T>
+__global__ void __launch_bounds__(S_THREADS)
+sample_simt_kernel(const T* __restrict__ A, int64_t n, int64_t lda,
+                   const T* __restrict__ R, int64_t ldr, int64_t c0, int64_t ncols,
+                   int nchunk, T* __restrict__ Sr, int64_t lds,
+                   const int32_t* __restrict__ leaf_of, T* __restrict__ P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* As = reinterpret_cast<T*>(smem_raw);        // [S_BM][S_BK]
+  T* Rs = As + S_BM * S_BK;                       // [S_BK][S_DC]
+  T* Rp = Rs + S_BK * S_DC;                       // [S_BM][S_DC]
+  __shared__ int32_t leaf_rows[S_BM];
+  __shared__ int32_t leaf_cols[S_BK];
+
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int panel = blockIdx.x / nchunk;
+  const int chunk = blockIdx.x - panel * nchunk;
+  const int64_t i0 = (int64_t)panel * S_BM;
+  const int64_t cq = (int64_t)chunk * S_DC;          // offset inside [c0, c0+ncols)
+  const int cw = (int)(ncols - cq < (int64_t)S_DC ? ncols - cq : (int64_t)S_DC);  // live columns of this chunk
+
+  // panel rows of R (feed the column sample) and their leaf ids
+  for (int e = tid; e < S_BM * S_DC; e += S_THREADS) {
+    int r = e / S_DC, c = e - r * S_DC;
+    int64_t i = i0 + r;
+    Rp[e] = (i < n && c < cw) ? R[i * ldr + c0 + cq + c] : T(0);
+  }
+  for (int r = tid; r < S_BM; r += S_THREADS) {
+    int64_t i = i0 + r;
+    leaf_rows[r] = (leaf_of && i < n) ? leaf_of[i] : -1;
+  }
+
+  T acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+
+  T* Pp = P + (int64_t)blockIdx.x * n * S_DC;
+
+  for (int64_t j0 = 0; j0 < n; j0 += S_BK) {
+    __syncthreads();
+    for (int c = tid; c < S_BK; c += S_THREADS) {
+      int64_t j = j0 + c;
+      leaf_cols[c] = (leaf_of && j < n) ? leaf_of[j] : -2;
+    }
+    __syncthreads();
+    for (int e = tid; e < S_BM * S_BK; e += S_THREADS) {
+      int r = e / S_BK, c = e - r * S_BK;
+      int64_t i = i0 + r, j = j0 + c;
+      T v = T(0);
+      if (i < n && j < n && leaf_rows[r] != leaf_cols[c]) v = A[i * lda + j];
+      As[e] = v;
+    }
+    for (int e = tid; e < S_BK * S_DC; e += S_THREADS) {
+      int r = e / S_DC, c = e - r * S_DC;
+      int64_t j = j0 + r;
+      Rs[e] = (j < n && c < cw) ? R[j * ldr + c0 + cq + c] : T(0);
+    }
+    __syncthreads();
+    // row sample: acc += A_tile * R_tile
+#pragma unroll 4
+    for (int k = 0; k < S_BK; ++k) {
+      T a[8], b[4];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) a[r] = As[(ty * 8 + r) * S_BK + k];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Rs[k * S_DC + tx * 4 + c];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+    // column sample of this tile: pc = A_tile^T * R_panel
+    T pc[2][4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) pc[r][c] = T(0);
+#pragma unroll 4
+    for (int i = 0; i < S_BM; ++i) {
+      T a0 = As[i * S_BK + ty * 2], a1 = As[i * S_BK + ty * 2 + 1];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        T b = Rp[i * S_DC + tx * 4 + c];
+        pc[0][c] = fma(a0, b, pc[0][c]);
+        pc[1][c] = fma(a1, b, pc[1][c]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      int64_t j = j0 + ty * 2 + r;
+      if (j < n) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Pp[j * S_DC + tx * 4 + c] = pc[r][c];
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    int64_t i = i0 + ty * 8 + r;
+    if (i >= n) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int cc = tx * 4 + c;
+      if (cc < cw) Sr[i * lds + c0 + cq + cc] = acc[r][c];
+    }
+  }
+}
+
+// Sc[j][c0 + q*DC + cc] = sum over panels p (in order) of P[p][q][j][cc]
+template <typename T>
+__global__ void reduce_partials_kernel(const T* __restrict__ P, int64_t n, int npanel, int nchunk,
+                                       int64_t c0, int64_t ncols, T* __restrict__ Sc, int64_t lds) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t total = (int64_t)nchunk * n * S_DC;
+  if (t >= total) return;
+  int q = (int)(t / (n * S_DC));
+  int64_t rem = t - (int64_t)q * n * S_DC;
+  int64_t j = rem / S_DC;
+  int cc = (int)(rem - j * S_DC);
+  int64_t col = (int64_t)q * S_DC + cc;
+  if (col >= ncols) return;
+  T s = T(0);
+  for (int p = 0; p < npanel; ++p) s += P[((int64_t)p * nchunk + q) * n * S_DC + j * S_DC + cc];
+  Sc[j * lds + c0 + col] = s;
+}
+
+}  // namespace
+
+size_t sample_scratch_bytes(int64_t n, int64_t ncols, int mode, bool f64) {
+  (void)mode;
+  int64_t npanel = (n + S_BM - 1) / S_BM;
+  int64_t nchunk = (ncols + S_DC - 1) / S_DC;
+  return (size_t)npanel * nchunk * n * S_DC * (f64 ? 8 : 4);
+}
+
+template <typename T>
+Err launch_sample(const T* A, int64_t n, int64_t lda, const T* R, int64_t ldr, int64_t c0,
+                  int64_t c1, T* Sr, T* Sc, int64_t lds, const int32_t* leaf_of, int mode,
+                  SampleScratch* scratch, cudaStream_t s, float* ms_out) {
+  (void)mode;
+  int64_t ncols = c1 - c0;
+  if (n <= 0 || ncols <= 0) return ok();
+  const bool f64 = sizeof(T) == 8;
+  size_t need = sample_scratch_bytes(n, ncols, mode, f64);
+  if (scratch->bytes < need) {
+    dfree(scratch->part, s);
+    scratch->part = nullptr;
+    scratch->bytes = 0;
+    HSS_TRY(dalloc(&scratch->part, need, s));
+    scratch->bytes = need;
+  }
+  int npanel = (int)((n + S_BM - 1) / S_BM);
+  int nchunk = (int)((ncols + S_DC - 1) / S_DC);
+  size_t smem = sizeof(T) * (S_BM * S_BK + S_BK * S_DC + S_BM * S_DC);
+  HSS_CUDA_TRY(cudaFuncSetAttribute(sample_simt_kernel<T>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ms_out) {
+    HSS_CUDA_TRY(cudaEventCreate(&e0));
+    HSS_CUDA_TRY(cudaEventCreate(&e1));
+    HSS_CUDA_TRY(cudaEventRecord(e0, s));
+  }
+  T* P = reinterpret_cast<T*>(scratch->part);
+  sample_simt_kernel<T><<<npanel * nchunk, S_THREADS, smem, s>>>(
+      A, n, lda, R, ldr, c0, ncols, nchunk, Sr, lds, leaf_of, P);
+  HSS_TRY(check_launch("sample_simt_kernel"));
+  int64_t total = (int64_t)nchunk * n * S_DC;
+  reduce_partials_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+      P, n, npanel, nchunk, c0, ncols, Sc, lds);
+  HSS_TRY(check_launch("reduce_partials_kernel"));
+  if (ms_out) {
+    HSS_CUDA_TRY(cudaEventRecord(e1, s));
+    HSS_CUDA_TRY(cudaEventSynchronize(e1));
+    HSS_CUDA_TRY(cudaEventElapsedTime(ms_out, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  return ok();
+}
+
+template Err launch_sample<float>(const float*, int64_t, int64_t, const float*, int64_t, int64_t,
+                                  int64_t, float*, float*, int64_t, const int32_t*, int,
+                                  SampleScratch*, cudaStream_t, float*);
+template Err launch_sample<double>(const double*, int64_t, int64_t, const double*, int64_t,
+                                   int64_t, int64_t, double*, double*, int64_t, const int32_t*,
+                                   int, SampleScratch*, cudaStream_t, float*);
+
+}  // namespace hss

@@ -1,0 +1,762 @@
+// ULV-like factorization (Algorithm 3) and solution (Algorithm 4, Appendix A)
+// of a compressed HSS form, in FP64 whatever the input precision.
+//
+// Factorization, one CTA per node, level by level (deepest first):
+//   D_tau  = A(I,I) at a leaf, [Dtil_1, B12 Vtb_2^T; B21 Vtb_1^T, Dtil_2] above;
+//   Vhat   = V at a leaf, diag(Vtb_1, Vtb_2) V above;
+//   W      = Omega D_tau with Omega = [-E I; I 0] Pi^T (Omega U = [0; I]);
+//   LQ of the top r = m - k rows of W by Householder reflectors applied from
+//   the right to every row of W, so W_t Q^T = [L 0] and W_b Q^T = [W_b Q_t^T,
+//   Dtil];  Vtilde = Q Vhat.   Root: LU with partial pivoting of D_0.
+// Solve: upward sweep b_tau -> btilde = Omega b -> y = L^{-1} btilde_t,
+// z = Vtt^T y (+ V^T [z_1; z_2]); root LU solve; downward sweep
+// x_child = Q_child^T [y_child; x_parent part].
+#include "hss_internal.cuh"
+#include "hss_tree.h"
+
+#include <algorithm>
+#include <climits>
+
+using namespace hss;
+
+namespace hss {
+namespace {
+
+constexpr int U_THREADS = 256;
+constexpr int U_WARPS = U_THREADS / 32;
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ double block_sum(double v, double* red) {
+  v = wsum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < U_WARPS; ++q) s += red[q];
+  return s;
+}
+
+__device__ __forceinline__ double ld_any(const void* p, int64_t i, int f64) {
+  return f64 ? reinterpret_cast<const double*>(p)[i] : (double)reinterpret_cast<const float*>(p)[i];
+}
+
+struct FacItem {
+  int m, k, kc, mc, leaf, root;
+  const void* D;          // leaf block (input dtype), ld m
+  const double* Dtil1;
+  const double* Dtil2;
+  const double* Vtb1;
+  const double* Vtb2;
+  int k1, k2, kc1, kc2;
+  const void* B12;        // k1 x kc2
+  const void* B21;        // k2 x kc1
+  const int32_t* permr;
+  const double* Er;
+  const int32_t* permc;
+  const double* Ec;
+  double* hv;
+  double* tau;
+  double* L;
+  double* WbQt;
+  double* Dtil;
+  double* Vtt;
+  double* Vtb;
+  double* Dw;     // m x m scratch
+  double* W;      // m x m scratch
+  double* Vh;     // m x kc scratch
+  double* Vd;     // mc x kc scratch
+  int32_t* piv;   // root
+  int32_t* status;
+};
+
+__global__ void __launch_bounds__(U_THREADS) ulv_factor_kernel(const FacItem* items, int f64) {
+  extern __shared__ double vsh[];
+  __shared__ double red[U_WARPS];
+  __shared__ double redv[U_WARPS];
+  __shared__ int redi[U_WARPS];
+  const FacItem it = items[blockIdx.x];
+  const int m = it.m, k = it.k, r = m - k, kc = it.kc;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* Dw = it.Dw;
+  // 1. D_tau
+  for (int64_t e = tid; e < (int64_t)m * m; e += U_THREADS) {
+    int i = (int)(e / m), j = (int)(e - (int64_t)i * m);
+    double v;
+    if (it.leaf) {
+      v = ld_any(it.D, e, f64);
+    } else {
+      const int k1 = it.k1;
+      if (i < k1 && j < k1) v = it.Dtil1[i * k1 + j];
+      else if (i >= k1 && j >= k1) v = it.Dtil2[(i - k1) * it.k2 + (j - k1)];
+      else if (i < k1) {   // B12 Vtb_2^T
+        v = 0.0;
+        for (int l = 0; l < it.kc2; ++l)
+          v = fma(ld_any(it.B12, (int64_t)i * it.kc2 + l, f64), it.Vtb2[(j - k1) * it.kc2 + l], v);
+      } else {             // B21 Vtb_1^T
+        v = 0.0;
+        for (int l = 0; l < it.kc1; ++l)
+          v = fma(ld_any(it.B21, (int64_t)(i - k1) * it.kc1 + l, f64), it.Vtb1[j * it.kc1 + l], v);
+      }
+    }
+    Dw[e] = v;
+  }
+  __syncthreads();
+  if (it.root) {
+    // LU with partial pivoting, lowest index on ties
+    for (int i = 0; i < m; ++i) {
+      double bv = -1.0;
+      int bi = INT_MAX;
+      for (int j = i + tid; j < m; j += U_THREADS) {
+        double x = fabs(Dw[(int64_t)j * m + i]);
+        if (x > bv) {
+          bv = x;
+          bi = j;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) {
+          bv = ov;
+          bi = oi;
+        }
+      }
+      __syncthreads();
+      if (lane == 0) {
+        redv[warp] = bv;
+        redi[warp] = bi;
+      }
+      __syncthreads();
+      bv = redv[0];
+      bi = redi[0];
+      for (int q = 1; q < U_WARPS; ++q)
+        if (redv[q] > bv || (redv[q] == bv && redi[q] < bi)) {
+          bv = redv[q];
+          bi = redi[q];
+        }
+      if (bv == 0.0) {
+        if (tid == 0) *it.status = HSS_ERR_SINGULAR;
+        return;
+      }
+      if (bi != i)
+        for (int c = tid; c < m; c += U_THREADS) {
+          double t = Dw[(int64_t)i * m + c];
+          Dw[(int64_t)i * m + c] = Dw[(int64_t)bi * m + c];
+          Dw[(int64_t)bi * m + c] = t;
+        }
+      if (tid == 0) it.piv[i] = bi;
+      __syncthreads();
+      const double piv = Dw[(int64_t)i * m + i];
+      for (int j = i + 1 + warp; j < m; j += U_WARPS) {
+        double l = Dw[(int64_t)j * m + i] / piv;
+        for (int c = i + 1 + lane; c < m; c += 32)
+          Dw[(int64_t)j * m + c] = fma(-l, Dw[(int64_t)i * m + c], Dw[(int64_t)j * m + c]);
+        if (lane == 0) Dw[(int64_t)j * m + i] = l;
+      }
+      __syncthreads();
+    }
+    return;
+  }
+  // 2. Vhat
+  double* Vd = it.leaf ? it.Vh : it.Vd;
+  const int mc = it.mc;
+  for (int64_t e = tid; e < (int64_t)mc * kc; e += U_THREADS) Vd[e] = 0.0;
+  __syncthreads();
+  for (int l = tid; l < kc; l += U_THREADS) Vd[(int64_t)it.permc[l] * kc + l] = 1.0;
+  for (int64_t e = tid; e < (int64_t)(mc - kc) * kc; e += U_THREADS) {
+    int q = (int)(e / kc), l = (int)(e - (int64_t)q * kc);
+    Vd[(int64_t)it.permc[kc + q] * kc + l] = it.Ec[e];
+  }
+  __syncthreads();
+  if (!it.leaf) {
+    for (int64_t e = tid; e < (int64_t)m * kc; e += U_THREADS) {
+      int i = (int)(e / kc), l = (int)(e - (int64_t)i * kc);
+      double v = 0.0;
+      if (i < it.k1) {
+        for (int q = 0; q < it.kc1; ++q) v = fma(it.Vtb1[i * it.kc1 + q], Vd[(int64_t)q * kc + l], v);
+      } else {
+        int ii = i - it.k1;
+        for (int q = 0; q < it.kc2; ++q)
+          v = fma(it.Vtb2[ii * it.kc2 + q], Vd[(int64_t)(it.kc1 + q) * kc + l], v);
+      }
+      it.Vh[e] = v;
+    }
+  }
+  // 3. W = Omega D
+  double* W = it.W;
+  for (int64_t e = tid; e < (int64_t)m * m; e += U_THREADS) {
+    int i = (int)(e / m), j = (int)(e - (int64_t)i * m);
+    double v;
+    if (i < r) {
+      v = Dw[(int64_t)it.permr[k + i] * m + j];
+      for (int l = 0; l < k; ++l) v = fma(-it.Er[(int64_t)i * k + l], Dw[(int64_t)it.permr[l] * m + j], v);
+    } else {
+      v = Dw[(int64_t)it.permr[i - r] * m + j];
+    }
+    W[e] = v;
+  }
+  __syncthreads();
+  // 4. LQ of the top r rows, reflectors applied to every row of W
+  for (int i = 0; i < r; ++i) {
+    double* wi = W + (int64_t)i * m;
+    double sa = 0.0, st = 0.0;
+    for (int c = i + tid; c < m; c += U_THREADS) {
+      double x = wi[c];
+      sa = fma(x, x, sa);
+      if (c > i) st = fma(x, x, st);
+    }
+    sa = block_sum(sa, red);
+    st = block_sum(st, red);
+    const double alpha = wi[i];
+    const double sigma = sqrt(sa);
+    double tau, beta, scal;
+    if (st == 0.0) {
+      tau = 0.0;
+      beta = alpha;
+      scal = 0.0;
+    } else {
+      beta = -copysign(sigma, alpha);
+      tau = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+    }
+    for (int c = tid; c < m; c += U_THREADS) {
+      double v = c < i ? 0.0 : (c == i ? 1.0 : wi[c] * scal);
+      vsh[c] = v;
+      it.hv[(int64_t)i * m + c] = v;
+    }
+    __syncthreads();
+    for (int c = i + tid; c < m; c += U_THREADS) wi[c] = c == i ? beta : 0.0;
+    if (tid == 0) it.tau[i] = tau;
+    for (int j = i + 1 + warp; j < m; j += U_WARPS) {
+      double* wj = W + (int64_t)j * m;
+      double dot = 0.0;
+      for (int c = i + lane; c < m; c += 32) dot = fma(wj[c], vsh[c], dot);
+      dot = wsum(dot) * tau;
+      for (int c = i + lane; c < m; c += 32) wj[c] = fma(-dot, vsh[c], wj[c]);
+    }
+    __syncthreads();
+  }
+  for (int64_t e = tid; e < (int64_t)r * r; e += U_THREADS) {
+    int i = (int)(e / r), j = (int)(e - (int64_t)i * r);
+    it.L[e] = j <= i ? W[(int64_t)i * m + j] : 0.0;
+  }
+  for (int64_t e = tid; e < (int64_t)k * r; e += U_THREADS) {
+    int l = (int)(e / r), j = (int)(e - (int64_t)l * r);
+    it.WbQt[e] = W[(int64_t)(r + l) * m + j];
+  }
+  for (int64_t e = tid; e < (int64_t)k * k; e += U_THREADS) {
+    int l = (int)(e / k), j = (int)(e - (int64_t)l * k);
+    it.Dtil[e] = W[(int64_t)(r + l) * m + r + j];
+  }
+  __syncthreads();
+  // 5. Vtilde = Q Vhat = H_{r-1} ... H_0 Vhat (H_0 first), one thread per column
+  for (int l = tid; l < kc; l += U_THREADS) {
+    double* vh = it.Vh;
+    for (int i = 0; i < r; ++i) {
+      const double* h = it.hv + (int64_t)i * m;
+      double dot = 0.0;
+      for (int c = i; c < m; ++c) dot = fma(h[c], vh[(int64_t)c * kc + l], dot);
+      dot *= it.tau[i];
+      for (int c = i; c < m; ++c) vh[(int64_t)c * kc + l] = fma(-dot, h[c], vh[(int64_t)c * kc + l]);
+    }
+    for (int i = 0; i < m; ++i) {
+      double v = vh[(int64_t)i * kc + l];
+      if (i < r) it.Vtt[(int64_t)i * kc + l] = v;
+      else it.Vtb[(int64_t)(i - r) * kc + l] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- solve
+struct SolItem {
+  int m, k, kc, mc, leaf, root, lo, nrhs;
+  const void* Bin;   // leaf rhs rows (input dtype), ld ldb
+  int64_t ldb;
+  // children data (non-leaf)
+  const double* btb1;
+  const double* btb2;
+  const double* y1;
+  const double* y2;
+  const double* z1;
+  const double* z2;
+  const double* WbQt1;
+  const double* WbQt2;
+  int k1, k2, kc1, kc2, r1, r2;
+  const void* B12;
+  const void* B21;
+  // this node
+  const int32_t* permr;
+  const double* Er;
+  const int32_t* permc;
+  const double* Ec;
+  const double* L;
+  const double* Vtt;
+  const double* lu;
+  const int32_t* piv;
+  double* b;     // m x nrhs scratch
+  double* btb;   // k x nrhs out
+  double* y;     // r x nrhs out
+  double* z;     // kc x nrhs out
+  double* x;     // root: m x nrhs out
+};
+
+__global__ void __launch_bounds__(U_THREADS) ulv_solve_up_kernel(const SolItem* items, int f64) {
+  const SolItem it = items[blockIdx.x];
+  const int m = it.m, k = it.k, r = m - k, kc = it.kc, nr = it.nrhs;
+  const int tid = threadIdx.x;
+  double* b = it.b;
+  for (int64_t e = tid; e < (int64_t)m * nr; e += U_THREADS) {
+    int i = (int)(e / nr), c = (int)(e - (int64_t)i * nr);
+    double v;
+    if (it.leaf) {
+      v = ld_any(it.Bin, (int64_t)(it.lo + i) * it.ldb + c, f64);
+    } else if (i < it.k1) {
+      v = it.btb1[(int64_t)i * nr + c];
+      for (int q = 0; q < it.r1; ++q) v = fma(-it.WbQt1[(int64_t)i * it.r1 + q], it.y1[(int64_t)q * nr + c], v);
+      for (int l = 0; l < it.kc2; ++l)
+        v = fma(-ld_any(it.B12, (int64_t)i * it.kc2 + l, f64), it.z2[(int64_t)l * nr + c], v);
+    } else {
+      int ii = i - it.k1;
+      v = it.btb2[(int64_t)ii * nr + c];
+      for (int l = 0; l < it.kc1; ++l)
+        v = fma(-ld_any(it.B21, (int64_t)ii * it.kc1 + l, f64), it.z1[(int64_t)l * nr + c], v);
+      for (int q = 0; q < it.r2; ++q) v = fma(-it.WbQt2[(int64_t)ii * it.r2 + q], it.y2[(int64_t)q * nr + c], v);
+    }
+    b[e] = v;
+  }
+  __syncthreads();
+  if (it.root) {
+    for (int c = tid; c < nr; c += U_THREADS) {
+      double* x = it.x;
+      for (int i = 0; i < m; ++i) x[(int64_t)i * nr + c] = b[(int64_t)i * nr + c];
+      for (int i = 0; i < m; ++i) {
+        int p = it.piv[i];
+        if (p != i) {
+          double t = x[(int64_t)i * nr + c];
+          x[(int64_t)i * nr + c] = x[(int64_t)p * nr + c];
+          x[(int64_t)p * nr + c] = t;
+        }
+      }
+      for (int i = 0; i < m; ++i) {
+        double v = x[(int64_t)i * nr + c];
+        for (int j = 0; j < i; ++j) v = fma(-it.lu[(int64_t)i * m + j], x[(int64_t)j * nr + c], v);
+        x[(int64_t)i * nr + c] = v;
+      }
+      for (int i = m - 1; i >= 0; --i) {
+        double v = x[(int64_t)i * nr + c];
+        for (int j = i + 1; j < m; ++j) v = fma(-it.lu[(int64_t)i * m + j], x[(int64_t)j * nr + c], v);
+        x[(int64_t)i * nr + c] = v / it.lu[(int64_t)i * m + i];
+      }
+    }
+    return;
+  }
+  // btilde = Omega b: top r rows -> y (before the solve), bottom k rows -> btb
+  for (int64_t e = tid; e < (int64_t)m * nr; e += U_THREADS) {
+    int i = (int)(e / nr), c = (int)(e - (int64_t)i * nr);
+    if (i < r) {
+      double v = b[(int64_t)it.permr[k + i] * nr + c];
+      for (int l = 0; l < k; ++l) v = fma(-it.Er[(int64_t)i * k + l], b[(int64_t)it.permr[l] * nr + c], v);
+      it.y[(int64_t)i * nr + c] = v;
+    } else {
+      it.btb[(int64_t)(i - r) * nr + c] = b[(int64_t)it.permr[i - r] * nr + c];
+    }
+  }
+  __syncthreads();
+  // y = L^{-1} btilde_t
+  for (int c = tid; c < nr; c += U_THREADS) {
+    for (int i = 0; i < r; ++i) {
+      double v = it.y[(int64_t)i * nr + c];
+      for (int j = 0; j < i; ++j) v = fma(-it.L[(int64_t)i * r + j], it.y[(int64_t)j * nr + c], v);
+      it.y[(int64_t)i * nr + c] = v / it.L[(int64_t)i * r + i];
+    }
+  }
+  __syncthreads();
+  // z = Vtt^T y (+ V^T [z1; z2])
+  for (int64_t e = tid; e < (int64_t)kc * nr; e += U_THREADS) {
+    int l = (int)(e / nr), c = (int)(e - (int64_t)l * nr);
+    double v = 0.0;
+    for (int q = 0; q < r; ++q) v = fma(it.Vtt[(int64_t)q * kc + l], it.y[(int64_t)q * nr + c], v);
+    if (!it.leaf) {
+      auto zrow = [&](int row) -> double {
+        return row < it.kc1 ? it.z1[(int64_t)row * nr + c] : it.z2[(int64_t)(row - it.kc1) * nr + c];
+      };
+      v += zrow(it.permc[l]);
+      for (int q = 0; q < it.mc - kc; ++q) v = fma(it.Ec[(int64_t)q * kc + l], zrow(it.permc[kc + q]), v);
+    }
+    it.z[e] = v;
+  }
+}
+
+struct DownItem {
+  int m, r, nrhs, leaf, lo;   // child: m rows, r reflectors
+  const double* y;            // r x nrhs
+  const double* xp;           // parent part: (m - r) x nrhs
+  const double* hv;
+  const double* tau;
+  double* x;                  // m x nrhs (non-leaf child) -- or
+  void* Xout;                 // leaf child: output rows
+  int64_t ldx;
+};
+
+__global__ void __launch_bounds__(U_THREADS) ulv_solve_down_kernel(const DownItem* items, int f64) {
+  const DownItem it = items[blockIdx.x];
+  const int m = it.m, r = it.r, nr = it.nrhs;
+  for (int c = threadIdx.x; c < nr; c += U_THREADS) {
+    double* v = it.x;   // m x nrhs scratch (also for leaves)
+    for (int i = 0; i < m; ++i)
+      v[(int64_t)i * nr + c] = i < r ? it.y[(int64_t)i * nr + c] : it.xp[(int64_t)(i - r) * nr + c];
+    for (int i = r - 1; i >= 0; --i) {   // Q^T = H_0 H_1 ... H_{r-1}
+      const double* h = it.hv + (int64_t)i * m;
+      double dot = 0.0;
+      for (int q = i; q < m; ++q) dot = fma(h[q], v[(int64_t)q * nr + c], dot);
+      dot *= it.tau[i];
+      for (int q = i; q < m; ++q) v[(int64_t)q * nr + c] = fma(-dot, h[q], v[(int64_t)q * nr + c]);
+    }
+    if (it.leaf) {
+      for (int i = 0; i < m; ++i) {
+        double val = v[(int64_t)i * nr + c];
+        int64_t o = (int64_t)(it.lo + i) * it.ldx + c;
+        if (f64) reinterpret_cast<double*>(it.Xout)[o] = val;
+        else reinterpret_cast<float*>(it.Xout)[o] = (float)val;
+      }
+    }
+  }
+}
+
+__global__ void copy_out_kernel(const double* x, int m, int nr, void* X, int64_t ldx, int f64) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)m * nr) return;
+  int i = (int)(e / nr), c = (int)(e - (int64_t)i * nr);
+  if (f64) reinterpret_cast<double*>(X)[(int64_t)i * ldx + c] = x[e];
+  else reinterpret_cast<float*>(X)[(int64_t)i * ldx + c] = (float)x[e];
+}
+
+template <typename TI>
+Err upload_and_launch(const std::vector<TI>& items, cudaStream_t s, TI** dev) {
+  HSS_TRY(dalloc_t(dev, std::max<size_t>(items.size(), 1), s));
+  HSS_CUDA_TRY(cudaMemcpyAsync(*dev, items.data(), items.size() * sizeof(TI),
+                               cudaMemcpyHostToDevice, s));
+  return ok();
+}
+
+}  // namespace
+}  // namespace hss
+
+// ---------------------------------------------------------------- factor
+extern "C" hss_status hss_factor(hss_t h, void* stream) {
+  if (!h) return HSS_ERR_INVALID;
+  if (h->gen.empty() || h->gen[0].state != NODE_COMPRESSED) {
+    h->err = "hss_factor: the handle holds no complete compressed form";
+    return HSS_ERR_STATE;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  h->ulv.release(s);
+  const Tree& tr = h->tree;
+  const int nn = (int)tr.nodes.size();
+  const int f64 = h->dtype == HSS_F64;
+  UlvFactors& F = h->ulv;
+  F.nodes.assign(nn, UlvNode{});
+  // sizes: m = leaf size or k(c1) + k(c2); r = m - kr; kc
+  std::vector<size_t> off(nn + 1, 0);
+  size_t tot = 0;
+  auto m_of = [&](int id) {
+    const TNode& nd = tr.nodes[id];
+    return nd.c1 < 0 ? nd.hi - nd.lo : h->gen[nd.c1].kr + h->gen[nd.c2].kr;
+  };
+  for (int id = 0; id < nn; ++id) {
+    UlvNode& u = F.nodes[id];
+    u.m = m_of(id);
+    off[id] = tot;
+    if (id == 0) {
+      tot += (size_t)u.m * u.m + (u.m + 1) / 2 + 1;   // LU + pivots (int32 packed)
+      continue;
+    }
+    const NodeGen& g = h->gen[id];
+    u.k = g.kr;
+    u.kc = g.kc;
+    int r = u.m - u.k;
+    tot += (size_t)r * u.m + r + (size_t)r * r + (size_t)u.k * r + (size_t)u.k * u.k +
+           (size_t)r * u.kc + (size_t)u.k * u.kc;
+  }
+  double* blk = nullptr;
+  Err e = dalloc_t(&blk, std::max<size_t>(tot, 1), s);
+  if (e.st) {
+    h->err = e.msg;
+    return e.st;
+  }
+  F.block = blk;
+  F.bytes = tot * sizeof(double);
+  for (int id = 0; id < nn; ++id) {
+    UlvNode& u = F.nodes[id];
+    double* p = blk + off[id];
+    if (id == 0) {
+      F.root_m = u.m;
+      F.root_lu = p;
+      F.root_piv = reinterpret_cast<int32_t*>(p + (size_t)u.m * u.m);
+      continue;
+    }
+    int r = u.m - u.k;
+    u.hv = p;
+    p += (size_t)r * u.m;
+    u.tau = p;
+    p += r;
+    u.L = p;
+    p += (size_t)r * r;
+    u.WbQt = p;
+    p += (size_t)u.k * r;
+    u.Dtil = p;
+    p += (size_t)u.k * u.k;
+    u.Vtt = p;
+    p += (size_t)r * u.kc;
+    u.Vtb = p;
+  }
+  int32_t* status = nullptr;
+  e = dalloc_t(&status, 1, s);
+  if (e.st == HSS_OK) e = cudaMemsetAsync(status, 0, 4, s) == cudaSuccess ? ok() : fail(HSS_ERR_CUDA, "memset");
+  for (int depth = tr.maxdepth; depth >= 0 && e.st == HSS_OK; --depth) {
+    std::vector<FacItem> items;
+    size_t scratch = 0;
+    int maxm = 1;
+    for (int id : tr.levels[depth]) {
+      const UlvNode& u = F.nodes[id];
+      const NodeGen& g = h->gen[id];
+      scratch += 2 * (size_t)u.m * u.m + (size_t)u.m * std::max(u.kc, 1) +
+                 (size_t)std::max(g.mc, 1) * std::max(u.kc, 1);
+      maxm = std::max(maxm, u.m);
+    }
+    double* sc = nullptr;
+    e = dalloc_t(&sc, std::max<size_t>(scratch, 1), s);
+    if (e.st) break;
+    size_t so = 0;
+    for (int id : tr.levels[depth]) {
+      const TNode& nd = tr.nodes[id];
+      const UlvNode& u = F.nodes[id];
+      const NodeGen& g = h->gen[id];
+      FacItem it{};
+      it.m = u.m;
+      it.k = u.k;
+      it.kc = u.kc;
+      it.mc = g.mc;
+      it.leaf = nd.c1 < 0;
+      it.root = id == 0;
+      it.D = g.D;
+      if (!it.leaf) {
+        const UlvNode& a = F.nodes[nd.c1];
+        const UlvNode& b = F.nodes[nd.c2];
+        it.Dtil1 = a.Dtil;
+        it.Dtil2 = b.Dtil;
+        it.Vtb1 = a.Vtb;
+        it.Vtb2 = b.Vtb;
+        it.k1 = a.k;
+        it.k2 = b.k;
+        it.kc1 = a.kc;
+        it.kc2 = b.kc;
+        it.B12 = g.B12;
+        it.B21 = g.B21;
+      }
+      it.permr = g.permr;
+      it.Er = g.Er;
+      it.permc = g.permc;
+      it.Ec = g.Ec;
+      it.hv = u.hv;
+      it.tau = u.tau;
+      it.L = u.L;
+      it.WbQt = u.WbQt;
+      it.Dtil = u.Dtil;
+      it.Vtt = u.Vtt;
+      it.Vtb = u.Vtb;
+      it.Dw = it.root ? F.root_lu : sc + so;
+      so += (size_t)u.m * u.m;
+      it.W = sc + so;
+      so += (size_t)u.m * u.m;
+      it.Vh = sc + so;
+      so += (size_t)u.m * std::max(u.kc, 1);
+      it.Vd = sc + so;
+      so += (size_t)std::max(g.mc, 1) * std::max(u.kc, 1);
+      it.piv = F.root_piv;
+      it.status = status;
+      items.push_back(it);
+    }
+    FacItem* dev = nullptr;
+    e = upload_and_launch(items, s, &dev);
+    if (e.st == HSS_OK) {
+      size_t smem = sizeof(double) * maxm;
+      if (cudaFuncSetAttribute(ulv_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem) != cudaSuccess)
+        e = fail(HSS_ERR_CUDA, "ulv_factor_kernel smem attribute");
+      else {
+        ulv_factor_kernel<<<(unsigned)items.size(), U_THREADS, smem, s>>>(dev, f64);
+        e = check_launch("ulv_factor_kernel");
+      }
+    }
+    dfree(dev, s);
+    dfree(sc, s);
+  }
+  int32_t st = 0;
+  if (e.st == HSS_OK) {
+    cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) e = fail(HSS_ERR_CUDA, "hss_factor: sync");
+  }
+  dfree(status, s);
+  if (e.st == HSS_OK && st != 0) e = fail(HSS_ERR_SINGULAR, "hss_factor: zero pivot in the root LU");
+  if (e.st != HSS_OK) {
+    h->err = e.msg;
+    F.release(s);
+    return e.st;
+  }
+  F.done = true;
+  h->info.factored = 1;
+  h->info.bytes_ulv = (int64_t)F.bytes;
+  return HSS_OK;
+}
+
+// ----------------------------------------------------------------- solve
+extern "C" hss_status hss_solve(hss_t h, const void* B, int64_t ldb, int64_t nrhs, void* X,
+                                int64_t ldx, void* stream) {
+  if (!h) return HSS_ERR_INVALID;
+  if (!h->ulv.done) {
+    h->err = "hss_solve: hss_factor has not run on this handle";
+    return HSS_ERR_STATE;
+  }
+  if (!B || !X || nrhs < 0 || ldb < nrhs || ldx < nrhs || nrhs > INT32_MAX) {
+    h->err = "hss_solve: bad B, X, nrhs or leading dimension";
+    return HSS_ERR_INVALID;
+  }
+  if (nrhs == 0) return HSS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Tree& tr = h->tree;
+  const int nn = (int)tr.nodes.size();
+  const int f64 = h->dtype == HSS_F64;
+  const int nr = (int)nrhs;
+  const UlvFactors& F = h->ulv;
+  // per node: b (m), btb (k), y (r), z (kc), x (m) -- all x nrhs
+  std::vector<size_t> ob(nn), obt(nn), oy(nn), oz(nn), ox(nn);
+  size_t tot = 0;
+  for (int id = 0; id < nn; ++id) {
+    const UlvNode& u = F.nodes[id];
+    int r = u.m - u.k;
+    ob[id] = tot;
+    tot += (size_t)u.m * nr;
+    obt[id] = tot;
+    tot += (size_t)u.k * nr;
+    oy[id] = tot;
+    tot += (size_t)r * nr;
+    oz[id] = tot;
+    tot += (size_t)u.kc * nr;
+    ox[id] = tot;
+    tot += (size_t)u.m * nr;
+  }
+  double* buf = nullptr;
+  Err e = dalloc_t(&buf, std::max<size_t>(tot, 1), s);
+  for (int depth = tr.maxdepth; depth >= 0 && e.st == HSS_OK; --depth) {
+    std::vector<SolItem> items;
+    for (int id : tr.levels[depth]) {
+      const TNode& nd = tr.nodes[id];
+      const UlvNode& u = F.nodes[id];
+      const NodeGen& g = h->gen[id];
+      SolItem it{};
+      it.m = u.m;
+      it.k = u.k;
+      it.kc = u.kc;
+      it.mc = g.mc;
+      it.leaf = nd.c1 < 0;
+      it.root = id == 0;
+      it.lo = nd.lo;
+      it.nrhs = nr;
+      it.Bin = B;
+      it.ldb = ldb;
+      if (!it.leaf) {
+        const UlvNode& a = F.nodes[nd.c1];
+        const UlvNode& b = F.nodes[nd.c2];
+        it.btb1 = buf + obt[nd.c1];
+        it.btb2 = buf + obt[nd.c2];
+        it.y1 = buf + oy[nd.c1];
+        it.y2 = buf + oy[nd.c2];
+        it.z1 = buf + oz[nd.c1];
+        it.z2 = buf + oz[nd.c2];
+        it.WbQt1 = a.WbQt;
+        it.WbQt2 = b.WbQt;
+        it.k1 = a.k;
+        it.k2 = b.k;
+        it.kc1 = a.kc;
+        it.kc2 = b.kc;
+        it.r1 = a.m - a.k;
+        it.r2 = b.m - b.k;
+        it.B12 = g.B12;
+        it.B21 = g.B21;
+      }
+      it.permr = g.permr;
+      it.Er = g.Er;
+      it.permc = g.permc;
+      it.Ec = g.Ec;
+      it.L = u.L;
+      it.Vtt = u.Vtt;
+      it.lu = F.root_lu;
+      it.piv = F.root_piv;
+      it.b = buf + ob[id];
+      it.btb = buf + obt[id];
+      it.y = buf + oy[id];
+      it.z = buf + oz[id];
+      it.x = buf + ox[id];
+      items.push_back(it);
+    }
+    SolItem* dev = nullptr;
+    e = upload_and_launch(items, s, &dev);
+    if (e.st == HSS_OK) {
+      ulv_solve_up_kernel<<<(unsigned)items.size(), U_THREADS, 0, s>>>(dev, f64);
+      e = check_launch("ulv_solve_up_kernel");
+    }
+    dfree(dev, s);
+  }
+  if (e.st == HSS_OK && nn == 1) {
+    int m = F.nodes[0].m;
+    int64_t total = (int64_t)m * nr;
+    copy_out_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(buf + ox[0], m, nr, X, ldx, f64);
+    e = check_launch("copy_out_kernel");
+  }
+  for (int depth = 0; depth < tr.maxdepth && e.st == HSS_OK; ++depth) {
+    std::vector<DownItem> items;
+    for (int id : tr.levels[depth]) {
+      const TNode& nd = tr.nodes[id];
+      if (nd.c1 < 0) continue;
+      const int ka = F.nodes[nd.c1].k;
+      for (int side = 0; side < 2; ++side) {
+        int c = side ? nd.c2 : nd.c1;
+        const UlvNode& u = F.nodes[c];
+        const TNode& cn = tr.nodes[c];
+        DownItem it{};
+        it.m = u.m;
+        it.r = u.m - u.k;
+        it.nrhs = nr;
+        it.leaf = cn.c1 < 0;
+        it.lo = cn.lo;
+        it.y = buf + oy[c];
+        it.xp = buf + ox[id] + (side ? (size_t)ka * nr : 0);
+        it.hv = u.hv;
+        it.tau = u.tau;
+        it.x = buf + ox[c];
+        it.Xout = X;
+        it.ldx = ldx;
+        items.push_back(it);
+      }
+    }
+    if (items.empty()) continue;
+    DownItem* dev = nullptr;
+    e = upload_and_launch(items, s, &dev);
+    if (e.st == HSS_OK) {
+      ulv_solve_down_kernel<<<(unsigned)items.size(), U_THREADS, 0, s>>>(dev, f64);
+      e = check_launch("ulv_solve_down_kernel");
+    }
+    dfree(dev, s);
+  }
+  dfree(buf, s);
+  if (e.st != HSS_OK) h->err = e.msg;
+  return e.st;
+}

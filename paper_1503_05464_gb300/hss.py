@@ -1,0 +1,278 @@
+"""Thin ctypes binding of libhss.so (include/hss.h).
+
+Argument marshalling only: every step of the compression, product,
+factorization and solve runs in the library's CUDA kernels.  Tensors are
+PyTorch CUDA tensors (device memory and streams come from PyTorch); the
+functions keep the C names.  If the library has not been built, or no CUDA
+device is present, the calls raise: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhss.so")
+
+HSS_OK, HSS_ERR_INVALID, HSS_ERR_OOM, HSS_ERR_CUDA, HSS_ERR_RANK_CAP, HSS_ERR_SINGULAR, \
+    HSS_ERR_TIMEOUT, HSS_ERR_STATE = range(8)
+HSS_F32, HSS_F64 = 0, 1
+SAMPLE_MODES = {"native": 0, "tf32": 1, "bf16x2": 2, "bf16x3": 3}
+
+STATUS_NAMES = {0: "HSS_OK", 1: "HSS_ERR_INVALID", 2: "HSS_ERR_OOM", 3: "HSS_ERR_CUDA",
+                4: "HSS_ERR_RANK_CAP", 5: "HSS_ERR_SINGULAR", 6: "HSS_ERR_TIMEOUT",
+                7: "HSS_ERR_STATE"}
+
+
+class HssError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class HssOpts(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int32), ("rtol", ctypes.c_double),
+                ("atol", ctypes.c_double), ("d0", ctypes.c_int32), ("d_step", ctypes.c_int32),
+                ("d_max", ctypes.c_int32), ("oversample_p", ctypes.c_int32),
+                ("sample_mode", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class HssInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nodes", ctypes.c_int32), ("leaves", ctypes.c_int32),
+                ("levels", ctypes.c_int32), ("max_rank_r", ctypes.c_int32),
+                ("max_rank_c", ctypes.c_int32), ("d_final", ctypes.c_int32),
+                ("passes", ctypes.c_int32), ("bytes_hss", ctypes.c_int64),
+                ("bytes_ulv", ctypes.c_int64), ("ms_compress", ctypes.c_double),
+                ("ms_sample", ctypes.c_double), ("ms_id", ctypes.c_double),
+                ("ms_levels", ctypes.c_double), ("flops_sample", ctypes.c_double),
+                ("flops_id", ctypes.c_double), ("factored", ctypes.c_int32),
+                ("launches", ctypes.c_int64), ("bytes_d2h", ctypes.c_int64)]
+
+
+_lib = None
+EXPORTS = ["hss_default_opts", "hss_compress", "hss_matvec", "hss_factor", "hss_solve",
+           "hss_info", "hss_node_ranks", "hss_destroy", "hss_last_error",
+           "hss_random_gaussian", "hss_sample", "hss_id_batched", "hss_kernel_launches"]
+
+
+def load(path: str = LIB_PATH):
+    """Load libhss.so and declare the C signatures (no CUDA call is made)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1503_05464_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, f64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
+    L.hss_default_opts.argtypes = [ctypes.POINTER(HssOpts)]
+    L.hss_compress.argtypes = [vp, i64, i64, i32, ctypes.POINTER(HssOpts), vp, ctypes.POINTER(vp)]
+    L.hss_matvec.argtypes = [vp, vp, i64, i64, vp, i64, vp]
+    L.hss_factor.argtypes = [vp, vp]
+    L.hss_solve.argtypes = [vp, vp, i64, i64, vp, i64, vp]
+    L.hss_info.argtypes = [vp, ctypes.POINTER(HssInfo)]
+    L.hss_node_ranks.argtypes = [vp, vp, vp, vp, vp, i32, ctypes.POINTER(i32)]
+    L.hss_destroy.argtypes = [vp]
+    L.hss_destroy.restype = None
+    L.hss_last_error.argtypes = [vp]
+    L.hss_last_error.restype = ctypes.c_char_p
+    L.hss_random_gaussian.argtypes = [u64, i64, i64, i64, vp, i64, i32, vp]
+    L.hss_sample.argtypes = [vp, i64, i64, i32, vp, i64, i64, i64, vp, vp, i64, vp, i32, i32, vp]
+    L.hss_id_batched.argtypes = [i32, vp, vp, vp, vp, i32, f64, f64, vp, vp, vp, vp]
+    L.hss_kernel_launches.argtypes = []
+    L.hss_kernel_launches.restype = ctypes.c_int64
+    for name in EXPORTS:
+        if name not in ("hss_destroy", "hss_last_error", "hss_kernel_launches"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(st, handle=None):
+    if st != HSS_OK:
+        msg = load().hss_last_error(handle).decode(errors="replace")
+        raise HssError(st, msg)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return HSS_F32
+    if t.dtype == torch.float64:
+        return HSS_F64
+    raise TypeError(f"unsupported dtype {t.dtype} (float32 or float64)")
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if not t.is_cuda:
+            raise ValueError("tensors must live on a CUDA device")
+        if t.dim() == 2 and t.stride(1) != 1:
+            raise ValueError("matrices must be row-major with unit column stride")
+
+
+def hss_default_opts(**kw) -> HssOpts:
+    o = HssOpts()
+    _check(load().hss_default_opts(ctypes.byref(o)))
+    for k, v in kw.items():
+        if k == "sample_mode" and isinstance(v, str):
+            v = SAMPLE_MODES[v]
+        setattr(o, k, v)
+    return o
+
+
+class HSS:
+    """Owner of an hss_t handle (hss_destroy on deletion)."""
+
+    def __init__(self, handle: int, n: int, dtype: torch.dtype):
+        self.handle = ctypes.c_void_p(handle)
+        self.n = n
+        self.dtype = dtype
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.hss_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def close(self):
+        self.__del__()
+
+
+def hss_compress(A: torch.Tensor, opts: HssOpts | None = None, stream=None, **kw) -> HSS:
+    """Randomized HSS compression of the square row-major CUDA matrix A."""
+    _require_cuda(A)
+    n = A.shape[0]
+    if A.dim() != 2 or A.shape[1] != n:
+        raise ValueError("A must be square")
+    if opts is None:
+        opts = hss_default_opts(**kw)
+    out = ctypes.c_void_p()
+    st = load().hss_compress(ctypes.c_void_p(A.data_ptr()), n, A.stride(0), _dtype(A),
+                             ctypes.byref(opts), _stream(stream), ctypes.byref(out))
+    if st == HSS_ERR_RANK_CAP and out.value:
+        msg = load().hss_last_error(out).decode()
+        load().hss_destroy(out)
+        raise HssError(st, msg)
+    _check(st)
+    return HSS(out.value, n, A.dtype)
+
+
+def hss_matvec(h: HSS, X: torch.Tensor, B: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """B = H X (Algorithm 2); X is n x nrhs (or length n)."""
+    vec = X.dim() == 1
+    X2 = X.view(-1, 1) if vec else X
+    _require_cuda(X2)
+    if B is None:
+        B = torch.empty((h.n, X2.shape[1]), dtype=X2.dtype, device=X2.device)
+    B2 = B.view(-1, 1) if B.dim() == 1 else B
+    _check(load().hss_matvec(h.handle, ctypes.c_void_p(X2.data_ptr()), X2.stride(0), X2.shape[1],
+                             ctypes.c_void_p(B2.data_ptr()), B2.stride(0), _stream(stream)),
+           h.handle)
+    return B2.view(-1) if vec else B2
+
+
+def hss_factor(h: HSS, stream=None) -> None:
+    """ULV-like factorization (Algorithm 3)."""
+    _check(load().hss_factor(h.handle, _stream(stream)), h.handle)
+
+
+def hss_solve(h: HSS, B: torch.Tensor, X: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """X = H^{-1} B with the ULV factors (Algorithm 4)."""
+    vec = B.dim() == 1
+    B2 = B.view(-1, 1) if vec else B
+    _require_cuda(B2)
+    if X is None:
+        X = torch.empty((h.n, B2.shape[1]), dtype=B2.dtype, device=B2.device)
+    X2 = X.view(-1, 1) if X.dim() == 1 else X
+    _check(load().hss_solve(h.handle, ctypes.c_void_p(B2.data_ptr()), B2.stride(0), B2.shape[1],
+                            ctypes.c_void_p(X2.data_ptr()), X2.stride(0), _stream(stream)),
+           h.handle)
+    return X2.view(-1) if vec else X2
+
+
+def hss_kernel_launches() -> int:
+    """Kernels libhss has launched in this process so far."""
+    return int(load().hss_kernel_launches())
+
+
+def hss_info(h: HSS) -> dict:
+    info = HssInfo()
+    _check(load().hss_info(h.handle, ctypes.byref(info)), h.handle)
+    return {name: getattr(info, name) for name, _ in HssInfo._fields_}
+
+
+def hss_node_ranks(h: HSS):
+    """[(lo, hi, kr, kc)] for every node, breadth-first (root first, kr = kc = -1)."""
+    L = load()
+    cnt = ctypes.c_int32()
+    _check(L.hss_node_ranks(h.handle, None, None, None, None, 0, ctypes.byref(cnt)), h.handle)
+    n = cnt.value
+    arrs = [(ctypes.c_int32 * n)() for _ in range(4)]
+    _check(L.hss_node_ranks(h.handle, *arrs, n, ctypes.byref(cnt)), h.handle)
+    return [(arrs[0][i], arrs[1][i], arrs[2][i], arrs[3][i]) for i in range(n)]
+
+
+def hss_random_gaussian(seed: int, n: int, c0: int, c1: int, R: torch.Tensor, stream=None):
+    """Columns [c0, c1) of the random matrix R into the row-major CUDA tensor R."""
+    _require_cuda(R)
+    _check(load().hss_random_gaussian(seed, n, c0, c1, ctypes.c_void_p(R.data_ptr()), R.stride(0),
+                                      _dtype(R), _stream(stream)))
+    return R
+
+
+def hss_sample(A, R, c0, c1, Sr, Sc, leaf_starts=None, mode="native", stream=None):
+    """Fused sampling of columns [c0, c1): Sr = (A-D) R, Sc = (A-D)^T R."""
+    _require_cuda(A, R, Sr, Sc)
+    if Sr.stride(0) != Sc.stride(0):
+        raise ValueError("Sr and Sc must share a leading dimension")
+    if isinstance(mode, str):
+        mode = SAMPLE_MODES[mode]
+    if leaf_starts is None:
+        ls, nleaf = None, 0
+    else:
+        arr = (ctypes.c_int64 * len(leaf_starts))(*[int(x) for x in leaf_starts])
+        ls, nleaf = ctypes.cast(arr, ctypes.c_void_p), len(leaf_starts) - 1
+    _check(load().hss_sample(ctypes.c_void_p(A.data_ptr()), A.shape[0], A.stride(0), _dtype(A),
+                             ctypes.c_void_p(R.data_ptr()), R.stride(0), c0, c1,
+                             ctypes.c_void_p(Sr.data_ptr()), ctypes.c_void_p(Sc.data_ptr()),
+                             Sr.stride(0), ls, nleaf, mode, _stream(stream)))
+
+
+def hss_id_batched(Ys, rtol, atol=0.0, stream=None):
+    """Batched FP64 CPQR interpolative decompositions.
+
+    Ys: list of CUDA tensors Y_b^T (m_b x d_b, row j = column j of Y_b), one
+    dtype.  Returns [(k, perm (m,), E ((m-k) x k))] as CUDA tensors.
+    """
+    if not Ys:
+        return []
+    dev = Ys[0].device
+    dt = _dtype(Ys[0])
+    _require_cuda(*Ys)
+    cnt = len(Ys)
+    m = torch.tensor([y.shape[0] for y in Ys], dtype=torch.int32, device=dev)
+    d = torch.tensor([y.shape[1] for y in Ys], dtype=torch.int32, device=dev)
+    ld = torch.tensor([y.stride(0) for y in Ys], dtype=torch.int32, device=dev)
+    ptrs = torch.tensor([y.data_ptr() for y in Ys], dtype=torch.int64, device=dev)
+    perms = [torch.empty(max(y.shape[0], 1), dtype=torch.int32, device=dev) for y in Ys]
+    Es = [torch.empty(max(y.shape[0] * min(y.shape), 1), dtype=torch.float64, device=dev) for y in Ys]
+    pp = torch.tensor([p.data_ptr() for p in perms], dtype=torch.int64, device=dev)
+    ep = torch.tensor([e.data_ptr() for e in Es], dtype=torch.int64, device=dev)
+    k = torch.empty(cnt, dtype=torch.int32, device=dev)
+    vp = ctypes.c_void_p
+    _check(load().hss_id_batched(cnt, vp(ptrs.data_ptr()), vp(m.data_ptr()), vp(d.data_ptr()),
+                                 vp(ld.data_ptr()), dt, rtol, atol, vp(pp.data_ptr()),
+                                 vp(ep.data_ptr()), vp(k.data_ptr()), _stream(stream)))
+    torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    ks = k.tolist()
+    out = []
+    for y, kk, p, e in zip(Ys, ks, perms, Es):
+        mm = y.shape[0]
+        out.append((kk, p[:mm], e[: (mm - kk) * kk].view(mm - kk, kk)))
+    return out

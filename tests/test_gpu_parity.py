@@ -1,0 +1,303 @@
+"""GPU path vs the CPU oracle, element by element where the result is unique.
+
+Tolerances (from the arithmetic):
+* R: bit-exact except where the FP64 Box-Muller value sits on a bfloat16
+  rounding boundary (at most one bfloat16 ulp, at most 1e-6 of the entries).
+* sampling: FP64 |dS| <= 1e-12 (|A||R|); FP32 |dS| <= 4 n eps32 (|A||R|).
+* ID: same rank (+-1 only on a tie within 1e-12 of the threshold), same pivots,
+  E to 1e-9 relative.
+* compression (not unique: pivots and ranks may move near eps): ranks within
+  +-2 of the oracle, ||A - H||_F / ||A||_F <= 2 rtol, matvec vs the oracle's
+  H x within 4 rtol, solve residual <= 10x the oracle's.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import hss_oracle as O  # noqa: E402
+import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1503_05464_gb300 as pkg
+    assert torch.cuda.is_available(), "the GPU tests need a CUDA device"
+    return pkg
+
+
+DEV = "cuda:0"
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+# -------------------------------------------------------------------- R
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_random_matrix_matches_oracle(P, dtype):
+    n, c0, c1 = 3001, 5, 77
+    R = torch.zeros((n, 80), dtype=dtype, device=DEV)
+    P.hss_random_gaussian(1234, n, c0, c1, R)
+    got = R.cpu().numpy().astype(np.float64)
+    want = O.gaussian_bf16(1234, n, c0, c1)
+    assert np.all(got[:, :c0] == 0) and np.all(got[:, c1:] == 0)
+    diff = got[:, c0:c1] != want
+    assert diff.sum() <= max(1, int(1e-6 * want.size))
+    if diff.any():   # a boundary flip is one bfloat16 ulp
+        ulp = np.ldexp(1.0, np.frexp(want[diff])[1] - 8)
+        assert np.all(np.abs(got[:, c0:c1][diff] - want[diff]) <= ulp)
+
+
+# ------------------------------------------------------------- sampling
+@pytest.mark.parametrize("n,leaf,dtype,c0,c1", [
+    (777, 50, torch.float64, 0, 70),
+    (1000, 125, torch.float32, 0, 64),
+    (1283, 100, torch.float32, 33, 161),     # ragged n, ragged chunk, column offset
+    (300, 1000, torch.float64, 0, 20),       # single leaf: everything masked
+])
+def test_fused_sampling_matches_oracle(P, n, leaf, dtype, c0, c1):
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n)) + 5 * np.eye(n)
+    A[: n // 3] *= 3.0                        # unsymmetric, S^c != S^r
+    At = torch.tensor(A, dtype=dtype, device=DEV)
+    A64 = At.cpu().numpy().astype(np.float64)
+    R = torch.zeros((n, c1), dtype=dtype, device=DEV)
+    P.hss_random_gaussian(99, n, 0, c1, R)
+    Sr = torch.full((n, c1), 7.0, dtype=dtype, device=DEV)
+    Sc = torch.full((n, c1), 7.0, dtype=dtype, device=DEV)
+    nodes = O.bisection_tree(n, leaf)
+    starts = [nd.lo for nd in nodes if nd.is_leaf] + [n]
+    P.hss_sample(At, R, c0, c1, Sr, Sc, leaf_starts=starts)
+    torch.cuda.synchronize()
+    R64 = R.cpu().numpy().astype(np.float64)
+    wr, wc = O.leaf_local_samples(A64, R64[:, c0:c1], nodes)
+    mask = np.ones((n, n))
+    for nd in nodes:
+        if nd.is_leaf:
+            mask[nd.lo:nd.hi, nd.lo:nd.hi] = 0
+    br = (np.abs(A64) * mask) @ np.abs(R64[:, c0:c1])
+    bc = (np.abs(A64) * mask).T @ np.abs(R64[:, c0:c1])
+    tol = 1e-12 if dtype == torch.float64 else 4 * n * 2.0 ** -24
+    gr = Sr.cpu().numpy().astype(np.float64)
+    gc = Sc.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(gr[:, c0:c1] - wr) <= tol * br + 1e-300)
+    assert np.all(np.abs(gc[:, c0:c1] - wc) <= tol * bc + 1e-300)
+    assert np.all(gr[:, :c0] == 7.0) and np.all(gc[:, :c0] == 7.0)
+
+
+def test_sampling_is_deterministic(P):
+    n = 900
+    A = torch.randn(n, n, device=DEV)
+    R = torch.zeros((n, 64), device=DEV)
+    P.hss_random_gaussian(3, n, 0, 64, R)
+    outs = []
+    for _ in range(2):
+        Sr = torch.empty((n, 64), device=DEV)
+        Sc = torch.empty((n, 64), device=DEV)
+        P.hss_sample(A, R, 0, 64, Sr, Sc, leaf_starts=[0, 300, 600, 900])
+        outs.append((Sr.clone(), Sc.clone()))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
+# ------------------------------------------------------------------- ID
+def _decaying(rng, d, m, rate):
+    U, _ = np.linalg.qr(rng.standard_normal((d, min(d, m))))
+    V, _ = np.linalg.qr(rng.standard_normal((m, min(d, m))))
+    s = rate ** np.arange(min(d, m))
+    return U @ np.diag(s) @ V.T
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batched_id_matches_oracle(P, dtype):
+    rng = np.random.default_rng(1)
+    shapes = [(40, 30, 0.5), (64, 100, 0.7), (100, 64, 0.8), (7, 5, 0.9), (33, 1, 0.5),
+              (1, 9, 0.5), (128, 156, 0.85)]
+    Ys, ref = [], []
+    rtol = 1e-6
+    for d, m, rate in shapes:
+        Y = _decaying(rng, d, m, rate)
+        Yt = torch.tensor(Y.T.copy(), dtype=dtype, device=DEV)    # m rows of d values
+        Ys.append(Yt)
+        ref.append(O.interpolative_decomposition(Yt.cpu().numpy().astype(np.float64).T, rtol))
+    outs = P.hss_id_batched(Ys, rtol)
+    for (d, m, _), (k, perm, E), r, Yt in zip(shapes, outs, ref, Ys):
+        Y = Yt.cpu().numpy().astype(np.float64).T
+        assert abs(k - r.k) <= 1
+        perm = perm.cpu().numpy()
+        assert sorted(perm.tolist()) == list(range(m))
+        if k == r.k:
+            assert list(perm[:k]) == list(r.perm[:k])
+            # E rows follow the order of perm[k:]; compare the generators
+            G = np.zeros((m, k))
+            G[perm[:k]] = np.eye(k)
+            G[perm[k:]] = E.cpu().numpy()
+            np.testing.assert_allclose(G, r.basis(), rtol=1e-7, atol=1e-9)
+        # reconstruction Y ~= Y(:, J) X within the truncation level
+        G = np.zeros((m, k))
+        G[perm[:k]] = np.eye(k)
+        G[perm[k:]] = E.cpu().numpy()
+        err = np.linalg.norm(Y - Y[:, perm[:k]] @ G.T, 2)
+        assert err <= 10 * math.sqrt(m) * rtol * np.linalg.norm(Y, 2) + 1e-12
+
+
+def test_batched_id_exact_rank(P):
+    rng = np.random.default_rng(2)
+    Ys = []
+    for r in (0, 1, 5, 17):
+        Y = rng.standard_normal((60, r)) @ rng.standard_normal((r, 45))
+        Ys.append(torch.tensor(Y.T.copy(), dtype=torch.float64, device=DEV))
+    outs = P.hss_id_batched(Ys, 1e-12)
+    assert [o[0] for o in outs] == [0, 1, 5, 17]
+
+
+# ----------------------------------------------------------- compression
+def _ranks_close(P, h, ho, slack=2):
+    ranks = P.hss_node_ranks(h)
+    ro = ho.ranks()
+    for i, (lo, hi, kr, kc) in enumerate(ranks):
+        if i == 0:
+            continue
+        assert (lo, hi) == (ho.nodes[i].lo, ho.nodes[i].hi)
+        assert abs(kr - ro[i][0]) <= slack and abs(kc - ro[i][1]) <= slack, (i, kr, kc, ro[i])
+    return ranks
+
+
+def _dense_from_gpu(P, h, n, dtype):
+    eye = torch.eye(n, dtype=dtype, device=DEV)
+    return P.hss_matvec(h, eye).cpu().numpy().astype(np.float64)
+
+
+def test_compress_known_ranks_exact(P):
+    A, true_ranks = W.random_hss(1024, 64, 10, seed=5, diag_shift=10.0)
+    At = torch.tensor(A, device=DEV)
+    h = P.hss_compress(At, leaf_size=64, rtol=1e-12, d0=24, d_step=16, seed=3)
+    for i, (lo, hi, kr, kc) in enumerate(P.hss_node_ranks(h)):
+        if i:
+            assert (kr, kc) == (true_ranks[(lo, hi)],) * 2
+    H = _dense_from_gpu(P, h, 1024, torch.float64)
+    assert _rel(H, A) <= 1e-10
+
+
+def test_compress_config1_toeplitz_fp64(P):
+    """Toeplitz n=2000 FP64, leaf 128, d0 64, step 32, rtol 1e-6."""
+    n, rtol = 2000, 1e-6
+    At = W.toeplitz_inv_distance(n, dtype=np.float64, device=DEV)
+    A = At.cpu().numpy()
+    kw = dict(leaf_size=128, rtol=rtol, d0=64, d_step=32, seed=1001)
+    h = P.hss_compress(At, **kw)
+    ho = O.compress(A, rtol, leaf_size=128, d0=64, d_step=32, seed=1001)
+    _ranks_close(P, h, ho)
+    info = P.hss_info(h)
+    assert info["passes"] == ho.passes and info["d_final"] == ho.d
+    H = _dense_from_gpu(P, h, n, torch.float64)
+    assert _rel(H, A) <= 2 * rtol
+    x = np.random.default_rng(0).standard_normal((n, 1))
+    b = P.hss_matvec(h, torch.tensor(x, device=DEV)).cpu().numpy()
+    assert _rel(b, O.matvec(ho, x)) <= 4 * rtol
+    assert _rel(b, A @ x) <= 2 * rtol
+    P.hss_factor(h)
+    xs = P.hss_solve(h, torch.tensor(x, device=DEV)).cpu().numpy()
+    O.ulv_factor(ho)
+    xo = O.ulv_solve(ho, x)
+    res_gpu = _rel(A @ xs, x)
+    res_ora = _rel(A @ xo, x)
+    assert res_gpu <= 10 * max(res_ora, 1e-15)
+    # the GPU solve inverts its own H to working precision
+    assert _rel(H @ xs, x) <= 1e-10
+
+
+def test_compress_adaptive_restarts_match_oracle(P):
+    A, _ = W.random_hss(1024, 64, 20, seed=4, diag_shift=20.0)
+    At = torch.tensor(A, device=DEV)
+    h = P.hss_compress(At, leaf_size=64, rtol=1e-13, d0=16, d_step=8, seed=7)
+    ho = O.compress(A, 1e-13, leaf_size=64, d0=16, d_step=8, seed=7)
+    info = P.hss_info(h)
+    assert info["passes"] == ho.passes > 1
+    assert info["d_final"] == ho.d
+    _ranks_close(P, h, ho, slack=0)
+    assert _rel(_dense_from_gpu(P, h, 1024, torch.float64), A) <= 1e-10
+
+
+def test_compress_unsymmetric_fp32(P):
+    n, rtol = 1500, 1e-4
+    A = W.toeplitz_inv_distance(n).numpy() + 0.05 * np.triu(np.ones((n, n)), 1)
+    At = torch.tensor(A, dtype=torch.float32, device=DEV)
+    A32 = At.cpu().numpy().astype(np.float64)
+    h = P.hss_compress(At, leaf_size=96, rtol=rtol, d0=48, d_step=24, seed=11)
+    ho = O.compress(A32, rtol, leaf_size=96, d0=48, d_step=24, seed=11)
+    _ranks_close(P, h, ho)
+    H = _dense_from_gpu(P, h, n, torch.float32)
+    assert _rel(H, A32) <= 2 * rtol
+    P.hss_factor(h)
+    b = np.random.default_rng(3).standard_normal((n, 3))
+    xs = P.hss_solve(h, torch.tensor(b, dtype=torch.float32, device=DEV)).cpu().numpy()
+    O.ulv_factor(ho)
+    xo = O.ulv_solve(ho, b)
+    assert _rel(A32 @ xs, b) <= 10 * max(_rel(A32 @ xo, b), 1e-6)
+
+
+def test_compress_gaussian_kernel_fp32_reduced(P):
+    """Config-2 family at n=4000 (points in the unit cube, RCB order)."""
+    n, leaf, rtol = 4000, 256, 1e-4
+    pts = W.points_unit_cube(n, 1002)
+    pts = pts[W.rcb_order(pts, leaf)]
+    At = W.gaussian_kernel(pts, 0.2, 1.0, dtype=np.float32, device=DEV)
+    A32 = At.cpu().numpy().astype(np.float64)
+    h = P.hss_compress(At, leaf_size=leaf, rtol=rtol, d0=128, d_step=64, seed=1003)
+    ho = O.compress(A32, rtol, leaf_size=leaf, d0=128, d_step=64, seed=1003)
+    _ranks_close(P, h, ho)
+    H = _dense_from_gpu(P, h, n, torch.float32)
+    assert _rel(H, A32) <= 2 * rtol
+    P.hss_factor(h)
+    b = np.random.default_rng(4).standard_normal((n, 8))
+    xs = P.hss_solve(h, torch.tensor(b, dtype=torch.float32, device=DEV)).cpu().numpy()
+    O.ulv_factor(ho)
+    xo = O.ulv_solve(ho, b)
+    assert _rel(A32 @ xs, b) <= 10 * max(_rel(A32 @ xo, b), 1e-6)
+
+
+# ------------------------------------------------------------ edge cases
+def test_single_node_tree(P):
+    n = 100
+    A = np.random.default_rng(0).standard_normal((n, n)) + 10 * np.eye(n)
+    At = torch.tensor(A, device=DEV)
+    h = P.hss_compress(At, leaf_size=128)
+    x = torch.randn(n, 2, dtype=torch.float64, device=DEV)
+    np.testing.assert_allclose(P.hss_matvec(h, x).cpu().numpy(), A @ x.cpu().numpy(), rtol=1e-12)
+    P.hss_factor(h)
+    xs = P.hss_solve(h, x).cpu().numpy()
+    np.testing.assert_allclose(A @ xs, x.cpu().numpy(), atol=1e-10)
+
+
+def test_block_diagonal_rank_zero(P):
+    import scipy.linalg as sla
+    B = sla.block_diag(*[np.eye(32) * (i + 2) for i in range(8)])
+    h = P.hss_compress(torch.tensor(B, device=DEV), leaf_size=32, d0=16, d_step=8)
+    assert all(r[2] == 0 and r[3] == 0 for r in P.hss_node_ranks(h)[1:])
+    b = torch.arange(256.0, dtype=torch.float64, device=DEV)
+    np.testing.assert_allclose(P.hss_matvec(h, b).cpu().numpy(), B @ b.cpu().numpy())
+    P.hss_factor(h)
+    np.testing.assert_allclose(P.hss_solve(h, b).cpu().numpy(), np.linalg.solve(B, b.cpu().numpy()),
+                               rtol=1e-12)
+
+
+def test_errors_are_status_codes(P):
+    A = torch.randn(64, 64, device=DEV)
+    with pytest.raises(P.HssError) as e:
+        P.hss_compress(A, leaf_size=0)
+    assert e.value.status == P.hss.HSS_ERR_INVALID
+    h = P.hss_compress(A + 20 * torch.eye(64, device=DEV), leaf_size=16, rtol=1e-3, d0=8, d_step=8)
+    with pytest.raises(P.HssError) as e:
+        P.hss_solve(h, torch.ones(64, device=DEV))
+    assert e.value.status == P.hss.HSS_ERR_STATE
+    with pytest.raises(P.HssError) as e:     # d_max too small for a random matrix
+        P.hss_compress(torch.randn(256, 256, device=DEV), leaf_size=64, rtol=1e-12, d0=16,
+                       d_step=16, d_max=32)
+    assert e.value.status == P.hss.HSS_ERR_RANK_CAP
