@@ -35,7 +35,7 @@ Readings taken where the paper is silent (each is also listed in the design doc):
 * Root: no ID; B12/B21 are gathered and the ULV root is LU with partial
   pivoting.
 
-Parity pins for every function here live in tests/test_oracle_*.py.
+Pins for every function here live in tests/test_oracle.py.
 """
 from __future__ import annotations
 

@@ -8,7 +8,10 @@
 // written to a slab of partial sums, which a second kernel reduces over the
 // panels in a fixed order (deterministic: no floating-point atomics).
 // Entries with leaf(i) == leaf(j) are masked to zero while A is staged, which
-// subtracts the leaf diagonal blocks D exactly (no cancellation).
+// subtracts the leaf diagonal blocks D exactly (no cancellation).  In FP32 the
+// row sample is summed per column tile and the tile sums are added with Kahan
+// compensation; the panel partials of the column sample are summed in FP64:
+// the sample error stays near one rounding instead of growing like sqrt(n).
 #include "hss_internal.cuh"
 
 #include <cuda_bf16.h>
@@ -57,11 +60,14 @@ sample_simt_kernel(const T* __restrict__ A, int64_t n, int64_t lda,
     leaf_rows[r] = (leaf_of && i < n) ? leaf_of[i] : -1;
   }
 
-  T acc[8][4];
+  // Row sample: FP32 partial sums per column tile, added across tiles with
+  // Kahan compensation (cmp) so that the error does not grow with n.
+  constexpr bool kCompensate = sizeof(T) == 4;
+  T acc[8][4], cmp[8][4];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int b = 0; b < 4; ++b) acc[a][b] = cmp[a][b] = T(0);
 
   T* Pp = P + (int64_t)blockIdx.x * n * S_DC;
 
@@ -86,6 +92,11 @@ sample_simt_kernel(const T* __restrict__ A, int64_t n, int64_t lda,
     }
     __syncthreads();
     // row sample: acc += A_tile * R_tile
+    T tp[8][4];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) tp[r][c] = T(0);
 #pragma unroll 4
     for (int k = 0; k < S_BK; ++k) {
       T a[8], b[4];
@@ -96,8 +107,21 @@ sample_simt_kernel(const T* __restrict__ A, int64_t n, int64_t lda,
 #pragma unroll
       for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        for (int c = 0; c < 4; ++c) tp[r][c] = fma(a[r], b[c], tp[r][c]);
     }
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (kCompensate) {
+          T y = tp[r][c] - cmp[r][c];
+          T t = acc[r][c] + y;
+          cmp[r][c] = (t - acc[r][c]) - y;
+          acc[r][c] = t;
+        } else {
+          acc[r][c] += tp[r][c];
+        }
+      }
     // column sample of this tile: pc = A_tile^T * R_panel
     T pc[2][4];
 #pragma unroll
@@ -148,9 +172,9 @@ __global__ void reduce_partials_kernel(const T* __restrict__ P, int64_t n, int n
   int cc = (int)(rem - j * S_DC);
   int64_t col = (int64_t)q * S_DC + cc;
   if (col >= ncols) return;
-  T s = T(0);
-  for (int p = 0; p < npanel; ++p) s += P[((int64_t)p * nchunk + q) * n * S_DC + j * S_DC + cc];
-  Sc[j * lds + c0 + col] = s;
+  double s = 0.0;   // FP64 sum over the panels (memory-bound: free)
+  for (int p = 0; p < npanel; ++p) s += (double)P[((int64_t)p * nchunk + q) * n * S_DC + j * S_DC + cc];
+  Sc[j * lds + c0 + col] = (T)s;
 }
 
 }  // namespace

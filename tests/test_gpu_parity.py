@@ -7,8 +7,11 @@ Tolerances (from the arithmetic):
 * ID: same rank (+-1 only on a tie within 1e-12 of the threshold), same pivots,
   E to 1e-9 relative.
 * compression (not unique: pivots and ranks may move near eps): ranks within
-  +-2 of the oracle, ||A - H||_F / ||A||_F <= 2 rtol, matvec vs the oracle's
-  H x within 4 rtol, solve residual <= 10x the oracle's.
+  +-2 of the oracle, ||A - H||_F / ||A||_F <= 2 max(rtol, e_oracle) where
+  e_oracle is the oracle's own error at the same eps (the paper's stopping
+  test is local and relative, so the global error of the method itself can
+  exceed rtol), matvec vs the oracle's H x within 4 rtol, solve residual
+  <= 10x the oracle's.
 """
 import math
 
@@ -169,6 +172,11 @@ def _ranks_close(P, h, ho, slack=2):
     return ranks
 
 
+def _err_bound(A, ho, rtol):
+    e_or = _rel(O.to_dense(ho), A)
+    return 2 * max(rtol, e_or)
+
+
 def _dense_from_gpu(P, h, n, dtype):
     eye = torch.eye(n, dtype=dtype, device=DEV)
     return P.hss_matvec(h, eye).cpu().numpy().astype(np.float64)
@@ -197,7 +205,7 @@ def test_compress_config1_toeplitz_fp64(P):
     info = P.hss_info(h)
     assert info["passes"] == ho.passes and info["d_final"] == ho.d
     H = _dense_from_gpu(P, h, n, torch.float64)
-    assert _rel(H, A) <= 2 * rtol
+    assert _rel(H, A) <= 2 * rtol and _rel(H, A) <= _err_bound(A, ho, rtol)
     x = np.random.default_rng(0).standard_normal((n, 1))
     b = P.hss_matvec(h, torch.tensor(x, device=DEV)).cpu().numpy()
     assert _rel(b, O.matvec(ho, x)) <= 4 * rtol
@@ -234,7 +242,7 @@ def test_compress_unsymmetric_fp32(P):
     ho = O.compress(A32, rtol, leaf_size=96, d0=48, d_step=24, seed=11)
     _ranks_close(P, h, ho)
     H = _dense_from_gpu(P, h, n, torch.float32)
-    assert _rel(H, A32) <= 2 * rtol
+    assert _rel(H, A32) <= _err_bound(A32, ho, rtol)
     P.hss_factor(h)
     b = np.random.default_rng(3).standard_normal((n, 3))
     xs = P.hss_solve(h, torch.tensor(b, dtype=torch.float32, device=DEV)).cpu().numpy()
@@ -254,7 +262,7 @@ def test_compress_gaussian_kernel_fp32_reduced(P):
     ho = O.compress(A32, rtol, leaf_size=leaf, d0=128, d_step=64, seed=1003)
     _ranks_close(P, h, ho)
     H = _dense_from_gpu(P, h, n, torch.float32)
-    assert _rel(H, A32) <= 2 * rtol
+    assert _rel(H, A32) <= _err_bound(A32, ho, rtol)
     P.hss_factor(h)
     b = np.random.default_rng(4).standard_normal((n, 8))
     xs = P.hss_solve(h, torch.tensor(b, dtype=torch.float32, device=DEV)).cpu().numpy()
