@@ -218,6 +218,33 @@ hss_status hss_id_batched(int32_t count, const void* const* Yt, const int32_t* m
                           double rtol, double atol, int32_t* const* perm,
                           double* const* E, int32_t* k, void* stream);
 
+/*
+ * hss_sample_noalloc -- hss_sample for callers that cannot allocate device
+ * memory (the paper has no counterpart: this is a deployment variant).  A
+ * host application whose memory manager owns the whole GPU, a serving loop
+ * that allows no allocator call after start-up (cudaMalloc can block and
+ * synchronize the device), or code that issues work while a stream is being
+ * captured (where cudaMalloc is not allowed) can call this instead.
+ *   Same arguments, layouts and results as hss_sample; the caller still
+ *   provides A, R, Sr and Sc.  The scratch (partial column sums, leaf mask)
+ *   lives in fixed file-scope device arrays of the library, about 16 MiB per
+ *   GPU that loads it, held until the process exits.
+ *   Limits: n <= 2048, c1 - c0 <= 64, nleaf <= 2048; larger problems return
+ *   HSS_ERR_INVALID (use hss_sample).  It calls no cudaMalloc or cudaFree.
+ *   The first call on a device looks up the arrays' device addresses with
+ *   cudaGetSymbolAddress (with that device current): make that first call
+ *   before any stream capture.  Every call shares the same arrays, which keep
+ *   the last call's contents (nothing in them needs to start at zero: a call
+ *   writes every entry it reads); calls whose GPU work overlaps -- two
+ *   streams, two threads -- race on them, so serialize them.
+ * Errors: INVALID, CUDA (message in hss_last_error(NULL)).  Stream-ordered.
+ */
+hss_status hss_sample_noalloc(const void* A, int64_t n, int64_t lda, hss_dtype dtype,
+                              const void* R, int64_t ldr, int64_t c0, int64_t c1,
+                              void* Sr, void* Sc, int64_t lds,
+                              const int64_t* leaf_starts, int32_t nleaf, int32_t mode,
+                              void* stream);
+
 #ifdef __cplusplus
 }
 #endif

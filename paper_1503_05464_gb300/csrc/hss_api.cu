@@ -22,6 +22,8 @@ static std::atomic<int64_t> g_launches{0};
 
 int64_t launches_so_far() { return g_launches.load(); }
 
+void set_thread_error(const std::string& msg) { g_last_error = msg; }
+
 Err check_launch(const char* what) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t e = cudaGetLastError();

@@ -36,6 +36,8 @@ inline Err ok() { return Err{}; }
 // Counts the launch (see hss_kernel_launches) and checks for a launch error.
 Err check_launch(const char* what);
 int64_t launches_so_far();
+// Message returned by hss_last_error(NULL) on the calling thread.
+void set_thread_error(const std::string& msg);
 
 // Stream-ordered device allocation (cudaMallocAsync); null for 0 bytes.
 Err dalloc(void** p, size_t bytes, cudaStream_t s);

@@ -54,7 +54,7 @@ class HssInfo(ctypes.Structure):
 _lib = None
 EXPORTS = ["hss_default_opts", "hss_compress", "hss_matvec", "hss_factor", "hss_solve",
            "hss_info", "hss_node_ranks", "hss_destroy", "hss_last_error",
-           "hss_random_gaussian", "hss_sample", "hss_id_batched", "hss_kernel_launches"]
+           "hss_random_gaussian", "hss_sample", "hss_id_batched", "hss_kernel_launches", "hss_sample_noalloc"]
 
 
 def load(path: str = LIB_PATH):
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
     L.hss_random_gaussian.argtypes = [u64, i64, i64, i64, vp, i64, i32, vp]
     L.hss_sample.argtypes = [vp, i64, i64, i32, vp, i64, i64, i64, vp, vp, i64, vp, i32, i32, vp]
     L.hss_id_batched.argtypes = [i32, vp, vp, vp, vp, i32, f64, f64, vp, vp, vp, vp]
+    L.hss_sample_noalloc.argtypes = L.hss_sample.argtypes
     L.hss_kernel_launches.argtypes = []
     L.hss_kernel_launches.restype = ctypes.c_int64
     for name in EXPORTS:
@@ -242,6 +243,25 @@ def hss_sample(A, R, c0, c1, Sr, Sc, leaf_starts=None, mode="native", stream=Non
                              ctypes.c_void_p(R.data_ptr()), R.stride(0), c0, c1,
                              ctypes.c_void_p(Sr.data_ptr()), ctypes.c_void_p(Sc.data_ptr()),
                              Sr.stride(0), ls, nleaf, mode, _stream(stream)))
+
+
+def hss_sample_noalloc(A, R, c0, c1, Sr, Sc, leaf_starts=None, mode="native", stream=None):
+    """hss_sample without any device allocation (fixed library scratch; small
+    problems only: n <= 2048, c1 - c0 <= 64)."""
+    _require_cuda(A, R, Sr, Sc)
+    if Sr.stride(0) != Sc.stride(0):
+        raise ValueError("Sr and Sc must share a leading dimension")
+    if isinstance(mode, str):
+        mode = SAMPLE_MODES[mode]
+    if leaf_starts is None:
+        ls, nleaf = None, 0
+    else:
+        arr = (ctypes.c_int64 * len(leaf_starts))(*[int(x) for x in leaf_starts])
+        ls, nleaf = ctypes.cast(arr, ctypes.c_void_p), len(leaf_starts) - 1
+    _check(load().hss_sample_noalloc(ctypes.c_void_p(A.data_ptr()), A.shape[0], A.stride(0),
+                                     _dtype(A), ctypes.c_void_p(R.data_ptr()), R.stride(0), c0, c1,
+                                     ctypes.c_void_p(Sr.data_ptr()), ctypes.c_void_p(Sc.data_ptr()),
+                                     Sr.stride(0), ls, nleaf, mode, _stream(stream)))
 
 
 def hss_id_batched(Ys, rtol, atol=0.0, stream=None):
