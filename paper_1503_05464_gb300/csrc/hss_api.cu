@@ -323,7 +323,6 @@ Err Compressor<T>::process_level(int depth) {
   if (nfresh) {
     std::vector<IdItem> items;
     size_t work = 0, norms = 0;
-    int maxd = d;
     for (size_t q = 0; q < nfresh; ++q) {
       work += (size_t)loc[q].mr * d + (size_t)loc[q].mc * d;
       norms += 2 * (size_t)loc[q].mr + 2 * (size_t)loc[q].mc;
@@ -361,8 +360,7 @@ Err Compressor<T>::process_level(int depth) {
     HSS_CUDA_TRY(cudaEventCreate(&e0));
     HSS_CUDA_TRY(cudaEventCreate(&e1));
     HSS_CUDA_TRY(cudaEventRecord(e0, s));
-    HSS_TRY(launch_id_batched(ibuf, (int)items.size(), sizeof(T) == 8, h->opts.rtol,
-                              h->opts.atol, maxd, s));
+    HSS_TRY(launch_id_batched(ibuf, items, sizeof(T) == 8, h->opts.rtol, h->opts.atol, s));
     HSS_CUDA_TRY(cudaEventRecord(e1, s));
     std::vector<int32_t> ks(2 * nfresh);
     HSS_CUDA_TRY(cudaMemcpyAsync(ks.data(), kbuf, ks.size() * sizeof(int32_t),
@@ -685,13 +683,11 @@ hss_status hss_id_batched(int32_t count, const void* const* Yt, const int32_t* m
   if (cudaStreamSynchronize(s) != cudaSuccess)
     return set_err(nullptr, fail(HSS_ERR_CUDA, "hss_id_batched: reading the batch table"));
   size_t work = 0, norms = 0;
-  int maxd = 1;
   for (int i = 0; i < count; ++i) {
     if (hm[i] < 0 || hd[i] < 0 || hl[i] < hd[i])
       return set_err(nullptr, fail(HSS_ERR_INVALID, "hss_id_batched: bad m, d or ldy"));
     work += (size_t)hm[i] * hd[i];
     norms += 2 * (size_t)hm[i];
-    maxd = std::max(maxd, (int)hd[i]);
   }
   double *wb = nullptr, *nb = nullptr;
   IdItem* ib = nullptr;
@@ -707,7 +703,7 @@ hss_status hss_id_batched(int32_t count, const void* const* Yt, const int32_t* m
       no += 2 * (size_t)hm[i];
     }
     cudaMemcpyAsync(ib, items.data(), count * sizeof(IdItem), cudaMemcpyHostToDevice, s);
-    e = launch_id_batched(ib, count, dtype == HSS_F64, rtol, atol, maxd, s);
+    e = launch_id_batched(ib, items, dtype == HSS_F64, rtol, atol, s);
   }
   dfree(wb, s);
   dfree(nb, s);

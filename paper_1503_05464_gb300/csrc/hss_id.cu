@@ -2,26 +2,37 @@
 // column-pivoted Householder QR in FP64 (Section 2.2; Section 3.1: the QR
 // with column pivoting stops as soon as |R_ii| <= eps |R_11|).
 //
-// One CTA factors one Y.  Y is d x m and is stored transposed: its column j
-// is the contiguous row j of the input, so every pivot candidate is read with
-// coalesced loads by one warp.  Per step the CTA
-//   1. picks the active column of largest (downdated) residual norm, lowest
-//      index on ties (block arg-max reduction),
-//   2. recomputes that column's residual norm exactly -> |R_ii|, applies the
-//      stopping test against max(rtol |R_11|, atol),
-//   3. builds the Householder reflector of the pivot column,
-//   4. applies it to every active column (one warp per column: dot product,
-//      warp reduction, update) and downdates the column norms, recomputing a
-//      norm when cancellation would make the downdate inaccurate (the LAPACK
-//      xGEQP3 safeguard, threshold sqrt(eps)).
-// Columns are never swapped: the pivot order is recorded in perm[0..k) and
-// the remaining columns follow in increasing index order.  Finally
-// T = R1^{-1} R2 by back substitution (one thread per column of R2) and
-// E = T^T is written, so that the generator is Pi [I; E].
+// One thread-block cluster of C CTAs (C = 1..16, one SM each) factors one Y.
+// Y is d x m and is stored transposed: its column j is the contiguous row j
+// of the input.  Column j belongs to CTA j % C, which keeps it in its shared
+// memory (or, for matrices too large for the cluster's shared memory, in a
+// global work copy) together with its residual norm.  Per elimination step:
+//   1. every CTA has published the largest residual norm among its active
+//      columns; after a cluster barrier each CTA reads all C candidates
+//      through distributed shared memory and picks the same pivot (largest
+//      norm, lowest index on ties);
+//   2. the pivot's owner recomputes that column's residual norm exactly
+//      (|R_ii|), takes the stopping decision against max(rtol |R_11|, atol),
+//      builds the Householder reflector and publishes it with the decision;
+//   3. after a second cluster barrier every CTA copies the reflector, applies
+//      it to its active columns (one warp per column: dot product, warp
+//      reduction, update), downdates their norms -- recomputing a norm when
+//      cancellation makes the downdate inaccurate (LAPACK xGEQP3's safeguard,
+//      threshold sqrt(eps)) -- and publishes its next candidate.
+// Columns never move: perm[0..k) records the pivot order, the remaining
+// columns follow in increasing index order.  The pivot columns' R entries go
+// to a global k x k buffer, and each CTA solves T = R1^{-1} R2 for the
+// remaining columns it owns (one thread per column), writing E = T^T so that
+// the generator is Pi [I; E].
 #include "hss_internal.cuh"
 
+#include <cooperative_groups.h>
+
+#include <algorithm>
 #include <cfloat>
 #include <climits>
+
+namespace cg = cooperative_groups;
 
 namespace hss {
 
@@ -29,6 +40,7 @@ namespace {
 
 constexpr int ID_THREADS = 256;
 constexpr int ID_WARPS = ID_THREADS / 32;
+constexpr size_t ID_SMEM_CAP = 200 * 1024;   // shared-memory budget per CTA
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -36,219 +48,368 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// block-wide sum of two values; every thread gets the result
-__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
-  a = warp_sum(a);
-  b = warp_sum(b);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) {
-    red[w] = a;
-    red[ID_WARPS + w] = b;
-  }
-  __syncthreads();
-  a = 0.0;
-  b = 0.0;
-#pragma unroll
-  for (int q = 0; q < ID_WARPS; ++q) {
-    a += red[q];
-    b += red[ID_WARPS + q];
-  }
-}
-
-// block-wide arg-max of (val, idx): larger val wins, lower idx on ties
-__device__ __forceinline__ void block_argmax(double& val, int& idx, double* redv, int* redi) {
+__device__ __forceinline__ void warp_argmax(double& v, int& j) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    double ov = __shfl_xor_sync(0xffffffffu, val, o);
-    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-    if (ov > val || (ov == val && oi < idx)) {
-      val = ov;
-      idx = oi;
-    }
-  }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) {
-    redv[w] = val;
-    redi[w] = idx;
-  }
-  __syncthreads();
-  val = redv[0];
-  idx = redi[0];
-#pragma unroll
-  for (int q = 1; q < ID_WARPS; ++q) {
-    if (redv[q] > val || (redv[q] == val && redi[q] < idx)) {
-      val = redv[q];
-      idx = redi[q];
+    double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    int oj = __shfl_xor_sync(0xffffffffu, j, o);
+    if (ov > v || (ov == v && oj < j)) {
+      v = ov;
+      j = oj;
     }
   }
 }
 
-template <typename TY>
-__global__ void __launch_bounds__(ID_THREADS)
-id_cpqr_kernel(const IdItem* __restrict__ items, double rtol, double atol) {
-  extern __shared__ double vsh[];     // Householder vector, d entries
-  __shared__ double red[2 * ID_WARPS];
-  __shared__ int redi[ID_WARPS];
-  __shared__ int s_rest_count;
+// Values one CTA publishes to the others of its cluster.
+struct Pub {
+  double cand_val;   // largest active residual norm of this CTA (-1: none)
+  int cand_idx;      // its global column index
+  int stop;          // owner of the pivot: 1 = stop before this step
+  double tau;        // owner: reflector coefficient
+  double r11;        // owner at step 0: |R_11|
+};
 
-  const IdItem it = items[blockIdx.x];
+__global__ void __launch_bounds__(ID_THREADS)
+id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in, double rtol, double atol,
+                       int w_in_smem, double* __restrict__ r1buf_base,
+                       const int64_t* __restrict__ r1off) {
+  extern __shared__ __align__(16) double smem[];
+  __shared__ Pub pub;
+  __shared__ double redv[ID_WARPS];
+  __shared__ int redi[ID_WARPS];
+  __shared__ double s_a, s_t;
+
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int crank = (int)cluster.block_rank();
+  const int item = blockIdx.x / C;
+  const IdItem it = items[item];
   const int m = it.m, d = it.d;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int32_t* perm = it.perm;
   if (m <= 0) {
-    if (tid == 0) *it.k = 0;
-    return;
+    if (crank == 0 && tid == 0) *it.k = 0;
+    return;   // uniform across the cluster
   }
-  double* W = it.work;
-  double* nrm = it.norms;
-  double* nrm0 = it.norms + m;
-  const TY* Y = reinterpret_cast<const TY*>(it.Yt);
+  const int mloc = (m - crank + C - 1) / C;       // columns crank, crank+C, ...
+  const int mloc_max = (m + C - 1) / C;
+  double* vloc = smem;                            // d
+  double* vbuf = vloc + d;                        // d (published reflector)
+  double* nrm = vbuf + d;                         // mloc_max
+  double* nrm0 = nrm + mloc_max;                  // mloc_max
+  int* pstep = reinterpret_cast<int*>(nrm0 + mloc_max);   // mloc_max: pivot step or -1
+  double* Wsm = reinterpret_cast<double*>(pstep + ((mloc_max + 1) & ~1));
+  auto col = [&](int jl) -> double* {
+    return w_in_smem ? Wsm + (size_t)jl * d : it.work + (size_t)(jl * C + crank) * d;
+  };
   const double tol3z = sqrt(DBL_EPSILON * 0.5);
+  int32_t* perm = it.perm;
 
-  // load Y^T into the FP64 work copy and take the column norms
-  for (int j = warp; j < m; j += ID_WARPS) {
-    const TY* y = Y + (int64_t)j * it.ldy;
-    double* w = W + (int64_t)j * d;
+  // load the owned columns (FP64 copy) and their norms
+  for (int jl = warp; jl < mloc; jl += ID_WARPS) {
+    const int j = jl * C + crank;
+    double* w = col(jl);
     double ss = 0.0;
-    for (int c = lane; c < d; c += 32) {
-      double x = (double)y[c];
-      w[c] = x;
-      ss = fma(x, x, ss);
+    if (f64in) {
+      const double* y = reinterpret_cast<const double*>(it.Yt) + (size_t)j * it.ldy;
+      for (int c = lane; c < d; c += 32) {
+        double x = y[c];
+        w[c] = x;
+        ss = fma(x, x, ss);
+      }
+    } else {
+      const float* y = reinterpret_cast<const float*>(it.Yt) + (size_t)j * it.ldy;
+      for (int c = lane; c < d; c += 32) {
+        double x = (double)y[c];
+        w[c] = x;
+        ss = fma(x, x, ss);
+      }
     }
     ss = warp_sum(ss);
     if (lane == 0) {
-      nrm[j] = sqrt(ss);
-      nrm0[j] = nrm[j];
+      nrm[jl] = sqrt(ss);
+      nrm0[jl] = nrm[jl];
+      pstep[jl] = -1;
     }
   }
   __syncthreads();
+  // local arg-max -> published candidate
+  auto publish_candidate = [&]() {
+    double bv = -1.0;
+    int bj = INT_MAX;
+    for (int jl = tid; jl < mloc; jl += ID_THREADS) {
+      double x = nrm[jl];
+      if (x > bv) {
+        bv = x;
+        bj = jl * C + crank;
+      }
+    }
+    warp_argmax(bv, bj);
+    if (lane == 0) {
+      redv[warp] = bv;
+      redi[warp] = bj;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double v = redv[0];
+      int j = redi[0];
+      for (int q = 1; q < ID_WARPS; ++q)
+        if (redv[q] > v || (redv[q] == v && redi[q] < j)) {
+          v = redv[q];
+          j = redi[q];
+        }
+      pub.cand_val = v;
+      pub.cand_idx = j;
+    }
+  };
+  publish_candidate();
 
   const int kmax = min(m, d);
   int k = kmax;
   double r11 = 0.0;
   for (int i = 0; i < kmax; ++i) {
-    // 1. pivot: largest residual norm among active columns (nrm >= 0)
+    cluster.sync();   // (A) candidates published
     double bv = -1.0;
-    int bi = INT_MAX;
-    for (int j = tid; j < m; j += ID_THREADS) {
-      double x = nrm[j];
-      if (x > bv) {   // increasing j per thread: strict > keeps the lowest index
-        bv = x;
-        bi = j;
+    int p = INT_MAX;
+    for (int r = 0; r < C; ++r) {
+      const Pub* rp = cluster.map_shared_rank(&pub, r);
+      double v = rp->cand_val;
+      int j = rp->cand_idx;
+      if (v > bv || (v == bv && j < p)) {
+        bv = v;
+        p = j;
       }
     }
-    block_argmax(bv, bi, red, redi);
-    const int p = bi;
-    double* wp = W + (int64_t)p * d;
-    // 2. exact residual norm of the pivot column: |R_ii|
-    double s_all = 0.0, s_tail = 0.0;
-    for (int c = i + tid; c < d; c += ID_THREADS) {
-      double x = wp[c];
-      s_all = fma(x, x, s_all);
-      if (c > i) s_tail = fma(x, x, s_tail);
+    const int owner = p % C;
+    if (owner == crank) {
+      // exact residual norm of the pivot column and its reflector
+      double* wp = col(p / C);
+      double sa = 0.0, st = 0.0;
+      for (int c = i + tid; c < d; c += ID_THREADS) {
+        double x = wp[c];
+        sa = fma(x, x, sa);
+        if (c > i) st = fma(x, x, st);
+      }
+      sa = warp_sum(sa);
+      st = warp_sum(st);
+      if (lane == 0) redv[warp] = sa;
+      __syncthreads();
+      if (tid == 0) {
+        double a = 0.0;
+        for (int q = 0; q < ID_WARPS; ++q) a += redv[q];
+        s_a = a;
+      }
+      __syncthreads();
+      if (lane == 0) redv[warp] = st;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int q = 0; q < ID_WARPS; ++q) t += redv[q];
+        s_t = t;
+      }
+      __syncthreads();
+      const double sigma = sqrt(s_a);
+      const double r11_now = (i == 0) ? sigma : r11;
+      const int stop = (r11_now == 0.0 || sigma <= fmax(rtol * r11_now, atol)) ? 1 : 0;
+      const double alpha = wp[i];
+      double tau = 0.0, beta = alpha, scal = 0.0;
+      if (!stop && s_t != 0.0) {
+        beta = -copysign(sigma, alpha);
+        tau = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      if (!stop) {
+        for (int c = i + tid; c < d; c += ID_THREADS) vbuf[c - i] = (c == i) ? 1.0 : wp[c] * scal;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        pub.stop = stop;
+        pub.tau = tau;
+        pub.r11 = r11_now;
+        if (!stop) {
+          wp[i] = beta;   // R_ii
+          perm[i] = p;
+          nrm[p / C] = -1.0;
+          pstep[p / C] = i;
+        }
+      }
     }
-    block_sum2(s_all, s_tail, red);
-    const double sigma = sqrt(s_all);
-    if (i == 0) r11 = sigma;
-    if (r11 == 0.0 || sigma <= fmax(rtol * r11, atol)) {
+    cluster.sync();   // (B) reflector and decision published
+    const Pub* op = cluster.map_shared_rank(&pub, owner);
+    const int stop = op->stop;
+    const double tau = op->tau;
+    if (i == 0) r11 = op->r11;
+    if (stop) {
       k = i;
-      break;
+      break;   // every CTA of the cluster reads the same decision
     }
-    // 3. Householder reflector H = I - tau v v^T with v[0] = 1 (LAPACK xLARFG)
-    const double alpha = wp[i];
-    double tau, beta, scal;
-    if (s_tail == 0.0) {
-      tau = 0.0;
-      beta = alpha;
-      scal = 0.0;
-    } else {
-      beta = -copysign(sigma, alpha);
-      tau = (beta - alpha) / beta;
-      scal = 1.0 / (alpha - beta);
-    }
-    for (int c = i + tid; c < d; c += ID_THREADS) vsh[c - i] = (c == i) ? 1.0 : wp[c] * scal;
+    const double* ov = cluster.map_shared_rank(vbuf, owner);
+    for (int c = tid; c < d - i; c += ID_THREADS) vloc[c] = ov[c];
     __syncthreads();
-    if (tid == 0) {
-      wp[i] = beta;       // R_ii
-      perm[i] = p;
-      nrm[p] = -1.0;      // no longer a candidate
-    }
-    __syncthreads();
-    // 4. apply H to the active columns, downdate their norms
-    {
-      for (int j = warp; j < m; j += ID_WARPS) {
-        double nj = nrm[j];
-        if (nj < 0.0) continue;
-        double* wj = W + (int64_t)j * d;
-        double dot = 0.0;
-        for (int c = i + lane; c < d; c += 32) dot = fma(vsh[c - i], wj[c], dot);
-        dot = warp_sum(dot) * tau;
-        for (int c = i + lane; c < d; c += 32) wj[c] = fma(-dot, vsh[c - i], wj[c]);
-        __syncwarp();
-        double rij = wj[i];
-        bool recompute = false;
-        double newn = nj;
-        if (nj != 0.0) {
-          double t = fabs(rij) / nj;
-          t = fmax(0.0, (1.0 + t) * (1.0 - t));
-          double r = nj / nrm0[j];
-          double t2 = t * r * r;
-          if (t2 <= tol3z) recompute = true;
-          else newn = nj * sqrt(t);
-        }
-        if (recompute) {
-          double ss = 0.0;
-          for (int c = i + 1 + lane; c < d; c += 32) ss = fma(wj[c], wj[c], ss);
-          ss = warp_sum(ss);
-          newn = sqrt(ss);
-          if (lane == 0) nrm0[j] = newn;
-        }
-        if (lane == 0) nrm[j] = newn;
+    for (int jl = warp; jl < mloc; jl += ID_WARPS) {
+      double nj = nrm[jl];
+      if (nj < 0.0) continue;
+      double* wj = col(jl);
+      double dot = 0.0;
+      for (int c = i + lane; c < d; c += 32) dot = fma(vloc[c - i], wj[c], dot);
+      dot = warp_sum(dot) * tau;
+      for (int c = i + lane; c < d; c += 32) wj[c] = fma(-dot, vloc[c - i], wj[c]);
+      __syncwarp();
+      double rij = wj[i];
+      bool recompute = false;
+      double newn = nj;
+      if (nj != 0.0) {
+        double t = fabs(rij) / nj;
+        t = fmax(0.0, (1.0 + t) * (1.0 - t));
+        double r = nj / nrm0[jl];
+        if (t * r * r <= tol3z) recompute = true;
+        else newn = nj * sqrt(t);
       }
+      if (recompute) {
+        double ss = 0.0;
+        for (int c = i + 1 + lane; c < d; c += 32) ss = fma(wj[c], wj[c], ss);
+        ss = warp_sum(ss);
+        newn = sqrt(ss);
+        if (lane == 0) nrm0[jl] = newn;
+      }
+      if (lane == 0) nrm[jl] = newn;
     }
     __syncthreads();
+    publish_candidate();
   }
 
-  // perm[k..m) = remaining columns in increasing order
+  // R1 (k x k, column b = pivot b's first b+1 entries) to global, remaining
+  // columns flagged for the ordering of perm[k..m)
+  double* R1 = r1buf_base + r1off[item];
+  int* flag = reinterpret_cast<int*>(it.norms);   // m ints of the norms scratch
+  for (int jl = warp; jl < mloc; jl += ID_WARPS) {
+    const int j = jl * C + crank;
+    const int b = pstep[jl];
+    if (b >= 0 && b < k) {
+      const double* w = col(jl);
+      for (int a = lane; a <= b; a += 32) R1[(size_t)b * k + a] = w[a];
+    }
+    if (lane == 0) flag[j] = (b < 0 || b >= k) ? 1 : 0;
+  }
+  cluster.sync();   // R1 and flags visible to the whole cluster
+  if (crank == 0 && tid == 0) *it.k = k;
+  // position of each remaining column in perm[k..m): count of remaining
+  // columns of lower index (one serial scan per CTA; m is small)
+  int* restpos = pstep;   // reuse: local rest position
   if (tid == 0) {
-    int q = k;
-    for (int j = 0; j < m; ++j)
-      if (nrm[j] >= 0.0) perm[q++] = j;
-    s_rest_count = q - k;
-    *it.k = k;
+    int q = 0;
+    for (int j = 0; j < m; ++j) {
+      if (flag[j]) {
+        if (j % C == crank) restpos[j / C] = q;
+        ++q;
+      }
+    }
+    for (int jl = 0; jl < mloc; ++jl) {
+      const int j = jl * C + crank;
+      if (!flag[j]) restpos[jl] = -1;
+    }
   }
   __syncthreads();
-  const int nr = m - k;
-  // T = R1^{-1} R2, R1[a][b] = W[perm[b]][a] (a <= b < k), R2[a][q] = W[perm[k+q]][a]
-  for (int q = tid; q < nr; q += ID_THREADS) {
-    const double* r2 = W + (int64_t)perm[k + q] * d;
-    double* e = it.E + (int64_t)q * k;
+  for (int jl = tid; jl < mloc; jl += ID_THREADS) {
+    const int q = restpos[jl];
+    if (q < 0) continue;
+    perm[k + q] = jl * C + crank;
+    const double* r2 = col(jl);
+    double* e = it.E + (size_t)q * k;
     for (int a = k - 1; a >= 0; --a) {
       double s = r2[a];
-      for (int b = a + 1; b < k; ++b) s = fma(-W[(int64_t)perm[b] * d + a], e[b], s);
-      e[a] = s / W[(int64_t)perm[a] * d + a];
+      for (int b = a + 1; b < k; ++b) s = fma(-R1[(size_t)b * k + a], e[b], s);
+      e[a] = s / R1[(size_t)a * k + a];
     }
   }
 }
 
 }  // namespace
 
-Err launch_id_batched(const IdItem* items_dev, int count, bool f64, double rtol, double atol,
-                      int max_d, cudaStream_t s) {
+Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, bool f64,
+                      double rtol, double atol, cudaStream_t s) {
+  const int count = (int)h.size();
   if (count <= 0) return ok();
-  size_t smem = sizeof(double) * (size_t)(max_d > 0 ? max_d : 1);
-  if (f64) {
-    HSS_CUDA_TRY(cudaFuncSetAttribute(id_cpqr_kernel<double>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    id_cpqr_kernel<double><<<count, ID_THREADS, smem, s>>>(items_dev, rtol, atol);
-  } else {
-    HSS_CUDA_TRY(cudaFuncSetAttribute(id_cpqr_kernel<float>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    id_cpqr_kernel<float><<<count, ID_THREADS, smem, s>>>(items_dev, rtol, atol);
+  int max_m = 1, max_d = 1;
+  for (const IdItem& x : h) {
+    max_m = std::max(max_m, x.m);
+    max_d = std::max(max_d, x.d);
   }
-  return check_launch("id_cpqr_kernel");
+  int sms = 152;
+  {
+    int dev = 0;
+    HSS_CUDA_TRY(cudaGetDevice(&dev));
+    HSS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  // cluster size: spread each item over more SMs when the batch is small,
+  // keeping at least ~16 columns per CTA
+  int C = 1;
+  while (C < 16 && (long)count * C * 2 <= sms && max_m / (C * 2) >= 16) C *= 2;
+  const int d = std::max(max_d, 1);
+  auto need = [&](int c) {
+    int mloc = (max_m + c - 1) / c;
+    return sizeof(double) * (2 * (size_t)d + 2 * (size_t)mloc) +
+           sizeof(int) * (size_t)((mloc + 1) & ~1);
+  };
+  size_t base = need(C);
+  size_t wbytes = sizeof(double) * (size_t)((max_m + C - 1) / C) * d;
+  int w_in_smem = base + wbytes <= ID_SMEM_CAP ? 1 : 0;
+  size_t smem = base + (w_in_smem ? wbytes : 0);
+  if (smem > 227 * 1024)
+    return fail(HSS_ERR_INVALID, "ID: sample count d too large for the reflector buffers");
+  // R1 buffers: k <= min(m, d) per item
+  std::vector<int64_t> off(count);
+  int64_t tot = 0;
+  for (int q = 0; q < count; ++q) {
+    off[q] = tot;
+    int64_t kk = std::min(h[q].m, h[q].d);
+    tot += std::max<int64_t>(kk * kk, 1);
+  }
+  double* r1 = nullptr;
+  int64_t* offd = nullptr;
+  HSS_TRY(dalloc_t(&r1, (size_t)tot, s));
+  HSS_TRY(dalloc_t(&offd, (size_t)count, s));
+  HSS_CUDA_TRY(cudaMemcpyAsync(offd, off.data(), count * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  HSS_CUDA_TRY(cudaFuncSetAttribute(id_cpqr_cluster_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HSS_CUDA_TRY(cudaFuncSetAttribute(id_cpqr_cluster_kernel,
+                                    cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(count * C), 1, 1);
+  cfg.blockDim = dim3(ID_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // the cluster must fit in one GPC with this shared memory: shrink C if not
+  while (C > 1) {
+    int nclusters = 0;
+    cudaError_t oe = cudaOccupancyMaxActiveClusters(&nclusters, id_cpqr_cluster_kernel, &cfg);
+    if (oe == cudaSuccess && nclusters > 0) break;
+    cudaGetLastError();
+    C /= 2;
+    attr[0].val.clusterDim.x = C;
+    cfg.gridDim = dim3((unsigned)(count * C), 1, 1);
+    base = need(C);
+    wbytes = sizeof(double) * (size_t)((max_m + C - 1) / C) * d;
+    w_in_smem = base + wbytes <= ID_SMEM_CAP ? 1 : 0;
+    smem = base + (w_in_smem ? wbytes : 0);
+    cfg.dynamicSmemBytes = smem;
+    HSS_CUDA_TRY(cudaFuncSetAttribute(id_cpqr_cluster_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  cudaError_t e = cudaLaunchKernelEx(&cfg, id_cpqr_cluster_kernel, items_dev, f64 ? 1 : 0, rtol,
+                                     atol, w_in_smem, r1, (const int64_t*)offd);
+  Err res = e == cudaSuccess ? check_launch("id_cpqr_cluster_kernel")
+                             : fail(HSS_ERR_CUDA, std::string("id_cpqr_cluster_kernel launch: ") +
+                                                      cudaGetErrorString(e));
+  dfree(r1, s);
+  dfree(offd, s);
+  return res;
 }
 
 }  // namespace hss

@@ -79,9 +79,10 @@ struct IdItem {
   double* work;     // m * d doubles of scratch
   double* norms;    // 2 * m doubles of scratch
 };
-// max_d: largest d of the batch (shared-memory size of the reflector).
-Err launch_id_batched(const IdItem* items_dev, int count, bool f64, double rtol,
-                      double atol, int max_d, cudaStream_t s);
+// items_dev: device copy of `host_items` (the host copy sizes the launch).
+// Each item's norms scratch must hold 2*m doubles and its work m*d doubles.
+Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& host_items, bool f64,
+                      double rtol, double atol, cudaStream_t s);
 
 // --------------------------------------------- batched gathered GEMM
 // out[j][c] = (X ? X[xrow(j)][c] : 0) + sign * sum_l Mat(j,l) * Z[zrow(l)][c]
