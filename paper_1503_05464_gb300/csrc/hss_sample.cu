@@ -179,6 +179,18 @@ __global__ void reduce_partials_kernel(const T* __restrict__ P, int64_t n, int n
 
 }  // namespace
 
+Err launch_reduce_partials(const float* P, int64_t n, int npanel, int nchunk, int64_t c0,
+                           int64_t ncols, float* Sc, int64_t lds, cudaStream_t s) {
+  int64_t total = (int64_t)nchunk * n * S_DC;
+  reduce_partials_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+      P, n, npanel, nchunk, c0, ncols, Sc, lds);
+  return check_launch("reduce_partials_kernel");
+}
+
+Err launch_sample_mma(const float* A, int64_t n, int64_t lda, const float* R, int64_t ldr,
+                      int64_t c0, int64_t ncols, float* Sr, float* Sc, int64_t lds,
+                      const int32_t* leaf_of, int mode, float* P, cudaStream_t s);
+
 size_t sample_scratch_bytes(int64_t n, int64_t ncols, int mode, bool f64) {
   (void)mode;
   int64_t npanel = (n + S_BM - 1) / S_BM;
@@ -190,7 +202,6 @@ template <typename T>
 Err launch_sample(const T* A, int64_t n, int64_t lda, const T* R, int64_t ldr, int64_t c0,
                   int64_t c1, T* Sr, T* Sc, int64_t lds, const int32_t* leaf_of, int mode,
                   SampleScratch* scratch, cudaStream_t s, float* ms_out) {
-  (void)mode;
   int64_t ncols = c1 - c0;
   if (n <= 0 || ncols <= 0) return ok();
   const bool f64 = sizeof(T) == 8;
@@ -214,13 +225,20 @@ Err launch_sample(const T* A, int64_t n, int64_t lda, const T* R, int64_t ldr, i
     HSS_CUDA_TRY(cudaEventRecord(e0, s));
   }
   T* P = reinterpret_cast<T*>(scratch->part);
-  sample_simt_kernel<T><<<npanel * nchunk, S_THREADS, smem, s>>>(
-      A, n, lda, R, ldr, c0, ncols, nchunk, Sr, lds, leaf_of, P);
-  HSS_TRY(check_launch("sample_simt_kernel"));
-  int64_t total = (int64_t)nchunk * n * S_DC;
-  reduce_partials_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-      P, n, npanel, nchunk, c0, ncols, Sc, lds);
-  HSS_TRY(check_launch("reduce_partials_kernel"));
+  if (sizeof(T) == 4 && mode != HSS_SAMPLE_NATIVE) {
+    HSS_TRY(launch_sample_mma(reinterpret_cast<const float*>(A), n, lda,
+                              reinterpret_cast<const float*>(R), ldr, c0, ncols,
+                              reinterpret_cast<float*>(Sr), reinterpret_cast<float*>(Sc), lds,
+                              leaf_of, mode, reinterpret_cast<float*>(P), s));
+  } else {
+    sample_simt_kernel<T><<<npanel * nchunk, S_THREADS, smem, s>>>(
+        A, n, lda, R, ldr, c0, ncols, nchunk, Sr, lds, leaf_of, P);
+    HSS_TRY(check_launch("sample_simt_kernel"));
+    int64_t total = (int64_t)nchunk * n * S_DC;
+    reduce_partials_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        P, n, npanel, nchunk, c0, ncols, Sc, lds);
+    HSS_TRY(check_launch("reduce_partials_kernel"));
+  }
   if (ms_out) {
     HSS_CUDA_TRY(cudaEventRecord(e1, s));
     HSS_CUDA_TRY(cudaEventSynchronize(e1));

@@ -76,7 +76,7 @@ def test_fused_sampling_matches_oracle(P, n, leaf, dtype, c0, c1):
     Sr = torch.full((n, c1), 7.0, dtype=dtype, device=DEV)
     Sc = torch.full((n, c1), 7.0, dtype=dtype, device=DEV)
     nodes = O.bisection_tree(n, leaf)
-    starts = [nd.lo for nd in nodes if nd.is_leaf] + [n]
+    starts = sorted(nd.lo for nd in nodes if nd.is_leaf) + [n]
     P.hss_sample(At, R, c0, c1, Sr, Sc, leaf_starts=starts)
     torch.cuda.synchronize()
     R64 = R.cpu().numpy().astype(np.float64)
@@ -95,7 +95,47 @@ def test_fused_sampling_matches_oracle(P, n, leaf, dtype, c0, c1):
     assert np.all(gr[:, :c0] == 7.0) and np.all(gc[:, :c0] == 7.0)
 
 
-def test_sampling_is_deterministic(P):
+# representation error of A in each sampling mode (R is bfloat16-exact)
+MODE_REL = {"tf32": 2.0 ** -11, "bf16x2": 2.0 ** -16, "bf16x3": 2.0 ** -23}
+
+
+@pytest.mark.parametrize("mode", ["tf32", "bf16x2", "bf16x3"])
+@pytest.mark.parametrize("n,leaf,c0,c1", [(1000, 125, 0, 64), (1283, 100, 33, 161), (517, 64, 0, 128)])
+def test_tensor_core_sampling_matches_oracle(P, mode, n, leaf, c0, c1):
+    rng = np.random.default_rng(n + len(mode))
+    A = rng.standard_normal((n, n)) * np.exp(rng.standard_normal((n, n)))   # wide magnitudes
+    A[: n // 3] *= 3.0
+    At = torch.tensor(A, dtype=torch.float32, device=DEV)
+    A64 = At.cpu().numpy().astype(np.float64)
+    R = torch.zeros((n, c1), dtype=torch.float32, device=DEV)
+    P.hss_random_gaussian(5, n, 0, c1, R)
+    Sr = torch.full((n, c1), 7.0, device=DEV)
+    Sc = torch.full((n, c1), 7.0, device=DEV)
+    nodes = O.bisection_tree(n, leaf)
+    starts = sorted(nd.lo for nd in nodes if nd.is_leaf) + [n]
+    P.hss_sample(At, R, c0, c1, Sr, Sc, leaf_starts=starts, mode=mode)
+    torch.cuda.synchronize()
+    R64 = R.cpu().numpy().astype(np.float64)
+    wr, wc = O.leaf_local_samples(A64, R64[:, c0:c1], nodes)
+    mask = np.ones((n, n))
+    for nd in nodes:
+        if nd.is_leaf:
+            mask[nd.lo:nd.hi, nd.lo:nd.hi] = 0
+    br = (np.abs(A64) * mask) @ np.abs(R64[:, c0:c1])
+    bc = (np.abs(A64) * mask).T @ np.abs(R64[:, c0:c1])
+    tol = MODE_REL[mode] + 4 * n * 2.0 ** -24
+    gr = Sr.cpu().numpy().astype(np.float64)
+    gc = Sc.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(gr[:, c0:c1] - wr) <= tol * br)
+    assert np.all(np.abs(gc[:, c0:c1] - wc) <= tol * bc)
+    assert np.all(gr[:, :c0] == 7.0) and np.all(gc[:, :c0] == 7.0)
+    # the split modes must actually be more accurate than one bfloat16 term
+    if mode == "bf16x3":
+        assert np.abs(gr[:, c0:c1] - wr).max() <= 1e-5 * np.abs(wr).max()
+
+
+@pytest.mark.parametrize("mode", ["native", "bf16x3"])
+def test_sampling_is_deterministic(P, mode):
     n = 900
     A = torch.randn(n, n, device=DEV)
     R = torch.zeros((n, 64), device=DEV)
@@ -104,7 +144,7 @@ def test_sampling_is_deterministic(P):
     for _ in range(2):
         Sr = torch.empty((n, 64), device=DEV)
         Sc = torch.empty((n, 64), device=DEV)
-        P.hss_sample(A, R, 0, 64, Sr, Sc, leaf_starts=[0, 300, 600, 900])
+        P.hss_sample(A, R, 0, 64, Sr, Sc, leaf_starts=[0, 300, 600, 900], mode=mode)
         outs.append((Sr.clone(), Sc.clone()))
     assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
 
@@ -251,14 +291,16 @@ def test_compress_unsymmetric_fp32(P):
     assert _rel(A32 @ xs, b) <= 10 * max(_rel(A32 @ xo, b), 1e-6)
 
 
-def test_compress_gaussian_kernel_fp32_reduced(P):
+@pytest.mark.parametrize("mode", ["native", "bf16x3"])
+def test_compress_gaussian_kernel_fp32_reduced(P, mode):
     """Config-2 family at n=4000 (points in the unit cube, RCB order)."""
     n, leaf, rtol = 4000, 256, 1e-4
     pts = W.points_unit_cube(n, 1002)
     pts = pts[W.rcb_order(pts, leaf)]
     At = W.gaussian_kernel(pts, 0.2, 1.0, dtype=np.float32, device=DEV)
     A32 = At.cpu().numpy().astype(np.float64)
-    h = P.hss_compress(At, leaf_size=leaf, rtol=rtol, d0=128, d_step=64, seed=1003)
+    h = P.hss_compress(At, leaf_size=leaf, rtol=rtol, d0=128, d_step=64, seed=1003,
+                       sample_mode=mode)
     ho = O.compress(A32, rtol, leaf_size=leaf, d0=128, d_step=64, seed=1003)
     _ranks_close(P, h, ho)
     H = _dense_from_gpu(P, h, n, torch.float32)
