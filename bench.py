@@ -242,6 +242,9 @@ def run_ours(args, wl):
                    "family": wl["family"], "l2": "input larger than L2 (no flush needed)"},
         "roofline": roof,
         "phases": phases,
+        "host_ms": {k: round(statistics.mean(i[k] for i in infos), 3) for k in
+                    ("ms_compress", "ms_levels", "ms_host_id_launch", "ms_host_wait",
+                     "ms_host_sample")},
         "hss": {"passes": info["passes"], "d_final": info["d_final"],
                 "max_rank": max(info["max_rank_r"], info["max_rank_c"]),
                 "bytes_hss": info["bytes_hss"], "levels": info["levels"]},
@@ -317,11 +320,14 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="gauss20k", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="native", choices=["native", "tf32", "bf16x2", "bf16x3"])
+    ap.add_argument("--mode", default=None, choices=["native", "tf32", "bf16x2", "bf16x3"],
+                    help="sampling arithmetic (default: bf16x3 for FP32 inputs, native for FP64)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
+    if args.mode is None:
+        args.mode = "bf16x3" if wl["dtype"] == "f32" else "native"
     if args.steps is None:
         args.steps = 3 if args.impl == "reference" else 10
     if args.impl == "reference":

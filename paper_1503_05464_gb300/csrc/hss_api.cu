@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <numeric>
 
 namespace hss {
@@ -31,14 +32,42 @@ Err check_launch(const char* what) {
   return ok();
 }
 
+// The library allocates from its own stream-ordered pool, one per device,
+// that keeps freed memory reserved (release threshold = max): repeated
+// compressions reuse their multi-gigabyte scratch instead of remapping it.
+static Err library_pool(cudaMemPool_t* out) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  HSS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(HSS_ERR_INVALID, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    HSS_CUDA_TRY(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = UINT64_MAX;
+    HSS_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    pools[dev] = pool;
+  }
+  *out = pools[dev];
+  return ok();
+}
+
 Err dalloc(void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
   if (bytes == 0) return ok();
-  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  cudaMemPool_t pool;
+  HSS_TRY(library_pool(&pool));
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
-    return fail(HSS_ERR_OOM, "cudaMallocAsync(" + std::to_string(bytes) + " bytes): " +
+    return fail(HSS_ERR_OOM, "cudaMallocFromPoolAsync(" + std::to_string(bytes) + " bytes): " +
                                  cudaGetErrorString(e));
   }
   return ok();
@@ -74,27 +103,39 @@ struct Compressor {
   T* Sc = nullptr;
   int32_t* leaf_of = nullptr;
   SampleScratch scratch;
+  Arena tmp{(size_t)64 << 20};   // per-node samples S_tau, R_tau (freed after compression)
+  Arena lvl{(size_t)64 << 20};   // per-level scratch, rewound at every level
+  PinnedStage stage;             // pinned staging of the level's item tables
   float ms_sample = 0.f, ms_id = 0.f;
+  Compressor(hss_s* h_, const T* A_, int64_t lda_, cudaStream_t s_)
+      : h(h_), A(A_), lda(lda_), s(s_) {
+    lvl.stage = &stage;
+  }
 
   ~Compressor() {
+    cudaStreamSynchronize(s);   // staged uploads and in-flight kernels are done
     dfree(R, s);
     dfree(Sr, s);
     dfree(Sc, s);
     dfree(leaf_of, s);
     dfree(scratch.part, s);
+    tmp.release(s);
+    lvl.release(s);
   }
 
   int64_t n() const { return h->n; }
 
-  // grow a rows x old_ld row-major buffer to new_ld (keeps the first `cols` columns)
-  Err regrow(T** p, int64_t rows, int old_ld, int new_ld, int cols) {
+  // grow a rows x old_ld row-major buffer to new_ld (keeps the first `cols`
+  // columns); global buffers are freed, node buffers come from `tmp`
+  Err regrow(T** p, int64_t rows, int old_ld, int new_ld, int cols, bool node) {
     if (!*p || rows == 0) return ok();
     T* q = nullptr;
-    HSS_TRY(dalloc_t(&q, (size_t)rows * new_ld, s));
+    if (node) HSS_TRY(tmp.alloc_t(&q, (size_t)rows * new_ld, s));
+    else HSS_TRY(dalloc_t(&q, (size_t)rows * new_ld, s));
     if (cols > 0)
       HSS_CUDA_TRY(cudaMemcpy2DAsync(q, sizeof(T) * new_ld, *p, sizeof(T) * old_ld,
                                      sizeof(T) * cols, rows, cudaMemcpyDeviceToDevice, s));
-    dfree(*p, s);
+    if (!node) dfree(*p, s);
     *p = q;
     return ok();
   }
@@ -108,21 +149,33 @@ struct Compressor {
     nc = (nc + 31) / 32 * 32;
     int old = h->dcap, cols = h->d;
     for (T** g : {&R, &Sr, &Sc}) {
-      if (*g) HSS_TRY(regrow(g, n(), old, nc, cols));
+      if (*g) HSS_TRY(regrow(g, n(), old, nc, cols, false));
       else HSS_TRY(dalloc_t(g, (size_t)n() * nc, s));
     }
     for (size_t i = 0; i < h->gen.size(); ++i) {
       NodeGen& g = h->gen[i];
-      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Sr), g.kr, old, nc, g.ncols));
-      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Sc), g.kc, old, nc, g.ncols));
-      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Rr), g.kc, old, nc, g.ncols));
-      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Rc), g.kr, old, nc, g.ncols));
+      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Sr), g.kr, old, nc, g.ncols, true));
+      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Sc), g.kc, old, nc, g.ncols, true));
+      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Rr), g.kc, old, nc, g.ncols, true));
+      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Rc), g.kr, old, nc, g.ncols, true));
     }
     h->dcap = nc;
     return ok();
   }
 
+  static double now_ms() {
+    return std::chrono::duration<double, std::milli>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+  }
+
   Err sample_columns(int c0, int c1) {
+    const double t0 = now_ms();
+    struct Acc {
+      double t0;
+      double* dst;
+      ~Acc() { *dst += now_ms() - t0; }
+    } acc{t0, &h->info.ms_host_sample};
     HSS_TRY(launch_random_gaussian<T>(h->opts.seed, n(), c0, c1, R, h->dcap, s));
     float ms = 0.f;
     HSS_TRY(launch_sample<T>(A, n(), lda, R, h->dcap, c0, c1, Sr, Sc, h->dcap, leaf_of,
@@ -160,7 +213,7 @@ Err Compressor<T>::run() {
     if (nd.c1 >= 0) continue;
     int m = nd.hi - nd.lo;
     NodeGen& g = h->gen[i];
-    HSS_TRY(dalloc(&g.D, sizeof(T) * m * m, s));
+    HSS_TRY(h->store.alloc(&g.D, sizeof(T) * m * m, s));
     HSS_CUDA_TRY(cudaMemcpy2DAsync(g.D, sizeof(T) * m, A + (int64_t)nd.lo * lda + nd.lo,
                                    sizeof(T) * lda, sizeof(T) * m, m, cudaMemcpyDeviceToDevice,
                                    s));
@@ -179,18 +232,20 @@ Err Compressor<T>::run() {
   h->d = d;
   while (true) {
     h->passes++;
+    const double tl0 = now_ms();
     for (int depth = tr.maxdepth; depth >= 1; --depth) HSS_TRY(process_level(depth));
+    h->info.ms_levels += now_ms() - tl0;
     const TNode& root = tr.nodes[0];
     NodeGen& g1 = h->gen[root.c1];
     NodeGen& g2 = h->gen[root.c2];
     if (g1.state == NODE_COMPRESSED && g2.state == NODE_COMPRESSED) {
       NodeGen& g0 = h->gen[0];
-      HSS_TRY(dalloc(&g0.B12, sizeof(T) * g1.kr * g2.kc, s));
-      HSS_TRY(dalloc(&g0.B21, sizeof(T) * g2.kr * g1.kc, s));
+      HSS_TRY(h->store.alloc(&g0.B12, sizeof(T) * g1.kr * g2.kc, s));
+      HSS_TRY(h->store.alloc(&g0.B21, sizeof(T) * g2.kr * g1.kc, s));
       std::vector<GatherItem<T>> gi = {
           {reinterpret_cast<T*>(g0.B12), g1.Ir, g2.Ic, g1.kr, g2.kc},
           {reinterpret_cast<T*>(g0.B21), g2.Ir, g1.Ic, g2.kr, g1.kc}};
-      HSS_TRY(launch_gather_batched<T>(A, lda, gi, s, nullptr, 0));
+      HSS_TRY(launch_gather_batched<T>(A, lda, gi, s, nullptr, 0, &lvl));
       h->info.bytes_hss += sizeof(T) * ((int64_t)g1.kr * g2.kc + (int64_t)g2.kr * g1.kc);
       g0.state = NODE_COMPRESSED;
       break;
@@ -212,6 +267,7 @@ template <typename T>
 Err Compressor<T>::process_level(int depth) {
   Tree& tr = h->tree;
   const int d = h->d, ld = h->dcap;
+  lvl.reset();   // earlier levels' scratch: reused in stream order
   std::vector<int> fresh, update;
   for (int id : tr.levels[depth]) {
     const TNode& nd = tr.nodes[id];
@@ -239,12 +295,12 @@ Err Compressor<T>::process_level(int depth) {
       if (g.B12) continue;   // kept from an earlier failed pass (children unchanged)
       NodeGen& a = h->gen[nd.c1];
       NodeGen& b = h->gen[nd.c2];
-      HSS_TRY(dalloc(&g.B12, sizeof(T) * a.kr * b.kc, s));
-      HSS_TRY(dalloc(&g.B21, sizeof(T) * b.kr * a.kc, s));
+      HSS_TRY(h->store.alloc(&g.B12, sizeof(T) * a.kr * b.kc, s));
+      HSS_TRY(h->store.alloc(&g.B21, sizeof(T) * b.kr * a.kc, s));
       gi.push_back({reinterpret_cast<T*>(g.B12), a.Ir, b.Ic, a.kr, b.kc});
       gi.push_back({reinterpret_cast<T*>(g.B21), b.Ir, a.Ic, b.kr, a.kc});
     }
-    HSS_TRY(launch_gather_batched<T>(A, lda, gi, s, nullptr, 0));
+    HSS_TRY(launch_gather_batched<T>(A, lda, gi, s, nullptr, 0, &lvl));
   }
 
   // local samples Y^r, Y^c (m x ld row-major; row j = column j of the ID input)
@@ -266,8 +322,8 @@ Err Compressor<T>::process_level(int depth) {
     NodeGen& b = h->gen[nd.c2];
     L.mr = a.kr + b.kr;
     L.mc = a.kc + b.kc;
-    HSS_TRY(dalloc_t(&L.own_r, (size_t)std::max(L.mr, 1) * ld, s));
-    HSS_TRY(dalloc_t(&L.own_c, (size_t)std::max(L.mc, 1) * ld, s));
+    HSS_TRY(lvl.alloc_t(&L.own_r, (size_t)std::max(L.mr, 1) * ld, s));
+    HSS_TRY(lvl.alloc_t(&L.own_c, (size_t)std::max(L.mc, 1) * ld, s));
     L.Yr = L.own_r;
     L.Yc = L.own_c;
     auto item = [&](T* out, int rows, const T* X, const void* M, int64_t ldm, int trans,
@@ -316,7 +372,7 @@ Err Compressor<T>::process_level(int depth) {
   for (int id : fresh) HSS_TRY(make_loc(id, 0));
   const size_t nfresh = loc.size();
   for (int id : update) HSS_TRY(make_loc(id, h->gen[id].ncols));
-  HSS_TRY(launch_gemm_batched<T>(gm, s, nullptr, 0));
+  HSS_TRY(launch_gemm_batched<T>(gm, s, nullptr, 0, &lvl));
   gm.clear();
 
   // batched ID of every fresh node, row and column side
@@ -331,19 +387,19 @@ Err Compressor<T>::process_level(int depth) {
     double* nbuf = nullptr;
     int32_t* kbuf = nullptr;
     IdItem* ibuf = nullptr;
-    HSS_TRY(dalloc_t(&wbuf, std::max<size_t>(work, 1), s));
-    HSS_TRY(dalloc_t(&nbuf, std::max<size_t>(norms, 1), s));
-    HSS_TRY(dalloc_t(&kbuf, 2 * nfresh, s));
-    HSS_TRY(dalloc_t(&ibuf, 2 * nfresh, s));
+    HSS_TRY(lvl.alloc_t(&wbuf, std::max<size_t>(work, 1), s));
+    HSS_TRY(lvl.alloc_t(&nbuf, std::max<size_t>(norms, 1), s));
+    HSS_TRY(lvl.alloc_t(&kbuf, 2 * nfresh, s));
+    HSS_TRY(lvl.alloc_t(&ibuf, 2 * nfresh, s));
     size_t wo = 0, no = 0;
     for (size_t q = 0; q < nfresh; ++q) {
       Loc& L = loc[q];
       NodeGen& g = h->gen[L.id];
-      g.free_id(s);
-      HSS_TRY(dalloc_t(&g.permr, std::max(L.mr, 1), s));
-      HSS_TRY(dalloc_t(&g.permc, std::max(L.mc, 1), s));
-      HSS_TRY(dalloc_t(&g.Er, std::max<size_t>((size_t)L.mr * std::min(L.mr, d), 1), s));
-      HSS_TRY(dalloc_t(&g.Ec, std::max<size_t>((size_t)L.mc * std::min(L.mc, d), 1), s));
+      g.free_id();
+      HSS_TRY(h->store.alloc_t(&g.permr, std::max(L.mr, 1), s));
+      HSS_TRY(h->store.alloc_t(&g.permc, std::max(L.mc, 1), s));
+      HSS_TRY(h->store.alloc_t(&g.Er, std::max<size_t>((size_t)L.mr * std::min(L.mr, d), 1), s));
+      HSS_TRY(h->store.alloc_t(&g.Ec, std::max<size_t>((size_t)L.mc * std::min(L.mc, d), 1), s));
       IdItem a{L.Yr, L.mr, d, ld, g.permr, g.Er, kbuf + 2 * q, wbuf + wo, nbuf + no};
       wo += (size_t)L.mr * d;
       no += 2 * (size_t)L.mr;
@@ -354,28 +410,28 @@ Err Compressor<T>::process_level(int depth) {
       items.push_back(b);
       h->info.flops_id += 0.0;  // filled after ranks are known
     }
-    HSS_CUDA_TRY(cudaMemcpyAsync(ibuf, items.data(), items.size() * sizeof(IdItem),
-                                 cudaMemcpyHostToDevice, s));
+    HSS_TRY(lvl.upload(ibuf, items.data(), items.size() * sizeof(IdItem), s));
     cudaEvent_t e0, e1;
     HSS_CUDA_TRY(cudaEventCreate(&e0));
     HSS_CUDA_TRY(cudaEventCreate(&e1));
+    const double th0 = now_ms();
     HSS_CUDA_TRY(cudaEventRecord(e0, s));
-    HSS_TRY(launch_id_batched(ibuf, items, sizeof(T) == 8, h->opts.rtol, h->opts.atol, s));
+    HSS_TRY(launch_id_batched(ibuf, items, sizeof(T) == 8, h->opts.rtol, h->opts.atol, s, &lvl));
     HSS_CUDA_TRY(cudaEventRecord(e1, s));
+    h->info.ms_host_id_launch += now_ms() - th0;
     std::vector<int32_t> ks(2 * nfresh);
     HSS_CUDA_TRY(cudaMemcpyAsync(ks.data(), kbuf, ks.size() * sizeof(int32_t),
                                  cudaMemcpyDeviceToHost, s));
     h->info.bytes_d2h += (int64_t)(ks.size() * sizeof(int32_t));
+    const double tw0 = now_ms();
     HSS_CUDA_TRY(cudaStreamSynchronize(s));
+    h->info.ms_host_wait += now_ms() - tw0;
+    stage.reset();   // every staged upload so far has landed
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     ms_id += ms;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    dfree(wbuf, s);
-    dfree(nbuf, s);
-    dfree(kbuf, s);
-    dfree(ibuf, s);
 
     // adaptive test (Section 3.2): fail iff d < m and k > d - p on either side
     const int p = h->opts.oversample_p;
@@ -388,7 +444,7 @@ Err Compressor<T>::process_level(int depth) {
       bool failc = d < L.mc && kc > d - p;
       if (failr || failc) {
         g.state = NODE_PARTIALLY;
-        g.free_id(s);
+        g.free_id();
         continue;
       }
       g.kr = kr;
@@ -402,7 +458,7 @@ Err Compressor<T>::process_level(int depth) {
   }
 
   // selections and basis products for fresh (all columns) and updated nodes
-  std::vector<int32_t*> idx_jobs;
+  std::vector<IndexItem> idx_items;
   for (size_t q = 0; q < loc.size(); ++q) {
     Loc& L = loc[q];
     const TNode& nd = tr.nodes[L.id];
@@ -411,12 +467,12 @@ Err Compressor<T>::process_level(int depth) {
     const bool is_fresh = q < nfresh;
     int c0 = is_fresh ? 0 : g.ncols;
     if (is_fresh) {
-      HSS_TRY(dalloc(&g.Sr, sizeof(T) * std::max(g.kr, 1) * ld, s));
-      HSS_TRY(dalloc(&g.Sc, sizeof(T) * std::max(g.kc, 1) * ld, s));
-      HSS_TRY(dalloc(&g.Rr, sizeof(T) * std::max(g.kc, 1) * ld, s));
-      HSS_TRY(dalloc(&g.Rc, sizeof(T) * std::max(g.kr, 1) * ld, s));
-      HSS_TRY(dalloc_t(&g.Ir, std::max(g.kr, 1), s));
-      HSS_TRY(dalloc_t(&g.Ic, std::max(g.kc, 1), s));
+      HSS_TRY(tmp.alloc(&g.Sr, sizeof(T) * std::max(g.kr, 1) * ld, s));
+      HSS_TRY(tmp.alloc(&g.Sc, sizeof(T) * std::max(g.kc, 1) * ld, s));
+      HSS_TRY(tmp.alloc(&g.Rr, sizeof(T) * std::max(g.kc, 1) * ld, s));
+      HSS_TRY(tmp.alloc(&g.Rc, sizeof(T) * std::max(g.kr, 1) * ld, s));
+      HSS_TRY(h->store.alloc_t(&g.Ir, std::max(g.kr, 1), s));
+      HSS_TRY(h->store.alloc_t(&g.Ic, std::max(g.kc, 1), s));
     }
     // S^r_tau = S^r_loc(J^r, :), S^c_tau = S^c_loc(J^c, :)
     GemmItem<T> it{};
@@ -481,32 +537,21 @@ Err Compressor<T>::process_level(int depth) {
     if (is_fresh) {
       // skeleton index sets I^r = I(J^r), I^c = I(J^c)
       if (nd.c1 < 0) {
-        HSS_TRY(launch_index_compose(g.Ir, tr.iota_dev + nd.lo, g.permr, g.kr, s));
-        HSS_TRY(launch_index_compose(g.Ic, tr.iota_dev + nd.lo, g.permc, g.kc, s));
+        idx_items.push_back({g.Ir, g.permr, nullptr, nullptr, 0, nd.lo, g.kr});
+        idx_items.push_back({g.Ic, g.permc, nullptr, nullptr, 0, nd.lo, g.kc});
       } else {
         NodeGen& a = h->gen[nd.c1];
         NodeGen& b = h->gen[nd.c2];
-        int32_t* cat = nullptr;
-        HSS_TRY(dalloc_t(&cat, std::max(1, a.kr + b.kr + a.kc + b.kc), s));
-        if (a.kr) HSS_CUDA_TRY(cudaMemcpyAsync(cat, a.Ir, a.kr * 4, cudaMemcpyDeviceToDevice, s));
-        if (b.kr)
-          HSS_CUDA_TRY(cudaMemcpyAsync(cat + a.kr, b.Ir, b.kr * 4, cudaMemcpyDeviceToDevice, s));
-        int32_t* catc = cat + a.kr + b.kr;
-        if (a.kc) HSS_CUDA_TRY(cudaMemcpyAsync(catc, a.Ic, a.kc * 4, cudaMemcpyDeviceToDevice, s));
-        if (b.kc)
-          HSS_CUDA_TRY(cudaMemcpyAsync(catc + a.kc, b.Ic, b.kc * 4, cudaMemcpyDeviceToDevice, s));
-        HSS_TRY(launch_index_compose(g.Ir, cat, g.permr, g.kr, s));
-        HSS_TRY(launch_index_compose(g.Ic, catc, g.permc, g.kc, s));
-        dfree(cat, s);
+        idx_items.push_back({g.Ir, g.permr, a.Ir, b.Ir, a.kr, 0, g.kr});
+        idx_items.push_back({g.Ic, g.permc, a.Ic, b.Ic, a.kc, 0, g.kc});
       }
     }
   }
-  HSS_TRY(launch_gemm_batched<T>(gm, s, nullptr, 0));
+  HSS_TRY(launch_index_batched(idx_items, s, &lvl));
+  HSS_TRY(launch_gemm_batched<T>(gm, s, nullptr, 0, &lvl));
   for (size_t q = 0; q < loc.size(); ++q) {
     NodeGen& g = h->gen[loc[q].id];
     if (g.state == NODE_COMPRESSED) g.ncols = d;
-    dfree(loc[q].own_r, s);
-    dfree(loc[q].own_c, s);
   }
   return ok();
 }
@@ -560,12 +605,12 @@ hss_status hss_compress(const void* A, int64_t n, int64_t lda, hss_dtype dtype,
   Err e = build_bisection_tree(h->tree, n, o.leaf_size, h->stream);
   if (e.st == HSS_OK) {
     if (dtype == HSS_F32) {
-      Compressor<float> c{h.get(), (const float*)A, lda, h->stream};
+      Compressor<float> c(h.get(), (const float*)A, lda, h->stream);
       e = c.run();
       h->info.ms_sample = c.ms_sample;
       h->info.ms_id = c.ms_id;
     } else {
-      Compressor<double> c{h.get(), (const double*)A, lda, h->stream};
+      Compressor<double> c(h.get(), (const double*)A, lda, h->stream);
       e = c.run();
       h->info.ms_sample = c.ms_sample;
       h->info.ms_id = c.ms_id;

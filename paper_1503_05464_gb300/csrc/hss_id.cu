@@ -11,9 +11,10 @@
 //      columns; after a cluster barrier each CTA reads all C candidates
 //      through distributed shared memory and picks the same pivot (largest
 //      norm, lowest index on ties);
-//   2. the pivot's owner recomputes that column's residual norm exactly
-//      (|R_ii|), takes the stopping decision against max(rtol |R_11|, atol),
-//      builds the Householder reflector and publishes it with the decision;
+//   2. one warp of the pivot's owner recomputes that column's residual norm
+//      exactly (|R_ii|), takes the stopping decision against
+//      max(rtol |R_11|, atol), builds the Householder reflector and publishes
+//      it with the decision;
 //   3. after a second cluster barrier every CTA copies the reflector, applies
 //      it to its active columns (one warp per column: dot product, warp
 //      reduction, update), downdates their norms -- recomputing a norm when
@@ -31,6 +32,8 @@
 #include <algorithm>
 #include <cfloat>
 #include <climits>
+#include <map>
+#include <mutex>
 
 namespace cg = cooperative_groups;
 
@@ -77,7 +80,6 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in, double rtol,
   __shared__ Pub pub;
   __shared__ double redv[ID_WARPS];
   __shared__ int redi[ID_WARPS];
-  __shared__ double s_a, s_t;
 
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
@@ -98,9 +100,18 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in, double rtol,
   double* nrm0 = nrm + mloc_max;                  // mloc_max
   int* pstep = reinterpret_cast<int*>(nrm0 + mloc_max);   // mloc_max: pivot step or -1
   double* Wsm = reinterpret_cast<double*>(pstep + ((mloc_max + 1) & ~1));
+  // odd column stride in shared memory: a thread per column reads without
+  // bank conflicts
+  const int ldw = d | 1;
   auto col = [&](int jl) -> double* {
-    return w_in_smem ? Wsm + (size_t)jl * d : it.work + (size_t)(jl * C + crank) * d;
+    return w_in_smem ? Wsm + (size_t)jl * ldw : it.work + (size_t)(jl * C + crank) * d;
   };
+  // team of TS threads per column (power of two): all 256 threads stay busy
+  // whether a CTA owns 8 columns or 500
+  int TS = 1;
+  while (TS < 32 && mloc_max * TS * 2 <= ID_THREADS) TS *= 2;
+  const int member = lane & (TS - 1);
+  const int cols_per_warp = 32 / TS;
   const double tol3z = sqrt(DBL_EPSILON * 0.5);
   int32_t* perm = it.perm;
 
@@ -168,9 +179,11 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in, double rtol,
   double r11 = 0.0;
   for (int i = 0; i < kmax; ++i) {
     cluster.sync();   // (A) candidates published
+    // every warp reads the C candidates in parallel (lane r <- CTA r) and
+    // reduces them: all threads agree on the pivot without a block barrier
     double bv = -1.0;
     int p = INT_MAX;
-    for (int r = 0; r < C; ++r) {
+    for (int r = lane; r < C; r += 32) {
       const Pub* rp = cluster.map_shared_rank(&pub, r);
       double v = rp->cand_val;
       int j = rp->cand_idx;
@@ -179,49 +192,34 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in, double rtol,
         p = j;
       }
     }
+    warp_argmax(bv, p);
     const int owner = p % C;
-    if (owner == crank) {
-      // exact residual norm of the pivot column and its reflector
+    if (owner == crank && warp == 0) {
+      // one warp: exact residual norm of the pivot column and its reflector
       double* wp = col(p / C);
       double sa = 0.0, st = 0.0;
-      for (int c = i + tid; c < d; c += ID_THREADS) {
+      for (int c = i + lane; c < d; c += 32) {
         double x = wp[c];
         sa = fma(x, x, sa);
         if (c > i) st = fma(x, x, st);
       }
       sa = warp_sum(sa);
       st = warp_sum(st);
-      if (lane == 0) redv[warp] = sa;
-      __syncthreads();
-      if (tid == 0) {
-        double a = 0.0;
-        for (int q = 0; q < ID_WARPS; ++q) a += redv[q];
-        s_a = a;
-      }
-      __syncthreads();
-      if (lane == 0) redv[warp] = st;
-      __syncthreads();
-      if (tid == 0) {
-        double t = 0.0;
-        for (int q = 0; q < ID_WARPS; ++q) t += redv[q];
-        s_t = t;
-      }
-      __syncthreads();
-      const double sigma = sqrt(s_a);
+      const double sigma = sqrt(sa);
       const double r11_now = (i == 0) ? sigma : r11;
       const int stop = (r11_now == 0.0 || sigma <= fmax(rtol * r11_now, atol)) ? 1 : 0;
       const double alpha = wp[i];
       double tau = 0.0, beta = alpha, scal = 0.0;
-      if (!stop && s_t != 0.0) {
+      if (!stop && st != 0.0) {
         beta = -copysign(sigma, alpha);
         tau = (beta - alpha) / beta;
         scal = 1.0 / (alpha - beta);
       }
       if (!stop) {
-        for (int c = i + tid; c < d; c += ID_THREADS) vbuf[c - i] = (c == i) ? 1.0 : wp[c] * scal;
+        for (int c = i + lane; c < d; c += 32) vbuf[c - i] = (c == i) ? 1.0 : wp[c] * scal;
       }
-      __syncthreads();
-      if (tid == 0) {
+      __syncwarp();
+      if (lane == 0) {
         pub.stop = stop;
         pub.tau = tau;
         pub.r11 = r11_now;
@@ -245,33 +243,42 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in, double rtol,
     const double* ov = cluster.map_shared_rank(vbuf, owner);
     for (int c = tid; c < d - i; c += ID_THREADS) vloc[c] = ov[c];
     __syncthreads();
-    for (int jl = warp; jl < mloc; jl += ID_WARPS) {
-      double nj = nrm[jl];
-      if (nj < 0.0) continue;
-      double* wj = col(jl);
+    for (int jb = warp * cols_per_warp; jb < mloc; jb += ID_WARPS * cols_per_warp) {
+      const int jl = jb + lane / TS;
+      const double nj = jl < mloc ? nrm[jl] : -1.0;
+      const bool act = nj >= 0.0;
+      double* wj = act ? col(jl) : nullptr;
       double dot = 0.0;
-      for (int c = i + lane; c < d; c += 32) dot = fma(vloc[c - i], wj[c], dot);
-      dot = warp_sum(dot) * tau;
-      for (int c = i + lane; c < d; c += 32) wj[c] = fma(-dot, vloc[c - i], wj[c]);
+      if (act)
+        for (int c = i + member; c < d; c += TS) dot = fma(vloc[c - i], wj[c], dot);
+      for (int o = TS >> 1; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+      dot *= tau;
+      if (act)
+        for (int c = i + member; c < d; c += TS) wj[c] = fma(-dot, vloc[c - i], wj[c]);
       __syncwarp();
-      double rij = wj[i];
+      // norm downdate by the team leader (LAPACK xGEQP3 safeguard)
       bool recompute = false;
       double newn = nj;
-      if (nj != 0.0) {
+      if (act && member == 0 && nj != 0.0) {
+        const double rij = wj[i];
         double t = fabs(rij) / nj;
         t = fmax(0.0, (1.0 + t) * (1.0 - t));
         double r = nj / nrm0[jl];
         if (t * r * r <= tol3z) recompute = true;
         else newn = nj * sqrt(t);
       }
-      if (recompute) {
+      recompute = __shfl_sync(0xffffffffu, recompute ? 1 : 0, lane & ~(TS - 1)) != 0;
+      if (__any_sync(0xffffffffu, recompute)) {
         double ss = 0.0;
-        for (int c = i + 1 + lane; c < d; c += 32) ss = fma(wj[c], wj[c], ss);
-        ss = warp_sum(ss);
-        newn = sqrt(ss);
-        if (lane == 0) nrm0[jl] = newn;
+        if (recompute)
+          for (int c = i + 1 + member; c < d; c += TS) ss = fma(wj[c], wj[c], ss);
+        for (int o = TS >> 1; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (recompute) {
+          newn = sqrt(ss);
+          if (member == 0) nrm0[jl] = newn;
+        }
       }
-      if (lane == 0) nrm[jl] = newn;
+      if (act && member == 0) nrm[jl] = newn;
     }
     __syncthreads();
     publish_candidate();
@@ -326,7 +333,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in, double rtol,
 }  // namespace
 
 Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, bool f64,
-                      double rtol, double atol, cudaStream_t s) {
+                      double rtol, double atol, cudaStream_t s, Arena* scratch) {
   const int count = (int)h.size();
   if (count <= 0) return ok();
   int max_m = 1, max_d = 1;
@@ -351,7 +358,7 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
            sizeof(int) * (size_t)((mloc + 1) & ~1);
   };
   size_t base = need(C);
-  size_t wbytes = sizeof(double) * (size_t)((max_m + C - 1) / C) * d;
+  size_t wbytes = sizeof(double) * (size_t)((max_m + C - 1) / C) * (d | 1);
   int w_in_smem = base + wbytes <= ID_SMEM_CAP ? 1 : 0;
   size_t smem = base + (w_in_smem ? wbytes : 0);
   if (smem > 227 * 1024)
@@ -366,13 +373,34 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
   }
   double* r1 = nullptr;
   int64_t* offd = nullptr;
-  HSS_TRY(dalloc_t(&r1, (size_t)tot, s));
-  HSS_TRY(dalloc_t(&offd, (size_t)count, s));
-  HSS_CUDA_TRY(cudaMemcpyAsync(offd, off.data(), count * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  HSS_CUDA_TRY(cudaFuncSetAttribute(id_cpqr_cluster_kernel,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  HSS_CUDA_TRY(cudaFuncSetAttribute(id_cpqr_cluster_kernel,
-                                    cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  if (scratch) {
+    HSS_TRY(scratch->alloc_t(&r1, (size_t)tot, s));
+    HSS_TRY(scratch->alloc_t(&offd, (size_t)count, s));
+  } else {
+    HSS_TRY(dalloc_t(&r1, (size_t)tot, s));
+    HSS_TRY(dalloc_t(&offd, (size_t)count, s));
+  }
+  if (scratch) HSS_TRY(scratch->upload(offd, off.data(), count * sizeof(int64_t), s));
+  else HSS_CUDA_TRY(cudaMemcpyAsync(offd, off.data(), count * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  {
+    // kernel attributes: once per device (the shared-memory cap is the
+    // hardware maximum; each launch asks for what it needs)
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    HSS_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && !done[dev]) {
+      int optin = 0;
+      HSS_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      HSS_CUDA_TRY(cudaFuncSetAttribute(id_cpqr_cluster_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        optin - 1024));
+      HSS_CUDA_TRY(cudaFuncSetAttribute(id_cpqr_cluster_kernel,
+                                        cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+      done[dev] = true;
+    }
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(count * C), 1, 1);
   cfg.blockDim = dim3(ID_THREADS, 1, 1);
@@ -386,29 +414,45 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   // the cluster must fit in one GPC with this shared memory: shrink C if not
+  // (answers cached per cluster size and shared-memory size)
+  static std::mutex occ_mu;
+  static std::map<std::pair<int, size_t>, int> occ_cache;
   while (C > 1) {
     int nclusters = 0;
-    cudaError_t oe = cudaOccupancyMaxActiveClusters(&nclusters, id_cpqr_cluster_kernel, &cfg);
-    if (oe == cudaSuccess && nclusters > 0) break;
-    cudaGetLastError();
+    {
+      std::lock_guard<std::mutex> lock(occ_mu);
+      auto key = std::make_pair(C, smem);
+      auto itc = occ_cache.find(key);
+      if (itc != occ_cache.end()) {
+        nclusters = itc->second;
+      } else {
+        cudaError_t oe = cudaOccupancyMaxActiveClusters(&nclusters, id_cpqr_cluster_kernel, &cfg);
+        if (oe != cudaSuccess) {
+          cudaGetLastError();
+          nclusters = 0;
+        }
+        occ_cache[key] = nclusters;
+      }
+    }
+    if (nclusters > 0) break;
     C /= 2;
     attr[0].val.clusterDim.x = C;
     cfg.gridDim = dim3((unsigned)(count * C), 1, 1);
     base = need(C);
-    wbytes = sizeof(double) * (size_t)((max_m + C - 1) / C) * d;
+    wbytes = sizeof(double) * (size_t)((max_m + C - 1) / C) * (d | 1);
     w_in_smem = base + wbytes <= ID_SMEM_CAP ? 1 : 0;
     smem = base + (w_in_smem ? wbytes : 0);
     cfg.dynamicSmemBytes = smem;
-    HSS_CUDA_TRY(cudaFuncSetAttribute(id_cpqr_cluster_kernel,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
   cudaError_t e = cudaLaunchKernelEx(&cfg, id_cpqr_cluster_kernel, items_dev, f64 ? 1 : 0, rtol,
                                      atol, w_in_smem, r1, (const int64_t*)offd);
   Err res = e == cudaSuccess ? check_launch("id_cpqr_cluster_kernel")
                              : fail(HSS_ERR_CUDA, std::string("id_cpqr_cluster_kernel launch: ") +
                                                       cudaGetErrorString(e));
-  dfree(r1, s);
-  dfree(offd, s);
+  if (!scratch) {
+    dfree(r1, s);
+    dfree(offd, s);
+  }
   return res;
 }
 

@@ -3,7 +3,10 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <algorithm>
+#include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/hss.h"
@@ -48,6 +51,124 @@ inline Err dalloc_t(T** p, size_t count, cudaStream_t s) {
   return dalloc(reinterpret_cast<void**>(p), count * sizeof(T), s);
 }
 
+// Pinned host staging for small host->device uploads (item tables): a copy
+// from pageable memory would synchronize the stream first.  put() copies the
+// bytes into the pinned block and queues the transfer; reset() may only be
+// called when every transfer queued so far has completed (after a stream
+// synchronization).  Growing also waits for the stream.
+// The owner must have synchronized the stream before destroying it; the
+// block then goes to a per-thread cache for the next compression.
+class PinnedStage {
+ public:
+  ~PinnedStage() {
+    if (!buf_) return;
+    if (cache_buf() == nullptr) {
+      cache_buf() = buf_;
+      cache_cap() = cap_;
+    } else {
+      cudaFreeHost(buf_);
+    }
+  }
+  Err put(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return ok();
+    if (!buf_ && cache_buf() && cache_cap() >= bytes) {
+      buf_ = cache_buf();
+      cap_ = cache_cap();
+      cache_buf() = nullptr;
+      cache_cap() = 0;
+      off_ = 0;
+    }
+    if (off_ + bytes > cap_) {
+      HSS_CUDA_TRY(cudaStreamSynchronize(s));
+      size_t ncap = std::max(cap_ * 2, std::max(bytes, (size_t)4 << 20));
+      if (buf_) cudaFreeHost(buf_);
+      buf_ = nullptr;
+      cap_ = 0;
+      HSS_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&buf_), ncap));
+      cap_ = ncap;
+      off_ = 0;
+    }
+    std::memcpy(buf_ + off_, src, bytes);
+    HSS_CUDA_TRY(cudaMemcpyAsync(dst, buf_ + off_, bytes, cudaMemcpyHostToDevice, s));
+    off_ += (bytes + 63) & ~size_t(63);
+    return ok();
+  }
+  void reset() { off_ = 0; }
+
+ private:
+  static char*& cache_buf() {
+    static thread_local char* b = nullptr;
+    return b;
+  }
+  static size_t& cache_cap() {
+    static thread_local size_t c = 0;
+    return c;
+  }
+  char* buf_ = nullptr;
+  size_t cap_ = 0, off_ = 0;
+};
+
+// Bump allocator over large device chunks.  Allocations are 256-byte aligned
+// and never freed one by one: reset() rewinds (safe in stream order for work
+// queued later on the same stream), release() returns the chunks.
+class Arena {
+ public:
+  explicit Arena(size_t min_chunk = (size_t)64 << 20) : min_chunk_(min_chunk) {}
+  ~Arena() { release(nullptr); }
+  Arena(const Arena&) = delete;
+  Arena& operator=(const Arena&) = delete;
+  Err alloc(void** p, size_t bytes, cudaStream_t s) {
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    while (cur_ < chunks_.size()) {
+      if (off_ + bytes <= chunks_[cur_].second) {
+        *p = chunks_[cur_].first + off_;
+        off_ += bytes;
+        return ok();
+      }
+      ++cur_;
+      off_ = 0;
+    }
+    void* q = nullptr;
+    HSS_TRY(dalloc(&q, std::max(min_chunk_, bytes), s));
+    chunks_.emplace_back(static_cast<char*>(q), std::max(min_chunk_, bytes));
+    cur_ = chunks_.size() - 1;
+    off_ = bytes;
+    *p = q;
+    return ok();
+  }
+  template <typename T>
+  Err alloc_t(T** p, size_t count, cudaStream_t s) {
+    return alloc(reinterpret_cast<void**>(p), count * sizeof(T), s);
+  }
+  void reset() {
+    cur_ = 0;
+    off_ = 0;
+  }
+  void release(cudaStream_t s) {
+    for (auto& c : chunks_) dfree(c.first, s);
+    chunks_.clear();
+    reset();
+  }
+  size_t bytes() const {
+    size_t b = 0;
+    for (auto& c : chunks_) b += c.second;
+    return b;
+  }
+  // Optional pinned staging for uploads of tables that live in this arena.
+  PinnedStage* stage = nullptr;
+  Err upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (stage) return stage->put(dst, src, bytes, s);
+    HSS_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+    return ok();
+  }
+
+ private:
+  std::vector<std::pair<char*, size_t>> chunks_;
+  size_t cur_ = 0, off_ = 0;
+  size_t min_chunk_;
+};
+
 // ----------------------------------------------------------- random matrix
 // R[i, j] for j in [c0, c1), row-major with ldr (Section 2.2).
 template <typename T>
@@ -82,7 +203,7 @@ struct IdItem {
 // items_dev: device copy of `host_items` (the host copy sizes the launch).
 // Each item's norms scratch must hold 2*m doubles and its work m*d doubles.
 Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& host_items, bool f64,
-                      double rtol, double atol, cudaStream_t s);
+                      double rtol, double atol, cudaStream_t s, Arena* scratch = nullptr);
 
 // --------------------------------------------- batched gathered GEMM
 // out[j][c] = (X ? X[xrow(j)][c] : 0) + sign * sum_l Mat(j,l) * Z[zrow(l)][c]
@@ -114,7 +235,7 @@ struct GemmItem {
 };
 template <typename T>
 Err launch_gemm_batched(const std::vector<GemmItem<T>>& items, cudaStream_t s,
-                        void* scratch_dev, size_t scratch_bytes);
+                        void* scratch_dev, size_t scratch_bytes, Arena* scratch = nullptr);
 
 // ------------------------------------------------------------- gathers
 // out[j][l] = A[rows[j]][cols[l]] for a batch of blocks.
@@ -127,10 +248,33 @@ struct GatherItem {
 };
 template <typename T>
 Err launch_gather_batched(const T* A, int64_t lda, const std::vector<GatherItem<T>>& items,
-                          cudaStream_t s, void* scratch_dev, size_t scratch_bytes);
+                          cudaStream_t s, void* scratch_dev, size_t scratch_bytes,
+                          Arena* scratch = nullptr);
 
 // map[j] = base[idx[j]]  (skeleton index sets I^r_tau = I(J))
 Err launch_index_compose(int32_t* out, const int32_t* base, const int32_t* idx, int count,
                          cudaStream_t s);
+
+// Batched skeleton index sets (Algorithm 1: I^r_tau = I_tau(J) at a leaf,
+// [I^r_c1 I^r_c2](J) above): out[q] = lo + idx[q] when base0 is null, else
+// the idx[q]-th entry of the concatenation [base0 (n0 entries), base1].
+struct IndexItem {
+  int32_t* out;
+  const int32_t* idx;
+  const int32_t* base0;
+  const int32_t* base1;
+  int32_t n0, lo, count;
+};
+Err launch_index_batched(const std::vector<IndexItem>& items, cudaStream_t s,
+                         Arena* scratch = nullptr);
+
+// Batched inverse permutations: inv[perm[q]] = q for q < m.
+struct InvItem {
+  int32_t* inv;
+  const int32_t* perm;
+  int32_t m;
+};
+Err launch_invert_batched(const std::vector<InvItem>& items, cudaStream_t s,
+                          Arena* scratch = nullptr);
 
 }  // namespace hss

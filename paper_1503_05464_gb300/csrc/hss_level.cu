@@ -129,11 +129,106 @@ __global__ void index_compose_kernel(int32_t* out, const int32_t* base, const in
   if (t < count) out[t] = base[idx[t]];
 }
 
+__global__ void index_batched_kernel(const IndexItem* __restrict__ items,
+                                     const int64_t* __restrict__ start, int nitems, int64_t total) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  int lo = 0, hi = nitems - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  const IndexItem it = items[lo];
+  const int q = (int)(t - start[lo]);
+  const int j = it.idx[q];
+  it.out[q] = it.base0 ? (j < it.n0 ? it.base0[j] : it.base1[j - it.n0]) : it.lo + j;
+}
+
+__global__ void invert_batched_kernel(const InvItem* __restrict__ items,
+                                      const int64_t* __restrict__ start, int nitems,
+                                      int64_t total) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  int lo = 0, hi = nitems - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  const InvItem it = items[lo];
+  const int q = (int)(t - start[lo]);
+  it.inv[it.perm[q]] = q;
+}
+
+// upload an item table and its prefix of element counts; one allocation
+template <typename I>
+Err upload_table(const std::vector<I>& items, const std::vector<int64_t>& starts, void** buf,
+                 size_t* off, cudaStream_t s, Arena* scratch) {
+  size_t bi = items.size() * sizeof(I);
+  *off = (bi + 255) & ~size_t(255);
+  if (scratch) {
+    HSS_TRY(scratch->alloc(buf, *off + starts.size() * sizeof(int64_t), s));
+    HSS_TRY(scratch->upload(*buf, items.data(), bi, s));
+    HSS_TRY(scratch->upload((char*)*buf + *off, starts.data(), starts.size() * sizeof(int64_t), s));
+    return ok();
+  }
+  HSS_TRY(dalloc(buf, *off + starts.size() * sizeof(int64_t), s));
+  HSS_CUDA_TRY(cudaMemcpyAsync(*buf, items.data(), bi, cudaMemcpyHostToDevice, s));
+  HSS_CUDA_TRY(cudaMemcpyAsync((char*)*buf + *off, starts.data(), starts.size() * sizeof(int64_t),
+                               cudaMemcpyHostToDevice, s));
+  return ok();
+}
+
 }  // namespace
+
+Err launch_index_batched(const std::vector<IndexItem>& items, cudaStream_t s, Arena* scratch) {
+  std::vector<IndexItem> live;
+  std::vector<int64_t> starts;
+  int64_t total = 0;
+  for (const auto& it : items) {
+    if (it.count <= 0) continue;
+    live.push_back(it);
+    starts.push_back(total);
+    total += it.count;
+  }
+  if (live.empty()) return ok();
+  void* buf = nullptr;
+  size_t off = 0;
+  HSS_TRY(upload_table(live, starts, &buf, &off, s, scratch));
+  index_batched_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+      reinterpret_cast<const IndexItem*>(buf), reinterpret_cast<const int64_t*>((char*)buf + off),
+      (int)live.size(), total);
+  Err e = check_launch("index_batched_kernel");
+  if (!scratch) dfree(buf, s);
+  return e;
+}
+
+Err launch_invert_batched(const std::vector<InvItem>& items, cudaStream_t s, Arena* scratch) {
+  std::vector<InvItem> live;
+  std::vector<int64_t> starts;
+  int64_t total = 0;
+  for (const auto& it : items) {
+    if (it.m <= 0) continue;
+    live.push_back(it);
+    starts.push_back(total);
+    total += it.m;
+  }
+  if (live.empty()) return ok();
+  void* buf = nullptr;
+  size_t off = 0;
+  HSS_TRY(upload_table(live, starts, &buf, &off, s, scratch));
+  invert_batched_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+      reinterpret_cast<const InvItem*>(buf), reinterpret_cast<const int64_t*>((char*)buf + off),
+      (int)live.size(), total);
+  Err e = check_launch("invert_batched_kernel");
+  if (!scratch) dfree(buf, s);
+  return e;
+}
 
 template <typename T>
 Err launch_gemm_batched(const std::vector<GemmItem<T>>& items, cudaStream_t s,
-                        void* scratch_dev, size_t scratch_bytes) {
+                        void* scratch_dev, size_t scratch_bytes, Arena* scratch) {
   std::vector<GemmItem<T>> live;
   std::vector<int> starts;
   int tiles = 0;
@@ -151,11 +246,20 @@ Err launch_gemm_batched(const std::vector<GemmItem<T>>& items, cudaStream_t s,
   void* buf = scratch_dev;
   bool own = false;
   if (!buf || scratch_bytes < off + bs) {
-    HSS_TRY(dalloc(&buf, off + bs, s));
-    own = true;
+    if (scratch) {
+      HSS_TRY(scratch->alloc(&buf, off + bs, s));
+    } else {
+      HSS_TRY(dalloc(&buf, off + bs, s));
+      own = true;
+    }
   }
-  HSS_CUDA_TRY(cudaMemcpyAsync(buf, live.data(), bi, cudaMemcpyHostToDevice, s));
-  HSS_CUDA_TRY(cudaMemcpyAsync((char*)buf + off, starts.data(), bs, cudaMemcpyHostToDevice, s));
+  if (scratch) {
+    HSS_TRY(scratch->upload(buf, live.data(), bi, s));
+    HSS_TRY(scratch->upload((char*)buf + off, starts.data(), bs, s));
+  } else {
+    HSS_CUDA_TRY(cudaMemcpyAsync(buf, live.data(), bi, cudaMemcpyHostToDevice, s));
+    HSS_CUDA_TRY(cudaMemcpyAsync((char*)buf + off, starts.data(), bs, cudaMemcpyHostToDevice, s));
+  }
   gemm_batched_kernel<T><<<tiles, G_THREADS, 0, s>>>(
       reinterpret_cast<const GemmItem<T>*>(buf), reinterpret_cast<const int*>((char*)buf + off),
       (int)live.size());
@@ -166,7 +270,8 @@ Err launch_gemm_batched(const std::vector<GemmItem<T>>& items, cudaStream_t s,
 
 template <typename T>
 Err launch_gather_batched(const T* A, int64_t lda, const std::vector<GatherItem<T>>& items,
-                          cudaStream_t s, void* scratch_dev, size_t scratch_bytes) {
+                          cudaStream_t s, void* scratch_dev, size_t scratch_bytes,
+                          Arena* scratch) {
   std::vector<GatherItem<T>> live;
   std::vector<int64_t> starts;
   int64_t total = 0;
@@ -183,11 +288,20 @@ Err launch_gather_batched(const T* A, int64_t lda, const std::vector<GatherItem<
   void* buf = scratch_dev;
   bool own = false;
   if (!buf || scratch_bytes < off + bs) {
-    HSS_TRY(dalloc(&buf, off + bs, s));
-    own = true;
+    if (scratch) {
+      HSS_TRY(scratch->alloc(&buf, off + bs, s));
+    } else {
+      HSS_TRY(dalloc(&buf, off + bs, s));
+      own = true;
+    }
   }
-  HSS_CUDA_TRY(cudaMemcpyAsync(buf, live.data(), bi, cudaMemcpyHostToDevice, s));
-  HSS_CUDA_TRY(cudaMemcpyAsync((char*)buf + off, starts.data(), bs, cudaMemcpyHostToDevice, s));
+  if (scratch) {
+    HSS_TRY(scratch->upload(buf, live.data(), bi, s));
+    HSS_TRY(scratch->upload((char*)buf + off, starts.data(), bs, s));
+  } else {
+    HSS_CUDA_TRY(cudaMemcpyAsync(buf, live.data(), bi, cudaMemcpyHostToDevice, s));
+    HSS_CUDA_TRY(cudaMemcpyAsync((char*)buf + off, starts.data(), bs, cudaMemcpyHostToDevice, s));
+  }
   gather_batched_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
       A, lda, reinterpret_cast<const GatherItem<T>*>(buf),
       reinterpret_cast<const int64_t*>((char*)buf + off), (int)live.size(), total);
@@ -204,14 +318,14 @@ Err launch_index_compose(int32_t* out, const int32_t* base, const int32_t* idx, 
 }
 
 template Err launch_gemm_batched<float>(const std::vector<GemmItem<float>>&, cudaStream_t, void*,
-                                        size_t);
+                                        size_t, Arena*);
 template Err launch_gemm_batched<double>(const std::vector<GemmItem<double>>&, cudaStream_t,
-                                         void*, size_t);
+                                         void*, size_t, Arena*);
 template Err launch_gather_batched<float>(const float*, int64_t,
                                           const std::vector<GatherItem<float>>&, cudaStream_t,
-                                          void*, size_t);
+                                          void*, size_t, Arena*);
 template Err launch_gather_batched<double>(const double*, int64_t,
                                            const std::vector<GatherItem<double>>&, cudaStream_t,
-                                           void*, size_t);
+                                           void*, size_t, Arena*);
 
 }  // namespace hss

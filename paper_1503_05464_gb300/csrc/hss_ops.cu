@@ -15,10 +15,6 @@ __global__ void iota_kernel(int32_t* p, int64_t n) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < n) p[t] = (int32_t)t;
 }
-__global__ void invert_perm_kernel(int32_t* inv, const int32_t* perm, int m) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < m) inv[perm[t]] = t;
-}
 }  // namespace
 
 Err build_bisection_tree(Tree& t, int64_t n, int leaf_size, cudaStream_t s) {
@@ -46,16 +42,13 @@ Err build_bisection_tree(Tree& t, int64_t n, int leaf_size, cudaStream_t s) {
 }
 
 Err finalize_generators(hss_s* h, cudaStream_t s) {
+  std::vector<InvItem> inv;
   for (size_t i = 0; i < h->gen.size(); ++i) {
     NodeGen& g = h->gen[i];
-    g.free_samples(s);
+    g.free_samples();
     if (i == 0 || g.state != NODE_COMPRESSED) continue;
-    dfree(g.iperm_r, s);
-    HSS_TRY(dalloc_t(&g.iperm_r, std::max(g.mr, 1), s));
-    if (g.mr > 0) {
-      invert_perm_kernel<<<(g.mr + 255) / 256, 256, 0, s>>>(g.iperm_r, g.permr, g.mr);
-      HSS_TRY(check_launch("invert_perm_kernel"));
-    }
+    HSS_TRY(h->store.alloc_t(&g.iperm_r, std::max(g.mr, 1), s));
+    inv.push_back({g.iperm_r, g.permr, g.mr});
     int64_t esz = h->dtype == HSS_F64 ? 8 : 4;
     h->info.bytes_hss += 8 * ((int64_t)(g.mr - g.kr) * g.kr + (int64_t)(g.mc - g.kc) * g.kc) +
                          4 * ((int64_t)g.mr + g.mc);
@@ -66,7 +59,7 @@ Err finalize_generators(hss_s* h, cudaStream_t s) {
       h->info.bytes_hss += esz * ((int64_t)a.kr * b.kc + (int64_t)b.kr * a.kc);
     }
   }
-  return ok();
+  return launch_invert_batched(inv, s);
 }
 
 void fill_info(hss_s* h) {

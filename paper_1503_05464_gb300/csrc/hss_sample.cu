@@ -159,29 +159,48 @@ sample_simt_kernel(const T* __restrict__ A, int64_t n, int64_t lda,
   }
 }
 
-// Sc[j][c0 + q*DC + cc] = sum over panels p (in order) of P[p][q][j][cc]
+// Sc[j][c0 + q*DC + cc] = sum over panels p (in order) of P[p][q][j][cc];
+// one thread sums four adjacent columns, eight panels in flight per step
 template <typename T>
 __global__ void reduce_partials_kernel(const T* __restrict__ P, int64_t n, int npanel, int nchunk,
                                        int64_t c0, int64_t ncols, T* __restrict__ Sc, int64_t lds) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t total = (int64_t)nchunk * n * S_DC;
+  int64_t total = (int64_t)nchunk * n * (S_DC / 4);
   if (t >= total) return;
-  int q = (int)(t / (n * S_DC));
-  int64_t rem = t - (int64_t)q * n * S_DC;
-  int64_t j = rem / S_DC;
-  int cc = (int)(rem - j * S_DC);
-  int64_t col = (int64_t)q * S_DC + cc;
-  if (col >= ncols) return;
-  double s = 0.0;   // FP64 sum over the panels (memory-bound: free)
-  for (int p = 0; p < npanel; ++p) s += (double)P[((int64_t)p * nchunk + q) * n * S_DC + j * S_DC + cc];
-  Sc[j * lds + c0 + col] = (T)s;
+  int q = (int)(t / (n * (S_DC / 4)));
+  int64_t rem = t - (int64_t)q * n * (S_DC / 4);
+  int64_t j = rem / (S_DC / 4);
+  int cc = (int)(rem - j * (S_DC / 4)) * 4;
+  const int64_t pstride = (int64_t)nchunk * n * S_DC;
+  const T* src = P + (int64_t)q * n * S_DC + j * S_DC + cc;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};   // FP64 sum over the panels (memory-bound: free)
+  int p = 0;
+  for (; p + 8 <= npanel; p += 8) {
+    T v[8][4];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[u][e] = src[(int64_t)(p + u) * pstride + e];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) s[e] += (double)v[u][e];
+  }
+  for (; p < npanel; ++p)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) s[e] += (double)src[(int64_t)p * pstride + e];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    int64_t col = (int64_t)q * S_DC + cc + e;
+    if (col < ncols) Sc[j * lds + c0 + col] = (T)s[e];
+  }
 }
 
 }  // namespace
 
 Err launch_reduce_partials(const float* P, int64_t n, int npanel, int nchunk, int64_t c0,
                            int64_t ncols, float* Sc, int64_t lds, cudaStream_t s) {
-  int64_t total = (int64_t)nchunk * n * S_DC;
+  int64_t total = (int64_t)nchunk * n * (S_DC / 4);
   reduce_partials_kernel<float><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
       P, n, npanel, nchunk, c0, ncols, Sc, lds);
   return check_launch("reduce_partials_kernel");
@@ -234,7 +253,7 @@ Err launch_sample(const T* A, int64_t n, int64_t lda, const T* R, int64_t ldr, i
     sample_simt_kernel<T><<<npanel * nchunk, S_THREADS, smem, s>>>(
         A, n, lda, R, ldr, c0, ncols, nchunk, Sr, lds, leaf_of, P);
     HSS_TRY(check_launch("sample_simt_kernel"));
-    int64_t total = (int64_t)nchunk * n * S_DC;
+    int64_t total = (int64_t)nchunk * n * (S_DC / 4);
     reduce_partials_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
         P, n, npanel, nchunk, c0, ncols, Sc, lds);
     HSS_TRY(check_launch("reduce_partials_kernel"));

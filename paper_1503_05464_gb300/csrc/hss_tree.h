@@ -48,33 +48,13 @@ struct NodeGen {
   void* Rr = nullptr;     // R^r_tau = V^T R_in (kc x dcap)
   void* Rc = nullptr;     // R^c_tau = U^T R_in (kr x dcap)
 
-  void free_id(cudaStream_t s) {
-    dfree(permr, s);
-    dfree(permc, s);
-    dfree(Er, s);
-    dfree(Ec, s);
+  // Every buffer above lives in an arena (generators: the handle's store;
+  // samples: the compression's temporaries); dropping a pointer frees nothing.
+  void free_id() {
     permr = permc = nullptr;
     Er = Ec = nullptr;
   }
-  void free_samples(cudaStream_t s) {
-    dfree(Sr, s);
-    dfree(Sc, s);
-    dfree(Rr, s);
-    dfree(Rc, s);
-    Sr = Sc = Rr = Rc = nullptr;
-  }
-  void release(cudaStream_t s) {
-    free_id(s);
-    free_samples(s);
-    dfree(D, s);
-    dfree(B12, s);
-    dfree(B21, s);
-    dfree(iperm_r, s);
-    dfree(Ir, s);
-    dfree(Ic, s);
-    D = B12 = B21 = nullptr;
-    iperm_r = Ir = Ic = nullptr;
-  }
+  void free_samples() { Sr = Sc = Rr = Rc = nullptr; }
 };
 
 // ULV factors of one non-root node (Algorithm 3), all FP64:
@@ -128,14 +108,15 @@ struct hss_s {
   hss_info_t info{};
   std::string err;
   hss::UlvFactors ulv;
+  hss::Arena store{(size_t)16 << 20};   // generators: D, B, E, permutations, skeletons
   cudaStream_t stream = nullptr;
   // The caller's stream may be gone by now: drain the device, then free on
   // the legacy stream.
   ~hss_s() {
     cudaDeviceSynchronize();
-    for (auto& g : gen) g.release(nullptr);
     ulv.release(nullptr);
     hss::dfree(tree.iota_dev, nullptr);
+    store.release(nullptr);
     cudaDeviceSynchronize();
   }
 };

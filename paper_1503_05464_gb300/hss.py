@@ -48,7 +48,9 @@ class HssInfo(ctypes.Structure):
                 ("ms_sample", ctypes.c_double), ("ms_id", ctypes.c_double),
                 ("ms_levels", ctypes.c_double), ("flops_sample", ctypes.c_double),
                 ("flops_id", ctypes.c_double), ("factored", ctypes.c_int32),
-                ("launches", ctypes.c_int64), ("bytes_d2h", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("bytes_d2h", ctypes.c_int64),
+                ("ms_host_id_launch", ctypes.c_double), ("ms_host_wait", ctypes.c_double),
+                ("ms_host_sample", ctypes.c_double)]
 
 
 _lib = None
