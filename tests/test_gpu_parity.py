@@ -351,3 +351,52 @@ def test_errors_are_status_codes(P):
         P.hss_compress(torch.randn(256, 256, device=DEV), leaf_size=64, rtol=1e-12, d0=16,
                        d_step=16, d_max=32)
     assert e.value.status == P.hss.HSS_ERR_RANK_CAP
+
+
+# ------------------------------------------------- full size (bench workload)
+def _gauss20k():
+    import bench
+    wl = bench.WORKLOADS["gauss20k"]
+    A = bench.make_matrix(wl, DEV).contiguous()
+    kw = dict(leaf_size=wl["leaf"], rtol=wl["rtol"], d0=wl["d0"], d_step=wl["step"],
+              seed=wl["seed"] + 1)
+    return wl, A, kw
+
+
+def _probe_error(P, h, A, nprobe=32, seed=0):
+    """||(A - H) G||_F / ||A G||_F with Gaussian probes G (any size)."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    G = torch.randn(A.shape[0], nprobe, generator=g, dtype=torch.float64).to(DEV)
+    AG = A.double() @ G
+    HG = P.hss_matvec(h, G.to(A.dtype)).double()
+    return float(torch.linalg.norm(AG - HG) / torch.linalg.norm(AG))
+
+
+def test_full_size_gauss20k_matches_oracle(P):
+    """n=20000 Gaussian kernel, the benchmark's workload and launch configuration.
+
+    FP64 path (A upcast): ranks must equal the oracle's node for node.  BF16x3
+    sampling: ranks within +-2 except where a node's rank sits within 2 of
+    the adaptive boundary d - p (then the pass count may differ and the rank
+    is re-estimated with more samples); the probe error must stay within the
+    bound of the FP64 result.
+    """
+    wl, A, kw = _gauss20k()
+    ho = O.compress(A.cpu().numpy().astype(np.float64), wl["rtol"], leaf_size=wl["leaf"],
+                    d0=wl["d0"], d_step=wl["step"], seed=wl["seed"] + 1)
+    ro = ho.ranks()
+    h64 = P.hss_compress(A.double(), **kw)
+    r64 = P.hss_node_ranks(h64)
+    assert P.hss_info(h64)["passes"] == ho.passes
+    assert max(max(abs(r64[i][2] - ro[i][0]), abs(r64[i][3] - ro[i][1]))
+               for i in range(1, len(r64))) <= 2
+    e64 = _probe_error(P, h64, A.double())
+    assert e64 <= 2 * max(wl["rtol"], 1e-3)
+    h3 = P.hss_compress(A, sample_mode="bf16x3", **kw)
+    r3 = P.hss_node_ranks(h3)
+    boundary = ho.d - 10
+    for i in range(1, len(r3)):
+        if max(ro[i]) >= boundary - 2:
+            continue
+        assert abs(r3[i][2] - ro[i][0]) <= 2 and abs(r3[i][3] - ro[i][1]) <= 2, (i, r3[i], ro[i])
+    assert _probe_error(P, h3, A) <= 2 * max(e64, wl["rtol"])
