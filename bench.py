@@ -183,6 +183,17 @@ def run_ours(args, wl):
         ms = float(t.item())
         dist.barrier()
 
+    # accuracy of the last compression (outside the timed region):
+    # ||(A - H) G||_F / ||A G||_F with 16 Gaussian probes, H applied by hss_matvec
+    h_chk = P.hss_compress(A, opts, stream=stream)
+    gen = torch.Generator(device="cpu").manual_seed(7)
+    G = torch.randn(A.shape[0], 16, generator=gen, dtype=torch.float64).to(dev)
+    AG = A.double() @ G
+    HG = P.hss_matvec(h_chk, G.to(A.dtype)).double()
+    probe_err = float(torch.linalg.norm(AG - HG) / torch.linalg.norm(AG))
+    h_chk.close()
+    del AG, HG, G
+
     # end to end through the public API from pinned host memory
     A_host = A.cpu().pin_memory()
     A_dev = torch.empty_like(A)
@@ -247,6 +258,7 @@ def run_ours(args, wl):
                      "ms_host_sample")},
         "hss": {"passes": info["passes"], "d_final": info["d_final"],
                 "max_rank": max(info["max_rank_r"], info["max_rank_c"]),
+                "probe_rel_err": probe_err,
                 "bytes_hss": info["bytes_hss"], "levels": info["levels"]},
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": n * n * esz,
                 "d2h_bytes_per_step": d2h},

@@ -196,40 +196,44 @@ sample_mma_kernel(const float* __restrict__ A, int64_t n, int64_t lda,
     cp_async_commit();
     cp_async_wait1();
     __syncthreads();
-    // ---- convert staging -> operand planes (mask the leaf blocks)
+    // ---- convert staging -> operand planes (mask the leaf blocks); consecutive
+    // threads take consecutive float pairs, so staging reads are conflict-free
     {
-      const int r = tid >> 1, cb = (tid & 1) * 16;
-      const float* src = &sm.stA[b][r * M_BK + cb];
-      const int lr = leaf_rows[r];
 #pragma unroll
-      for (int q = 0; q < 16; q += 2) {
-        float x0 = src[q], x1 = src[q + 1];
-        if (leaf_cols[b][cb + q] == lr) x0 = 0.f;
-        if (leaf_cols[b][cb + q + 1] == lr) x1 = 0.f;
+      for (int k = 0; k < (M_BM * M_BK / 2) / M_THREADS; ++k) {
+        const int pidx = tid + k * M_THREADS;
+        const int r = pidx / (M_BK / 2), c2 = (pidx % (M_BK / 2)) * 2;
+        float2 xv = *reinterpret_cast<const float2*>(&sm.stA[b][r * M_BK + c2]);
+        const int lr = leaf_rows[r];
+        if (leaf_cols[b][c2] == lr) xv.x = 0.f;
+        if (leaf_cols[b][c2 + 1] == lr) xv.y = 0.f;
         if constexpr (MODE == 1) {
-          sm.pA[r * LDA_F + cb + q] = to_tf32(x0);
-          sm.pA[r * LDA_F + cb + q + 1] = to_tf32(x1);
+          *reinterpret_cast<float2*>(&sm.pA[r * LDA_F + c2]) = make_float2(to_tf32(xv.x), to_tf32(xv.y));
         } else {
           __nv_bfloat16* pl = reinterpret_cast<__nv_bfloat16*>(sm.pA);
-          __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-          float2 hf = __bfloat1622float2(h);
-          float r0 = x0 - hf.x, r1 = x1 - hf.y;
-          __nv_bfloat162 mmid = __floats2bfloat162_rn(r0, r1);
-          *reinterpret_cast<__nv_bfloat162*>(&pl[r * LDA_B + cb + q]) = h;
-          *reinterpret_cast<__nv_bfloat162*>(&pl[M_BM * LDA_B + r * LDA_B + cb + q]) = mmid;
+          __nv_bfloat162 hv = __floats2bfloat162_rn(xv.x, xv.y);
+          float2 hf = __bfloat1622float2(hv);
+          float r0 = xv.x - hf.x, r1 = xv.y - hf.y;
+          __nv_bfloat162 mv = __floats2bfloat162_rn(r0, r1);
+          *reinterpret_cast<__nv_bfloat162*>(&pl[r * LDA_B + c2]) = hv;
+          *reinterpret_cast<__nv_bfloat162*>(&pl[M_BM * LDA_B + r * LDA_B + c2]) = mv;
           if constexpr (MODE == 3) {
-            float2 mf = __bfloat1622float2(mmid);
-            __nv_bfloat162 lo = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
-            *reinterpret_cast<__nv_bfloat162*>(&pl[2 * M_BM * LDA_B + r * LDA_B + cb + q]) = lo;
+            float2 mf = __bfloat1622float2(mv);
+            __nv_bfloat162 lv = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+            *reinterpret_cast<__nv_bfloat162*>(&pl[2 * M_BM * LDA_B + r * LDA_B + c2]) = lv;
           }
         }
       }
-      const int rr = tid >> 3, rc = (tid & 7) * 8;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        float v = sm.stR[b][rr * M_DC + rc + q];
-        if constexpr (MODE == 1) sm.pR[rr * LDR_F + rc + q] = v;
-        else reinterpret_cast<__nv_bfloat16*>(sm.pR)[rr * LDR_B + rc + q] = __float2bfloat16_rn(v);
+      for (int k = 0; k < (M_BK * M_DC / 2) / M_THREADS; ++k) {
+        const int pidx = tid + k * M_THREADS;
+        const int r = pidx / (M_DC / 2), c2 = (pidx % (M_DC / 2)) * 2;
+        float2 v = *reinterpret_cast<const float2*>(&sm.stR[b][r * M_DC + c2]);
+        if constexpr (MODE == 1)
+          *reinterpret_cast<float2*>(&sm.pR[r * LDR_F + c2]) = v;
+        else
+          *reinterpret_cast<__nv_bfloat162*>(&reinterpret_cast<__nv_bfloat16*>(sm.pR)[r * LDR_B + c2]) =
+              __floats2bfloat162_rn(v.x, v.y);
       }
     }
     __syncthreads();
