@@ -164,6 +164,56 @@ void hss_destroy(hss_t h);
 const char* hss_last_error(hss_t h);
 
 /* ---------------------------------------------------------------------------
+ * Batched compression (many matrices in lockstep) and its incremental form.
+ *
+ * A batch holds jobs of one dtype on one stream.  Each hss_batch_step runs
+ * one round: new jobs build their tree and draw their first samples; every
+ * other job processes one tree level (Algorithm 1, Algorithm 5 per node),
+ * and the level work of all jobs goes into shared launches (one ID launch for
+ * every node side of every job, one rank read-back per round).  Jobs may be
+ * submitted between steps (continuous batching).
+ * ------------------------------------------------------------------------- */
+typedef struct hss_batch_s* hss_batch_t;
+
+/* Creates an empty batch.  Errors: INVALID. */
+hss_status hss_batch_create(hss_dtype dtype, void* stream, hss_batch_t* out);
+
+/* Queues the compression of A (device, n x n row-major, lda; the batch's
+ * dtype).  A must stay valid until the job finishes (hss_batch_take
+ * succeeds).  *ticket identifies the job.  Errors: INVALID (bad A, n, lda,
+ * options; message in hss_batch_last_error). */
+hss_status hss_batch_submit(hss_batch_t b, const void* A, int64_t n, int64_t lda,
+                            const hss_opts* opts, int64_t* ticket);
+
+/* Runs one round; *active receives the number of jobs still running.
+ * Synchronizes the stream once per round (rank read-back).  Errors: CUDA,
+ * OOM (batch-wide failures); a job's own failure is reported by take. */
+hss_status hss_batch_step(hss_batch_t b, int32_t* active);
+
+/* Hands over the handle of a finished job (the batch forgets the ticket).
+ * Returns the job's status: OK, RANK_CAP (handle still returned), or its
+ * error (no handle); STATE if the job is still running; INVALID for an
+ * unknown ticket. */
+hss_status hss_batch_take(hss_batch_t b, int64_t ticket, hss_t* out);
+
+/* Message of the batch's last failed call (never NULL). */
+const char* hss_batch_last_error(hss_batch_t b);
+
+/* Destroys the batch and every job not taken. */
+void hss_batch_destroy(hss_batch_t b);
+
+/* Compresses `count` matrices together (one batch run to completion).
+ *   A, n, lda: host arrays of count entries (A[i] device pointers).
+ *   opts: NULL (defaults), one hss_opts (opts_stride = 0) or count of them
+ *   (opts_stride = 1).  out: host array of count handles; status: optional
+ *   host array of count per-matrix statuses.  Returns the first non-OK
+ *   status.  Synchronizes the stream. */
+hss_status hss_compress_batched(int32_t count, const void* const* A, const int64_t* n,
+                                const int64_t* lda, hss_dtype dtype, const hss_opts* opts,
+                                int32_t opts_stride, void* stream, hss_t* out,
+                                hss_status* status);
+
+/* ---------------------------------------------------------------------------
  * Step-level entry points.  They run single steps of the compression on
  * caller buffers; hss_compress runs the same kernels.
  * ------------------------------------------------------------------------- */

@@ -208,6 +208,7 @@ def interpolative_decomposition(Y: np.ndarray, rtol: float, atol: float = 0.0) -
 class NodeData:
     state: int = UNTOUCHED
     ncols: int = 0                       # sample columns incorporated so far
+    d_compressed: int = 0                # sample count when the ID succeeded
     idr: ID | None = None                # row ID  -> U = Pi^r [I; E^r]
     idc: ID | None = None                # column ID -> V = Pi^c [I; E^c]
     Sr: np.ndarray | None = None         # S^r_tau  (k^r x d)
@@ -371,6 +372,7 @@ def _process_node(A, R, Sr, Sc, nodes, data, nd, d, rtol, atol, p):
         me.Ir = np.concatenate([c1.Ir, c2.Ir])[idr.J]
         me.Ic = np.concatenate([c1.Ic, c2.Ic])[idc.J]
     me.ncols = d
+    me.d_compressed = d
     me.state = COMPRESSED
 
 

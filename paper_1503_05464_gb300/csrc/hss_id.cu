@@ -30,6 +30,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <array>
 #include <cfloat>
 #include <climits>
 #include <map>
@@ -63,6 +64,36 @@ __device__ __forceinline__ void warp_argmax(double& v, int& j) {
   }
 }
 
+// Sum over the column entries c >= i of f(c) with a summation order that does
+// not depend on the team size TS: entry c accumulates (in increasing c) into
+// partial c mod 32, and the 32 partials are combined by a fixed butterfly
+// (pairs p, p + o for o = 16, 8, ..., 1).  Levels o >= TS pair partials held
+// by the same thread, the others go through shuffles within the team.  So a
+// node's ID is bitwise the same whatever cluster size or batch it runs in.
+template <int TS, typename F>
+__device__ __forceinline__ double team_sum(int i, int d, int member, F f) {
+  constexpr int NP = 32 / TS;
+  double acc[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) acc[q] = 0.0;
+  for (int base = (i / 32) * 32; base < d; base += 32) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const int c = base + member + q * TS;
+      if (c >= i && c < d) acc[q] = f(c, acc[q]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o >= TS; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < o / TS; ++q) acc[q] = acc[q] + acc[q + o / TS];
+  }
+  double v = acc[0];
+#pragma unroll
+  for (int o = TS >> 1; o > 0; o >>= 1) v = v + __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Values one CTA publishes to the others of its cluster.
 struct Pub {
   double cand_val;   // largest active residual norm of this CTA (-1: none)
@@ -72,8 +103,9 @@ struct Pub {
   double r11;        // owner at step 0: |R_11|
 };
 
+template <int TS>
 __global__ void __launch_bounds__(ID_THREADS)
-id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in, double rtol, double atol,
+id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
                        int w_in_smem, double* __restrict__ r1buf_base,
                        const int64_t* __restrict__ r1off) {
   extern __shared__ __align__(16) double smem[];
@@ -87,6 +119,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in, double rtol,
   const int item = blockIdx.x / C;
   const IdItem it = items[item];
   const int m = it.m, d = it.d;
+  const double rtol = it.rtol, atol = it.atol;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (m <= 0) {
     if (crank == 0 && tid == 0) *it.k = 0;
@@ -106,10 +139,8 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in, double rtol,
   auto col = [&](int jl) -> double* {
     return w_in_smem ? Wsm + (size_t)jl * ldw : it.work + (size_t)(jl * C + crank) * d;
   };
-  // team of TS threads per column (power of two): all 256 threads stay busy
-  // whether a CTA owns 8 columns or 500
-  int TS = 1;
-  while (TS < 32 && mloc_max * TS * 2 <= ID_THREADS) TS *= 2;
+  // team of TS threads per column (power of two, chosen by the launcher):
+  // all 256 threads stay busy whether a CTA owns 8 columns or 500
   const int member = lane & (TS - 1);
   const int cols_per_warp = 32 / TS;
   const double tol3z = sqrt(DBL_EPSILON * 0.5);
@@ -248,10 +279,9 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in, double rtol,
       const double nj = jl < mloc ? nrm[jl] : -1.0;
       const bool act = nj >= 0.0;
       double* wj = act ? col(jl) : nullptr;
-      double dot = 0.0;
-      if (act)
-        for (int c = i + member; c < d; c += TS) dot = fma(vloc[c - i], wj[c], dot);
-      for (int o = TS >> 1; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+      double dot = team_sum<TS>(i, act ? d : 0, member, [&](int c, double a) {
+        return fma(vloc[c - i], wj[c], a);
+      });
       dot *= tau;
       if (act)
         for (int c = i + member; c < d; c += TS) wj[c] = fma(-dot, vloc[c - i], wj[c]);
@@ -269,10 +299,9 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in, double rtol,
       }
       recompute = __shfl_sync(0xffffffffu, recompute ? 1 : 0, lane & ~(TS - 1)) != 0;
       if (__any_sync(0xffffffffu, recompute)) {
-        double ss = 0.0;
-        if (recompute)
-          for (int c = i + 1 + member; c < d; c += TS) ss = fma(wj[c], wj[c], ss);
-        for (int o = TS >> 1; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        double ss = team_sum<TS>(i + 1, recompute ? d : 0, member, [&](int c, double a) {
+          return fma(wj[c], wj[c], a);
+        });
         if (recompute) {
           newn = sqrt(ss);
           if (member == 0) nrm0[jl] = newn;
@@ -330,10 +359,16 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in, double rtol,
   }
 }
 
+using IdKernel = void (*)(const IdItem*, int, int, double*, const int64_t*);
+std::array<IdKernel, 6> kernels() {
+  return {id_cpqr_cluster_kernel<1>, id_cpqr_cluster_kernel<2>, id_cpqr_cluster_kernel<4>,
+          id_cpqr_cluster_kernel<8>, id_cpqr_cluster_kernel<16>, id_cpqr_cluster_kernel<32>};
+}
+
 }  // namespace
 
 Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, bool f64,
-                      double rtol, double atol, cudaStream_t s, Arena* scratch) {
+                      cudaStream_t s, Arena* scratch) {
   const int count = (int)h.size();
   if (count <= 0) return ok();
   int max_m = 1, max_d = 1;
@@ -393,11 +428,11 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
     if (dev >= 0 && dev < 64 && !done[dev]) {
       int optin = 0;
       HSS_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-      HSS_CUDA_TRY(cudaFuncSetAttribute(id_cpqr_cluster_kernel,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        optin - 1024));
-      HSS_CUDA_TRY(cudaFuncSetAttribute(id_cpqr_cluster_kernel,
-                                        cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+      for (auto fn : kernels()) {
+        HSS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          optin - 1024));
+        HSS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+      }
       done[dev] = true;
     }
   }
@@ -426,7 +461,7 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
       if (itc != occ_cache.end()) {
         nclusters = itc->second;
       } else {
-        cudaError_t oe = cudaOccupancyMaxActiveClusters(&nclusters, id_cpqr_cluster_kernel, &cfg);
+        cudaError_t oe = cudaOccupancyMaxActiveClusters(&nclusters, id_cpqr_cluster_kernel<1>, &cfg);
         if (oe != cudaSuccess) {
           cudaGetLastError();
           nclusters = 0;
@@ -444,8 +479,17 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
     smem = base + (w_in_smem ? wbytes : 0);
     cfg.dynamicSmemBytes = smem;
   }
-  cudaError_t e = cudaLaunchKernelEx(&cfg, id_cpqr_cluster_kernel, items_dev, f64 ? 1 : 0, rtol,
-                                     atol, w_in_smem, r1, (const int64_t*)offd);
+  // threads per column: results do not depend on it (fixed summation tree)
+  int TS = 1;
+  {
+    const int mloc = (max_m + C - 1) / C;
+    while (TS < 32 && mloc * TS * 2 <= ID_THREADS) TS *= 2;
+  }
+  const auto fns = kernels();
+  int ti = 0;
+  while ((1 << ti) < TS) ++ti;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, fns[ti], items_dev, f64 ? 1 : 0, w_in_smem, r1,
+                                     (const int64_t*)offd);
   Err res = e == cudaSuccess ? check_launch("id_cpqr_cluster_kernel")
                              : fail(HSS_ERR_CUDA, std::string("id_cpqr_cluster_kernel launch: ") +
                                                       cudaGetErrorString(e));

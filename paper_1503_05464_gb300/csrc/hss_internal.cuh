@@ -199,11 +199,13 @@ struct IdItem {
   int32_t* k;       // rank out
   double* work;     // m * d doubles of scratch
   double* norms;    // 2 * m doubles of scratch
+  double rtol;      // stop at the first |R_ii| <= max(rtol |R_11|, atol)
+  double atol;
 };
 // items_dev: device copy of `host_items` (the host copy sizes the launch).
 // Each item's norms scratch must hold 2*m doubles and its work m*d doubles.
 Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& host_items, bool f64,
-                      double rtol, double atol, cudaStream_t s, Arena* scratch = nullptr);
+                      cudaStream_t s, Arena* scratch = nullptr);
 
 // --------------------------------------------- batched gathered GEMM
 // out[j][c] = (X ? X[xrow(j)][c] : 0) + sign * sum_l Mat(j,l) * Z[zrow(l)][c]
@@ -238,13 +240,16 @@ Err launch_gemm_batched(const std::vector<GemmItem<T>>& items, cudaStream_t s,
                         void* scratch_dev, size_t scratch_bytes, Arena* scratch = nullptr);
 
 // ------------------------------------------------------------- gathers
-// out[j][l] = A[rows[j]][cols[l]] for a batch of blocks.
+// out[j][l] = A[rows[j]][cols[l]] for a batch of blocks (each item names its A;
+// the launch's A/lda are used for items whose A is null).
 template <typename T>
 struct GatherItem {
   T* out;                // rows x cols, row-major, ld = cols
   const int32_t* rows;
   const int32_t* cols;
   int32_t nr, nc;
+  const T* A;            // source matrix of this item (row-major, lda)
+  int64_t lda;
 };
 template <typename T>
 Err launch_gather_batched(const T* A, int64_t lda, const std::vector<GatherItem<T>>& items,

@@ -120,7 +120,9 @@ __global__ void gather_batched_kernel(const T* __restrict__ A, int64_t lda,
   const GatherItem<T> it = items[lo];
   int64_t e = t - start[lo];
   int j = (int)(e / it.nc), l = (int)(e - (int64_t)j * it.nc);
-  it.out[e] = A[(int64_t)it.rows[j] * lda + it.cols[l]];
+  const T* src = it.A ? it.A : A;
+  const int64_t ld = it.A ? it.lda : lda;
+  it.out[e] = src[(int64_t)it.rows[j] * ld + it.cols[l]];
 }
 
 __global__ void index_compose_kernel(int32_t* out, const int32_t* base, const int32_t* idx,

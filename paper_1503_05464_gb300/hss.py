@@ -56,7 +56,9 @@ class HssInfo(ctypes.Structure):
 _lib = None
 EXPORTS = ["hss_default_opts", "hss_compress", "hss_matvec", "hss_factor", "hss_solve",
            "hss_info", "hss_node_ranks", "hss_destroy", "hss_last_error",
-           "hss_random_gaussian", "hss_sample", "hss_id_batched", "hss_kernel_launches", "hss_sample_noalloc"]
+           "hss_random_gaussian", "hss_sample", "hss_id_batched", "hss_kernel_launches", "hss_sample_noalloc",
+           "hss_batch_create", "hss_batch_submit", "hss_batch_step", "hss_batch_take",
+           "hss_batch_last_error", "hss_batch_destroy", "hss_compress_batched"]
 
 
 def load(path: str = LIB_PATH):
@@ -85,8 +87,19 @@ def load(path: str = LIB_PATH):
     L.hss_sample_noalloc.argtypes = L.hss_sample.argtypes
     L.hss_kernel_launches.argtypes = []
     L.hss_kernel_launches.restype = ctypes.c_int64
+    L.hss_batch_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
+    L.hss_batch_submit.argtypes = [vp, vp, i64, i64, ctypes.POINTER(HssOpts), ctypes.POINTER(i64)]
+    L.hss_batch_step.argtypes = [vp, ctypes.POINTER(i32)]
+    L.hss_batch_take.argtypes = [vp, i64, ctypes.POINTER(vp)]
+    L.hss_batch_last_error.argtypes = [vp]
+    L.hss_batch_last_error.restype = ctypes.c_char_p
+    L.hss_batch_destroy.argtypes = [vp]
+    L.hss_batch_destroy.restype = None
+    L.hss_compress_batched.argtypes = [i32, vp, vp, vp, i32, ctypes.POINTER(HssOpts), i32, vp,
+                                       vp, vp]
     for name in EXPORTS:
-        if name not in ("hss_destroy", "hss_last_error", "hss_kernel_launches"):
+        if name not in ("hss_destroy", "hss_last_error", "hss_kernel_launches",
+                        "hss_batch_last_error", "hss_batch_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -164,6 +177,82 @@ def hss_compress(A: torch.Tensor, opts: HssOpts | None = None, stream=None, **kw
         raise HssError(st, msg)
     _check(st)
     return HSS(out.value, n, A.dtype)
+
+
+def hss_compress_batched(As, opts=None, stream=None, **kw):
+    """Compresses a list of square CUDA matrices together (one dtype); the
+    level work of all of them shares launches.  Returns a list of HSS
+    handles (None for a matrix that failed) and the per-matrix statuses."""
+    if not As:
+        return [], []
+    _require_cuda(*As)
+    cnt = len(As)
+    dt = _dtype(As[0])
+    if opts is None:
+        opts = hss_default_opts(**kw)
+    ptrs = (ctypes.c_void_p * cnt)(*[a.data_ptr() for a in As])
+    ns = (ctypes.c_int64 * cnt)(*[a.shape[0] for a in As])
+    lds = (ctypes.c_int64 * cnt)(*[a.stride(0) for a in As])
+    outs = (ctypes.c_void_p * cnt)()
+    sts = (ctypes.c_int * cnt)()
+    if isinstance(opts, (list, tuple)):
+        arr = (HssOpts * cnt)(*opts)
+        optp, stride = ctypes.cast(arr, ctypes.POINTER(HssOpts)), 1
+    else:
+        optp, stride = ctypes.pointer(opts), 0
+    load().hss_compress_batched(cnt, ptrs, ns, lds, dt, optp, stride, _stream(stream), outs, sts)
+    handles = [HSS(outs[i], As[i].shape[0], As[i].dtype) if outs[i] else None for i in range(cnt)]
+    return handles, [sts[i] for i in range(cnt)]
+
+
+class HssBatch:
+    """Incremental batch (continuous batching): submit matrices at any time,
+    step() runs one round for every job, take() hands over finished ones."""
+
+    def __init__(self, dtype=torch.float32, stream=None):
+        self.b = ctypes.c_void_p()
+        dt = HSS_F32 if dtype == torch.float32 else HSS_F64
+        self.dtype = dtype
+        self.stream = stream
+        _check(load().hss_batch_create(dt, _stream(stream), ctypes.byref(self.b)))
+        self.keep = {}
+
+    def submit(self, A: torch.Tensor, opts: HssOpts | None = None, **kw) -> int:
+        _require_cuda(A)
+        if opts is None:
+            opts = hss_default_opts(**kw)
+        t = ctypes.c_int64()
+        st = load().hss_batch_submit(self.b, ctypes.c_void_p(A.data_ptr()), A.shape[0],
+                                     A.stride(0), ctypes.byref(opts), ctypes.byref(t))
+        if st != HSS_OK:
+            raise HssError(st, load().hss_batch_last_error(self.b).decode())
+        self.keep[t.value] = A          # A must outlive its job
+        return t.value
+
+    def step(self) -> int:
+        act = ctypes.c_int32()
+        st = load().hss_batch_step(self.b, ctypes.byref(act))
+        if st != HSS_OK:
+            raise HssError(st, load().hss_batch_last_error(self.b).decode())
+        return act.value
+
+    def take(self, ticket: int):
+        """(HSS or None, status); status HSS_ERR_STATE while still running."""
+        out = ctypes.c_void_p()
+        st = load().hss_batch_take(self.b, ticket, ctypes.byref(out))
+        if st == HSS_ERR_STATE:
+            return None, st
+        A = self.keep.pop(ticket, None)
+        h = HSS(out.value, A.shape[0], A.dtype) if out.value else None
+        return h, st
+
+    def close(self):
+        if self.b and self.b.value and _lib is not None:
+            _lib.hss_batch_destroy(self.b)
+            self.b = ctypes.c_void_p(0)
+
+    def __del__(self):
+        self.close()
 
 
 def hss_matvec(h: HSS, X: torch.Tensor, B: torch.Tensor | None = None, stream=None) -> torch.Tensor:

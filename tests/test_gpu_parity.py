@@ -399,9 +399,19 @@ def test_full_size_gauss20k_matches_oracle(P):
     assert e64 <= 2 * max(wl["rtol"], e_or)
     h3 = P.hss_compress(A, sample_mode="bf16x3", **kw)
     r3 = P.hss_node_ranks(h3)
-    boundary = ho.d - 10
+    # nodes whose oracle rank is within 2 of the adaptive boundary d - p of
+    # the pass that compressed them may take another pass; skip them and
+    # their ancestors (whose inputs then differ)
+    skip = set()
+    for nd in ho.nodes:
+        if nd.id and max(ro[nd.id]) >= ho.data[nd.id].d_compressed - 10 - 2:
+            q = nd.id
+            while q >= 0:
+                skip.add(q)
+                q = ho.nodes[q].parent
+    assert len(skip) < len(ho.nodes) // 4
     for i in range(1, len(r3)):
-        if max(ro[i]) >= boundary - 2:
+        if i in skip:
             continue
         assert abs(r3[i][2] - ro[i][0]) <= 2 and abs(r3[i][3] - ro[i][1]) <= 2, (i, r3[i], ro[i])
     assert _probe_error(P, h3, A) <= 2 * max(e_or, wl["rtol"])
