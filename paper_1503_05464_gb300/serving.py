@@ -1,0 +1,213 @@
+"""Serving loop: compress + solve requests with continuous batching.
+
+Each request brings a dense matrix (here a Schur complement of a 3D Laplacian,
+n = k^2) and a schedule of right-hand-side batches.  The loop
+
+* admits an arrived request as soon as its estimated device memory fits the
+  HBM budget, and submits its compression to a running incremental batch
+  (hss_batch_submit): requests that arrive while others are being compressed
+  join the same per-level launches at the next round;
+* advances the batch one round at a time (one tree level of every job);
+* when a compression finishes, runs the ULV factorization, frees the input
+  matrix and keeps the compressed form resident;
+* serves each due right-hand-side batch with hss_solve on the resident form;
+* releases a request's form after its last solve.
+
+It reports p50/p99 latencies (arrival to first solution, and per solve batch)
+and throughput.  All GPU work runs in libhss; this module only schedules.
+"""
+from __future__ import annotations
+
+import heapq
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import hss as H
+
+
+@dataclass
+class Request:
+    rid: int
+    k: int                          # grid size: n = k^2
+    arrival: float                  # seconds after start
+    solves: list                    # [(seconds after compression done, nrhs)]
+    scale: float = 1.0
+    # filled by the server
+    A: torch.Tensor | None = None
+    ticket: int = -1
+    handle: H.HSS | None = None
+    t_admit: float = math.nan
+    t_compressed: float = math.nan
+    t_first_solution: float = math.nan
+    reserved: int = 0
+    resident: int = 0
+    solves_left: int = 0
+    ranks: int = 0
+
+    @property
+    def n(self):
+        return self.k * self.k
+
+
+def poisson_requests(count, rate, ks, seed, max_solves=3, nrhs_range=(1, 64)):
+    """`count` requests, exponential inter-arrival times at `rate` per second,
+    grid sizes drawn from `ks`, 1..max_solves solve batches of 1..64 RHS."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += rng.exponential(1.0 / rate)
+        ns = int(rng.integers(1, max_solves + 1))
+        solves = sorted((float(rng.exponential(0.05)), int(rng.integers(nrhs_range[0], nrhs_range[1] + 1)))
+                        for _ in range(ns))
+        out.append(Request(i, int(rng.choice(ks)), t, solves, scale=float(1.0 + 0.1 * rng.random())))
+    return out
+
+
+def estimate_bytes(n, opts, esz=4):
+    """Peak device memory of one compression: the matrix, the samples, the
+    column-sample partial slab of one pass, and the resident form."""
+    d = max(opts.d0, 64) * 4
+    a = n * n * esz
+    samples = 3 * n * d * esz
+    slab = ((n + 127) // 128) * ((opts.d0 + 63) // 64) * n * 64 * esz
+    return a + samples + slab
+
+
+@dataclass
+class ServeStats:
+    requests: int = 0
+    solves: int = 0
+    rhs: int = 0
+    wall_s: float = 0.0
+    request_latency: list = field(default_factory=list)
+    solve_latency: list = field(default_factory=list)
+    compress_latency: list = field(default_factory=list)
+    peak_reserved: int = 0
+    max_inflight: int = 0
+
+    def summary(self):
+        def pct(v, q):
+            return float(np.percentile(v, q)) if v else None
+        return {
+            "requests": self.requests, "solves": self.solves, "rhs": self.rhs,
+            "wall_s": self.wall_s,
+            "request_p50_s": pct(self.request_latency, 50),
+            "request_p99_s": pct(self.request_latency, 99),
+            "solve_p50_s": pct(self.solve_latency, 50),
+            "solve_p99_s": pct(self.solve_latency, 99),
+            "compress_p50_s": pct(self.compress_latency, 50),
+            "solves_per_s": self.solves / self.wall_s if self.wall_s else None,
+            "rhs_per_s": self.rhs / self.wall_s if self.wall_s else None,
+            "peak_reserved_gb": self.peak_reserved / 1e9,
+            "max_inflight": self.max_inflight,
+        }
+
+
+class Server:
+    def __init__(self, make_matrix, opts, budget_bytes, stream=None, keep_handles=False):
+        self.make_matrix = make_matrix          # k -> device template matrix
+        self.opts = opts
+        self.budget = budget_bytes
+        self.stream = stream
+        self.keep = keep_handles
+        self.templates = {}
+        self.done = []
+
+    def _template(self, k):
+        if k not in self.templates:
+            self.templates[k] = self.make_matrix(k)
+        return self.templates[k]
+
+    def run(self, requests):
+        st = ServeStats(requests=len(requests))
+        pending = sorted(requests, key=lambda r: r.arrival)
+        for r in pending:                     # generate inputs before the clock starts
+            self._template(r.k)
+        torch.cuda.synchronize()
+        batch = H.HssBatch(torch.float32, self.stream)
+        inflight = {}
+        due = []                              # heap of (time, seq, request, nrhs)
+        used = 0
+        seq = 0
+        t0 = time.perf_counter()
+
+        def now():
+            return time.perf_counter() - t0
+
+        while pending or inflight or due:
+            t = now()
+            # admission: arrived requests whose estimate fits the budget
+            while pending and pending[0].arrival <= t:
+                r = pending[0]
+                need = estimate_bytes(r.n, self.opts)
+                if used + need > self.budget and inflight:
+                    break
+                pending.pop(0)
+                r.A = self._template(r.k) * r.scale
+                r.reserved = need
+                used += need
+                r.t_admit = now()
+                r.ticket = batch.submit(r.A, self.opts)
+                inflight[r.ticket] = r
+            st.peak_reserved = max(st.peak_reserved, used)
+            st.max_inflight = max(st.max_inflight, len(inflight))
+            # one round of every compression in flight
+            if inflight:
+                batch.step()
+                for ticket in list(inflight):
+                    h, status = batch.take(ticket)
+                    if status == H.HSS_ERR_STATE:
+                        continue
+                    r = inflight.pop(ticket)
+                    if h is None:
+                        raise H.HssError(status, f"request {r.rid} failed")
+                    H.hss_factor(h, self.stream)
+                    info = H.hss_info(h)
+                    r.handle = h
+                    r.ranks = max(info["max_rank_r"], info["max_rank_c"])
+                    r.t_compressed = now()
+                    st.compress_latency.append(r.t_compressed - r.arrival)
+                    r.A = None
+                    used -= r.reserved
+                    r.resident = info["bytes_hss"] + info["bytes_ulv"]
+                    used += r.resident
+                    r.solves_left = len(r.solves)
+                    for off, nrhs in r.solves:
+                        heapq.heappush(due, (r.t_compressed + off, seq, r, nrhs))
+                        seq += 1
+            # due right-hand sides
+            t = now()
+            while due and due[0][0] <= t:
+                tdue, _, r, nrhs = heapq.heappop(due)
+                g = torch.Generator(device="cuda").manual_seed(1000 * r.rid + nrhs)
+                B = torch.randn(r.n, nrhs, device="cuda", generator=g)
+                X = H.hss_solve(r.handle, B, stream=self.stream)
+                torch.cuda.current_stream().synchronize() if self.stream is None else self.stream.synchronize()
+                tf = now()
+                st.solve_latency.append(tf - tdue)
+                st.solves += 1
+                st.rhs += nrhs
+                if math.isnan(r.t_first_solution):
+                    r.t_first_solution = tf
+                    st.request_latency.append(tf - r.arrival)
+                r.solves_left -= 1
+                if r.solves_left == 0:
+                    used -= r.resident
+                    if self.keep:
+                        self.done.append(r)
+                    else:
+                        r.handle.close()
+                        r.handle = None
+                del X, B
+            if not inflight and not due and pending:
+                wait = pending[0].arrival - now()
+                if wait > 0:
+                    time.sleep(min(wait, 0.01))
+        st.wall_s = now()
+        batch.close()
+        return st

@@ -291,3 +291,31 @@ def test_ulv_two_level_by_hand():
     O.ulv_factor(h)
     b = np.random.default_rng(2).standard_normal(96)
     np.testing.assert_allclose(A @ O.ulv_solve(h, b), b, atol=1e-9)
+
+
+# --------------------------------------------- Schur complement input family
+@pytest.mark.parametrize("k", [2, 3, 5, 6])
+def test_laplacian_schur_closed_form_matches_sparse_elimination(k):
+    """The closed form equals A22 - A21 A11^{-1} A12 of the explicit 7-point
+    Laplacian on a k x k x (2k+1) grid (Dirichlet), middle plane last."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    nz = 2 * k + 1
+
+    def lap1(m):
+        return sp.diags([-np.ones(m - 1), 2 * np.ones(m), -np.ones(m - 1)], [-1, 0, 1])
+
+    I = sp.identity(k)
+    Lxy = sp.kron(lap1(k), I) + sp.kron(I, lap1(k))
+    L = sp.kron(lap1(nz), sp.identity(k * k)) + sp.kron(sp.identity(nz), Lxy)
+    L = L.tocsc()
+    mid = np.arange(k * k) + k * k * k          # plane z = k
+    rest = np.setdiff1d(np.arange(nz * k * k), mid)
+    A11 = L[rest][:, rest]
+    A12 = L[rest][:, mid].toarray()
+    S = L[mid][:, mid].toarray() - L[mid][:, rest] @ spla.spsolve(A11, A12)
+    Sc = W.laplacian_schur(k, dtype=np.float64).numpy()
+    np.testing.assert_allclose(Sc, S, atol=1e-12)
+    # closed-form eigenvalues and solve
+    ev = np.sort(W.laplacian_schur_eigs(k).ravel())
+    np.testing.assert_allclose(np.sort(np.linalg.eigvalsh(S)), ev, atol=1e-12)

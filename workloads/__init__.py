@@ -15,6 +15,9 @@ Matrix families (stand-ins for the paper's application matrices, Section 4.1):
                              uniform on the unit sphere.
 * ``random_hss``             a dense matrix assembled from random HSS generators
                              with prescribed ranks (known-rank test input).
+* ``laplacian_schur``        the dense Schur complement, onto the middle plane,
+                             of the 7-point Laplacian on a k x k x (2k+1) grid
+                             with Dirichlet boundaries (n = k^2).
 
 Point clouds are put in recursive-coordinate-bisection order whose splits match
 the cluster tree's bisection (left part = floor(s/2) points), so that the
@@ -200,3 +203,44 @@ def random_hss(n: int, leaf_size: int, rank: int, seed: int, diag_shift: float =
     else:
         rec(root, True)
     return A, ranks
+
+
+# ------------------------------------------- Schur complement of a 3D Laplacian
+def dst_basis(k: int) -> np.ndarray:
+    """Orthonormal DST-I basis: phi[i, p] = sqrt(2/(k+1)) sin((i+1)(p+1) pi/(k+1))."""
+    i = np.arange(1, k + 1)
+    return np.sqrt(2.0 / (k + 1)) * np.sin(np.outer(i, i) * np.pi / (k + 1))
+
+
+def laplacian_schur_eigs(k: int) -> np.ndarray:
+    """Eigenvalues s[p, q] of the middle-plane Schur complement.
+
+    With the 2D sine transform of the k x k plane, the 7-point operator splits
+    into independent chains along z (diagonal 2 + mu_p + mu_q, off-diagonal
+    -1, mu_p = 2 - 2 cos(p pi/(k+1))).  Eliminating the k-node chain on each
+    side of the middle node leaves s = a - 2 c_k, with a = 2 + mu_p + mu_q,
+    c_1 = 1/a, c_j = 1/(a - c_{j-1}) (the last diagonal entry of the inverse
+    of a k-node chain).
+    """
+    p = np.arange(1, k + 1)
+    mu = 2.0 - 2.0 * np.cos(p * np.pi / (k + 1))
+    a = 2.0 + mu[:, None] + mu[None, :]
+    c = 1.0 / a
+    for _ in range(k - 1):
+        c = 1.0 / (a - c)
+    return a - 2.0 * c
+
+
+def laplacian_schur(k: int, dtype=np.float32, device="cpu"):
+    """Dense n x n (n = k^2) Schur complement S = A22 - A21 A11^{-1} A12 of the
+    7-point Laplacian on a k x k x (2k+1) grid split at the middle plane, from
+    its closed form S = (phi x phi) diag(s) (phi x phi)^T, computed in FP64."""
+    dev = _dev(device)
+    phi = torch.as_tensor(dst_basis(k), dtype=torch.float64, device=dev)
+    sv = torch.as_tensor(laplacian_schur_eigs(k), dtype=torch.float64, device=dev)
+    # M[p, i2, j2] = sum_q s[p,q] phi[i2,q] phi[j2,q]
+    M = torch.einsum("pq,iq,jq->pij", sv, phi, phi).reshape(k, k * k)
+    # S[(i1, j1), (i2, j2)] = sum_p phi[i1,p] phi[j1,p] M[p, (i2, j2)]
+    PP = (phi[:, None, :] * phi[None, :, :]).reshape(k * k, k)
+    S = (PP @ M).reshape(k, k, k, k).permute(0, 2, 1, 3).reshape(k * k, k * k)
+    return S.to(_tdtype(dtype)).contiguous()
