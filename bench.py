@@ -16,6 +16,20 @@ Workloads (synthetic, seeded; stand-ins for the paper's application matrices):
   bem60k      FP32 a_ij = 1/(4 pi |x_i-x_j|), a_ii = sqrt(n), n=60000 points
               on the unit sphere in RCB order, leaf 512, rtol 1e-6, d0=256,
               step 128
+  batch512    512 FP32 matrices, n uniform in [1000, 8000], half Toeplitz and
+              half Gaussian kernel (h uniform in [0.1, 0.4]); a step is one
+              batched compression of all of them + ULV factor + a 16-RHS solve
+              each; value = seconds per matrix; the same work done one matrix
+              at a time is reported beside it
+  serve       Poisson stream of compress+solve requests on Schur complements of
+              the 7-point Laplacian (n = k^2, k in {45, 71, 100, 141, 200}),
+              rtol 1e-6, 150 GB admission budget, arrival rate 80% of the
+              measured service rate; value = p50 request latency (arrival to
+              first solution); --requests sets the stream length
+
+The default line (gauss20k) also carries a "serving" object (a bounded
+stream of the serve workload) and a "batching" object (64 matrices of the
+batch512 mix, batched vs one at a time); --no-extras leaves them out.
 
 --impl reference times the CPU oracle (FP64 numpy/scipy, the reference
 implementation written from the paper) on the host cores, on the same
@@ -46,6 +60,9 @@ WORKLOADS = {
                        step=32, dtype="f64", seed=1001),
     "bem60k": dict(family="bem_like_sphere", n=60000, leaf=512, rtol=1e-6, d0=256, step=128,
                    dtype="f32", seed=1003),
+    "batch512": dict(family="mixed_batch", count=512, seed=1004, dtype="f32", nrhs=16),
+    "serve": dict(family="laplacian_schur", ks=[45, 71, 100, 141, 200], rtol=1e-6, leaf=256,
+                  d0=128, step=64, dtype="f32", seed=1005, budget=150e9, load=0.8),
 }
 
 METRIC = "HSS compress s"
@@ -146,6 +163,8 @@ def run_ours(args, wl):
     import __graft_entry__ as g
     g.build()
     import paper_1503_05464_gb300 as P
+    if wl["family"] in ("mixed_batch", "laplacian_schur"):
+        return run_aux(args, wl, P, dev, rank, world)
 
     A = make_matrix(wl, dev).contiguous()
     torch.cuda.synchronize()
@@ -267,8 +286,166 @@ def run_ours(args, wl):
     clocks = clk.summary()
     if clocks:
         out["clocks"] = clocks
+    if not args.no_extras:
+        # the batched and served forms, each beside the plain one-at-a-time method
+        out["batching"] = run_batching(P, dev, stream, count=64, seed=WORKLOADS["batch512"]["seed"])
+        out["serving"] = run_serving(P, dev, stream, WORKLOADS["serve"], count=args.requests or 100)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, A.cpu().numpy())
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _event_time(stream, fn):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, out
+
+
+def run_batching(P, dev, stream, count, seed, nrhs=16):
+    """Batched compression of `count` mixed matrices (one launch per level of
+    every job per round) + ULV factor + an nrhs solve of each, against the same
+    work done one matrix at a time.  Both results must agree exactly (same
+    ranks, same solution bits)."""
+    import torch
+    import workloads as W
+    specs = W.mixed_batch_specs(count, seed)
+    mats = [W.build_matrix(sp, np.float32, dev) for sp in specs]
+    opts = [P.hss_default_opts(leaf_size=sp["leaf"], rtol=sp["rtol"], d0=sp["d0"],
+                               d_step=sp["step"], seed=seed + 1, sample_mode="bf16x3")
+            for sp in specs]
+    g = torch.Generator(device=dev).manual_seed(seed)
+    Bs = [torch.randn(A.shape[0], nrhs, device=dev, generator=g) for A in mats]
+
+    def batched(ms, os_, bs):
+        hs, sts = P.hss_compress_batched(ms, list(os_), stream=stream)
+        xs = []
+        for h, b in zip(hs, bs):
+            P.hss_factor(h, stream)
+            xs.append(P.hss_solve(h, b, stream=stream))
+        return hs, sts, xs
+
+    def sequential(ms, os_, bs):
+        hs, xs = [], []
+        for A, o, b in zip(ms, os_, bs):
+            h = P.hss_compress(A, o, stream=stream)
+            P.hss_factor(h, stream)
+            xs.append(P.hss_solve(h, b, stream=stream))
+            hs.append(h)
+        return hs, xs
+
+    batched(mats[:8], opts[:8], Bs[:8])          # warm-up (allocator, attributes)
+    sequential(mats[:8], opts[:8], Bs[:8])
+    l0 = P.hss.hss_kernel_launches()
+    t_b, (hb, sts, xb) = _event_time(stream, lambda: batched(mats, opts, Bs))
+    lb = P.hss.hss_kernel_launches() - l0
+    ranks_b = [P.hss_node_ranks(h) for h in hb]
+    for h in hb:
+        h.close()
+    l0 = P.hss.hss_kernel_launches()
+    t_s, (hs_, xs_) = _event_time(stream, lambda: sequential(mats, opts, Bs))
+    ls = P.hss.hss_kernel_launches() - l0
+    same = all(P.hss_node_ranks(h) == r for h, r in zip(hs_, ranks_b)) and \
+        all(torch.equal(a, b) for a, b in zip(xb, xs_))
+    res = 0.0
+    for i in range(0, count, max(1, count // 16)):
+        A = mats[i].double()
+        r = torch.linalg.norm(A @ xb[i].double() - Bs[i].double()) / torch.linalg.norm(Bs[i].double())
+        res = max(res, float(r))
+    for h in hs_:
+        h.close()
+    del mats, Bs, xb, xs_
+    torch.cuda.empty_cache()
+    return {"matrices": count, "nrhs": nrhs, "failed": sum(1 for x in sts if x != 0),
+            "batched_s": t_b, "sequential_s": t_s, "speedup": t_s / t_b,
+            "batched_s_per_matrix": t_b / count, "launches_batched": lb,
+            "launches_sequential": ls, "identical_to_alone": bool(same),
+            "max_solve_rel_residual": res,
+            "gb_fp32_inputs": sum(sp["n"] ** 2 * 4 for sp in specs) / 1e9,
+            "mix": "n ~ U[1000, 8000]; Toeplitz rtol 1e-6 (64/32) and Gaussian kernel "
+                   "h ~ U[0.1, 0.4] rtol 1e-4 (128/64); leaf 128 (n < 4000) or 256; bf16x3"}
+
+
+def run_serving(P, dev, stream, wl, count, load=None, warm=True):
+    """A Poisson stream of compress+solve requests through serving.Server
+    (continuous batching, HBM-budget admission); the arrival rate is `load`
+    times the service rate measured by compressing + factoring one request
+    of each size alone."""
+    import torch
+    import workloads as W
+    from paper_1503_05464_gb300 import serving as S
+    opts = P.hss_default_opts(leaf_size=wl["leaf"], rtol=wl["rtol"], d0=wl["d0"],
+                              d_step=wl["step"], seed=wl["seed"] + 1, sample_mode="bf16x3")
+    make = lambda k: W.laplacian_schur(k, dtype=np.float32, device=dev)
+    service = {}
+    for k in wl["ks"]:
+        A = make(k)
+        if warm:
+            P.hss_compress(A, opts, stream=stream).close()
+        t, h = _event_time(stream, lambda: P.hss_compress(A, opts, stream=stream))
+        t2, _ = _event_time(stream, lambda: P.hss_factor(h, stream))
+        service[k] = t + t2
+        h.close()
+        del A
+    torch.cuda.empty_cache()
+    mean_service = sum(service.values()) / len(service)
+    load = wl["load"] if load is None else load
+    rate = load / mean_service
+    reqs = S.poisson_requests(count, rate, wl["ks"], seed=wl["seed"], max_solves=3,
+                              nrhs_range=(1, 64))
+    srv = S.Server(make, opts, budget_bytes=int(wl["budget"]), stream=stream)
+    l0 = P.hss.hss_kernel_launches()
+    st = srv.run(reqs)
+    summ = st.summary()
+    summ.update({"arrival_rate_per_s": rate, "load": load,
+                 "service_s_alone": {str(k * k): v for k, v in service.items()},
+                 "launches": P.hss.hss_kernel_launches() - l0,
+                 "sizes": [k * k for k in wl["ks"]], "rtol": wl["rtol"],
+                 "budget_gb": wl["budget"] / 1e9})
+    srv.templates.clear()
+    torch.cuda.empty_cache()
+    return summ
+
+
+def run_aux(args, wl, P, dev, rank, world):
+    """The batch512 and serve workloads (each rank runs its own replica)."""
+    import torch
+    import torch.distributed as dist
+    stream = torch.cuda.current_stream()
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        if wl["family"] == "mixed_batch":
+            res = run_batching(P, dev, stream, count=wl["count"], seed=wl["seed"], nrhs=wl["nrhs"])
+            value, key = res["batched_s_per_matrix"], "batching"
+            ms = res["batched_s"] * 1e3
+        else:
+            res = run_serving(P, dev, stream, wl, count=args.requests or 2000)
+            value, key = res["request_p50_s"], "serving"
+            ms = res["wall_s"] * 1e3
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    out = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": 1,
+           "warmup": 1, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64-id", "data": "synthetic",
+           "config": {"workload": args.workload, "sample_mode": "bf16x3",
+                      "value_is": ("batched seconds per matrix (compress + factor + solve)"
+                                   if key == "batching" else
+                                   "p50 request latency, arrival to first solution")},
+           key: res}
+    clocks = clk.summary()
+    if clocks:
+        out["clocks"] = clocks
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -299,12 +476,48 @@ def cpu_baseline(wl, A_np):
             "sample": f"one full FP64 oracle compression of {wl['family']} n={wl['n']}"}
 
 
+def run_reference_aux(args, wl, O):
+    """Oracle on a bounded sample of the batch512 / serve workloads: each step
+    compresses, factors and solves two matrices (the batch mix's first two, or
+    one Schur complement of each of the two smallest request sizes)."""
+    import workloads as W
+    if wl["family"] == "mixed_batch":
+        specs = W.mixed_batch_specs(wl["count"], wl["seed"])[:2]
+        items = [(W.build_matrix(sp, np.float32, "cpu").numpy().astype(np.float64),
+                  sp["rtol"], sp["leaf"], sp["d0"], sp["step"], wl["nrhs"]) for sp in specs]
+        sample = "compress + factor + 16-RHS solve of 2 matrices of the batch mix per step"
+    else:
+        items = [(W.laplacian_schur(k, dtype=np.float32).numpy().astype(np.float64), wl["rtol"],
+                  wl["leaf"], wl["d0"], wl["step"], 8) for k in wl["ks"][:2]]
+        sample = "compress + factor + 8-RHS solve of one Schur request of n=2025 and n=5041 per step"
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for A, rtol, leaf, d0, step, nrhs in items:
+            h = O.compress(A, rtol, leaf_size=leaf, d0=d0, d_step=step, seed=wl["seed"] + 1)
+            O.ulv_factor(h)
+            O.ulv_solve(h, np.ones((A.shape[0], nrhs)))
+        if i >= args.warmup:
+            times.append((time.perf_counter() - t0) / len(items))
+    v = sum(times) / len(times)
+    out = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": v * 1e3 * len(items), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference", "config": {"workload": args.workload},
+           "cpu_baseline": {"value": v, "unit": "s", "cores": _threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args, wl):
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import workloads  # noqa: F401
     from oracle import hss_oracle as O
+    if wl["family"] in ("mixed_batch", "laplacian_schur"):
+        return run_reference_aux(args, wl, O)
     A = make_matrix(wl, "cpu").numpy().astype(np.float64)
     times = []
     for i in range(args.warmup + args.steps):
@@ -336,6 +549,10 @@ def main():
                     help="sampling arithmetic (default: bf16x3 for FP32 inputs, native for FP64)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave the batching and serving objects out of the default line")
+    ap.add_argument("--requests", type=int, default=None,
+                    help="length of the served request stream")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.mode is None:

@@ -14,6 +14,9 @@
 // the sample error stays near one rounding instead of growing like sqrt(n).
 #include "hss_internal.cuh"
 
+#include <cstdlib>
+#include <cstring>
+
 #include <cuda_bf16.h>
 
 namespace hss {
@@ -210,6 +213,19 @@ Err launch_sample_mma(const float* A, int64_t n, int64_t lda, const float* R, in
                       int64_t c0, int64_t ncols, float* Sr, float* Sc, int64_t lds,
                       const int32_t* leaf_of, int mode, float* P, cudaStream_t s);
 
+bool sample_tc_supported(const float* A, int64_t n, int64_t lda, int mode);
+Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int64_t ldr,
+                     int64_t c0, int64_t ncols, float* Sr, float* Sc, int64_t lds,
+                     const int32_t* leaf_of, int mode, SampleScratch* scratch, cudaStream_t s);
+
+static bool legacy_mma_requested() {
+  static const bool v = [] {
+    const char* e = std::getenv("HSS_SAMPLE_KERNEL");
+    return e != nullptr && std::strcmp(e, "mma") == 0;
+  }();
+  return v;
+}
+
 size_t sample_scratch_bytes(int64_t n, int64_t ncols, int mode, bool f64) {
   (void)mode;
   int64_t npanel = (n + S_BM - 1) / S_BM;
@@ -224,7 +240,11 @@ Err launch_sample(const T* A, int64_t n, int64_t lda, const T* R, int64_t ldr, i
   int64_t ncols = c1 - c0;
   if (n <= 0 || ncols <= 0) return ok();
   const bool f64 = sizeof(T) == 8;
-  size_t need = sample_scratch_bytes(n, ncols, mode, f64);
+  // split-bfloat16 modes run on tcgen05 when A's layout suits TMA (16-byte
+  // aligned rows); HSS_SAMPLE_KERNEL=mma selects the warp-level mma.sync kernel
+  const bool tc = !f64 && !legacy_mma_requested() &&
+                  sample_tc_supported(reinterpret_cast<const float*>(A), n, lda, mode);
+  size_t need = tc ? 0 : sample_scratch_bytes(n, ncols, mode, f64);
   if (scratch->bytes < need) {
     dfree(scratch->part, s);
     scratch->part = nullptr;
@@ -244,7 +264,12 @@ Err launch_sample(const T* A, int64_t n, int64_t lda, const T* R, int64_t ldr, i
     HSS_CUDA_TRY(cudaEventRecord(e0, s));
   }
   T* P = reinterpret_cast<T*>(scratch->part);
-  if (sizeof(T) == 4 && mode != HSS_SAMPLE_NATIVE) {
+  if (tc) {
+    HSS_TRY(launch_sample_tc(reinterpret_cast<const float*>(A), n, lda,
+                             reinterpret_cast<const float*>(R), ldr, c0, ncols,
+                             reinterpret_cast<float*>(Sr), reinterpret_cast<float*>(Sc), lds,
+                             leaf_of, mode, scratch, s));
+  } else if (sizeof(T) == 4 && mode != HSS_SAMPLE_NATIVE) {
     HSS_TRY(launch_sample_mma(reinterpret_cast<const float*>(A), n, lda,
                               reinterpret_cast<const float*>(R), ldr, c0, ncols,
                               reinterpret_cast<float*>(Sr), reinterpret_cast<float*>(Sc), lds,

@@ -1,0 +1,651 @@
+// Fused sampling on the 5th-generation tensor cores (tcgen05 + TMA + TMEM)
+// for FP32 inputs in the split-bfloat16 modes:
+//   Sr[:, c] = (A - D) R[:, c]  and  Sc[:, c] = (A - D)^T R[:, c]
+// (Section 2.2, step 2; Algorithm 1's leaf samples: D = the leaf diagonal
+// blocks), each tile of A read from HBM once for both products.
+//
+// Work decomposition.  A is cut into 128-row panels and 64-column tiles; the
+// tiles are numbered panel-major and split evenly over one persistent CTA
+// per SM (a CTA's range may start or end inside a panel, so every CTA gets
+// the same number of tiles whatever n is).  For a tile (panel p, columns J):
+//   row product     Sr_p    += A_pJ  R_J      M = 128 rows, N = c, K = 64
+//   column product  Sc_J^T   = R_p^T A_pJ     M = c (<= 128), N = 64, K = 128
+// with A_pJ = hi + mid (+ lo) bfloat16 planes.  Both products read the same
+// shared-memory planes: K-major for the row product, MN-major (transposed)
+// for the column product.  R is bfloat16-exact (its Gaussian entries are
+// rounded to bfloat16 when drawn), so it needs no split.
+//
+// Pipeline (warp-specialised, mbarrier hand-offs, 384 threads):
+//   warp 0     TMA producer: FP32 half-tiles of A (128 x 32, 128-byte
+//              swizzle) into a 4-stage ring, R_J (64 rows) and R_p (128
+//              rows) as bfloat16 boxes;
+//   warps 4-7  converters: one row each; apply the leaf mask, split into
+//              the bfloat16 planes (double-buffered, swizzled operand layout);
+//   warp 1     MMA issuer (one thread): tcgen05.mma into TMEM;
+//   warps 8-11 epilogue: TMEM -> registers; the column product of each tile
+//              goes to a partial slab Sc_part[p][j][c] (summed over panels in
+//              FP64 afterwards); the row product is folded every two tiles
+//              into a Kahan-compensated FP32 sum kept in TMEM, and written at
+//              the end of each panel segment as an FP64 partial.
+// TMEM columns: [0,128) row accumulator, [128,256) two column accumulators,
+// [256,384) Kahan sum, [384,512) Kahan compensation.
+//
+// Every wait is bounded: on a timeout the CTA records an error code, stops,
+// waits (bounded) for its own copies and MMAs in flight, frees its TMEM and
+// returns; the host turns the code into HSS_ERR_TIMEOUT.
+#include "hss_internal.cuh"
+#include "hss_tc.cuh"
+
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+namespace hss {
+
+Err launch_sample_mma(const float* A, int64_t n, int64_t lda, const float* R, int64_t ldr,
+                      int64_t c0, int64_t ncols, float* Sr, float* Sc, int64_t lds,
+                      const int32_t* leaf_of, int mode, float* P, cudaStream_t s);
+size_t sample_scratch_bytes(int64_t n, int64_t ncols, int mode, bool f64);
+
+namespace {
+
+using namespace tc;
+
+constexpr int BM = 128;          // panel rows
+constexpr int BN = 64;           // column tile of A
+constexpr int CMAX = 128;        // sample columns per sweep
+constexpr int ASTAGES = 4;       // FP32 half-tile ring
+constexpr int FOLD = 2;          // tiles between Kahan folds of the row product
+constexpr int THREADS = 384;
+constexpr long long WAIT_LIMIT = 1ll << 32;   // clock cycles (about 2 s)
+
+constexpr uint32_t A_HALF_BYTES = BM * 32 * 4;   // 16 KB
+constexpr uint32_t PLANE_BYTES = BM * BN * 2;    // 16 KB
+constexpr uint32_t RJ_BYTES = BN * CMAX * 2;     // 16 KB (two 8 KB boxes)
+constexpr uint32_t RI_BYTES = BM * CMAX * 2;     // 32 KB (two 16 KB boxes)
+
+template <int NT>
+struct Layout {
+  static constexpr uint32_t a = 0;
+  static constexpr uint32_t planes = a + ASTAGES * A_HALF_BYTES;
+  static constexpr uint32_t rj = planes + 2 * NT * PLANE_BYTES;
+  static constexpr uint32_t ri = rj + 2 * RJ_BYTES;
+  static constexpr uint32_t bars = ri + RI_BYTES;
+  static constexpr uint32_t total = bars + 256;
+  static constexpr uint32_t alloc = total + 1024;   // room to align the base to 1 KB
+};
+
+// barrier slots
+enum {
+  B_AFULL = 0, B_AEMPTY = 4, B_PFULL = 8, B_PEMPTY = 10, B_RJFULL = 12, B_RJEMPTY = 14,
+  B_RIFULL = 16, B_RIEMPTY = 17, B_CFULL = 18, B_CEMPTY = 20, B_RFULL = 22, B_REMPTY = 23,
+  B_DRAIN = 24, B_COUNT = 25
+};
+
+struct TcArgs {
+  int n;          // matrix order
+  int c;          // sample columns of this sweep (1..128)
+  int ncb;        // 64-column boxes of R per row (1 or 2)
+  int nr;         // N of the row product (c rounded up to 16)
+  int ntc;        // column tiles per panel
+  int npanel;
+  long long T;    // tiles in total
+  int P;          // CTAs
+  int maxparts;   // panel segments per panel, at most
+  const int32_t* leaf_of;
+  float* sc_part;    // [npanel][n][c]
+  double* sr_part;   // [npanel][maxparts][c][128]
+  int* err;
+};
+
+__device__ __forceinline__ long long tile_begin(long long q, long long T, long long P) {
+  return q * T / P;
+}
+// the CTA whose tile range holds tile t
+__device__ __forceinline__ long long tile_owner(long long t, long long T, long long P) {
+  return ((t + 1) * P - 1) / T;
+}
+
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
+  const float y = x - comp;
+  const float t = sum + y;
+  comp = (t - sum) - y;
+  sum = t;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(THREADS, 1)
+    sample_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                     const __grid_constant__ CUtensorMap tmRJ,
+                     const __grid_constant__ CUtensorMap tmRI, const TcArgs g) {
+  using L = Layout<NT>;
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) &
+                                           ~static_cast<uintptr_t>(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::bars);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::bars + B_COUNT * 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L::bars + B_COUNT * 8 + 4);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  auto bar = [&](int i) { return su32(&bars[i]); };
+
+  if (tid == 0) {
+    for (int i = 0; i < ASTAGES; ++i) {
+      mbar_init(bar(B_AFULL + i), 1);
+      mbar_init(bar(B_AEMPTY + i), BM);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(bar(B_PFULL + i), BM);
+      mbar_init(bar(B_PEMPTY + i), 1);
+      mbar_init(bar(B_RJFULL + i), 1);
+      mbar_init(bar(B_RJEMPTY + i), 1);
+      mbar_init(bar(B_CFULL + i), 1);
+      mbar_init(bar(B_CEMPTY + i), BM);
+    }
+    mbar_init(bar(B_RIFULL), 1);
+    mbar_init(bar(B_RIEMPTY), 1);
+    mbar_init(bar(B_RFULL), 1);
+    mbar_init(bar(B_REMPTY), BM);
+    mbar_init(bar(B_DRAIN), 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    prefetch_tmap(&tmA);
+    prefetch_tmap(&tmRJ);
+    prefetch_tmap(&tmRI);
+  }
+  if (warp == 1) {
+    tmem_alloc(su32(tslot), 512);
+    tmem_relinquish();
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = *tslot;
+
+  const long long q = blockIdx.x;
+  const long long tb = tile_begin(q, g.T, g.P), te = tile_begin(q + 1, g.T, g.P);
+  const int ntc = g.ntc;
+
+  if (warp == 0) {
+    // ------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int a_cnt = 0, tl = 0, seg = 0, ri_uses = 0;
+      for (long long t = tb; t < te; ++t) {
+        const int p = static_cast<int>(t / ntc), J = static_cast<int>(t % ntc);
+        const bool first = (t == tb) || J == 0, last = (t == te - 1) || J == ntc - 1;
+        if (first) {
+          if (!mbar_wait(bar(B_RIEMPTY), (seg & 1) ^ 1, abort_flag, g.err, 1, WAIT_LIMIT)) break;
+          mbar_expect_tx(bar(B_RIFULL), g.ncb * (RI_BYTES / 2));
+          for (int cb = 0; cb < g.ncb; ++cb)
+            tma_load_2d(su32(sm + L::ri + cb * (RI_BYTES / 2)), &tmRI, cb * 64, p * BM,
+                        bar(B_RIFULL));
+          ++ri_uses;
+        }
+        bool ok = true;
+        for (int h = 0; h < 2 && ok; ++h) {
+          const int s = a_cnt % ASTAGES, u = a_cnt / ASTAGES;
+          ok = mbar_wait(bar(B_AEMPTY + s), (u & 1) ^ 1, abort_flag, g.err, 2, WAIT_LIMIT);
+          if (!ok) break;
+          mbar_expect_tx(bar(B_AFULL + s), A_HALF_BYTES);
+          tma_load_2d(su32(sm + L::a + s * A_HALF_BYTES), &tmA, J * BN + h * 32, p * BM,
+                      bar(B_AFULL + s));
+          ++a_cnt;
+        }
+        if (!ok) break;
+        const int r = tl & 1, u = tl >> 1;
+        if (!mbar_wait(bar(B_RJEMPTY + r), (u & 1) ^ 1, abort_flag, g.err, 3, WAIT_LIMIT)) break;
+        mbar_expect_tx(bar(B_RJFULL + r), g.ncb * (RJ_BYTES / 2));
+        for (int cb = 0; cb < g.ncb; ++cb)
+          tma_load_2d(su32(sm + L::rj + r * RJ_BYTES + cb * (RJ_BYTES / 2)), &tmRJ, cb * 64,
+                      J * BN, bar(B_RJFULL + r));
+        ++tl;
+        if (last) ++seg;
+      }
+      if (*abort_flag) {
+        // let every copy this thread issued land before the CTA exits
+        volatile int never = 0;
+        for (int s = 0; s < ASTAGES; ++s) {
+          const int uses = (a_cnt - s + ASTAGES - 1) / ASTAGES;
+          if (uses > 0) mbar_wait(bar(B_AFULL + s), (uses - 1) & 1, &never, g.err, 9, WAIT_LIMIT);
+        }
+        for (int r = 0; r < 2; ++r) {
+          const int uses = (tl - r + 1) / 2;
+          if (uses > 0) mbar_wait(bar(B_RJFULL + r), (uses - 1) & 1, &never, g.err, 9, WAIT_LIMIT);
+        }
+        if (ri_uses) mbar_wait(bar(B_RIFULL), (ri_uses - 1) & 1, &never, g.err, 9, WAIT_LIMIT);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idr = idesc_bf16(BM, g.nr, 0, 1);    // planes K-major, R_J MN-major
+      const uint32_t idc = idesc_bf16(BM, BN, 1, 1);      // R_p^T MN-major, planes MN-major
+      const uint32_t pl0 = su32(sm + L::planes), rj0 = su32(sm + L::rj), ri0 = su32(sm + L::ri);
+      int tl = 0, seg = 0, folds = 0, since = 0;
+      for (long long t = tb; t < te; ++t) {
+        const int J = static_cast<int>(t % ntc);
+        const bool first = (t == tb) || J == 0, last = (t == te - 1) || J == ntc - 1;
+        if (first && !mbar_wait(bar(B_RIFULL), seg & 1, abort_flag, g.err, 4, WAIT_LIMIT)) break;
+        const int ps = tl & 1, u = tl >> 1;
+        if (!mbar_wait(bar(B_PFULL + ps), u & 1, abort_flag, g.err, 5, WAIT_LIMIT)) break;
+        if (!mbar_wait(bar(B_RJFULL + ps), u & 1, abort_flag, g.err, 6, WAIT_LIMIT)) break;
+        if (!mbar_wait(bar(B_CEMPTY + ps), (u & 1) ^ 1, abort_flag, g.err, 7, WAIT_LIMIT)) break;
+        if (since == 0 && folds > 0 &&
+            !mbar_wait(bar(B_REMPTY), (folds - 1) & 1, abort_flag, g.err, 8, WAIT_LIMIT))
+          break;
+        fence_after();
+        const uint32_t pbase = pl0 + ps * NT * PLANE_BYTES;
+        const uint32_t rjb = rj0 + ps * RJ_BYTES;
+#pragma unroll
+        for (int term = 0; term < NT; ++term) {
+#pragma unroll
+          for (int k = 0; k < BN / 16; ++k)
+            mma_bf16(tbase, sdesc(pbase + term * PLANE_BYTES + 32 * k, 16, 1024),
+                     sdesc(rjb + 2048 * k, RJ_BYTES / 2, 1024), idr,
+                     (since > 0 || term > 0 || k > 0) ? 1u : 0u);
+        }
+        const uint32_t dc = tbase + 128 + 64 * ps;
+#pragma unroll
+        for (int term = 0; term < NT; ++term) {
+#pragma unroll
+          for (int k = 0; k < BM / 16; ++k)
+            mma_bf16(dc, sdesc(ri0 + 2048 * k, RI_BYTES / 2, 1024),
+                     sdesc(pbase + term * PLANE_BYTES + 2048 * k, 8192, 1024), idc,
+                     (term > 0 || k > 0) ? 1u : 0u);
+        }
+        mma_commit(bar(B_PEMPTY + ps));
+        mma_commit(bar(B_RJEMPTY + ps));
+        mma_commit(bar(B_CFULL + ps));
+        ++since;
+        if (since == FOLD || last) {
+          mma_commit(bar(B_RFULL));
+          ++folds;
+          since = 0;
+        }
+        if (last) {
+          mma_commit(bar(B_RIEMPTY));
+          ++seg;
+        }
+        ++tl;
+      }
+      // every MMA issued has completed before TMEM is released
+      mma_commit(bar(B_DRAIN));
+      volatile int never = 0;
+      mbar_wait(bar(B_DRAIN), 0, &never, g.err, 10, WAIT_LIMIT);
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // -------------------------------------------------------- converters
+    const int row = tid - 128;
+    int a_cnt = 0, tl = 0;
+    for (long long t = tb; t < te; ++t) {
+      const int p = static_cast<int>(t / ntc), J = static_cast<int>(t % ntc);
+      const int ps = tl & 1, u = tl >> 1;
+      if (!mbar_wait(bar(B_PEMPTY + ps), (u & 1) ^ 1, abort_flag, g.err, 11, WAIT_LIMIT)) break;
+      // leaf mask: only tiles whose row and column ranges share a leaf
+      const int n = g.n;
+      const int i0 = p * BM, j0 = J * BN;
+      const int li_lo = g.leaf_of[min(i0, n - 1)], li_hi = g.leaf_of[min(i0 + BM - 1, n - 1)];
+      const int lj_lo = g.leaf_of[min(j0, n - 1)], lj_hi = g.leaf_of[min(j0 + BN - 1, n - 1)];
+      const bool need_mask = !(lj_hi < li_lo || lj_lo > li_hi);
+      const int i = i0 + row;
+      const int li = (i < n) ? g.leaf_of[i] : -1;
+      uint8_t* pbase = sm + L::planes + ps * NT * PLANE_BYTES;
+      bool ok = true;
+      for (int h = 0; h < 2; ++h) {
+        const int s = a_cnt % ASTAGES, ua = a_cnt / ASTAGES;
+        if (!mbar_wait(bar(B_AFULL + s), ua & 1, abort_flag, g.err, 12, WAIT_LIMIT)) {
+          ok = false;
+          break;
+        }
+        const uint8_t* src = sm + L::a + s * A_HALF_BYTES;
+        float v[32];
+#pragma unroll
+        for (int qd = 0; qd < 8; ++qd) {
+          const float4 x = *reinterpret_cast<const float4*>(src + sw128(row, qd * 16));
+          v[4 * qd] = x.x;
+          v[4 * qd + 1] = x.y;
+          v[4 * qd + 2] = x.z;
+          v[4 * qd + 3] = x.w;
+        }
+        mbar_arrive(bar(B_AEMPTY + s));
+        ++a_cnt;
+        if (need_mask) {
+          const int jb = j0 + h * 32;
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const int j = jb + e;
+            if (j < n && g.leaf_of[j] == li) v[e] = 0.f;
+          }
+        }
+#pragma unroll
+        for (int qd = 0; qd < 4; ++qd) {
+          uint32_t hw[4], mw[4], lw[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float x0 = v[8 * qd + 2 * e], x1 = v[8 * qd + 2 * e + 1];
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(x0, x1);
+            const float2 hf = __bfloat1622float2(hv);
+            const float r0 = x0 - hf.x, r1 = x1 - hf.y;
+            const __nv_bfloat162 mv = __floats2bfloat162_rn(r0, r1);
+            hw[e] = *reinterpret_cast<const uint32_t*>(&hv);
+            mw[e] = *reinterpret_cast<const uint32_t*>(&mv);
+            if (NT == 3) {
+              const float2 mf = __bfloat1622float2(mv);
+              const __nv_bfloat162 lv = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+              lw[e] = *reinterpret_cast<const uint32_t*>(&lv);
+            }
+          }
+          const uint32_t off = sw128(row, h * 64 + qd * 16);
+          *reinterpret_cast<uint4*>(pbase + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(pbase + PLANE_BYTES + off) =
+              make_uint4(mw[0], mw[1], mw[2], mw[3]);
+          if (NT == 3)
+            *reinterpret_cast<uint4*>(pbase + 2 * PLANE_BYTES + off) =
+                make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+      }
+      if (!ok) break;
+      fence_proxy_async();
+      mbar_arrive(bar(B_PFULL + ps));
+      ++tl;
+    }
+  } else if (warp >= 8) {
+    // ---------------------------------------------------------- epilogue
+    const int e = tid - 256;                    // TMEM lane: row / sample column
+    const uint32_t loff = static_cast<uint32_t>((warp & 3) * 32) << 16;
+    const int n = g.n, c = g.c;
+    const int nch = (c + 31) / 32;
+    int tl = 0, folds = 0, since = 0;
+    bool fresh = true;
+    for (long long t = tb; t < te; ++t) {
+      const int p = static_cast<int>(t / ntc), J = static_cast<int>(t % ntc);
+      const bool last = (t == te - 1) || J == ntc - 1;
+      const int b = tl & 1, u = tl >> 1;
+      if (!mbar_wait(bar(B_CFULL + b), u & 1, abort_flag, g.err, 13, WAIT_LIMIT)) break;
+      fence_after();
+      float v[64];
+      tmem_ld32(tbase + loff + 128 + 64 * b, v);
+      tmem_ld32(tbase + loff + 128 + 64 * b + 32, v + 32);
+      tmem_wait_ld();
+      fence_before();
+      mbar_arrive(bar(B_CEMPTY + b));
+      if (e < c) {
+        float* dst = g.sc_part + (static_cast<size_t>(p) * n + static_cast<size_t>(J) * BN) * c + e;
+        const int jn = min(BN, n - J * BN);
+#pragma unroll
+        for (int jj = 0; jj < BN; ++jj)
+          if (jj < jn) dst[static_cast<size_t>(jj) * c] = v[jj];
+      }
+      ++since;
+      if (since == FOLD || last) {
+        if (!mbar_wait(bar(B_RFULL), folds & 1, abort_flag, g.err, 14, WAIT_LIMIT)) break;
+        fence_after();
+        for (int ch = 0; ch < nch; ++ch) {
+          float a[32], s[32], k[32];
+          tmem_ld32(tbase + loff + 32 * ch, a);
+          if (!fresh) {
+            tmem_ld32(tbase + loff + 256 + 32 * ch, s);
+            tmem_ld32(tbase + loff + 384 + 32 * ch, k);
+          }
+          tmem_wait_ld();
+          if (fresh) {
+#pragma unroll
+            for (int x = 0; x < 32; ++x) {
+              s[x] = a[x];
+              k[x] = 0.f;
+            }
+          } else {
+#pragma unroll
+            for (int x = 0; x < 32; ++x) kahan_add(s[x], k[x], a[x]);
+          }
+          tmem_st32(tbase + loff + 256 + 32 * ch, s);
+          tmem_st32(tbase + loff + 384 + 32 * ch, k);
+        }
+        tmem_wait_st();
+        fence_before();
+        mbar_arrive(bar(B_REMPTY));
+        ++folds;
+        since = 0;
+        fresh = false;
+        if (last) {
+          // FP64 partial of this panel segment, layout [p][part][c][128]
+          const long long owner0 = tile_owner(static_cast<long long>(p) * ntc, g.T, g.P);
+          const int part = static_cast<int>(q - owner0);
+          double* dst =
+              g.sr_part + ((static_cast<size_t>(p) * g.maxparts + part) * c) * BM + e;
+          for (int ch = 0; ch < nch; ++ch) {
+            float s[32], k[32];
+            tmem_ld32(tbase + loff + 256 + 32 * ch, s);
+            tmem_ld32(tbase + loff + 384 + 32 * ch, k);
+            tmem_wait_ld();
+#pragma unroll
+            for (int x = 0; x < 32; ++x) {
+              const int cc = 32 * ch + x;
+              if (cc < c)
+                dst[static_cast<size_t>(cc) * BM] =
+                    static_cast<double>(s[x]) - static_cast<double>(k[x]);
+            }
+          }
+          fresh = true;
+        }
+      }
+      ++tl;
+    }
+  }
+
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    tmem_dealloc(tbase, 512);
+  }
+}
+
+// Sc[j, c0 + cc] = sum over panels of Sc_part[p][j][cc] (FP64, panel order);
+// Sr[i, c0 + cc] = sum over segments of Sr_part[p][part][cc][i % 128].
+__global__ void sample_tc_reduce_kernel(const float* __restrict__ sc_part,
+                                        const double* __restrict__ sr_part, int n, int c,
+                                        int npanel, int ntc, long long T, int P, int maxparts,
+                                        float* Sr, float* Sc, long long lds) {
+  const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long nc = static_cast<long long>(n) * c;
+  if (idx < nc) {
+    const int j = static_cast<int>(idx / c), cc = static_cast<int>(idx % c);
+    const float* src = sc_part + static_cast<size_t>(j) * c + cc;
+    const size_t stride = static_cast<size_t>(n) * c;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int p = 0;
+    for (; p + 4 <= npanel; p += 4) {
+      s0 += src[stride * p];
+      s1 += src[stride * (p + 1)];
+      s2 += src[stride * (p + 2)];
+      s3 += src[stride * (p + 3)];
+    }
+    for (; p < npanel; ++p) s0 += src[stride * p];
+    Sc[static_cast<size_t>(j) * lds + cc] = static_cast<float>((s0 + s1) + (s2 + s3));
+  } else if (idx < 2 * nc) {
+    const long long r = idx - nc;
+    const int i = static_cast<int>(r / c), cc = static_cast<int>(r % c);
+    const int p = i / BM, row = i % BM;
+    const long long q0 = ((static_cast<long long>(p) * ntc + 1) * P - 1) / T;
+    const long long q1 = ((static_cast<long long>(p + 1) * ntc) * P - 1) / T;
+    double s = 0.0;
+    for (long long part = 0; part <= q1 - q0; ++part)
+      s += sr_part[((static_cast<size_t>(p) * maxparts + part) * c + cc) * BM + row];
+    Sr[static_cast<size_t>(i) * lds + cc] = static_cast<float>(s);
+  }
+}
+
+// R16[i, cc] = R[i, c0 + cc] (bfloat16-exact) for cc < c, zero up to cpad
+__global__ void r_to_bf16_kernel(const float* __restrict__ R, long long ldr, int n, int c,
+                                 int cpad, __nv_bfloat16* R16) {
+  const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= static_cast<long long>(n) * cpad) return;
+  const int i = static_cast<int>(idx / cpad), cc = static_cast<int>(idx % cpad);
+  R16[idx] = __float2bfloat16_rn(cc < c ? R[static_cast<size_t>(i) * ldr + cc] : 0.f);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+Err make_map(CUtensorMap* m, CUtensorMapDataType dt, const void* base, uint64_t cols,
+             uint64_t rows, uint64_t pitch_bytes, uint32_t bx, uint32_t by) {
+  auto fn = encode_fn();
+  if (!fn) return fail(HSS_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {pitch_bytes};
+  cuuint32_t box[2] = {bx, by};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, dt, 2, const_cast<void*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(HSS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  return ok();
+}
+
+struct DevInfo {
+  int sms = 0;
+  bool attr3 = false, attr2 = false;
+};
+
+DevInfo& dev_info(int dev) {
+  static std::mutex mu;
+  static DevInfo info[64];
+  std::lock_guard<std::mutex> lk(mu);
+  DevInfo& d = info[dev & 63];
+  if (d.sms == 0) cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+  return d;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+struct TcPlan {
+  int npanel, ntc, P, maxparts;
+  long long T;
+};
+
+TcPlan plan(int64_t n, int sms) {
+  TcPlan pl;
+  pl.npanel = static_cast<int>((n + BM - 1) / BM);
+  pl.ntc = static_cast<int>((n + BN - 1) / BN);
+  pl.T = static_cast<long long>(pl.npanel) * pl.ntc;
+  pl.P = static_cast<int>(pl.T < sms ? pl.T : sms);
+  const long long per = pl.T / pl.P;   // fewest tiles a CTA gets
+  pl.maxparts = static_cast<int>((pl.ntc + per - 1) / per) + 1;
+  return pl;
+}
+
+}  // namespace
+
+size_t sample_tc_scratch_bytes(int64_t n, int64_t ncols, int sms) {
+  const TcPlan pl = plan(n, sms);
+  const int64_t c = ncols < CMAX ? ncols : CMAX;
+  const int64_t cpad = (c + 63) / 64 * 64;
+  return align256(static_cast<size_t>(n) * cpad * 2) +
+         align256(static_cast<size_t>(pl.npanel) * n * c * 4) +
+         align256(static_cast<size_t>(pl.npanel) * pl.maxparts * c * BM * 8) + 256;
+}
+
+bool sample_tc_supported(const float* A, int64_t n, int64_t lda, int mode) {
+  return (mode == HSS_SAMPLE_BF16X2 || mode == HSS_SAMPLE_BF16X3) && n >= 1 &&
+         n <= (int64_t)1 << 30 && lda % 4 == 0 &&
+         (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+}
+
+Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int64_t ldr,
+                     int64_t c0, int64_t ncols, float* Sr, float* Sc, int64_t lds,
+                     const int32_t* leaf_of, int mode, SampleScratch* scratch, cudaStream_t s) {
+  int dev = 0;
+  HSS_CUDA_TRY(cudaGetDevice(&dev));
+  DevInfo& di = dev_info(dev);
+  const TcPlan pl = plan(n, di.sms);
+  const size_t need = sample_tc_scratch_bytes(n, ncols, di.sms);
+  if (scratch->bytes < need) {
+    dfree(scratch->part, s);
+    scratch->part = nullptr;
+    scratch->bytes = 0;
+    HSS_TRY(dalloc(&scratch->part, need, s));
+    scratch->bytes = need;
+  }
+  const bool three = mode == HSS_SAMPLE_BF16X3;
+  const uint32_t smem = three ? Layout<3>::alloc : Layout<2>::alloc;
+  if (three && !di.attr3) {
+    HSS_CUDA_TRY(cudaFuncSetAttribute(sample_tc_kernel<3>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    di.attr3 = true;
+  }
+  if (!three && !di.attr2) {
+    HSS_CUDA_TRY(cudaFuncSetAttribute(sample_tc_kernel<2>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    di.attr2 = true;
+  }
+  // sweeps of at most 128 columns, widths balanced
+  const int64_t nsw = (ncols + CMAX - 1) / CMAX;
+  int64_t done = 0;
+  for (int64_t w = 0; w < nsw; ++w) {
+    const int c = static_cast<int>((ncols - done) / (nsw - w));
+    const int cpad = (c + 63) / 64 * 64;
+    uint8_t* base = static_cast<uint8_t*>(scratch->part);
+    __nv_bfloat16* R16 = reinterpret_cast<__nv_bfloat16*>(base);
+    base += align256(static_cast<size_t>(n) * cpad * 2);
+    float* scp = reinterpret_cast<float*>(base);
+    base += align256(static_cast<size_t>(pl.npanel) * n * c * 4);
+    double* srp = reinterpret_cast<double*>(base);
+    base += align256(static_cast<size_t>(pl.npanel) * pl.maxparts * c * BM * 8);
+    int* err = reinterpret_cast<int*>(base);
+
+    const long long nconv = static_cast<long long>(n) * cpad;
+    r_to_bf16_kernel<<<static_cast<unsigned>((nconv + 255) / 256), 256, 0, s>>>(
+        R + c0 + done, ldr, static_cast<int>(n), c, cpad, R16);
+    HSS_TRY(check_launch("r_to_bf16_kernel"));
+
+    CUtensorMap tmA, tmRJ, tmRI;
+    HSS_TRY(make_map(&tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, n, n, lda * 4, 32, BM));
+    HSS_TRY(make_map(&tmRJ, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, R16, cpad, n, cpad * 2, 64, BN));
+    HSS_TRY(make_map(&tmRI, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, R16, cpad, n, cpad * 2, 64, BM));
+    TcArgs g;
+    g.n = static_cast<int>(n);
+    g.c = c;
+    g.ncb = cpad / 64;
+    g.nr = (c + 15) / 16 * 16;
+    g.ntc = pl.ntc;
+    g.npanel = pl.npanel;
+    g.T = pl.T;
+    g.P = pl.P;
+    g.maxparts = pl.maxparts;
+    g.leaf_of = leaf_of;
+    g.sc_part = scp;
+    g.sr_part = srp;
+    g.err = err;
+    HSS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+    if (three)
+      sample_tc_kernel<3><<<pl.P, THREADS, smem, s>>>(tmA, tmRJ, tmRI, g);
+    else
+      sample_tc_kernel<2><<<pl.P, THREADS, smem, s>>>(tmA, tmRJ, tmRI, g);
+    HSS_TRY(check_launch("sample_tc_kernel"));
+    const long long nred = 2ll * n * c;
+    sample_tc_reduce_kernel<<<static_cast<unsigned>((nred + 255) / 256), 256, 0, s>>>(
+        scp, srp, static_cast<int>(n), c, pl.npanel, pl.ntc, pl.T, pl.P, pl.maxparts,
+        Sr + c0 + done, Sc + c0 + done, lds);
+    HSS_TRY(check_launch("sample_tc_reduce_kernel"));
+    int herr = 0;
+    HSS_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HSS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (herr) return fail(HSS_ERR_TIMEOUT, "sample_tc_kernel: a pipeline wait timed out");
+    done += c;
+  }
+  return ok();
+}
+
+}  // namespace hss

@@ -100,12 +100,24 @@ MODE_REL = {"tf32": 2.0 ** -11, "bf16x2": 2.0 ** -16, "bf16x3": 2.0 ** -23}
 
 
 @pytest.mark.parametrize("mode", ["tf32", "bf16x2", "bf16x3"])
-@pytest.mark.parametrize("n,leaf,c0,c1", [(1000, 125, 0, 64), (1283, 100, 33, 161), (517, 64, 0, 128)])
-def test_tensor_core_sampling_matches_oracle(P, mode, n, leaf, c0, c1):
+@pytest.mark.parametrize("n,leaf,c0,c1,pad", [
+    (1000, 125, 0, 64, 0), (1283, 100, 33, 161, 0), (517, 64, 0, 128, 0),
+    # rows 16-byte aligned: the split modes run on tcgen05 (several column
+    # tiles and panels with ragged tails, several sweeps of <= 128 columns,
+    # panels split between CTAs, tiny and strided inputs)
+    (1284, 100, 33, 161, 0), (516, 64, 0, 128, 0), (2052, 200, 0, 200, 0), (12, 4, 0, 16, 0),
+    (300, 40, 5, 37, 0), (4100, 300, 0, 96, 0), (777, 90, 0, 80, 5)])
+def test_tensor_core_sampling_matches_oracle(P, mode, n, leaf, c0, c1, pad):
     rng = np.random.default_rng(n + len(mode))
     A = rng.standard_normal((n, n)) * np.exp(rng.standard_normal((n, n)))   # wide magnitudes
     A[: n // 3] *= 3.0
-    At = torch.tensor(A, dtype=torch.float32, device=DEV)
+    if pad:    # a view with a leading dimension n + pad rounded up to a multiple of 4
+        ld = (n + pad + 3) // 4 * 4
+        big = torch.zeros((n, ld), dtype=torch.float32, device=DEV)
+        big[:, :n] = torch.tensor(A, dtype=torch.float32, device=DEV)
+        At = big[:, :n]
+    else:
+        At = torch.tensor(A, dtype=torch.float32, device=DEV)
     A64 = At.cpu().numpy().astype(np.float64)
     R = torch.zeros((n, c1), dtype=torch.float32, device=DEV)
     P.hss_random_gaussian(5, n, 0, c1, R)

@@ -244,3 +244,39 @@ def laplacian_schur(k: int, dtype=np.float32, device="cpu"):
     PP = (phi[:, None, :] * phi[None, :, :]).reshape(k * k, k)
     S = (PP @ M).reshape(k, k, k, k).permute(0, 2, 1, 3).reshape(k * k, k * k)
     return S.to(_tdtype(dtype)).contiguous()
+
+
+# --------------------------------------------------- mixed batch of matrices
+def mixed_batch_specs(count: int, seed: int, n_range=(1000, 8000)):
+    """Specs of `count` independent matrices for batched compression: n uniform
+    in n_range, half Toeplitz a_ij = 1/(1+|i-j|) (a_ii = 10), half Gaussian
+    kernel (h uniform in [0.1, 0.4], lambda = 1, points uniform in the unit
+    cube in RCB order).  Per-family settings: Toeplitz rtol 1e-6, d0/step
+    64/32; Gaussian rtol 1e-4, 128/64; leaf 128 below n = 4000, else 256."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        leaf = 128 if n < 4000 else 256
+        if rng.random() < 0.5:
+            out.append(dict(family="toeplitz_inv_distance", n=n, leaf=leaf, rtol=1e-6,
+                            d0=64, step=32))
+        else:
+            out.append(dict(family="gaussian_kernel", n=n, leaf=leaf, rtol=1e-4, d0=128,
+                            step=64, h=float(rng.uniform(0.1, 0.4)), lam=1.0,
+                            seed=int(rng.integers(1 << 31))))
+    return out
+
+
+def build_matrix(spec: dict, dtype=np.float32, device="cpu"):
+    """Dense matrix of one spec from mixed_batch_specs (or of the same keys)."""
+    fam = spec["family"]
+    if fam == "toeplitz_inv_distance":
+        return toeplitz_inv_distance(spec["n"], dtype=dtype, device=device).contiguous()
+    if fam == "gaussian_kernel":
+        pts = points_unit_cube(spec["n"], spec["seed"])
+        pts = pts[rcb_order(pts, spec["leaf"])]
+        return gaussian_kernel(pts, spec["h"], spec["lam"], dtype=dtype, device=device)
+    if fam == "laplacian_schur":
+        return laplacian_schur(spec["k"], dtype=dtype, device=device)
+    raise ValueError(fam)
