@@ -15,20 +15,27 @@
 // for the column product.  R is bfloat16-exact (its Gaussian entries are
 // rounded to bfloat16 when drawn), so it needs no split.
 //
-// Pipeline (warp-specialised, mbarrier hand-offs, 384 threads):
-//   warp 0     TMA producer: FP32 half-tiles of A (128 x 32, 128-byte
-//              swizzle) into a 4-stage ring, R_J (64 rows) and R_p (128
-//              rows) as bfloat16 boxes;
-//   warps 4-7  converters: one row each; apply the leaf mask, split into
-//              the bfloat16 planes (double-buffered, swizzled operand layout);
-//   warp 1     MMA issuer (one thread): tcgen05.mma into TMEM;
-//   warps 8-11 epilogue: TMEM -> registers; the column product of each tile
-//              goes to a partial slab Sc_part[p][j][c] (summed over panels in
-//              FP64 afterwards); the row product is folded every two tiles
-//              into a Kahan-compensated FP32 sum kept in TMEM, and written at
-//              the end of each panel segment as an FP64 partial.
-// TMEM columns: [0,128) row accumulator, [128,256) two column accumulators,
-// [256,384) Kahan sum, [384,512) Kahan compensation.
+// Pipeline (warp-specialised, mbarrier hand-offs, 512 threads):
+//   warp 0       TMA producer: FP32 half-tiles of A (128 x 32, 128-byte
+//                swizzle) into a 4-stage ring; R_J (64 rows) per tile and
+//                R_p (128 rows) per panel segment, bfloat16;
+//   warps 4-7    converters: one row each; apply the leaf mask (the index
+//                range of the row's leaf), split into the bfloat16 planes
+//                (double-buffered, swizzled operand layout);
+//   warp 1       MMA issuer (one thread): tcgen05.mma into TMEM;
+//   warps 8-11   column drain: the column product of each tile (TMEM, double
+//                buffered) to a partial slab Sc_part[p][j][c];
+//   warps 12-15  row fold: the row accumulator (TMEM, double buffered, one
+//                buffer per group of FOLD tiles) is added into a running FP32
+//                sum in TMEM; the sum is flushed to a row slab at the end of
+//                every flush group of at most 16 tiles and of every segment.
+// TMEM columns: [0,256) two row accumulators, [256,384) two column
+// accumulators, [384,512) the running row sum.
+//
+// Numerics: FP32 accumulation runs over at most FOLD tiles in the tensor core
+// and one flush group in the running sum; the slabs are summed in the reduce
+// kernel with compensated FP32 (Neumaier) summation in a fixed order, so the
+// result is deterministic and independent of what else runs on the GPU.
 //
 // Every wait is bounded: on a timeout the CTA records an error code, stops,
 // waits (bounded) for its own copies and MMAs in flight, frees its TMEM and
@@ -43,11 +50,6 @@
 
 namespace hss {
 
-Err launch_sample_mma(const float* A, int64_t n, int64_t lda, const float* R, int64_t ldr,
-                      int64_t c0, int64_t ncols, float* Sr, float* Sc, int64_t lds,
-                      const int32_t* leaf_of, int mode, float* P, cudaStream_t s);
-size_t sample_scratch_bytes(int64_t n, int64_t ncols, int mode, bool f64);
-
 namespace {
 
 using namespace tc;
@@ -56,14 +58,17 @@ constexpr int BM = 128;          // panel rows
 constexpr int BN = 64;           // column tile of A
 constexpr int CMAX = 128;        // sample columns per sweep
 constexpr int ASTAGES = 4;       // FP32 half-tile ring
-constexpr int FOLD = 2;          // tiles between Kahan folds of the row product
-constexpr int THREADS = 384;
+constexpr int FOLD = 2;          // tiles per row accumulator buffer
+constexpr int FLUSH_MAX = 16;    // tiles per flush group of the running row sum, at most
+constexpr int THREADS = 512;
 constexpr long long WAIT_LIMIT = 1ll << 32;   // clock cycles (about 2 s)
 
 constexpr uint32_t A_HALF_BYTES = BM * 32 * 4;   // 16 KB
 constexpr uint32_t PLANE_BYTES = BM * BN * 2;    // 16 KB
 constexpr uint32_t RJ_BYTES = BN * CMAX * 2;     // 16 KB (two 8 KB boxes)
 constexpr uint32_t RI_BYTES = BM * CMAX * 2;     // 32 KB (two 16 KB boxes)
+// TMEM column map
+constexpr uint32_t T_ROW = 0, T_COL = 256, T_SUM = 384;
 
 template <int NT>
 struct Layout {
@@ -78,9 +83,10 @@ struct Layout {
 
 // barrier slots
 enum {
-  B_AFULL = 0, B_AEMPTY = 4, B_PFULL = 8, B_PEMPTY = 10, B_RJFULL = 12, B_RJEMPTY = 14,
-  B_RIFULL = 16, B_RIEMPTY = 17, B_CFULL = 18, B_CEMPTY = 20, B_RFULL = 22, B_REMPTY = 23,
-  B_DRAIN = 24, B_COUNT = 25
+  B_AFULL = 0, B_AEMPTY = ASTAGES, B_PFULL = 2 * ASTAGES, B_PEMPTY = B_PFULL + 2,
+  B_RJFULL = B_PEMPTY + 2, B_RJEMPTY = B_RJFULL + 2, B_RIFULL = B_RJEMPTY + 2,
+  B_RIEMPTY = B_RIFULL + 1, B_CFULL = B_RIEMPTY + 1, B_CEMPTY = B_CFULL + 2,
+  B_RFULL = B_CEMPTY + 2, B_REMPTY = B_RFULL + 2, B_DRAIN = B_REMPTY + 2, B_COUNT = B_DRAIN + 1
 };
 
 struct TcArgs {
@@ -92,26 +98,22 @@ struct TcArgs {
   int npanel;
   long long T;    // tiles in total
   int P;          // CTAs
-  int maxparts;   // panel segments per panel, at most
-  const int32_t* leaf_of;
+  int gs;         // tiles per flush group
+  int ngroups;    // flush groups per panel
+  const int32_t* leaf_of;    // leaf id of each index (null: no mask)
+  const int32_t* leaf_lo;    // first index of each leaf id
+  const int32_t* leaf_hi;    // one past the last index of each leaf id
   float* sc_part;    // [npanel][n][c]
-  double* sr_part;   // [npanel][maxparts][c][128]
+  float* sr_part;    // [npanel][ngroups][2][c][128]
   int* err;
 };
 
-__device__ __forceinline__ long long tile_begin(long long q, long long T, long long P) {
+__host__ __device__ __forceinline__ long long tile_begin(long long q, long long T, long long P) {
   return q * T / P;
 }
 // the CTA whose tile range holds tile t
-__device__ __forceinline__ long long tile_owner(long long t, long long T, long long P) {
+__host__ __device__ __forceinline__ long long tile_owner(long long t, long long T, long long P) {
   return ((t + 1) * P - 1) / T;
-}
-
-__device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
-  const float y = x - comp;
-  const float t = sum + y;
-  comp = (t - sum) - y;
-  sum = t;
 }
 
 template <int NT>
@@ -141,11 +143,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(bar(B_RJEMPTY + i), 1);
       mbar_init(bar(B_CFULL + i), 1);
       mbar_init(bar(B_CEMPTY + i), BM);
+      mbar_init(bar(B_RFULL + i), 1);
+      mbar_init(bar(B_REMPTY + i), BM);
     }
     mbar_init(bar(B_RIFULL), 1);
     mbar_init(bar(B_RIEMPTY), 1);
-    mbar_init(bar(B_RFULL), 1);
-    mbar_init(bar(B_REMPTY), BM);
     mbar_init(bar(B_DRAIN), 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -164,22 +166,23 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const long long q = blockIdx.x;
   const long long tb = tile_begin(q, g.T, g.P), te = tile_begin(q + 1, g.T, g.P);
-  const int ntc = g.ntc;
+  const int ntc = g.ntc, gs = g.gs;
 
   if (warp == 0) {
     // ------------------------------------------------------ TMA producer
     if (lane == 0) {
-      int a_cnt = 0, tl = 0, seg = 0, ri_uses = 0;
+      int a_cnt = 0, tl = 0, ri_cnt = 0;
       for (long long t = tb; t < te; ++t) {
         const int p = static_cast<int>(t / ntc), J = static_cast<int>(t % ntc);
-        const bool first = (t == tb) || J == 0, last = (t == te - 1) || J == ntc - 1;
+        const bool first = (t == tb) || J == 0;
         if (first) {
-          if (!mbar_wait(bar(B_RIEMPTY), (seg & 1) ^ 1, abort_flag, g.err, 1, WAIT_LIMIT)) break;
+          if (!mbar_wait(bar(B_RIEMPTY), (ri_cnt & 1) ^ 1, abort_flag, g.err, 1, WAIT_LIMIT))
+            break;
           mbar_expect_tx(bar(B_RIFULL), g.ncb * (RI_BYTES / 2));
           for (int cb = 0; cb < g.ncb; ++cb)
             tma_load_2d(su32(sm + L::ri + cb * (RI_BYTES / 2)), &tmRI, cb * 64, p * BM,
                         bar(B_RIFULL));
-          ++ri_uses;
+          ++ri_cnt;
         }
         bool ok = true;
         for (int h = 0; h < 2 && ok; ++h) {
@@ -199,7 +202,6 @@ __global__ void __launch_bounds__(THREADS, 1)
           tma_load_2d(su32(sm + L::rj + r * RJ_BYTES + cb * (RJ_BYTES / 2)), &tmRJ, cb * 64,
                       J * BN, bar(B_RJFULL + r));
         ++tl;
-        if (last) ++seg;
       }
       if (*abort_flag) {
         // let every copy this thread issued land before the CTA exits
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int uses = (tl - r + 1) / 2;
           if (uses > 0) mbar_wait(bar(B_RJFULL + r), (uses - 1) & 1, &never, g.err, 9, WAIT_LIMIT);
         }
-        if (ri_uses) mbar_wait(bar(B_RIFULL), (ri_uses - 1) & 1, &never, g.err, 9, WAIT_LIMIT);
+        if (ri_cnt > 0) mbar_wait(bar(B_RIFULL), (ri_cnt - 1) & 1, &never, g.err, 9, WAIT_LIMIT);
       }
     }
   } else if (warp == 1) {
@@ -220,46 +222,54 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       const uint32_t idr = idesc_bf16(BM, g.nr, 0, 1);    // planes K-major, R_J MN-major
       const uint32_t idc = idesc_bf16(BM, BN, 1, 1);      // R_p^T MN-major, planes MN-major
-      const uint32_t pl0 = su32(sm + L::planes), rj0 = su32(sm + L::rj), ri0 = su32(sm + L::ri);
-      int tl = 0, seg = 0, folds = 0, since = 0;
+      // descriptors of stage 0; other stages and K steps add (offset >> 4)
+      // to the start-address field
+      const uint64_t a_row = sdesc(su32(sm + L::planes), 16, 1024);        // plane, K-major
+      const uint64_t b_col = sdesc(su32(sm + L::planes), 8192, 1024);      // plane, MN-major
+      const uint64_t b_row = sdesc(su32(sm + L::rj), RJ_BYTES / 2, 1024);  // R_J, MN-major
+      const uint64_t a_col = sdesc(su32(sm + L::ri), RI_BYTES / 2, 1024);  // R_p, MN-major
+      int tl = 0, seg = 0, fg = 0, since = 0;
       for (long long t = tb; t < te; ++t) {
         const int J = static_cast<int>(t % ntc);
         const bool first = (t == tb) || J == 0, last = (t == te - 1) || J == ntc - 1;
+        const bool gend = last || (J % gs) == gs - 1;
         if (first && !mbar_wait(bar(B_RIFULL), seg & 1, abort_flag, g.err, 4, WAIT_LIMIT)) break;
         const int ps = tl & 1, u = tl >> 1;
         if (!mbar_wait(bar(B_PFULL + ps), u & 1, abort_flag, g.err, 5, WAIT_LIMIT)) break;
         if (!mbar_wait(bar(B_RJFULL + ps), u & 1, abort_flag, g.err, 6, WAIT_LIMIT)) break;
         if (!mbar_wait(bar(B_CEMPTY + ps), (u & 1) ^ 1, abort_flag, g.err, 7, WAIT_LIMIT)) break;
-        if (since == 0 && folds > 0 &&
-            !mbar_wait(bar(B_REMPTY), (folds - 1) & 1, abort_flag, g.err, 8, WAIT_LIMIT))
+        const int rb = fg & 1;
+        if (since == 0 &&
+            !mbar_wait(bar(B_REMPTY + rb), ((fg >> 1) & 1) ^ 1, abort_flag, g.err, 8, WAIT_LIMIT))
           break;
         fence_after();
-        const uint32_t pbase = pl0 + ps * NT * PLANE_BYTES;
-        const uint32_t rjb = rj0 + ps * RJ_BYTES;
+        const uint64_t poff = (ps * NT * PLANE_BYTES) >> 4;
+        const uint64_t roff = (ps * RJ_BYTES) >> 4;
+        const uint32_t dr = tbase + T_ROW + 128 * rb;
 #pragma unroll
         for (int term = 0; term < NT; ++term) {
 #pragma unroll
           for (int k = 0; k < BN / 16; ++k)
-            mma_bf16(tbase, sdesc(pbase + term * PLANE_BYTES + 32 * k, 16, 1024),
-                     sdesc(rjb + 2048 * k, RJ_BYTES / 2, 1024), idr,
+            mma_bf16(dr, a_row + poff + ((term * PLANE_BYTES + 32 * k) >> 4),
+                     b_row + roff + ((2048 * k) >> 4), idr,
                      (since > 0 || term > 0 || k > 0) ? 1u : 0u);
         }
-        const uint32_t dc = tbase + 128 + 64 * ps;
+        const uint32_t dc = tbase + T_COL + 64 * ps;
 #pragma unroll
         for (int term = 0; term < NT; ++term) {
 #pragma unroll
           for (int k = 0; k < BM / 16; ++k)
-            mma_bf16(dc, sdesc(ri0 + 2048 * k, RI_BYTES / 2, 1024),
-                     sdesc(pbase + term * PLANE_BYTES + 2048 * k, 8192, 1024), idc,
+            mma_bf16(dc, a_col + ((2048 * k) >> 4),
+                     b_col + poff + ((term * PLANE_BYTES + 2048 * k) >> 4), idc,
                      (term > 0 || k > 0) ? 1u : 0u);
         }
         mma_commit(bar(B_PEMPTY + ps));
         mma_commit(bar(B_RJEMPTY + ps));
         mma_commit(bar(B_CFULL + ps));
         ++since;
-        if (since == FOLD || last) {
-          mma_commit(bar(B_RFULL));
-          ++folds;
+        if (since == FOLD || gend) {
+          mma_commit(bar(B_RFULL + rb));
+          ++fg;
           since = 0;
         }
         if (last) {
@@ -277,18 +287,23 @@ __global__ void __launch_bounds__(THREADS, 1)
     // -------------------------------------------------------- converters
     const int row = tid - 128;
     int a_cnt = 0, tl = 0;
+    int mlo = 0, mhi = 0;   // the leaf of this thread's row: columns [mlo, mhi) are masked
     for (long long t = tb; t < te; ++t) {
       const int p = static_cast<int>(t / ntc), J = static_cast<int>(t % ntc);
       const int ps = tl & 1, u = tl >> 1;
-      if (!mbar_wait(bar(B_PEMPTY + ps), (u & 1) ^ 1, abort_flag, g.err, 11, WAIT_LIMIT)) break;
-      // leaf mask: only tiles whose row and column ranges share a leaf
       const int n = g.n;
-      const int i0 = p * BM, j0 = J * BN;
-      const int li_lo = g.leaf_of[min(i0, n - 1)], li_hi = g.leaf_of[min(i0 + BM - 1, n - 1)];
-      const int lj_lo = g.leaf_of[min(j0, n - 1)], lj_hi = g.leaf_of[min(j0 + BN - 1, n - 1)];
-      const bool need_mask = !(lj_hi < li_lo || lj_lo > li_hi);
-      const int i = i0 + row;
-      const int li = (i < n) ? g.leaf_of[i] : -1;
+      if (t == tb || J == 0) {
+        const int i = p * BM + row;
+        mlo = mhi = 0;
+        if (g.leaf_of != nullptr && i < n) {
+          const int id = g.leaf_of[i];
+          mlo = g.leaf_lo[id];
+          mhi = g.leaf_hi[id];
+        }
+      }
+      if (!mbar_wait(bar(B_PEMPTY + ps), (u & 1) ^ 1, abort_flag, g.err, 11, WAIT_LIMIT)) break;
+      const int j0 = J * BN;
+      const bool need_mask = mlo < j0 + BN && mhi > j0;
       uint8_t* pbase = sm + L::planes + ps * NT * PLANE_BYTES;
       bool ok = true;
       for (int h = 0; h < 2; ++h) {
@@ -314,7 +329,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
             const int j = jb + e;
-            if (j < n && g.leaf_of[j] == li) v[e] = 0.f;
+            if (j >= mlo && j < mhi) v[e] = 0.f;
           }
         }
 #pragma unroll
@@ -349,23 +364,20 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_arrive(bar(B_PFULL + ps));
       ++tl;
     }
-  } else if (warp >= 8) {
-    // ---------------------------------------------------------- epilogue
-    const int e = tid - 256;                    // TMEM lane: row / sample column
+  } else if (warp >= 8 && warp < 12) {
+    // ------------------------------------------------------ column drain
+    const int e = tid - 256;                    // TMEM lane: sample column
     const uint32_t loff = static_cast<uint32_t>((warp & 3) * 32) << 16;
     const int n = g.n, c = g.c;
-    const int nch = (c + 31) / 32;
-    int tl = 0, folds = 0, since = 0;
-    bool fresh = true;
+    int tl = 0;
     for (long long t = tb; t < te; ++t) {
       const int p = static_cast<int>(t / ntc), J = static_cast<int>(t % ntc);
-      const bool last = (t == te - 1) || J == ntc - 1;
       const int b = tl & 1, u = tl >> 1;
       if (!mbar_wait(bar(B_CFULL + b), u & 1, abort_flag, g.err, 13, WAIT_LIMIT)) break;
       fence_after();
       float v[64];
-      tmem_ld32(tbase + loff + 128 + 64 * b, v);
-      tmem_ld32(tbase + loff + 128 + 64 * b + 32, v + 32);
+      tmem_ld32(tbase + loff + T_COL + 64 * b, v);
+      tmem_ld32(tbase + loff + T_COL + 64 * b + 32, v + 32);
       tmem_wait_ld();
       fence_before();
       mbar_arrive(bar(B_CEMPTY + b));
@@ -376,60 +388,61 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int jj = 0; jj < BN; ++jj)
           if (jj < jn) dst[static_cast<size_t>(jj) * c] = v[jj];
       }
+      ++tl;
+    }
+  } else if (warp >= 12) {
+    // --------------------------------------------------------- row fold
+    const int e = tid - 384;                    // TMEM lane: panel row
+    const uint32_t loff = static_cast<uint32_t>((warp & 3) * 32) << 16;
+    const int c = g.c;
+    const int nch = (c + 31) / 32;
+    int fg = 0, since = 0, jfirst = -1;
+    bool fresh = true;
+    for (long long t = tb; t < te; ++t) {
+      const int p = static_cast<int>(t / ntc), J = static_cast<int>(t % ntc);
+      const bool last = (t == te - 1) || J == ntc - 1;
+      const bool gend = last || (J % gs) == gs - 1;
+      if (jfirst < 0) jfirst = J;
       ++since;
-      if (since == FOLD || last) {
-        if (!mbar_wait(bar(B_RFULL), folds & 1, abort_flag, g.err, 14, WAIT_LIMIT)) break;
-        fence_after();
-        for (int ch = 0; ch < nch; ++ch) {
-          float a[32], s[32], k[32];
-          tmem_ld32(tbase + loff + 32 * ch, a);
-          if (!fresh) {
-            tmem_ld32(tbase + loff + 256 + 32 * ch, s);
-            tmem_ld32(tbase + loff + 384 + 32 * ch, k);
-          }
-          tmem_wait_ld();
-          if (fresh) {
+      if (!(since == FOLD || gend)) continue;
+      since = 0;
+      const int rb = fg & 1;
+      if (!mbar_wait(bar(B_RFULL + rb), (fg >> 1) & 1, abort_flag, g.err, 14, WAIT_LIMIT)) break;
+      fence_after();
+      for (int ch = 0; ch < nch; ++ch) {
+        float a[32], s[32];
+        tmem_ld32(tbase + loff + T_ROW + 128 * rb + 32 * ch, a);
+        if (!fresh) tmem_ld32(tbase + loff + T_SUM + 32 * ch, s);
+        tmem_wait_ld();
+        if (fresh) {
 #pragma unroll
-            for (int x = 0; x < 32; ++x) {
-              s[x] = a[x];
-              k[x] = 0.f;
-            }
-          } else {
+          for (int x = 0; x < 32; ++x) s[x] = a[x];
+        } else {
 #pragma unroll
-            for (int x = 0; x < 32; ++x) kahan_add(s[x], k[x], a[x]);
-          }
-          tmem_st32(tbase + loff + 256 + 32 * ch, s);
-          tmem_st32(tbase + loff + 384 + 32 * ch, k);
+          for (int x = 0; x < 32; ++x) s[x] += a[x];
         }
-        tmem_wait_st();
-        fence_before();
-        mbar_arrive(bar(B_REMPTY));
-        ++folds;
-        since = 0;
-        fresh = false;
-        if (last) {
-          // FP64 partial of this panel segment, layout [p][part][c][128]
-          const long long owner0 = tile_owner(static_cast<long long>(p) * ntc, g.T, g.P);
-          const int part = static_cast<int>(q - owner0);
-          double* dst =
-              g.sr_part + ((static_cast<size_t>(p) * g.maxparts + part) * c) * BM + e;
-          for (int ch = 0; ch < nch; ++ch) {
-            float s[32], k[32];
-            tmem_ld32(tbase + loff + 256 + 32 * ch, s);
-            tmem_ld32(tbase + loff + 384 + 32 * ch, k);
-            tmem_wait_ld();
+        if (gend) {
+          // flush: slot (p, group, side), side 1 when the chunk starts inside
+          // the group (a CTA range began there)
+          const int grp = J / gs;
+          const int side = (jfirst % gs) != 0 ? 1 : 0;
+          float* dst = g.sr_part +
+                       ((((static_cast<size_t>(p) * g.ngroups + grp) * 2 + side) * c) * BM) + e;
 #pragma unroll
-            for (int x = 0; x < 32; ++x) {
-              const int cc = 32 * ch + x;
-              if (cc < c)
-                dst[static_cast<size_t>(cc) * BM] =
-                    static_cast<double>(s[x]) - static_cast<double>(k[x]);
-            }
+          for (int x = 0; x < 32; ++x) {
+            const int cc = 32 * ch + x;
+            if (cc < c) dst[static_cast<size_t>(cc) * BM] = s[x];
           }
-          fresh = true;
+        } else {
+          tmem_st32(tbase + loff + T_SUM + 32 * ch, s);
         }
       }
-      ++tl;
+      tmem_wait_st();
+      fence_before();
+      mbar_arrive(bar(B_REMPTY + rb));
+      ++fg;
+      fresh = gend;
+      if (gend) jfirst = -1;
     }
   }
 
@@ -441,39 +454,84 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
-// Sc[j, c0 + cc] = sum over panels of Sc_part[p][j][cc] (FP64, panel order);
-// Sr[i, c0 + cc] = sum over segments of Sr_part[p][part][cc][i % 128].
+// Neumaier-compensated FP32 summation: s + c carries the sum to about one
+// rounding of the exact value (FP64 throughput on this part is far below
+// what streaming the slab needs)
+__device__ __forceinline__ void neumaier_add(float& s, float& c, float x) {
+  const float t = s + x;
+  c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+  s = t;
+}
+
+// Sc[j, c0 + cc] = sum over panels of Sc_part[p][j][cc] (panel order, one
+// thread per V consecutive columns cc);
+// Sr[i, c0 + cc] = sum over the flush slots of row i's panel, in order.
+template <int V>
 __global__ void sample_tc_reduce_kernel(const float* __restrict__ sc_part,
-                                        const double* __restrict__ sr_part, int n, int c,
-                                        int npanel, int ntc, long long T, int P, int maxparts,
-                                        float* Sr, float* Sc, long long lds) {
+                                        const float* __restrict__ sr_part, int n, int c,
+                                        int npanel, int ntc, long long T, int P, int gs,
+                                        int ngroups, float* Sr, float* Sc, long long lds) {
   const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const long long nc = static_cast<long long>(n) * c;
-  if (idx < nc) {
-    const int j = static_cast<int>(idx / c), cc = static_cast<int>(idx % c);
+  const int cv = c / V;
+  const long long ncv = static_cast<long long>(n) * cv;
+  if (idx < ncv) {
+    const int j = static_cast<int>(idx / cv), cc = static_cast<int>(idx % cv) * V;
     const float* src = sc_part + static_cast<size_t>(j) * c + cc;
     const size_t stride = static_cast<size_t>(n) * c;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    float s[V], k[V];
+#pragma unroll
+    for (int x = 0; x < V; ++x) s[x] = k[x] = 0.f;
     int p = 0;
-    for (; p + 4 <= npanel; p += 4) {
-      s0 += src[stride * p];
-      s1 += src[stride * (p + 1)];
-      s2 += src[stride * (p + 2)];
-      s3 += src[stride * (p + 3)];
+    for (; p + 8 <= npanel; p += 8) {
+      float v[8][V];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if constexpr (V == 4) {
+          const float4 f = __ldcs(reinterpret_cast<const float4*>(src + stride * (p + u)));
+          v[u][0] = f.x;
+          v[u][1] = f.y;
+          v[u][2] = f.z;
+          v[u][3] = f.w;
+        } else {
+          v[u][0] = __ldcs(src + stride * (p + u));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int x = 0; x < V; ++x) neumaier_add(s[x], k[x], v[u][x]);
     }
-    for (; p < npanel; ++p) s0 += src[stride * p];
-    Sc[static_cast<size_t>(j) * lds + cc] = static_cast<float>((s0 + s1) + (s2 + s3));
-  } else if (idx < 2 * nc) {
-    const long long r = idx - nc;
+    for (; p < npanel; ++p)
+#pragma unroll
+      for (int x = 0; x < V; ++x) neumaier_add(s[x], k[x], src[stride * p + x]);
+#pragma unroll
+    for (int x = 0; x < V; ++x) Sc[static_cast<size_t>(j) * lds + cc + x] = s[x] + k[x];
+  } else if (idx < ncv + static_cast<long long>(n) * c) {
+    const long long r = idx - ncv;
     const int i = static_cast<int>(r / c), cc = static_cast<int>(r % c);
     const int p = i / BM, row = i % BM;
-    const long long q0 = ((static_cast<long long>(p) * ntc + 1) * P - 1) / T;
-    const long long q1 = ((static_cast<long long>(p + 1) * ntc) * P - 1) / T;
-    double s = 0.0;
-    for (long long part = 0; part <= q1 - q0; ++part)
-      s += sr_part[((static_cast<size_t>(p) * maxparts + part) * c + cc) * BM + row];
-    Sr[static_cast<size_t>(i) * lds + cc] = static_cast<float>(s);
+    float s = 0.f, k = 0.f;
+    for (int grp = 0; grp < ngroups; ++grp) {
+      const long long t0 = static_cast<long long>(p) * ntc + static_cast<long long>(grp) * gs;
+      const long long t1 = static_cast<long long>(p) * ntc + min((grp + 1) * gs, ntc) - 1;
+      const size_t slot = (static_cast<size_t>(p) * ngroups + grp) * 2;
+      neumaier_add(s, k, sr_part[((slot * c) + cc) * BM + row]);
+      if (tile_owner(t0, T, P) != tile_owner(t1, T, P))   // a CTA range starts inside
+        neumaier_add(s, k, sr_part[(((slot + 1) * c) + cc) * BM + row]);
+    }
+    Sr[static_cast<size_t>(i) * lds + cc] = s + k;
   }
+}
+
+// leaf_lo[id] / leaf_hi[id] = the index range of leaf `id` (leaves are
+// contiguous index ranges; their ids need not increase with the index)
+__global__ void leaf_bounds_kernel(const int32_t* __restrict__ leaf_of, int n, int32_t* leaf_lo,
+                                   int32_t* leaf_hi) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int id = leaf_of[i];
+  if (i == 0 || leaf_of[i - 1] != id) leaf_lo[id] = i;
+  if (i == n - 1 || leaf_of[i + 1] != id) leaf_hi[id] = i + 1;
 }
 
 // R16[i, cc] = R[i, c0 + cc] (bfloat16-exact) for cc < c, zero up to cpad
@@ -531,7 +589,7 @@ DevInfo& dev_info(int dev) {
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 struct TcPlan {
-  int npanel, ntc, P, maxparts;
+  int npanel, ntc, P, gs, ngroups;
   long long T;
 };
 
@@ -541,8 +599,11 @@ TcPlan plan(int64_t n, int sms) {
   pl.ntc = static_cast<int>((n + BN - 1) / BN);
   pl.T = static_cast<long long>(pl.npanel) * pl.ntc;
   pl.P = static_cast<int>(pl.T < sms ? pl.T : sms);
-  const long long per = pl.T / pl.P;   // fewest tiles a CTA gets
-  pl.maxparts = static_cast<int>((pl.ntc + per - 1) / per) + 1;
+  // a flush group holds at most one start of a CTA range: no longer than
+  // the shortest range
+  const long long per = pl.T / pl.P;
+  pl.gs = static_cast<int>(per < FLUSH_MAX ? per : FLUSH_MAX);
+  pl.ngroups = (pl.ntc + pl.gs - 1) / pl.gs;
   return pl;
 }
 
@@ -554,7 +615,8 @@ size_t sample_tc_scratch_bytes(int64_t n, int64_t ncols, int sms) {
   const int64_t cpad = (c + 63) / 64 * 64;
   return align256(static_cast<size_t>(n) * cpad * 2) +
          align256(static_cast<size_t>(pl.npanel) * n * c * 4) +
-         align256(static_cast<size_t>(pl.npanel) * pl.maxparts * c * BM * 8) + 256;
+         align256(static_cast<size_t>(pl.npanel) * pl.ngroups * 2 * c * BM * 4) +
+         2 * align256(static_cast<size_t>(n) * 4) + 256;
 }
 
 bool sample_tc_supported(const float* A, int64_t n, int64_t lda, int mode) {
@@ -601,9 +663,18 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     base += align256(static_cast<size_t>(n) * cpad * 2);
     float* scp = reinterpret_cast<float*>(base);
     base += align256(static_cast<size_t>(pl.npanel) * n * c * 4);
-    double* srp = reinterpret_cast<double*>(base);
-    base += align256(static_cast<size_t>(pl.npanel) * pl.maxparts * c * BM * 8);
+    float* srp = reinterpret_cast<float*>(base);
+    base += align256(static_cast<size_t>(pl.npanel) * pl.ngroups * 2 * c * BM * 4);
+    int32_t* leaf_lo = reinterpret_cast<int32_t*>(base);
+    base += align256(static_cast<size_t>(n) * 4);
+    int32_t* leaf_hi = reinterpret_cast<int32_t*>(base);
+    base += align256(static_cast<size_t>(n) * 4);
     int* err = reinterpret_cast<int*>(base);
+    if (leaf_of != nullptr && w == 0) {
+      leaf_bounds_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
+          leaf_of, static_cast<int>(n), leaf_lo, leaf_hi);
+      HSS_TRY(check_launch("leaf_bounds_kernel"));
+    }
 
     const long long nconv = static_cast<long long>(n) * cpad;
     r_to_bf16_kernel<<<static_cast<unsigned>((nconv + 255) / 256), 256, 0, s>>>(
@@ -623,8 +694,11 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     g.npanel = pl.npanel;
     g.T = pl.T;
     g.P = pl.P;
-    g.maxparts = pl.maxparts;
+    g.gs = pl.gs;
+    g.ngroups = pl.ngroups;
     g.leaf_of = leaf_of;
+    g.leaf_lo = leaf_lo;
+    g.leaf_hi = leaf_hi;
     g.sc_part = scp;
     g.sr_part = srp;
     g.err = err;
@@ -634,10 +708,17 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     else
       sample_tc_kernel<2><<<pl.P, THREADS, smem, s>>>(tmA, tmRJ, tmRI, g);
     HSS_TRY(check_launch("sample_tc_kernel"));
-    const long long nred = 2ll * n * c;
-    sample_tc_reduce_kernel<<<static_cast<unsigned>((nred + 255) / 256), 256, 0, s>>>(
-        scp, srp, static_cast<int>(n), c, pl.npanel, pl.ntc, pl.T, pl.P, pl.maxparts,
-        Sr + c0 + done, Sc + c0 + done, lds);
+    if (c % 4 == 0) {
+      const long long nred = static_cast<long long>(n) * (c / 4) + static_cast<long long>(n) * c;
+      sample_tc_reduce_kernel<4><<<static_cast<unsigned>((nred + 255) / 256), 256, 0, s>>>(
+          scp, srp, static_cast<int>(n), c, pl.npanel, pl.ntc, pl.T, pl.P, pl.gs, pl.ngroups,
+          Sr + c0 + done, Sc + c0 + done, lds);
+    } else {
+      const long long nred = 2ll * n * c;
+      sample_tc_reduce_kernel<1><<<static_cast<unsigned>((nred + 255) / 256), 256, 0, s>>>(
+          scp, srp, static_cast<int>(n), c, pl.npanel, pl.ntc, pl.T, pl.P, pl.gs, pl.ngroups,
+          Sr + c0 + done, Sc + c0 + done, lds);
+    }
     HSS_TRY(check_launch("sample_tc_reduce_kernel"));
     int herr = 0;
     HSS_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));

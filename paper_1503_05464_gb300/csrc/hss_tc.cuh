@@ -46,6 +46,18 @@ __device__ __forceinline__ bool mbar_try(uint32_t b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// as mbar_try, but the thread may be suspended (issuing nothing) for up to
+// `hint_ns` nanoseconds while the phase is incomplete
+__device__ __forceinline__ bool mbar_try_suspend(uint32_t b, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, "
+      "0, p; }"
+      : "=r"(ok)
+      : "r"(b), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
 
 // Bounded wait for the phase of `parity` to complete.  Gives up (returns
 // false) when *abort is set by another thread or after `limit` clock cycles,
@@ -54,7 +66,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t b, uint32_t parity, volatile 
                                           int* err, int code, long long limit) {
   if (mbar_try(b, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_try(b, parity)) {
+  while (!mbar_try_suspend(b, parity, 200000u)) {
     if (*abort) return false;
     if (clock64() - t0 > limit) {
       *abort = 1;
@@ -124,6 +136,23 @@ __device__ __forceinline__ void tmem_st32(uint32_t ta, const float* v) {
       "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
       "r"(r[29]), "r"(r[30]), "r"(r[31]));
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%"
+      "15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(ta));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t ta, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%"
+      "14,%15,%16};" ::"r"(ta),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15]));
+}
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -139,6 +168,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
       "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, "
       "p; }" ::"r"(d),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+// the same with A read from tensor memory: row m of A is TMEM lane m, and
+// column (k / 2) holds the bfloat16 pair (k, k + 1) in its low / high half
+__device__ __forceinline__ void mma_bf16_tmem_a(uint32_t d, uint32_t a_tmem, uint64_t b,
+                                                uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, "
+      "%3, p; }" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
 }
 // arrive once on `bar` when every tcgen05 operation issued so far by this
 // thread has completed

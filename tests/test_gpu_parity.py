@@ -325,6 +325,30 @@ def test_compress_gaussian_kernel_fp32_reduced(P, mode):
     assert _rel(A32 @ xs, b) <= 10 * max(_rel(A32 @ xo, b), 1e-6)
 
 
+@pytest.mark.parametrize("mode", ["bf16x2", "bf16x3"])
+def test_compress_uneven_tree_split_modes(P, mode):
+    """n = 8 * leaf + 4: leaves sit at two depths, so the breadth-first leaf
+    numbering does not increase with the index; the leaf mask of the
+    tensor-core sampling must follow index ranges, not id order."""
+    n, leaf, rtol = 8 * 128 + 4, 128, 1e-4
+    nodes = O.bisection_tree(n, leaf)
+    depths = {nd.depth for nd in nodes if nd.is_leaf}
+    assert len(depths) == 2
+    pts = W.points_unit_cube(n, 77)
+    pts = pts[W.rcb_order(pts, leaf)]
+    At = W.gaussian_kernel(pts, 0.15, 1.0, dtype=np.float32, device=DEV)
+    A32 = At.cpu().numpy().astype(np.float64)
+    h = P.hss_compress(At, leaf_size=leaf, rtol=rtol, d0=64, d_step=32, seed=12,
+                       sample_mode=mode)
+    ho = O.compress(A32, rtol, leaf_size=leaf, d0=64, d_step=32, seed=12)
+    H = _dense_from_gpu(P, h, n, torch.float32)
+    assert _rel(H, A32) <= _err_bound(A32, ho, rtol)
+    ranks = P.hss_node_ranks(h)
+    ro = ho.ranks()
+    for i in range(1, len(ranks)):
+        assert abs(ranks[i][2] - ro[i][0]) <= 2 + (2 if mode == "bf16x2" else 0), (i, ranks[i], ro[i])
+
+
 # ------------------------------------------------------------ edge cases
 def test_single_node_tree(P):
     n = 100
