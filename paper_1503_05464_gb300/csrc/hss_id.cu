@@ -6,25 +6,29 @@
 // Y is d x m and is stored transposed: its column j is the contiguous row j
 // of the input.  Column j belongs to CTA j % C, which keeps it in its shared
 // memory (or, for matrices too large for the cluster's shared memory, in a
-// global work copy) together with its residual norm.  Per elimination step:
-//   1. every CTA has published the largest residual norm among its active
-//      columns; after a cluster barrier each CTA reads all C candidates
-//      through distributed shared memory and picks the same pivot (largest
-//      norm, lowest index on ties);
-//   2. one warp of the pivot's owner recomputes that column's residual norm
-//      exactly (|R_ii|), takes the stopping decision against
-//      max(rtol |R_11|, atol), builds the Householder reflector and publishes
-//      it with the decision;
-//   3. after a second cluster barrier every CTA copies the reflector, applies
-//      it to its active columns (one warp per column: dot product, warp
-//      reduction, update), downdates their norms -- recomputing a norm when
-//      cancellation makes the downdate inaccurate (LAPACK xGEQP3's safeguard,
-//      threshold sqrt(eps)) -- and publishes its next candidate.
-// Columns never move: perm[0..k) records the pivot order, the remaining
-// columns follow in increasing index order.  The pivot columns' R entries go
-// to a global k x k buffer, and each CTA solves T = R1^{-1} R2 for the
-// remaining columns it owns (one thread per column), writing E = T^T so that
-// the generator is Pi [I; E].
+// global work copy) together with its residual norm.  One cluster barrier per
+// elimination step:
+//   1. after the barrier every CTA reads all C published candidates (largest
+//      residual norm among each CTA's active columns) through distributed
+//      shared memory and picks the same pivot (largest norm, lowest index on
+//      ties);
+//   2. every CTA copies the pivot column from its owner and derives, with the
+//      same arithmetic in the same order, its exact residual norm |R_ii|, the
+//      stopping decision against max(rtol |R_11|, atol) and the Householder
+//      reflector -- so no CTA waits for the owner, and all agree bitwise;
+//   3. every CTA applies the reflector to its active columns (a team of
+//      threads per column: dot product, fixed-order reduction, update),
+//      downdates their norms -- recomputing a norm when cancellation makes the
+//      downdate inaccurate (LAPACK xGEQP3's safeguard, threshold sqrt(eps)) --
+//      and publishes its next candidate into the other of two slots (a CTA can
+//      be at most one step ahead of another, so the slot being read is never
+//      the one being written).
+// Columns never move and a pivot column is never written after it is chosen
+// (its R_ii is kept aside), so peers can read it while its owner goes on.
+// perm[0..k) records the pivot order, the remaining columns follow in
+// increasing index order.  The pivot columns' R entries go to a global k x k
+// buffer, and each CTA solves T = R1^{-1} R2 for the remaining columns it owns
+// (one thread per column), writing E = T^T so that the generator is Pi [I; E].
 #include "hss_internal.cuh"
 
 #include <cooperative_groups.h>
@@ -50,6 +54,21 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Residual norms are >= 0 and inactive columns carry -1: as 64-bit integers
+// their bit patterns order the same way (the sign bit makes -1 negative), so
+// the arg-max runs on the integer pipes instead of the narrow FP64 one.
+__device__ __forceinline__ void warp_argmax_bits(long long& v, int& j) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oj = __shfl_xor_sync(0xffffffffu, j, o);
+    if (ov > v || (ov == v && oj < j)) {
+      v = ov;
+      j = oj;
+    }
+  }
 }
 
 __device__ __forceinline__ void warp_argmax(double& v, int& j) {
@@ -109,9 +128,12 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
                        int w_in_smem, double* __restrict__ r1buf_base,
                        const int64_t* __restrict__ r1off) {
   extern __shared__ __align__(16) double smem[];
-  __shared__ Pub pub;
+  __shared__ Pub pub[2];
   __shared__ double redv[ID_WARPS];
+  __shared__ long long redb[ID_WARPS];
   __shared__ int redi[ID_WARPS];
+  __shared__ double hh[4];   // this step's sigma, tau, beta, scale
+  __shared__ int hstop;
 
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
@@ -127,11 +149,11 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   }
   const int mloc = (m - crank + C - 1) / C;       // columns crank, crank+C, ...
   const int mloc_max = (m + C - 1) / C;
-  double* vloc = smem;                            // d
-  double* vbuf = vloc + d;                        // d (published reflector)
-  double* nrm = vbuf + d;                         // mloc_max
+  double* vloc = smem;                            // d: pivot column, then reflector
+  double* nrm = vloc + d;                         // mloc_max
   double* nrm0 = nrm + mloc_max;                  // mloc_max
-  int* pstep = reinterpret_cast<int*>(nrm0 + mloc_max);   // mloc_max: pivot step or -1
+  double* rdiag = nrm0 + mloc_max;                // mloc_max: R_ii of the pivot columns
+  int* pstep = reinterpret_cast<int*>(rdiag + mloc_max);   // mloc_max: pivot step or -1
   double* Wsm = reinterpret_cast<double*>(pstep + ((mloc_max + 1) & ~1));
   // odd column stride in shared memory: a thread per column reads without
   // bank conflicts
@@ -199,8 +221,8 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
           v = redv[q];
           j = redi[q];
         }
-      pub.cand_val = v;
-      pub.cand_idx = j;
+      pub[0].cand_val = v;
+      pub[0].cand_idx = j;
     }
   };
   publish_candidate();
@@ -209,71 +231,80 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   int k = kmax;
   double r11 = 0.0;
   for (int i = 0; i < kmax; ++i) {
-    cluster.sync();   // (A) candidates published
+    cluster.sync();   // candidates of step i published, updates of step i-1 done
+    const int slot = i & 1;
     // every warp reads the C candidates in parallel (lane r <- CTA r) and
     // reduces them: all threads agree on the pivot without a block barrier
-    double bv = -1.0;
+    long long bv = LLONG_MIN;
     int p = INT_MAX;
     for (int r = lane; r < C; r += 32) {
-      const Pub* rp = cluster.map_shared_rank(&pub, r);
-      double v = rp->cand_val;
-      int j = rp->cand_idx;
+      const Pub* rp = cluster.map_shared_rank(&pub[slot], r);
+      const long long v = __double_as_longlong(rp->cand_val);
+      const int j = rp->cand_idx;
       if (v > bv || (v == bv && j < p)) {
         bv = v;
         p = j;
       }
     }
-    warp_argmax(bv, p);
+    warp_argmax_bits(bv, p);
     const int owner = p % C;
-    if (owner == crank && warp == 0) {
-      // one warp: exact residual norm of the pivot column and its reflector
-      double* wp = col(p / C);
-      double sa = 0.0, st = 0.0;
-      for (int c = i + lane; c < d; c += 32) {
-        double x = wp[c];
-        sa = fma(x, x, sa);
-        if (c > i) st = fma(x, x, st);
-      }
-      sa = warp_sum(sa);
-      st = warp_sum(st);
-      const double sigma = sqrt(sa);
-      const double r11_now = (i == 0) ? sigma : r11;
-      const int stop = (r11_now == 0.0 || sigma <= fmax(rtol * r11_now, atol)) ? 1 : 0;
-      const double alpha = wp[i];
-      double tau = 0.0, beta = alpha, scal = 0.0;
-      if (!stop && st != 0.0) {
-        beta = -copysign(sigma, alpha);
-        tau = (beta - alpha) / beta;
-        scal = 1.0 / (alpha - beta);
-      }
-      if (!stop) {
-        for (int c = i + lane; c < d; c += 32) vbuf[c - i] = (c == i) ? 1.0 : wp[c] * scal;
-      }
-      __syncwarp();
-      if (lane == 0) {
-        pub.stop = stop;
-        pub.tau = tau;
-        pub.r11 = r11_now;
-        if (!stop) {
-          wp[i] = beta;   // R_ii
-          perm[i] = p;
-          nrm[p / C] = -1.0;
-          pstep[p / C] = i;
-        }
-      }
+    // the pivot column, entries i..d-1, from its owner
+    {
+      const double* src = w_in_smem ? cluster.map_shared_rank(Wsm + (size_t)(p / C) * ldw, owner)
+                                     : it.work + (size_t)p * d;
+      for (int c = i + tid; c < d; c += ID_THREADS) vloc[c - i] = src[c];
     }
-    cluster.sync();   // (B) reflector and decision published
-    const Pub* op = cluster.map_shared_rank(&pub, owner);
-    const int stop = op->stop;
-    const double tau = op->tau;
-    if (i == 0) r11 = op->r11;
-    if (stop) {
-      k = i;
-      break;   // every CTA of the cluster reads the same decision
-    }
-    const double* ov = cluster.map_shared_rank(vbuf, owner);
-    for (int c = tid; c < d - i; c += ID_THREADS) vloc[c] = ov[c];
     __syncthreads();
+    {
+      // exact residual norm and reflector, the same arithmetic on every CTA:
+      // st = sum of x_c^2 for c > i, thread t taking c = i + 1 + t + 256 q in
+      // increasing q, then a warp butterfly and the 8 warp sums in order
+      double st = 0.0;
+      for (int c = i + 1 + tid; c < d; c += ID_THREADS) {
+        const double x = vloc[c - i];
+        st = fma(x, x, st);
+      }
+      st = warp_sum(st);
+      if (lane == 0) redv[warp] = st;
+      __syncthreads();
+      if (tid == 0) {
+        st = redv[0];
+        for (int q = 1; q < ID_WARPS; ++q) st += redv[q];
+        const double alpha = vloc[0];
+        const double sa = fma(alpha, alpha, st);
+        const double sigma = sqrt(sa);
+        const double r11_now = (i == 0) ? sigma : r11;
+        const int stop = (r11_now == 0.0 || sigma <= fmax(rtol * r11_now, atol)) ? 1 : 0;
+        double tau = 0.0, beta = alpha, scal = 0.0;
+        if (!stop && st != 0.0) {
+          beta = -copysign(sigma, alpha);
+          tau = (beta - alpha) / beta;
+          scal = 1.0 / (alpha - beta);
+        }
+        hh[0] = sigma;
+        hh[1] = tau;
+        hh[2] = beta;
+        hh[3] = scal;
+        hstop = stop;
+      }
+    }
+    __syncthreads();
+    if (i == 0) r11 = hh[0];
+    if (hstop) {
+      k = i;
+      break;   // every CTA of the cluster takes the same decision
+    }
+    const double tau = hh[1], scal = hh[3];
+    for (int c = i + tid; c < d; c += ID_THREADS) vloc[c - i] = (c == i) ? 1.0 : vloc[c - i] * scal;
+    if (owner == crank && tid == 0) {
+      rdiag[p / C] = hh[2];
+      nrm[p / C] = -1.0;
+      pstep[p / C] = i;
+    }
+    if (crank == 0 && tid == 0) perm[i] = p;
+    __syncthreads();
+    long long cv = LLONG_MIN;   // this thread's best candidate for step i + 1 (norm bits)
+    int cj = INT_MAX;
     for (int jb = warp * cols_per_warp; jb < mloc; jb += ID_WARPS * cols_per_warp) {
       const int jl = jb + lane / TS;
       const double nj = jl < mloc ? nrm[jl] : -1.0;
@@ -307,10 +338,35 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
           if (member == 0) nrm0[jl] = newn;
         }
       }
-      if (act && member == 0) nrm[jl] = newn;
+      if (act && member == 0) {
+        nrm[jl] = newn;
+        const int j = jl * C + crank;
+        const long long nb = __double_as_longlong(newn);
+        if (nb > cv || (nb == cv && j < cj)) {
+          cv = nb;
+          cj = j;
+        }
+      }
+    }
+    // next candidate: warp arg-max, then one thread over the warps
+    warp_argmax_bits(cv, cj);
+    if (lane == 0) {
+      redb[warp] = cv;
+      redi[warp] = cj;
     }
     __syncthreads();
-    publish_candidate();
+    if (tid == 0) {
+      long long v = redb[0];
+      int j = redi[0];
+      for (int q = 1; q < ID_WARPS; ++q)
+        if (redb[q] > v || (redb[q] == v && redi[q] < j)) {
+          v = redb[q];
+          j = redi[q];
+        }
+      // no active column: -1 (the bit pattern of LLONG_MIN is not a norm)
+      pub[slot ^ 1].cand_val = v == LLONG_MIN ? -1.0 : __longlong_as_double(v);
+      pub[slot ^ 1].cand_idx = j;
+    }
   }
 
   // R1 (k x k, column b = pivot b's first b+1 entries) to global, remaining
@@ -322,7 +378,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     const int b = pstep[jl];
     if (b >= 0 && b < k) {
       const double* w = col(jl);
-      for (int a = lane; a <= b; a += 32) R1[(size_t)b * k + a] = w[a];
+      for (int a = lane; a <= b; a += 32) R1[(size_t)b * k + a] = (a == b) ? rdiag[jl] : w[a];
     }
     if (lane == 0) flag[j] = (b < 0 || b >= k) ? 1 : 0;
   }
@@ -389,7 +445,7 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
   const int d = std::max(max_d, 1);
   auto need = [&](int c) {
     int mloc = (max_m + c - 1) / c;
-    return sizeof(double) * (2 * (size_t)d + 2 * (size_t)mloc) +
+    return sizeof(double) * ((size_t)d + 3 * (size_t)mloc) +
            sizeof(int) * (size_t)((mloc + 1) & ~1);
   };
   size_t base = need(C);
