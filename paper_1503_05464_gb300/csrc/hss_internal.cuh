@@ -234,6 +234,7 @@ struct GemmItem {
   int32_t m_trans;       // 0: M[j*ldm+l], 1: M[l*ldm+j]
   int32_t m_is_f64;
   T sign;
+  int32_t z_trans;       // 0: Z row l, column c; 1: Z row c, column l (rows of Z are columns)
 };
 template <typename T>
 Err launch_gemm_batched(const std::vector<GemmItem<T>>& items, cudaStream_t s,

@@ -1,7 +1,8 @@
 // Batched level kernels of the tree traversals (Algorithms 1, 2): every node
 // of a tree level is one item of a single launch.
 //
-//  * gemm_batched: out[j][c] = X[xrow(j)][c] + sign * sum_l Mat(j,l) Z[zrow(l)][c]
+//  * gemm_batched: out[j][c] = X[xrow(j)][c] + sign * sum_l Mat(j,l) Z(l, c), with
+//    Z(l, c) = Z[zrow(l)][c], or Z[zrow(c)][l] when the item asks for Z^T
 //    covers Algorithm 1's merges S_nu - B R_nu, the row selections
 //    S_tau = S_loc(J,:), the basis products V^T R = R(J) + E^T R(rest), and
 //    Algorithm 2's products.  Rows of X and Z may come through an index map
@@ -70,7 +71,7 @@ gemm_batched_kernel(const GemmItem<T>* __restrict__ items, const int* __restrict
       int l = e / G_TN, c = e - l * G_TN;
       int ll = l0 + l, cc = cb + c;
       T v = T(0);
-      if (ll < it.inner && cc < it.c1) v = src_row(it.Z, ll)[cc];
+      if (ll < it.inner && cc < it.c1) v = it.z_trans ? src_row(it.Z, cc)[ll] : src_row(it.Z, ll)[cc];
       Zs[l][c] = v;
     }
     __syncthreads();

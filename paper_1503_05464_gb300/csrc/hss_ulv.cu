@@ -20,6 +20,10 @@
 using namespace hss;
 
 namespace hss {
+
+size_t ulv_big_min_m();
+Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaStream_t s);
+
 namespace {
 
 constexpr int U_THREADS = 256;
@@ -521,10 +525,16 @@ extern "C" hss_status hss_factor(hss_t h, void* stream) {
   e = dalloc_t(&status, 1, s);
   if (e.st == HSS_OK) e = cudaMemsetAsync(status, 0, 4, s) == cudaSuccess ? ok() : fail(HSS_ERR_CUDA, "memset");
   for (int depth = tr.maxdepth; depth >= 0 && e.st == HSS_OK; --depth) {
+    // large nodes: blocked path over the whole GPU; the rest: one CTA each
+    std::vector<int> big, small;
+    for (int id : tr.levels[depth])
+      ((size_t)F.nodes[id].m >= ulv_big_min_m() ? big : small).push_back(id);
+    e = ulv_factor_big(h, big, status, s);
+    if (e.st != HSS_OK || small.empty()) continue;
     std::vector<FacItem> items;
     size_t scratch = 0;
     int maxm = 1;
-    for (int id : tr.levels[depth]) {
+    for (int id : small) {
       const UlvNode& u = F.nodes[id];
       const NodeGen& g = h->gen[id];
       scratch += 2 * (size_t)u.m * u.m + (size_t)u.m * std::max(u.kc, 1) +
@@ -535,7 +545,7 @@ extern "C" hss_status hss_factor(hss_t h, void* stream) {
     e = dalloc_t(&sc, std::max<size_t>(scratch, 1), s);
     if (e.st) break;
     size_t so = 0;
-    for (int id : tr.levels[depth]) {
+    for (int id : small) {
       const TNode& nd = tr.nodes[id];
       const UlvNode& u = F.nodes[id];
       const NodeGen& g = h->gen[id];

@@ -1,0 +1,588 @@
+// ULV factorization (Algorithm 3) of large nodes, spread over the whole GPU.
+//
+// The per-node kernel of hss_ulv.cu runs one CTA per node, which suits the
+// many small nodes of the lower levels.  A node of order m in the thousands
+// (ranks of that size occur at tight tolerances) would keep one SM busy for
+// O(m^3) FP64 work, so large nodes take a blocked path instead, batched over
+// the large nodes of a level:
+//   D_tau   diagonal blocks copied, off-diagonal blocks B Vtb^T by batched GEMM;
+//   Vhat    diag(Vtb_1, Vtb_2) V by batched GEMM (V = Pi [I; E] scattered);
+//   W       Omega D_tau: top rows D(perm(k+i)) - E D(perm(0..k)) by GEMM;
+//   LQ      in panels of NB rows: a one-CTA panel factorization (the same
+//           Householder steps as the per-node kernel), the panel's compact WY
+//           factor T (I - V^T T V = H_i0 ... H_i1), then the trailing rows
+//           W <- W - ((W V^T) T) V by three batched GEMMs;
+//   Vtilde  Q Vhat panel by panel: Vhat <- Vhat - V^T (T^T (V Vhat));
+//   root    right-looking blocked LU with partial pivoting (panel, triangular
+//           solve of the block row, GEMM update of the trailing matrix).
+// The factors have the per-node kernel's layout, so the solve is unchanged.
+#include "hss_internal.cuh"
+#include "hss_tree.h"
+
+#include <algorithm>
+#include <climits>
+
+namespace hss {
+
+namespace {
+
+constexpr int NB = 32;           // panel width
+constexpr int B_THREADS = 256;
+constexpr int B_WARPS = B_THREADS / 32;
+
+__device__ __forceinline__ double wsum_b(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ double block_sum_b(double v, double* red) {
+  v = wsum_b(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < B_WARPS; ++q) s += red[q];
+  return s;
+}
+
+// dst[i][j] (rows x cols, ld_dst) = src[i][j] (input dtype or FP64), with an
+// optional destination row map and an optional lower-triangle mask
+struct CopyItem {
+  const void* src;
+  int64_t lds;
+  int src_f64;
+  double* dst;
+  int64_t ldd;
+  int rows, cols;
+  const int32_t* dst_row;   // null: row i
+  int lower;                // 1: entries j > i become 0
+};
+
+__global__ void copy_items_kernel(const CopyItem* items, const int64_t* start, int nitems,
+                                  int64_t total) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  int lo = 0, hi = nitems - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  const CopyItem it = items[lo];
+  const int64_t e = t - start[lo];
+  const int i = static_cast<int>(e / it.cols), j = static_cast<int>(e % it.cols);
+  double v = it.src_f64 ? reinterpret_cast<const double*>(it.src)[i * it.lds + j]
+                        : static_cast<double>(reinterpret_cast<const float*>(it.src)[i * it.lds + j]);
+  if (it.lower && j > i) v = 0.0;
+  const int di = it.dst_row ? it.dst_row[i] : i;
+  it.dst[di * it.ldd + j] = v;
+}
+
+// V[perm[l]][l] = 1 for l < kc (the identity part of V = Pi [I; E])
+struct EyeItem {
+  double* V;
+  int kc;
+  const int32_t* perm;
+};
+
+__global__ void scatter_identity_kernel(const EyeItem* items) {
+  const EyeItem it = items[blockIdx.y];
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < it.kc) it.V[static_cast<int64_t>(it.perm[l]) * it.kc + l] = 1.0;
+}
+
+struct LqPanel {
+  double* W;       // m x m, row-major
+  double* hv;      // r x m reflectors
+  double* tau;     // r
+  int m, i0, nbb;
+};
+
+// rows [i0, i0 + nbb) of W: Householder steps restricted to the panel rows
+__global__ void __launch_bounds__(B_THREADS) lq_panel_kernel(const LqPanel* items) {
+  extern __shared__ double vsh[];
+  __shared__ double red[B_WARPS];
+  const LqPanel it = items[blockIdx.x];
+  const int m = it.m, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = it.i0; i < it.i0 + it.nbb; ++i) {
+    double* wi = it.W + static_cast<int64_t>(i) * m;
+    double sa = 0.0, st = 0.0;
+    for (int c = i + tid; c < m; c += B_THREADS) {
+      const double x = wi[c];
+      sa = fma(x, x, sa);
+      if (c > i) st = fma(x, x, st);
+    }
+    sa = block_sum_b(sa, red);
+    st = block_sum_b(st, red);
+    const double alpha = wi[i];
+    const double sigma = sqrt(sa);
+    double tau, beta, scal;
+    if (st == 0.0) {
+      tau = 0.0;
+      beta = alpha;
+      scal = 0.0;
+    } else {
+      beta = -copysign(sigma, alpha);
+      tau = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+    }
+    for (int c = tid; c < m; c += B_THREADS) {
+      const double v = c < i ? 0.0 : (c == i ? 1.0 : wi[c] * scal);
+      vsh[c] = v;
+      it.hv[static_cast<int64_t>(i) * m + c] = v;
+    }
+    __syncthreads();
+    for (int c = i + tid; c < m; c += B_THREADS) wi[c] = c == i ? beta : 0.0;
+    if (tid == 0) it.tau[i] = tau;
+    for (int j = i + 1 + warp; j < it.i0 + it.nbb; j += B_WARPS) {
+      double* wj = it.W + static_cast<int64_t>(j) * m;
+      double dot = 0.0;
+      for (int c = i + lane; c < m; c += 32) dot = fma(wj[c], vsh[c], dot);
+      dot = wsum_b(dot) * tau;
+      for (int c = i + lane; c < m; c += 32) wj[c] = fma(-dot, vsh[c], wj[c]);
+    }
+    __syncthreads();
+  }
+}
+
+struct TItem {
+  const double* G;    // nbb x nbb, ld NB: V V^T of the panel
+  const double* tau;  // nbb
+  double* T;          // nbb x nbb, ld NB (upper triangular)
+  int nbb;
+};
+
+// compact WY factor, forward accumulation of row reflectors:
+// T(j,j) = tau_j, T(0:j, j) = -tau_j T(0:j, 0:j) (V(0:j,:) v_j^T)
+__global__ void wy_t_kernel(const TItem* items) {
+  const TItem it = items[blockIdx.x];
+  const int n = it.nbb, tid = threadIdx.x;
+  for (int e = tid; e < NB * NB; e += blockDim.x) it.T[e] = 0.0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const double tj = it.tau[j];
+    double w = 0.0;
+    if (tid < j)
+      for (int l = tid; l < j; ++l) w = fma(it.T[tid * NB + l], it.G[l * NB + j], w);
+    __syncthreads();
+    if (tid < j) it.T[tid * NB + j] = -tj * w;
+    if (tid == 0) it.T[j * NB + j] = tj;
+    __syncthreads();
+  }
+}
+
+struct LuPanel {
+  double* A;        // m x m
+  int32_t* piv;
+  int32_t* status;
+  int m, j0, nbb;
+};
+
+// columns [j0, j0 + nbb): partial pivoting (largest |a|, lowest row on ties),
+// whole-row swaps, column scaling and the rank-1 updates inside the panel
+__global__ void __launch_bounds__(B_THREADS) lu_panel_kernel(const LuPanel* items) {
+  __shared__ double redv[B_WARPS];
+  __shared__ int redi[B_WARPS];
+  const LuPanel it = items[blockIdx.x];
+  const int m = it.m, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* A = it.A;
+  for (int j = it.j0; j < it.j0 + it.nbb; ++j) {
+    double bv = -1.0;
+    int bi = INT_MAX;
+    for (int i = j + tid; i < m; i += B_THREADS) {
+      const double x = fabs(A[static_cast<int64_t>(i) * m + j]);
+      if (x > bv) {
+        bv = x;
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    __syncthreads();
+    if (lane == 0) {
+      redv[warp] = bv;
+      redi[warp] = bi;
+    }
+    __syncthreads();
+    bv = redv[0];
+    bi = redi[0];
+    for (int q = 1; q < B_WARPS; ++q)
+      if (redv[q] > bv || (redv[q] == bv && redi[q] < bi)) {
+        bv = redv[q];
+        bi = redi[q];
+      }
+    if (bv == 0.0) {
+      if (tid == 0) *it.status = HSS_ERR_SINGULAR;
+      return;   // uniform across the CTA
+    }
+    if (bi != j)
+      for (int c = tid; c < m; c += B_THREADS) {
+        const double t = A[static_cast<int64_t>(j) * m + c];
+        A[static_cast<int64_t>(j) * m + c] = A[static_cast<int64_t>(bi) * m + c];
+        A[static_cast<int64_t>(bi) * m + c] = t;
+      }
+    if (tid == 0) it.piv[j] = bi;
+    __syncthreads();
+    const double pv = A[static_cast<int64_t>(j) * m + j];
+    const int cend = it.j0 + it.nbb;
+    for (int i = j + 1 + warp; i < m; i += B_WARPS) {
+      double* ai = A + static_cast<int64_t>(i) * m;
+      const double l = ai[j] / pv;
+      for (int c = j + 1 + lane; c < cend; c += 32)
+        ai[c] = fma(-l, A[static_cast<int64_t>(j) * m + c], ai[c]);
+      if (lane == 0) ai[j] = l;
+    }
+    __syncthreads();
+  }
+}
+
+// U12 = L11^{-1} A12 (unit lower L11 of the panel), one thread per column
+__global__ void lu_trsm_kernel(double* A, int m, int j0, int nbb) {
+  __shared__ double L11[NB * NB];
+  for (int e = threadIdx.x; e < nbb * nbb; e += blockDim.x) {
+    const int a = e / nbb, b = e % nbb;
+    L11[a * NB + b] = A[static_cast<int64_t>(j0 + a) * m + j0 + b];
+  }
+  __syncthreads();
+  const int c = j0 + nbb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m) return;
+  double x[NB];
+#pragma unroll
+  for (int a = 0; a < NB; ++a) {
+    if (a < nbb) {
+      double v = A[static_cast<int64_t>(j0 + a) * m + c];
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        if (b < a) v = fma(-L11[a * NB + b], x[b], v);
+      x[a] = v;
+      A[static_cast<int64_t>(j0 + a) * m + c] = v;
+    }
+  }
+}
+
+template <typename TI>
+Err upload(const std::vector<TI>& v, cudaStream_t s, Arena& ar, TI** out) {
+  HSS_TRY(ar.alloc_t(out, std::max<size_t>(v.size(), 1), s));
+  return ar.upload(*out, v.data(), v.size() * sizeof(TI), s);
+}
+
+Err launch_copies(const std::vector<CopyItem>& items, cudaStream_t s, Arena& ar) {
+  std::vector<CopyItem> live;
+  std::vector<int64_t> start;
+  int64_t total = 0;
+  for (const CopyItem& c : items) {
+    if (c.rows <= 0 || c.cols <= 0) continue;
+    live.push_back(c);
+    start.push_back(total);
+    total += static_cast<int64_t>(c.rows) * c.cols;
+  }
+  if (live.empty()) return ok();
+  CopyItem* di = nullptr;
+  int64_t* ds = nullptr;
+  HSS_TRY(upload(live, s, ar, &di));
+  HSS_TRY(upload(start, s, ar, &ds));
+  copy_items_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
+      di, ds, static_cast<int>(live.size()), total);
+  return check_launch("copy_items_kernel");
+}
+
+GemmItem<double> gemm(double* out, int64_t ldo, int rows, int cols, int inner, const double* M,
+                      int64_t ldm, int m_trans, const double* Z, int64_t ldz, int z_trans,
+                      const double* X, int64_t ldx, double sign) {
+  GemmItem<double> g{};
+  g.out = out;
+  g.ldo = ldo;
+  g.rows = rows;
+  g.inner = inner;
+  g.c0 = 0;
+  g.c1 = cols;
+  g.M = M;
+  g.ldm = ldm;
+  g.m_trans = m_trans;
+  g.m_is_f64 = 1;
+  g.Z.p0 = Z;
+  g.Z.ld0 = ldz;
+  g.z_trans = z_trans;
+  if (X) {
+    g.X.p0 = X;
+    g.X.ld0 = ldx;
+  }
+  g.sign = sign;
+  return g;
+}
+
+Err run_gemms(const std::vector<GemmItem<double>>& v, cudaStream_t s, Arena& ar) {
+  std::vector<GemmItem<double>> live;
+  for (const auto& g : v)
+    if (g.rows > 0 && g.c1 > g.c0) live.push_back(g);
+  if (live.empty()) return ok();
+  return launch_gemm_batched<double>(live, s, nullptr, 0, &ar);
+}
+
+}  // namespace
+
+size_t ulv_big_min_m() { return 320; }
+
+// Factor the large nodes `ids` of one level (all non-root, or the root alone).
+Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaStream_t s) {
+  if (ids.empty()) return ok();
+  const Tree& tr = h->tree;
+  UlvFactors& F = h->ulv;
+  const bool f64in = h->dtype == HSS_F64;
+  Arena ar{(size_t)8 << 20};
+  struct Node {
+    int id, m, k, r, kc, mc, leaf, root;
+    double *Dw, *W, *Vh, *Vd, *Bd, *Y, *Y2, *G, *Tall, *Z1, *Z2;
+  };
+  std::vector<Node> N;
+  Err e = ok();
+  for (int id : ids) {
+    const TNode& nd = tr.nodes[id];
+    const UlvNode& u = F.nodes[id];
+    const NodeGen& g = h->gen[id];
+    Node x{};
+    x.id = id;
+    x.m = u.m;
+    x.root = id == 0;
+    x.leaf = nd.c1 < 0;
+    x.k = x.root ? 0 : u.k;
+    x.r = x.m - x.k;
+    x.kc = x.root ? 0 : u.kc;
+    x.mc = x.root ? 0 : g.mc;
+    const size_t mm = static_cast<size_t>(x.m) * x.m;
+    const int npan = (x.r + NB - 1) / NB;
+    size_t bd = 0;
+    if (!x.leaf) {
+      const UlvNode& a = F.nodes[nd.c1];
+      const UlvNode& b = F.nodes[nd.c2];
+      bd = static_cast<size_t>(a.k) * b.kc + static_cast<size_t>(b.k) * a.kc;
+    }
+    HSS_TRY(ar.alloc_t(&x.Dw, x.root ? 1 : mm, s));
+    if (x.root) x.Dw = F.root_lu;
+    if (!x.root) {
+      HSS_TRY(ar.alloc_t(&x.W, mm, s));
+      HSS_TRY(ar.alloc_t(&x.Vh, static_cast<size_t>(x.m) * std::max(x.kc, 1), s));
+      HSS_TRY(ar.alloc_t(&x.Vd, static_cast<size_t>(std::max(x.mc, 1)) * std::max(x.kc, 1), s));
+      HSS_TRY(ar.alloc_t(&x.Y, static_cast<size_t>(x.m) * NB, s));
+      HSS_TRY(ar.alloc_t(&x.Y2, static_cast<size_t>(x.m) * NB, s));
+      HSS_TRY(ar.alloc_t(&x.G, NB * NB, s));
+      HSS_TRY(ar.alloc_t(&x.Tall, static_cast<size_t>(std::max(npan, 1)) * NB * NB, s));
+      HSS_TRY(ar.alloc_t(&x.Z1, static_cast<size_t>(NB) * std::max(x.kc, 1), s));
+      HSS_TRY(ar.alloc_t(&x.Z2, static_cast<size_t>(NB) * std::max(x.kc, 1), s));
+    }
+    if (bd) HSS_TRY(ar.alloc_t(&x.Bd, bd, s));
+    N.push_back(x);
+  }
+
+  // ---- D_tau (and the FP64 copies of B12, B21)
+  {
+    std::vector<CopyItem> cp;
+    std::vector<GemmItem<double>> gm;
+    for (Node& x : N) {
+      const TNode& nd = tr.nodes[x.id];
+      const NodeGen& g = h->gen[x.id];
+      if (x.leaf) {
+        cp.push_back({g.D, x.m, f64in ? 1 : 0, x.Dw, x.m, x.m, x.m, nullptr, 0});
+        continue;
+      }
+      const UlvNode& a = F.nodes[nd.c1];
+      const UlvNode& b = F.nodes[nd.c2];
+      const int k1 = a.k, k2 = b.k;
+      cp.push_back({a.Dtil, k1, 1, x.Dw, x.m, k1, k1, nullptr, 0});
+      cp.push_back({b.Dtil, k2, 1, x.Dw + static_cast<size_t>(k1) * x.m + k1, x.m, k2, k2, nullptr, 0});
+      double* b12 = x.Bd;
+      double* b21 = x.Bd + static_cast<size_t>(k1) * b.kc;
+      cp.push_back({g.B12, b.kc, f64in ? 1 : 0, b12, b.kc, k1, b.kc, nullptr, 0});
+      cp.push_back({g.B21, a.kc, f64in ? 1 : 0, b21, a.kc, k2, a.kc, nullptr, 0});
+      // B12 Vtb_2^T and B21 Vtb_1^T
+      gm.push_back(gemm(x.Dw + k1, x.m, k1, k2, b.kc, b12, b.kc, 0, b.Vtb, b.kc, 1, nullptr, 0, 1.0));
+      gm.push_back(gemm(x.Dw + static_cast<size_t>(k1) * x.m, x.m, k2, k1, a.kc, b21, a.kc, 0,
+                        a.Vtb, a.kc, 1, nullptr, 0, 1.0));
+    }
+    HSS_TRY(launch_copies(cp, s, ar));
+    HSS_TRY(run_gemms(gm, s, ar));
+  }
+
+  // ---- root: blocked LU with partial pivoting
+  if (N.size() == 1 && N[0].root) {
+    Node& x = N[0];
+    const int m = x.m;
+    for (int j0 = 0; j0 < m; j0 += NB) {
+      const int nbb = std::min(NB, m - j0);
+      std::vector<LuPanel> lp{{x.Dw, F.root_piv, status, m, j0, nbb}};
+      LuPanel* dlp = nullptr;
+      HSS_TRY(upload(lp, s, ar, &dlp));
+      lu_panel_kernel<<<1, B_THREADS, 0, s>>>(dlp);
+      HSS_TRY(check_launch("lu_panel_kernel"));
+      const int rest = m - j0 - nbb;
+      if (rest <= 0) break;
+      lu_trsm_kernel<<<(rest + 127) / 128, 128, 0, s>>>(x.Dw, m, j0, nbb);
+      HSS_TRY(check_launch("lu_trsm_kernel"));
+      double* a22 = x.Dw + static_cast<size_t>(j0 + nbb) * m + j0 + nbb;
+      std::vector<GemmItem<double>> gm{gemm(a22, m, rest, rest, nbb,
+                                            x.Dw + static_cast<size_t>(j0 + nbb) * m + j0, m, 0,
+                                            x.Dw + static_cast<size_t>(j0) * m + j0 + nbb, m, 0,
+                                            a22, m, -1.0)};
+      HSS_TRY(run_gemms(gm, s, ar));
+    }
+    ar.release(s);
+    return ok();
+  }
+
+  // ---- Vhat = V (leaf) or diag(Vtb_1, Vtb_2) V, with V = Pi [I; E^c]
+  {
+    std::vector<CopyItem> cp;
+    std::vector<EyeItem> ey;
+    std::vector<GemmItem<double>> gm;
+    for (Node& x : N) {
+      if (x.kc == 0) continue;
+      const NodeGen& g = h->gen[x.id];
+      HSS_CUDA_TRY(cudaMemsetAsync(x.Vd, 0, sizeof(double) * x.mc * x.kc, s));
+      cp.push_back({g.Ec, x.kc, 1, x.Vd, x.kc, x.mc - x.kc, x.kc, g.permc + x.kc, 0});
+      ey.push_back({x.Vd, x.kc, g.permc});
+    }
+    HSS_TRY(launch_copies(cp, s, ar));
+    if (!ey.empty()) {
+      int maxkc = 1;
+      for (const EyeItem& q : ey) maxkc = std::max(maxkc, q.kc);
+      EyeItem* dey = nullptr;
+      HSS_TRY(upload(ey, s, ar, &dey));
+      scatter_identity_kernel<<<dim3((maxkc + 255) / 256, static_cast<unsigned>(ey.size())), 256,
+                                0, s>>>(dey);
+      HSS_TRY(check_launch("scatter_identity_kernel"));
+    }
+    for (Node& x : N) {
+      if (x.kc == 0) continue;
+      const TNode& nd = tr.nodes[x.id];
+      if (x.leaf) {
+        HSS_CUDA_TRY(cudaMemcpyAsync(x.Vh, x.Vd, sizeof(double) * x.m * x.kc,
+                                     cudaMemcpyDeviceToDevice, s));
+        continue;
+      }
+      const UlvNode& a = F.nodes[nd.c1];
+      const UlvNode& b = F.nodes[nd.c2];
+      gm.push_back(gemm(x.Vh, x.kc, a.k, x.kc, a.kc, a.Vtb, a.kc, 0, x.Vd, x.kc, 0, nullptr, 0, 1.0));
+      gm.push_back(gemm(x.Vh + static_cast<size_t>(a.k) * x.kc, x.kc, b.k, x.kc, b.kc, b.Vtb, b.kc,
+                        0, x.Vd + static_cast<size_t>(a.kc) * x.kc, x.kc, 0, nullptr, 0, 1.0));
+    }
+    HSS_TRY(run_gemms(gm, s, ar));
+  }
+
+  // ---- W = Omega D_tau
+  {
+    std::vector<GemmItem<double>> gm;
+    for (Node& x : N) {
+      const NodeGen& g = h->gen[x.id];
+      GemmItem<double> top = gemm(x.W, x.m, x.r, x.m, x.k, g.Er, x.k, 0, x.Dw, x.m, 0, x.Dw, x.m, -1.0);
+      top.Z.map = g.permr;
+      top.X.map = g.permr + x.k;
+      gm.push_back(top);
+      GemmItem<double> bot =
+          gemm(x.W + static_cast<size_t>(x.r) * x.m, x.m, x.k, x.m, 0, nullptr, 1, 0, nullptr, 1, 0,
+               x.Dw, x.m, 1.0);
+      bot.X.map = g.permr;
+      gm.push_back(bot);
+    }
+    HSS_TRY(run_gemms(gm, s, ar));
+  }
+
+  // ---- LQ of the top r rows in panels, trailing rows by GEMM
+  int maxm = 1, maxr = 0;
+  for (Node& x : N) {
+    maxm = std::max(maxm, x.m);
+    maxr = std::max(maxr, x.r);
+  }
+  if (static_cast<size_t>(maxm) * sizeof(double) > 200 * 1024)
+    return fail(HSS_ERR_INVALID, "ULV: node too large for the panel reflector buffer");
+  HSS_CUDA_TRY(cudaFuncSetAttribute(lq_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(maxm * sizeof(double))));
+  for (int i0 = 0; i0 < maxr; i0 += NB) {
+    std::vector<LqPanel> lp;
+    std::vector<TItem> ti;
+    std::vector<GemmItem<double>> gG, gY, gY2, gW;
+    for (Node& x : N) {
+      if (i0 >= x.r) continue;
+      const UlvNode& u = F.nodes[x.id];
+      const int nbb = std::min(NB, x.r - i0);
+      lp.push_back({x.W, u.hv, u.tau, x.m, i0, nbb});
+      const double* vp = u.hv + static_cast<size_t>(i0) * x.m + i0;
+      double* T = x.Tall + static_cast<size_t>(i0 / NB) * NB * NB;
+      gG.push_back(gemm(x.G, NB, nbb, nbb, x.m - i0, vp, x.m, 0, vp, x.m, 1, nullptr, 0, 1.0));
+      ti.push_back({x.G, u.tau + i0, T, nbb});
+      const int rows_t = x.m - i0 - nbb;
+      if (rows_t > 0) {
+        double* wt = x.W + static_cast<size_t>(i0 + nbb) * x.m + i0;
+        gY.push_back(gemm(x.Y, NB, rows_t, nbb, x.m - i0, wt, x.m, 0, vp, x.m, 1, nullptr, 0, 1.0));
+        gY2.push_back(gemm(x.Y2, NB, rows_t, nbb, nbb, x.Y, NB, 0, T, NB, 0, nullptr, 0, 1.0));
+        gW.push_back(gemm(wt, x.m, rows_t, x.m - i0, nbb, x.Y2, NB, 0, vp, x.m, 0, wt, x.m, -1.0));
+      }
+    }
+    LqPanel* dlp = nullptr;
+    HSS_TRY(upload(lp, s, ar, &dlp));
+    lq_panel_kernel<<<static_cast<unsigned>(lp.size()), B_THREADS, maxm * sizeof(double), s>>>(dlp);
+    HSS_TRY(check_launch("lq_panel_kernel"));
+    HSS_TRY(run_gemms(gG, s, ar));
+    TItem* dti = nullptr;
+    HSS_TRY(upload(ti, s, ar, &dti));
+    wy_t_kernel<<<static_cast<unsigned>(ti.size()), 64, 0, s>>>(dti);
+    HSS_TRY(check_launch("wy_t_kernel"));
+    HSS_TRY(run_gemms(gY, s, ar));
+    HSS_TRY(run_gemms(gY2, s, ar));
+    HSS_TRY(run_gemms(gW, s, ar));
+  }
+
+  // ---- L, W_b Q_t^T, Dtil
+  {
+    std::vector<CopyItem> cp;
+    for (Node& x : N) {
+      const UlvNode& u = F.nodes[x.id];
+      cp.push_back({x.W, x.m, 1, u.L, x.r, x.r, x.r, nullptr, 1});
+      cp.push_back({x.W + static_cast<size_t>(x.r) * x.m, x.m, 1, u.WbQt, x.r, x.k, x.r, nullptr, 0});
+      cp.push_back({x.W + static_cast<size_t>(x.r) * x.m + x.r, x.m, 1, u.Dtil, x.k, x.k, x.k,
+                    nullptr, 0});
+    }
+    HSS_TRY(launch_copies(cp, s, ar));
+  }
+
+  // ---- Vtilde = Q Vhat, panel by panel in order
+  for (int i0 = 0; i0 < maxr; i0 += NB) {
+    std::vector<GemmItem<double>> g1, g2, g3;
+    for (Node& x : N) {
+      if (i0 >= x.r || x.kc == 0) continue;
+      const UlvNode& u = F.nodes[x.id];
+      const int nbb = std::min(NB, x.r - i0);
+      const double* vp = u.hv + static_cast<size_t>(i0) * x.m + i0;
+      const double* T = x.Tall + static_cast<size_t>(i0 / NB) * NB * NB;
+      double* vh = x.Vh + static_cast<size_t>(i0) * x.kc;
+      g1.push_back(gemm(x.Z1, x.kc, nbb, x.kc, x.m - i0, vp, x.m, 0, vh, x.kc, 0, nullptr, 0, 1.0));
+      g2.push_back(gemm(x.Z2, x.kc, nbb, x.kc, nbb, T, NB, 1, x.Z1, x.kc, 0, nullptr, 0, 1.0));
+      g3.push_back(gemm(vh, x.kc, x.m - i0, x.kc, nbb, vp, x.m, 1, x.Z2, x.kc, 0, vh, x.kc, -1.0));
+    }
+    HSS_TRY(run_gemms(g1, s, ar));
+    HSS_TRY(run_gemms(g2, s, ar));
+    HSS_TRY(run_gemms(g3, s, ar));
+  }
+  {
+    std::vector<CopyItem> cp;
+    for (Node& x : N) {
+      if (x.kc == 0) continue;
+      const UlvNode& u = F.nodes[x.id];
+      cp.push_back({x.Vh, x.kc, 1, u.Vtt, x.kc, x.r, x.kc, nullptr, 0});
+      cp.push_back({x.Vh + static_cast<size_t>(x.r) * x.kc, x.kc, 1, u.Vtb, x.kc, x.k, x.kc, nullptr, 0});
+    }
+    HSS_TRY(launch_copies(cp, s, ar));
+  }
+  ar.release(s);
+  return e;
+}
+
+}  // namespace hss

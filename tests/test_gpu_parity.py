@@ -454,3 +454,31 @@ def test_full_size_gauss20k_matches_oracle(P):
         if i not in skip:
             assert abs(r3[i][2] - ro[i][0]) <= max(2, 0.05 * ro[i][0]), (i, r3[i], ro[i])
     assert _probe_error(P, h3, A) <= 2 * max(e_or, wl["rtol"])
+
+
+# ------------------------------------------------ ULV of large nodes (blocked path)
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_ulv_large_nodes_match_dense_solve(P, dtype):
+    """Leaves of 512 and ranks of 200 put every node (and the root LU) on the
+    blocked multi-kernel path; the solution must match a dense solve and the
+    oracle's ULV solution."""
+    n, leaf, rank = 2048, 512, 200
+    A, _ = W.random_hss(n, leaf, rank, seed=31, diag_shift=40.0)
+    At = torch.tensor(A, dtype=dtype, device=DEV)
+    A64 = At.cpu().numpy().astype(np.float64)
+    rtol = 1e-12 if dtype == torch.float64 else 1e-6
+    h = P.hss_compress(At, leaf_size=leaf, rtol=rtol, d0=256, d_step=128, seed=8,
+                       sample_mode="native" if dtype == torch.float64 else "bf16x3")
+    ranks = P.hss_node_ranks(h)
+    assert max(max(kr, kc) for _, _, kr, kc in ranks[1:]) >= 160   # large nodes present
+    P.hss_factor(h)
+    b = np.random.default_rng(5).standard_normal((n, 3))
+    xs = P.hss_solve(h, torch.tensor(b, dtype=dtype, device=DEV)).cpu().numpy().astype(np.float64)
+    xd = np.linalg.solve(A64, b)
+    if dtype == torch.float64:
+        np.testing.assert_allclose(xs, xd, rtol=0, atol=1e-8 * np.abs(xd).max())
+    else:
+        ho = O.compress(A64, rtol, leaf_size=leaf, d0=256, d_step=128, seed=8)
+        O.ulv_factor(ho)
+        xo = O.ulv_solve(ho, b)
+        assert _rel(A64 @ xs, b) <= 10 * max(_rel(A64 @ xo, b), 1e-6)
