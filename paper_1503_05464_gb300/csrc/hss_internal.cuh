@@ -232,7 +232,7 @@ struct GemmItem {
   const void* M;         // T or double (see m_is_f64)
   int64_t ldm;
   int32_t m_trans;       // 0: M[j*ldm+l], 1: M[l*ldm+j]
-  int32_t m_is_f64;
+  int32_t m_is_f64;      // 0: M has type T, 1: double, 2: float
   T sign;
   int32_t z_trans;       // 0: Z row l, column c; 1: Z row c, column l (rows of Z are columns)
 };

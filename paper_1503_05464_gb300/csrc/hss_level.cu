@@ -28,6 +28,7 @@ __device__ __forceinline__ const T* src_row(const RowSrc<T>& s, int r) {
 template <typename T>
 __device__ __forceinline__ T mat_at(const GemmItem<T>& it, int j, int l) {
   int64_t off = it.m_trans ? (int64_t)l * it.ldm + j : (int64_t)j * it.ldm + l;
+  if (it.m_is_f64 == 2) return (T)(reinterpret_cast<const float*>(it.M)[off]);
   return it.m_is_f64 ? (T)(reinterpret_cast<const double*>(it.M)[off])
                      : reinterpret_cast<const T*>(it.M)[off];
 }

@@ -71,6 +71,7 @@ struct UlvNode {
   double* Dtil = nullptr;   // k x k
   double* Vtt = nullptr;    // r x kc
   double* Vtb = nullptr;    // k x kc
+  double* T = nullptr;      // large nodes: compact WY factors, ceil(r/32) blocks of 32 x 32
   double* D = nullptr;      // working D_tau (m x m), freed after factorization
 };
 
@@ -93,6 +94,17 @@ struct UlvFactors {
 };
 
 Err finalize_generators(hss_s* h, cudaStream_t s);
+
+// per-node buffers of a solve (all FP64, nrhs columns): b (m), btb (k),
+// y (r), z (kc), x (m rows)
+struct UlvBufs {
+  double *b = nullptr, *btb = nullptr, *y = nullptr, *z = nullptr, *x = nullptr;
+};
+// one large child of the downward sweep and its part of the parent's x
+struct DownBig {
+  int child;
+  const double* xp;
+};
 void fill_info(hss_s* h);
 
 }  // namespace hss

@@ -23,6 +23,10 @@ namespace hss {
 
 size_t ulv_big_min_m();
 Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaStream_t s);
+Err ulv_solve_up_big(hss_s* h, const std::vector<int>& ids, const std::vector<UlvBufs>& bufs,
+                     const void* B, int64_t ldb, int nr, cudaStream_t s);
+Err ulv_solve_down_big(hss_s* h, const std::vector<DownBig>& kids, const std::vector<UlvBufs>& bufs,
+                       int nr, void* X, int64_t ldx, cudaStream_t s);
 
 namespace {
 
@@ -488,6 +492,7 @@ extern "C" hss_status hss_factor(hss_t h, void* stream) {
     int r = u.m - u.k;
     tot += (size_t)r * u.m + r + (size_t)r * r + (size_t)u.k * r + (size_t)u.k * u.k +
            (size_t)r * u.kc + (size_t)u.k * u.kc;
+    if ((size_t)u.m >= ulv_big_min_m()) tot += (size_t)((r + 31) / 32) * 32 * 32;
   }
   double* blk = nullptr;
   Err e = dalloc_t(&blk, std::max<size_t>(tot, 1), s);
@@ -520,6 +525,8 @@ extern "C" hss_status hss_factor(hss_t h, void* stream) {
     u.Vtt = p;
     p += (size_t)r * u.kc;
     u.Vtb = p;
+    p += (size_t)u.k * u.kc;
+    if ((size_t)u.m >= ulv_big_min_m()) u.T = p;
   }
   int32_t* status = nullptr;
   e = dalloc_t(&status, 1, s);
@@ -665,9 +672,20 @@ extern "C" hss_status hss_solve(hss_t h, const void* B, int64_t ldb, int64_t nrh
   }
   double* buf = nullptr;
   Err e = dalloc_t(&buf, std::max<size_t>(tot, 1), s);
+  std::vector<UlvBufs> bufs(nn);
+  if (e.st == HSS_OK)
+    for (int id = 0; id < nn; ++id)
+      bufs[id] = {buf + ob[id], buf + obt[id], buf + oy[id], buf + oz[id], buf + ox[id]};
+  auto is_big = [&](int id) { return (size_t)F.nodes[id].m >= ulv_big_min_m(); };
   for (int depth = tr.maxdepth; depth >= 0 && e.st == HSS_OK; --depth) {
+    std::vector<int> big;
+    for (int id : tr.levels[depth])
+      if (is_big(id)) big.push_back(id);
+    e = ulv_solve_up_big(h, big, bufs, B, ldb, nr, s);
+    if (e.st != HSS_OK) break;
     std::vector<SolItem> items;
     for (int id : tr.levels[depth]) {
+      if (is_big(id)) continue;
       const TNode& nd = tr.nodes[id];
       const UlvNode& u = F.nodes[id];
       const NodeGen& g = h->gen[id];
@@ -717,6 +735,7 @@ extern "C" hss_status hss_solve(hss_t h, const void* B, int64_t ldb, int64_t nrh
       it.x = buf + ox[id];
       items.push_back(it);
     }
+    if (items.empty()) continue;
     SolItem* dev = nullptr;
     e = upload_and_launch(items, s, &dev);
     if (e.st == HSS_OK) {
@@ -733,12 +752,17 @@ extern "C" hss_status hss_solve(hss_t h, const void* B, int64_t ldb, int64_t nrh
   }
   for (int depth = 0; depth < tr.maxdepth && e.st == HSS_OK; ++depth) {
     std::vector<DownItem> items;
+    std::vector<DownBig> bigkids;
     for (int id : tr.levels[depth]) {
       const TNode& nd = tr.nodes[id];
       if (nd.c1 < 0) continue;
       const int ka = F.nodes[nd.c1].k;
       for (int side = 0; side < 2; ++side) {
         int c = side ? nd.c2 : nd.c1;
+        if (is_big(c)) {
+          bigkids.push_back({c, buf + ox[id] + (side ? (size_t)ka * nr : 0)});
+          continue;
+        }
         const UlvNode& u = F.nodes[c];
         const TNode& cn = tr.nodes[c];
         DownItem it{};
@@ -757,7 +781,8 @@ extern "C" hss_status hss_solve(hss_t h, const void* B, int64_t ldb, int64_t nrh
         items.push_back(it);
       }
     }
-    if (items.empty()) continue;
+    e = ulv_solve_down_big(h, bigkids, bufs, nr, X, ldx, s);
+    if (e.st != HSS_OK || items.empty()) continue;
     DownItem* dev = nullptr;
     e = upload_and_launch(items, s, &dev);
     if (e.st == HSS_OK) {

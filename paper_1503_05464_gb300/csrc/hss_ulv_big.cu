@@ -269,6 +269,81 @@ __global__ void lu_trsm_kernel(double* A, int m, int j0, int nbb) {
   }
 }
 
+// ------------------------------------------------------------ solve parts
+// Diagonal block of a blocked triangular solve: rows [i0, i0 + nbb) of X
+// (ld nr) against the block of the triangular matrix (ld ldl) at (i0, i0).
+struct TriItem {
+  const double* Lm;
+  int64_t ldl;
+  double* X;
+  int nr, i0, nbb, upper, unit;
+};
+
+__global__ void tri_block_kernel(const TriItem* items) {
+  __shared__ double Lb[NB * NB];
+  const TriItem it = items[blockIdx.x];
+  for (int e = threadIdx.x; e < it.nbb * it.nbb; e += blockDim.x) {
+    const int a = e / it.nbb, b = e % it.nbb;
+    Lb[a * NB + b] = it.Lm[static_cast<int64_t>(it.i0 + a) * it.ldl + it.i0 + b];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < it.nr; c += blockDim.x) {
+    double x[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a)
+      x[a] = a < it.nbb ? it.X[static_cast<int64_t>(it.i0 + a) * it.nr + c] : 0.0;
+    if (!it.upper) {
+#pragma unroll
+      for (int a = 0; a < NB; ++a) {
+        if (a >= it.nbb) break;
+        double v = x[a];
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+          if (b < a) v = fma(-Lb[a * NB + b], x[b], v);
+        x[a] = it.unit ? v : v / Lb[a * NB + a];
+      }
+    } else {
+#pragma unroll
+      for (int a = NB - 1; a >= 0; --a) {
+        if (a >= it.nbb) continue;
+        double v = x[a];
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+          if (b > a && b < it.nbb) v = fma(-Lb[a * NB + b], x[b], v);
+        x[a] = it.unit ? v : v / Lb[a * NB + a];
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < NB; ++a)
+      if (a < it.nbb) it.X[static_cast<int64_t>(it.i0 + a) * it.nr + c] = x[a];
+  }
+}
+
+// the root's row interchanges, in factorization order, one thread per column
+__global__ void apply_piv_kernel(double* x, const int32_t* piv, int m, int nr) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nr) return;
+  for (int i = 0; i < m; ++i) {
+    const int p = piv[i];
+    if (p != i) {
+      const double t = x[static_cast<int64_t>(i) * nr + c];
+      x[static_cast<int64_t>(i) * nr + c] = x[static_cast<int64_t>(p) * nr + c];
+      x[static_cast<int64_t>(p) * nr + c] = t;
+    }
+  }
+}
+
+// X[lo + i][c] = v[i][c] in the output dtype
+__global__ void store_rows_kernel(const double* v, int m, int nr, void* X, int64_t ldx, int lo,
+                                  int f64) {
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= static_cast<int64_t>(m) * nr) return;
+  const int i = static_cast<int>(e / nr), c = static_cast<int>(e % nr);
+  const int64_t o = static_cast<int64_t>(lo + i) * ldx + c;
+  if (f64) reinterpret_cast<double*>(X)[o] = v[e];
+  else reinterpret_cast<float*>(X)[o] = static_cast<float>(v[e]);
+}
+
 template <typename TI>
 Err upload(const std::vector<TI>& v, cudaStream_t s, Arena& ar, TI** out) {
   HSS_TRY(ar.alloc_t(out, std::max<size_t>(v.size(), 1), s));
@@ -375,7 +450,8 @@ Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaS
       HSS_TRY(ar.alloc_t(&x.Y, static_cast<size_t>(x.m) * NB, s));
       HSS_TRY(ar.alloc_t(&x.Y2, static_cast<size_t>(x.m) * NB, s));
       HSS_TRY(ar.alloc_t(&x.G, NB * NB, s));
-      HSS_TRY(ar.alloc_t(&x.Tall, static_cast<size_t>(std::max(npan, 1)) * NB * NB, s));
+      x.Tall = F.nodes[id].T;   // kept for the solve's Q^T
+      if (!x.Tall) HSS_TRY(ar.alloc_t(&x.Tall, static_cast<size_t>(std::max(npan, 1)) * NB * NB, s));
       HSS_TRY(ar.alloc_t(&x.Z1, static_cast<size_t>(NB) * std::max(x.kc, 1), s));
       HSS_TRY(ar.alloc_t(&x.Z2, static_cast<size_t>(NB) * std::max(x.kc, 1), s));
     }
@@ -583,6 +659,235 @@ Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaS
   }
   ar.release(s);
   return e;
+}
+
+namespace {
+
+// X <- tri^{-1} X for a batch of (matrix, X) pairs of order ord[i], blocked:
+// NB-row diagonal blocks, then one GEMM per block for the rest
+Err blocked_trsm(const std::vector<TriItem>& base, const std::vector<int>& ord, bool upper,
+                 cudaStream_t s, Arena& ar) {
+  int maxo = 0;
+  for (int o : ord) maxo = std::max(maxo, o);
+  const int nblk = (maxo + NB - 1) / NB;
+  for (int q = 0; q < nblk; ++q) {
+    std::vector<TriItem> tri;
+    std::vector<GemmItem<double>> gm;
+    for (size_t t = 0; t < base.size(); ++t) {
+      const int o = ord[t];
+      const int nbl = (o + NB - 1) / NB;
+      if (q >= nbl) continue;
+      const int blk = upper ? nbl - 1 - q : q;
+      const int i0 = blk * NB, nbb = std::min(NB, o - i0);
+      TriItem ti = base[t];
+      ti.i0 = i0;
+      ti.nbb = nbb;
+      tri.push_back(ti);
+      const int nr = ti.nr;
+      if (!upper && i0 + nbb < o) {
+        double* out = ti.X + static_cast<size_t>(i0 + nbb) * nr;
+        gm.push_back(gemm(out, nr, o - i0 - nbb, nr, nbb,
+                          ti.Lm + static_cast<size_t>(i0 + nbb) * ti.ldl + i0, ti.ldl, 0,
+                          ti.X + static_cast<size_t>(i0) * nr, nr, 0, out, nr, -1.0));
+      }
+      if (upper && i0 > 0) {
+        gm.push_back(gemm(ti.X, nr, i0, nr, nbb, ti.Lm + i0, ti.ldl, 0,
+                          ti.X + static_cast<size_t>(i0) * nr, nr, 0, ti.X, nr, -1.0));
+      }
+    }
+    if (tri.empty()) continue;
+    TriItem* dt = nullptr;
+    HSS_TRY(upload(tri, s, ar, &dt));
+    tri_block_kernel<<<static_cast<unsigned>(tri.size()), 64, 0, s>>>(dt);
+    HSS_TRY(check_launch("tri_block_kernel"));
+    HSS_TRY(run_gemms(gm, s, ar));
+  }
+  return ok();
+}
+
+}  // namespace
+
+// Upward sweep of the solve (Algorithm 4) for the large nodes `ids` of one
+// level; buffers of every node are given by `bufs`.
+Err ulv_solve_up_big(hss_s* h, const std::vector<int>& ids, const std::vector<UlvBufs>& bufs,
+                     const void* B, int64_t ldb, int nr, cudaStream_t s) {
+  if (ids.empty()) return ok();
+  const Tree& tr = h->tree;
+  const UlvFactors& F = h->ulv;
+  const int f64 = h->dtype == HSS_F64;
+  const size_t esz = f64 ? 8 : 4;
+  Arena ar{(size_t)4 << 20};
+  // b: leaf rows of B, or the children's contributions
+  {
+    std::vector<CopyItem> cp;
+    std::vector<GemmItem<double>> g1, g2;
+    for (int id : ids) {
+      const TNode& nd = tr.nodes[id];
+      const UlvNode& u = F.nodes[id];
+      const UlvBufs& me = bufs[id];
+      if (nd.c1 < 0) {
+        cp.push_back({static_cast<const char*>(B) + static_cast<size_t>(nd.lo) * ldb * esz, ldb, f64,
+                      me.b, nr, u.m, nr, nullptr, 0});
+        continue;
+      }
+      const NodeGen& g = h->gen[id];
+      const UlvNode& a = F.nodes[nd.c1];
+      const UlvNode& b = F.nodes[nd.c2];
+      const UlvBufs& ba = bufs[nd.c1];
+      const UlvBufs& bb = bufs[nd.c2];
+      const int ra = a.m - a.k, rb = b.m - b.k;
+      double* top = me.b;
+      double* bot = me.b + static_cast<size_t>(a.k) * nr;
+      g1.push_back(gemm(top, nr, a.k, nr, ra, a.WbQt, ra, 0, ba.y, nr, 0, ba.btb, nr, -1.0));
+      GemmItem<double> b21 = gemm(bot, nr, b.k, nr, a.kc, nullptr, a.kc, 0, ba.z, nr, 0, bb.btb, nr, -1.0);
+      b21.M = g.B21;
+      b21.m_is_f64 = f64 ? 1 : 2;
+      g1.push_back(b21);
+      GemmItem<double> b12 = gemm(top, nr, a.k, nr, b.kc, nullptr, b.kc, 0, bb.z, nr, 0, top, nr, -1.0);
+      b12.M = g.B12;
+      b12.m_is_f64 = f64 ? 1 : 2;
+      g2.push_back(b12);
+      g2.push_back(gemm(bot, nr, b.k, nr, rb, b.WbQt, rb, 0, bb.y, nr, 0, bot, nr, -1.0));
+    }
+    HSS_TRY(launch_copies(cp, s, ar));
+    HSS_TRY(run_gemms(g1, s, ar));
+    HSS_TRY(run_gemms(g2, s, ar));
+  }
+  // root: x = U^{-1} L^{-1} P b
+  if (ids.size() == 1 && ids[0] == 0) {
+    const UlvBufs& me = bufs[0];
+    const int m = F.root_m;
+    HSS_CUDA_TRY(cudaMemcpyAsync(me.x, me.b, sizeof(double) * m * nr, cudaMemcpyDeviceToDevice, s));
+    apply_piv_kernel<<<(nr + 127) / 128, 128, 0, s>>>(me.x, F.root_piv, m, nr);
+    HSS_TRY(check_launch("apply_piv_kernel"));
+    std::vector<TriItem> base{{F.root_lu, m, me.x, nr, 0, 0, 0, 1}};
+    std::vector<int> ord{m};
+    HSS_TRY(blocked_trsm(base, ord, false, s, ar));
+    base[0].upper = 1;
+    base[0].unit = 0;
+    HSS_TRY(blocked_trsm(base, ord, true, s, ar));
+    ar.release(s);
+    return ok();
+  }
+  // btilde = Omega b; y = L^{-1} btilde_t; z = Vtt^T y (+ V^T [z1; z2])
+  {
+    std::vector<GemmItem<double>> gm;
+    std::vector<TriItem> base;
+    std::vector<int> ord;
+    for (int id : ids) {
+      const UlvNode& u = F.nodes[id];
+      const NodeGen& g = h->gen[id];
+      const UlvBufs& me = bufs[id];
+      const int r = u.m - u.k;
+      GemmItem<double> top = gemm(me.y, nr, r, nr, u.k, g.Er, u.k, 0, me.b, nr, 0, me.b, nr, -1.0);
+      top.Z.map = g.permr;
+      top.X.map = g.permr + u.k;
+      gm.push_back(top);
+      GemmItem<double> bot = gemm(me.btb, nr, u.k, nr, 0, nullptr, 1, 0, nullptr, 1, 0, me.b, nr, 1.0);
+      bot.X.map = g.permr;
+      gm.push_back(bot);
+      if (r > 0) {
+        base.push_back({u.L, r, me.y, nr, 0, 0, 0, 0});
+        ord.push_back(r);
+      }
+    }
+    HSS_TRY(run_gemms(gm, s, ar));
+    HSS_TRY(blocked_trsm(base, ord, false, s, ar));
+  }
+  {
+    std::vector<GemmItem<double>> g1, g2;
+    for (int id : ids) {
+      const TNode& nd = tr.nodes[id];
+      const UlvNode& u = F.nodes[id];
+      const NodeGen& g = h->gen[id];
+      const UlvBufs& me = bufs[id];
+      const int r = u.m - u.k;
+      if (u.kc == 0) continue;
+      GemmItem<double> z = gemm(me.z, nr, u.kc, nr, r, u.Vtt, u.kc, 1, me.y, nr, 0, nullptr, 0, 1.0);
+      if (nd.c1 >= 0) {
+        const UlvNode& a = F.nodes[nd.c1];
+        z.X.p0 = bufs[nd.c1].z;
+        z.X.ld0 = nr;
+        z.X.p1 = bufs[nd.c2].z;
+        z.X.ld1 = nr;
+        z.X.split = a.kc;
+        z.X.map = g.permc;
+        GemmItem<double> ez = gemm(me.z, nr, u.kc, nr, g.mc - u.kc, g.Ec, u.kc, 1, nullptr, nr, 0,
+                                   me.z, nr, 1.0);
+        ez.Z.p0 = bufs[nd.c1].z;
+        ez.Z.ld0 = nr;
+        ez.Z.p1 = bufs[nd.c2].z;
+        ez.Z.ld1 = nr;
+        ez.Z.split = a.kc;
+        ez.Z.map = g.permc + u.kc;
+        g2.push_back(ez);
+      }
+      g1.push_back(z);
+    }
+    HSS_TRY(run_gemms(g1, s, ar));
+    HSS_TRY(run_gemms(g2, s, ar));
+  }
+  ar.release(s);
+  return ok();
+}
+
+// Downward sweep for large children: v = [y; x_parent part], v <- Q^T v with
+// Q^T = H_0 H_1 ... H_{r-1} applied panel by panel from the last, then the
+// leaves' rows of X.
+Err ulv_solve_down_big(hss_s* h, const std::vector<DownBig>& kids, const std::vector<UlvBufs>& bufs,
+                       int nr, void* X, int64_t ldx, cudaStream_t s) {
+  if (kids.empty()) return ok();
+  const Tree& tr = h->tree;
+  const UlvFactors& F = h->ulv;
+  const int f64 = h->dtype == HSS_F64;
+  Arena ar{(size_t)4 << 20};
+  int maxr = 0;
+  std::vector<double*> z1(kids.size()), z2(kids.size());
+  for (size_t t = 0; t < kids.size(); ++t) {
+    const DownBig& d = kids[t];
+    const UlvNode& u = F.nodes[d.child];
+    const UlvBufs& me = bufs[d.child];
+    const int r = u.m - u.k;
+    maxr = std::max(maxr, r);
+    HSS_CUDA_TRY(cudaMemcpyAsync(me.x, me.y, sizeof(double) * r * nr, cudaMemcpyDeviceToDevice, s));
+    HSS_CUDA_TRY(cudaMemcpyAsync(me.x + static_cast<size_t>(r) * nr, d.xp,
+                                 sizeof(double) * u.k * nr, cudaMemcpyDeviceToDevice, s));
+    HSS_TRY(ar.alloc_t(&z1[t], static_cast<size_t>(NB) * nr, s));
+    HSS_TRY(ar.alloc_t(&z2[t], static_cast<size_t>(NB) * nr, s));
+  }
+  const int npmax = (maxr + NB - 1) / NB;
+  for (int q = 0; q < npmax; ++q) {
+    std::vector<GemmItem<double>> g1, g2, g3;
+    for (size_t t = 0; t < kids.size(); ++t) {
+      const UlvNode& u = F.nodes[kids[t].child];
+      const UlvBufs& me = bufs[kids[t].child];
+      const int r = u.m - u.k, m = u.m;
+      const int np = (r + NB - 1) / NB;
+      if (q >= np) continue;
+      const int p = np - 1 - q;
+      const int i0 = p * NB, nbb = std::min(NB, r - i0);
+      const double* vp = u.hv + static_cast<size_t>(i0) * m + i0;
+      const double* T = u.T + static_cast<size_t>(p) * NB * NB;
+      double* v = me.x + static_cast<size_t>(i0) * nr;
+      g1.push_back(gemm(z1[t], nr, nbb, nr, m - i0, vp, m, 0, v, nr, 0, nullptr, 0, 1.0));
+      g2.push_back(gemm(z2[t], nr, nbb, nr, nbb, T, NB, 0, z1[t], nr, 0, nullptr, 0, 1.0));
+      g3.push_back(gemm(v, nr, m - i0, nr, nbb, vp, m, 1, z2[t], nr, 0, v, nr, -1.0));
+    }
+    HSS_TRY(run_gemms(g1, s, ar));
+    HSS_TRY(run_gemms(g2, s, ar));
+    HSS_TRY(run_gemms(g3, s, ar));
+  }
+  for (const DownBig& d : kids) {
+    const TNode& cn = tr.nodes[d.child];
+    if (cn.c1 >= 0) continue;
+    const UlvNode& u = F.nodes[d.child];
+    const int64_t total = static_cast<int64_t>(u.m) * nr;
+    store_rows_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
+        bufs[d.child].x, u.m, nr, X, ldx, cn.lo, f64);
+    HSS_TRY(check_launch("store_rows_kernel"));
+  }
+  ar.release(s);
+  return ok();
 }
 
 }  // namespace hss
