@@ -15,17 +15,18 @@
 // for the column product.  R is bfloat16-exact (its Gaussian entries are
 // rounded to bfloat16 when drawn), so it needs no split.
 //
-// Pipeline (warp-specialised, mbarrier hand-offs, 512 threads):
+// Pipeline (warp-specialised, mbarrier hand-offs, 576 threads):
 //   warp 0       TMA producer: FP32 half-tiles of A (128 x 32, 128-byte
 //                swizzle) into a 4-stage ring; R_J (64 rows) per tile and
 //                R_p (128 rows) per panel segment, bfloat16;
-//   warps 4-7    converters: one row each; apply the leaf mask (the index
-//                range of the row's leaf), split into the bfloat16 planes
-//                (double-buffered, swizzled operand layout);
+//   warps 2-9    converters: two threads per row, one per half-tile; apply
+//                the leaf mask (the index range of the row's leaf), split into
+//                the bfloat16 planes (double-buffered, swizzled operand
+//                layout); two warps per scheduler keep the ALUs fed;
 //   warp 1       MMA issuer (one thread): tcgen05.mma into TMEM;
-//   warps 8-11   column drain: the column product of each tile (TMEM, double
+//   warps 10-13  column drain: the column product of each tile (TMEM, double
 //                buffered) to a partial slab Sc_part[p][j][c];
-//   warps 12-15  row fold: the row accumulator (TMEM, double buffered, one
+//   warps 14-17  row fold: the row accumulator (TMEM, double buffered, one
 //                buffer per group of FOLD tiles) is added into a running FP32
 //                sum in TMEM; the sum is flushed to a row slab at the end of
 //                every flush group of at most 16 tiles and of every segment.
@@ -60,7 +61,7 @@ constexpr int CMAX = 128;        // sample columns per sweep
 constexpr int ASTAGES = 4;       // FP32 half-tile ring
 constexpr int FOLD = 2;          // tiles per row accumulator buffer
 constexpr int FLUSH_MAX = 16;    // tiles per flush group of the running row sum, at most
-constexpr int THREADS = 512;
+constexpr int THREADS = 576;
 constexpr long long WAIT_LIMIT = 1ll << 32;   // clock cycles (about 2 s)
 
 constexpr uint32_t A_HALF_BYTES = BM * 32 * 4;   // 16 KB
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(bar(B_AEMPTY + i), BM);
     }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(bar(B_PFULL + i), BM);
+      mbar_init(bar(B_PFULL + i), 2 * BM);
       mbar_init(bar(B_PEMPTY + i), 1);
       mbar_init(bar(B_RJFULL + i), 1);
       mbar_init(bar(B_RJEMPTY + i), 1);
@@ -283,10 +284,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       volatile int never = 0;
       mbar_wait(bar(B_DRAIN), 0, &never, g.err, 10, WAIT_LIMIT);
     }
-  } else if (warp >= 4 && warp < 8) {
+  } else if (warp >= 2 && warp < 10) {
     // -------------------------------------------------------- converters
-    const int row = tid - 128;
-    int a_cnt = 0, tl = 0;
+    const int ct = tid - 64;
+    const int row = ct & (BM - 1), h = ct >> 7;   // row of the tile, half-tile
+    int tl = 0;
     int mlo = 0, mhi = 0;   // the leaf of this thread's row: columns [mlo, mhi) are masked
     for (long long t = tb; t < te; ++t) {
       const int p = static_cast<int>(t / ntc), J = static_cast<int>(t % ntc);
@@ -303,70 +305,63 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       if (!mbar_wait(bar(B_PEMPTY + ps), (u & 1) ^ 1, abort_flag, g.err, 11, WAIT_LIMIT)) break;
       const int j0 = J * BN;
-      const bool need_mask = mlo < j0 + BN && mhi > j0;
+      const int jb = j0 + h * 32;
+      const bool need_mask = mlo < jb + 32 && mhi > jb;
       uint8_t* pbase = sm + L::planes + ps * NT * PLANE_BYTES;
-      bool ok = true;
-      for (int h = 0; h < 2; ++h) {
-        const int s = a_cnt % ASTAGES, ua = a_cnt / ASTAGES;
-        if (!mbar_wait(bar(B_AFULL + s), ua & 1, abort_flag, g.err, 12, WAIT_LIMIT)) {
-          ok = false;
-          break;
-        }
-        const uint8_t* src = sm + L::a + s * A_HALF_BYTES;
-        float v[32];
+      const int a_idx = 2 * tl + h;
+      const int s = a_idx % ASTAGES, ua = a_idx / ASTAGES;
+      if (!mbar_wait(bar(B_AFULL + s), ua & 1, abort_flag, g.err, 12, WAIT_LIMIT)) break;
+      const uint8_t* src = sm + L::a + s * A_HALF_BYTES;
+      float v[32];
 #pragma unroll
-        for (int qd = 0; qd < 8; ++qd) {
-          const float4 x = *reinterpret_cast<const float4*>(src + sw128(row, qd * 16));
-          v[4 * qd] = x.x;
-          v[4 * qd + 1] = x.y;
-          v[4 * qd + 2] = x.z;
-          v[4 * qd + 3] = x.w;
-        }
-        mbar_arrive(bar(B_AEMPTY + s));
-        ++a_cnt;
-        if (need_mask) {
-          const int jb = j0 + h * 32;
+      for (int qd = 0; qd < 8; ++qd) {
+        const float4 x = *reinterpret_cast<const float4*>(src + sw128(row, qd * 16));
+        v[4 * qd] = x.x;
+        v[4 * qd + 1] = x.y;
+        v[4 * qd + 2] = x.z;
+        v[4 * qd + 3] = x.w;
+      }
+      mbar_arrive(bar(B_AEMPTY + s));
+      if (need_mask) {
 #pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const int j = jb + e;
-            if (j >= mlo && j < mhi) v[e] = 0.f;
-          }
-        }
-#pragma unroll
-        for (int qd = 0; qd < 4; ++qd) {
-          uint32_t hw[4], mw[4], lw[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float x0 = v[8 * qd + 2 * e], x1 = v[8 * qd + 2 * e + 1];
-            const __nv_bfloat162 hv = __floats2bfloat162_rn(x0, x1);
-            const float2 hf = __bfloat1622float2(hv);
-            const float r0 = x0 - hf.x, r1 = x1 - hf.y;
-            const __nv_bfloat162 mv = __floats2bfloat162_rn(r0, r1);
-            hw[e] = *reinterpret_cast<const uint32_t*>(&hv);
-            mw[e] = *reinterpret_cast<const uint32_t*>(&mv);
-            if (NT == 3) {
-              const float2 mf = __bfloat1622float2(mv);
-              const __nv_bfloat162 lv = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
-              lw[e] = *reinterpret_cast<const uint32_t*>(&lv);
-            }
-          }
-          const uint32_t off = sw128(row, h * 64 + qd * 16);
-          *reinterpret_cast<uint4*>(pbase + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-          *reinterpret_cast<uint4*>(pbase + PLANE_BYTES + off) =
-              make_uint4(mw[0], mw[1], mw[2], mw[3]);
-          if (NT == 3)
-            *reinterpret_cast<uint4*>(pbase + 2 * PLANE_BYTES + off) =
-                make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        for (int e = 0; e < 32; ++e) {
+          const int j = jb + e;
+          if (j >= mlo && j < mhi) v[e] = 0.f;
         }
       }
-      if (!ok) break;
+#pragma unroll
+      for (int qd = 0; qd < 4; ++qd) {
+        uint32_t hw[4], mw[4], lw[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float x0 = v[8 * qd + 2 * e], x1 = v[8 * qd + 2 * e + 1];
+          const __nv_bfloat162 hv = __floats2bfloat162_rn(x0, x1);
+          const float2 hf = __bfloat1622float2(hv);
+          const float r0 = x0 - hf.x, r1 = x1 - hf.y;
+          const __nv_bfloat162 mv = __floats2bfloat162_rn(r0, r1);
+          hw[e] = *reinterpret_cast<const uint32_t*>(&hv);
+          mw[e] = *reinterpret_cast<const uint32_t*>(&mv);
+          if (NT == 3) {
+            const float2 mf = __bfloat1622float2(mv);
+            const __nv_bfloat162 lv = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+            lw[e] = *reinterpret_cast<const uint32_t*>(&lv);
+          }
+        }
+        const uint32_t off = sw128(row, h * 64 + qd * 16);
+        *reinterpret_cast<uint4*>(pbase + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(pbase + PLANE_BYTES + off) =
+            make_uint4(mw[0], mw[1], mw[2], mw[3]);
+        if (NT == 3)
+          *reinterpret_cast<uint4*>(pbase + 2 * PLANE_BYTES + off) =
+              make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
       fence_proxy_async();
       mbar_arrive(bar(B_PFULL + ps));
       ++tl;
     }
-  } else if (warp >= 8 && warp < 12) {
+  } else if (warp >= 10 && warp < 14) {
     // ------------------------------------------------------ column drain
-    const int e = tid - 256;                    // TMEM lane: sample column
+    const int e = (warp & 3) * 32 + lane;       // TMEM lane: sample column
     const uint32_t loff = static_cast<uint32_t>((warp & 3) * 32) << 16;
     const int n = g.n, c = g.c;
     int tl = 0;
@@ -390,9 +385,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       ++tl;
     }
-  } else if (warp >= 12) {
+  } else if (warp >= 14) {
     // --------------------------------------------------------- row fold
-    const int e = tid - 384;                    // TMEM lane: panel row
+    const int e = (warp & 3) * 32 + lane;       // TMEM lane: panel row
     const uint32_t loff = static_cast<uint32_t>((warp & 3) * 32) << 16;
     const int c = g.c;
     const int nch = (c + 31) / 32;
@@ -463,14 +458,28 @@ __device__ __forceinline__ void neumaier_add(float& s, float& c, float x) {
   s = t;
 }
 
+// side1[p][grp] = 1 when a CTA range starts inside flush group grp of panel p
+// (the group then has a second slot)
+__global__ void row_slot_flags_kernel(int npanel, int ntc, long long T, int P, int gs,
+                                      int ngroups, uint8_t* side1) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= npanel * ngroups) return;
+  const int p = idx / ngroups, grp = idx % ngroups;
+  const long long t0 = static_cast<long long>(p) * ntc + static_cast<long long>(grp) * gs;
+  const long long t1 = static_cast<long long>(p) * ntc + min((grp + 1) * gs, ntc) - 1;
+  side1[idx] = tile_owner(t0, T, P) != tile_owner(t1, T, P) ? 1 : 0;
+}
+
 // Sc[j, c0 + cc] = sum over panels of Sc_part[p][j][cc] (panel order, one
 // thread per V consecutive columns cc);
-// Sr[i, c0 + cc] = sum over the flush slots of row i's panel, in order.
+// Sr[i, c0 + cc] = sum over the flush slots of row i's panel, in order (one
+// thread per (panel, cc, row), rows fastest: the slot reads are contiguous).
 template <int V>
 __global__ void sample_tc_reduce_kernel(const float* __restrict__ sc_part,
-                                        const float* __restrict__ sr_part, int n, int c,
-                                        int npanel, int ntc, long long T, int P, int gs,
-                                        int ngroups, float* Sr, float* Sc, long long lds) {
+                                        const float* __restrict__ sr_part,
+                                        const uint8_t* __restrict__ side1, int n, int c,
+                                        int npanel, int ngroups, float* Sr, float* Sc,
+                                        long long lds) {
   const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int cv = c / V;
   const long long ncv = static_cast<long long>(n) * cv;
@@ -506,18 +515,19 @@ __global__ void sample_tc_reduce_kernel(const float* __restrict__ sc_part,
       for (int x = 0; x < V; ++x) neumaier_add(s[x], k[x], src[stride * p + x]);
 #pragma unroll
     for (int x = 0; x < V; ++x) Sc[static_cast<size_t>(j) * lds + cc + x] = s[x] + k[x];
-  } else if (idx < ncv + static_cast<long long>(n) * c) {
+  } else if (idx < ncv + static_cast<long long>(npanel) * c * BM) {
     const long long r = idx - ncv;
-    const int i = static_cast<int>(r / c), cc = static_cast<int>(r % c);
-    const int p = i / BM, row = i % BM;
+    const int row = static_cast<int>(r % BM);
+    const long long pc = r / BM;
+    const int cc = static_cast<int>(pc % c), p = static_cast<int>(pc / c);
+    const int i = p * BM + row;
+    if (i >= n) return;
     float s = 0.f, k = 0.f;
     for (int grp = 0; grp < ngroups; ++grp) {
-      const long long t0 = static_cast<long long>(p) * ntc + static_cast<long long>(grp) * gs;
-      const long long t1 = static_cast<long long>(p) * ntc + min((grp + 1) * gs, ntc) - 1;
       const size_t slot = (static_cast<size_t>(p) * ngroups + grp) * 2;
-      neumaier_add(s, k, sr_part[((slot * c) + cc) * BM + row]);
-      if (tile_owner(t0, T, P) != tile_owner(t1, T, P))   // a CTA range starts inside
-        neumaier_add(s, k, sr_part[(((slot + 1) * c) + cc) * BM + row]);
+      neumaier_add(s, k, __ldcs(sr_part + ((slot * c) + cc) * BM + row));
+      if (side1[p * ngroups + grp])
+        neumaier_add(s, k, __ldcs(sr_part + (((slot + 1) * c) + cc) * BM + row));
     }
     Sr[static_cast<size_t>(i) * lds + cc] = s + k;
   }
@@ -616,7 +626,8 @@ size_t sample_tc_scratch_bytes(int64_t n, int64_t ncols, int sms) {
   return align256(static_cast<size_t>(n) * cpad * 2) +
          align256(static_cast<size_t>(pl.npanel) * n * c * 4) +
          align256(static_cast<size_t>(pl.npanel) * pl.ngroups * 2 * c * BM * 4) +
-         2 * align256(static_cast<size_t>(n) * 4) + 256;
+         2 * align256(static_cast<size_t>(n) * 4) +
+         align256(static_cast<size_t>(pl.npanel) * pl.ngroups) + 256;
 }
 
 bool sample_tc_supported(const float* A, int64_t n, int64_t lda, int mode) {
@@ -669,6 +680,8 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     base += align256(static_cast<size_t>(n) * 4);
     int32_t* leaf_hi = reinterpret_cast<int32_t*>(base);
     base += align256(static_cast<size_t>(n) * 4);
+    uint8_t* side1 = base;
+    base += align256(static_cast<size_t>(pl.npanel) * pl.ngroups);
     int* err = reinterpret_cast<int*>(base);
     if (leaf_of != nullptr && w == 0) {
       leaf_bounds_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
@@ -708,16 +721,23 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     else
       sample_tc_kernel<2><<<pl.P, THREADS, smem, s>>>(tmA, tmRJ, tmRI, g);
     HSS_TRY(check_launch("sample_tc_kernel"));
+    {
+      const int nf = pl.npanel * pl.ngroups;
+      row_slot_flags_kernel<<<(nf + 255) / 256, 256, 0, s>>>(pl.npanel, pl.ntc, pl.T, pl.P, pl.gs,
+                                                              pl.ngroups, side1);
+      HSS_TRY(check_launch("row_slot_flags_kernel"));
+    }
+    const long long nrow = static_cast<long long>(pl.npanel) * c * BM;
     if (c % 4 == 0) {
-      const long long nred = static_cast<long long>(n) * (c / 4) + static_cast<long long>(n) * c;
+      const long long nred = static_cast<long long>(n) * (c / 4) + nrow;
       sample_tc_reduce_kernel<4><<<static_cast<unsigned>((nred + 255) / 256), 256, 0, s>>>(
-          scp, srp, static_cast<int>(n), c, pl.npanel, pl.ntc, pl.T, pl.P, pl.gs, pl.ngroups,
-          Sr + c0 + done, Sc + c0 + done, lds);
+          scp, srp, side1, static_cast<int>(n), c, pl.npanel, pl.ngroups, Sr + c0 + done,
+          Sc + c0 + done, lds);
     } else {
-      const long long nred = 2ll * n * c;
+      const long long nred = static_cast<long long>(n) * c + nrow;
       sample_tc_reduce_kernel<1><<<static_cast<unsigned>((nred + 255) / 256), 256, 0, s>>>(
-          scp, srp, static_cast<int>(n), c, pl.npanel, pl.ntc, pl.T, pl.P, pl.gs, pl.ngroups,
-          Sr + c0 + done, Sc + c0 + done, lds);
+          scp, srp, side1, static_cast<int>(n), c, pl.npanel, pl.ngroups, Sr + c0 + done,
+          Sc + c0 + done, lds);
     }
     HSS_TRY(check_launch("sample_tc_reduce_kernel"));
     int herr = 0;
