@@ -25,7 +25,7 @@
 //                layout); two warps per scheduler keep the ALUs fed;
 //   warp 1       MMA issuer (one thread): tcgen05.mma into TMEM;
 //   warps 10-13  column drain: the column product of each tile (TMEM, double
-//                buffered) to a partial slab Sc_part[p][j][c];
+//                buffered) to a partial slab Sc_part[p][c][j] (j contiguous);
 //   warps 14-17  row fold: the row accumulator (TMEM, double buffered, one
 //                buffer per group of FOLD tiles) is added into a running FP32
 //                sum in TMEM; the sum is flushed to a row slab at the end of
@@ -104,7 +104,8 @@ struct TcArgs {
   const int32_t* leaf_of;    // leaf id of each index (null: no mask)
   const int32_t* leaf_lo;    // first index of each leaf id
   const int32_t* leaf_hi;    // one past the last index of each leaf id
-  float* sc_part;    // [npanel][n][c]
+  float* sc_part;    // [npanel][c][npad], npad = column tiles x 64
+  int npad;
   float* sr_part;    // [npanel][ngroups][2][c][128]
   int* err;
 };
@@ -321,7 +322,6 @@ __global__ void __launch_bounds__(THREADS, 1)
         v[4 * qd + 2] = x.z;
         v[4 * qd + 3] = x.w;
       }
-      mbar_arrive(bar(B_AEMPTY + s));
       if (need_mask) {
 #pragma unroll
         for (int e = 0; e < 32; ++e) {
@@ -355,8 +355,14 @@ __global__ void __launch_bounds__(THREADS, 1)
           *reinterpret_cast<uint4*>(pbase + 2 * PLANE_BYTES + off) =
               make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
+      // the fence orders this thread's shared-memory accesses (the stage reads
+      // and the plane writes) before the async-proxy accesses that the two
+      // arrivals release: the tensor core's plane reads and the next TMA copy
+      // into the stage (without it a late stage read can return the next
+      // tile's data)
       fence_proxy_async();
       mbar_arrive(bar(B_PFULL + ps));
+      mbar_arrive(bar(B_AEMPTY + s));
       ++tl;
     }
   } else if (warp >= 10 && warp < 14) {
@@ -369,6 +375,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int p = static_cast<int>(t / ntc), J = static_cast<int>(t % ntc);
       const int b = tl & 1, u = tl >> 1;
       if (!mbar_wait(bar(B_CFULL + b), u & 1, abort_flag, g.err, 13, WAIT_LIMIT)) break;
+      __syncwarp();   // tcgen05.ld is warp-aligned: reconverge after the per-lane wait
       fence_after();
       float v[64];
       tmem_ld32(tbase + loff + T_COL + 64 * b, v);
@@ -377,11 +384,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       fence_before();
       mbar_arrive(bar(B_CEMPTY + b));
       if (e < c) {
-        float* dst = g.sc_part + (static_cast<size_t>(p) * n + static_cast<size_t>(J) * BN) * c + e;
-        const int jn = min(BN, n - J * BN);
+        // slab row (p, e) holds the tile's 64 values contiguously: 16 aligned
+        // 16-byte stores (rows are padded to whole tiles; past n the TMA fill
+        // is zero, so the pad holds zeros, which the reduction reads and drops)
+        float4* dst = reinterpret_cast<float4*>(
+            g.sc_part + (static_cast<size_t>(p) * c + e) * g.npad + static_cast<size_t>(J) * BN);
 #pragma unroll
-        for (int jj = 0; jj < BN; ++jj)
-          if (jj < jn) dst[static_cast<size_t>(jj) * c] = v[jj];
+        for (int q4 = 0; q4 < BN / 4; ++q4)
+          dst[q4] = make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
       }
       ++tl;
     }
@@ -403,6 +413,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       since = 0;
       const int rb = fg & 1;
       if (!mbar_wait(bar(B_RFULL + rb), (fg >> 1) & 1, abort_flag, g.err, 14, WAIT_LIMIT)) break;
+      __syncwarp();
       fence_after();
       for (int ch = 0; ch < nch; ++ch) {
         float a[32], s[32];
@@ -444,6 +455,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   fence_before();
   __syncthreads();
   if (warp == 1) {
+    __syncwarp();
     fence_after();
     tmem_dealloc(tbase, 512);
   }
@@ -470,51 +482,50 @@ __global__ void row_slot_flags_kernel(int npanel, int ntc, long long T, int P, i
   side1[idx] = tile_owner(t0, T, P) != tile_owner(t1, T, P) ? 1 : 0;
 }
 
-// Sc[j, c0 + cc] = sum over panels of Sc_part[p][j][cc] (panel order, one
-// thread per V consecutive columns cc);
+// Sc[j, c0 + cc] = sum over panels of Sc_part[p][cc][j] (panel order; one
+// thread per 4 consecutive j of one column cc, j fastest: 16-byte reads);
 // Sr[i, c0 + cc] = sum over the flush slots of row i's panel, in order (one
 // thread per (panel, cc, row), rows fastest: the slot reads are contiguous).
-template <int V>
 __global__ void sample_tc_reduce_kernel(const float* __restrict__ sc_part,
                                         const float* __restrict__ sr_part,
-                                        const uint8_t* __restrict__ side1, int n, int c,
-                                        int npanel, int ngroups, float* Sr, float* Sc,
+                                        const uint8_t* __restrict__ side1, int n, int npad,
+                                        int c, int npanel, int ngroups, float* Sr, float* Sc,
                                         long long lds) {
   const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int cv = c / V;
-  const long long ncv = static_cast<long long>(n) * cv;
+  const int nq = npad / 4;
+  const long long ncv = static_cast<long long>(nq) * c;
   if (idx < ncv) {
-    const int j = static_cast<int>(idx / cv), cc = static_cast<int>(idx % cv) * V;
-    const float* src = sc_part + static_cast<size_t>(j) * c + cc;
-    const size_t stride = static_cast<size_t>(n) * c;
-    float s[V], k[V];
+    const int jq = static_cast<int>(idx % nq), cc = static_cast<int>(idx / nq);
+    const int j = 4 * jq;
+    if (j >= n) return;
+    const float* src = sc_part + static_cast<size_t>(cc) * npad + j;
+    const size_t stride = static_cast<size_t>(c) * npad;
+    float s[4], k[4];
 #pragma unroll
-    for (int x = 0; x < V; ++x) s[x] = k[x] = 0.f;
+    for (int x = 0; x < 4; ++x) s[x] = k[x] = 0.f;
     int p = 0;
     for (; p + 8 <= npanel; p += 8) {
-      float v[8][V];
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldcs(reinterpret_cast<const float4*>(src + stride * (p + u)));
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        if constexpr (V == 4) {
-          const float4 f = __ldcs(reinterpret_cast<const float4*>(src + stride * (p + u)));
-          v[u][0] = f.x;
-          v[u][1] = f.y;
-          v[u][2] = f.z;
-          v[u][3] = f.w;
-        } else {
-          v[u][0] = __ldcs(src + stride * (p + u));
-        }
+        neumaier_add(s[0], k[0], v[u].x);
+        neumaier_add(s[1], k[1], v[u].y);
+        neumaier_add(s[2], k[2], v[u].z);
+        neumaier_add(s[3], k[3], v[u].w);
       }
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-#pragma unroll
-        for (int x = 0; x < V; ++x) neumaier_add(s[x], k[x], v[u][x]);
     }
-    for (; p < npanel; ++p)
+    for (; p < npanel; ++p) {
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(src + stride * p));
+      neumaier_add(s[0], k[0], v.x);
+      neumaier_add(s[1], k[1], v.y);
+      neumaier_add(s[2], k[2], v.z);
+      neumaier_add(s[3], k[3], v.w);
+    }
 #pragma unroll
-      for (int x = 0; x < V; ++x) neumaier_add(s[x], k[x], src[stride * p + x]);
-#pragma unroll
-    for (int x = 0; x < V; ++x) Sc[static_cast<size_t>(j) * lds + cc + x] = s[x] + k[x];
+    for (int x = 0; x < 4; ++x)
+      if (j + x < n) Sc[static_cast<size_t>(j + x) * lds + cc] = s[x] + k[x];
   } else if (idx < ncv + static_cast<long long>(npanel) * c * BM) {
     const long long r = idx - ncv;
     const int row = static_cast<int>(r % BM);
@@ -624,7 +635,7 @@ size_t sample_tc_scratch_bytes(int64_t n, int64_t ncols, int sms) {
   const int64_t c = ncols < CMAX ? ncols : CMAX;
   const int64_t cpad = (c + 63) / 64 * 64;
   return align256(static_cast<size_t>(n) * cpad * 2) +
-         align256(static_cast<size_t>(pl.npanel) * n * c * 4) +
+         align256(static_cast<size_t>(pl.npanel) * c * pl.ntc * BN * 4) +
          align256(static_cast<size_t>(pl.npanel) * pl.ngroups * 2 * c * BM * 4) +
          2 * align256(static_cast<size_t>(n) * 4) +
          align256(static_cast<size_t>(pl.npanel) * pl.ngroups) + 256;
@@ -673,7 +684,7 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     __nv_bfloat16* R16 = reinterpret_cast<__nv_bfloat16*>(base);
     base += align256(static_cast<size_t>(n) * cpad * 2);
     float* scp = reinterpret_cast<float*>(base);
-    base += align256(static_cast<size_t>(pl.npanel) * n * c * 4);
+    base += align256(static_cast<size_t>(pl.npanel) * c * pl.ntc * BN * 4);
     float* srp = reinterpret_cast<float*>(base);
     base += align256(static_cast<size_t>(pl.npanel) * pl.ngroups * 2 * c * BM * 4);
     int32_t* leaf_lo = reinterpret_cast<int32_t*>(base);
@@ -713,6 +724,7 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     g.leaf_lo = leaf_lo;
     g.leaf_hi = leaf_hi;
     g.sc_part = scp;
+    g.npad = pl.ntc * BN;
     g.sr_part = srp;
     g.err = err;
     HSS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
@@ -728,17 +740,11 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
       HSS_TRY(check_launch("row_slot_flags_kernel"));
     }
     const long long nrow = static_cast<long long>(pl.npanel) * c * BM;
-    if (c % 4 == 0) {
-      const long long nred = static_cast<long long>(n) * (c / 4) + nrow;
-      sample_tc_reduce_kernel<4><<<static_cast<unsigned>((nred + 255) / 256), 256, 0, s>>>(
-          scp, srp, side1, static_cast<int>(n), c, pl.npanel, pl.ngroups, Sr + c0 + done,
-          Sc + c0 + done, lds);
-    } else {
-      const long long nred = static_cast<long long>(n) * c + nrow;
-      sample_tc_reduce_kernel<1><<<static_cast<unsigned>((nred + 255) / 256), 256, 0, s>>>(
-          scp, srp, side1, static_cast<int>(n), c, pl.npanel, pl.ngroups, Sr + c0 + done,
-          Sc + c0 + done, lds);
-    }
+    const int npad = pl.ntc * BN;
+    const long long nred = static_cast<long long>(npad / 4) * c + nrow;
+    sample_tc_reduce_kernel<<<static_cast<unsigned>((nred + 255) / 256), 256, 0, s>>>(
+        scp, srp, side1, static_cast<int>(n), npad, c, pl.npanel, pl.ngroups, Sr + c0 + done,
+        Sc + c0 + done, lds);
     HSS_TRY(check_launch("sample_tc_reduce_kernel"));
     int herr = 0;
     HSS_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -46,6 +46,17 @@ __device__ __forceinline__ bool mbar_try(uint32_t b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// non-blocking test: never suspends the thread
+__device__ __forceinline__ bool mbar_test(uint32_t b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, "
+      "p; }"
+      : "=r"(ok)
+      : "r"(b), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 // as mbar_try, but the thread may be suspended (issuing nothing) for up to
 // `hint_ns` nanoseconds while the phase is incomplete
 __device__ __forceinline__ bool mbar_try_suspend(uint32_t b, uint32_t parity, uint32_t hint_ns) {
@@ -64,9 +75,9 @@ __device__ __forceinline__ bool mbar_try_suspend(uint32_t b, uint32_t parity, ui
 // in which case it sets *abort and the error word.
 __device__ __forceinline__ bool mbar_wait(uint32_t b, uint32_t parity, volatile int* abort,
                                           int* err, int code, long long limit) {
-  if (mbar_try(b, parity)) return true;
+  if (mbar_test(b, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_try_suspend(b, parity, 200000u)) {
+  while (!mbar_test(b, parity)) {
     if (*abort) return false;
     if (clock64() - t0 > limit) {
       *abort = 1;
