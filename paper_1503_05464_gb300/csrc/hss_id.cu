@@ -28,7 +28,8 @@
 // perm[0..k) records the pivot order, the remaining columns follow in
 // increasing index order.  The pivot columns' R entries go to a global k x k
 // buffer, and each CTA solves T = R1^{-1} R2 for the remaining columns it owns
-// (one thread per column), writing E = T^T so that the generator is Pi [I; E].
+// (column-oriented back substitution, all threads of the CTA), writing E = T^T
+// so that the generator is Pi [I; E].
 #include "hss_internal.cuh"
 
 #include <cooperative_groups.h>
@@ -134,6 +135,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   __shared__ int redi[ID_WARPS];
   __shared__ double hh[4];   // this step's sigma, tau, beta, scale
   __shared__ int hstop;
+  __shared__ int nrest;
 
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
@@ -401,17 +403,40 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     }
   }
   __syncthreads();
-  for (int jl = tid; jl < mloc; jl += ID_THREADS) {
-    const int q = restpos[jl];
-    if (q < 0) continue;
-    perm[k + q] = jl * C + crank;
-    const double* r2 = col(jl);
-    double* e = it.E + (size_t)q * k;
-    for (int a = k - 1; a >= 0; --a) {
-      double s = r2[a];
-      for (int b = a + 1; b < k; ++b) s = fma(-R1[(size_t)b * k + a], e[b], s);
-      e[a] = s / R1[(size_t)a * k + a];
+  // T = R1^{-1} R2 for the remaining columns this CTA owns, by column-oriented
+  // back substitution with the whole CTA: at step a each remaining column's
+  // T_a = rhs_a / R_aa (one thread per column), then rhs_c -= R_ca T_a for
+  // c < a (threads over (c, column) pairs, reading column a of R1
+  // contiguously).  The right-hand sides are the columns' first k entries,
+  // solved in place.  Per column the operations and their order (a = k-1
+  // down to 0) do not depend on the CTA or cluster size.
+  int* rlist = reinterpret_cast<int*>(nrm);   // local indices of the remaining columns
+  if (tid == 0) {
+    int nr = 0;
+    for (int jl = 0; jl < mloc; ++jl)
+      if (restpos[jl] >= 0) rlist[nr++] = jl;
+    nrest = nr;
+  }
+  __syncthreads();
+  const int nr = nrest;
+  for (int u = tid; u < nr; u += ID_THREADS) perm[k + restpos[rlist[u]]] = rlist[u] * C + crank;
+  for (int a = k - 1; a >= 0 && nr > 0; --a) {
+    const double raa = R1[(size_t)a * k + a];
+    for (int u = tid; u < nr; u += ID_THREADS) {
+      const int jl = rlist[u];
+      double* r2 = col(jl);
+      const double x = r2[a] / raa;
+      r2[a] = x;
+      it.E[(size_t)restpos[jl] * k + a] = x;
     }
+    __syncthreads();
+    const double* ra = R1 + (size_t)a * k;   // column a: R_ca for c <= a
+    for (int idx = tid; idx < a * nr; idx += ID_THREADS) {
+      const int u = idx / a, c = idx - u * a;
+      double* r2 = col(rlist[u]);
+      r2[c] = fma(-ra[c], r2[a], r2[c]);
+    }
+    __syncthreads();
   }
 }
 
