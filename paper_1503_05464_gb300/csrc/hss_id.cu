@@ -72,18 +72,6 @@ __device__ __forceinline__ void warp_argmax_bits(long long& v, int& j) {
   }
 }
 
-__device__ __forceinline__ void warp_argmax(double& v, int& j) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    double ov = __shfl_xor_sync(0xffffffffu, v, o);
-    int oj = __shfl_xor_sync(0xffffffffu, j, o);
-    if (ov > v || (ov == v && oj < j)) {
-      v = ov;
-      j = oj;
-    }
-  }
-}
-
 // Sum over the column entries c >= i of f(c) with a summation order that does
 // not depend on the team size TS: entry c accumulates (in increasing c) into
 // partial c mod 32, and the 32 partials are combined by a fixed butterfly
@@ -114,22 +102,20 @@ __device__ __forceinline__ double team_sum(int i, int d, int member, F f) {
   return v;
 }
 
-// Values one CTA publishes to the others of its cluster.
-struct Pub {
-  double cand_val;   // largest active residual norm of this CTA (-1: none)
-  int cand_idx;      // its global column index
-  int stop;          // owner of the pivot: 1 = stop before this step
-  double tau;        // owner: reflector coefficient
-  double r11;        // owner at step 0: |R_11|
+// A CTA's pivot candidate as its peers receive it.
+struct Cand {
+  long long v;   // bit pattern of its largest active residual norm (LLONG_MIN: none)
+  int j;         // its global column index
+  int pad;
 };
 
 template <int TS>
-__global__ void __launch_bounds__(ID_THREADS)
+__global__ void __launch_bounds__(ID_THREADS, 1)
 id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
                        int w_in_smem, double* __restrict__ r1buf_base,
                        const int64_t* __restrict__ r1off) {
   extern __shared__ __align__(16) double smem[];
-  __shared__ Pub pub[2];
+  __shared__ Cand cands[2][16];
   __shared__ double redv[ID_WARPS];
   __shared__ long long redb[ID_WARPS];
   __shared__ int redi[ID_WARPS];
@@ -156,7 +142,8 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   double* nrm0 = nrm + mloc_max;                  // mloc_max
   double* rdiag = nrm0 + mloc_max;                // mloc_max: R_ii of the pivot columns
   int* pstep = reinterpret_cast<int*>(rdiag + mloc_max);   // mloc_max: pivot step or -1
-  double* Wsm = reinterpret_cast<double*>(pstep + ((mloc_max + 1) & ~1));
+  double* colbuf = reinterpret_cast<double*>(pstep + ((mloc_max + 1) & ~1));   // 2 d: R1 columns
+  double* Wsm = colbuf + 2 * d;
   // odd column stride in shared memory: a thread per column reads without
   // bank conflicts
   const int ldw = d | 1;
@@ -197,56 +184,50 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
       pstep[jl] = -1;
     }
   }
-  __syncthreads();
-  // local arg-max -> published candidate
-  auto publish_candidate = [&]() {
-    double bv = -1.0;
-    int bj = INT_MAX;
-    for (int jl = tid; jl < mloc; jl += ID_THREADS) {
-      double x = nrm[jl];
-      if (x > bv) {
-        bv = x;
-        bj = jl * C + crank;
-      }
-    }
-    warp_argmax(bv, bj);
-    if (lane == 0) {
-      redv[warp] = bv;
-      redi[warp] = bj;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double v = redv[0];
-      int j = redi[0];
-      for (int q = 1; q < ID_WARPS; ++q)
-        if (redv[q] > v || (redv[q] == v && redi[q] < j)) {
-          v = redv[q];
-          j = redi[q];
-        }
-      pub[0].cand_val = v;
-      pub[0].cand_idx = j;
+  // every CTA of the cluster has started (its shared memory may now be
+  // written by peers) and the columns and norms are loaded
+  cluster.sync();
+  // each CTA's candidate (largest residual norm of its active columns, as the
+  // norm's bit pattern; lowest index on ties) goes into slot s of every CTA's
+  // cands[s][crank], so the reads after the next cluster barrier are local
+  auto push_candidate = [&](int s, long long v, int j) {
+    if (warp == 0 && lane < C) {
+      Cand* dst = cluster.map_shared_rank(&cands[s][crank], lane);
+      dst->v = v;
+      dst->j = j;
     }
   };
-  publish_candidate();
+  if (warp == 0) {
+    long long bv = LLONG_MIN;
+    int bj = INT_MAX;
+    for (int jl = lane; jl < mloc; jl += 32) {
+      const long long x = __double_as_longlong(nrm[jl]);
+      const int j = jl * C + crank;
+      if (x > bv || (x == bv && j < bj)) {
+        bv = x;
+        bj = j;
+      }
+    }
+    warp_argmax_bits(bv, bj);
+    push_candidate(0, bv, bj);
+  }
 
   const int kmax = min(m, d);
+  // warps that downdate the norms (one lane per column: an FP64 instruction
+  // costs the same however few lanes are active)
+  const int nwd = min(ID_WARPS, (mloc_max + 31) / 32);
   int k = kmax;
   double r11 = 0.0;
   for (int i = 0; i < kmax; ++i) {
-    cluster.sync();   // candidates of step i published, updates of step i-1 done
+    cluster.sync();   // candidates of step i pushed, updates of step i-1 done
     const int slot = i & 1;
-    // every warp reads the C candidates in parallel (lane r <- CTA r) and
-    // reduces them: all threads agree on the pivot without a block barrier
+    // every warp reduces the C candidates (lane r <- CTA r): all threads agree
+    // on the pivot without a block barrier
     long long bv = LLONG_MIN;
     int p = INT_MAX;
-    for (int r = lane; r < C; r += 32) {
-      const Pub* rp = cluster.map_shared_rank(&pub[slot], r);
-      const long long v = __double_as_longlong(rp->cand_val);
-      const int j = rp->cand_idx;
-      if (v > bv || (v == bv && j < p)) {
-        bv = v;
-        p = j;
-      }
+    if (lane < C) {
+      bv = cands[slot][lane].v;
+      p = cands[slot][lane].j;
     }
     warp_argmax_bits(bv, p);
     const int owner = p % C;
@@ -260,7 +241,8 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     {
       // exact residual norm and reflector, the same arithmetic on every CTA:
       // st = sum of x_c^2 for c > i, thread t taking c = i + 1 + t + 256 q in
-      // increasing q, then a warp butterfly and the 8 warp sums in order
+      // increasing q, then a warp butterfly and a fixed pairwise tree over the
+      // 8 warp sums
       double st = 0.0;
       for (int c = i + 1 + tid; c < d; c += ID_THREADS) {
         const double x = vloc[c - i];
@@ -269,25 +251,24 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
       st = warp_sum(st);
       if (lane == 0) redv[warp] = st;
       __syncthreads();
-      if (tid == 0) {
-        st = redv[0];
-        for (int q = 1; q < ID_WARPS; ++q) st += redv[q];
+      // two threads on two schedulers: the two divisions run side by side
+      if (tid == 0 || tid == 32) {
+        st = ((redv[0] + redv[1]) + (redv[2] + redv[3])) + ((redv[4] + redv[5]) + (redv[6] + redv[7]));
         const double alpha = vloc[0];
         const double sa = fma(alpha, alpha, st);
         const double sigma = sqrt(sa);
         const double r11_now = (i == 0) ? sigma : r11;
         const int stop = (r11_now == 0.0 || sigma <= fmax(rtol * r11_now, atol)) ? 1 : 0;
-        double tau = 0.0, beta = alpha, scal = 0.0;
-        if (!stop && st != 0.0) {
-          beta = -copysign(sigma, alpha);
-          tau = (beta - alpha) / beta;
-          scal = 1.0 / (alpha - beta);
+        const bool refl = !stop && st != 0.0;
+        const double beta = refl ? -copysign(sigma, alpha) : alpha;
+        if (tid == 0) {
+          hh[0] = sigma;
+          hh[1] = refl ? (beta - alpha) / beta : 0.0;
+          hh[2] = beta;
+          hstop = stop;
+        } else {
+          hh[3] = refl ? 1.0 / (alpha - beta) : 0.0;
         }
-        hh[0] = sigma;
-        hh[1] = tau;
-        hh[2] = beta;
-        hh[3] = scal;
-        hstop = stop;
       }
     }
     __syncthreads();
@@ -305,12 +286,10 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     }
     if (crank == 0 && tid == 0) perm[i] = p;
     __syncthreads();
-    long long cv = LLONG_MIN;   // this thread's best candidate for step i + 1 (norm bits)
-    int cj = INT_MAX;
+    // apply the reflector: a team of TS threads per active column
     for (int jb = warp * cols_per_warp; jb < mloc; jb += ID_WARPS * cols_per_warp) {
       const int jl = jb + lane / TS;
-      const double nj = jl < mloc ? nrm[jl] : -1.0;
-      const bool act = nj >= 0.0;
+      const bool act = jl < mloc && nrm[jl] >= 0.0;
       double* wj = act ? col(jl) : nullptr;
       double dot = team_sum<TS>(i, act ? d : 0, member, [&](int c, double a) {
         return fma(vloc[c - i], wj[c], a);
@@ -318,56 +297,67 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
       dot *= tau;
       if (act)
         for (int c = i + member; c < d; c += TS) wj[c] = fma(-dot, vloc[c - i], wj[c]);
-      __syncwarp();
-      // norm downdate by the team leader (LAPACK xGEQP3 safeguard)
-      bool recompute = false;
-      double newn = nj;
-      if (act && member == 0 && nj != 0.0) {
-        const double rij = wj[i];
-        double t = fabs(rij) / nj;
-        t = fmax(0.0, (1.0 + t) * (1.0 - t));
-        double r = nj / nrm0[jl];
-        if (t * r * r <= tol3z) recompute = true;
-        else newn = nj * sqrt(t);
-      }
-      recompute = __shfl_sync(0xffffffffu, recompute ? 1 : 0, lane & ~(TS - 1)) != 0;
-      if (__any_sync(0xffffffffu, recompute)) {
-        double ss = team_sum<TS>(i + 1, recompute ? d : 0, member, [&](int c, double a) {
-          return fma(wj[c], wj[c], a);
-        });
-        if (recompute) {
-          newn = sqrt(ss);
-          if (member == 0) nrm0[jl] = newn;
-        }
-      }
-      if (act && member == 0) {
-        nrm[jl] = newn;
-        const int j = jl * C + crank;
-        const long long nb = __double_as_longlong(newn);
-        if (nb > cv || (nb == cv && j < cj)) {
-          cv = nb;
-          cj = j;
-        }
-      }
-    }
-    // next candidate: warp arg-max, then one thread over the warps
-    warp_argmax_bits(cv, cj);
-    if (lane == 0) {
-      redb[warp] = cv;
-      redi[warp] = cj;
     }
     __syncthreads();
-    if (tid == 0) {
-      long long v = redb[0];
-      int j = redi[0];
-      for (int q = 1; q < ID_WARPS; ++q)
-        if (redb[q] > v || (redb[q] == v && redi[q] < j)) {
-          v = redb[q];
-          j = redi[q];
+    // norm downdates (LAPACK xGEQP3's formula and safeguard), one lane per
+    // column, and this CTA's next candidate
+    if (warp < nwd) {
+      long long cv = LLONG_MIN;
+      int cj = INT_MAX;
+      for (int jl0 = warp * 32; jl0 < mloc; jl0 += nwd * 32) {
+        const int jl = jl0 + lane;
+        const double nj = jl < mloc ? nrm[jl] : -1.0;
+        const bool act = nj >= 0.0;
+        bool recompute = false;
+        double newn = nj;
+        if (act && nj != 0.0) {
+          double t = fabs(col(jl)[i]) / nj;
+          t = fmax(0.0, (1.0 + t) * (1.0 - t));
+          const double r = nj / nrm0[jl];
+          if (t * r * r <= tol3z) recompute = true;
+          else newn = nj * sqrt(t);
         }
-      // no active column: -1 (the bit pattern of LLONG_MIN is not a norm)
-      pub[slot ^ 1].cand_val = v == LLONG_MIN ? -1.0 : __longlong_as_double(v);
-      pub[slot ^ 1].cand_idx = j;
+        // cancellation: recompute those norms, one column at a time with the
+        // whole warp (the fixed summation tree gives the same bits as a team)
+        unsigned rm = __ballot_sync(0xffffffffu, recompute);
+        while (rm) {
+          const int src = __ffs(rm) - 1;
+          rm &= rm - 1;
+          const double* wr = col(jl0 + src);
+          const double ss = team_sum<32>(i + 1, d, lane, [&](int c, double a) {
+            return fma(wr[c], wr[c], a);
+          });
+          if (lane == src) {
+            newn = sqrt(ss);
+            nrm0[jl] = newn;
+          }
+        }
+        if (act) {
+          nrm[jl] = newn;
+          const long long nb = __double_as_longlong(newn);
+          const int j = jl * C + crank;
+          if (nb > cv || (nb == cv && j < cj)) {
+            cv = nb;
+            cj = j;
+          }
+        }
+      }
+      warp_argmax_bits(cv, cj);
+      if (nwd == 1) {
+        push_candidate(slot ^ 1, cv, cj);
+      } else if (lane == 0) {
+        redb[warp] = cv;
+        redi[warp] = cj;
+      }
+    }
+    if (nwd > 1) {
+      __syncthreads();
+      if (warp == 0) {
+        long long cv = lane < nwd ? redb[lane] : LLONG_MIN;
+        int cj = lane < nwd ? redi[lane] : INT_MAX;
+        warp_argmax_bits(cv, cj);
+        push_candidate(slot ^ 1, cv, cj);
+      }
     }
   }
 
@@ -386,30 +376,26 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   }
   cluster.sync();   // R1 and flags visible to the whole cluster
   if (crank == 0 && tid == 0) *it.k = k;
-  // position of each remaining column in perm[k..m): count of remaining
-  // columns of lower index (one serial scan per CTA; m is small)
+  // position of each remaining column in perm[k..m): the count of remaining
+  // columns of lower index
   int* restpos = pstep;   // reuse: local rest position
-  if (tid == 0) {
-    int q = 0;
-    for (int j = 0; j < m; ++j) {
-      if (flag[j]) {
-        if (j % C == crank) restpos[j / C] = q;
-        ++q;
-      }
+  for (int jl = tid; jl < mloc; jl += ID_THREADS) {
+    const int j = jl * C + crank;
+    int q = -1;
+    if (flag[j]) {
+      q = 0;
+      for (int x = 0; x < j; ++x) q += flag[x];
     }
-    for (int jl = 0; jl < mloc; ++jl) {
-      const int j = jl * C + crank;
-      if (!flag[j]) restpos[jl] = -1;
-    }
+    restpos[jl] = q;
   }
   __syncthreads();
   // T = R1^{-1} R2 for the remaining columns this CTA owns, by column-oriented
   // back substitution with the whole CTA: at step a each remaining column's
   // T_a = rhs_a / R_aa (one thread per column), then rhs_c -= R_ca T_a for
-  // c < a (threads over (c, column) pairs, reading column a of R1
-  // contiguously).  The right-hand sides are the columns' first k entries,
-  // solved in place.  Per column the operations and their order (a = k-1
-  // down to 0) do not depend on the CTA or cluster size.
+  // c < a (threads over (c, column) pairs).  The right-hand sides are the
+  // columns' first k entries, solved in place; R1's diagonal and its columns
+  // are staged in shared memory one step ahead.  Per column the operations and
+  // their order (a = k-1 down to 0) do not depend on the CTA or cluster size.
   int* rlist = reinterpret_cast<int*>(nrm);   // local indices of the remaining columns
   if (tid == 0) {
     int nr = 0;
@@ -417,20 +403,27 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
       if (restpos[jl] >= 0) rlist[nr++] = jl;
     nrest = nr;
   }
+  double* diag = vloc;    // k <= d entries
+  for (int a = tid; a < k; a += ID_THREADS) diag[a] = R1[(size_t)a * k + a];
+  if (k > 0)
+    for (int c = tid; c < k - 1; c += ID_THREADS) colbuf[((k - 1) & 1) * d + c] = R1[(size_t)(k - 1) * k + c];
   __syncthreads();
   const int nr = nrest;
   for (int u = tid; u < nr; u += ID_THREADS) perm[k + restpos[rlist[u]]] = rlist[u] * C + crank;
   for (int a = k - 1; a >= 0 && nr > 0; --a) {
-    const double raa = R1[(size_t)a * k + a];
+    // next step's column of R1 (entries c < a - 1), by the warps not dividing
+    if (a >= 1 && tid >= 32)
+      for (int c = tid - 32; c < a - 1; c += ID_THREADS - 32)
+        colbuf[((a - 1) & 1) * d + c] = R1[(size_t)(a - 1) * k + c];
     for (int u = tid; u < nr; u += ID_THREADS) {
       const int jl = rlist[u];
       double* r2 = col(jl);
-      const double x = r2[a] / raa;
+      const double x = r2[a] / diag[a];
       r2[a] = x;
       it.E[(size_t)restpos[jl] * k + a] = x;
     }
     __syncthreads();
-    const double* ra = R1 + (size_t)a * k;   // column a: R_ca for c <= a
+    const double* ra = colbuf + (a & 1) * d;   // R_ca for c < a
     for (int idx = tid; idx < a * nr; idx += ID_THREADS) {
       const int u = idx / a, c = idx - u * a;
       double* r2 = col(rlist[u]);
@@ -470,7 +463,7 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
   const int d = std::max(max_d, 1);
   auto need = [&](int c) {
     int mloc = (max_m + c - 1) / c;
-    return sizeof(double) * ((size_t)d + 3 * (size_t)mloc) +
+    return sizeof(double) * (3 * (size_t)d + 3 * (size_t)mloc) +
            sizeof(int) * (size_t)((mloc + 1) & ~1);
   };
   size_t base = need(C);
@@ -560,11 +553,26 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
     smem = base + (w_in_smem ? wbytes : 0);
     cfg.dynamicSmemBytes = smem;
   }
-  // threads per column: results do not depend on it (fixed summation tree)
+  // threads per column: results do not depend on it (fixed summation tree),
+  // so pick the team size with the fewest FP64 instructions on the busiest of
+  // the 4 schedulers.  An FP64 instruction costs the same however few lanes
+  // are active; per team and step: 2 d / TS fused multiply-adds (dot product
+  // and update), 32 / TS - 1 in-thread and log2 TS shuffle additions, and the
+  // multiplication by tau.  Team groups go to warps round-robin, warp w runs
+  // on scheduler w % 4.
   int TS = 1;
   {
     const int mloc = (max_m + C - 1) / C;
-    while (TS < 32 && mloc * TS * 2 <= ID_THREADS) TS *= 2;
+    long best = -1;
+    for (int ts = 1, lg = 0; ts <= 32; ts *= 2, ++lg) {
+      const long groups = ((long)mloc * ts + 31) / 32;
+      const long per = 2 * ((d + ts - 1) / ts) + (32 / ts - 1) + lg + 1;
+      const long cost = (groups + 3) / 4 * per;
+      if (best < 0 || cost < best) {
+        best = cost;
+        TS = ts;
+      }
+    }
   }
   const auto fns = kernels();
   int ti = 0;
