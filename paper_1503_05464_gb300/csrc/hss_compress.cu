@@ -95,37 +95,45 @@ struct Job {
   bool active() const { return state == SETUP || state == LEVEL; }
 
   // grow a rows x old_ld row-major buffer to new_ld (keeps the first `cols`
-  // columns); global buffers are freed, node buffers come from `tmp`
-  Err regrow(T** p, int64_t rows, int old_ld, int new_ld, int cols, bool node) {
+  // columns); global buffers are freed, node buffers come from `tmp`.  The
+  // copy is queued in `copies` (one batched launch for all buffers).
+  Err regrow(T** p, int64_t rows, int old_ld, int new_ld, int cols, bool node,
+             std::vector<Copy2D<T>>& copies) {
     if (!*p || rows == 0) return ok();
     T* q = nullptr;
     if (node) HSS_TRY(tmp.alloc_t(&q, (size_t)rows * new_ld, s));
     else HSS_TRY(dalloc_t(&q, (size_t)rows * new_ld, s));
-    if (cols > 0)
-      HSS_CUDA_TRY(cudaMemcpy2DAsync(q, sizeof(T) * new_ld, *p, sizeof(T) * old_ld,
-                                     sizeof(T) * cols, rows, cudaMemcpyDeviceToDevice, s));
-    if (!node) dfree(*p, s);
+    if (cols > 0) copies.push_back({q, *p, new_ld, old_ld, (int32_t)rows, cols});
+    if (!node) old_global.push_back(*p);
     *p = q;
     return ok();
   }
+  std::vector<T*> old_global;
 
+  // Room for dneed sample columns.  The first allocation leaves room for two
+  // more adaptive passes; later growth doubles.
   Err ensure_dcap(int dneed) {
     if (dneed <= h->dcap) return ok();
-    int nc = std::max(dneed, 2 * h->dcap);
-    nc = std::min(nc, h->opts.d_max);
+    const int64_t want = h->dcap == 0 ? (int64_t)dneed + 2 * (int64_t)h->opts.d_step
+                                      : std::max<int64_t>(dneed, 2 * (int64_t)h->dcap);
+    int nc = (int)std::min<int64_t>(want, h->opts.d_max);
     nc = std::max(nc, dneed);
     nc = (nc + 31) / 32 * 32;
     int old = h->dcap, cols = h->d;
+    std::vector<Copy2D<T>> copies;
     for (T** g : {&R, &Sr, &Sc}) {
-      if (*g) HSS_TRY(regrow(g, n(), old, nc, cols, false));
+      if (*g) HSS_TRY(regrow(g, n(), old, nc, cols, false, copies));
       else HSS_TRY(dalloc_t(g, (size_t)n() * nc, s));
     }
     for (NodeGen& g : h->gen) {
-      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Sr), g.kr, old, nc, g.ncols, true));
-      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Sc), g.kc, old, nc, g.ncols, true));
-      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Rr), g.kc, old, nc, g.ncols, true));
-      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Rc), g.kr, old, nc, g.ncols, true));
+      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Sr), g.kr, old, nc, g.ncols, true, copies));
+      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Sc), g.kc, old, nc, g.ncols, true, copies));
+      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Rr), g.kc, old, nc, g.ncols, true, copies));
+      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Rc), g.kr, old, nc, g.ncols, true, copies));
     }
+    HSS_TRY(launch_copy_batched<T>(copies, s, nullptr));
+    for (T* p : old_global) dfree(p, s);
+    old_global.clear();
     h->dcap = nc;
     return ok();
   }
@@ -160,17 +168,17 @@ struct Job {
       HSS_CUDA_TRY(cudaMemcpyAsync(leaf_of, lof.data(), N * sizeof(int32_t),
                                    cudaMemcpyHostToDevice, s));
     }
+    std::vector<Copy2D<T>> dcopies;
     for (size_t i = 0; i < tr.nodes.size(); ++i) {   // D_tau = A(I_tau, I_tau)
       const TNode& nd = tr.nodes[i];
       if (nd.c1 >= 0) continue;
       int m = nd.hi - nd.lo;
       NodeGen& g = h->gen[i];
       HSS_TRY(h->store.alloc(&g.D, sizeof(T) * m * m, s));
-      HSS_CUDA_TRY(cudaMemcpy2DAsync(g.D, sizeof(T) * m, A + (int64_t)nd.lo * lda + nd.lo,
-                                     sizeof(T) * lda, sizeof(T) * m, m,
-                                     cudaMemcpyDeviceToDevice, s));
+      dcopies.push_back({reinterpret_cast<T*>(g.D), A + (int64_t)nd.lo * lda + nd.lo, m, lda, m, m});
       h->info.bytes_hss += sizeof(T) * (int64_t)m * m;
     }
+    HSS_TRY(launch_copy_batched<T>(dcopies, s, nullptr));
     if (tr.nodes.size() == 1) {   // single node: H = D
       h->gen[0].state = NODE_COMPRESSED;
       h->passes = 1;

@@ -257,6 +257,18 @@ Err launch_gather_batched(const T* A, int64_t lda, const std::vector<GatherItem<
                           cudaStream_t s, void* scratch_dev, size_t scratch_bytes,
                           Arena* scratch = nullptr);
 
+// Batched strided copies: dst[r * ldd + c] = src[r * lds + c] for r < rows,
+// c < cols (one launch for many small blocks).
+template <typename T>
+struct Copy2D {
+  T* dst;
+  const T* src;
+  int64_t ldd, lds;
+  int32_t rows, cols;
+};
+template <typename T>
+Err launch_copy_batched(const std::vector<Copy2D<T>>& items, cudaStream_t s, Arena* scratch);
+
 // map[j] = base[idx[j]]  (skeleton index sets I^r_tau = I(J))
 Err launch_index_compose(int32_t* out, const int32_t* base, const int32_t* idx, int count,
                          cudaStream_t s);

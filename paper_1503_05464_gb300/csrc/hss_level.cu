@@ -127,6 +127,23 @@ __global__ void gather_batched_kernel(const T* __restrict__ A, int64_t lda,
   it.out[e] = src[(int64_t)it.rows[j] * ld + it.cols[l]];
 }
 
+template <typename T>
+__global__ void copy_batched_kernel(const Copy2D<T>* __restrict__ items,
+                                    const int64_t* __restrict__ start, int nitems, int64_t total) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  int lo = 0, hi = nitems - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  const Copy2D<T> it = items[lo];
+  const int64_t e = t - start[lo];
+  const int r = (int)(e / it.cols), c = (int)(e - (int64_t)r * it.cols);
+  it.dst[(int64_t)r * it.ldd + c] = it.src[(int64_t)r * it.lds + c];
+}
+
 __global__ void index_compose_kernel(int32_t* out, const int32_t* base, const int32_t* idx,
                                      int count) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -313,6 +330,45 @@ Err launch_gather_batched(const T* A, int64_t lda, const std::vector<GatherItem<
   if (own) dfree(buf, s);
   return e;
 }
+
+template <typename T>
+Err launch_copy_batched(const std::vector<Copy2D<T>>& items, cudaStream_t s, Arena* scratch) {
+  std::vector<Copy2D<T>> live;
+  std::vector<int64_t> starts;
+  int64_t total = 0;
+  for (const auto& it : items) {
+    if (it.rows <= 0 || it.cols <= 0) continue;
+    live.push_back(it);
+    starts.push_back(total);
+    total += (int64_t)it.rows * it.cols;
+  }
+  if (live.empty()) return ok();
+  const size_t bi = live.size() * sizeof(Copy2D<T>);
+  const size_t bs = starts.size() * sizeof(int64_t);
+  const size_t off = (bi + 255) & ~size_t(255);
+  void* buf = nullptr;
+  bool own = false;
+  if (scratch) {
+    HSS_TRY(scratch->alloc(&buf, off + bs, s));
+    HSS_TRY(scratch->upload(buf, live.data(), bi, s));
+    HSS_TRY(scratch->upload((char*)buf + off, starts.data(), bs, s));
+  } else {
+    HSS_TRY(dalloc(&buf, off + bs, s));
+    own = true;
+    HSS_CUDA_TRY(cudaMemcpyAsync(buf, live.data(), bi, cudaMemcpyHostToDevice, s));
+    HSS_CUDA_TRY(cudaMemcpyAsync((char*)buf + off, starts.data(), bs, cudaMemcpyHostToDevice, s));
+  }
+  copy_batched_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+      reinterpret_cast<const Copy2D<T>*>(buf), reinterpret_cast<const int64_t*>((char*)buf + off),
+      (int)live.size(), total);
+  Err e = check_launch("copy_batched_kernel");
+  if (own) dfree(buf, s);
+  return e;
+}
+
+template Err launch_copy_batched<float>(const std::vector<Copy2D<float>>&, cudaStream_t, Arena*);
+template Err launch_copy_batched<double>(const std::vector<Copy2D<double>>&, cudaStream_t,
+                                         Arena*);
 
 Err launch_index_compose(int32_t* out, const int32_t* base, const int32_t* idx, int count,
                          cudaStream_t s) {
