@@ -8,21 +8,24 @@
 // memory (or, for matrices too large for the cluster's shared memory, in a
 // global work copy) together with its residual norm.  One cluster barrier per
 // elimination step:
-//   1. after the barrier every CTA reads all C published candidates (largest
-//      residual norm among each CTA's active columns) through distributed
-//      shared memory and picks the same pivot (largest norm, lowest index on
-//      ties);
-//   2. every CTA copies the pivot column from its owner and derives, with the
-//      same arithmetic in the same order, its exact residual norm |R_ii|, the
-//      stopping decision against max(rtol |R_11|, atol) and the Householder
-//      reflector -- so no CTA waits for the owner, and all agree bitwise;
+//   1. before the barrier every CTA pushes its candidate (largest residual
+//      norm among its active columns, lowest index on ties) into every CTA's
+//      shared memory, with that column's exact residual: the entry at the
+//      next pivot row and the sum of squares below it (one warp, fixed
+//      summation tree);
+//   2. after the barrier every CTA picks the same pivot from the C local
+//      candidates and derives from the owner's pushed residual, with the same
+//      arithmetic, |R_ii|, the stopping decision against max(rtol |R_11|,
+//      atol) and the Householder reflector, while its other warps copy the
+//      pivot column from the owner -- so no CTA waits for the owner, and all
+//      agree bitwise;
 //   3. every CTA applies the reflector to its active columns (a team of
-//      threads per column: dot product, fixed-order reduction, update),
-//      downdates their norms -- recomputing a norm when cancellation makes the
-//      downdate inaccurate (LAPACK xGEQP3's safeguard, threshold sqrt(eps)) --
-//      and publishes its next candidate into the other of two slots (a CTA can
-//      be at most one step ahead of another, so the slot being read is never
-//      the one being written).
+//      threads per column: dot product, fixed-order reduction, update), then
+//      downdates their norms with one lane per column -- recomputing a norm
+//      when cancellation makes the downdate inaccurate (LAPACK xGEQP3's
+//      safeguard, threshold sqrt(eps)) -- and pushes its next candidate into
+//      the other of two slots (a CTA can be at most one step ahead of
+//      another, so the slot being read is never the one being written).
 // Columns never move and a pivot column is never written after it is chosen
 // (its R_ii is kept aside), so peers can read it while its owner goes on.
 // perm[0..k) records the pivot order, the remaining columns follow in
@@ -102,11 +105,15 @@ __device__ __forceinline__ double team_sum(int i, int d, int member, F f) {
   return v;
 }
 
-// A CTA's pivot candidate as its peers receive it.
+// A CTA's pivot candidate as its peers receive it: with the column's exact
+// residual (entry alpha at the next pivot row, sum st of the squares below
+// it) every CTA can form the reflector without waiting for the column.
 struct Cand {
-  long long v;   // bit pattern of its largest active residual norm (LLONG_MIN: none)
-  int j;         // its global column index
+  long long v;    // bit pattern of its largest active residual norm (LLONG_MIN: none)
+  int j;          // its global column index
   int pad;
+  double st;      // sum of x_c^2 below the next pivot row
+  double alpha;   // x at the next pivot row
 };
 
 template <int TS>
@@ -116,10 +123,9 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
                        const int64_t* __restrict__ r1off) {
   extern __shared__ __align__(16) double smem[];
   __shared__ Cand cands[2][16];
-  __shared__ double redv[ID_WARPS];
   __shared__ long long redb[ID_WARPS];
   __shared__ int redi[ID_WARPS];
-  __shared__ double hh[4];   // this step's sigma, tau, beta, scale
+  __shared__ double hh[4];   // this step's sigma, tau, (unused), scale
   __shared__ int hstop;
   __shared__ int nrest;
 
@@ -139,8 +145,8 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   const int mloc_max = (m + C - 1) / C;
   double* vloc = smem;                            // d: pivot column, then reflector
   double* nrm = vloc + d;                         // mloc_max
-  double* nrm0 = nrm + mloc_max;                  // mloc_max
-  double* rdiag = nrm0 + mloc_max;                // mloc_max: R_ii of the pivot columns
+  double* lim = nrm + mloc_max;                   // mloc_max: tol3z * (norm at last recompute)^2
+  double* rdiag = lim + mloc_max;                 // mloc_max: R_ii of the pivot columns
   int* pstep = reinterpret_cast<int*>(rdiag + mloc_max);   // mloc_max: pivot step or -1
   double* colbuf = reinterpret_cast<double*>(pstep + ((mloc_max + 1) & ~1));   // 2 d: R1 columns
   double* Wsm = colbuf + 2 * d;
@@ -180,7 +186,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     ss = warp_sum(ss);
     if (lane == 0) {
       nrm[jl] = sqrt(ss);
-      nrm0[jl] = nrm[jl];
+      lim[jl] = tol3z * (nrm[jl] * nrm[jl]);
       pstep[jl] = -1;
     }
   }
@@ -190,11 +196,21 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   // each CTA's candidate (largest residual norm of its active columns, as the
   // norm's bit pattern; lowest index on ties) goes into slot s of every CTA's
   // cands[s][crank], so the reads after the next cluster barrier are local
-  auto push_candidate = [&](int s, long long v, int j) {
-    if (warp == 0 && lane < C) {
+  // (one warp) push the candidate (v, j) for pivot row r: its residual is
+  // computed here with the fixed summation tree, so every CTA gets the same bits
+  auto push_candidate = [&](int s, long long v, int j, int r) {
+    double st = 0.0, alpha = 0.0;
+    if (v != LLONG_MIN) {
+      const double* w = col((j - crank) / C);
+      st = team_sum<32>(r + 1, d, lane, [&](int c, double a) { return fma(w[c], w[c], a); });
+      alpha = r < d ? w[r] : 0.0;
+    }
+    if (lane < C) {
       Cand* dst = cluster.map_shared_rank(&cands[s][crank], lane);
       dst->v = v;
       dst->j = j;
+      dst->st = st;
+      dst->alpha = alpha;
     }
   };
   if (warp == 0) {
@@ -209,7 +225,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
       }
     }
     warp_argmax_bits(bv, bj);
-    push_candidate(0, bv, bj);
+    push_candidate(0, bv, bj, 0);
   }
 
   const int kmax = min(m, d);
@@ -231,45 +247,37 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     }
     warp_argmax_bits(bv, p);
     const int owner = p % C;
-    // the pivot column, entries i..d-1, from its owner
-    {
+    if (tid == 0 || tid == 32) {
+      // the reflector from the owner's pushed residual, the same arithmetic on
+      // every CTA; two threads on two schedulers run the two divisions side
+      // by side while the other warps copy the pivot column
+      const double st = cands[slot][owner].st, alpha = cands[slot][owner].alpha;
+      const double sa = fma(alpha, alpha, st);
+      const double sigma = sqrt(sa);
+      const double r11_now = (i == 0) ? sigma : r11;
+      const int stop = (r11_now == 0.0 || sigma <= fmax(rtol * r11_now, atol)) ? 1 : 0;
+      const bool refl = !stop && st != 0.0;
+      const double beta = refl ? -copysign(sigma, alpha) : alpha;
+      if (tid == 0) {
+        hh[0] = sigma;
+        hh[1] = refl ? (beta - alpha) / beta : 0.0;
+        hstop = stop;
+        if (!stop) {
+          if (owner == crank) {
+            rdiag[p / C] = beta;
+            nrm[p / C] = -1.0;
+            pstep[p / C] = i;
+          }
+          if (crank == 0) perm[i] = p;
+        }
+      } else {
+        hh[3] = refl ? 1.0 / (alpha - beta) : 0.0;
+      }
+    } else if (tid >= 64) {
+      // the pivot column, entries i..d-1, from its owner
       const double* src = w_in_smem ? cluster.map_shared_rank(Wsm + (size_t)(p / C) * ldw, owner)
                                      : it.work + (size_t)p * d;
-      for (int c = i + tid; c < d; c += ID_THREADS) vloc[c - i] = src[c];
-    }
-    __syncthreads();
-    {
-      // exact residual norm and reflector, the same arithmetic on every CTA:
-      // st = sum of x_c^2 for c > i, thread t taking c = i + 1 + t + 256 q in
-      // increasing q, then a warp butterfly and a fixed pairwise tree over the
-      // 8 warp sums
-      double st = 0.0;
-      for (int c = i + 1 + tid; c < d; c += ID_THREADS) {
-        const double x = vloc[c - i];
-        st = fma(x, x, st);
-      }
-      st = warp_sum(st);
-      if (lane == 0) redv[warp] = st;
-      __syncthreads();
-      // two threads on two schedulers: the two divisions run side by side
-      if (tid == 0 || tid == 32) {
-        st = ((redv[0] + redv[1]) + (redv[2] + redv[3])) + ((redv[4] + redv[5]) + (redv[6] + redv[7]));
-        const double alpha = vloc[0];
-        const double sa = fma(alpha, alpha, st);
-        const double sigma = sqrt(sa);
-        const double r11_now = (i == 0) ? sigma : r11;
-        const int stop = (r11_now == 0.0 || sigma <= fmax(rtol * r11_now, atol)) ? 1 : 0;
-        const bool refl = !stop && st != 0.0;
-        const double beta = refl ? -copysign(sigma, alpha) : alpha;
-        if (tid == 0) {
-          hh[0] = sigma;
-          hh[1] = refl ? (beta - alpha) / beta : 0.0;
-          hh[2] = beta;
-          hstop = stop;
-        } else {
-          hh[3] = refl ? 1.0 / (alpha - beta) : 0.0;
-        }
-      }
+      for (int c = i + tid - 64; c < d; c += ID_THREADS - 64) vloc[c - i] = src[c];
     }
     __syncthreads();
     if (i == 0) r11 = hh[0];
@@ -279,12 +287,6 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     }
     const double tau = hh[1], scal = hh[3];
     for (int c = i + tid; c < d; c += ID_THREADS) vloc[c - i] = (c == i) ? 1.0 : vloc[c - i] * scal;
-    if (owner == crank && tid == 0) {
-      rdiag[p / C] = hh[2];
-      nrm[p / C] = -1.0;
-      pstep[p / C] = i;
-    }
-    if (crank == 0 && tid == 0) perm[i] = p;
     __syncthreads();
     // apply the reflector: a team of TS threads per active column
     for (int jb = warp * cols_per_warp; jb < mloc; jb += ID_WARPS * cols_per_warp) {
@@ -311,11 +313,12 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
         bool recompute = false;
         double newn = nj;
         if (act && nj != 0.0) {
-          double t = fabs(col(jl)[i]) / nj;
-          t = fmax(0.0, (1.0 + t) * (1.0 - t));
-          const double r = nj / nrm0[jl];
-          if (t * r * r <= tol3z) recompute = true;
-          else newn = nj * sqrt(t);
+          // xGEQP3's downdate nj sqrt(max(0, (1 - t)(1 + t))), t = |r| / nj,
+          // and its test t (nj / nrm0)^2 <= tol3z, both multiplied out by nj^2
+          const double r = fabs(col(jl)[i]);
+          const double q = fmax(0.0, (nj - r) * (nj + r));
+          if (q <= lim[jl]) recompute = true;
+          else newn = sqrt(q);
         }
         // cancellation: recompute those norms, one column at a time with the
         // whole warp (the fixed summation tree gives the same bits as a team)
@@ -329,7 +332,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
           });
           if (lane == src) {
             newn = sqrt(ss);
-            nrm0[jl] = newn;
+            lim[jl] = tol3z * (newn * newn);
           }
         }
         if (act) {
@@ -344,7 +347,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
       }
       warp_argmax_bits(cv, cj);
       if (nwd == 1) {
-        push_candidate(slot ^ 1, cv, cj);
+        push_candidate(slot ^ 1, cv, cj, i + 1);
       } else if (lane == 0) {
         redb[warp] = cv;
         redi[warp] = cj;
@@ -356,7 +359,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
         long long cv = lane < nwd ? redb[lane] : LLONG_MIN;
         int cj = lane < nwd ? redi[lane] : INT_MAX;
         warp_argmax_bits(cv, cj);
-        push_candidate(slot ^ 1, cv, cj);
+        push_candidate(slot ^ 1, cv, cj, i + 1);
       }
     }
   }
@@ -470,7 +473,7 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
   size_t wbytes = sizeof(double) * (size_t)((max_m + C - 1) / C) * (d | 1);
   int w_in_smem = base + wbytes <= ID_SMEM_CAP ? 1 : 0;
   size_t smem = base + (w_in_smem ? wbytes : 0);
-  if (smem > 227 * 1024)
+  if (smem > 227 * 1024 - 2048)   // room for the static shared memory
     return fail(HSS_ERR_INVALID, "ID: sample count d too large for the reflector buffers");
   // R1 buffers: k <= min(m, d) per item
   std::vector<int64_t> off(count);
@@ -503,8 +506,10 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
       int optin = 0;
       HSS_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
       for (auto fn : kernels()) {
+        cudaFuncAttributes fa;
+        HSS_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
         HSS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          optin - 1024));
+                                          optin - (int)fa.sharedSizeBytes));
         HSS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
       }
       done[dev] = true;

@@ -23,6 +23,7 @@ struct Err {
   do {                                                                        \
     cudaError_t e_ = (expr);                                                  \
     if (e_ != cudaSuccess) {                                                  \
+      cudaGetLastError(); /* reported here, not by a later launch check */    \
       return ::hss::fail(HSS_ERR_CUDA, std::string(#expr) + ": " +           \
                                            cudaGetErrorString(e_));           \
     }                                                                         \
