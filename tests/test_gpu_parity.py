@@ -58,6 +58,17 @@ def test_random_matrix_matches_oracle(P, dtype):
         assert np.all(np.abs(got[:, c0:c1][diff] - want[diff]) <= ulp)
 
 
+def test_random_matrix_large_sample_matches_oracle(P):
+    # a full-size block of R (2.56M entries): the FP32 evaluation with its
+    # FP64 fallback near bfloat16 rounding midpoints gives the FP64 values
+    n, c = 20000, 128
+    R = torch.zeros((n, c), dtype=torch.float32, device=DEV)
+    P.hss_random_gaussian(1003, n, 0, c, R)
+    got = R.cpu().numpy().astype(np.float64)
+    want = O.gaussian_bf16(1003, n, 0, c)
+    assert int((got != want).sum()) <= max(1, int(1e-6 * want.size))
+
+
 # ------------------------------------------------------------- sampling
 @pytest.mark.parametrize("n,leaf,dtype,c0,c1", [
     (777, 50, torch.float64, 0, 70),
