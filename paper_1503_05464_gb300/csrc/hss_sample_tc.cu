@@ -4,10 +4,12 @@
 // (Section 2.2, step 2; Algorithm 1's leaf samples: D = the leaf diagonal
 // blocks), each tile of A read from HBM once for both products.
 //
-// Work decomposition.  A is cut into 128-row panels and 64-column tiles; the
-// tiles are numbered panel-major and split evenly over one persistent CTA
-// per SM (a CTA's range may start or end inside a panel, so every CTA gets
-// the same number of tiles whatever n is).  For a tile (panel p, columns J):
+// Work decomposition.  A is cut into 128-row panels and 64-column tiles.  A
+// thread-block cluster of two CTAs takes a panel pair (2 pg, 2 pg + 1): the
+// cluster tiles (pg, J) are numbered pair-major and split evenly over the
+// clusters (one CTA per SM; a cluster's range may start or end inside a pair),
+// and the two CTAs walk the same column tiles J in step, each on its own panel
+// p.  For a tile (panel p, columns J):
 //   row product     Sr_p    += A_pJ  R_J      M = 128 rows, N = c, K = 64
 //   column product  Sc_J^T   = R_p^T A_pJ     M = c (<= 128), N = 64, K = 128
 // with A_pJ = hi + mid (+ lo) bfloat16 planes.  Both products read the same
@@ -17,26 +19,32 @@
 //
 // Pipeline (warp-specialised, mbarrier hand-offs, 576 threads):
 //   warp 0       TMA producer: FP32 half-tiles of A (128 x 32, 128-byte
-//                swizzle) into a 4-stage ring; R_J (64 rows) per tile and
+//                swizzle), one stage per converter group; R_J (64 rows) per tile and
 //                R_p (128 rows) per panel segment, bfloat16;
 //   warps 2-9    converters: two threads per row, one per half-tile; apply
 //                the leaf mask (the index range of the row's leaf), split into
 //                the bfloat16 planes (double-buffered, swizzled operand
 //                layout); two warps per scheduler keep the ALUs fed;
 //   warp 1       MMA issuer (one thread): tcgen05.mma into TMEM;
-//   warps 10-13  column drain: the column product of each tile (TMEM, double
-//                buffered) to a partial slab Sc_part[p][c][j] (j contiguous);
-//   warps 14-17  row fold: the row accumulator (TMEM, double buffered, one
-//                buffer per group of FOLD tiles) is added into a running FP32
-//                sum in TMEM; the sum is flushed to a row slab at the end of
-//                every flush group of at most 16 tiles and of every segment.
-// TMEM columns: [0,256) two row accumulators, [256,384) two column
-// accumulators, [384,512) the running row sum.
+//   warps 10-13  column drain: the column product of each tile (TMEM, three
+//                buffers) is summed over the panel pair through distributed
+//                shared memory (each CTA sends its partner the half of the 64
+//                columns the partner owns and adds the half it receives,
+//                pipelined by one tile) and written to a partial slab
+//                Sc_part[pg][c][j] (j contiguous): half the slab of one
+//                partial per panel;
+//   warps 14-17  row fold: the row accumulator (TMEM, double buffered) holds
+//                the sum over a flush group of at most 16 tiles and is written
+//                to the group's slot of a row slab.
+// TMEM columns: [0,256) two row accumulators, [256,448) three column
+// accumulators.  When the panel count is odd the last pair's second panel
+// lies past n: its tiles read the TMA's zero fill, add nothing, and flush no
+// row partial.
 //
-// Numerics: FP32 accumulation runs over at most FOLD tiles in the tensor core
-// and one flush group in the running sum; the slabs are summed in the reduce
-// kernel with compensated FP32 (Neumaier) summation in a fixed order, so the
-// result is deterministic and independent of what else runs on the GPU.
+// Numerics: FP32 accumulation runs over at most one flush group (16 tiles) in
+// the tensor core; the slabs are summed in the reduce kernel with compensated
+// FP32 (Neumaier) summation in a fixed order, so the result is deterministic
+// and independent of what else runs on the GPU.
 //
 // Every wait is bounded: on a timeout the CTA records an error code, stops,
 // waits (bounded) for its own copies and MMAs in flight, frees its TMEM and
@@ -58,8 +66,13 @@ using namespace tc;
 constexpr int BM = 128;          // panel rows
 constexpr int BN = 64;           // column tile of A
 constexpr int CMAX = 128;        // sample columns per sweep
-constexpr int ASTAGES = 4;       // FP32 half-tile ring
-constexpr int FOLD = 2;          // tiles per row accumulator buffer
+// FP32 half-tile stages: an even number (stage s serves converter group
+// s % 2); two with three bfloat16 planes (shared memory is full), four with two
+constexpr int ASTAGES_MAX = 4;
+template <int NT>
+constexpr int astages() { return NT == 3 ? 2 : 4; }
+constexpr int KC = 2;            // CTAs per cluster: panels 2g and 2g+1 reduce their column products
+constexpr int CBUF = 3;          // column accumulators in TMEM
 constexpr int FLUSH_MAX = 16;    // tiles per flush group of the running row sum, at most
 constexpr int THREADS = 576;
 constexpr long long WAIT_LIMIT = 1ll << 32;   // clock cycles (about 2 s)
@@ -68,26 +81,31 @@ constexpr uint32_t A_HALF_BYTES = BM * 32 * 4;   // 16 KB
 constexpr uint32_t PLANE_BYTES = BM * BN * 2;    // 16 KB
 constexpr uint32_t RJ_BYTES = BN * CMAX * 2;     // 16 KB (two 8 KB boxes)
 constexpr uint32_t RI_BYTES = BM * CMAX * 2;     // 32 KB (two 16 KB boxes)
-// TMEM column map
-constexpr uint32_t T_ROW = 0, T_COL = 256, T_SUM = 384;
+constexpr uint32_t X_BYTES = CMAX * (BN / KC) * 4;   // 16 KB: the partner's half of a column product
+constexpr int XSLOTS = 2;                             // exchange buffers (double buffered)
+// TMEM column map: two row accumulators (one per flush group), three column
+// accumulators
+constexpr uint32_t T_ROW = 0, T_COL = 256;
 
 template <int NT>
 struct Layout {
   static constexpr uint32_t a = 0;
-  static constexpr uint32_t planes = a + ASTAGES * A_HALF_BYTES;
+  static constexpr uint32_t planes = a + astages<NT>() * A_HALF_BYTES;
   static constexpr uint32_t rj = planes + 2 * NT * PLANE_BYTES;
   static constexpr uint32_t ri = rj + 2 * RJ_BYTES;
-  static constexpr uint32_t bars = ri + RI_BYTES;
-  static constexpr uint32_t total = bars + 256;
+  static constexpr uint32_t xb = ri + RI_BYTES;
+  static constexpr uint32_t bars = xb + XSLOTS * X_BYTES;
+  static constexpr uint32_t total = bars + 512;
   static constexpr uint32_t alloc = total + 1024;   // room to align the base to 1 KB
 };
 
 // barrier slots
 enum {
-  B_AFULL = 0, B_AEMPTY = ASTAGES, B_PFULL = 2 * ASTAGES, B_PEMPTY = B_PFULL + 2,
+  B_AFULL = 0, B_AEMPTY = ASTAGES_MAX, B_PFULL = 2 * ASTAGES_MAX, B_PEMPTY = B_PFULL + 2,
   B_RJFULL = B_PEMPTY + 2, B_RJEMPTY = B_RJFULL + 2, B_RIFULL = B_RJEMPTY + 2,
-  B_RIEMPTY = B_RIFULL + 1, B_CFULL = B_RIEMPTY + 1, B_CEMPTY = B_CFULL + 2,
-  B_RFULL = B_CEMPTY + 2, B_REMPTY = B_RFULL + 2, B_DRAIN = B_REMPTY + 2, B_COUNT = B_DRAIN + 1
+  B_RIEMPTY = B_RIFULL + 1, B_CFULL = B_RIEMPTY + 1, B_CEMPTY = B_CFULL + CBUF,
+  B_RFULL = B_CEMPTY + CBUF, B_REMPTY = B_RFULL + 2, B_DRAIN = B_REMPTY + 2, B_XFULL = B_DRAIN + 1,
+  B_XEMPTY = B_XFULL + XSLOTS, B_COUNT = B_XEMPTY + XSLOTS
 };
 
 struct TcArgs {
@@ -97,14 +115,15 @@ struct TcArgs {
   int nr;         // N of the row product (c rounded up to 16)
   int ntc;        // column tiles per panel
   int npanel;
-  long long T;    // tiles in total
-  int P;          // CTAs
+  int ngp;        // panel pairs (a cluster's two CTAs take panels 2g and 2g + 1)
+  long long T;    // cluster tiles (panel pair, column tile) in total
+  int Q;          // clusters
   int gs;         // tiles per flush group
   int ngroups;    // flush groups per panel
   const int32_t* leaf_of;    // leaf id of each index (null: no mask)
   const int32_t* leaf_lo;    // first index of each leaf id
   const int32_t* leaf_hi;    // one past the last index of each leaf id
-  float* sc_part;    // [npanel][c][npad], npad = column tiles x 64
+  float* sc_part;    // [ngp][c][npad], npad = column tiles x 64
   int npad;
   float* sr_part;    // [npanel][ngroups][2][c][128]
   int* err;
@@ -113,7 +132,7 @@ struct TcArgs {
 __host__ __device__ __forceinline__ long long tile_begin(long long q, long long T, long long P) {
   return q * T / P;
 }
-// the CTA whose tile range holds tile t
+// the cluster whose tile range holds tile t
 __host__ __device__ __forceinline__ long long tile_owner(long long t, long long T, long long P) {
   return ((t + 1) * P - 1) / T;
 }
@@ -124,17 +143,23 @@ __global__ void __launch_bounds__(THREADS, 1)
                      const __grid_constant__ CUtensorMap tmRJ,
                      const __grid_constant__ CUtensorMap tmRI, const TcArgs g) {
   using L = Layout<NT>;
+  constexpr int AS = astages<NT>();
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) &
                                            ~static_cast<uintptr_t>(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::bars);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::bars + B_COUNT * 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L::bars + B_COUNT * 8 + 4);
+  // column drain: stop after wait 0 / wait 1 of a tile, as its waiting thread
+  // saw it (one flag per wait: each is written once per tile, between the
+  // group's named barriers)
+  volatile int* dstop = abort_flag + 1;
+  volatile int* fstop = abort_flag + 3;   // the row fold warps: one per row accumulator
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   auto bar = [&](int i) { return su32(&bars[i]); };
 
   if (tid == 0) {
-    for (int i = 0; i < ASTAGES; ++i) {
+    for (int i = 0; i < AS; ++i) {
       mbar_init(bar(B_AFULL + i), 1);
       mbar_init(bar(B_AEMPTY + i), BM);
     }
@@ -143,14 +168,20 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(bar(B_PEMPTY + i), 1);
       mbar_init(bar(B_RJFULL + i), 1);
       mbar_init(bar(B_RJEMPTY + i), 1);
-      mbar_init(bar(B_CFULL + i), 1);
-      mbar_init(bar(B_CEMPTY + i), BM);
       mbar_init(bar(B_RFULL + i), 1);
       mbar_init(bar(B_REMPTY + i), BM);
+    }
+    for (int i = 0; i < CBUF; ++i) {
+      mbar_init(bar(B_CFULL + i), 1);
+      mbar_init(bar(B_CEMPTY + i), BM);
     }
     mbar_init(bar(B_RIFULL), 1);
     mbar_init(bar(B_RIEMPTY), 1);
     mbar_init(bar(B_DRAIN), 1);
+    for (int i = 0; i < XSLOTS; ++i) {
+      mbar_init(bar(B_XFULL + i), 1);
+      mbar_init(bar(B_XEMPTY + i), 1);
+    }
     *abort_flag = 0;
     fence_mbar_init();
     prefetch_tmap(&tmA);
@@ -165,9 +196,15 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   fence_after();
   const uint32_t tbase = *tslot;
+  // both CTAs of the cluster have started and initialised their barriers
+  // before either touches the other's shared memory
+  cluster_sync_all();
 
-  const long long q = blockIdx.x;
-  const long long tb = tile_begin(q, g.T, g.P), te = tile_begin(q + 1, g.T, g.P);
+  // the cluster walks cluster tiles (panel pair pg, column tile J); this CTA
+  // takes panel KC pg + crank of each
+  const int crank = static_cast<int>(cluster_ctarank());
+  const long long q = blockIdx.x / KC;
+  const long long tb = tile_begin(q, g.T, g.Q), te = tile_begin(q + 1, g.T, g.Q);
   const int ntc = g.ntc, gs = g.gs;
 
   if (warp == 0) {
@@ -175,7 +212,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       int a_cnt = 0, tl = 0, ri_cnt = 0;
       for (long long t = tb; t < te; ++t) {
-        const int p = static_cast<int>(t / ntc), J = static_cast<int>(t % ntc);
+        const int p = KC * static_cast<int>(t / ntc) + crank, J = static_cast<int>(t % ntc);
         const bool first = (t == tb) || J == 0;
         if (first) {
           if (!mbar_wait(bar(B_RIEMPTY), (ri_cnt & 1) ^ 1, abort_flag, g.err, 1, WAIT_LIMIT))
@@ -188,7 +225,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         bool ok = true;
         for (int h = 0; h < 2 && ok; ++h) {
-          const int s = a_cnt % ASTAGES, u = a_cnt / ASTAGES;
+          const int s = a_cnt % AS, u = a_cnt / AS;
           ok = mbar_wait(bar(B_AEMPTY + s), (u & 1) ^ 1, abort_flag, g.err, 2, WAIT_LIMIT);
           if (!ok) break;
           mbar_expect_tx(bar(B_AFULL + s), A_HALF_BYTES);
@@ -208,8 +245,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (*abort_flag) {
         // let every copy this thread issued land before the CTA exits
         volatile int never = 0;
-        for (int s = 0; s < ASTAGES; ++s) {
-          const int uses = (a_cnt - s + ASTAGES - 1) / ASTAGES;
+        for (int s = 0; s < AS; ++s) {
+          const int uses = (a_cnt - s + AS - 1) / AS;
           if (uses > 0) mbar_wait(bar(B_AFULL + s), (uses - 1) & 1, &never, g.err, 9, WAIT_LIMIT);
         }
         for (int r = 0; r < 2; ++r) {
@@ -237,9 +274,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         const bool gend = last || (J % gs) == gs - 1;
         if (first && !mbar_wait(bar(B_RIFULL), seg & 1, abort_flag, g.err, 4, WAIT_LIMIT)) break;
         const int ps = tl & 1, u = tl >> 1;
+        const int cb = tl % CBUF, cu = tl / CBUF;
         if (!mbar_wait(bar(B_PFULL + ps), u & 1, abort_flag, g.err, 5, WAIT_LIMIT)) break;
         if (!mbar_wait(bar(B_RJFULL + ps), u & 1, abort_flag, g.err, 6, WAIT_LIMIT)) break;
-        if (!mbar_wait(bar(B_CEMPTY + ps), (u & 1) ^ 1, abort_flag, g.err, 7, WAIT_LIMIT)) break;
+        if (!mbar_wait(bar(B_CEMPTY + cb), (cu & 1) ^ 1, abort_flag, g.err, 7, WAIT_LIMIT)) break;
         const int rb = fg & 1;
         if (since == 0 &&
             !mbar_wait(bar(B_REMPTY + rb), ((fg >> 1) & 1) ^ 1, abort_flag, g.err, 8, WAIT_LIMIT))
@@ -256,7 +294,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                      b_row + roff + ((2048 * k) >> 4), idr,
                      (since > 0 || term > 0 || k > 0) ? 1u : 0u);
         }
-        const uint32_t dc = tbase + T_COL + 64 * ps;
+        const uint32_t dc = tbase + T_COL + 64 * cb;
 #pragma unroll
         for (int term = 0; term < NT; ++term) {
 #pragma unroll
@@ -267,9 +305,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         mma_commit(bar(B_PEMPTY + ps));
         mma_commit(bar(B_RJEMPTY + ps));
-        mma_commit(bar(B_CFULL + ps));
+        mma_commit(bar(B_CFULL + cb));
         ++since;
-        if (since == FOLD || gend) {
+        if (gend) {   // the row accumulator holds the flush group's sum
           mma_commit(bar(B_RFULL + rb));
           ++fg;
           since = 0;
@@ -292,7 +330,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     int tl = 0;
     int mlo = 0, mhi = 0;   // the leaf of this thread's row: columns [mlo, mhi) are masked
     for (long long t = tb; t < te; ++t) {
-      const int p = static_cast<int>(t / ntc), J = static_cast<int>(t % ntc);
+      const int p = KC * static_cast<int>(t / ntc) + crank, J = static_cast<int>(t % ntc);
       const int ps = tl & 1, u = tl >> 1;
       const int n = g.n;
       if (t == tb || J == 0) {
@@ -304,13 +342,12 @@ __global__ void __launch_bounds__(THREADS, 1)
           mhi = g.leaf_hi[id];
         }
       }
-      if (!mbar_wait(bar(B_PEMPTY + ps), (u & 1) ^ 1, abort_flag, g.err, 11, WAIT_LIMIT)) break;
       const int j0 = J * BN;
       const int jb = j0 + h * 32;
       const bool need_mask = mlo < jb + 32 && mhi > jb;
       uint8_t* pbase = sm + L::planes + ps * NT * PLANE_BYTES;
       const int a_idx = 2 * tl + h;
-      const int s = a_idx % ASTAGES, ua = a_idx / ASTAGES;
+      const int s = a_idx % AS, ua = a_idx / AS;
       if (!mbar_wait(bar(B_AFULL + s), ua & 1, abort_flag, g.err, 12, WAIT_LIMIT)) break;
       const uint8_t* src = sm + L::a + s * A_HALF_BYTES;
       float v[32];
@@ -322,6 +359,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         v[4 * qd + 2] = x.z;
         v[4 * qd + 3] = x.w;
       }
+      // the stage goes back to the producer as soon as it is read: the fence
+      // orders these shared-memory reads before the next TMA copy into the
+      // stage, which the arrival releases (without it a late read could return
+      // the next copy's data)
+      fence_proxy_async();
+      mbar_arrive(bar(B_AEMPTY + s));
+      // the plane buffer of this tile: free once the MMAs two tiles back are done
+      if (!mbar_wait(bar(B_PEMPTY + ps), (u & 1) ^ 1, abort_flag, g.err, 11, WAIT_LIMIT)) break;
       if (need_mask) {
 #pragma unroll
         for (int e = 0; e < 32; ++e) {
@@ -355,105 +400,167 @@ __global__ void __launch_bounds__(THREADS, 1)
           *reinterpret_cast<uint4*>(pbase + 2 * PLANE_BYTES + off) =
               make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
-      // the fence orders this thread's shared-memory accesses (the stage reads
-      // and the plane writes) before the async-proxy accesses that the two
-      // arrivals release: the tensor core's plane reads and the next TMA copy
-      // into the stage (without it a late stage read can return the next
-      // tile's data)
+      // the plane writes, before the tensor core's reads that the arrival releases
       fence_proxy_async();
       mbar_arrive(bar(B_PFULL + ps));
-      mbar_arrive(bar(B_AEMPTY + s));
       ++tl;
     }
   } else if (warp >= 10 && warp < 14) {
     // ------------------------------------------------------ column drain
+    // Each tile's column product (c x 64, in one of three TMEM buffers) is
+    // summed over the cluster's two panels before it reaches HBM.  Pipelined
+    // by one tile: iteration i sends the partner the half of tile i's 64
+    // columns that the partner owns (st.async into its shared memory,
+    // counted on its X_FULL), then adds the half received for tile i - 1 to
+    // this CTA's own half of it (still in TMEM) and writes the sum to the
+    // slab row of the panel pair.  One thread does the waits and the group
+    // follows it through named barriers, so its control flow stays uniform.
     const int e = (warp & 3) * 32 + lane;       // TMEM lane: sample column
     const uint32_t loff = static_cast<uint32_t>((warp & 3) * 32) << 16;
-    const int n = g.n, c = g.c;
-    int tl = 0;
-    for (long long t = tb; t < te; ++t) {
-      const int p = static_cast<int>(t / ntc), J = static_cast<int>(t % ntc);
-      const int b = tl & 1, u = tl >> 1;
-      if (!mbar_wait(bar(B_CFULL + b), u & 1, abort_flag, g.err, 13, WAIT_LIMIT)) break;
-      __syncwarp();   // tcgen05.ld is warp-aligned: reconverge after the per-lane wait
-      fence_after();
-      float v[64];
-      tmem_ld32(tbase + loff + T_COL + 64 * b, v);
-      tmem_ld32(tbase + loff + T_COL + 64 * b + 32, v + 32);
-      tmem_wait_ld();
-      fence_before();
-      mbar_arrive(bar(B_CEMPTY + b));
-      if (e < c) {
-        // slab row (p, e) holds the tile's 64 values contiguously: 16 aligned
-        // 16-byte stores (rows are padded to whole tiles; past n the TMA fill
-        // is zero, so the pad holds zeros, which the reduction reads and drops)
-        float4* dst = reinterpret_cast<float4*>(
-            g.sc_part + (static_cast<size_t>(p) * c + e) * g.npad + static_cast<size_t>(J) * BN);
+    const int c = g.c;
+    const bool elect = warp == 10 && lane == 0;
+    constexpr int HB = BN / KC;                 // columns per half
+    const uint32_t own = static_cast<uint32_t>(crank * HB), oth = static_cast<uint32_t>((crank ^ 1) * HB);
+    const uint32_t peer = static_cast<uint32_t>(crank ^ 1);
+    const uint32_t xpeer = mapa(su32(sm + L::xb), peer);          // slot x at + x X_BYTES
+    const uint32_t xfull_peer = mapa(bar(B_XFULL), peer);          // slot x at + 8 x
+    const uint32_t xempty_peer = mapa(bar(B_XEMPTY), peer);
+    const uint32_t xrow = static_cast<uint32_t>(e) * (HB * 4);   // this thread's row of a slot
+    const int nt = static_cast<int>(te - tb);
+    for (int i = 0; i <= nt; ++i) {
+      if (i < nt) {
+        // ---- tile i: the partner's half to the partner
+        const int cb = i % CBUF, cu = i / CBUF;
+        const int xs = i % XSLOTS, xu = i / XSLOTS;
+        if (elect) {
+          // the tile's column product is in TMEM, and the partner has read
+          // what this CTA last sent it through this slot
+          const bool ok =
+              mbar_wait(bar(B_CFULL + cb), cu & 1, abort_flag, g.err, 13, WAIT_LIMIT) &&
+              mbar_wait(bar(B_XEMPTY + xs), (xu & 1) ^ 1, abort_flag, g.err, 15, WAIT_LIMIT);
+          dstop[0] = ok ? 0 : 1;
+        }
+        named_sync(1, 128);
+        if (dstop[0]) break;
+        fence_after();
+        float w[HB];
+        tmem_ld32(tbase + loff + T_COL + 64 * cb + oth, w);
+        tmem_wait_ld();
+        if (e < c) {
+          // 16-byte chunks swizzled by row: conflict-free on both sides
 #pragma unroll
-        for (int q4 = 0; q4 < BN / 4; ++q4)
-          dst[q4] = make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
+          for (int q4 = 0; q4 < HB / 4; ++q4)
+            st_async_v4(xpeer + xs * X_BYTES + xrow + ((q4 ^ (e & 7)) << 4), xfull_peer + 8 * xs,
+                        w[4 * q4], w[4 * q4 + 1], w[4 * q4 + 2], w[4 * q4 + 3]);
+        }
       }
-      ++tl;
+      if (i >= 1) {
+        // ---- tile i - 1: this CTA's half plus the partner's, to the slab
+        const int i1 = i - 1;
+        const long long t = tb + i1;
+        const int pg = static_cast<int>(t / ntc), J = static_cast<int>(t % ntc);
+        const int cb = i1 % CBUF;
+        const int xs = i1 % XSLOTS, xu = i1 / XSLOTS;
+        if (elect) {
+          mbar_expect_tx(bar(B_XFULL + xs), static_cast<uint32_t>(c) * (HB * 4));
+          dstop[1] =
+              mbar_wait(bar(B_XFULL + xs), xu & 1, abort_flag, g.err, 16, WAIT_LIMIT) ? 0 : 1;
+        }
+        named_sync(1, 128);
+        if (dstop[1]) break;
+        // the partner's half into registers, and the slot back to the partner
+        // at once (its next send into the slot waits only for these reads)
+        float r[HB];
+        {
+          const uint8_t* xslot = sm + L::xb + xs * X_BYTES + xrow;
+#pragma unroll
+          for (int q4 = 0; q4 < HB / 4; ++q4) {
+            const float4 x = *reinterpret_cast<const float4*>(xslot + ((q4 ^ (e & 7)) << 4));
+            r[4 * q4] = x.x;
+            r[4 * q4 + 1] = x.y;
+            r[4 * q4 + 2] = x.z;
+            r[4 * q4 + 3] = x.w;
+          }
+        }
+        named_sync(1, 128);
+        if (elect) mbar_arrive_remote(xempty_peer + 8 * xs);
+        fence_after();
+        float m[HB];
+        tmem_ld32(tbase + loff + T_COL + 64 * cb + own, m);
+        tmem_wait_ld();
+        fence_before();
+        mbar_arrive(bar(B_CEMPTY + cb));   // both halves of the buffer are read
+        if (e < c) {
+          // slab row (pg, e), columns J 64 + own .. + 31: the pair's sum
+          // (padded to whole tiles; past n the TMA fill is zero, so the pad
+          // holds zeros, which the reduction reads and drops)
+          float4* dst = reinterpret_cast<float4*>(g.sc_part + (static_cast<size_t>(pg) * c + e) * g.npad +
+                                                  static_cast<size_t>(J) * BN + own);
+#pragma unroll
+          for (int q4 = 0; q4 < HB / 4; ++q4)
+            dst[q4] = make_float4(m[4 * q4] + r[4 * q4], m[4 * q4 + 1] + r[4 * q4 + 1],
+                                  m[4 * q4 + 2] + r[4 * q4 + 2], m[4 * q4 + 3] + r[4 * q4 + 3]);
+        }
+      }
     }
   } else if (warp >= 14) {
     // --------------------------------------------------------- row fold
+    // At the end of a flush group (at most 16 tiles) the row accumulator
+    // (TMEM, double buffered), which holds the group's sum, goes to the
+    // group's slot of the row slab.  One thread does the waits and the group
+    // follows it through named barriers.
     const int e = (warp & 3) * 32 + lane;       // TMEM lane: panel row
     const uint32_t loff = static_cast<uint32_t>((warp & 3) * 32) << 16;
     const int c = g.c;
     const int nch = (c + 31) / 32;
-    int fg = 0, since = 0, jfirst = -1;
-    bool fresh = true;
+    const bool elect = warp == 14 && lane == 0;
+    int fg = 0, jfirst = -1;
     for (long long t = tb; t < te; ++t) {
-      const int p = static_cast<int>(t / ntc), J = static_cast<int>(t % ntc);
+      const int pg = static_cast<int>(t / ntc);
+      const int p = KC * pg + crank, J = static_cast<int>(t % ntc);
       const bool last = (t == te - 1) || J == ntc - 1;
       const bool gend = last || (J % gs) == gs - 1;
       if (jfirst < 0) jfirst = J;
-      ++since;
-      if (!(since == FOLD || gend)) continue;
-      since = 0;
+      if (!gend) continue;
+      // ---- the row slab at the end of a flush group
       const int rb = fg & 1;
-      if (!mbar_wait(bar(B_RFULL + rb), (fg >> 1) & 1, abort_flag, g.err, 14, WAIT_LIMIT)) break;
-      __syncwarp();
+      // (the flag alternates with the group: it is written again only after
+      // the next group's barrier, which every thread reaches after reading it)
+      if (elect)
+        fstop[rb] = mbar_wait(bar(B_RFULL + rb), (fg >> 1) & 1, abort_flag, g.err, 14, WAIT_LIMIT) ? 0 : 1;
+      named_sync(2, 128);
+      if (fstop[rb]) break;
       fence_after();
+      // slot (p, group, side), side 1 when the chunk starts inside the group
+      // (a cluster range began there); a panel past the last (the second of
+      // a pair when the panel count is odd) has none
+      const int grp = J / gs;
+      const int side = (jfirst % gs) != 0 ? 1 : 0;
+      float* dst = g.sr_part +
+                   ((((static_cast<size_t>(p) * g.ngroups + grp) * 2 + side) * c) * BM) + e;
       for (int ch = 0; ch < nch; ++ch) {
-        float a[32], s[32];
+        float a[32];
         tmem_ld32(tbase + loff + T_ROW + 128 * rb + 32 * ch, a);
-        if (!fresh) tmem_ld32(tbase + loff + T_SUM + 32 * ch, s);
         tmem_wait_ld();
-        if (fresh) {
-#pragma unroll
-          for (int x = 0; x < 32; ++x) s[x] = a[x];
-        } else {
-#pragma unroll
-          for (int x = 0; x < 32; ++x) s[x] += a[x];
-        }
-        if (gend) {
-          // flush: slot (p, group, side), side 1 when the chunk starts inside
-          // the group (a CTA range began there)
-          const int grp = J / gs;
-          const int side = (jfirst % gs) != 0 ? 1 : 0;
-          float* dst = g.sr_part +
-                       ((((static_cast<size_t>(p) * g.ngroups + grp) * 2 + side) * c) * BM) + e;
+        if (p < g.npanel) {
 #pragma unroll
           for (int x = 0; x < 32; ++x) {
             const int cc = 32 * ch + x;
-            if (cc < c) dst[static_cast<size_t>(cc) * BM] = s[x];
+            if (cc < c) dst[static_cast<size_t>(cc) * BM] = a[x];
           }
-        } else {
-          tmem_st32(tbase + loff + T_SUM + 32 * ch, s);
         }
       }
-      tmem_wait_st();
       fence_before();
       mbar_arrive(bar(B_REMPTY + rb));
       ++fg;
-      fresh = gend;
-      if (gend) jfirst = -1;
+      jfirst = -1;
     }
   }
 
   fence_before();
   __syncthreads();
+  // no CTA leaves while its partner may still write into its shared memory
+  cluster_sync_all();
   if (warp == 1) {
     __syncwarp();
     fence_after();
@@ -470,27 +577,27 @@ __device__ __forceinline__ void neumaier_add(float& s, float& c, float x) {
   s = t;
 }
 
-// side1[p][grp] = 1 when a CTA range starts inside flush group grp of panel p
-// (the group then has a second slot)
-__global__ void row_slot_flags_kernel(int npanel, int ntc, long long T, int P, int gs,
+// side1[pg][grp] = 1 when a cluster range starts inside flush group grp of
+// panel pair pg (both panels' groups then have a second slot)
+__global__ void row_slot_flags_kernel(int ngp, int ntc, long long T, int Q, int gs,
                                       int ngroups, uint8_t* side1) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= npanel * ngroups) return;
-  const int p = idx / ngroups, grp = idx % ngroups;
-  const long long t0 = static_cast<long long>(p) * ntc + static_cast<long long>(grp) * gs;
-  const long long t1 = static_cast<long long>(p) * ntc + min((grp + 1) * gs, ntc) - 1;
-  side1[idx] = tile_owner(t0, T, P) != tile_owner(t1, T, P) ? 1 : 0;
+  if (idx >= ngp * ngroups) return;
+  const int pg = idx / ngroups, grp = idx % ngroups;
+  const long long t0 = static_cast<long long>(pg) * ntc + static_cast<long long>(grp) * gs;
+  const long long t1 = static_cast<long long>(pg) * ntc + min((grp + 1) * gs, ntc) - 1;
+  side1[idx] = tile_owner(t0, T, Q) != tile_owner(t1, T, Q) ? 1 : 0;
 }
 
-// Sc[j, c0 + cc] = sum over panels of Sc_part[p][cc][j] (panel order; one
-// thread per 4 consecutive j of one column cc, j fastest: 16-byte reads);
+// Sc[j, c0 + cc] = sum over panel pairs of Sc_part[pg][cc][j] (pair order;
+// one thread per 4 consecutive j of one column cc, j fastest: 16-byte reads);
 // Sr[i, c0 + cc] = sum over the flush slots of row i's panel, in order (one
 // thread per (panel, cc, row), rows fastest: the slot reads are contiguous).
 __global__ void sample_tc_reduce_kernel(const float* __restrict__ sc_part,
                                         const float* __restrict__ sr_part,
                                         const uint8_t* __restrict__ side1, int n, int npad,
-                                        int c, int npanel, int ngroups, float* Sr, float* Sc,
-                                        long long lds) {
+                                        int c, int npanel, int ngp, int ngroups, float* Sr,
+                                        float* Sc, long long lds) {
   const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int nq = npad / 4;
   const long long ncv = static_cast<long long>(nq) * c;
@@ -504,7 +611,7 @@ __global__ void sample_tc_reduce_kernel(const float* __restrict__ sc_part,
 #pragma unroll
     for (int x = 0; x < 4; ++x) s[x] = k[x] = 0.f;
     int p = 0;
-    for (; p + 8 <= npanel; p += 8) {
+    for (; p + 8 <= ngp; p += 8) {
       float4 v[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) v[u] = __ldcs(reinterpret_cast<const float4*>(src + stride * (p + u)));
@@ -516,7 +623,7 @@ __global__ void sample_tc_reduce_kernel(const float* __restrict__ sc_part,
         neumaier_add(s[3], k[3], v[u].w);
       }
     }
-    for (; p < npanel; ++p) {
+    for (; p < ngp; ++p) {
       const float4 v = __ldcs(reinterpret_cast<const float4*>(src + stride * p));
       neumaier_add(s[0], k[0], v.x);
       neumaier_add(s[1], k[1], v.y);
@@ -537,7 +644,7 @@ __global__ void sample_tc_reduce_kernel(const float* __restrict__ sc_part,
     for (int grp = 0; grp < ngroups; ++grp) {
       const size_t slot = (static_cast<size_t>(p) * ngroups + grp) * 2;
       neumaier_add(s, k, __ldcs(sr_part + ((slot * c) + cc) * BM + row));
-      if (side1[p * ngroups + grp])
+      if (side1[(p / KC) * ngroups + grp])
         neumaier_add(s, k, __ldcs(sr_part + (((slot + 1) * c) + cc) * BM + row));
     }
     Sr[static_cast<size_t>(i) * lds + cc] = s + k;
@@ -595,6 +702,7 @@ Err make_map(CUtensorMap* m, CUtensorMapDataType dt, const void* base, uint64_t 
 
 struct DevInfo {
   int sms = 0;
+  int clusters = 0;   // clusters of KC CTAs that fit at once
   bool attr3 = false, attr2 = false;
 };
 
@@ -610,19 +718,20 @@ DevInfo& dev_info(int dev) {
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 struct TcPlan {
-  int npanel, ntc, P, gs, ngroups;
+  int npanel, ntc, ngp, Q, gs, ngroups;
   long long T;
 };
 
-TcPlan plan(int64_t n, int sms) {
+TcPlan plan(int64_t n, int clusters) {
   TcPlan pl;
   pl.npanel = static_cast<int>((n + BM - 1) / BM);
   pl.ntc = static_cast<int>((n + BN - 1) / BN);
-  pl.T = static_cast<long long>(pl.npanel) * pl.ntc;
-  pl.P = static_cast<int>(pl.T < sms ? pl.T : sms);
-  // a flush group holds at most one start of a CTA range: no longer than
+  pl.ngp = (pl.npanel + KC - 1) / KC;
+  pl.T = static_cast<long long>(pl.ngp) * pl.ntc;
+  pl.Q = static_cast<int>(pl.T < clusters ? pl.T : clusters);
+  // a flush group holds at most one start of a cluster range: no longer than
   // the shortest range
-  const long long per = pl.T / pl.P;
+  const long long per = pl.T / pl.Q;
   pl.gs = static_cast<int>(per < FLUSH_MAX ? per : FLUSH_MAX);
   pl.ngroups = (pl.ntc + pl.gs - 1) / pl.gs;
   return pl;
@@ -630,15 +739,15 @@ TcPlan plan(int64_t n, int sms) {
 
 }  // namespace
 
-size_t sample_tc_scratch_bytes(int64_t n, int64_t ncols, int sms) {
-  const TcPlan pl = plan(n, sms);
+size_t sample_tc_scratch_bytes(int64_t n, int64_t ncols, int clusters) {
+  const TcPlan pl = plan(n, clusters);
   const int64_t c = ncols < CMAX ? ncols : CMAX;
   const int64_t cpad = (c + 63) / 64 * 64;
   return align256(static_cast<size_t>(n) * cpad * 2) +
-         align256(static_cast<size_t>(pl.npanel) * c * pl.ntc * BN * 4) +
+         align256(static_cast<size_t>(pl.ngp) * c * pl.ntc * BN * 4) +
          align256(static_cast<size_t>(pl.npanel) * pl.ngroups * 2 * c * BM * 4) +
          2 * align256(static_cast<size_t>(n) * 4) +
-         align256(static_cast<size_t>(pl.npanel) * pl.ngroups) + 256;
+         align256(static_cast<size_t>(pl.ngp) * pl.ngroups) + 256;
 }
 
 bool sample_tc_supported(const float* A, int64_t n, int64_t lda, int mode) {
@@ -653,8 +762,45 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
   int dev = 0;
   HSS_CUDA_TRY(cudaGetDevice(&dev));
   DevInfo& di = dev_info(dev);
-  const TcPlan pl = plan(n, di.sms);
-  const size_t need = sample_tc_scratch_bytes(n, ncols, di.sms);
+  const bool three = mode == HSS_SAMPLE_BF16X3;
+  const uint32_t smem = three ? Layout<3>::alloc : Layout<2>::alloc;
+  if (!di.attr3) {
+    HSS_CUDA_TRY(cudaFuncSetAttribute(sample_tc_kernel<3>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)Layout<3>::alloc));
+    di.attr3 = true;
+  }
+  if (!di.attr2) {
+    HSS_CUDA_TRY(cudaFuncSetAttribute(sample_tc_kernel<2>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)Layout<2>::alloc));
+    di.attr2 = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = KC;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (di.clusters == 0) {
+    // the larger (three-plane) layout decides how many clusters fit at once
+    cudaLaunchConfig_t q = cfg;
+    q.gridDim = dim3(static_cast<unsigned>(di.sms / KC * KC), 1, 1);
+    q.dynamicSmemBytes = Layout<3>::alloc;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, sample_tc_kernel<3>, &q) != cudaSuccess) {
+      cudaGetLastError();
+      nc = 0;
+    }
+    di.clusters = nc > 0 ? nc : di.sms / KC;
+  }
+  const TcPlan pl = plan(n, di.clusters);
+  const size_t need = sample_tc_scratch_bytes(n, ncols, di.clusters);
   if (scratch->bytes < need) {
     dfree(scratch->part, s);
     scratch->part = nullptr;
@@ -662,18 +808,7 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     HSS_TRY(dalloc(&scratch->part, need, s));
     scratch->bytes = need;
   }
-  const bool three = mode == HSS_SAMPLE_BF16X3;
-  const uint32_t smem = three ? Layout<3>::alloc : Layout<2>::alloc;
-  if (three && !di.attr3) {
-    HSS_CUDA_TRY(cudaFuncSetAttribute(sample_tc_kernel<3>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    di.attr3 = true;
-  }
-  if (!three && !di.attr2) {
-    HSS_CUDA_TRY(cudaFuncSetAttribute(sample_tc_kernel<2>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    di.attr2 = true;
-  }
+  cfg.gridDim = dim3(static_cast<unsigned>(pl.Q * KC), 1, 1);
   // sweeps of at most 128 columns, widths balanced
   const int64_t nsw = (ncols + CMAX - 1) / CMAX;
   int64_t done = 0;
@@ -684,7 +819,7 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     __nv_bfloat16* R16 = reinterpret_cast<__nv_bfloat16*>(base);
     base += align256(static_cast<size_t>(n) * cpad * 2);
     float* scp = reinterpret_cast<float*>(base);
-    base += align256(static_cast<size_t>(pl.npanel) * c * pl.ntc * BN * 4);
+    base += align256(static_cast<size_t>(pl.ngp) * c * pl.ntc * BN * 4);
     float* srp = reinterpret_cast<float*>(base);
     base += align256(static_cast<size_t>(pl.npanel) * pl.ngroups * 2 * c * BM * 4);
     int32_t* leaf_lo = reinterpret_cast<int32_t*>(base);
@@ -692,7 +827,7 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     int32_t* leaf_hi = reinterpret_cast<int32_t*>(base);
     base += align256(static_cast<size_t>(n) * 4);
     uint8_t* side1 = base;
-    base += align256(static_cast<size_t>(pl.npanel) * pl.ngroups);
+    base += align256(static_cast<size_t>(pl.ngp) * pl.ngroups);
     int* err = reinterpret_cast<int*>(base);
     if (leaf_of != nullptr && w == 0) {
       leaf_bounds_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(
@@ -716,8 +851,9 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     g.nr = (c + 15) / 16 * 16;
     g.ntc = pl.ntc;
     g.npanel = pl.npanel;
+    g.ngp = pl.ngp;
     g.T = pl.T;
-    g.P = pl.P;
+    g.Q = pl.Q;
     g.gs = pl.gs;
     g.ngroups = pl.ngroups;
     g.leaf_of = leaf_of;
@@ -728,14 +864,16 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     g.sr_part = srp;
     g.err = err;
     HSS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-    if (three)
-      sample_tc_kernel<3><<<pl.P, THREADS, smem, s>>>(tmA, tmRJ, tmRI, g);
-    else
-      sample_tc_kernel<2><<<pl.P, THREADS, smem, s>>>(tmA, tmRJ, tmRI, g);
+    cudaError_t le = three ? cudaLaunchKernelEx(&cfg, sample_tc_kernel<3>, tmA, tmRJ, tmRI, g)
+                           : cudaLaunchKernelEx(&cfg, sample_tc_kernel<2>, tmA, tmRJ, tmRI, g);
+    if (le != cudaSuccess) {
+      cudaGetLastError();
+      return fail(HSS_ERR_CUDA, std::string("sample_tc_kernel launch: ") + cudaGetErrorString(le));
+    }
     HSS_TRY(check_launch("sample_tc_kernel"));
     {
-      const int nf = pl.npanel * pl.ngroups;
-      row_slot_flags_kernel<<<(nf + 255) / 256, 256, 0, s>>>(pl.npanel, pl.ntc, pl.T, pl.P, pl.gs,
+      const int nf = pl.ngp * pl.ngroups;
+      row_slot_flags_kernel<<<(nf + 255) / 256, 256, 0, s>>>(pl.ngp, pl.ntc, pl.T, pl.Q, pl.gs,
                                                               pl.ngroups, side1);
       HSS_TRY(check_launch("row_slot_flags_kernel"));
     }
@@ -743,13 +881,15 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     const int npad = pl.ntc * BN;
     const long long nred = static_cast<long long>(npad / 4) * c + nrow;
     sample_tc_reduce_kernel<<<static_cast<unsigned>((nred + 255) / 256), 256, 0, s>>>(
-        scp, srp, side1, static_cast<int>(n), npad, c, pl.npanel, pl.ngroups, Sr + c0 + done,
-        Sc + c0 + done, lds);
+        scp, srp, side1, static_cast<int>(n), npad, c, pl.npanel, pl.ngp, pl.ngroups,
+        Sr + c0 + done, Sc + c0 + done, lds);
     HSS_TRY(check_launch("sample_tc_reduce_kernel"));
     int herr = 0;
     HSS_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     HSS_CUDA_TRY(cudaStreamSynchronize(s));
-    if (herr) return fail(HSS_ERR_TIMEOUT, "sample_tc_kernel: a pipeline wait timed out");
+    if (herr)
+      return fail(HSS_ERR_TIMEOUT,
+                  "sample_tc_kernel: a pipeline wait timed out (wait " + std::to_string(herr) + ")");
     done += c;
   }
   return ok();
