@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   // saw it (one flag per wait: each is written once per tile, between the
   // group's named barriers)
   volatile int* dstop = abort_flag + 1;
-  volatile int* fstop = abort_flag + 3;   // the row fold warps: one per row accumulator
+  volatile int* fstop = abort_flag + 3;   // the row fold warps: one per row accumulator, one per tile
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   auto bar = [&](int i) { return su32(&bars[i]); };
 
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int i = 0; i < CBUF; ++i) {
       mbar_init(bar(B_CFULL + i), 1);
-      mbar_init(bar(B_CEMPTY + i), BM);
+      mbar_init(bar(B_CEMPTY + i), 2 * BM);   // the drain's and the fold's reads
     }
     mbar_init(bar(B_RIFULL), 1);
     mbar_init(bar(B_RIEMPTY), 1);
@@ -408,88 +408,114 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp >= 10 && warp < 14) {
     // ------------------------------------------------------ column drain
     // Each tile's column product (c x 64, in one of three TMEM buffers) is
-    // summed over the cluster's two panels before it reaches HBM.  Pipelined
-    // by one tile: iteration i sends the partner the half of tile i's 64
-    // columns that the partner owns (st.async into its shared memory,
-    // counted on its X_FULL), then adds the half received for tile i - 1 to
-    // this CTA's own half of it (still in TMEM) and writes the sum to the
-    // slab row of the panel pair.  One thread does the waits and the group
-    // follows it through named barriers, so its control flow stays uniform.
+    // summed over the cluster's two panels before it reaches HBM: these warps
+    // send the partner the half of the 64 columns that the partner owns
+    // (st.async into its shared memory, counted on its X_FULL); the row fold
+    // warps add the half received to this CTA's own half and store the sum.
+    // One thread does the waits and the group follows it through a named
+    // barrier, so its control flow stays uniform.
     const int e = (warp & 3) * 32 + lane;       // TMEM lane: sample column
     const uint32_t loff = static_cast<uint32_t>((warp & 3) * 32) << 16;
     const int c = g.c;
     const bool elect = warp == 10 && lane == 0;
     constexpr int HB = BN / KC;                 // columns per half
-    const uint32_t own = static_cast<uint32_t>(crank * HB), oth = static_cast<uint32_t>((crank ^ 1) * HB);
+    const uint32_t oth = static_cast<uint32_t>((crank ^ 1) * HB);
     const uint32_t peer = static_cast<uint32_t>(crank ^ 1);
     const uint32_t xpeer = mapa(su32(sm + L::xb), peer);          // slot x at + x X_BYTES
     const uint32_t xfull_peer = mapa(bar(B_XFULL), peer);          // slot x at + 8 x
-    const uint32_t xempty_peer = mapa(bar(B_XEMPTY), peer);
     const uint32_t xrow = static_cast<uint32_t>(e) * (HB * 4);   // this thread's row of a slot
     const int nt = static_cast<int>(te - tb);
-    for (int i = 0; i <= nt; ++i) {
-      if (i < nt) {
-        // ---- tile i: the partner's half to the partner
-        const int cb = i % CBUF, cu = i / CBUF;
-        const int xs = i % XSLOTS, xu = i / XSLOTS;
-        if (elect) {
-          // the tile's column product is in TMEM, and the partner has read
-          // what this CTA last sent it through this slot
-          const bool ok =
-              mbar_wait(bar(B_CFULL + cb), cu & 1, abort_flag, g.err, 13, WAIT_LIMIT) &&
-              mbar_wait(bar(B_XEMPTY + xs), (xu & 1) ^ 1, abort_flag, g.err, 15, WAIT_LIMIT);
-          dstop[0] = ok ? 0 : 1;
-        }
-        named_sync(1, 128);
-        if (dstop[0]) break;
-        fence_after();
-        float w[HB];
-        tmem_ld32(tbase + loff + T_COL + 64 * cb + oth, w);
-        tmem_wait_ld();
-        if (e < c) {
-          // 16-byte chunks swizzled by row: conflict-free on both sides
+    for (int i = 0; i < nt; ++i) {
+      const int cb = i % CBUF, cu = i / CBUF;
+      const int xs = i % XSLOTS, xu = i / XSLOTS;
+      // (one barrier per tile: the flag alternates, so it is written again
+      // only after the next barrier, which every thread reaches after reading)
+      if (elect) {
+        // the tile's column product is in TMEM, and the partner has read
+        // what this CTA last sent it through this slot
+        const bool ok =
+            mbar_wait(bar(B_CFULL + cb), cu & 1, abort_flag, g.err, 13, WAIT_LIMIT) &&
+            mbar_wait(bar(B_XEMPTY + xs), (xu & 1) ^ 1, abort_flag, g.err, 15, WAIT_LIMIT);
+        dstop[i & 1] = ok ? 0 : 1;
+      }
+      named_sync(1, 128);
+      if (dstop[i & 1]) break;
+      fence_after();
+      float w[HB];
+      tmem_ld32(tbase + loff + T_COL + 64 * cb + oth, w);
+      tmem_wait_ld();
+      fence_before();
+      mbar_arrive(bar(B_CEMPTY + cb));
+      if (e < c) {
+        // 16-byte chunks swizzled by row: conflict-free on both sides
 #pragma unroll
-          for (int q4 = 0; q4 < HB / 4; ++q4)
-            st_async_v4(xpeer + xs * X_BYTES + xrow + ((q4 ^ (e & 7)) << 4), xfull_peer + 8 * xs,
-                        w[4 * q4], w[4 * q4 + 1], w[4 * q4 + 2], w[4 * q4 + 3]);
+        for (int q4 = 0; q4 < HB / 4; ++q4)
+          st_async_v4(xpeer + xs * X_BYTES + xrow + ((q4 ^ (e & 7)) << 4), xfull_peer + 8 * xs,
+                      w[4 * q4], w[4 * q4 + 1], w[4 * q4 + 2], w[4 * q4 + 3]);
+      }
+    }
+  } else if (warp >= 14) {
+    // --------------------------------------------------------- row fold
+    // Per tile: the half of the column product received from the partner
+    // (an exchange slot) plus this CTA's own half (TMEM) goes to the column
+    // slab, and the slot goes back to the partner.  At the end of a flush
+    // group (at most 16 tiles) the row accumulator (TMEM, double buffered),
+    // which holds the group's sum, goes to the group's slot of the row slab.
+    // One thread does the waits and the group follows it through named
+    // barriers.
+    const int e = (warp & 3) * 32 + lane;       // TMEM lane: sample column / panel row
+    const uint32_t loff = static_cast<uint32_t>((warp & 3) * 32) << 16;
+    const int c = g.c;
+    const int nch = (c + 31) / 32;
+    const bool elect = warp == 14 && lane == 0;
+    constexpr int HB = BN / KC;
+    const uint32_t own = static_cast<uint32_t>(crank * HB);
+    const uint32_t xempty_peer = mapa(bar(B_XEMPTY), static_cast<uint32_t>(crank ^ 1));
+    const uint32_t xrow = static_cast<uint32_t>(e) * (HB * 4);
+    int fg = 0, jfirst = -1, i = 0;
+    for (long long t = tb; t < te; ++t, ++i) {
+      const int pg = static_cast<int>(t / ntc);
+      const int p = KC * pg + crank, J = static_cast<int>(t % ntc);
+      const bool last = (t == te - 1) || J == ntc - 1;
+      const bool gend = last || (J % gs) == gs - 1;
+      if (jfirst < 0) jfirst = J;
+      // ---- tile i's column sums
+      const int cb = i % CBUF, cu = i / CBUF;
+      const int xs = i % XSLOTS, xu = i / XSLOTS;
+      if (elect) {
+        // this CTA's column product of the tile is in TMEM (the buffer cannot
+        // move on to a later tile before this group has read it), and the
+        // partner's half has arrived
+        mbar_expect_tx(bar(B_XFULL + xs), static_cast<uint32_t>(c) * (HB * 4));
+        const bool ok =
+            mbar_wait(bar(B_CFULL + cb), cu & 1, abort_flag, g.err, 18, WAIT_LIMIT) &&
+            mbar_wait(bar(B_XFULL + xs), xu & 1, abort_flag, g.err, 16, WAIT_LIMIT);
+        fstop[2] = ok ? 0 : 1;
+      }
+      named_sync(2, 128);
+      if (fstop[2]) break;
+      // the partner's half into registers, and the slot back to the partner
+      float r[HB];
+      {
+        const uint8_t* xslot = sm + L::xb + xs * X_BYTES + xrow;
+#pragma unroll
+        for (int q4 = 0; q4 < HB / 4; ++q4) {
+          const float4 x = *reinterpret_cast<const float4*>(xslot + ((q4 ^ (e & 7)) << 4));
+          r[4 * q4] = x.x;
+          r[4 * q4 + 1] = x.y;
+          r[4 * q4 + 2] = x.z;
+          r[4 * q4 + 3] = x.w;
         }
       }
-      if (i >= 1) {
-        // ---- tile i - 1: this CTA's half plus the partner's, to the slab
-        const int i1 = i - 1;
-        const long long t = tb + i1;
-        const int pg = static_cast<int>(t / ntc), J = static_cast<int>(t % ntc);
-        const int cb = i1 % CBUF;
-        const int xs = i1 % XSLOTS, xu = i1 / XSLOTS;
-        if (elect) {
-          mbar_expect_tx(bar(B_XFULL + xs), static_cast<uint32_t>(c) * (HB * 4));
-          dstop[1] =
-              mbar_wait(bar(B_XFULL + xs), xu & 1, abort_flag, g.err, 16, WAIT_LIMIT) ? 0 : 1;
-        }
-        named_sync(1, 128);
-        if (dstop[1]) break;
-        // the partner's half into registers, and the slot back to the partner
-        // at once (its next send into the slot waits only for these reads)
-        float r[HB];
-        {
-          const uint8_t* xslot = sm + L::xb + xs * X_BYTES + xrow;
-#pragma unroll
-          for (int q4 = 0; q4 < HB / 4; ++q4) {
-            const float4 x = *reinterpret_cast<const float4*>(xslot + ((q4 ^ (e & 7)) << 4));
-            r[4 * q4] = x.x;
-            r[4 * q4 + 1] = x.y;
-            r[4 * q4 + 2] = x.z;
-            r[4 * q4 + 3] = x.w;
-          }
-        }
-        named_sync(1, 128);
-        if (elect) mbar_arrive_remote(xempty_peer + 8 * xs);
-        fence_after();
+      named_sync(2, 128);
+      if (elect) mbar_arrive_remote(xempty_peer + 8 * xs);
+      fence_after();
+      {
         float m[HB];
         tmem_ld32(tbase + loff + T_COL + 64 * cb + own, m);
         tmem_wait_ld();
         fence_before();
-        mbar_arrive(bar(B_CEMPTY + cb));   // both halves of the buffer are read
+        mbar_arrive(bar(B_CEMPTY + cb));
         if (e < c) {
           // slab row (pg, e), columns J 64 + own .. + 31: the pair's sum
           // (padded to whole tiles; past n the TMA fill is zero, so the pad
@@ -502,25 +528,6 @@ __global__ void __launch_bounds__(THREADS, 1)
                                   m[4 * q4 + 2] + r[4 * q4 + 2], m[4 * q4 + 3] + r[4 * q4 + 3]);
         }
       }
-    }
-  } else if (warp >= 14) {
-    // --------------------------------------------------------- row fold
-    // At the end of a flush group (at most 16 tiles) the row accumulator
-    // (TMEM, double buffered), which holds the group's sum, goes to the
-    // group's slot of the row slab.  One thread does the waits and the group
-    // follows it through named barriers.
-    const int e = (warp & 3) * 32 + lane;       // TMEM lane: panel row
-    const uint32_t loff = static_cast<uint32_t>((warp & 3) * 32) << 16;
-    const int c = g.c;
-    const int nch = (c + 31) / 32;
-    const bool elect = warp == 14 && lane == 0;
-    int fg = 0, jfirst = -1;
-    for (long long t = tb; t < te; ++t) {
-      const int pg = static_cast<int>(t / ntc);
-      const int p = KC * pg + crank, J = static_cast<int>(t % ntc);
-      const bool last = (t == te - 1) || J == ntc - 1;
-      const bool gend = last || (J % gs) == gs - 1;
-      if (jfirst < 0) jfirst = J;
       if (!gend) continue;
       // ---- the row slab at the end of a flush group
       const int rb = fg & 1;
