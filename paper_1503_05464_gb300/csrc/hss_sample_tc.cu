@@ -31,7 +31,7 @@
 //                shared memory (each CTA sends its partner the half of the 64
 //                columns the partner owns and adds the half it receives,
 //                pipelined by one tile) and written to a partial slab
-//                Sc_part[pg][c][j] (j contiguous): half the slab of one
+//                Sc_part[pg][j][c] (c contiguous): half the slab of one
 //                partial per panel;
 //   warps 14-17  row fold: the row accumulator (TMEM, double buffered) holds
 //                the sum over a flush group of at most 16 tiles and is written
@@ -123,7 +123,7 @@ struct TcArgs {
   const int32_t* leaf_of;    // leaf id of each index (null: no mask)
   const int32_t* leaf_lo;    // first index of each leaf id
   const int32_t* leaf_hi;    // one past the last index of each leaf id
-  float* sc_part;    // [ngp][c][npad], npad = column tiles x 64
+  float* sc_part;    // [ngp][npad][c], npad = column tiles x 64
   int npad;
   float* sr_part;    // [npanel][ngroups][2][c][128]
   int* err;
@@ -517,15 +517,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         fence_before();
         mbar_arrive(bar(B_CEMPTY + cb));
         if (e < c) {
-          // slab row (pg, e), columns J 64 + own .. + 31: the pair's sum
-          // (padded to whole tiles; past n the TMA fill is zero, so the pad
-          // holds zeros, which the reduction reads and drops)
-          float4* dst = reinterpret_cast<float4*>(g.sc_part + (static_cast<size_t>(pg) * c + e) * g.npad +
-                                                  static_cast<size_t>(J) * BN + own);
+          // the pair's sum for columns j = J 64 + own .. + 31 and sample
+          // column e: Sc_part[pg][j][e], so that a warp stores one whole
+          // 128-byte row per instruction (rows are padded to whole tiles;
+          // past n the TMA fill is zero, so the pad holds zeros, which the
+          // reduction never reads)
+          float* dst = g.sc_part +
+                       (static_cast<size_t>(pg) * g.npad + static_cast<size_t>(J) * BN + own) * c + e;
 #pragma unroll
-          for (int q4 = 0; q4 < HB / 4; ++q4)
-            dst[q4] = make_float4(m[4 * q4] + r[4 * q4], m[4 * q4 + 1] + r[4 * q4 + 1],
-                                  m[4 * q4 + 2] + r[4 * q4 + 2], m[4 * q4 + 3] + r[4 * q4 + 3]);
+          for (int x = 0; x < HB; ++x) dst[static_cast<size_t>(x) * c] = m[x] + r[x];
         }
       }
       if (!gend) continue;
@@ -596,50 +596,51 @@ __global__ void row_slot_flags_kernel(int ngp, int ntc, long long T, int Q, int 
   side1[idx] = tile_owner(t0, T, Q) != tile_owner(t1, T, Q) ? 1 : 0;
 }
 
-// Sc[j, c0 + cc] = sum over panel pairs of Sc_part[pg][cc][j] (pair order;
-// one thread per 4 consecutive j of one column cc, j fastest: 16-byte reads);
+// Sc[j, c0 + cc] = sum over panel pairs of Sc_part[pg][j][cc] (pair order;
+// one thread per V consecutive columns cc of one j, cc fastest);
 // Sr[i, c0 + cc] = sum over the flush slots of row i's panel, in order (one
 // thread per (panel, cc, row), rows fastest: the slot reads are contiguous).
+template <int V>
 __global__ void sample_tc_reduce_kernel(const float* __restrict__ sc_part,
                                         const float* __restrict__ sr_part,
                                         const uint8_t* __restrict__ side1, int n, int npad,
                                         int c, int npanel, int ngp, int ngroups, float* Sr,
                                         float* Sc, long long lds) {
   const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int nq = npad / 4;
-  const long long ncv = static_cast<long long>(nq) * c;
+  const int cv = c / V;
+  const long long ncv = static_cast<long long>(n) * cv;
   if (idx < ncv) {
-    const int jq = static_cast<int>(idx % nq), cc = static_cast<int>(idx / nq);
-    const int j = 4 * jq;
-    if (j >= n) return;
-    const float* src = sc_part + static_cast<size_t>(cc) * npad + j;
-    const size_t stride = static_cast<size_t>(c) * npad;
-    float s[4], k[4];
+    const int j = static_cast<int>(idx / cv), cc = static_cast<int>(idx % cv) * V;
+    const float* src = sc_part + static_cast<size_t>(j) * c + cc;
+    const size_t stride = static_cast<size_t>(npad) * c;
+    float s[V], k[V];
 #pragma unroll
-    for (int x = 0; x < 4; ++x) s[x] = k[x] = 0.f;
+    for (int x = 0; x < V; ++x) s[x] = k[x] = 0.f;
     int p = 0;
     for (; p + 8 <= ngp; p += 8) {
-      float4 v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = __ldcs(reinterpret_cast<const float4*>(src + stride * (p + u)));
+      float v[8][V];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        neumaier_add(s[0], k[0], v[u].x);
-        neumaier_add(s[1], k[1], v[u].y);
-        neumaier_add(s[2], k[2], v[u].z);
-        neumaier_add(s[3], k[3], v[u].w);
+        if constexpr (V == 4) {
+          const float4 f = __ldcs(reinterpret_cast<const float4*>(src + stride * (p + u)));
+          v[u][0] = f.x;
+          v[u][1] = f.y;
+          v[u][2] = f.z;
+          v[u][3] = f.w;
+        } else {
+          v[u][0] = __ldcs(src + stride * (p + u));
+        }
       }
-    }
-    for (; p < ngp; ++p) {
-      const float4 v = __ldcs(reinterpret_cast<const float4*>(src + stride * p));
-      neumaier_add(s[0], k[0], v.x);
-      neumaier_add(s[1], k[1], v.y);
-      neumaier_add(s[2], k[2], v.z);
-      neumaier_add(s[3], k[3], v.w);
-    }
 #pragma unroll
-    for (int x = 0; x < 4; ++x)
-      if (j + x < n) Sc[static_cast<size_t>(j + x) * lds + cc] = s[x] + k[x];
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int x = 0; x < V; ++x) neumaier_add(s[x], k[x], v[u][x]);
+    }
+    for (; p < ngp; ++p)
+#pragma unroll
+      for (int x = 0; x < V; ++x) neumaier_add(s[x], k[x], __ldcs(src + stride * p + x));
+#pragma unroll
+    for (int x = 0; x < V; ++x) Sc[static_cast<size_t>(j) * lds + cc + x] = s[x] + k[x];
   } else if (idx < ncv + static_cast<long long>(npanel) * c * BM) {
     const long long r = idx - ncv;
     const int row = static_cast<int>(r % BM);
@@ -886,10 +887,17 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     }
     const long long nrow = static_cast<long long>(pl.npanel) * c * BM;
     const int npad = pl.ntc * BN;
-    const long long nred = static_cast<long long>(npad / 4) * c + nrow;
-    sample_tc_reduce_kernel<<<static_cast<unsigned>((nred + 255) / 256), 256, 0, s>>>(
-        scp, srp, side1, static_cast<int>(n), npad, c, pl.npanel, pl.ngp, pl.ngroups,
-        Sr + c0 + done, Sc + c0 + done, lds);
+    if (c % 4 == 0) {
+      const long long nred = static_cast<long long>(n) * (c / 4) + nrow;
+      sample_tc_reduce_kernel<4><<<static_cast<unsigned>((nred + 255) / 256), 256, 0, s>>>(
+          scp, srp, side1, static_cast<int>(n), npad, c, pl.npanel, pl.ngp, pl.ngroups,
+          Sr + c0 + done, Sc + c0 + done, lds);
+    } else {
+      const long long nred = static_cast<long long>(n) * c + nrow;
+      sample_tc_reduce_kernel<1><<<static_cast<unsigned>((nred + 255) / 256), 256, 0, s>>>(
+          scp, srp, side1, static_cast<int>(n), npad, c, pl.npanel, pl.ngp, pl.ngroups,
+          Sr + c0 + done, Sc + c0 + done, lds);
+    }
     HSS_TRY(check_launch("sample_tc_reduce_kernel"));
     int herr = 0;
     HSS_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
