@@ -37,7 +37,10 @@
 //                the sum over a flush group of at most 16 tiles and is written
 //                to the group's slot of a row slab.
 // TMEM columns: [0,256) two row accumulators, [256,448) three column
-// accumulators.  When the panel count is odd the last pair's second panel
+// accumulators, [448,512) R_p^T, the column product's A operand (the drain
+// warps copy it from shared memory at the start of each panel segment, so
+// the tensor core reads only the planes from shared memory for that
+// product).  When the panel count is odd the last pair's second panel
 // lies past n: its tiles read the TMA's zero fill, add nothing, and flush no
 // row partial.
 //
@@ -84,8 +87,9 @@ constexpr uint32_t RI_BYTES = BM * CMAX * 2;     // 32 KB (two 16 KB boxes)
 constexpr uint32_t X_BYTES = CMAX * (BN / KC) * 4;   // 16 KB: the partner's half of a column product
 constexpr int XSLOTS = 2;                             // exchange buffers (double buffered)
 // TMEM column map: two row accumulators (one per flush group), three column
-// accumulators
-constexpr uint32_t T_ROW = 0, T_COL = 256;
+// accumulators, and R_p^T (the column product's A operand: lane = sample
+// column, 64 columns of bfloat16 pairs along the panel rows)
+constexpr uint32_t T_ROW = 0, T_COL = 256, T_RP = 448;
 
 template <int NT>
 struct Layout {
@@ -105,7 +109,8 @@ enum {
   B_RJFULL = B_PEMPTY + 2, B_RJEMPTY = B_RJFULL + 2, B_RIFULL = B_RJEMPTY + 2,
   B_RIEMPTY = B_RIFULL + 1, B_CFULL = B_RIEMPTY + 1, B_CEMPTY = B_CFULL + CBUF,
   B_RFULL = B_CEMPTY + CBUF, B_REMPTY = B_RFULL + 2, B_DRAIN = B_REMPTY + 2, B_XFULL = B_DRAIN + 1,
-  B_XEMPTY = B_XFULL + XSLOTS, B_COUNT = B_XEMPTY + XSLOTS
+  B_XEMPTY = B_XFULL + XSLOTS, B_RTFULL = B_XEMPTY + XSLOTS, B_RSEMPTY = B_RTFULL + 1,
+  B_COUNT = B_RSEMPTY + 1
 };
 
 struct TcArgs {
@@ -153,8 +158,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   // column drain: stop after wait 0 / wait 1 of a tile, as its waiting thread
   // saw it (one flag per wait: each is written once per tile, between the
   // group's named barriers)
-  volatile int* dstop = abort_flag + 1;
-  volatile int* fstop = abort_flag + 3;   // the row fold warps: one per row accumulator, one per tile
+  volatile int* dstop = abort_flag + 1;   // [0], [1]: per tile; [2]: R_p copy
+  volatile int* fstop = abort_flag + 4;   // the row fold warps: one per row accumulator, one per tile
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   auto bar = [&](int i) { return su32(&bars[i]); };
 
@@ -177,6 +182,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     mbar_init(bar(B_RIFULL), 1);
     mbar_init(bar(B_RIEMPTY), 1);
+    mbar_init(bar(B_RTFULL), 1);
+    mbar_init(bar(B_RSEMPTY), 1);
     mbar_init(bar(B_DRAIN), 1);
     for (int i = 0; i < XSLOTS; ++i) {
       mbar_init(bar(B_XFULL + i), 1);
@@ -215,7 +222,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int p = KC * static_cast<int>(t / ntc) + crank, J = static_cast<int>(t % ntc);
         const bool first = (t == tb) || J == 0;
         if (first) {
-          if (!mbar_wait(bar(B_RIEMPTY), (ri_cnt & 1) ^ 1, abort_flag, g.err, 1, WAIT_LIMIT))
+          // the previous segment's R_p has been copied to TMEM
+          if (!mbar_wait(bar(B_RSEMPTY), (ri_cnt & 1) ^ 1, abort_flag, g.err, 1, WAIT_LIMIT))
             break;
           mbar_expect_tx(bar(B_RIFULL), g.ncb * (RI_BYTES / 2));
           for (int cb = 0; cb < g.ncb; ++cb)
@@ -260,19 +268,18 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ------------------------------------------------------- MMA issuer
     if (lane == 0) {
       const uint32_t idr = idesc_bf16(BM, g.nr, 0, 1);    // planes K-major, R_J MN-major
-      const uint32_t idc = idesc_bf16(BM, BN, 1, 1);      // R_p^T MN-major, planes MN-major
+      const uint32_t idc = idesc_bf16(BM, BN, 0, 1);      // R_p^T from TMEM, planes MN-major
       // descriptors of stage 0; other stages and K steps add (offset >> 4)
       // to the start-address field
       const uint64_t a_row = sdesc(su32(sm + L::planes), 16, 1024);        // plane, K-major
       const uint64_t b_col = sdesc(su32(sm + L::planes), 8192, 1024);      // plane, MN-major
       const uint64_t b_row = sdesc(su32(sm + L::rj), RJ_BYTES / 2, 1024);  // R_J, MN-major
-      const uint64_t a_col = sdesc(su32(sm + L::ri), RI_BYTES / 2, 1024);  // R_p, MN-major
       int tl = 0, seg = 0, fg = 0, since = 0;
       for (long long t = tb; t < te; ++t) {
         const int J = static_cast<int>(t % ntc);
         const bool first = (t == tb) || J == 0, last = (t == te - 1) || J == ntc - 1;
         const bool gend = last || (J % gs) == gs - 1;
-        if (first && !mbar_wait(bar(B_RIFULL), seg & 1, abort_flag, g.err, 4, WAIT_LIMIT)) break;
+        if (first && !mbar_wait(bar(B_RTFULL), seg & 1, abort_flag, g.err, 4, WAIT_LIMIT)) break;
         const int ps = tl & 1, u = tl >> 1;
         const int cb = tl % CBUF, cu = tl / CBUF;
         if (!mbar_wait(bar(B_PFULL + ps), u & 1, abort_flag, g.err, 5, WAIT_LIMIT)) break;
@@ -299,9 +306,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int term = 0; term < NT; ++term) {
 #pragma unroll
           for (int k = 0; k < BM / 16; ++k)
-            mma_bf16(dc, a_col + ((2048 * k) >> 4),
-                     b_col + poff + ((term * PLANE_BYTES + 2048 * k) >> 4), idc,
-                     (term > 0 || k > 0) ? 1u : 0u);
+            mma_bf16_tmem_a(dc, tbase + T_RP + 8 * k,
+                            b_col + poff + ((term * PLANE_BYTES + 2048 * k) >> 4), idc,
+                            (term > 0 || k > 0) ? 1u : 0u);
         }
         mma_commit(bar(B_PEMPTY + ps));
         mma_commit(bar(B_RJEMPTY + ps));
@@ -425,9 +432,52 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t xfull_peer = mapa(bar(B_XFULL), peer);          // slot x at + 8 x
     const uint32_t xrow = static_cast<uint32_t>(e) * (HB * 4);   // this thread's row of a slot
     const int nt = static_cast<int>(te - tb);
+    int rseg = 0;
     for (int i = 0; i < nt; ++i) {
       const int cb = i % CBUF, cu = i / CBUF;
       const int xs = i % XSLOTS, xu = i / XSLOTS;
+      const int J = static_cast<int>((tb + i) % ntc);
+      if (i == 0 || J == 0) {
+        // a panel segment starts: R_p (bfloat16, in shared memory from the
+        // TMA) goes to TMEM transposed, as the column product's A operand,
+        // once the previous segment's MMAs are done with TMEM
+        if (elect) {
+          const bool ok =
+              mbar_wait(bar(B_RIFULL), rseg & 1, abort_flag, g.err, 19, WAIT_LIMIT) &&
+              mbar_wait(bar(B_RIEMPTY), (rseg & 1) ^ 1, abort_flag, g.err, 20, WAIT_LIMIT);
+          dstop[2] = ok ? 0 : 1;
+        }
+        named_sync(1, 128);
+        if (dstop[2]) break;
+        fence_after();
+        {
+          // lane e: R_p[r][e] for the 128 panel rows r, two per 32-bit column
+          const uint8_t* rbox = sm + L::ri + (e >> 6) * (RI_BYTES / 2);
+          const uint32_t eb = static_cast<uint32_t>(e & 63) * 2;
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            uint32_t wv[32];
+#pragma unroll
+            for (int x = 0; x < 32; ++x) {
+              const int r = 2 * (32 * half + x);
+              const uint32_t lo = *reinterpret_cast<const uint16_t*>(rbox + sw128(r, eb));
+              const uint32_t hi = *reinterpret_cast<const uint16_t*>(rbox + sw128(r + 1, eb));
+              wv[x] = lo | (hi << 16);
+            }
+            tmem_st32(tbase + loff + T_RP + 32 * half, reinterpret_cast<const float*>(wv));
+          }
+          tmem_wait_st();
+        }
+        // the reads of R_p, before the next TMA copy into its buffer
+        fence_proxy_async();
+        fence_before();
+        named_sync(1, 128);
+        if (elect) {
+          mbar_arrive(bar(B_RTFULL));    // the MMAs may read it
+          mbar_arrive(bar(B_RSEMPTY));   // the producer may load the next R_p
+        }
+        ++rseg;
+      }
       // (one barrier per tile: the flag alternates, so it is written again
       // only after the next barrier, which every thread reaches after reading)
       if (elect) {
