@@ -1,4 +1,5 @@
 // Blackwell (sm_103a) primitives as inline PTX: mbarriers, TMA tiled loads,
+// thread-block clusters and distributed shared memory,
 // TMEM allocation and access, tcgen05.mma descriptors.
 //
 // Shared-memory operand layout used throughout: "128-byte swizzled" regions
@@ -37,15 +38,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t b, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint32_t b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
 }
-__device__ __forceinline__ bool mbar_try(uint32_t b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-      : "=r"(ok)
-      : "r"(b), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
 // non-blocking test: never suspends the thread
 __device__ __forceinline__ bool mbar_test(uint32_t b, uint32_t parity) {
   uint32_t ok;
@@ -54,18 +46,6 @@ __device__ __forceinline__ bool mbar_test(uint32_t b, uint32_t parity) {
       "p; }"
       : "=r"(ok)
       : "r"(b), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// as mbar_try, but the thread may be suspended (issuing nothing) for up to
-// `hint_ns` nanoseconds while the phase is incomplete
-__device__ __forceinline__ bool mbar_try_suspend(uint32_t b, uint32_t parity, uint32_t hint_ns) {
-  uint32_t ok;
-  asm volatile(
-      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, "
-      "0, p; }"
-      : "=r"(ok)
-      : "r"(b), "r"(parity), "r"(hint_ns)
       : "memory");
   return ok != 0;
 }
@@ -88,32 +68,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t b, uint32_t parity, volatile 
   return true;
 }
 
-// as mbar_wait, with acquire at cluster scope: for phases completed by other
-// CTAs of the cluster (their st.async bytes, their remote arrivals)
-__device__ __forceinline__ bool mbar_test_cluster(uint32_t b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{ .reg .pred p; mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; "
-      "selp.u32 %0, 1, 0, p; }"
-      : "=r"(ok)
-      : "r"(b), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_cluster(uint32_t b, uint32_t parity, volatile int* abort,
-                                                  int* err, int code, long long limit) {
-  if (mbar_test_cluster(b, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_test_cluster(b, parity)) {
-    if (*abort) return false;
-    if (clock64() - t0 > limit) {
-      *abort = 1;
-      atomicCAS(err, 0, code);
-      return false;
-    }
-  }
-  return true;
-}
 
 // ------------------------------------------------------------- clusters
 __device__ __forceinline__ uint32_t cluster_ctarank() {
@@ -212,23 +166,6 @@ __device__ __forceinline__ void tmem_st32(uint32_t ta, const float* v) {
       "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
       "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
       "r"(r[29]), "r"(r[30]), "r"(r[31]));
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%"
-      "15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(ta));
-}
-__device__ __forceinline__ void tmem_st16(uint32_t ta, const uint32_t* r) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%"
-      "14,%15,%16};" ::"r"(ta),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
-      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
-      "r"(r[15]));
 }
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
