@@ -116,11 +116,34 @@ struct Cand {
   double alpha;   // x at the next pivot row
 };
 
-template <int TS>
+// A node side spread over more CTAs than a cluster holds (a "group"): the
+// group's CTAs meet at a barrier in global memory (a counter per item) and
+// exchange their candidates there; their columns stay in the global work
+// copy.  Used when one step's update is long enough (large m and d) that the
+// barrier's few microseconds are small beside it.
+struct GroupArgs {
+  int gsz;          // CTAs per item (0: the launch uses clusters)
+  Cand* cand;       // [items][2][gsz]
+  unsigned* ctr;    // [items] barrier counters, zero at launch
+  int* abort;       // set when a barrier wait gives up
+  int* err;         // first error code
+};
+constexpr long long GROUP_WAIT_LIMIT = 1ll << 33;   // clock cycles (about 4 s)
+// smallest per-CTA update of one step in cluster mode (columns x sample
+// count) for which the group mode is used
+constexpr long GROUP_MIN_STEP_WORK = 1l << 17;
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int TS, bool GRP>
 __global__ void __launch_bounds__(ID_THREADS, 1)
 id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
                        int w_in_smem, double* __restrict__ r1buf_base,
-                       const int64_t* __restrict__ r1off) {
+                       const int64_t* __restrict__ r1off, GroupArgs ga) {
   extern __shared__ __align__(16) double smem[];
   __shared__ Cand cands[2][16];
   __shared__ long long redb[ID_WARPS];
@@ -128,15 +151,57 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   __shared__ double hh[4];   // this step's sigma, tau, (unused), scale
   __shared__ int hstop;
   __shared__ int nrest;
+  __shared__ int gstop;
 
-  cg::cluster_group cluster = cg::this_cluster();
-  const int C = (int)cluster.num_blocks();
-  const int crank = (int)cluster.block_rank();
+  int C, crank;
+  if constexpr (GRP) {
+    C = ga.gsz;
+    crank = static_cast<int>(blockIdx.x) % C;
+  } else {
+    cg::cluster_group cl = cg::this_cluster();
+    C = (int)cl.num_blocks();
+    crank = (int)cl.block_rank();
+  }
   const int item = blockIdx.x / C;
   const IdItem it = items[item];
   const int m = it.m, d = it.d;
   const double rtol = it.rtol, atol = it.atol;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // every CTA of the cluster / group: a cluster barrier, or a barrier in
+  // global memory (bounded: on a timeout the launch is abandoned and every
+  // CTA returns at its next barrier)
+  unsigned nsync = 0;
+  auto sync_all = [&]() -> bool {
+    if constexpr (GRP) {
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        atomicAdd(ga.ctr + item, 1u);
+        const unsigned target = (++nsync) * static_cast<unsigned>(C);
+        const long long t0 = clock64();
+        int st = 0;
+        while (ld_acquire_gpu(ga.ctr + item) < target) {
+          if (*reinterpret_cast<volatile int*>(ga.abort)) {
+            st = 1;
+            break;
+          }
+          if (clock64() - t0 > GROUP_WAIT_LIMIT) {
+            atomicExch(ga.abort, 1);
+            atomicCAS(ga.err, 0, 1);
+            st = 1;
+            break;
+          }
+        }
+        __threadfence();
+        gstop = st;
+      }
+      __syncthreads();
+      return gstop == 0;
+    } else {
+      cg::this_cluster().sync();
+      return true;
+    }
+  };
   if (m <= 0) {
     if (crank == 0 && tid == 0) *it.k = 0;
     return;   // uniform across the cluster
@@ -192,7 +257,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   }
   // every CTA of the cluster has started (its shared memory may now be
   // written by peers) and the columns and norms are loaded
-  cluster.sync();
+  if (!sync_all()) return;
   // each CTA's candidate (largest residual norm of its active columns, as the
   // norm's bit pattern; lowest index on ties) goes into slot s of every CTA's
   // cands[s][crank], so the reads after the next cluster barrier are local
@@ -205,8 +270,16 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
       st = team_sum<32>(r + 1, d, lane, [&](int c, double a) { return fma(w[c], w[c], a); });
       alpha = r < d ? w[r] : 0.0;
     }
-    if (lane < C) {
-      Cand* dst = cluster.map_shared_rank(&cands[s][crank], lane);
+    if constexpr (GRP) {
+      if (lane == 0) {
+        Cand* dst = ga.cand + (static_cast<size_t>(item) * 2 + s) * C + crank;
+        dst->v = v;
+        dst->j = j;
+        dst->st = st;
+        dst->alpha = alpha;
+      }
+    } else if (lane < C) {
+      Cand* dst = cg::this_cluster().map_shared_rank(&cands[s][crank], lane);
       dst->v = v;
       dst->j = j;
       dst->st = st;
@@ -235,13 +308,24 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   int k = kmax;
   double r11 = 0.0;
   for (int i = 0; i < kmax; ++i) {
-    cluster.sync();   // candidates of step i pushed, updates of step i-1 done
+    if (!sync_all()) return;   // candidates of step i pushed, updates of step i-1 done
     const int slot = i & 1;
     // every warp reduces the C candidates (lane r <- CTA r): all threads agree
     // on the pivot without a block barrier
     long long bv = LLONG_MIN;
     int p = INT_MAX;
-    if (lane < C) {
+    const Cand* gc = nullptr;
+    if constexpr (GRP) {
+      gc = ga.cand + (static_cast<size_t>(item) * 2 + slot) * C;
+      for (int r = lane; r < C; r += 32) {
+        const long long v = __ldcg(&gc[r].v);
+        const int j = __ldcg(&gc[r].j);
+        if (v > bv || (v == bv && j < p)) {
+          bv = v;
+          p = j;
+        }
+      }
+    } else if (lane < C) {
       bv = cands[slot][lane].v;
       p = cands[slot][lane].j;
     }
@@ -251,7 +335,14 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
       // the reflector from the owner's pushed residual, the same arithmetic on
       // every CTA; two threads on two schedulers run the two divisions side
       // by side while the other warps copy the pivot column
-      const double st = cands[slot][owner].st, alpha = cands[slot][owner].alpha;
+      double st, alpha;
+      if constexpr (GRP) {
+        st = __ldcg(&gc[owner].st);
+        alpha = __ldcg(&gc[owner].alpha);
+      } else {
+        st = cands[slot][owner].st;
+        alpha = cands[slot][owner].alpha;
+      }
       const double sa = fma(alpha, alpha, st);
       const double sigma = sqrt(sa);
       const double r11_now = (i == 0) ? sigma : r11;
@@ -275,9 +366,13 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
       }
     } else if (tid >= 64) {
       // the pivot column, entries i..d-1, from its owner
-      const double* src = w_in_smem ? cluster.map_shared_rank(Wsm + (size_t)(p / C) * ldw, owner)
-                                     : it.work + (size_t)p * d;
-      for (int c = i + tid - 64; c < d; c += ID_THREADS - 64) vloc[c - i] = src[c];
+      if (w_in_smem) {
+        const double* src = cg::this_cluster().map_shared_rank(Wsm + (size_t)(p / C) * ldw, owner);
+        for (int c = i + tid - 64; c < d; c += ID_THREADS - 64) vloc[c - i] = src[c];
+      } else {
+        const double* src = it.work + (size_t)p * d;   // written by another CTA: read from L2
+        for (int c = i + tid - 64; c < d; c += ID_THREADS - 64) vloc[c - i] = __ldcg(src + c);
+      }
     }
     __syncthreads();
     if (i == 0) r11 = hh[0];
@@ -377,7 +472,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     }
     if (lane == 0) flag[j] = (b < 0 || b >= k) ? 1 : 0;
   }
-  cluster.sync();   // R1 and flags visible to the whole cluster
+  if (!sync_all()) return;   // R1 and flags visible to the whole cluster
   if (crank == 0 && tid == 0) *it.k = k;
   // position of each remaining column in perm[k..m): the count of remaining
   // columns of lower index
@@ -385,9 +480,9 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   for (int jl = tid; jl < mloc; jl += ID_THREADS) {
     const int j = jl * C + crank;
     int q = -1;
-    if (flag[j]) {
+    if (__ldcg(flag + j)) {
       q = 0;
-      for (int x = 0; x < j; ++x) q += flag[x];
+      for (int x = 0; x < j; ++x) q += __ldcg(flag + x);
     }
     restpos[jl] = q;
   }
@@ -407,9 +502,10 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     nrest = nr;
   }
   double* diag = vloc;    // k <= d entries
-  for (int a = tid; a < k; a += ID_THREADS) diag[a] = R1[(size_t)a * k + a];
+  for (int a = tid; a < k; a += ID_THREADS) diag[a] = __ldcg(R1 + (size_t)a * k + a);
   if (k > 0)
-    for (int c = tid; c < k - 1; c += ID_THREADS) colbuf[((k - 1) & 1) * d + c] = R1[(size_t)(k - 1) * k + c];
+    for (int c = tid; c < k - 1; c += ID_THREADS)
+      colbuf[((k - 1) & 1) * d + c] = __ldcg(R1 + (size_t)(k - 1) * k + c);
   __syncthreads();
   const int nr = nrest;
   for (int u = tid; u < nr; u += ID_THREADS) perm[k + restpos[rlist[u]]] = rlist[u] * C + crank;
@@ -417,7 +513,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     // next step's column of R1 (entries c < a - 1), by the warps not dividing
     if (a >= 1 && tid >= 32)
       for (int c = tid - 32; c < a - 1; c += ID_THREADS - 32)
-        colbuf[((a - 1) & 1) * d + c] = R1[(size_t)(a - 1) * k + c];
+        colbuf[((a - 1) & 1) * d + c] = __ldcg(R1 + (size_t)(a - 1) * k + c);
     for (int u = tid; u < nr; u += ID_THREADS) {
       const int jl = rlist[u];
       double* r2 = col(jl);
@@ -436,10 +532,16 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   }
 }
 
-using IdKernel = void (*)(const IdItem*, int, int, double*, const int64_t*);
+using IdKernel = void (*)(const IdItem*, int, int, double*, const int64_t*, GroupArgs);
 std::array<IdKernel, 6> kernels() {
-  return {id_cpqr_cluster_kernel<1>, id_cpqr_cluster_kernel<2>, id_cpqr_cluster_kernel<4>,
-          id_cpqr_cluster_kernel<8>, id_cpqr_cluster_kernel<16>, id_cpqr_cluster_kernel<32>};
+  return {id_cpqr_cluster_kernel<1, false>, id_cpqr_cluster_kernel<2, false>,
+          id_cpqr_cluster_kernel<4, false>, id_cpqr_cluster_kernel<8, false>,
+          id_cpqr_cluster_kernel<16, false>, id_cpqr_cluster_kernel<32, false>};
+}
+std::array<IdKernel, 6> group_kernels() {
+  return {id_cpqr_cluster_kernel<1, true>, id_cpqr_cluster_kernel<2, true>,
+          id_cpqr_cluster_kernel<4, true>, id_cpqr_cluster_kernel<8, true>,
+          id_cpqr_cluster_kernel<16, true>, id_cpqr_cluster_kernel<32, true>};
 }
 
 }  // namespace
@@ -512,6 +614,12 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
                                           optin - (int)fa.sharedSizeBytes));
         HSS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
       }
+      for (auto fn : group_kernels()) {
+        cudaFuncAttributes fa;
+        HSS_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+        HSS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          optin - (int)fa.sharedSizeBytes));
+      }
       done[dev] = true;
     }
   }
@@ -540,7 +648,7 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
       if (itc != occ_cache.end()) {
         nclusters = itc->second;
       } else {
-        cudaError_t oe = cudaOccupancyMaxActiveClusters(&nclusters, id_cpqr_cluster_kernel<1>, &cfg);
+        cudaError_t oe = cudaOccupancyMaxActiveClusters(&nclusters, id_cpqr_cluster_kernel<1, false>, &cfg);
         if (oe != cudaSuccess) {
           cudaGetLastError();
           nclusters = 0;
@@ -558,6 +666,17 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
     smem = base + (w_in_smem ? wbytes : 0);
     cfg.dynamicSmemBytes = smem;
   }
+  // group mode: a few large items, whose clusters would leave most SMs idle
+  // and whose steps are long (the update of a CTA's share of the columns
+  // dominates a barrier in global memory): each item gets gsz CTAs, all
+  // resident at once (cooperative launch), at least 8 columns per CTA
+  int gsz = 0;
+  {
+    const int per_item = sms / count;
+    const long step_work = (long)((max_m + C - 1) / C) * d;   // per CTA, cluster mode
+    const int g = std::min(per_item, max_m / 8);
+    if (g > 2 * C && step_work >= GROUP_MIN_STEP_WORK) gsz = g;
+  }
   // threads per column: results do not depend on it (fixed summation tree),
   // so pick the team size with the fewest FP64 instructions on the busiest of
   // the 4 schedulers.  An FP64 instruction costs the same however few lanes
@@ -567,7 +686,8 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
   // on scheduler w % 4.
   int TS = 1;
   {
-    const int mloc = (max_m + C - 1) / C;
+    const int ctas = gsz > 0 ? gsz : C;
+    const int mloc = (max_m + ctas - 1) / ctas;
     long best = -1;
     for (int ts = 1, lg = 0; ts <= 32; ts *= 2, ++lg) {
       const long groups = ((long)mloc * ts + 31) / 32;
@@ -579,14 +699,57 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
       }
     }
   }
-  const auto fns = kernels();
   int ti = 0;
   while ((1 << ti) < TS) ++ti;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, fns[ti], items_dev, f64 ? 1 : 0, w_in_smem, r1,
-                                     (const int64_t*)offd);
-  Err res = e == cudaSuccess ? check_launch("id_cpqr_cluster_kernel")
-                             : fail(HSS_ERR_CUDA, std::string("id_cpqr_cluster_kernel launch: ") +
-                                                      cudaGetErrorString(e));
+  GroupArgs ga = {};
+  Err res;
+  if (gsz > 0) {
+    const size_t gsmem = need(gsz);
+    // candidates [count][2][gsz], then the counters, the abort flag and the
+    // error code (zeroed together)
+    const size_t cand_bytes = sizeof(Cand) * 2 * (size_t)gsz * count;
+    const size_t ctl_bytes = sizeof(unsigned) * ((size_t)count + 2);
+    char* gbuf = nullptr;
+    if (scratch) HSS_TRY(scratch->alloc(reinterpret_cast<void**>(&gbuf), cand_bytes + ctl_bytes, s));
+    else HSS_TRY(dalloc(reinterpret_cast<void**>(&gbuf), cand_bytes + ctl_bytes, s));
+    ga.gsz = gsz;
+    ga.cand = reinterpret_cast<Cand*>(gbuf);
+    ga.ctr = reinterpret_cast<unsigned*>(gbuf + cand_bytes);
+    ga.abort = reinterpret_cast<int*>(ga.ctr + count);
+    ga.err = ga.abort + 1;
+    HSS_CUDA_TRY(cudaMemsetAsync(ga.ctr, 0, ctl_bytes, s));
+    cudaLaunchConfig_t gcfg = {};
+    gcfg.gridDim = dim3((unsigned)(count * gsz), 1, 1);
+    gcfg.blockDim = dim3(ID_THREADS, 1, 1);
+    gcfg.dynamicSmemBytes = gsmem;
+    gcfg.stream = s;
+    cudaLaunchAttribute gattr[1];
+    gattr[0].id = cudaLaunchAttributeCooperative;
+    gattr[0].val.cooperative = 1;
+    gcfg.attrs = gattr;
+    gcfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&gcfg, group_kernels()[ti], items_dev, f64 ? 1 : 0, 0, r1,
+                                       (const int64_t*)offd, ga);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      res = fail(HSS_ERR_CUDA, std::string("id_cpqr group launch: ") + cudaGetErrorString(e));
+    } else {
+      res = check_launch("id_cpqr_cluster_kernel");
+    }
+    if (res.st == HSS_OK) {
+      int herr = 0;
+      HSS_CUDA_TRY(cudaMemcpyAsync(&herr, ga.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      HSS_CUDA_TRY(cudaStreamSynchronize(s));
+      if (herr) res = fail(HSS_ERR_TIMEOUT, "id_cpqr: a group barrier wait timed out");
+    }
+    if (!scratch) dfree(gbuf, s);
+  } else {
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernels()[ti], items_dev, f64 ? 1 : 0, w_in_smem, r1,
+                                       (const int64_t*)offd, ga);
+    res = e == cudaSuccess ? check_launch("id_cpqr_cluster_kernel")
+                           : fail(HSS_ERR_CUDA, std::string("id_cpqr_cluster_kernel launch: ") +
+                                                    cudaGetErrorString(e));
+  }
   if (!scratch) {
     dfree(r1, s);
     dfree(offd, s);

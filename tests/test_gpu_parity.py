@@ -235,6 +235,36 @@ def test_batched_id_matches_oracle(P, dtype):
         assert err <= 10 * math.sqrt(m) * rtol * np.linalg.norm(Y, 2) + 1e-12
 
 
+def test_large_id_over_cta_groups_matches_oracle(P):
+    """A node side too large for one cluster (m = 2048 columns, d = 1024
+    samples): batches of 1, 2 and 3 items spread it over 152, 76 and 50 CTAs
+    meeting at barriers in global memory.  Same pivots and generators as the
+    oracle's CPQR (the smallest relative gap between the two largest residual
+    norms along its 503 steps is 4.6e-6, far above rounding), and the same
+    bits whatever the number of CTAs."""
+    rng = np.random.default_rng(7)
+    d, m, rtol = 1024, 2048, 1e-6
+    Y = _decaying(rng, d, m, 0.97)
+    r = O.interpolative_decomposition(Y, rtol)
+    Yt = torch.tensor(Y.T.copy(), dtype=torch.float64, device=DEV)
+    others = [torch.tensor(_decaying(rng, d, 1500, 0.9).T.copy(), dtype=torch.float64, device=DEV)
+              for _ in range(2)]
+    runs = [P.hss_id_batched([Yt] + others[:c], rtol)[0] for c in range(3)]
+    k, perm, E = runs[0]
+    assert k == r.k == 503
+    perm = perm.cpu().numpy()
+    assert list(perm[:k]) == list(r.perm[:k])
+    assert sorted(perm.tolist()) == list(range(m))
+    G = np.zeros((m, k))
+    G[perm[:k]] = np.eye(k)
+    G[perm[k:]] = E.cpu().numpy()
+    np.testing.assert_allclose(G, r.basis(), rtol=1e-7, atol=1e-9)
+    for k2, perm2, E2 in runs[1:]:
+        assert k2 == k
+        assert np.array_equal(perm2.cpu().numpy(), perm)
+        assert torch.equal(E2, runs[0][2])
+
+
 def test_batched_id_exact_rank(P):
     rng = np.random.default_rng(2)
     Ys = []
