@@ -142,6 +142,11 @@ struct Job {
     const double t0 = now_ms();
     HSS_TRY(launch_random_gaussian<T>(h->opts.seed, n(), c0, c1, R, h->dcap, s));
     float ms = 0.f;
+    // 16-tile chains in the tensor core's FP32 accumulation measured a row
+    // sample error of 1.65e-6 (relative Frobenius, a Schur complement of
+    // n = 10000), two-tile chains 3.6e-7: the long ones only where rtol is
+    // at least 60 times above that
+    scratch.row_chain = h->opts.rtol >= 1e-4 ? 16 : 2;
     HSS_TRY(launch_sample<T>(A, n(), lda, R, h->dcap, c0, c1, Sr, Sc, h->dcap, leaf_of,
                              h->opts.sample_mode, &scratch, s, timing ? &ms : nullptr));
     ms_sample += ms;

@@ -182,6 +182,11 @@ Err launch_random_gaussian(uint64_t seed, int64_t n, int64_t c0, int64_t c1, T* 
 struct SampleScratch {
   void* part = nullptr;     // partial column sums, one slab per row panel
   size_t bytes = 0;
+  // tcgen05 kernel: tiles per FP32 accumulation chain of the row product in
+  // the tensor core (1..16; the error of that accumulation grows about
+  // linearly with the chain, so short chains unless the caller's tolerance
+  // leaves room)
+  int row_chain = 2;
 };
 template <typename T>
 Err launch_sample(const T* A, int64_t n, int64_t lda, const T* R, int64_t ldr,

@@ -33,21 +33,29 @@
 //                pipelined by one tile) and written to a partial slab
 //                Sc_part[pg][j][c] (c contiguous): half the slab of one
 //                partial per panel;
-//   warps 14-17  row fold: the row accumulator (TMEM, double buffered) holds
-//                the sum over a flush group of at most 16 tiles and is written
-//                to the group's slot of a row slab.
-// TMEM columns: [0,256) two row accumulators, [256,448) three column
-// accumulators, [448,512) R_p^T, the column product's A operand (the drain
+//   warps 14-17  row fold: the row accumulator (TMEM) holds a chain of at
+//                most g.chain tiles; the fold adds it to the flush group's
+//                running sum (TMEM) and gives it back to the MMA, and writes
+//                the sum of a flush group (at most 16 tiles) to the group's
+//                slot of a row slab.  The MMA issues a tile's column product
+//                before its row product, so the tensor core stays busy while
+//                the fold reads the previous chain.
+// TMEM columns: [0,128) the row accumulator, [128,256) the running row sum,
+// [256,448) three column accumulators, [448,512) R_p^T, the column
+// product's A operand (the drain
 // warps copy it from shared memory at the start of each panel segment, so
 // the tensor core reads only the planes from shared memory for that
 // product).  When the panel count is odd the last pair's second panel
 // lies past n: its tiles read the TMA's zero fill, add nothing, and flush no
 // row partial.
 //
-// Numerics: FP32 accumulation runs over at most one flush group (16 tiles) in
-// the tensor core; the slabs are summed in the reduce kernel with compensated
-// FP32 (Neumaier) summation in a fixed order, so the result is deterministic
-// and independent of what else runs on the GPU.
+// Numerics: the tensor core's FP32 accumulation runs over at most 24 MMAs
+// (one tile of the column product, one chain of two tiles of the row
+// product; callers with a loose tolerance may ask for chains of up to 16
+// tiles); the chains of a flush group are added in FP32 by the fold warps,
+// and the slabs are summed in the reduce kernel with compensated FP32
+// (Neumaier) summation in a fixed order, so the result is deterministic and
+// independent of what else runs on the GPU.
 //
 // Every wait is bounded: on a timeout the CTA records an error code, stops,
 // waits (bounded) for its own copies and MMAs in flight, frees its TMEM and
@@ -77,6 +85,12 @@ constexpr int astages() { return NT == 3 ? 2 : 4; }
 constexpr int KC = 2;            // CTAs per cluster: panels 2g and 2g+1 reduce their column products
 constexpr int CBUF = 3;          // column accumulators in TMEM
 constexpr int FLUSH_MAX = 16;    // tiles per flush group of the running row sum, at most
+// The row product accumulates in the tensor core over chains of g.chain
+// tiles (2 by default: 24 MMAs with three planes, as many as the column
+// product's per tile); the error of the tensor core's FP32 accumulation grows
+// about linearly with the chain (measured: 16 tiles gave 4.6x the row-sample
+// error of 2 tiles), so the fold warps add the chains of a flush group in
+// FP32 on the CUDA cores.
 constexpr int THREADS = 576;
 constexpr long long WAIT_LIMIT = 1ll << 32;   // clock cycles (about 2 s)
 
@@ -86,10 +100,11 @@ constexpr uint32_t RJ_BYTES = BN * CMAX * 2;     // 16 KB (two 8 KB boxes)
 constexpr uint32_t RI_BYTES = BM * CMAX * 2;     // 32 KB (two 16 KB boxes)
 constexpr uint32_t X_BYTES = CMAX * (BN / KC) * 4;   // 16 KB: the partner's half of a column product
 constexpr int XSLOTS = 2;                             // exchange buffers (double buffered)
-// TMEM column map: two row accumulators (one per flush group), three column
-// accumulators, and R_p^T (the column product's A operand: lane = sample
-// column, 64 columns of bfloat16 pairs along the panel rows)
-constexpr uint32_t T_ROW = 0, T_COL = 256, T_RP = 448;
+// TMEM column map: the row accumulator (one chain), the flush group's running
+// row sum (fold warps only), three column accumulators, and R_p^T (the column
+// product's A operand: lane = sample column, 64 columns of bfloat16 pairs
+// along the panel rows)
+constexpr uint32_t T_ROW = 0, T_RSUM = 128, T_COL = 256, T_RP = 448;
 
 template <int NT>
 struct Layout {
@@ -108,7 +123,7 @@ enum {
   B_AFULL = 0, B_AEMPTY = ASTAGES_MAX, B_PFULL = 2 * ASTAGES_MAX, B_PEMPTY = B_PFULL + 2,
   B_RJFULL = B_PEMPTY + 2, B_RJEMPTY = B_RJFULL + 2, B_RIFULL = B_RJEMPTY + 2,
   B_RIEMPTY = B_RIFULL + 1, B_CFULL = B_RIEMPTY + 1, B_CEMPTY = B_CFULL + CBUF,
-  B_RFULL = B_CEMPTY + CBUF, B_REMPTY = B_RFULL + 2, B_DRAIN = B_REMPTY + 2, B_XFULL = B_DRAIN + 1,
+  B_RFULL = B_CEMPTY + CBUF, B_REMPTY = B_RFULL + 1, B_DRAIN = B_REMPTY + 1, B_XFULL = B_DRAIN + 1,
   B_XEMPTY = B_XFULL + XSLOTS, B_RTFULL = B_XEMPTY + XSLOTS, B_RSEMPTY = B_RTFULL + 1,
   B_COUNT = B_RSEMPTY + 1
 };
@@ -124,6 +139,7 @@ struct TcArgs {
   long long T;    // cluster tiles (panel pair, column tile) in total
   int Q;          // clusters
   int gs;         // tiles per flush group
+  int chain;      // tiles per accumulation chain of the row product (1..gs)
   int ngroups;    // flush groups per panel
   const int32_t* leaf_of;    // leaf id of each index (null: no mask)
   const int32_t* leaf_lo;    // first index of each leaf id
@@ -159,7 +175,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   // saw it (one flag per wait: each is written once per tile, between the
   // group's named barriers)
   volatile int* dstop = abort_flag + 1;   // [0], [1]: per tile; [2]: R_p copy
-  volatile int* fstop = abort_flag + 4;   // the row fold warps: one per row accumulator, one per tile
+  volatile int* fstop = abort_flag + 4;   // the row fold warps: [0], [1] by chain parity; [2] per tile
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   auto bar = [&](int i) { return su32(&bars[i]); };
 
@@ -173,9 +189,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(bar(B_PEMPTY + i), 1);
       mbar_init(bar(B_RJFULL + i), 1);
       mbar_init(bar(B_RJEMPTY + i), 1);
-      mbar_init(bar(B_RFULL + i), 1);
-      mbar_init(bar(B_REMPTY + i), BM);
     }
+    mbar_init(bar(B_RFULL), 1);
+    mbar_init(bar(B_REMPTY), BM);
     for (int i = 0; i < CBUF; ++i) {
       mbar_init(bar(B_CFULL + i), 1);
       mbar_init(bar(B_CEMPTY + i), 2 * BM);   // the drain's and the fold's reads
@@ -212,7 +228,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int crank = static_cast<int>(cluster_ctarank());
   const long long q = blockIdx.x / KC;
   const long long tb = tile_begin(q, g.T, g.Q), te = tile_begin(q + 1, g.T, g.Q);
-  const int ntc = g.ntc, gs = g.gs;
+  const int ntc = g.ntc, gs = g.gs, chain = g.chain;
 
   if (warp == 0) {
     // ------------------------------------------------------ TMA producer
@@ -274,33 +290,23 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint64_t a_row = sdesc(su32(sm + L::planes), 16, 1024);        // plane, K-major
       const uint64_t b_col = sdesc(su32(sm + L::planes), 8192, 1024);      // plane, MN-major
       const uint64_t b_row = sdesc(su32(sm + L::rj), RJ_BYTES / 2, 1024);  // R_J, MN-major
-      int tl = 0, seg = 0, fg = 0, since = 0;
+      int tl = 0, seg = 0, ch = 0, since = 0;
       for (long long t = tb; t < te; ++t) {
         const int J = static_cast<int>(t % ntc);
         const bool first = (t == tb) || J == 0, last = (t == te - 1) || J == ntc - 1;
         const bool gend = last || (J % gs) == gs - 1;
+        const bool cend = gend || ((J % gs) % chain) == chain - 1;
         if (first && !mbar_wait(bar(B_RTFULL), seg & 1, abort_flag, g.err, 4, WAIT_LIMIT)) break;
         const int ps = tl & 1, u = tl >> 1;
         const int cb = tl % CBUF, cu = tl / CBUF;
         if (!mbar_wait(bar(B_PFULL + ps), u & 1, abort_flag, g.err, 5, WAIT_LIMIT)) break;
         if (!mbar_wait(bar(B_RJFULL + ps), u & 1, abort_flag, g.err, 6, WAIT_LIMIT)) break;
         if (!mbar_wait(bar(B_CEMPTY + cb), (cu & 1) ^ 1, abort_flag, g.err, 7, WAIT_LIMIT)) break;
-        const int rb = fg & 1;
-        if (since == 0 &&
-            !mbar_wait(bar(B_REMPTY + rb), ((fg >> 1) & 1) ^ 1, abort_flag, g.err, 8, WAIT_LIMIT))
-          break;
         fence_after();
         const uint64_t poff = (ps * NT * PLANE_BYTES) >> 4;
         const uint64_t roff = (ps * RJ_BYTES) >> 4;
-        const uint32_t dr = tbase + T_ROW + 128 * rb;
-#pragma unroll
-        for (int term = 0; term < NT; ++term) {
-#pragma unroll
-          for (int k = 0; k < BN / 16; ++k)
-            mma_bf16(dr, a_row + poff + ((term * PLANE_BYTES + 32 * k) >> 4),
-                     b_row + roff + ((2048 * k) >> 4), idr,
-                     (since > 0 || term > 0 || k > 0) ? 1u : 0u);
-        }
+        // the column product first: it keeps the tensor core busy while the
+        // fold warps read the previous chain's row accumulator
         const uint32_t dc = tbase + T_COL + 64 * cb;
 #pragma unroll
         for (int term = 0; term < NT; ++term) {
@@ -310,13 +316,26 @@ __global__ void __launch_bounds__(THREADS, 1)
                             b_col + poff + ((term * PLANE_BYTES + 2048 * k) >> 4), idc,
                             (term > 0 || k > 0) ? 1u : 0u);
         }
+        if (since == 0) {
+          if (!mbar_wait(bar(B_REMPTY), (ch & 1) ^ 1, abort_flag, g.err, 8, WAIT_LIMIT)) break;
+          fence_after();
+        }
+        const uint32_t dr = tbase + T_ROW;
+#pragma unroll
+        for (int term = 0; term < NT; ++term) {
+#pragma unroll
+          for (int k = 0; k < BN / 16; ++k)
+            mma_bf16(dr, a_row + poff + ((term * PLANE_BYTES + 32 * k) >> 4),
+                     b_row + roff + ((2048 * k) >> 4), idr,
+                     (since > 0 || term > 0 || k > 0) ? 1u : 0u);
+        }
         mma_commit(bar(B_PEMPTY + ps));
         mma_commit(bar(B_RJEMPTY + ps));
         mma_commit(bar(B_CFULL + cb));
         ++since;
-        if (gend) {   // the row accumulator holds the flush group's sum
-          mma_commit(bar(B_RFULL + rb));
-          ++fg;
+        if (cend) {   // the row accumulator holds the chain's sum
+          mma_commit(bar(B_RFULL));
+          ++ch;
           since = 0;
         }
         if (last) {
@@ -508,9 +527,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     // --------------------------------------------------------- row fold
     // Per tile: the half of the column product received from the partner
     // (an exchange slot) plus this CTA's own half (TMEM) goes to the column
-    // slab, and the slot goes back to the partner.  At the end of a flush
-    // group (at most 16 tiles) the row accumulator (TMEM, double buffered),
-    // which holds the group's sum, goes to the group's slot of the row slab.
+    // slab, and the slot goes back to the partner.  At the end of a chain
+    // (at most g.chain tiles) the row accumulator is added to the flush group's
+    // running sum (TMEM, FP32 on the CUDA cores); at the end of a flush group
+    // (at most 16 tiles) the sum goes to the group's slot of the row slab.
     // One thread does the waits and the group follows it through named
     // barriers.
     const int e = (warp & 3) * 32 + lane;       // TMEM lane: sample column / panel row
@@ -522,12 +542,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t own = static_cast<uint32_t>(crank * HB);
     const uint32_t xempty_peer = mapa(bar(B_XEMPTY), static_cast<uint32_t>(crank ^ 1));
     const uint32_t xrow = static_cast<uint32_t>(e) * (HB * 4);
-    int fg = 0, jfirst = -1, i = 0;
+    int ch = 0, jfirst = -1, i = 0;
+    bool gfirst = true;   // the next chain is the first of this CTA's part of a group
     for (long long t = tb; t < te; ++t, ++i) {
       const int pg = static_cast<int>(t / ntc);
       const int p = KC * pg + crank, J = static_cast<int>(t % ntc);
       const bool last = (t == te - 1) || J == ntc - 1;
       const bool gend = last || (J % gs) == gs - 1;
+      const bool cend = gend || ((J % gs) % chain) == chain - 1;
       if (jfirst < 0) jfirst = J;
       // ---- tile i's column sums
       const int cb = i % CBUF, cu = i / CBUF;
@@ -578,15 +600,16 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int x = 0; x < HB; ++x) dst[static_cast<size_t>(x) * c] = m[x] + r[x];
         }
       }
-      if (!gend) continue;
-      // ---- the row slab at the end of a flush group
-      const int rb = fg & 1;
-      // (the flag alternates with the group: it is written again only after
-      // the next group's barrier, which every thread reaches after reading it)
+      if (!cend) continue;
+      // ---- the end of a chain: into the running sum, or to the row slab at
+      // the end of a flush group
+      const int fb = ch & 1;
+      // (the flag alternates with the chain: it is written again only after
+      // the next chain's barrier, which every thread reaches after reading it)
       if (elect)
-        fstop[rb] = mbar_wait(bar(B_RFULL + rb), (fg >> 1) & 1, abort_flag, g.err, 14, WAIT_LIMIT) ? 0 : 1;
+        fstop[fb] = mbar_wait(bar(B_RFULL), ch & 1, abort_flag, g.err, 14, WAIT_LIMIT) ? 0 : 1;
       named_sync(2, 128);
-      if (fstop[rb]) break;
+      if (fstop[fb]) break;
       fence_after();
       // slot (p, group, side), side 1 when the chunk starts inside the group
       // (a cluster range began there); a panel past the last (the second of
@@ -595,22 +618,44 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int side = (jfirst % gs) != 0 ? 1 : 0;
       float* dst = g.sr_part +
                    ((((static_cast<size_t>(p) * g.ngroups + grp) * 2 + side) * c) * BM) + e;
-      for (int ch = 0; ch < nch; ++ch) {
+      for (int q = 0; q < nch; ++q) {
         float a[32];
-        tmem_ld32(tbase + loff + T_ROW + 128 * rb + 32 * ch, a);
-        tmem_wait_ld();
-        if (p < g.npanel) {
+        tmem_ld32(tbase + loff + T_ROW + 32 * q, a);
+        if (!gfirst) {
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            float sum[16];
+            tmem_ld16(tbase + loff + T_RSUM + 32 * q + 16 * hh, sum);
+            tmem_wait_ld();
+#pragma unroll
+            for (int x = 0; x < 16; ++x) a[16 * hh + x] = sum[x] + a[16 * hh + x];
+          }
+        } else {
+          tmem_wait_ld();
+        }
+        tmem_st32(tbase + loff + T_RSUM + 32 * q, a);
+      }
+      // the running sum is in place (the next chain, or the slab stores below,
+      // read it), and the row accumulator goes back to the MMA
+      tmem_wait_st();
+      fence_before();
+      mbar_arrive(bar(B_REMPTY));
+      ++ch;
+      gfirst = gend;
+      if (!gend) continue;
+      jfirst = -1;
+      if (p < g.npanel) {
+        for (int q = 0; q < nch; ++q) {
+          float a[32];
+          tmem_ld32(tbase + loff + T_RSUM + 32 * q, a);
+          tmem_wait_ld();
 #pragma unroll
           for (int x = 0; x < 32; ++x) {
-            const int cc = 32 * ch + x;
+            const int cc = 32 * q + x;
             if (cc < c) dst[static_cast<size_t>(cc) * BM] = a[x];
           }
         }
       }
-      fence_before();
-      mbar_arrive(bar(B_REMPTY + rb));
-      ++fg;
-      jfirst = -1;
     }
   }
 
@@ -913,6 +958,7 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     g.T = pl.T;
     g.Q = pl.Q;
     g.gs = pl.gs;
+    g.chain = std::max(1, std::min(scratch->row_chain, pl.gs));
     g.ngroups = pl.ngroups;
     g.leaf_of = leaf_of;
     g.leaf_lo = leaf_lo;

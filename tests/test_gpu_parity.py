@@ -157,6 +157,30 @@ def test_tensor_core_sampling_matches_oracle(P, mode, n, leaf, c0, c1, pad):
         assert np.abs(gr[:, c0:c1] - wr).max() <= 1e-5 * np.abs(wr).max()
 
 
+def test_tensor_core_sampling_accuracy_on_schur_complement(P):
+    """bf16x3 samples of the Schur complement of the 7-point Laplacian
+    (n = 10000, leaf 256, 128 columns) against the oracle's FP64 leaf
+    samples: relative Frobenius error <= 6e-7 in both products.  The
+    tensor core's FP32 accumulation runs over at most 24 MMAs in either
+    product; with the row product accumulated over 16-tile groups its error
+    was 1.65e-6 here (plain FP32 SIMT sampling: 1.1e-7 / 2.0e-7), enough to
+    raise the ranks at rtol 1e-6 from 691 to 886."""
+    At = W.laplacian_schur(100, dtype=np.float32, device=DEV)
+    n, c = At.shape[0], 128
+    nodes = O.bisection_tree(n, 256)
+    starts = sorted(nd.lo for nd in nodes if nd.is_leaf) + [n]
+    R = torch.zeros((n, c), dtype=torch.float32, device=DEV)
+    P.hss_random_gaussian(11, n, 0, c, R)
+    Sr = torch.empty((n, c), device=DEV)
+    Sc = torch.empty((n, c), device=DEV)
+    P.hss_sample(At, R, 0, c, Sr, Sc, leaf_starts=starts, mode="bf16x3")
+    torch.cuda.synchronize()
+    wr, wc = O.leaf_local_samples(At.cpu().numpy(), R.cpu().numpy(), nodes)
+    er = _rel(Sr.cpu().numpy().astype(np.float64), wr)
+    ec = _rel(Sc.cpu().numpy().astype(np.float64), wc)
+    assert er <= 6e-7 and ec <= 6e-7, (er, ec)
+
+
 @pytest.mark.parametrize("mode", ["bf16x2", "bf16x3"])
 def test_tensor_core_sampling_repeats_identically(P, mode):
     # many CTAs, a ragged tail and a masked leaf diagonal: every repeat must
