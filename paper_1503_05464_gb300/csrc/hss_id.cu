@@ -684,25 +684,24 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
   // and update), 32 / TS - 1 in-thread and log2 TS shuffle additions, and the
   // multiplication by tau.  Team groups go to warps round-robin, warp w runs
   // on scheduler w % 4.
-  int TS = 1;
-  {
-    const int ctas = gsz > 0 ? gsz : C;
+  auto team_index = [&](int ctas) {
     const int mloc = (max_m + ctas - 1) / ctas;
     long best = -1;
+    int ti = 0;
     for (int ts = 1, lg = 0; ts <= 32; ts *= 2, ++lg) {
       const long groups = ((long)mloc * ts + 31) / 32;
       const long per = 2 * ((d + ts - 1) / ts) + (32 / ts - 1) + lg + 1;
       const long cost = (groups + 3) / 4 * per;
       if (best < 0 || cost < best) {
         best = cost;
-        TS = ts;
+        ti = lg;
       }
     }
-  }
-  int ti = 0;
-  while ((1 << ti) < TS) ++ti;
+    return ti;
+  };
   GroupArgs ga = {};
   Err res;
+  bool done = false;
   if (gsz > 0) {
     const size_t gsmem = need(gsz);
     // candidates [count][2][gsz], then the counters, the abort flag and the
@@ -728,24 +727,32 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
     gattr[0].val.cooperative = 1;
     gcfg.attrs = gattr;
     gcfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&gcfg, group_kernels()[ti], items_dev, f64 ? 1 : 0, 0, r1,
-                                       (const int64_t*)offd, ga);
-    if (e != cudaSuccess) {
+    cudaError_t e = cudaLaunchKernelEx(&gcfg, group_kernels()[team_index(gsz)], items_dev,
+                                       f64 ? 1 : 0, 0, r1, (const int64_t*)offd, ga);
+    if (e == cudaErrorCooperativeLaunchTooLarge) {
+      // fewer SMs than expected are free for this context: clusters instead
       cudaGetLastError();
-      res = fail(HSS_ERR_CUDA, std::string("id_cpqr group launch: ") + cudaGetErrorString(e));
     } else {
-      res = check_launch("id_cpqr_cluster_kernel");
-    }
-    if (res.st == HSS_OK) {
-      int herr = 0;
-      HSS_CUDA_TRY(cudaMemcpyAsync(&herr, ga.err, sizeof(int), cudaMemcpyDeviceToHost, s));
-      HSS_CUDA_TRY(cudaStreamSynchronize(s));
-      if (herr) res = fail(HSS_ERR_TIMEOUT, "id_cpqr: a group barrier wait timed out");
+      done = true;
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        res = fail(HSS_ERR_CUDA, std::string("id_cpqr group launch: ") + cudaGetErrorString(e));
+      } else {
+        res = check_launch("id_cpqr_cluster_kernel");
+      }
+      if (res.st == HSS_OK) {
+        int herr = 0;
+        HSS_CUDA_TRY(cudaMemcpyAsync(&herr, ga.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        HSS_CUDA_TRY(cudaStreamSynchronize(s));
+        if (herr) res = fail(HSS_ERR_TIMEOUT, "id_cpqr: a group barrier wait timed out");
+      }
     }
     if (!scratch) dfree(gbuf, s);
-  } else {
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kernels()[ti], items_dev, f64 ? 1 : 0, w_in_smem, r1,
-                                       (const int64_t*)offd, ga);
+    ga = GroupArgs{};
+  }
+  if (!done) {
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernels()[team_index(C)], items_dev, f64 ? 1 : 0,
+                                       w_in_smem, r1, (const int64_t*)offd, ga);
     res = e == cudaSuccess ? check_launch("id_cpqr_cluster_kernel")
                            : fail(HSS_ERR_CUDA, std::string("id_cpqr_cluster_kernel launch: ") +
                                                     cudaGetErrorString(e));
