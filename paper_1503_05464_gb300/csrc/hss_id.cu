@@ -33,6 +33,14 @@
 // buffer, and each CTA solves T = R1^{-1} R2 for the remaining columns it owns
 // (column-oriented back substitution, all threads of the CTA), writing E = T^T
 // so that the generator is Pi [I; E].
+//
+// Group mode: when a launch holds a few large items (a CTA's share of one
+// step is long), each item instead gets floor(SMs / items) CTAs of one
+// cooperative launch, so that every SM works.  They keep their columns in the
+// global work copy, exchange candidates through global memory and meet at a
+// bounded barrier in global memory (a counter per item); each column's
+// arithmetic is that of the cluster mode, so the bits do not depend on the
+// number of CTAs.
 #include "hss_internal.cuh"
 
 #include <cooperative_groups.h>
