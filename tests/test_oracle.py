@@ -53,6 +53,16 @@ def test_bf16_rounding_closed_form():
     np.testing.assert_array_equal(O.round_to_bf16(x), want)
 
 
+def test_splitmix64_known_answers():
+    # the first five outputs of SplitMix64 (Steele, Lea, Flood 2014) seeded
+    # with 1234567, the known-answer values that accompany reference
+    # implementations of the generator
+    want = [6457827717110365317, 3203168211198807973, 9817491932198370423,
+            4593380528125082431, 16408922859458223821]
+    got = O.splitmix64(1234567, np.arange(1, 6, dtype=np.uint64))
+    assert [int(x) for x in got] == want
+
+
 def test_random_matrix_is_gaussian_bf16():
     R = O.gaussian_bf16(1234, 4000, 0, 64)
     # every value is exactly representable in bfloat16 (8 significant bits)
