@@ -107,9 +107,10 @@ hss_status hss_default_opts(hss_opts* opts);
  *          are copied out, the caller may free A afterwards.
  *   opts   host; NULL = hss_default_opts.
  *   out    host; receives a new handle (NULL on error).
- * Errors: INVALID (n < 1, lda < n, bad options), OOM, CUDA, RANK_CAP (the
- * handle is still returned in *out with the nodes that did compress, and
- * must be destroyed).  Synchronizes `stream`.
+ * Errors: INVALID (n < 1, lda < n, bad options), OOM, CUDA, TIMEOUT (a
+ * bounded device-side wait of the sampling or ID kernels gave up; no handle),
+ * RANK_CAP (the handle is still returned in *out with the nodes that did
+ * compress, and must be destroyed).  Synchronizes `stream`.
  */
 hss_status hss_compress(const void* A, int64_t n, int64_t lda, hss_dtype dtype,
                         const hss_opts* opts, void* stream, hss_t* out);
@@ -239,7 +240,12 @@ hss_status hss_random_gaussian(uint64_t seed, int64_t n, int64_t c0, int64_t c1,
  * mask, Sr(I_t, :) is Algorithm 1's S^r_loc = S^r(I_t,:) - D_t R(I_t,:).
  *   A  device n x n row-major (lda);  R, Sr, Sc device n x ld row-major with
  *   ldr / lds >= c1.  mode: hss_sample_mode (NATIVE only for HSS_F64).
- * Errors: INVALID, OOM (scratch for the partial sums), CUDA.  Stream-ordered.
+ * The split-BF16 modes on the tensor cores accumulate in FP32 over at most
+ * 24 MMAs at a time and sum those partial results in FP32 on the CUDA cores.
+ * Errors: INVALID, OOM (scratch for the partial sums), CUDA, TIMEOUT (a
+ * bounded pipeline wait of the tensor-core kernel gave up).  The tensor-core
+ * path synchronizes the stream to read its error flag; the others are
+ * stream-ordered.
  */
 hss_status hss_sample(const void* A, int64_t n, int64_t lda, hss_dtype dtype,
                       const void* R, int64_t ldr, int64_t c0, int64_t c1,
@@ -264,7 +270,12 @@ hss_status hss_sample(const void* A, int64_t n, int64_t lda, hss_dtype dtype,
  *          needs m_b * min(d_b, m_b) doubles at most.  E = (R1^{-1} R2)^T,
  *          so that X^T = Pi [I; E] with Pi the permutation `perm`.
  *   k      device int32 array (count): the ranks.
- * Errors: INVALID, OOM, CUDA.  Stream-ordered.
+ * A few large items are spread over all SMs (a cooperative launch whose CTAs
+ * meet at a bounded barrier in global memory); the results are bitwise the
+ * same either way.
+ * Errors: INVALID, OOM, CUDA, TIMEOUT (a barrier wait of that mode gave up;
+ * the outputs are then undefined).  Stream-ordered, except that the
+ * spread-out mode synchronizes the stream to read its error flag.
  */
 hss_status hss_id_batched(int32_t count, const void* const* Yt, const int32_t* m,
                           const int32_t* d, const int32_t* ldy, hss_dtype dtype,
