@@ -284,30 +284,47 @@ hss_status hss_id_batched(int32_t count, const void* const* Yt, const int32_t* m
 
 /*
  * hss_sample_noalloc -- hss_sample for callers that cannot allocate device
- * memory (the paper has no counterpart: this is a deployment variant).  A
- * host application whose memory manager owns the whole GPU, a serving loop
- * that allows no allocator call after start-up (cudaMalloc can block and
- * synchronize the device), or code that issues work while a stream is being
- * captured (where cudaMalloc is not allowed) can call this instead.
+ * memory.  The paper has no counterpart: this is a deployment variant.  Two
+ * kinds of caller need it: a host application whose own memory manager owns
+ * the whole GPU (memory taken behind its back breaks its budget), and a
+ * serving loop that allows no allocator call once it runs, because cudaMalloc
+ * and cudaFree can block or synchronize the device and stall other work.
  *   Same arguments, layouts and results as hss_sample; the caller still
- *   provides A, R, Sr and Sc.  The scratch (partial column sums, leaf mask)
- *   lives in fixed file-scope device arrays of the library, about 16 MiB per
- *   GPU that loads it, held until the process exits.
- *   Limits: n <= 2048, c1 - c0 <= 64, nleaf <= 2048; larger problems return
- *   HSS_ERR_INVALID (use hss_sample).  It calls no cudaMalloc or cudaFree.
+ *   provides A, R, Sr and Sc.  The scratch (partial sums of both products,
+ *   the leaf mask) lives in fixed file-scope device arrays of the library,
+ *   about 36 MiB on every GPU that loads it, held until the process exits.
+ *   Limits: n <= 2048, c1 - c0 <= 64, nleaf <= 2048; larger problems, and any
+ *   call whose scratch need exceeds the fixed arrays, return HSS_ERR_INVALID
+ *   before any work is queued (use hss_sample).  It calls no cudaMalloc,
+ *   cudaFree or other allocating routine.
  *   The first call on a device looks up the arrays' device addresses with
- *   cudaGetSymbolAddress (with that device current): make that first call
- *   before any stream capture.  Every call shares the same arrays, which keep
- *   the last call's contents (nothing in them needs to start at zero: a call
- *   writes every entry it reads); calls whose GPU work overlaps -- two
- *   streams, two threads -- race on them, so serialize them.
- * Errors: INVALID, CUDA (message in hss_last_error(NULL)).  Stream-ordered.
+ *   cudaGetSymbolAddress (with that device current); make that first call
+ *   before any stream capture.  leaf_starts is copied to the device with
+ *   cudaMemcpyAsync from the caller's host memory: from pageable memory that
+ *   copy returns only once the bytes are staged, pinned memory keeps it
+ *   asynchronous.  The split-BF16 modes on the tensor cores synchronize the
+ *   stream to read their error flag, as in hss_sample.
+ *   Every call shares the same arrays, which keep the last call's contents
+ *   (nothing in them needs to start at zero: a call writes every entry it
+ *   reads); calls whose GPU work overlaps -- two streams, two threads --
+ *   race on them, so serialize them.
+ * Errors: INVALID, CUDA, TIMEOUT (message in hss_last_error(NULL)).
  */
 hss_status hss_sample_noalloc(const void* A, int64_t n, int64_t lda, hss_dtype dtype,
                               const void* R, int64_t ldr, int64_t c0, int64_t c1,
                               void* Sr, void* Sc, int64_t lds,
                               const int64_t* leaf_starts, int32_t nleaf, int32_t mode,
                               void* stream);
+
+/*
+ * hss_pool_bytes -- device memory of the library's private stream-ordered
+ * pool on the current device: *used = bytes currently handed out (handles,
+ * temporaries of calls in flight), *reserved = bytes the pool holds from the
+ * device (freed memory is kept for reuse).  Either pointer may be NULL.  The
+ * fixed arrays of hss_sample_noalloc are not part of the pool.
+ * Errors: CUDA.
+ */
+hss_status hss_pool_bytes(int64_t* used, int64_t* reserved);
 
 #ifdef __cplusplus
 }

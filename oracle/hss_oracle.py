@@ -19,7 +19,7 @@ dense HSS matrix computations using randomization", arXiv:1503.05464):
 * ULV-like factorization                          -- Algorithm 3
 * solution with the ULV factors                   -- Algorithm 4, Appendix A
 
-Readings taken where the paper is silent (each is also listed in the design doc):
+Readings taken where the paper is silent:
 
 * One random matrix R serves both samples (S^r = A R, S^c = A^T R).
 * R[i, j] is a standard Gaussian made from the splitmix64 sequence with

@@ -115,6 +115,21 @@ void hss_destroy(hss_t h) { delete h; }
 
 int64_t hss_kernel_launches(void) { return launches_so_far(); }
 
+hss_status hss_pool_bytes(int64_t* used, int64_t* reserved) {
+  cudaMemPool_t pool;
+  Err e = library_pool(&pool);
+  if (e.st) return set_err(nullptr, e);
+  uint64_t u = 0, r = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u) != cudaSuccess ||
+      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(nullptr, fail(HSS_ERR_CUDA, "hss_pool_bytes: reading the pool attributes"));
+  }
+  if (used) *used = (int64_t)u;
+  if (reserved) *reserved = (int64_t)r;
+  return HSS_OK;
+}
+
 hss_status hss_info(hss_t h, hss_info_t* info) {
   if (!h || !info) return HSS_ERR_INVALID;
   *info = h->info;

@@ -187,6 +187,10 @@ struct SampleScratch {
   // linearly with the chain, so short chains unless the caller's tolerance
   // leaves room)
   int row_chain = 2;
+  // the memory belongs to someone else (a fixed array): a launcher that would
+  // need more returns HSS_ERR_INVALID before queuing work, instead of freeing
+  // and reallocating it
+  bool fixed = false;
 };
 template <typename T>
 Err launch_sample(const T* A, int64_t n, int64_t lda, const T* R, int64_t ldr,
@@ -194,6 +198,11 @@ Err launch_sample(const T* A, int64_t n, int64_t lda, const T* R, int64_t ldr,
                   const int32_t* leaf_of, int mode, SampleScratch* scratch,
                   cudaStream_t s, float* ms_out);
 size_t sample_scratch_bytes(int64_t n, int64_t ncols, int mode, bool f64);
+// Scratch bytes launch_sample needs for this call (the kernel it picks
+// depends on the mode, A's alignment and lda; the tensor-core kernel's need
+// on the device's cluster count).
+Err sample_scratch_need(const void* A, int64_t n, int64_t lda, int64_t ncols, int mode, bool f64,
+                        size_t* need);
 
 // ------------------------------------------------------- batched FP64 ID
 // One item: Y stored transposed (m rows of d values, row j = column j of Y).

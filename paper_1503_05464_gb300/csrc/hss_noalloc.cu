@@ -2,13 +2,12 @@
 // not allocate device memory.
 //
 // Who cannot allocate: a host application whose own memory manager owns the
-// whole device (allocating behind its back breaks its budget), a serving loop
-// that forbids allocator calls after start-up because cudaMalloc can block or
-// synchronize the device and stall latency-critical work, and code that issues
-// its work while a CUDA stream is being captured into a graph, where
-// cudaMalloc is not permitted.  For them this variant runs the same kernels as
-// hss_sample but keeps its scratch (the per-panel partial column sums and the
-// leaf-id mask) in file-scope device arrays of fixed size that are part of the
+// whole device (memory taken behind its back breaks its budget), and a
+// serving loop that allows no allocator calls once it is running, because
+// cudaMalloc and cudaFree can block or synchronize the device and stall
+// latency-critical work.  For them this variant runs the same kernels as
+// hss_sample but keeps its scratch (the per-panel partial sums and the leaf
+// mask) in file-scope device arrays of fixed size that are part of the
 // library image: every GPU that loads libhss holds them until the process
 // exits, and no call here allocates or frees anything.
 #include "hss_internal.cuh"
@@ -25,10 +24,13 @@ constexpr int64_t NOALLOC_MAX_COLS = 64;    // sample columns per call (c1 - c0)
 constexpr int NOALLOC_MAX_LEAVES = 2048;    // leaves of the mask
 constexpr int NOALLOC_MAX_DEVICES = 64;
 
-// Partial column sums: one slab of n x 64 values per 128-row panel, FP64-sized
-// so that either precision fits: 16 panels x 2048 x 64 x 8 bytes = 16 MiB.
-constexpr size_t NOALLOC_PART_BYTES =
-    (size_t)((NOALLOC_MAX_N + 127) / 128) * NOALLOC_MAX_N * 64 * sizeof(double);
+// Partial sums of both products.  Within the limits above the CUDA-core
+// kernels need at most 16 MiB (16 panels x 2048 x 64 FP64 values) and the
+// tensor-core kernel at most 35.2 MiB (its bfloat16 copy of R plus column and
+// row slabs; largest at n = 1983 with 125 clusters of two CTAs), so 36 MiB
+// holds every accepted call.  The need of each call is still checked before
+// any work is queued.
+constexpr size_t NOALLOC_PART_BYTES = (size_t)36 << 20;
 
 static __device__ __align__(256) unsigned char g_noalloc_part[NOALLOC_PART_BYTES];
 static __device__ __align__(256) int32_t g_noalloc_leaf_of[NOALLOC_MAX_N];
@@ -114,6 +116,14 @@ extern "C" hss_status hss_sample_noalloc(const void* A, int64_t n, int64_t lda, 
   NoallocPtrs* p = nullptr;
   Err e = noalloc_setup(&p);
   if (e.st) return noalloc_fail(e);
+  size_t need = 0;
+  e = sample_scratch_need(A, n, lda, c1 - c0, mode, dtype == HSS_F64, &need);
+  if (e.st) return noalloc_fail(e);
+  if (need > NOALLOC_PART_BYTES)
+    return noalloc_fail(fail(HSS_ERR_INVALID,
+                             "hss_sample_noalloc: this call needs " + std::to_string(need) +
+                                 " bytes of scratch, more than the fixed " +
+                                 std::to_string(NOALLOC_PART_BYTES) + "; use hss_sample"));
   const int32_t* lof = nullptr;
   if (nleaf > 0) {
     if (cudaMemcpyAsync(p->leaf_starts, leaf_starts, sizeof(int64_t) * (nleaf + 1),
@@ -125,10 +135,12 @@ extern "C" hss_status hss_sample_noalloc(const void* A, int64_t n, int64_t lda, 
     if (e.st) return noalloc_fail(e);
     lof = p->leaf_of;
   }
-  // the whole fixed slab is offered as the sampling scratch, so it never grows
+  // the whole fixed slab is the sampling scratch; `fixed` makes a launcher
+  // that would need more fail instead of freeing and reallocating it
   SampleScratch sc;
   sc.part = p->part;
   sc.bytes = NOALLOC_PART_BYTES;
+  sc.fixed = true;
   e = dtype == HSS_F64
           ? launch_sample<double>((const double*)A, n, lda, (const double*)R, ldr, c0, c1,
                                   (double*)Sr, (double*)Sc, lds, lof, mode, &sc, s, nullptr)

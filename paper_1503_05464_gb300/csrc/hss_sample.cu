@@ -214,6 +214,7 @@ Err launch_sample_mma(const float* A, int64_t n, int64_t lda, const float* R, in
                       const int32_t* leaf_of, int mode, float* P, cudaStream_t s);
 
 bool sample_tc_supported(const float* A, int64_t n, int64_t lda, int mode);
+Err sample_tc_need(int64_t n, int64_t ncols, size_t* need);
 Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int64_t ldr,
                      int64_t c0, int64_t ncols, float* Sr, float* Sc, int64_t lds,
                      const int32_t* leaf_of, int mode, SampleScratch* scratch, cudaStream_t s);
@@ -233,6 +234,17 @@ size_t sample_scratch_bytes(int64_t n, int64_t ncols, int mode, bool f64) {
   return (size_t)npanel * nchunk * n * S_DC * (f64 ? 8 : 4);
 }
 
+Err sample_scratch_need(const void* A, int64_t n, int64_t lda, int64_t ncols, int mode, bool f64,
+                        size_t* need) {
+  *need = 0;
+  if (n <= 0 || ncols <= 0) return ok();
+  if (!f64 && !legacy_mma_requested() &&
+      sample_tc_supported(reinterpret_cast<const float*>(A), n, lda, mode))
+    return sample_tc_need(n, ncols, need);
+  *need = sample_scratch_bytes(n, ncols, mode, f64);
+  return ok();
+}
+
 template <typename T>
 Err launch_sample(const T* A, int64_t n, int64_t lda, const T* R, int64_t ldr, int64_t c0,
                   int64_t c1, T* Sr, T* Sc, int64_t lds, const int32_t* leaf_of, int mode,
@@ -245,6 +257,8 @@ Err launch_sample(const T* A, int64_t n, int64_t lda, const T* R, int64_t ldr, i
   const bool tc = !f64 && !legacy_mma_requested() &&
                   sample_tc_supported(reinterpret_cast<const float*>(A), n, lda, mode);
   size_t need = tc ? 0 : sample_scratch_bytes(n, ncols, mode, f64);
+  if (scratch->bytes < need && scratch->fixed)
+    return fail(HSS_ERR_INVALID, "sampling: the fixed scratch is smaller than this call needs");
   if (scratch->bytes < need) {
     dfree(scratch->part, s);
     scratch->part = nullptr;

@@ -859,14 +859,9 @@ bool sample_tc_supported(const float* A, int64_t n, int64_t lda, int mode) {
          (reinterpret_cast<uintptr_t>(A) & 15) == 0;
 }
 
-Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int64_t ldr,
-                     int64_t c0, int64_t ncols, float* Sr, float* Sc, int64_t lds,
-                     const int32_t* leaf_of, int mode, SampleScratch* scratch, cudaStream_t s) {
-  int dev = 0;
-  HSS_CUDA_TRY(cudaGetDevice(&dev));
-  DevInfo& di = dev_info(dev);
-  const bool three = mode == HSS_SAMPLE_BF16X3;
-  const uint32_t smem = three ? Layout<3>::alloc : Layout<2>::alloc;
+// Clusters of KC CTAs of the sampling kernel that fit on the device at once
+// (queried once per device).
+static Err query_clusters(DevInfo& di, const cudaLaunchConfig_t& cfg) {
   if (!di.attr3) {
     HSS_CUDA_TRY(cudaFuncSetAttribute(sample_tc_kernel<3>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -879,17 +874,6 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
                                       (int)Layout<2>::alloc));
     di.attr2 = true;
   }
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = KC;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(THREADS, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
   if (di.clusters == 0) {
     // the larger (three-plane) layout decides how many clusters fit at once
     cudaLaunchConfig_t q = cfg;
@@ -902,8 +886,50 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     }
     di.clusters = nc > 0 ? nc : di.sms / KC;
   }
+  return ok();
+}
+
+static cudaLaunchConfig_t base_config(cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = KC;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(THREADS, 1, 1);
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+Err sample_tc_need(int64_t n, int64_t ncols, size_t* need) {
+  int dev = 0;
+  HSS_CUDA_TRY(cudaGetDevice(&dev));
+  DevInfo& di = dev_info(dev);
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = base_config(attr);
+  HSS_TRY(query_clusters(di, cfg));
+  *need = sample_tc_scratch_bytes(n, ncols, di.clusters);
+  return ok();
+}
+
+Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int64_t ldr,
+                     int64_t c0, int64_t ncols, float* Sr, float* Sc, int64_t lds,
+                     const int32_t* leaf_of, int mode, SampleScratch* scratch, cudaStream_t s) {
+  int dev = 0;
+  HSS_CUDA_TRY(cudaGetDevice(&dev));
+  DevInfo& di = dev_info(dev);
+  const bool three = mode == HSS_SAMPLE_BF16X3;
+  const uint32_t smem = three ? Layout<3>::alloc : Layout<2>::alloc;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = base_config(attr);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  HSS_TRY(query_clusters(di, cfg));
   const TcPlan pl = plan(n, di.clusters);
   const size_t need = sample_tc_scratch_bytes(n, ncols, di.clusters);
+  if (scratch->bytes < need && scratch->fixed)
+    return fail(HSS_ERR_INVALID,
+                "sample_tc: the fixed scratch is smaller than this call needs");
   if (scratch->bytes < need) {
     dfree(scratch->part, s);
     scratch->part = nullptr;

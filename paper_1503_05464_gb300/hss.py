@@ -57,6 +57,7 @@ _lib = None
 EXPORTS = ["hss_default_opts", "hss_compress", "hss_matvec", "hss_factor", "hss_solve",
            "hss_info", "hss_node_ranks", "hss_destroy", "hss_last_error",
            "hss_random_gaussian", "hss_sample", "hss_id_batched", "hss_kernel_launches", "hss_sample_noalloc",
+           "hss_pool_bytes",
            "hss_batch_create", "hss_batch_submit", "hss_batch_step", "hss_batch_take",
            "hss_batch_last_error", "hss_batch_destroy", "hss_compress_batched"]
 
@@ -85,6 +86,7 @@ def load(path: str = LIB_PATH):
     L.hss_sample.argtypes = [vp, i64, i64, i32, vp, i64, i64, i64, vp, vp, i64, vp, i32, i32, vp]
     L.hss_id_batched.argtypes = [i32, vp, vp, vp, vp, i32, f64, f64, vp, vp, vp, vp]
     L.hss_sample_noalloc.argtypes = L.hss_sample.argtypes
+    L.hss_pool_bytes.argtypes = [ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.hss_kernel_launches.argtypes = []
     L.hss_kernel_launches.restype = ctypes.c_int64
     L.hss_batch_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
@@ -293,6 +295,14 @@ def hss_kernel_launches() -> int:
     return int(load().hss_kernel_launches())
 
 
+def hss_pool_bytes() -> tuple[int, int]:
+    """(used, reserved) bytes of the library's device memory pool on the
+    current device."""
+    u, r = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().hss_pool_bytes(ctypes.byref(u), ctypes.byref(r)))
+    return u.value, r.value
+
+
 def hss_info(h: HSS) -> dict:
     info = HssInfo()
     _check(load().hss_info(h.handle, ctypes.byref(info)), h.handle)
@@ -337,8 +347,9 @@ def hss_sample(A, R, c0, c1, Sr, Sc, leaf_starts=None, mode="native", stream=Non
 
 
 def hss_sample_noalloc(A, R, c0, c1, Sr, Sc, leaf_starts=None, mode="native", stream=None):
-    """hss_sample without any device allocation (fixed library scratch; small
-    problems only: n <= 2048, c1 - c0 <= 64)."""
+    """hss_sample without any device allocation, for callers that may not
+    allocate (fixed library scratch; small problems only: n <= 2048,
+    c1 - c0 <= 64, at most 2048 leaves)."""
     _require_cuda(A, R, Sr, Sc)
     if Sr.stride(0) != Sc.stride(0):
         raise ValueError("Sr and Sc must share a leading dimension")

@@ -1,6 +1,6 @@
 """GPU path vs the CPU oracle, element by element where the result is unique.
 
-Tolerances (from the arithmetic, see DESIGN.md "Parity tolerances"):
+Tolerances (from the arithmetic):
 * R: bit-exact except where the FP64 Box-Muller value sits on a bfloat16
   rounding boundary (at most one bfloat16 ulp, at most 1e-6 of the entries).
 * sampling: FP64 |dS| <= 1e-12 (|A||R|); FP32 |dS| <= 4 n eps32 (|A||R|).

@@ -109,6 +109,36 @@ def _greedy_pivots(Y, kmax):
     return chosen, np.array(res)
 
 
+# ------------------------------------------------------- leaf local samples
+@pytest.mark.parametrize("n_extra", [0, 4])
+def test_leaf_local_samples_match_block_diagonal_removal(n_extra):
+    """Algorithm 1's leaf samples S^r(I,:) - D R(I,:) and S^c(I,:) - D^T R(I,:)
+    for every leaf equal (A - blockdiag(D)) R and (A - blockdiag(D))^T R with
+    the block diagonal assembled independently (scipy.linalg.block_diag of
+    the leaf blocks).  A is unsymmetric, so a D / D^T or row / column slip
+    shows; n = 8 leaf + 4 puts leaves at two depths with uneven sizes."""
+    leaf = 24
+    n = 8 * leaf + n_extra
+    rng = np.random.default_rng(11 + n_extra)
+    A = rng.standard_normal((n, n)) + np.triu(rng.standard_normal((n, n)), 1) * 3.0
+    R = rng.standard_normal((n, 7))
+    nodes = O.bisection_tree(n, leaf)
+    leaves = sorted((nd for nd in nodes if nd.is_leaf), key=lambda x: x.lo)
+    assert (len({nd.size for nd in leaves}) > 1) == (n_extra > 0)
+    assert (len({nd.depth for nd in leaves}) > 1) == (n_extra > 0)
+    Dblk = sla.block_diag(*[A[nd.lo:nd.hi, nd.lo:nd.hi] for nd in leaves])
+    assert Dblk.shape == (n, n)
+    Sr, Sc = O.leaf_local_samples(A, R, nodes)
+    np.testing.assert_allclose(Sr, (A - Dblk) @ R, rtol=0, atol=1e-12 * np.abs(A).sum())
+    np.testing.assert_allclose(Sc, (A - Dblk).T @ R, rtol=0, atol=1e-12 * np.abs(A).sum())
+    # and entry by entry from the definition, on a few rows
+    for i in (0, n // 3, n - 1):
+        lf = next(nd for nd in leaves if nd.lo <= i < nd.hi)
+        outside = np.r_[0:lf.lo, lf.hi:n]
+        np.testing.assert_allclose(Sr[i], A[i, outside] @ R[outside], rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(Sc[i], A[outside, i] @ R[outside], rtol=1e-12, atol=1e-12)
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_id_pivots_match_bruteforce_greedy(seed):
     rng = np.random.default_rng(seed)

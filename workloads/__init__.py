@@ -41,9 +41,26 @@ def points_unit_cube(n: int, seed: int) -> np.ndarray:
 
 
 def points_unit_sphere(n: int, seed: int) -> np.ndarray:
-    """n points uniform on the unit sphere (normalised Gaussian vectors)."""
-    g = np.random.default_rng(seed).standard_normal((n, 3))
-    return g / np.linalg.norm(g, axis=1, keepdims=True)
+    """n points uniform on the unit sphere (float64, shape n x 3).
+
+    Points uniform in the ball (rejection from the cube [-1, 1]^3, keeping
+    1e-4 <= |u|^2 <= 1) projected onto the sphere.  Only correctly rounded
+    operations are used (2u - 1, products, sums in a fixed order, sqrt,
+    division), so the points are bitwise the same on every platform.
+    """
+    rng = np.random.default_rng(seed)
+    out = np.empty((n, 3))
+    filled = 0
+    while filled < n:
+        u = rng.random((2 * (n - filled) + 64, 3)) * 2.0 - 1.0
+        r2 = u[:, 0] * u[:, 0]
+        r2 = r2 + u[:, 1] * u[:, 1]
+        r2 = r2 + u[:, 2] * u[:, 2]
+        keep = np.nonzero((r2 <= 1.0) & (r2 >= 1e-4))[0][: n - filled]
+        r = np.sqrt(r2[keep])
+        out[filled:filled + keep.size] = u[keep] / r[:, None]
+        filled += keep.size
+    return out
 
 
 def rcb_order(points: np.ndarray, leaf_size: int) -> np.ndarray:
@@ -102,14 +119,22 @@ def _tdtype(dtype):
     return torch.float64
 
 
-def _chunked_kernel(points: np.ndarray, fn, dtype, device, chunk=4096):
+def _chunked_kernel(points: np.ndarray, fn, dtype, device, chunk=2048):
+    """Dense kernel matrix, row blocks of `chunk`: fn(d2, r0, r1) maps the FP64
+    squared distances of rows [r0, r1) to the block's values.  d2 is summed
+    coordinate by coordinate in a fixed order with one rounding per operation,
+    so it is bitwise the same on the CPU and on the GPU."""
     dev = _dev(device)
     x = torch.as_tensor(points, dtype=torch.float64, device=dev)
     n = x.shape[0]
     out = torch.empty((n, n), dtype=_tdtype(dtype), device=dev)
     for r0 in range(0, n, chunk):
         r1 = min(n, r0 + chunk)
-        d2 = ((x[r0:r1, None, :] - x[None, :, :]) ** 2).sum(-1)
+        d2 = None
+        for a in range(x.shape[1]):
+            t = x[r0:r1, a, None] - x[None, :, a]
+            t = t * t
+            d2 = t if d2 is None else d2 + t
         blk = fn(d2, r0, r1)
         out[r0:r1] = blk.to(out.dtype)
     return out
@@ -126,17 +151,42 @@ def gaussian_kernel(points: np.ndarray, h: float, lam: float, dtype=np.float32, 
 
 
 def bem_like(points: np.ndarray, dtype=np.float32, device="cpu"):
-    """a_ij = 1/(4 pi |x_i-x_j|) for i != j, a_ii = sqrt(n) (computed in FP64)."""
+    """a_ij = 1/(4 pi |x_i-x_j|) for i != j, a_ii = sqrt(n) (computed in FP64
+    with correctly rounded operations only: the same bits on CPU and GPU)."""
     n = points.shape[0]
     diag = math.sqrt(n)
+    four_pi = 4.0 * math.pi
 
     def fn(d2, r0, r1):
         idx = torch.arange(r0, r1, device=d2.device)
         d2[idx - r0, idx] = 1.0
-        k = 1.0 / (4.0 * math.pi * torch.sqrt(d2))
+        k = torch.reciprocal(torch.sqrt(d2) * four_pi)
         k[idx - r0, idx] = diag
         return k
     return _chunked_kernel(points, fn, dtype, device)
+
+
+def fingerprint(A) -> str:
+    """Exact integer fingerprint of a matrix's stored bytes (any device):
+    with w_i the row sums of the entries' bit patterns read as signed
+    integers, returns hex(sum_i w_i) + ":" + hex(sum_i (i + 1) w_i)."""
+    if torch is None:
+        raise RuntimeError("torch is required")
+    t = torch.as_tensor(A)
+    ity = {4: torch.int32, 8: torch.int64, 2: torch.int16}[t.element_size()]
+    s1 = s2 = 0
+    for r0 in range(0, t.shape[0], 1024):
+        blk = t[r0:r0 + 1024].contiguous().view(ity)
+        if ity == torch.int64:   # split into two 32-bit halves to keep the sums exact
+            lo = (blk & 0xFFFFFFFF).sum(dim=1)
+            hi = (blk >> 32).sum(dim=1)
+            w = [int(a) + (int(b) << 32) for a, b in zip(lo.tolist(), hi.tolist())]
+        else:
+            w = [int(v) for v in blk.to(torch.int64).sum(dim=1).tolist()]
+        for i, v in enumerate(w):
+            s1 += v
+            s2 += (r0 + i + 1) * v
+    return f"{s1:x}:{s2:x}"
 
 
 # ------------------------------------------------ known-rank random HSS input
