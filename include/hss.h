@@ -70,6 +70,17 @@ typedef struct {
   int32_t oversample_p;  /* a node fails iff d < m and rank > d - oversample_p    */
   int32_t sample_mode;   /* hss_sample_mode                                      */
   uint64_t seed;         /* seed of the counter-based Gaussian generator of R    */
+  /* Cluster tree (Section 2.1; Section 4 compares balanced binary trees with
+   * unbalanced "comb" trees).  NULL = bisection by leaf_size.  Otherwise a
+   * host array of tree_nodes split points, one per node in breadth-first
+   * order (root first; the two children of a node are consecutive, left
+   * first, and come after every node of the parent's depth that precedes
+   * it): tree[q] = -1 makes node q a leaf, any lo < tree[q] < hi splits
+   * node q = [lo, hi) into [lo, tree[q]) and [tree[q], hi).  The root is
+   * [0, n).  Read during hss_compress / hss_batch_submit only (copied).
+   * INVALID if a split is out of range or the count does not match. */
+  const int64_t* tree;
+  int32_t tree_nodes;
 } hss_opts;
 
 /* Statistics of a handle (Table 3's columns: max rank, factor sizes, time). */
@@ -96,7 +107,8 @@ typedef struct {
 } hss_info_t;
 
 /* Fills *opts with defaults: leaf_size 128, rtol 1e-6, atol 0, d0 64,
- * d_step 32, d_max 0 (= n), oversample_p 10, NATIVE sampling, seed 0. */
+ * d_step 32, d_max 0 (= n), oversample_p 10, NATIVE sampling, seed 0,
+ * tree NULL (bisection). */
 hss_status hss_default_opts(hss_opts* opts);
 
 /*

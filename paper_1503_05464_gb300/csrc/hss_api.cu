@@ -103,6 +103,8 @@ hss_status hss_default_opts(hss_opts* o) {
   o->oversample_p = 10;
   o->sample_mode = HSS_SAMPLE_NATIVE;
   o->seed = 0;
+  o->tree = nullptr;
+  o->tree_nodes = 0;
   return HSS_OK;
 }
 

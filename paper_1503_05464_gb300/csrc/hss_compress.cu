@@ -159,7 +159,8 @@ struct Job {
   Err setup() {
     const int64_t N = n();
     Tree& tr = h->tree;
-    HSS_TRY(build_bisection_tree(tr, N, h->opts.leaf_size, s));
+    if (h->tree_splits.empty()) HSS_TRY(build_bisection_tree(tr, N, h->opts.leaf_size, s));
+    else HSS_TRY(build_split_tree(tr, N, h->tree_splits, s));
     h->gen.assign(tr.nodes.size(), NodeGen{});
     {
       std::vector<int32_t> lof(N);
@@ -598,7 +599,21 @@ static hss_status validate_opts(const void* A, int64_t n, int64_t lda, hss_dtype
     *msg = "bad options";
     return HSS_ERR_INVALID;
   }
+  if (o->tree) {
+    Err e = check_split_tree(n, o->tree, o->tree_nodes);
+    if (e.st) {
+      *msg = e.msg;
+      return e.st;
+    }
+  }
   return HSS_OK;
+}
+
+// the handle keeps its own copy of a caller's tree (opts.tree is borrowed)
+static void adopt_tree(hss_s* h, const hss_opts& o) {
+  if (o.tree) h->tree_splits.assign(o.tree, o.tree + o.tree_nodes);
+  h->opts.tree = nullptr;
+  h->opts.tree_nodes = 0;
 }
 
 // A batch: jobs of one dtype sharing one stream.
@@ -682,6 +697,7 @@ hss_status hss_batch_submit(hss_batch_t b, const void* A, int64_t n, int64_t lda
   e->h->n = n;
   e->h->dtype = b->dtype;
   e->h->opts = o;
+  adopt_tree(e->h.get(), o);
   e->h->stream = b->stream;
   e->t_submit = now_ms();
   if (b->dtype == HSS_F32) e->jf.reset(new Job<float>(e->h.get(), (const float*)A, lda, b->stream));
@@ -765,6 +781,7 @@ hss_status hss_compress(const void* A, int64_t n, int64_t lda, hss_dtype dtype,
   h->n = n;
   h->dtype = dtype;
   h->opts = o;
+  adopt_tree(h.get(), o);
   h->stream = (cudaStream_t)stream;
   Err e;
   auto run = [&](auto* jb, auto* drv) {

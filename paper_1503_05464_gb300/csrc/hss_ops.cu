@@ -17,6 +17,17 @@ __global__ void iota_kernel(int32_t* p, int64_t n) {
 }
 }  // namespace
 
+// levels, maximum depth and the device index array of a built node list
+static Err finish_tree(Tree& t, int64_t n, cudaStream_t s) {
+  t.maxdepth = 0;
+  for (const TNode& nd : t.nodes) t.maxdepth = std::max(t.maxdepth, nd.depth);
+  t.levels.assign(t.maxdepth + 1, {});
+  for (size_t q = 0; q < t.nodes.size(); ++q) t.levels[t.nodes[q].depth].push_back((int)q);
+  HSS_TRY(dalloc_t(&t.iota_dev, n, s));
+  iota_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t.iota_dev, n);
+  return check_launch("iota_kernel");
+}
+
 Err build_bisection_tree(Tree& t, int64_t n, int leaf_size, cudaStream_t s) {
   t.nodes.clear();
   t.nodes.push_back(TNode{0, (int)n, 0, -1, -1, -1});
@@ -32,13 +43,45 @@ Err build_bisection_tree(Tree& t, int64_t n, int leaf_size, cudaStream_t s) {
       t.nodes[q].c2 = a + 1;
     }
   }
-  t.maxdepth = 0;
-  for (const TNode& nd : t.nodes) t.maxdepth = std::max(t.maxdepth, nd.depth);
-  t.levels.assign(t.maxdepth + 1, {});
-  for (size_t q = 0; q < t.nodes.size(); ++q) t.levels[t.nodes[q].depth].push_back((int)q);
-  HSS_TRY(dalloc_t(&t.iota_dev, n, s));
-  iota_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t.iota_dev, n);
-  return check_launch("iota_kernel");
+  return finish_tree(t, n, s);
+}
+
+// Walks the split list breadth-first from the root [0, n); returns the node
+// count it describes (-1 on a split outside its node, or a list too short).
+static int64_t walk_splits(int64_t n, const int64_t* sp, int64_t count, std::vector<TNode>* out) {
+  std::vector<TNode> nodes;
+  nodes.push_back(TNode{0, (int)n, 0, -1, -1, -1});
+  for (size_t q = 0; q < nodes.size(); ++q) {
+    if ((int64_t)q >= count) return -1;
+    const int64_t mid = sp[q];
+    if (mid == -1) continue;
+    TNode nd = nodes[q];
+    if (mid <= nd.lo || mid >= nd.hi) return -1;
+    const int a = (int)nodes.size();
+    nodes.push_back(TNode{nd.lo, (int)mid, nd.depth + 1, (int)q, -1, -1});
+    nodes.push_back(TNode{(int)mid, nd.hi, nd.depth + 1, (int)q, -1, -1});
+    nodes[q].c1 = a;
+    nodes[q].c2 = a + 1;
+  }
+  if (out) *out = std::move(nodes);
+  return (int64_t)(out ? out->size() : nodes.size());
+}
+
+Err check_split_tree(int64_t n, const int64_t* splits, int32_t count) {
+  if (!splits || count < 1)
+    return fail(HSS_ERR_INVALID, "tree: NULL split list or tree_nodes < 1");
+  const int64_t got = walk_splits(n, splits, count, nullptr);
+  if (got < 0) return fail(HSS_ERR_INVALID, "tree: a split point lies outside its node");
+  if (got != count)
+    return fail(HSS_ERR_INVALID, "tree: the split list describes " + std::to_string(got) +
+                                     " nodes, tree_nodes is " + std::to_string(count));
+  return ok();
+}
+
+Err build_split_tree(Tree& t, int64_t n, const std::vector<int64_t>& splits, cudaStream_t s) {
+  HSS_TRY(check_split_tree(n, splits.data(), (int32_t)splits.size()));
+  walk_splits(n, splits.data(), (int64_t)splits.size(), &t.nodes);
+  return finish_tree(t, n, s);
 }
 
 Err finalize_generators(hss_s* h, cudaStream_t s) {

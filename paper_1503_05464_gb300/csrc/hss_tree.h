@@ -22,6 +22,11 @@ struct Tree {
 
 // Bisection: [lo, hi) with s = hi - lo > leaf_size splits at lo + floor(s/2).
 Err build_bisection_tree(Tree& t, int64_t n, int leaf_size, cudaStream_t s);
+// A caller's tree: splits[q] = split point of node q (breadth-first), -1 at a
+// leaf (the format of hss_opts.tree).
+Err build_split_tree(Tree& t, int64_t n, const std::vector<int64_t>& splits, cudaStream_t s);
+// Checks a split list against n without building anything.
+Err check_split_tree(int64_t n, const int64_t* splits, int32_t count);
 
 enum { NODE_UNTOUCHED = 0, NODE_PARTIALLY = 1, NODE_COMPRESSED = 2 };
 
@@ -115,6 +120,7 @@ struct hss_s {
   hss_dtype dtype = HSS_F32;
   hss_opts opts{};
   hss::Tree tree;
+  std::vector<int64_t> tree_splits;   // caller's tree (hss_opts.tree), empty = bisection
   std::vector<hss::NodeGen> gen;
   int d = 0, dcap = 0, passes = 0;
   hss_info_t info{};

@@ -36,7 +36,8 @@ class HssOpts(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int32), ("rtol", ctypes.c_double),
                 ("atol", ctypes.c_double), ("d0", ctypes.c_int32), ("d_step", ctypes.c_int32),
                 ("d_max", ctypes.c_int32), ("oversample_p", ctypes.c_int32),
-                ("sample_mode", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("sample_mode", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("tree", ctypes.POINTER(ctypes.c_int64)), ("tree_nodes", ctypes.c_int32)]
 
 
 class HssInfo(ctypes.Structure):
@@ -136,11 +137,23 @@ def _require_cuda(*ts):
 
 
 def hss_default_opts(**kw) -> HssOpts:
+    """hss_opts with the library defaults, then the keyword fields.  tree: a
+    list of split points, one per node in breadth-first order (-1 = leaf),
+    the format of hss_opts.tree."""
     o = HssOpts()
     _check(load().hss_default_opts(ctypes.byref(o)))
     for k, v in kw.items():
         if k == "sample_mode" and isinstance(v, str):
             v = SAMPLE_MODES[v]
+        if k == "tree":
+            if v is None:
+                o.tree, o.tree_nodes = None, 0
+                continue
+            arr = (ctypes.c_int64 * len(v))(*[int(x) for x in v])
+            o._tree_keep = arr          # the array must outlive the options
+            o.tree = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int64))
+            o.tree_nodes = len(v)
+            continue
         setattr(o, k, v)
     return o
 

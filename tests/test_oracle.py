@@ -359,3 +359,48 @@ def test_laplacian_schur_closed_form_matches_sparse_elimination(k):
     # closed-form eigenvalues and solve
     ev = np.sort(W.laplacian_schur_eigs(k).ravel())
     np.testing.assert_allclose(np.sort(np.linalg.eigvalsh(S)), ev, atol=1e-12)
+
+
+# ------------------------------------------------------------- comb trees
+def _oracle_nodes(n, splits):
+    return [O.Node(i, lo, hi, dep, par, ch)
+            for i, (lo, hi, dep, par, ch) in enumerate(W.split_intervals(n, splits))]
+
+
+def test_split_list_of_bisection_reproduces_the_bisection_tree():
+    """The breadth-first split list format (hss_opts.tree) describes the
+    bisection tree of Section 2.1 exactly when its splits are the midpoints."""
+    n, leaf = 1000, 60
+    ref = O.bisection_tree(n, leaf)
+    splits = [nd.lo + nd.size // 2 if not nd.is_leaf else -1 for nd in ref]
+    got = _oracle_nodes(n, splits)
+    assert [(a.lo, a.hi, a.depth, a.parent, a.children) for a in got] == \
+        [(b.lo, b.hi, b.depth, b.parent, tuple(b.children)) for b in ref]
+
+
+def test_comb_tree_compression_invariants():
+    """A comb tree (Section 4's unbalanced tree): every non-leaf splits off a
+    leaf.  The compressed form still satisfies the invariants that pin the
+    bisection case: matvec equals the dense H, H approximates A at the
+    tolerance, and the ULV solve equals a dense LU solve of H."""
+    n, leaf = 600, 50
+    A = W.toeplitz_inv_distance(n).numpy() + np.triu(np.ones((n, n))) * 0.01
+    splits = W.comb_tree_splits(n, leaf)
+    nodes = _oracle_nodes(n, splits)
+    assert max(nd.depth for nd in nodes) == n // leaf - 1
+    h = O.compress(A, 1e-9, d0=32, d_step=16, seed=5, tree=nodes)
+    H = O.to_dense(h)
+    assert np.linalg.norm(A - H) / np.linalg.norm(A) < 1e-7
+    X = np.random.default_rng(0).standard_normal((n, 3))
+    np.testing.assert_allclose(O.matvec(h, X), H @ X, rtol=0, atol=1e-12 * np.abs(H @ X).max())
+    O.ulv_factor(h)
+    Xs = O.ulv_solve(h, X)
+    np.testing.assert_allclose(Xs, sla.lu_solve(sla.lu_factor(H), X), rtol=0,
+                               atol=1e-10 * np.abs(Xs).max())
+    # every off-diagonal block A(I_t, rest) of a comb tree has the rank the ID
+    # found, to the tolerance (checked against its singular values)
+    for nd in nodes[1:]:
+        rest = np.r_[0:nd.lo, nd.hi:n]
+        sv = np.linalg.svd(A[nd.lo:nd.hi][:, rest], compute_uv=False)
+        kr = h.data[nd.id].idr.k
+        assert kr >= int(np.sum(sv > 1e-7 * sv[0]))

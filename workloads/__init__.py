@@ -189,6 +189,45 @@ def fingerprint(A) -> str:
     return f"{s1:x}:{s2:x}"
 
 
+# ---------------------------------------------------------------- cluster trees
+def comb_tree_splits(n: int, leaf_size: int) -> list:
+    """Split list (one entry per node, breadth-first, -1 = leaf) of a "comb"
+    tree: every non-leaf splits off a leaf of leaf_size indices on its left
+    and recurses on the rest, until the rest fits in a leaf (the unbalanced
+    tree of the paper's Section 4 tree comparison).  Breadth-first, each
+    depth holds the left leaf and then the remainder node, so the list is
+    [split, -1, split, -1, ..., -1, -1]."""
+    out = []
+    lo = 0
+    while n - lo > leaf_size:
+        out.append(lo + leaf_size)   # node [lo, n): left leaf, right remainder
+        out.append(-1)               # the left leaf of the next depth
+        lo += leaf_size
+    out.append(-1)                   # the last remainder
+    return out
+
+
+def split_intervals(n: int, splits) -> list:
+    """(lo, hi, depth, parent, children) of every node of a split list, in
+    breadth-first order (the input-side description of a caller's tree)."""
+    nodes = [[0, n, 0, -1, ()]]
+    q = 0
+    while q < len(nodes):
+        lo, hi, dep, _, _ = nodes[q]
+        mid = splits[q]
+        if mid != -1:
+            if not lo < mid < hi:
+                raise ValueError("split outside its node")
+            a = len(nodes)
+            nodes.append([lo, mid, dep + 1, q, ()])
+            nodes.append([mid, hi, dep + 1, q, ()])
+            nodes[q][4] = (a, a + 1)
+        q += 1
+    if len(nodes) != len(splits):
+        raise ValueError("split list length does not match the tree")
+    return [tuple(x) for x in nodes]
+
+
 # ------------------------------------------------ known-rank random HSS input
 def bisection_intervals(n: int, leaf_size: int):
     """Cluster tree by bisection, as nested tuples (lo, hi, left, right).
