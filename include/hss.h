@@ -226,6 +226,31 @@ hss_status hss_compress_batched(int32_t count, const void* const* A, const int64
                                 int32_t opts_stride, void* stream, hss_t* out,
                                 hss_status* status);
 
+/*
+ * hss_factor_batched -- hss_factor (Algorithm 3) of `count` handles of one
+ * dtype together: level by level from each tree's deepest level, the nodes
+ * of all handles at that round share one launch.  Each node's arithmetic is
+ * that of hss_factor, so the factors are bitwise the same.
+ *   hs: host array of count handles; status: optional host array of count
+ *   per-handle statuses (each handle keeps its own message).
+ * Returns the first non-OK status (INVALID for mixed dtypes).  Synchronizes
+ * the stream.
+ */
+hss_status hss_factor_batched(int32_t count, hss_t* hs, void* stream, hss_status* status);
+
+/*
+ * hss_solve_batched -- hss_solve (Algorithm 4) of `count` systems on handles
+ * of one dtype: X[q] = H_q^{-1} B[q], with B[q], X[q] device n_q x nrhs[q]
+ * row-major (ldb[q], ldx[q]); all host arrays of count entries.  The upward
+ * and downward sweeps of all systems share one launch per round; the
+ * results are bitwise those of one hss_solve per system.  A handle may
+ * appear more than once.  Returns the first non-OK status; status: optional
+ * per-system statuses.  Stream-ordered.
+ */
+hss_status hss_solve_batched(int32_t count, hss_t* hs, const void* const* B, const int64_t* ldb,
+                             const int64_t* nrhs, void* const* X, const int64_t* ldx,
+                             void* stream, hss_status* status);
+
 /* ---------------------------------------------------------------------------
  * Step-level entry points.  They run single steps of the compression on
  * caller buffers; hss_compress runs the same kernels.
@@ -337,6 +362,29 @@ hss_status hss_sample_noalloc(const void* A, int64_t n, int64_t lda, hss_dtype d
  * Errors: CUDA.
  */
 hss_status hss_pool_bytes(int64_t* used, int64_t* reserved);
+
+/* ---------------------------------------------------------------------------
+ * Fault injection, for testing how a caller handles failures (the paper has
+ * no counterpart).  Nothing here faults the GPU: an allocation failure is
+ * simulated on the host, and a device-side wait is only made to give up
+ * early, after which the kernel returns its error status normally.
+ * ------------------------------------------------------------------------- */
+typedef enum {
+  HSS_FAULT_NONE = 0,        /* clear every injected fault                          */
+  HSS_FAULT_OOM = 1,         /* the value-th device allocation from now (1 = the
+                                next) fails with HSS_ERR_OOM, once                  */
+  HSS_FAULT_WAIT_LIMIT = 2   /* the bounded barrier wait of the ID's spread-out
+                                (group) mode gives up after `value` clock cycles
+                                instead of about 2^33; 0 restores the default       */
+} hss_fault;
+
+/*
+ * hss_set_fault -- arms (or, with HSS_FAULT_NONE, clears) one injected fault
+ * for the whole process.  The environment variable HSS_FAULT, read when the
+ * library loads, arms the same faults without a call: "oom:N" or
+ * "wait:CYCLES".  Errors: INVALID (unknown kind, negative value).
+ */
+hss_status hss_set_fault(int32_t kind, int64_t value);
 
 #ifdef __cplusplus
 }

@@ -11,6 +11,7 @@
 #include <atomic>
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -58,9 +59,27 @@ static Err library_pool(cudaMemPool_t* out) {
   return ok();
 }
 
+// Injected faults (hss_set_fault, or HSS_FAULT in the environment at load).
+static std::atomic<int64_t> g_oom_countdown{0};   // > 0: allocations until the failing one
+static std::atomic<int64_t> g_wait_limit{0};
+
+static void parse_fault_env() {
+  const char* e = std::getenv("HSS_FAULT");
+  if (!e) return;
+  long long v = 0;
+  if (std::sscanf(e, "oom:%lld", &v) == 1 && v > 0) g_oom_countdown = v;
+  else if (std::sscanf(e, "wait:%lld", &v) == 1 && v > 0) g_wait_limit = v;
+}
+static const bool g_fault_env_read = (parse_fault_env(), true);
+
+int64_t fault_wait_limit() { return g_wait_limit.load(); }
+
 Err dalloc(void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
   if (bytes == 0) return ok();
+  if (g_oom_countdown.load() > 0 && g_oom_countdown.fetch_sub(1) == 1)
+    return fail(HSS_ERR_OOM, "device allocation of " + std::to_string(bytes) +
+                                 " bytes failed (injected fault)");
   cudaMemPool_t pool;
   HSS_TRY(library_pool(&pool));
   cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
@@ -116,6 +135,25 @@ const char* hss_last_error(hss_t h) {
 void hss_destroy(hss_t h) { delete h; }
 
 int64_t hss_kernel_launches(void) { return launches_so_far(); }
+
+hss_status hss_set_fault(int32_t kind, int64_t value) {
+  (void)g_fault_env_read;
+  if (value < 0) return set_err(nullptr, fail(HSS_ERR_INVALID, "hss_set_fault: negative value"));
+  switch (kind) {
+    case HSS_FAULT_NONE:
+      g_oom_countdown = 0;
+      g_wait_limit = 0;
+      return HSS_OK;
+    case HSS_FAULT_OOM:
+      g_oom_countdown = value;
+      return HSS_OK;
+    case HSS_FAULT_WAIT_LIMIT:
+      g_wait_limit = value;
+      return HSS_OK;
+    default:
+      return set_err(nullptr, fail(HSS_ERR_INVALID, "hss_set_fault: unknown kind"));
+  }
+}
 
 hss_status hss_pool_bytes(int64_t* used, int64_t* reserved) {
   cudaMemPool_t pool;

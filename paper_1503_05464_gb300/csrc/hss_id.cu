@@ -113,6 +113,92 @@ __device__ __forceinline__ double team_sum(int i, int d, int member, F f) {
   return v;
 }
 
+// v . w over the column entries c >= i (v indexed from i), with team_sum's
+// summation order (so the same bits).  With 4 or more threads per column the
+// next chunk of w is loaded while the current one is multiplied: the column
+// then sits in global memory, and the loads' latency is hidden behind the
+// FP64 pipe's work on the previous chunk.
+template <int TS>
+__device__ __forceinline__ double team_dot(int i, int d, int member, const double* __restrict__ v,
+                                           const double* w) {
+  if constexpr (TS < 4) {
+    return team_sum<TS>(i, d, member, [&](int c, double a) { return fma(v[c - i], w[c], a); });
+  } else {
+    constexpr int NP = 32 / TS;
+    double acc[NP], x[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) acc[q] = 0.0;
+    int base = (i / 32) * 32;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const int c = base + member + q * TS;
+      x[q] = (c >= i && c < d) ? w[c] : 0.0;
+    }
+    for (; base < d; base += 32) {
+      double nx[NP];
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const int c = base + 32 + member + q * TS;
+        nx[q] = c < d ? w[c] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const int c = base + member + q * TS;
+        if (c >= i && c < d) acc[q] = fma(v[c - i], x[q], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < NP; ++q) x[q] = nx[q];
+    }
+#pragma unroll
+    for (int o = 16; o >= TS; o >>= 1) {
+#pragma unroll
+      for (int q = 0; q < o / TS; ++q) acc[q] = acc[q] + acc[q + o / TS];
+    }
+    double r = acc[0];
+#pragma unroll
+    for (int o = TS >> 1; o > 0; o >>= 1) r = r + __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
+  }
+}
+
+// w[c] += a * v[c - i] for the column entries c >= i, in chunks of 32 rows:
+// each thread loads all its entries of a chunk before it updates and stores
+// them, so the loads of a chunk are in flight together.  Each entry is one
+// fused multiply-add, the same whatever TS.
+template <int TS>
+__device__ __forceinline__ void team_axpy(int i, int d, int member, double a,
+                                          const double* __restrict__ v, double* w) {
+  constexpr int NP = 32 / TS;
+  if constexpr (TS == 1) {
+    // a thread per column: its entries one after the other (32-entry chunks
+    // of 32 columns per warp measured 5x slower here)
+    for (int c = i; c < d; ++c) w[c] = fma(a, v[c - i], w[c]);
+    return;
+  }
+  int base = (i / 32) * 32;
+  double x[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const int c = base + member + q * TS;
+    x[q] = (c >= i && c < d) ? w[c] : 0.0;
+  }
+  for (; base < d; base += 32) {
+    double nx[NP];   // the next chunk, loaded before this one is stored
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const int c = base + 32 + member + q * TS;
+      nx[q] = c < d ? w[c] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const int c = base + member + q * TS;
+      if (c >= i && c < d) w[c] = fma(a, v[c - i], x[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) x[q] = nx[q];
+  }
+}
+
 // A CTA's pivot candidate as its peers receive it: with the column's exact
 // residual (entry alpha at the next pivot row, sum st of the squares below
 // it) every CTA can form the reflector without waiting for the column.
@@ -135,11 +221,12 @@ struct GroupArgs {
   unsigned* ctr;    // [items] barrier counters, zero at launch
   int* abort;       // set when a barrier wait gives up
   int* err;         // first error code
+  long long limit;  // clock cycles a barrier wait may take
 };
 constexpr long long GROUP_WAIT_LIMIT = 1ll << 33;   // clock cycles (about 4 s)
 // smallest per-CTA update of one step in cluster mode (columns x sample
 // count) for which the group mode is used
-constexpr long GROUP_MIN_STEP_WORK = 1l << 17;
+constexpr long GROUP_MIN_STEP_WORK = 1l << 15;
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
@@ -159,6 +246,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   __shared__ double hh[4];   // this step's sigma, tau, (unused), scale
   __shared__ int hstop;
   __shared__ int nrest;
+  __shared__ int nact;
   __shared__ int gstop;
 
   int C, crank;
@@ -193,7 +281,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
             st = 1;
             break;
           }
-          if (clock64() - t0 > GROUP_WAIT_LIMIT) {
+          if (clock64() - t0 > ga.limit) {
             atomicExch(ga.abort, 1);
             atomicCAS(ga.err, 0, 1);
             st = 1;
@@ -221,7 +309,15 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   double* lim = nrm + mloc_max;                   // mloc_max: tol3z * (norm at last recompute)^2
   double* rdiag = lim + mloc_max;                 // mloc_max: R_ii of the pivot columns
   int* pstep = reinterpret_cast<int*>(rdiag + mloc_max);   // mloc_max: pivot step or -1
-  double* colbuf = reinterpret_cast<double*>(pstep + ((mloc_max + 1) & ~1));   // 2 d: R1 columns
+  // the active (not yet pivoted) local columns, compacted: alist[0..nact)
+  // holds their local indices, apos[jl] is jl's position in alist.  Teams and
+  // norm-downdate lanes are dealt over this list, so no FP64 instruction is
+  // issued for a pivoted column (an FP64 instruction costs the same however
+  // few lanes are active).  Removal swaps in the last entry: which thread
+  // takes which column changes, the arithmetic of every column does not.
+  int* alist = pstep + ((mloc_max + 1) & ~1);
+  int* apos = alist + ((mloc_max + 1) & ~1);
+  double* colbuf = reinterpret_cast<double*>(apos + ((mloc_max + 1) & ~1));   // 2 d: R1 columns
   double* Wsm = colbuf + 2 * d;
   // odd column stride in shared memory: a thread per column reads without
   // bank conflicts
@@ -261,8 +357,11 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
       nrm[jl] = sqrt(ss);
       lim[jl] = tol3z * (nrm[jl] * nrm[jl]);
       pstep[jl] = -1;
+      alist[jl] = jl;
+      apos[jl] = jl;
     }
   }
+  if (tid == 0) nact = mloc;
   // every CTA of the cluster has started (its shared memory may now be
   // written by peers) and the columns and norms are loaded
   if (!sync_all()) return;
@@ -363,9 +462,14 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
         hstop = stop;
         if (!stop) {
           if (owner == crank) {
-            rdiag[p / C] = beta;
-            nrm[p / C] = -1.0;
-            pstep[p / C] = i;
+            const int jp = p / C;
+            rdiag[jp] = beta;
+            nrm[jp] = -1.0;
+            pstep[jp] = i;
+            const int pos = apos[jp], last = alist[nact - 1];
+            alist[pos] = last;
+            apos[last] = pos;
+            --nact;
           }
           if (crank == 0) perm[i] = p;
         }
@@ -391,17 +495,16 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     const double tau = hh[1], scal = hh[3];
     for (int c = i + tid; c < d; c += ID_THREADS) vloc[c - i] = (c == i) ? 1.0 : vloc[c - i] * scal;
     __syncthreads();
-    // apply the reflector: a team of TS threads per active column
-    for (int jb = warp * cols_per_warp; jb < mloc; jb += ID_WARPS * cols_per_warp) {
-      const int jl = jb + lane / TS;
-      const bool act = jl < mloc && nrm[jl] >= 0.0;
-      double* wj = act ? col(jl) : nullptr;
-      double dot = team_sum<TS>(i, act ? d : 0, member, [&](int c, double a) {
-        return fma(vloc[c - i], wj[c], a);
-      });
+    // apply the reflector: a team of TS threads per active column, the teams
+    // dealt over the compacted list of active columns
+    const int na = nact;
+    for (int jb = warp * cols_per_warp; jb < na; jb += ID_WARPS * cols_per_warp) {
+      const int q = jb + lane / TS;
+      const bool act = q < na;
+      double* wj = act ? col(alist[q]) : nullptr;
+      double dot = team_dot<TS>(i, act ? d : 0, member, vloc, wj);
       dot *= tau;
-      if (act)
-        for (int c = i + member; c < d; c += TS) wj[c] = fma(-dot, vloc[c - i], wj[c]);
+      if (act) team_axpy<TS>(i, d, member, -dot, vloc, wj);
     }
     __syncthreads();
     // norm downdates (LAPACK xGEQP3's formula and safeguard), one lane per
@@ -409,9 +512,9 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     if (warp < nwd) {
       long long cv = LLONG_MIN;
       int cj = INT_MAX;
-      for (int jl0 = warp * 32; jl0 < mloc; jl0 += nwd * 32) {
-        const int jl = jl0 + lane;
-        const double nj = jl < mloc ? nrm[jl] : -1.0;
+      for (int q0 = warp * 32; q0 < na; q0 += nwd * 32) {
+        const int jl = q0 + lane < na ? alist[q0 + lane] : 0;
+        const double nj = q0 + lane < na ? nrm[jl] : -1.0;
         const bool act = nj >= 0.0;
         bool recompute = false;
         double newn = nj;
@@ -429,7 +532,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
         while (rm) {
           const int src = __ffs(rm) - 1;
           rm &= rm - 1;
-          const double* wr = col(jl0 + src);
+          const double* wr = col(__shfl_sync(0xffffffffu, jl, src));
           const double ss = team_sum<32>(i + 1, d, lane, [&](int c, double a) {
             return fma(wr[c], wr[c], a);
           });
@@ -577,7 +680,7 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
   auto need = [&](int c) {
     int mloc = (max_m + c - 1) / c;
     return sizeof(double) * (3 * (size_t)d + 3 * (size_t)mloc) +
-           sizeof(int) * (size_t)((mloc + 1) & ~1);
+           3 * sizeof(int) * (size_t)((mloc + 1) & ~1);
   };
   size_t base = need(C);
   size_t wbytes = sizeof(double) * (size_t)((max_m + C - 1) / C) * (d | 1);
@@ -692,11 +795,13 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
   // and update), 32 / TS - 1 in-thread and log2 TS shuffle additions, and the
   // multiplication by tau.  Team groups go to warps round-robin, warp w runs
   // on scheduler w % 4.
-  auto team_index = [&](int ctas) {
+  auto team_index = [&](int ctas, bool global_cols) {
     const int mloc = (max_m + ctas - 1) / ctas;
     long best = -1;
     int ti = 0;
-    for (int ts = 1, lg = 0; ts <= 32; ts *= 2, ++lg) {
+    // columns in global memory: at least 4 threads per column (a thread per
+    // column streams its entries one at a time and measured slower)
+    for (int ts = global_cols ? 4 : 1, lg = global_cols ? 2 : 0; ts <= 32; ts *= 2, ++lg) {
       const long groups = ((long)mloc * ts + 31) / 32;
       const long per = 2 * ((d + ts - 1) / ts) + (32 / ts - 1) + lg + 1;
       const long cost = (groups + 3) / 4 * per;
@@ -720,6 +825,7 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
     if (scratch) HSS_TRY(scratch->alloc(reinterpret_cast<void**>(&gbuf), cand_bytes + ctl_bytes, s));
     else HSS_TRY(dalloc(reinterpret_cast<void**>(&gbuf), cand_bytes + ctl_bytes, s));
     ga.gsz = gsz;
+    ga.limit = fault_wait_limit() > 0 ? fault_wait_limit() : GROUP_WAIT_LIMIT;
     ga.cand = reinterpret_cast<Cand*>(gbuf);
     ga.ctr = reinterpret_cast<unsigned*>(gbuf + cand_bytes);
     ga.abort = reinterpret_cast<int*>(ga.ctr + count);
@@ -735,7 +841,7 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
     gattr[0].val.cooperative = 1;
     gcfg.attrs = gattr;
     gcfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&gcfg, group_kernels()[team_index(gsz)], items_dev,
+    cudaError_t e = cudaLaunchKernelEx(&gcfg, group_kernels()[team_index(gsz, true)], items_dev,
                                        f64 ? 1 : 0, 0, r1, (const int64_t*)offd, ga);
     if (e == cudaErrorCooperativeLaunchTooLarge) {
       // fewer SMs than expected are free for this context: clusters instead
@@ -759,7 +865,7 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
     ga = GroupArgs{};
   }
   if (!done) {
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kernels()[team_index(C)], items_dev, f64 ? 1 : 0,
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernels()[team_index(C, w_in_smem == 0)], items_dev, f64 ? 1 : 0,
                                        w_in_smem, r1, (const int64_t*)offd, ga);
     res = e == cudaSuccess ? check_launch("id_cpqr_cluster_kernel")
                            : fail(HSS_ERR_CUDA, std::string("id_cpqr_cluster_kernel launch: ") +

@@ -43,6 +43,10 @@ int64_t launches_so_far();
 // Message returned by hss_last_error(NULL) on the calling thread.
 void set_thread_error(const std::string& msg);
 
+// Injected faults (hss_set_fault): the group-mode barrier's wait limit in
+// clock cycles (0 = the kernel's default).
+int64_t fault_wait_limit();
+
 // Stream-ordered device allocation (cudaMallocAsync); null for 0 bytes.
 Err dalloc(void** p, size_t bytes, cudaStream_t s);
 void dfree(void* p, cudaStream_t s);

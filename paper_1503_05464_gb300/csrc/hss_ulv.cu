@@ -458,17 +458,14 @@ Err upload_and_launch(const std::vector<TI>& items, cudaStream_t s, TI** dev) {
 }  // namespace hss
 
 // ---------------------------------------------------------------- factor
-extern "C" hss_status hss_factor(hss_t h, void* stream) {
-  if (!h) return HSS_ERR_INVALID;
-  if (h->gen.empty() || h->gen[0].state != NODE_COMPRESSED) {
-    h->err = "hss_factor: the handle holds no complete compressed form";
-    return HSS_ERR_STATE;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
+namespace hss {
+namespace {
+
+// One allocation for every factor of the handle; sets each node's pointers.
+Err ulv_prepare(hss_s* h, cudaStream_t s) {
   h->ulv.release(s);
   const Tree& tr = h->tree;
   const int nn = (int)tr.nodes.size();
-  const int f64 = h->dtype == HSS_F64;
   UlvFactors& F = h->ulv;
   F.nodes.assign(nn, UlvNode{});
   // sizes: m = leaf size or k(c1) + k(c2); r = m - kr; kc
@@ -495,11 +492,7 @@ extern "C" hss_status hss_factor(hss_t h, void* stream) {
     if ((size_t)u.m >= ulv_big_min_m()) tot += (size_t)((r + 31) / 32) * 32 * 32;
   }
   double* blk = nullptr;
-  Err e = dalloc_t(&blk, std::max<size_t>(tot, 1), s);
-  if (e.st) {
-    h->err = e.msg;
-    return e.st;
-  }
+  HSS_TRY(dalloc_t(&blk, std::max<size_t>(tot, 1), s));
   F.block = blk;
   F.bytes = tot * sizeof(double);
   for (int id = 0; id < nn; ++id) {
@@ -528,87 +521,157 @@ extern "C" hss_status hss_factor(hss_t h, void* stream) {
     p += (size_t)u.k * u.kc;
     if ((size_t)u.m >= ulv_big_min_m()) u.T = p;
   }
-  int32_t* status = nullptr;
-  e = dalloc_t(&status, 1, s);
-  if (e.st == HSS_OK) e = cudaMemsetAsync(status, 0, 4, s) == cudaSuccess ? ok() : fail(HSS_ERR_CUDA, "memset");
-  for (int depth = tr.maxdepth; depth >= 0 && e.st == HSS_OK; --depth) {
-    // large nodes: blocked path over the whole GPU; the rest: one CTA each
-    std::vector<int> big, small;
-    for (int id : tr.levels[depth])
-      ((size_t)F.nodes[id].m >= ulv_big_min_m() ? big : small).push_back(id);
-    e = ulv_factor_big(h, big, status, s);
-    if (e.st != HSS_OK || small.empty()) continue;
-    std::vector<FacItem> items;
+  return ok();
+}
+
+// scratch doubles of one node of the one-CTA kernel
+size_t fac_scratch(const hss_s* h, int id) {
+  const UlvNode& u = h->ulv.nodes[id];
+  const NodeGen& g = h->gen[id];
+  return 2 * (size_t)u.m * u.m + (size_t)u.m * std::max(u.kc, 1) +
+         (size_t)std::max(g.mc, 1) * std::max(u.kc, 1);
+}
+
+FacItem fac_item(hss_s* h, int id, int32_t* status, double* sc) {
+  const Tree& tr = h->tree;
+  UlvFactors& F = h->ulv;
+  const TNode& nd = tr.nodes[id];
+  const UlvNode& u = F.nodes[id];
+  const NodeGen& g = h->gen[id];
+  FacItem it{};
+  it.m = u.m;
+  it.k = u.k;
+  it.kc = u.kc;
+  it.mc = g.mc;
+  it.leaf = nd.c1 < 0;
+  it.root = id == 0;
+  it.D = g.D;
+  if (!it.leaf) {
+    const UlvNode& a = F.nodes[nd.c1];
+    const UlvNode& b = F.nodes[nd.c2];
+    it.Dtil1 = a.Dtil;
+    it.Dtil2 = b.Dtil;
+    it.Vtb1 = a.Vtb;
+    it.Vtb2 = b.Vtb;
+    it.k1 = a.k;
+    it.k2 = b.k;
+    it.kc1 = a.kc;
+    it.kc2 = b.kc;
+    it.B12 = g.B12;
+    it.B21 = g.B21;
+  }
+  it.permr = g.permr;
+  it.Er = g.Er;
+  it.permc = g.permc;
+  it.Ec = g.Ec;
+  it.hv = u.hv;
+  it.tau = u.tau;
+  it.L = u.L;
+  it.WbQt = u.WbQt;
+  it.Dtil = u.Dtil;
+  it.Vtt = u.Vtt;
+  it.Vtb = u.Vtb;
+  size_t so = 0;
+  it.Dw = it.root ? F.root_lu : sc + so;
+  so += (size_t)u.m * u.m;
+  it.W = sc + so;
+  so += (size_t)u.m * u.m;
+  it.Vh = sc + so;
+  so += (size_t)u.m * std::max(u.kc, 1);
+  it.Vd = sc + so;
+  it.piv = F.root_piv;
+  it.status = status;
+  return it;
+}
+
+// Factors `count` handles of one dtype together: round r takes depth
+// maxdepth - r of every handle, deepest first; the small nodes of all
+// handles share one launch of the one-CTA kernel, the large ones take the
+// blocked whole-GPU path handle by handle.  Each node's arithmetic is the
+// same as alone, so the factors are bitwise those of a single-handle call.
+void factor_many(int count, hss_t* hs, cudaStream_t s, hss_status* st) {
+  std::vector<int> live;
+  int rounds = 0;
+  for (int q = 0; q < count; ++q) {
+    hss_s* h = hs[q];
+    st[q] = HSS_OK;
+    if (!h) {
+      st[q] = HSS_ERR_INVALID;
+      continue;
+    }
+    if (h->gen.empty() || h->gen[0].state != NODE_COMPRESSED) {
+      h->err = "hss_factor: the handle holds no complete compressed form";
+      st[q] = HSS_ERR_STATE;
+      continue;
+    }
+    Err e = ulv_prepare(h, s);
+    if (e.st) {
+      h->err = e.msg;
+      st[q] = e.st;
+      h->ulv.release(s);
+      continue;
+    }
+    live.push_back(q);
+    rounds = std::max(rounds, h->tree.maxdepth + 1);
+  }
+  auto fail_all = [&](const Err& e) {
+    for (int q : live)
+      if (st[q] == HSS_OK) {
+        hs[q]->err = e.msg;
+        st[q] = e.st;
+      }
+  };
+  int32_t* status = nullptr;   // one root-LU status per handle
+  Err e = dalloc_t(&status, std::max(count, 1), s);
+  if (e.st == HSS_OK && cudaMemsetAsync(status, 0, 4 * (size_t)std::max(count, 1), s) != cudaSuccess)
+    e = fail(HSS_ERR_CUDA, "hss_factor: memset");
+  if (e.st) fail_all(e);
+  const int f64 = (!live.empty() && hs[live[0]]->dtype == HSS_F64) ? 1 : 0;
+  for (int r = 0; r < rounds && e.st == HSS_OK; ++r) {
+    std::vector<std::pair<int, int>> small;   // (handle, node)
     size_t scratch = 0;
     int maxm = 1;
-    for (int id : small) {
-      const UlvNode& u = F.nodes[id];
-      const NodeGen& g = h->gen[id];
-      scratch += 2 * (size_t)u.m * u.m + (size_t)u.m * std::max(u.kc, 1) +
-                 (size_t)std::max(g.mc, 1) * std::max(u.kc, 1);
-      maxm = std::max(maxm, u.m);
+    for (int q : live) {
+      if (st[q] != HSS_OK) continue;
+      hss_s* h = hs[q];
+      const int depth = h->tree.maxdepth - r;
+      if (depth < 0) continue;
+      std::vector<int> big;
+      for (int id : h->tree.levels[depth]) {
+        if ((size_t)h->ulv.nodes[id].m >= ulv_big_min_m()) {
+          big.push_back(id);
+        } else {
+          small.push_back({q, id});
+          scratch += fac_scratch(h, id);
+          maxm = std::max(maxm, h->ulv.nodes[id].m);
+        }
+      }
+      Err eb = ulv_factor_big(h, big, status + q, s);
+      if (eb.st) {
+        h->err = eb.msg;
+        st[q] = eb.st;
+      }
     }
+    if (small.empty()) continue;
     double* sc = nullptr;
     e = dalloc_t(&sc, std::max<size_t>(scratch, 1), s);
     if (e.st) break;
+    std::vector<FacItem> items;
     size_t so = 0;
-    for (int id : small) {
-      const TNode& nd = tr.nodes[id];
-      const UlvNode& u = F.nodes[id];
-      const NodeGen& g = h->gen[id];
-      FacItem it{};
-      it.m = u.m;
-      it.k = u.k;
-      it.kc = u.kc;
-      it.mc = g.mc;
-      it.leaf = nd.c1 < 0;
-      it.root = id == 0;
-      it.D = g.D;
-      if (!it.leaf) {
-        const UlvNode& a = F.nodes[nd.c1];
-        const UlvNode& b = F.nodes[nd.c2];
-        it.Dtil1 = a.Dtil;
-        it.Dtil2 = b.Dtil;
-        it.Vtb1 = a.Vtb;
-        it.Vtb2 = b.Vtb;
-        it.k1 = a.k;
-        it.k2 = b.k;
-        it.kc1 = a.kc;
-        it.kc2 = b.kc;
-        it.B12 = g.B12;
-        it.B21 = g.B21;
-      }
-      it.permr = g.permr;
-      it.Er = g.Er;
-      it.permc = g.permc;
-      it.Ec = g.Ec;
-      it.hv = u.hv;
-      it.tau = u.tau;
-      it.L = u.L;
-      it.WbQt = u.WbQt;
-      it.Dtil = u.Dtil;
-      it.Vtt = u.Vtt;
-      it.Vtb = u.Vtb;
-      it.Dw = it.root ? F.root_lu : sc + so;
-      so += (size_t)u.m * u.m;
-      it.W = sc + so;
-      so += (size_t)u.m * u.m;
-      it.Vh = sc + so;
-      so += (size_t)u.m * std::max(u.kc, 1);
-      it.Vd = sc + so;
-      so += (size_t)std::max(g.mc, 1) * std::max(u.kc, 1);
-      it.piv = F.root_piv;
-      it.status = status;
-      items.push_back(it);
+    for (auto& qi : small) {
+      if (st[qi.first] != HSS_OK) continue;
+      items.push_back(fac_item(hs[qi.first], qi.second, status + qi.first, sc + so));
+      so += fac_scratch(hs[qi.first], qi.second);
     }
     FacItem* dev = nullptr;
-    e = upload_and_launch(items, s, &dev);
-    if (e.st == HSS_OK) {
+    if (!items.empty()) e = upload_and_launch(items, s, &dev);
+    if (e.st == HSS_OK && !items.empty()) {
       size_t smem = sizeof(double) * maxm;
       if (cudaFuncSetAttribute(ulv_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem) != cudaSuccess)
+                               (int)smem) != cudaSuccess) {
+        cudaGetLastError();
         e = fail(HSS_ERR_CUDA, "ulv_factor_kernel smem attribute");
-      else {
+      } else {
         ulv_factor_kernel<<<(unsigned)items.size(), U_THREADS, smem, s>>>(dev, f64);
         e = check_launch("ulv_factor_kernel");
       }
@@ -616,124 +679,210 @@ extern "C" hss_status hss_factor(hss_t h, void* stream) {
     dfree(dev, s);
     dfree(sc, s);
   }
-  int32_t st = 0;
-  if (e.st == HSS_OK) {
-    cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) e = fail(HSS_ERR_CUDA, "hss_factor: sync");
+  if (e.st) fail_all(e);
+  std::vector<int32_t> hst(std::max(count, 1), 0);
+  if (status) {
+    cudaMemcpyAsync(hst.data(), status, 4 * (size_t)count, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaGetLastError();
+      fail_all(fail(HSS_ERR_CUDA, "hss_factor: sync"));
+    }
   }
   dfree(status, s);
-  if (e.st == HSS_OK && st != 0) e = fail(HSS_ERR_SINGULAR, "hss_factor: zero pivot in the root LU");
-  if (e.st != HSS_OK) {
-    h->err = e.msg;
-    F.release(s);
-    return e.st;
+  for (int q : live) {
+    hss_s* h = hs[q];
+    if (st[q] == HSS_OK && hst[q] != 0) {
+      h->err = "hss_factor: zero pivot in the root LU";
+      st[q] = HSS_ERR_SINGULAR;
+    }
+    if (st[q] != HSS_OK) {
+      h->ulv.release(s);
+      continue;
+    }
+    h->ulv.done = true;
+    h->info.factored = 1;
+    h->info.bytes_ulv = (int64_t)h->ulv.bytes;
   }
-  F.done = true;
-  h->info.factored = 1;
-  h->info.bytes_ulv = (int64_t)F.bytes;
-  return HSS_OK;
+}
+
+}  // namespace
+}  // namespace hss
+
+extern "C" hss_status hss_factor(hss_t h, void* stream) {
+  if (!h) return HSS_ERR_INVALID;
+  hss_status st = HSS_OK;
+  factor_many(1, &h, (cudaStream_t)stream, &st);
+  return st;
+}
+
+extern "C" hss_status hss_factor_batched(int32_t count, hss_t* hs, void* stream,
+                                         hss_status* status) {
+  if (count < 0 || (count > 0 && !hs)) return HSS_ERR_INVALID;
+  for (int32_t q = 1; q < count; ++q)
+    if (hs[q] && hs[0] && hs[q]->dtype != hs[0]->dtype) {
+      set_thread_error("hss_factor_batched: handles of different dtypes");
+      return HSS_ERR_INVALID;
+    }
+  std::vector<hss_status> st(std::max(count, 1), HSS_OK);
+  factor_many(count, hs, (cudaStream_t)stream, st.data());
+  hss_status first = HSS_OK;
+  for (int32_t q = 0; q < count; ++q) {
+    if (status) status[q] = st[q];
+    if (st[q] != HSS_OK && first == HSS_OK) {
+      first = st[q];
+      if (hs[q]) set_thread_error(hs[q]->err);
+    }
+  }
+  return first;
 }
 
 // ----------------------------------------------------------------- solve
-extern "C" hss_status hss_solve(hss_t h, const void* B, int64_t ldb, int64_t nrhs, void* X,
-                                int64_t ldx, void* stream) {
-  if (!h) return HSS_ERR_INVALID;
-  if (!h->ulv.done) {
-    h->err = "hss_solve: hss_factor has not run on this handle";
-    return HSS_ERR_STATE;
-  }
-  if (!B || !X || nrhs < 0 || ldb < nrhs || ldx < nrhs || nrhs > INT32_MAX) {
-    h->err = "hss_solve: bad B, X, nrhs or leading dimension";
-    return HSS_ERR_INVALID;
-  }
-  if (nrhs == 0) return HSS_OK;
-  cudaStream_t s = (cudaStream_t)stream;
-  const Tree& tr = h->tree;
-  const int nn = (int)tr.nodes.size();
-  const int f64 = h->dtype == HSS_F64;
-  const int nr = (int)nrhs;
-  const UlvFactors& F = h->ulv;
-  // per node: b (m), btb (k), y (r), z (kc), x (m) -- all x nrhs
-  std::vector<size_t> ob(nn), obt(nn), oy(nn), oz(nn), ox(nn);
+namespace hss {
+namespace {
+
+// One solve of a batch: the handle, its right-hand sides and its buffers.
+struct SolveJob {
+  hss_s* h;
+  const void* B;
+  int64_t ldb;
+  int nr;
+  void* X;
+  int64_t ldx;
+  double* buf = nullptr;
+  std::vector<size_t> ob, obt, oy, oz, ox;
+  std::vector<UlvBufs> bufs;
+  hss_status* st;
+};
+
+// per node: b (m), btb (k), y (r), z (kc), x (m) -- all x nrhs
+Err solve_buffers(SolveJob& j, cudaStream_t s) {
+  const int nn = (int)j.h->tree.nodes.size();
+  const UlvFactors& F = j.h->ulv;
+  j.ob.resize(nn);
+  j.obt.resize(nn);
+  j.oy.resize(nn);
+  j.oz.resize(nn);
+  j.ox.resize(nn);
   size_t tot = 0;
   for (int id = 0; id < nn; ++id) {
     const UlvNode& u = F.nodes[id];
-    int r = u.m - u.k;
-    ob[id] = tot;
-    tot += (size_t)u.m * nr;
-    obt[id] = tot;
-    tot += (size_t)u.k * nr;
-    oy[id] = tot;
-    tot += (size_t)r * nr;
-    oz[id] = tot;
-    tot += (size_t)u.kc * nr;
-    ox[id] = tot;
-    tot += (size_t)u.m * nr;
+    const int r = u.m - u.k;
+    j.ob[id] = tot;
+    tot += (size_t)u.m * j.nr;
+    j.obt[id] = tot;
+    tot += (size_t)u.k * j.nr;
+    j.oy[id] = tot;
+    tot += (size_t)r * j.nr;
+    j.oz[id] = tot;
+    tot += (size_t)u.kc * j.nr;
+    j.ox[id] = tot;
+    tot += (size_t)u.m * j.nr;
   }
-  double* buf = nullptr;
-  Err e = dalloc_t(&buf, std::max<size_t>(tot, 1), s);
-  std::vector<UlvBufs> bufs(nn);
-  if (e.st == HSS_OK)
-    for (int id = 0; id < nn; ++id)
-      bufs[id] = {buf + ob[id], buf + obt[id], buf + oy[id], buf + oz[id], buf + ox[id]};
-  auto is_big = [&](int id) { return (size_t)F.nodes[id].m >= ulv_big_min_m(); };
-  for (int depth = tr.maxdepth; depth >= 0 && e.st == HSS_OK; --depth) {
-    std::vector<int> big;
-    for (int id : tr.levels[depth])
-      if (is_big(id)) big.push_back(id);
-    e = ulv_solve_up_big(h, big, bufs, B, ldb, nr, s);
-    if (e.st != HSS_OK) break;
-    std::vector<SolItem> items;
-    for (int id : tr.levels[depth]) {
-      if (is_big(id)) continue;
-      const TNode& nd = tr.nodes[id];
-      const UlvNode& u = F.nodes[id];
-      const NodeGen& g = h->gen[id];
-      SolItem it{};
-      it.m = u.m;
-      it.k = u.k;
-      it.kc = u.kc;
-      it.mc = g.mc;
-      it.leaf = nd.c1 < 0;
-      it.root = id == 0;
-      it.lo = nd.lo;
-      it.nrhs = nr;
-      it.Bin = B;
-      it.ldb = ldb;
-      if (!it.leaf) {
-        const UlvNode& a = F.nodes[nd.c1];
-        const UlvNode& b = F.nodes[nd.c2];
-        it.btb1 = buf + obt[nd.c1];
-        it.btb2 = buf + obt[nd.c2];
-        it.y1 = buf + oy[nd.c1];
-        it.y2 = buf + oy[nd.c2];
-        it.z1 = buf + oz[nd.c1];
-        it.z2 = buf + oz[nd.c2];
-        it.WbQt1 = a.WbQt;
-        it.WbQt2 = b.WbQt;
-        it.k1 = a.k;
-        it.k2 = b.k;
-        it.kc1 = a.kc;
-        it.kc2 = b.kc;
-        it.r1 = a.m - a.k;
-        it.r2 = b.m - b.k;
-        it.B12 = g.B12;
-        it.B21 = g.B21;
+  HSS_TRY(dalloc_t(&j.buf, std::max<size_t>(tot, 1), s));
+  j.bufs.resize(nn);
+  for (int id = 0; id < nn; ++id)
+    j.bufs[id] = {j.buf + j.ob[id], j.buf + j.obt[id], j.buf + j.oy[id], j.buf + j.oz[id],
+                  j.buf + j.ox[id]};
+  return ok();
+}
+
+SolItem up_item(const SolveJob& j, int id) {
+  const hss_s* h = j.h;
+  const Tree& tr = h->tree;
+  const UlvFactors& F = h->ulv;
+  const TNode& nd = tr.nodes[id];
+  const UlvNode& u = F.nodes[id];
+  const NodeGen& g = h->gen[id];
+  double* buf = j.buf;
+  SolItem it{};
+  it.m = u.m;
+  it.k = u.k;
+  it.kc = u.kc;
+  it.mc = g.mc;
+  it.leaf = nd.c1 < 0;
+  it.root = id == 0;
+  it.lo = nd.lo;
+  it.nrhs = j.nr;
+  it.Bin = j.B;
+  it.ldb = j.ldb;
+  if (!it.leaf) {
+    const UlvNode& a = F.nodes[nd.c1];
+    const UlvNode& b = F.nodes[nd.c2];
+    it.btb1 = buf + j.obt[nd.c1];
+    it.btb2 = buf + j.obt[nd.c2];
+    it.y1 = buf + j.oy[nd.c1];
+    it.y2 = buf + j.oy[nd.c2];
+    it.z1 = buf + j.oz[nd.c1];
+    it.z2 = buf + j.oz[nd.c2];
+    it.WbQt1 = a.WbQt;
+    it.WbQt2 = b.WbQt;
+    it.k1 = a.k;
+    it.k2 = b.k;
+    it.kc1 = a.kc;
+    it.kc2 = b.kc;
+    it.r1 = a.m - a.k;
+    it.r2 = b.m - b.k;
+    it.B12 = g.B12;
+    it.B21 = g.B21;
+  }
+  it.permr = g.permr;
+  it.Er = g.Er;
+  it.permc = g.permc;
+  it.Ec = g.Ec;
+  it.L = u.L;
+  it.Vtt = u.Vtt;
+  it.lu = F.root_lu;
+  it.piv = F.root_piv;
+  it.b = buf + j.ob[id];
+  it.btb = buf + j.obt[id];
+  it.y = buf + j.oy[id];
+  it.z = buf + j.oz[id];
+  it.x = buf + j.ox[id];
+  return it;
+}
+
+// Solves every job: the upward sweep takes depth maxdepth - r of every
+// handle in round r, the downward sweep depth r; the small nodes of all
+// handles share one launch per round, the large ones take the blocked path
+// handle by handle.  Per node the arithmetic is that of a single solve.
+void solve_many(std::vector<SolveJob>& jobs, cudaStream_t s) {
+  int rounds = 0;
+  const int f64 = (!jobs.empty() && jobs[0].h->dtype == HSS_F64) ? 1 : 0;
+  for (SolveJob& j : jobs) {
+    Err e = solve_buffers(j, s);
+    if (e.st) {
+      j.h->err = e.msg;
+      *j.st = e.st;
+    }
+    rounds = std::max(rounds, j.h->tree.maxdepth + 1);
+  }
+  auto is_big = [](const hss_s* h, int id) {
+    return (size_t)h->ulv.nodes[id].m >= ulv_big_min_m();
+  };
+  auto fail_all = [&](const Err& e) {
+    for (SolveJob& j : jobs)
+      if (*j.st == HSS_OK) {
+        j.h->err = e.msg;
+        *j.st = e.st;
       }
-      it.permr = g.permr;
-      it.Er = g.Er;
-      it.permc = g.permc;
-      it.Ec = g.Ec;
-      it.L = u.L;
-      it.Vtt = u.Vtt;
-      it.lu = F.root_lu;
-      it.piv = F.root_piv;
-      it.b = buf + ob[id];
-      it.btb = buf + obt[id];
-      it.y = buf + oy[id];
-      it.z = buf + oz[id];
-      it.x = buf + ox[id];
-      items.push_back(it);
+  };
+  Err e;
+  for (int r = 0; r < rounds && e.st == HSS_OK; ++r) {
+    std::vector<SolItem> items;
+    for (SolveJob& j : jobs) {
+      if (*j.st != HSS_OK) continue;
+      const int depth = j.h->tree.maxdepth - r;
+      if (depth < 0) continue;
+      std::vector<int> big;
+      for (int id : j.h->tree.levels[depth]) {
+        if (is_big(j.h, id)) big.push_back(id);
+        else items.push_back(up_item(j, id));
+      }
+      Err eb = ulv_solve_up_big(j.h, big, j.bufs, j.B, j.ldb, j.nr, s);
+      if (eb.st) {
+        j.h->err = eb.msg;
+        *j.st = eb.st;
+      }
     }
     if (items.empty()) continue;
     SolItem* dev = nullptr;
@@ -744,45 +893,59 @@ extern "C" hss_status hss_solve(hss_t h, const void* B, int64_t ldb, int64_t nrh
     }
     dfree(dev, s);
   }
-  if (e.st == HSS_OK && nn == 1) {
-    int m = F.nodes[0].m;
-    int64_t total = (int64_t)m * nr;
-    copy_out_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(buf + ox[0], m, nr, X, ldx, f64);
+  for (SolveJob& j : jobs) {
+    if (e.st || *j.st != HSS_OK || j.h->tree.nodes.size() != 1) continue;
+    const int m = j.h->ulv.nodes[0].m;
+    const int64_t total = (int64_t)m * j.nr;
+    copy_out_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(j.buf + j.ox[0], m, j.nr,
+                                                                     j.X, j.ldx, f64);
     e = check_launch("copy_out_kernel");
   }
-  for (int depth = 0; depth < tr.maxdepth && e.st == HSS_OK; ++depth) {
+  for (int r = 0; r < rounds && e.st == HSS_OK; ++r) {
     std::vector<DownItem> items;
-    std::vector<DownBig> bigkids;
-    for (int id : tr.levels[depth]) {
-      const TNode& nd = tr.nodes[id];
-      if (nd.c1 < 0) continue;
-      const int ka = F.nodes[nd.c1].k;
-      for (int side = 0; side < 2; ++side) {
-        int c = side ? nd.c2 : nd.c1;
-        if (is_big(c)) {
-          bigkids.push_back({c, buf + ox[id] + (side ? (size_t)ka * nr : 0)});
-          continue;
+    for (SolveJob& j : jobs) {
+      if (*j.st != HSS_OK) continue;
+      const hss_s* h = j.h;
+      const Tree& tr = h->tree;
+      const UlvFactors& F = h->ulv;
+      if (r >= tr.maxdepth) continue;
+      std::vector<DownBig> bigkids;
+      for (int id : tr.levels[r]) {
+        const TNode& nd = tr.nodes[id];
+        if (nd.c1 < 0) continue;
+        const int ka = F.nodes[nd.c1].k;
+        for (int side = 0; side < 2; ++side) {
+          const int c = side ? nd.c2 : nd.c1;
+          const double* xp = j.buf + j.ox[id] + (side ? (size_t)ka * j.nr : 0);
+          if (is_big(h, c)) {
+            bigkids.push_back({c, xp});
+            continue;
+          }
+          const UlvNode& u = F.nodes[c];
+          const TNode& cn = tr.nodes[c];
+          DownItem it{};
+          it.m = u.m;
+          it.r = u.m - u.k;
+          it.nrhs = j.nr;
+          it.leaf = cn.c1 < 0;
+          it.lo = cn.lo;
+          it.y = j.buf + j.oy[c];
+          it.xp = xp;
+          it.hv = u.hv;
+          it.tau = u.tau;
+          it.x = j.buf + j.ox[c];
+          it.Xout = j.X;
+          it.ldx = j.ldx;
+          items.push_back(it);
         }
-        const UlvNode& u = F.nodes[c];
-        const TNode& cn = tr.nodes[c];
-        DownItem it{};
-        it.m = u.m;
-        it.r = u.m - u.k;
-        it.nrhs = nr;
-        it.leaf = cn.c1 < 0;
-        it.lo = cn.lo;
-        it.y = buf + oy[c];
-        it.xp = buf + ox[id] + (side ? (size_t)ka * nr : 0);
-        it.hv = u.hv;
-        it.tau = u.tau;
-        it.x = buf + ox[c];
-        it.Xout = X;
-        it.ldx = ldx;
-        items.push_back(it);
+      }
+      Err eb = ulv_solve_down_big(j.h, bigkids, j.bufs, j.nr, j.X, j.ldx, s);
+      if (eb.st) {
+        j.h->err = eb.msg;
+        *j.st = eb.st;
       }
     }
-    e = ulv_solve_down_big(h, bigkids, bufs, nr, X, ldx, s);
-    if (e.st != HSS_OK || items.empty()) continue;
+    if (items.empty()) continue;
     DownItem* dev = nullptr;
     e = upload_and_launch(items, s, &dev);
     if (e.st == HSS_OK) {
@@ -791,7 +954,77 @@ extern "C" hss_status hss_solve(hss_t h, const void* B, int64_t ldb, int64_t nrh
     }
     dfree(dev, s);
   }
-  dfree(buf, s);
-  if (e.st != HSS_OK) h->err = e.msg;
-  return e.st;
+  if (e.st) fail_all(e);
+  for (SolveJob& j : jobs) dfree(j.buf, s);
+}
+
+// argument checks of one solve; INVALID / STATE with the handle's message
+hss_status check_solve(hss_s* h, const void* B, int64_t ldb, int64_t nrhs, const void* X,
+                       int64_t ldx) {
+  if (!h) return HSS_ERR_INVALID;
+  if (!h->ulv.done) {
+    h->err = "hss_solve: hss_factor has not run on this handle";
+    return HSS_ERR_STATE;
+  }
+  if (!B || !X || nrhs < 0 || ldb < nrhs || ldx < nrhs || nrhs > INT32_MAX) {
+    h->err = "hss_solve: bad B, X, nrhs or leading dimension";
+    return HSS_ERR_INVALID;
+  }
+  return HSS_OK;
+}
+
+}  // namespace
+}  // namespace hss
+
+extern "C" hss_status hss_solve(hss_t h, const void* B, int64_t ldb, int64_t nrhs, void* X,
+                                int64_t ldx, void* stream) {
+  hss_status st = check_solve(h, B, ldb, nrhs, X, ldx);
+  if (st != HSS_OK || nrhs == 0) return st;
+  std::vector<SolveJob> jobs(1);
+  jobs[0].h = h;
+  jobs[0].B = B;
+  jobs[0].ldb = ldb;
+  jobs[0].nr = (int)nrhs;
+  jobs[0].X = X;
+  jobs[0].ldx = ldx;
+  jobs[0].st = &st;
+  solve_many(jobs, (cudaStream_t)stream);
+  return st;
+}
+
+extern "C" hss_status hss_solve_batched(int32_t count, hss_t* hs, const void* const* B,
+                                        const int64_t* ldb, const int64_t* nrhs,
+                                        void* const* X, const int64_t* ldx, void* stream,
+                                        hss_status* status) {
+  if (count < 0 || (count > 0 && (!hs || !B || !ldb || !nrhs || !X || !ldx)))
+    return HSS_ERR_INVALID;
+  std::vector<hss_status> st(std::max(count, 1), HSS_OK);
+  std::vector<SolveJob> jobs;
+  for (int32_t q = 0; q < count; ++q) {
+    st[q] = check_solve(hs[q], B[q], ldb[q], nrhs[q], X[q], ldx[q]);
+    if (st[q] == HSS_OK && hs[0] && hs[q]->dtype != hs[0]->dtype) {
+      hs[q]->err = "hss_solve_batched: handles of different dtypes";
+      st[q] = HSS_ERR_INVALID;
+    }
+    if (st[q] != HSS_OK || nrhs[q] == 0) continue;
+    SolveJob j;
+    j.h = hs[q];
+    j.B = B[q];
+    j.ldb = ldb[q];
+    j.nr = (int)nrhs[q];
+    j.X = X[q];
+    j.ldx = ldx[q];
+    j.st = &st[q];
+    jobs.push_back(std::move(j));
+  }
+  solve_many(jobs, (cudaStream_t)stream);
+  hss_status first = HSS_OK;
+  for (int32_t q = 0; q < count; ++q) {
+    if (status) status[q] = st[q];
+    if (st[q] != HSS_OK && first == HSS_OK) {
+      first = st[q];
+      if (hs[q]) set_thread_error(hs[q]->err);
+    }
+  }
+  return first;
 }

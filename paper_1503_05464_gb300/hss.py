@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "libhss.so")
 HSS_OK, HSS_ERR_INVALID, HSS_ERR_OOM, HSS_ERR_CUDA, HSS_ERR_RANK_CAP, HSS_ERR_SINGULAR, \
     HSS_ERR_TIMEOUT, HSS_ERR_STATE = range(8)
 HSS_F32, HSS_F64 = 0, 1
+HSS_FAULT_NONE, HSS_FAULT_OOM, HSS_FAULT_WAIT_LIMIT = 0, 1, 2
 SAMPLE_MODES = {"native": 0, "tf32": 1, "bf16x2": 2, "bf16x3": 3}
 
 STATUS_NAMES = {0: "HSS_OK", 1: "HSS_ERR_INVALID", 2: "HSS_ERR_OOM", 3: "HSS_ERR_CUDA",
@@ -58,9 +59,10 @@ _lib = None
 EXPORTS = ["hss_default_opts", "hss_compress", "hss_matvec", "hss_factor", "hss_solve",
            "hss_info", "hss_node_ranks", "hss_destroy", "hss_last_error",
            "hss_random_gaussian", "hss_sample", "hss_id_batched", "hss_kernel_launches", "hss_sample_noalloc",
-           "hss_pool_bytes",
+           "hss_pool_bytes", "hss_set_fault",
            "hss_batch_create", "hss_batch_submit", "hss_batch_step", "hss_batch_take",
-           "hss_batch_last_error", "hss_batch_destroy", "hss_compress_batched"]
+           "hss_batch_last_error", "hss_batch_destroy", "hss_compress_batched",
+           "hss_factor_batched", "hss_solve_batched"]
 
 
 def load(path: str = LIB_PATH):
@@ -88,6 +90,7 @@ def load(path: str = LIB_PATH):
     L.hss_id_batched.argtypes = [i32, vp, vp, vp, vp, i32, f64, f64, vp, vp, vp, vp]
     L.hss_sample_noalloc.argtypes = L.hss_sample.argtypes
     L.hss_pool_bytes.argtypes = [ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.hss_set_fault.argtypes = [i32, i64]
     L.hss_kernel_launches.argtypes = []
     L.hss_kernel_launches.restype = ctypes.c_int64
     L.hss_batch_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
@@ -100,6 +103,8 @@ def load(path: str = LIB_PATH):
     L.hss_batch_destroy.restype = None
     L.hss_compress_batched.argtypes = [i32, vp, vp, vp, i32, ctypes.POINTER(HssOpts), i32, vp,
                                        vp, vp]
+    L.hss_factor_batched.argtypes = [i32, vp, vp, vp]
+    L.hss_solve_batched.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("hss_destroy", "hss_last_error", "hss_kernel_launches",
                         "hss_batch_last_error", "hss_batch_destroy"):
@@ -289,6 +294,40 @@ def hss_factor(h: HSS, stream=None) -> None:
     _check(load().hss_factor(h.handle, _stream(stream)), h.handle)
 
 
+def hss_factor_batched(hs, stream=None):
+    """ULV factorization of several handles together (one launch per level
+    round across all of them).  Returns the per-handle statuses."""
+    cnt = len(hs)
+    if cnt == 0:
+        return []
+    arr = (ctypes.c_void_p * cnt)(*[h.handle.value for h in hs])
+    sts = (ctypes.c_int * cnt)()
+    load().hss_factor_batched(cnt, arr, _stream(stream), sts)
+    return [sts[i] for i in range(cnt)]
+
+
+def hss_solve_batched(hs, Bs, stream=None):
+    """X_q = H_q^{-1} B_q for every pair (one launch per sweep round across
+    all of them).  Returns (list of X, list of statuses)."""
+    cnt = len(hs)
+    if cnt == 0:
+        return [], []
+    B2 = [b.view(-1, 1) if b.dim() == 1 else b for b in Bs]
+    _require_cuda(*B2)
+    Xs = [torch.empty((h.n, b.shape[1]), dtype=b.dtype, device=b.device) for h, b in zip(hs, B2)]
+    vp = ctypes.c_void_p
+    harr = (vp * cnt)(*[h.handle.value for h in hs])
+    barr = (vp * cnt)(*[b.data_ptr() for b in B2])
+    xarr = (vp * cnt)(*[x.data_ptr() for x in Xs])
+    ldb = (ctypes.c_int64 * cnt)(*[b.stride(0) for b in B2])
+    nr = (ctypes.c_int64 * cnt)(*[b.shape[1] for b in B2])
+    ldx = (ctypes.c_int64 * cnt)(*[x.stride(0) for x in Xs])
+    sts = (ctypes.c_int * cnt)()
+    load().hss_solve_batched(cnt, harr, barr, ldb, nr, xarr, ldx, _stream(stream), sts)
+    Xs = [x.view(-1) if b.dim() == 1 else x for x, b in zip(Xs, Bs)]
+    return Xs, [sts[i] for i in range(cnt)]
+
+
 def hss_solve(h: HSS, B: torch.Tensor, X: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """X = H^{-1} B with the ULV factors (Algorithm 4)."""
     vec = B.dim() == 1
@@ -306,6 +345,13 @@ def hss_solve(h: HSS, B: torch.Tensor, X: torch.Tensor | None = None, stream=Non
 def hss_kernel_launches() -> int:
     """Kernels libhss has launched in this process so far."""
     return int(load().hss_kernel_launches())
+
+
+def hss_set_fault(kind: int, value: int = 0) -> None:
+    """Arm an injected fault (HSS_FAULT_OOM: the value-th allocation from now
+    fails; HSS_FAULT_WAIT_LIMIT: the ID's group barrier gives up after value
+    cycles) or clear them (HSS_FAULT_NONE)."""
+    _check(load().hss_set_fault(kind, value))
 
 
 def hss_pool_bytes() -> tuple[int, int]:

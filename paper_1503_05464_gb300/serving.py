@@ -8,10 +8,13 @@ n = k^2) and a schedule of right-hand-side batches.  The loop
   (hss_batch_submit): requests that arrive while others are being compressed
   join the same per-level launches at the next round;
 * advances the batch one round at a time (one tree level of every job);
-* when a compression finishes, runs the ULV factorization, frees the input
-  matrix and keeps the compressed form resident;
-* serves each due right-hand-side batch with hss_solve on the resident form;
-* releases a request's form after its last solve.
+* hands each finished compression to a second host thread with its own CUDA
+  stream, which factors the newly finished forms together
+  (hss_factor_batched), keeps them resident, serves every due right-hand-side
+  batch together (hss_solve_batched) and releases a request's form after its
+  last solve -- so factorizations and solves overlap the compression rounds
+  on the device instead of stalling them;
+* frees each input matrix as soon as its compression is done.
 
 It reports p50/p99 latencies (arrival to first solution, and per solve batch)
 and throughput.  All GPU work runs in libhss; this module only schedules.
@@ -20,6 +23,8 @@ from __future__ import annotations
 
 import heapq
 import math
+import queue
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -131,33 +136,46 @@ class Server:
         torch.cuda.synchronize()
         batch = H.HssBatch(torch.float32, self.stream)
         inflight = {}
-        due = []                              # heap of (time, seq, request, nrhs)
-        used = 0
-        seq = 0
+        lock = threading.Lock()
+        acct = {"used": 0}
+        finished = queue.Queue()              # compressed requests for the solve thread
+        errors = []
         t0 = time.perf_counter()
 
         def now():
             return time.perf_counter() - t0
 
-        while pending or inflight or due:
-            t = now()
-            # admission: arrived requests whose estimate fits the budget
-            while pending and pending[0].arrival <= t:
-                r = pending[0]
-                need = estimate_bytes(r.n, self.opts)
-                if used + need > self.budget and inflight:
-                    break
-                pending.pop(0)
-                r.A = self._template(r.k) * r.scale
-                r.reserved = need
-                used += need
-                r.t_admit = now()
-                r.ticket = batch.submit(r.A, self.opts)
-                inflight[r.ticket] = r
-            st.peak_reserved = max(st.peak_reserved, used)
-            st.max_inflight = max(st.max_inflight, len(inflight))
-            # one round of every compression in flight
-            if inflight:
+        worker = threading.Thread(target=self._solve_thread,
+                                  args=(finished, st, lock, acct, now, errors), daemon=True)
+        worker.start()
+        try:
+            while pending or inflight:
+                t = now()
+                # admission: arrived requests whose estimate fits the budget
+                while pending and pending[0].arrival <= t:
+                    r = pending[0]
+                    need = estimate_bytes(r.n, self.opts)
+                    with lock:
+                        if acct["used"] + need > self.budget and (inflight or acct["used"] > 0):
+                            break
+                        acct["used"] += need
+                        st.peak_reserved = max(st.peak_reserved, acct["used"])
+                    pending.pop(0)
+                    r.A = self._template(r.k) * r.scale
+                    r.reserved = need
+                    r.t_admit = now()
+                    r.ticket = batch.submit(r.A, self.opts)
+                    inflight[r.ticket] = r
+                st.max_inflight = max(st.max_inflight, len(inflight))
+                if errors:
+                    raise errors[0]
+                if not inflight:
+                    if pending:
+                        wait = pending[0].arrival - now()
+                        if wait > 0:
+                            time.sleep(min(wait, 0.002))
+                    continue
+                # one round of every compression in flight
                 batch.step()
                 for ticket in list(inflight):
                     h, status = batch.take(ticket)
@@ -166,48 +184,91 @@ class Server:
                     r = inflight.pop(ticket)
                     if h is None:
                         raise H.HssError(status, f"request {r.rid} failed")
-                    H.hss_factor(h, self.stream)
-                    info = H.hss_info(h)
                     r.handle = h
-                    r.ranks = max(info["max_rank_r"], info["max_rank_c"])
                     r.t_compressed = now()
                     st.compress_latency.append(r.t_compressed - r.arrival)
-                    r.A = None
-                    used -= r.reserved
-                    r.resident = info["bytes_hss"] + info["bytes_ulv"]
-                    used += r.resident
-                    r.solves_left = len(r.solves)
-                    for off, nrhs in r.solves:
-                        heapq.heappush(due, (r.t_compressed + off, seq, r, nrhs))
-                        seq += 1
-            # due right-hand sides
-            t = now()
-            while due and due[0][0] <= t:
-                tdue, _, r, nrhs = heapq.heappop(due)
-                g = torch.Generator(device="cuda").manual_seed(1000 * r.rid + nrhs)
-                B = torch.randn(r.n, nrhs, device="cuda", generator=g)
-                X = H.hss_solve(r.handle, B, stream=self.stream)
-                torch.cuda.current_stream().synchronize() if self.stream is None else self.stream.synchronize()
-                tf = now()
-                st.solve_latency.append(tf - tdue)
-                st.solves += 1
-                st.rhs += nrhs
-                if math.isnan(r.t_first_solution):
-                    r.t_first_solution = tf
-                    st.request_latency.append(tf - r.arrival)
-                r.solves_left -= 1
-                if r.solves_left == 0:
-                    used -= r.resident
-                    if self.keep:
-                        self.done.append(r)
-                    else:
-                        r.handle.close()
-                        r.handle = None
-                del X, B
-            if not inflight and not due and pending:
-                wait = pending[0].arrival - now()
-                if wait > 0:
-                    time.sleep(min(wait, 0.01))
+                    r.A = None                # the input is no longer needed
+                    finished.put(r)
+        finally:
+            finished.put(None)                # no more compressions
+            worker.join()
+            batch.close()
+        if errors:
+            raise errors[0]
         st.wall_s = now()
-        batch.close()
         return st
+
+    def _solve_thread(self, finished, st, lock, acct, now, errors):
+        """Factors finished compressions and serves due right-hand sides on
+        its own stream; all requests of one pass share one launch per level."""
+        stream = torch.cuda.Stream()
+        due = []                              # heap of (time, seq, request, nrhs)
+        seq = 0
+        closing = False
+        try:
+            with torch.cuda.stream(stream):
+                while True:
+                    fresh = []
+                    while True:
+                        try:
+                            r = finished.get_nowait()
+                        except queue.Empty:
+                            break
+                        if r is None:
+                            closing = True
+                        else:
+                            fresh.append(r)
+                    if fresh:
+                        sts = H.hss_factor_batched([r.handle for r in fresh], stream=stream)
+                        for r, status in zip(fresh, sts):
+                            if status != H.HSS_OK:
+                                raise H.HssError(status, f"request {r.rid}: factorization failed")
+                            info = H.hss_info(r.handle)
+                            r.ranks = max(info["max_rank_r"], info["max_rank_c"])
+                            r.resident = info["bytes_hss"] + info["bytes_ulv"]
+                            with lock:
+                                acct["used"] += r.resident - r.reserved
+                            t = now()
+                            r.solves_left = len(r.solves)
+                            for off, nrhs in r.solves:
+                                heapq.heappush(due, (t + off, seq, r, nrhs))
+                                seq += 1
+                    t = now()
+                    batchq = []
+                    while due and due[0][0] <= t:
+                        batchq.append(heapq.heappop(due))
+                    if batchq:
+                        Bs = []
+                        for _, _, r, nrhs in batchq:
+                            g = torch.Generator(device="cuda").manual_seed(1000 * r.rid + nrhs)
+                            Bs.append(torch.randn(r.n, nrhs, device="cuda", generator=g))
+                        Xs, sts = H.hss_solve_batched([q[2].handle for q in batchq], Bs,
+                                                      stream=stream)
+                        stream.synchronize()
+                        tf = now()
+                        for (tdue, _, r, nrhs), status in zip(batchq, sts):
+                            if status != H.HSS_OK:
+                                raise H.HssError(status, f"request {r.rid}: solve failed")
+                            st.solve_latency.append(tf - tdue)
+                            st.solves += 1
+                            st.rhs += nrhs
+                            if math.isnan(r.t_first_solution):
+                                r.t_first_solution = tf
+                                st.request_latency.append(tf - r.arrival)
+                            r.solves_left -= 1
+                            if r.solves_left == 0:
+                                with lock:
+                                    acct["used"] -= r.resident
+                                if self.keep:
+                                    self.done.append(r)
+                                else:
+                                    r.handle.close()
+                                    r.handle = None
+                        del Xs, Bs
+                        continue
+                    if closing and not due and finished.empty():
+                        return
+                    nxt = due[0][0] - now() if due else 0.001
+                    time.sleep(max(0.0, min(nxt, 0.001)))
+        except Exception as e:                # reported by the admitting thread
+            errors.append(e)

@@ -109,3 +109,43 @@ def test_batch_reports_per_job_failures(P):
     assert sts[0] == 0 or sts[0] == P.hss.HSS_ERR_RANK_CAP
     assert sts[1] == P.hss.HSS_ERR_RANK_CAP    # random matrix: no low rank at d_max = 32
     assert hs[1] is not None                    # a rank-capped handle is still returned
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_batched_factor_and_solve_equal_alone(P, dtype):
+    """hss_factor_batched / hss_solve_batched (one launch per level round
+    across all handles, Algorithms 3 and 4) give bitwise the solutions of one
+    hss_factor / hss_solve per handle; trees of different depths, a
+    single-node tree and a handle solved twice in one batch included."""
+    if dtype == "f32":
+        mats = _mats_f32() + [W.toeplitz_inv_distance(90, dtype=np.float32, device=DEV)]
+        kw = dict(leaf_size=128, rtol=1e-5, d0=64, d_step=32, seed=9, sample_mode="bf16x3")
+    else:
+        mats = _mats_f64() + [W.toeplitz_inv_distance(90, dtype=np.float64, device=DEV)]
+        kw = dict(leaf_size=128, rtol=1e-8, d0=64, d_step=32, seed=9)
+    hs_b = [P.hss_compress(A, **kw) for A in mats]
+    hs_a = [P.hss_compress(A, **kw) for A in mats]
+    assert P.hss_factor_batched(hs_b) == [0] * len(mats)
+    for h in hs_a:
+        P.hss_factor(h)
+    g = torch.Generator(device=DEV).manual_seed(4)
+    Bs = [torch.randn(A.shape[0], 1 + 3 * i, device=DEV, generator=g).to(A.dtype)
+          for i, A in enumerate(mats)]
+    hs_q = hs_b + [hs_b[0]]
+    Bs_q = Bs + [Bs[0][:, :2].contiguous()]
+    Xs, sts = P.hss_solve_batched(hs_q, Bs_q)
+    assert sts == [0] * len(hs_q)
+    for h, B, X in zip(hs_a + [hs_a[0]], Bs_q, Xs):
+        assert torch.equal(P.hss_solve(h, B), X)
+    for A, B, X in zip(mats, Bs, Xs):
+        r = torch.linalg.norm(A.double() @ X.double() - B.double()) / torch.linalg.norm(B.double())
+        assert float(r) < (1e-2 if dtype == "f32" else 1e-6)
+
+
+def test_batched_factor_reports_each_handle(P):
+    A = W.toeplitz_inv_distance(600, dtype=np.float64, device=DEV)
+    h1 = P.hss_compress(A, leaf_size=64, rtol=1e-8, d0=32, d_step=16)
+    h2 = P.hss_compress(A, leaf_size=64, rtol=1e-8, d0=32, d_step=16)
+    P.hss_factor_batched([h1])
+    X, sts = P.hss_solve_batched([h1, h2], [torch.ones(600, dtype=torch.float64, device=DEV)] * 2)
+    assert sts[0] == 0 and sts[1] == P.hss.HSS_ERR_STATE
