@@ -291,7 +291,7 @@ def run_ours(args, wl):
         "id_cpqr_fp64": {"ms": id_ms, "bound": "alu", "achieved": id_tflops,
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": id_tflops / FP64_PEAK_TFLOPS,
-                         "peak_source": "measured FP64 FMA probe"},
+                         "peak_source": "GB300 nominal dense FP64 (own FMA probe: 1.20)"},
         "fused_sampling": {"ms": s_ms, "bound": bound, "achieved": samp_tflops,
                            "peak": unit_peak, "unit": "TFLOP/s", "roofline_ms": roof_ms,
                            "frac": roof_ms / s_ms if s_ms > 0 else 0.0,

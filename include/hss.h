@@ -363,6 +363,17 @@ hss_status hss_sample_noalloc(const void* A, int64_t n, int64_t lda, hss_dtype d
  */
 hss_status hss_pool_bytes(int64_t* used, int64_t* reserved);
 
+/*
+ * hss_tuner_stats -- state of the library's measuring tuner of the ID launch
+ * shape (threads per column).  Launches are grouped into shape classes; the
+ * first launches of a class time the instruction-count model's choice and
+ * its neighbours with CUDA events (the results do not depend on the choice),
+ * later ones use the fastest.  Outputs (any may be NULL): classes seen,
+ * classes settled, timed trial launches.  HSS_AUTOTUNE=0 in the environment
+ * switches the tuner off (the model's choice everywhere).  Never fails.
+ */
+hss_status hss_tuner_stats(int32_t* classes, int32_t* settled, int32_t* trials);
+
 /* ---------------------------------------------------------------------------
  * Fault injection, for testing how a caller handles failures (the paper has
  * no counterpart).  Nothing here faults the GPU: an allocation failure is

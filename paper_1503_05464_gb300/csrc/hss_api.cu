@@ -136,6 +136,11 @@ void hss_destroy(hss_t h) { delete h; }
 
 int64_t hss_kernel_launches(void) { return launches_so_far(); }
 
+hss_status hss_tuner_stats(int32_t* classes, int32_t* settled, int32_t* trials) {
+  id_tuner_stats(classes, settled, trials);
+  return HSS_OK;
+}
+
 hss_status hss_set_fault(int32_t kind, int64_t value) {
   (void)g_fault_env_read;
   if (value < 0) return set_err(nullptr, fail(HSS_ERR_INVALID, "hss_set_fault: negative value"));

@@ -49,8 +49,10 @@
 #include <array>
 #include <cfloat>
 #include <climits>
+#include <cstdlib>
 #include <map>
 #include <mutex>
+#include <tuple>
 
 namespace cg = cooperative_groups;
 
@@ -113,90 +115,78 @@ __device__ __forceinline__ double team_sum(int i, int d, int member, F f) {
   return v;
 }
 
-// v . w over the column entries c >= i (v indexed from i), with team_sum's
-// summation order (so the same bits).  With 4 or more threads per column the
-// next chunk of w is loaded while the current one is multiplied: the column
-// then sits in global memory, and the loads' latency is hidden behind the
-// FP64 pipe's work on the previous chunk.
+// One pass over a column for two elimination steps: the pending update of
+// step i-1, w[c] += a * up[c - (i-1)] for c >= i-1 (when `pending`), and the
+// dot product of the updated column with u_i over c >= i, summed in
+// team_sum's order.  Each entry gets the same operations, in the same order,
+// as an update pass followed by a dot-product pass, so the bits are those of
+// the two passes; the column is read and written once instead of read twice
+// and written once.
 template <int TS>
-__device__ __forceinline__ double team_dot(int i, int d, int member, const double* __restrict__ v,
-                                           const double* w) {
-  if constexpr (TS < 4) {
-    return team_sum<TS>(i, d, member, [&](int c, double a) { return fma(v[c - i], w[c], a); });
-  } else {
-    constexpr int NP = 32 / TS;
-    double acc[NP], x[NP];
+__device__ __forceinline__ double team_update_dot(int i, int d, int member, bool pending, double a,
+                                                  const double* __restrict__ up,
+                                                  const double* __restrict__ u, double* w) {
+  constexpr int NP = 32 / TS;                      // partial sums per thread
+  constexpr bool PF = TS >= 4;                     // columns in global memory: pipelined
+  // rows per chunk 32 G (G = 1: deeper chunks for large teams, 8 loads in
+  // flight per thread, measured slower)
+  constexpr int G = 1;
+  constexpr int NQ = NP * G;
+  double acc[NP];
 #pragma unroll
-    for (int q = 0; q < NP; ++q) acc[q] = 0.0;
-    int base = (i / 32) * 32;
+  for (int q = 0; q < NP; ++q) acc[q] = 0.0;
+  const int lo = pending ? i - 1 : i;
+  int base = (lo / 32) * 32;
+  double x[NQ];
+  if constexpr (PF) {
 #pragma unroll
-    for (int q = 0; q < NP; ++q) {
+    for (int q = 0; q < NQ; ++q) {
       const int c = base + member + q * TS;
-      x[q] = (c >= i && c < d) ? w[c] : 0.0;
+      x[q] = (c >= lo && c < d) ? w[c] : 0.0;
     }
-    for (; base < d; base += 32) {
-      double nx[NP];
+  }
+  for (; base < d; base += 32 * G) {
+    double nx[NQ];
+    if constexpr (PF) {
 #pragma unroll
-      for (int q = 0; q < NP; ++q) {
-        const int c = base + 32 + member + q * TS;
+      for (int q = 0; q < NQ; ++q) {
+        const int c = base + 32 * G + member + q * TS;
         nx[q] = c < d ? w[c] : 0.0;
       }
+    } else {
 #pragma unroll
-      for (int q = 0; q < NP; ++q) {
+      for (int q = 0; q < NQ; ++q) {
         const int c = base + member + q * TS;
-        if (c >= i && c < d) acc[q] = fma(v[c - i], x[q], acc[q]);
+        x[q] = (c >= lo && c < d) ? w[c] : 0.0;
       }
-#pragma unroll
-      for (int q = 0; q < NP; ++q) x[q] = nx[q];
     }
+    // entry c = base + member + q TS goes to partial q mod NP (= c mod 32
+    // within the team's rows), in increasing c
 #pragma unroll
-    for (int o = 16; o >= TS; o >>= 1) {
-#pragma unroll
-      for (int q = 0; q < o / TS; ++q) acc[q] = acc[q] + acc[q + o / TS];
-    }
-    double r = acc[0];
-#pragma unroll
-    for (int o = TS >> 1; o > 0; o >>= 1) r = r + __shfl_xor_sync(0xffffffffu, r, o);
-    return r;
-  }
-}
-
-// w[c] += a * v[c - i] for the column entries c >= i, in chunks of 32 rows:
-// each thread loads all its entries of a chunk before it updates and stores
-// them, so the loads of a chunk are in flight together.  Each entry is one
-// fused multiply-add, the same whatever TS.
-template <int TS>
-__device__ __forceinline__ void team_axpy(int i, int d, int member, double a,
-                                          const double* __restrict__ v, double* w) {
-  constexpr int NP = 32 / TS;
-  if constexpr (TS == 1) {
-    // a thread per column: its entries one after the other (32-entry chunks
-    // of 32 columns per warp measured 5x slower here)
-    for (int c = i; c < d; ++c) w[c] = fma(a, v[c - i], w[c]);
-    return;
-  }
-  int base = (i / 32) * 32;
-  double x[NP];
-#pragma unroll
-  for (int q = 0; q < NP; ++q) {
-    const int c = base + member + q * TS;
-    x[q] = (c >= i && c < d) ? w[c] : 0.0;
-  }
-  for (; base < d; base += 32) {
-    double nx[NP];   // the next chunk, loaded before this one is stored
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-      const int c = base + 32 + member + q * TS;
-      nx[q] = c < d ? w[c] : 0.0;
-    }
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
+    for (int q = 0; q < NQ; ++q) {
       const int c = base + member + q * TS;
-      if (c >= i && c < d) w[c] = fma(a, v[c - i], x[q]);
+      if (c >= lo && c < d) {
+        if (pending) {
+          x[q] = fma(a, up[c - lo], x[q]);
+          w[c] = x[q];
+        }
+        if (c >= i) acc[q % NP] = fma(u[c - i], x[q], acc[q % NP]);
+      }
     }
+    if constexpr (PF) {
 #pragma unroll
-    for (int q = 0; q < NP; ++q) x[q] = nx[q];
+      for (int q = 0; q < NQ; ++q) x[q] = nx[q];
+    }
   }
+#pragma unroll
+  for (int o = 16; o >= TS; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < o / TS; ++q) acc[q] = acc[q] + acc[q + o / TS];
+  }
+  double r = acc[0];
+#pragma unroll
+  for (int o = TS >> 1; o > 0; o >>= 1) r = r + __shfl_xor_sync(0xffffffffu, r, o);
+  return r;
 }
 
 // A CTA's pivot candidate as its peers receive it: with the column's exact
@@ -234,8 +224,8 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   return v;
 }
 
-template <int TS, bool GRP>
-__global__ void __launch_bounds__(ID_THREADS, 1)
+template <int TS, bool GRP, int MINB = 1>
+__global__ void __launch_bounds__(ID_THREADS, MINB)
 id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
                        int w_in_smem, double* __restrict__ r1buf_base,
                        const int64_t* __restrict__ r1off, GroupArgs ga) {
@@ -304,11 +294,14 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   }
   const int mloc = (m - crank + C - 1) / C;       // columns crank, crank+C, ...
   const int mloc_max = (m + C - 1) / C;
-  double* vloc = smem;                            // d: pivot column, then reflector
-  double* nrm = vloc + d;                         // mloc_max
+  // reflectors of steps i (vbuf + (i & 1) d) and i - 1: the update of a step
+  // is applied in the same pass as the next step's dot product
+  double* vbuf = smem;                            // 2 d
+  double* nrm = vbuf + 2 * d;                     // mloc_max
   double* lim = nrm + mloc_max;                   // mloc_max: tol3z * (norm at last recompute)^2
   double* rdiag = lim + mloc_max;                 // mloc_max: R_ii of the pivot columns
-  int* pstep = reinterpret_cast<int*>(rdiag + mloc_max);   // mloc_max: pivot step or -1
+  double* dprev = rdiag + mloc_max;               // mloc_max: tau (u_i . w), update pending
+  int* pstep = reinterpret_cast<int*>(dprev + mloc_max);   // mloc_max: pivot step or -1
   // the active (not yet pivoted) local columns, compacted: alist[0..nact)
   // holds their local indices, apos[jl] is jl's position in alist.  Teams and
   // norm-downdate lanes are dealt over this list, so no FP64 instruction is
@@ -317,7 +310,8 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   // takes which column changes, the arithmetic of every column does not.
   int* alist = pstep + ((mloc_max + 1) & ~1);
   int* apos = alist + ((mloc_max + 1) & ~1);
-  double* colbuf = reinterpret_cast<double*>(apos + ((mloc_max + 1) & ~1));   // 2 d: R1 columns
+  int* pend = apos + ((mloc_max + 1) & ~1);       // 1: the column's update by dprev is pending
+  double* colbuf = reinterpret_cast<double*>(pend + ((mloc_max + 1) & ~1));   // 2 d: R1 columns
   double* Wsm = colbuf + 2 * d;
   // odd column stride in shared memory: a thread per column reads without
   // bank conflicts
@@ -359,6 +353,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
       pstep[jl] = -1;
       alist[jl] = jl;
       apos[jl] = jl;
+      pend[jl] = 0;
     }
   }
   if (tid == 0) nact = mloc;
@@ -373,7 +368,17 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   auto push_candidate = [&](int s, long long v, int j, int r) {
     double st = 0.0, alpha = 0.0;
     if (v != LLONG_MIN) {
-      const double* w = col((j - crank) / C);
+      const int jl = (j - crank) / C;
+      double* w = col(jl);
+      if (r > 0 && pend[jl]) {
+        // the candidate's pending update of step r - 1, so that its residual
+        // (and the pivot column the peers copy) is current
+        const double a = -dprev[jl];
+        const double* up = vbuf + ((r - 1) & 1) * d;
+        for (int c = r - 1 + lane; c < d; c += 32) w[c] = fma(a, up[c - (r - 1)], w[c]);
+        __syncwarp();
+        if (lane == 0) pend[jl] = 0;
+      }
       st = team_sum<32>(r + 1, d, lane, [&](int c, double a) { return fma(w[c], w[c], a); });
       alpha = r < d ? w[r] : 0.0;
     }
@@ -415,8 +420,10 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   int k = kmax;
   double r11 = 0.0;
   for (int i = 0; i < kmax; ++i) {
-    if (!sync_all()) return;   // candidates of step i pushed, updates of step i-1 done
+    if (!sync_all()) return;   // candidates of step i pushed, dot products of step i-1 done
     const int slot = i & 1;
+    double* vloc = vbuf + (i & 1) * d;          // pivot column, then reflector u_i
+    const double* vprev = vbuf + ((i + 1) & 1) * d;   // u_{i-1}
     // every warp reduces the C candidates (lane r <- CTA r): all threads agree
     // on the pivot without a block barrier
     long long bv = LLONG_MIN;
@@ -495,16 +502,22 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     const double tau = hh[1], scal = hh[3];
     for (int c = i + tid; c < d; c += ID_THREADS) vloc[c - i] = (c == i) ? 1.0 : vloc[c - i] * scal;
     __syncthreads();
-    // apply the reflector: a team of TS threads per active column, the teams
-    // dealt over the compacted list of active columns
+    // one pass per active column (a team of TS threads, the teams dealt over
+    // the compacted list): the pending update of step i-1 and the dot
+    // product with u_i; the update of step i is left pending (dprev)
     const int na = nact;
     for (int jb = warp * cols_per_warp; jb < na; jb += ID_WARPS * cols_per_warp) {
       const int q = jb + lane / TS;
       const bool act = q < na;
-      double* wj = act ? col(alist[q]) : nullptr;
-      double dot = team_dot<TS>(i, act ? d : 0, member, vloc, wj);
-      dot *= tau;
-      if (act) team_axpy<TS>(i, d, member, -dot, vloc, wj);
+      const int jl = act ? alist[q] : 0;
+      double* wj = act ? col(jl) : nullptr;
+      const bool pd = act && pend[jl] != 0;
+      const double dot = team_update_dot<TS>(i, act ? d : 0, member, pd, pd ? -dprev[jl] : 0.0,
+                                             vprev, vloc, wj);
+      if (act && member == 0) {
+        dprev[jl] = dot * tau;
+        pend[jl] = 1;
+      }
     }
     __syncthreads();
     // norm downdates (LAPACK xGEQP3's formula and safeguard), one lane per
@@ -520,8 +533,9 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
         double newn = nj;
         if (act && nj != 0.0) {
           // xGEQP3's downdate nj sqrt(max(0, (1 - t)(1 + t))), t = |r| / nj,
-          // and its test t (nj / nrm0)^2 <= tol3z, both multiplied out by nj^2
-          const double r = fabs(col(jl)[i]);
+          // and its test t (nj / nrm0)^2 <= tol3z, both multiplied out by nj^2;
+          // r = the column's entry i after the (pending) update of step i
+          const double r = fabs(fma(-dprev[jl], 1.0, col(jl)[i]));
           const double q = fmax(0.0, (nj - r) * (nj + r));
           if (q <= lim[jl]) recompute = true;
           else newn = sqrt(q);
@@ -532,7 +546,15 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
         while (rm) {
           const int src = __ffs(rm) - 1;
           rm &= rm - 1;
-          const double* wr = col(__shfl_sync(0xffffffffu, jl, src));
+          const int jr = __shfl_sync(0xffffffffu, jl, src);
+          double* wr = col(jr);
+          if (pend[jr]) {   // the exact norm needs the updated column
+            const double a = -dprev[jr];
+            for (int c = i + lane; c < d; c += 32) wr[c] = fma(a, vloc[c - i], wr[c]);
+            __syncwarp();
+            if (lane == 0) pend[jr] = 0;
+            __syncwarp();
+          }
           const double ss = team_sum<32>(i + 1, d, lane, [&](int c, double a) {
             return fma(wr[c], wr[c], a);
           });
@@ -570,6 +592,21 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     }
   }
 
+  // the update of step k - 1 is still pending on the remaining columns
+  if (k > 0) {
+    const double* ul = vbuf + ((k - 1) & 1) * d;
+    const int na = nact;
+    for (int q = warp; q < na; q += ID_WARPS) {
+      const int jl = alist[q];
+      if (!pend[jl]) continue;
+      double* w = col(jl);
+      const double a = -dprev[jl];
+      for (int c = k - 1 + lane; c < d; c += 32) w[c] = fma(a, ul[c - (k - 1)], w[c]);
+      __syncwarp();
+      if (lane == 0) pend[jl] = 0;
+    }
+    __syncthreads();
+  }
   // R1 (k x k, column b = pivot b's first b+1 entries) to global, remaining
   // columns flagged for the ordering of perm[k..m)
   double* R1 = r1buf_base + r1off[item];
@@ -612,7 +649,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
       if (restpos[jl] >= 0) rlist[nr++] = jl;
     nrest = nr;
   }
-  double* diag = vloc;    // k <= d entries
+  double* diag = vbuf;    // k <= d entries
   for (int a = tid; a < k; a += ID_THREADS) diag[a] = __ldcg(R1 + (size_t)a * k + a);
   if (k > 0)
     for (int c = tid; c < k - 1; c += ID_THREADS)
@@ -654,8 +691,164 @@ std::array<IdKernel, 6> group_kernels() {
           id_cpqr_cluster_kernel<4, true>, id_cpqr_cluster_kernel<8, true>,
           id_cpqr_cluster_kernel<16, true>, id_cpqr_cluster_kernel<32, true>};
 }
+// the group mode with two CTAs per SM (at most 128 registers a thread): while
+// one CTA waits at a barrier or runs the serial part of a step (pivot choice,
+// reflector, norm downdates), the other keeps the SM's FP64 pipes busy
+std::array<IdKernel, 6> group_kernels2() {
+  return {id_cpqr_cluster_kernel<4, true, 2>, id_cpqr_cluster_kernel<4, true, 2>,
+          id_cpqr_cluster_kernel<4, true, 2>, id_cpqr_cluster_kernel<8, true, 2>,
+          id_cpqr_cluster_kernel<16, true, 2>, id_cpqr_cluster_kernel<32, true, 2>};
+}
+
+// Measuring tuner of the team size (threads per column) of the ID launches.
+// The results do not depend on the team size (fixed summation tree), so the
+// tuner may try several on real launches: launches are grouped into classes
+// (spread-out or cluster mode, columns in shared or global memory, and the
+// powers of two of the largest side, the sample count and the item count);
+// the first launches of a class try the instruction-count model's choice and
+// its two neighbours, twice each, timed with CUDA events and normalised by
+// the launch's sum of m d min(m, d); later launches of the class take the
+// fastest.  Events are read without waiting, when the next ID launch comes.
+// HSS_AUTOTUNE=0 in the environment keeps the model's choice everywhere.
+class TeamTuner {
+ public:
+  struct Key {
+    int dev, group, smem, lg_m, lg_d, lg_n;
+    bool operator<(const Key& o) const {
+      return std::tie(dev, group, smem, lg_m, lg_d, lg_n) <
+             std::tie(o.dev, o.group, o.smem, o.lg_m, o.lg_d, o.lg_n);
+    }
+  };
+  struct Trial {
+    Key key;
+    int ti;
+    double units;
+    cudaEvent_t e0, e1;
+  };
+
+  static TeamTuner& get() {
+    static TeamTuner t;
+    return t;
+  }
+  // team index for this launch; *trial receives events to record around it
+  // (nullptr when the class has settled)
+  int choose(const Key& k, int model_ti, int min_ti, double units, Trial** trial) {
+    std::lock_guard<std::mutex> lock(mu_);
+    harvest();
+    *trial = nullptr;
+    if (!enabled_) return model_ti;
+    Cls& c = cls_[k];
+    if (c.cand.empty()) {
+      for (int t : {model_ti, model_ti - 1, model_ti + 1})
+        if (t >= min_ti && t <= 5) c.cand.push_back(t);
+      c.sum.assign(c.cand.size(), 0.0);
+      c.cnt.assign(c.cand.size(), 0);
+      c.issued.assign(c.cand.size(), 0);
+    }
+    if (c.best >= 0) return c.best;
+    for (size_t q = 0; q < c.cand.size(); ++q) {
+      if (c.issued[q] < kTrials) {
+        Trial* t = new Trial{k, c.cand[q], units, nullptr, nullptr};
+        if (cudaEventCreate(&t->e0) != cudaSuccess || cudaEventCreate(&t->e1) != cudaSuccess) {
+          cudaGetLastError();
+          if (t->e0) cudaEventDestroy(t->e0);
+          delete t;
+          return model_ti;
+        }
+        ++c.issued[q];
+        ++trials_;
+        *trial = t;
+        return t->ti;
+      }
+    }
+    return model_ti;   // every trial issued, some not yet measured
+  }
+  void launched(Trial* t, bool ok) {
+    std::lock_guard<std::mutex> lock(mu_);
+    if (!ok) {
+      cudaEventDestroy(t->e0);
+      cudaEventDestroy(t->e1);
+      delete t;
+      return;
+    }
+    pending_.push_back(t);
+  }
+  void stats(int32_t* classes, int32_t* settled, int32_t* trials) {
+    std::lock_guard<std::mutex> lock(mu_);
+    harvest();
+    int s = 0;
+    for (auto& kv : cls_) s += kv.second.best >= 0;
+    if (classes) *classes = (int32_t)cls_.size();
+    if (settled) *settled = s;
+    if (trials) *trials = (int32_t)trials_;
+  }
+
+ private:
+  static constexpr int kTrials = 2;
+  struct Cls {
+    std::vector<int> cand, cnt, issued;
+    std::vector<double> sum;
+    int best = -1;
+  };
+  TeamTuner() {
+    const char* e = std::getenv("HSS_AUTOTUNE");
+    enabled_ = !(e && e[0] == '0');
+  }
+  void harvest() {
+    for (size_t q = 0; q < pending_.size();) {
+      Trial* t = pending_[q];
+      const cudaError_t st = cudaEventQuery(t->e1);
+      if (st == cudaErrorNotReady) {
+        ++q;
+        continue;
+      }
+      float ms = 0.f;
+      if (st == cudaSuccess && cudaEventElapsedTime(&ms, t->e0, t->e1) == cudaSuccess) {
+        Cls& c = cls_[t->key];
+        for (size_t i = 0; i < c.cand.size(); ++i)
+          if (c.cand[i] == t->ti) {
+            c.sum[i] += ms / std::max(t->units, 1.0);
+            ++c.cnt[i];
+          }
+        bool all = true;
+        for (int n : c.cnt) all = all && n >= kTrials;
+        if (all && c.best < 0) {
+          size_t b = 0;
+          for (size_t i = 1; i < c.cand.size(); ++i)
+            if (c.sum[i] < c.sum[b]) b = i;
+          c.best = c.cand[b];
+        }
+      } else {
+        cudaGetLastError();
+      }
+      cudaEventDestroy(t->e0);
+      cudaEventDestroy(t->e1);
+      delete t;
+      pending_[q] = pending_.back();
+      pending_.pop_back();
+    }
+  }
+  std::mutex mu_;
+  std::map<Key, Cls> cls_;
+  std::vector<Trial*> pending_;
+  int64_t trials_ = 0;
+  bool enabled_ = true;
+};
+
+int ilog2(long x) {
+  int l = 0;
+  while (x > 1) {
+    x >>= 1;
+    ++l;
+  }
+  return l;
+}
 
 }  // namespace
+
+void id_tuner_stats(int32_t* classes, int32_t* settled, int32_t* trials) {
+  TeamTuner::get().stats(classes, settled, trials);
+}
 
 Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, bool f64,
                       cudaStream_t s, Arena* scratch) {
@@ -679,8 +872,8 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
   const int d = std::max(max_d, 1);
   auto need = [&](int c) {
     int mloc = (max_m + c - 1) / c;
-    return sizeof(double) * (3 * (size_t)d + 3 * (size_t)mloc) +
-           3 * sizeof(int) * (size_t)((mloc + 1) & ~1);
+    return sizeof(double) * (4 * (size_t)d + 4 * (size_t)mloc) +
+           4 * sizeof(int) * (size_t)((mloc + 1) & ~1);
   };
   size_t base = need(C);
   size_t wbytes = sizeof(double) * (size_t)((max_m + C - 1) / C) * (d | 1);
@@ -725,7 +918,10 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
                                           optin - (int)fa.sharedSizeBytes));
         HSS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
       }
-      for (auto fn : group_kernels()) {
+      std::vector<IdKernel> gk;
+      for (auto fn : group_kernels()) gk.push_back(fn);
+      for (auto fn : group_kernels2()) gk.push_back(fn);
+      for (auto fn : gk) {
         cudaFuncAttributes fa;
         HSS_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
         HSS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -782,11 +978,25 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
   // dominates a barrier in global memory): each item gets gsz CTAs, all
   // resident at once (cooperative launch), at least 8 columns per CTA
   int gsz = 0;
+  bool two_per_sm = false;
   {
     const int per_item = sms / count;
     const long step_work = (long)((max_m + C - 1) / C) * d;   // per CTA, cluster mode
     const int g = std::min(per_item, max_m / 8);
-    if (g > 2 * C && step_work >= GROUP_MIN_STEP_WORK) gsz = g;
+    // twice the CTAs, two on each SM, when both fit (registers, shared
+    // memory) and each still has at least 8 columns
+    const int g2 = std::min(2 * per_item, max_m / 8);
+    if (step_work >= GROUP_MIN_STEP_WORK && g2 > 2 * C && g2 >= 2 * g - 1) {
+      int nb = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, group_kernels2()[5], ID_THREADS,
+                                                        need(g2)) == cudaSuccess &&
+          nb >= 2) {
+        gsz = g2;
+        two_per_sm = true;
+      }
+      cudaGetLastError();
+    }
+    if (!two_per_sm && g > 2 * C && step_work >= GROUP_MIN_STEP_WORK) gsz = g;
   }
   // threads per column: results do not depend on it (fixed summation tree),
   // so pick the team size with the fewest FP64 instructions on the busiest of
@@ -812,6 +1022,11 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
     }
     return ti;
   };
+  // the tuner's work measure of this launch and the device it runs on
+  double units = 0.0;
+  for (const IdItem& x : h) units += (double)x.m * x.d * std::min(x.m, x.d);
+  int dev_ordinal = 0;
+  HSS_CUDA_TRY(cudaGetDevice(&dev_ordinal));
   GroupArgs ga = {};
   Err res;
   bool done = false;
@@ -841,8 +1056,18 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
     gattr[0].val.cooperative = 1;
     gcfg.attrs = gattr;
     gcfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&gcfg, group_kernels()[team_index(gsz, true)], items_dev,
+    TeamTuner::Trial* trial = nullptr;
+    const int ti = TeamTuner::get().choose(
+        TeamTuner::Key{dev_ordinal, two_per_sm ? 2 : 1, 0, ilog2(max_m), ilog2(d), ilog2(count)},
+        team_index(gsz, true), 2, units, &trial);
+    if (trial) cudaEventRecord(trial->e0, s);
+    cudaError_t e = cudaLaunchKernelEx(&gcfg, (two_per_sm ? group_kernels2() : group_kernels())[ti],
+                                       items_dev,
                                        f64 ? 1 : 0, 0, r1, (const int64_t*)offd, ga);
+    if (trial) {
+      if (e == cudaSuccess) cudaEventRecord(trial->e1, s);
+      TeamTuner::get().launched(trial, e == cudaSuccess);
+    }
     if (e == cudaErrorCooperativeLaunchTooLarge) {
       // fewer SMs than expected are free for this context: clusters instead
       cudaGetLastError();
@@ -865,8 +1090,17 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
     ga = GroupArgs{};
   }
   if (!done) {
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kernels()[team_index(C, w_in_smem == 0)], items_dev, f64 ? 1 : 0,
+    TeamTuner::Trial* trial = nullptr;
+    const int ti = TeamTuner::get().choose(
+        TeamTuner::Key{dev_ordinal, 0, w_in_smem, ilog2(max_m), ilog2(d), ilog2(count)},
+        team_index(C, w_in_smem == 0), w_in_smem ? 0 : 2, units, &trial);
+    if (trial) cudaEventRecord(trial->e0, s);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernels()[ti], items_dev, f64 ? 1 : 0,
                                        w_in_smem, r1, (const int64_t*)offd, ga);
+    if (trial) {
+      if (e == cudaSuccess) cudaEventRecord(trial->e1, s);
+      TeamTuner::get().launched(trial, e == cudaSuccess);
+    }
     res = e == cudaSuccess ? check_launch("id_cpqr_cluster_kernel")
                            : fail(HSS_ERR_CUDA, std::string("id_cpqr_cluster_kernel launch: ") +
                                                     cudaGetErrorString(e));

@@ -225,6 +225,8 @@ struct IdItem {
 // Each item's norms scratch must hold 2*m doubles and its work m*d doubles.
 Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& host_items, bool f64,
                       cudaStream_t s, Arena* scratch = nullptr);
+// The ID team-size tuner: shape classes seen, classes settled, timed trials.
+void id_tuner_stats(int32_t* classes, int32_t* settled, int32_t* trials);
 
 // --------------------------------------------- batched gathered GEMM
 // out[j][c] = (X ? X[xrow(j)][c] : 0) + sign * sum_l Mat(j,l) * Z[zrow(l)][c]

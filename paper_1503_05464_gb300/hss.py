@@ -59,7 +59,7 @@ _lib = None
 EXPORTS = ["hss_default_opts", "hss_compress", "hss_matvec", "hss_factor", "hss_solve",
            "hss_info", "hss_node_ranks", "hss_destroy", "hss_last_error",
            "hss_random_gaussian", "hss_sample", "hss_id_batched", "hss_kernel_launches", "hss_sample_noalloc",
-           "hss_pool_bytes", "hss_set_fault",
+           "hss_pool_bytes", "hss_set_fault", "hss_tuner_stats",
            "hss_batch_create", "hss_batch_submit", "hss_batch_step", "hss_batch_take",
            "hss_batch_last_error", "hss_batch_destroy", "hss_compress_batched",
            "hss_factor_batched", "hss_solve_batched"]
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH):
     L.hss_sample_noalloc.argtypes = L.hss_sample.argtypes
     L.hss_pool_bytes.argtypes = [ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.hss_set_fault.argtypes = [i32, i64]
+    L.hss_tuner_stats.argtypes = [ctypes.POINTER(i32)] * 3
     L.hss_kernel_launches.argtypes = []
     L.hss_kernel_launches.restype = ctypes.c_int64
     L.hss_batch_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
@@ -352,6 +353,13 @@ def hss_set_fault(kind: int, value: int = 0) -> None:
     fails; HSS_FAULT_WAIT_LIMIT: the ID's group barrier gives up after value
     cycles) or clear them (HSS_FAULT_NONE)."""
     _check(load().hss_set_fault(kind, value))
+
+
+def hss_tuner_stats() -> dict:
+    """Shape classes seen / settled and timed trials of the ID launch tuner."""
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().hss_tuner_stats(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"classes": a.value, "settled": b.value, "trials": c.value}
 
 
 def hss_pool_bytes() -> tuple[int, int]:
