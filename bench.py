@@ -14,6 +14,8 @@ Workloads (synthetic, seeded; stand-ins for the paper's application matrices):
               adaptive sampling, Section 4, Table 5, n = 58800).  Checked
               against the FP64 oracle's result stored in
               tests/golden/bem60k_oracle.json (same matrix bits).
+  bem32k      the same family and settings at n=32768 (4.3 GB: the size of
+              the kernel captures in profiles/)
   gauss20k    FP32 Gaussian kernel, n=20000, h=0.2, lambda=1, points uniform in
               the unit cube in RCB order, leaf 256, rtol 1e-4, d0=128, step 64
   toeplitz2k  FP64 Toeplitz a_ij = 1/(1+|i-j|), a_ii = 10, n=2000, leaf 128,
@@ -66,6 +68,8 @@ WORKLOADS = {
                        step=32, dtype="f64", seed=1001),
     "bem60k": dict(family="bem_like_sphere", n=60000, leaf=512, rtol=1e-6, d0=256, step=128,
                    dtype="f32", seed=1003),
+    "bem32k": dict(family="bem_like_sphere", n=32768, leaf=512, rtol=1e-6, d0=256, step=128,
+                   dtype="f32", seed=1003),
     "batch512": dict(family="mixed_batch", count=512, seed=1004, dtype="f32", nrhs=16),
     "serve": dict(family="laplacian_schur", ks=[45, 71, 100, 141, 200], rtol=1e-6, leaf=256,
                   d0=128, step=64, dtype="f32", seed=1005, budget=150e9, load=0.8),
@@ -78,6 +82,9 @@ GOLDEN_BEM60K = os.path.join(ROOT, "tests", "golden", "bem60k_oracle.json")
 # on the same part: 1.20); FP32 FMA: 152 SMs x 128 lanes x 2 flops at the
 # probed ~1.79 GHz under load (own probe: 69.7 TFLOP/s)
 FP64_PEAK_TFLOPS = 1.25
+# DRAM bytes (read + write) per FP64 flop of the ID kernel over a whole bem32k
+# compression, from profiles/id_cpqr_dram_bem32k.md
+ID_DRAM_BYTES_PER_FLOP = None
 FP32_SIMT_PEAK_TFLOPS = 69.7
 
 
@@ -291,7 +298,9 @@ def run_ours(args, wl):
         "id_cpqr_fp64": {"ms": id_ms, "bound": "alu", "achieved": id_tflops,
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": id_tflops / FP64_PEAK_TFLOPS,
-                         "peak_source": "GB300 nominal dense FP64 (own FMA probe: 1.20)"},
+                         "peak_source": "GB300 nominal dense FP64 (own FMA probe: 1.20)",
+                         "flops": info["flops_id"], "launches": info["id_launches"],
+                         "flops_is": "sum over node sides of sum_{i<k} 4 (d-i)(m-i)"},
         "fused_sampling": {"ms": s_ms, "bound": bound, "achieved": samp_tflops,
                            "peak": unit_peak, "unit": "TFLOP/s", "roofline_ms": roof_ms,
                            "frac": roof_ms / s_ms if s_ms > 0 else 0.0,
@@ -307,6 +316,12 @@ def run_ours(args, wl):
         roof.pop(key, None)
     roof["kernel"] = dom
     roof["traffic"] = None
+    if dom == "id_cpqr_fp64" and info["id_launches"] > 0 and ID_DRAM_BYTES_PER_FLOP:
+        # DRAM bytes per FP64 flop of the ID launches, measured by ncu over a
+        # whole bem32k compression (profiles/id_cpqr_dram_bem32k.md), times
+        # this compression's flops per ID launch
+        roof["traffic"] = ID_DRAM_BYTES_PER_FLOP * info["flops_id"] / info["id_launches"]
+        roof["traffic_unit"] = "bytes per launch (scaled from the bem32k capture)"
     value = ms / 1e3 / (args.steps * world) if world > 1 else ms / 1e3 / args.steps
     out = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,

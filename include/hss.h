@@ -97,13 +97,15 @@ typedef struct {
   double ms_id;                     /* device time in the batched ID kernel    */
   double ms_levels;                 /* host wall time of the level loop        */
   double flops_sample;              /* 4 n^2 d summed over passes              */
-  double flops_id;                  /* sum over IDs of 4 d m k (FP64)          */
+  double flops_id;                  /* FP64 flops of the IDs: sum over node sides
+                                       of sum_{i<k} 4 (d - i)(m - i)            */
   int32_t factored;                 /* 1 after hss_factor                      */
   int64_t launches;                 /* kernels launched by hss_compress        */
   int64_t bytes_d2h;                /* bytes read back to the host (ranks)     */
   double ms_host_id_launch;         /* host time preparing and launching IDs   */
   double ms_host_wait;              /* host time blocked on the rank readback  */
   double ms_host_sample;            /* host wall time of the sampling passes   */
+  int64_t id_launches;              /* ID kernel launches of hss_compress      */
 } hss_info_t;
 
 /* Fills *opts with defaults: leaf_size 128, rtol 1e-6, atol 0, d0 64,

@@ -284,7 +284,7 @@ hss_status hss_id_batched(int32_t count, const void* const* Yt, const int32_t* m
     size_t wo = 0, no = 0;
     for (int i = 0; i < count; ++i) {
       items[i] = IdItem{hy[i], hm[i], hd[i], hl[i], hp[i], he[i], k + i, wb + wo, nb + no,
-                        rtol, atol};
+                        rtol, atol, INT32_MAX};
       wo += (size_t)hm[i] * hd[i];
       no += 2 * (size_t)hm[i];
     }

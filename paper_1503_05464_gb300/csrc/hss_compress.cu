@@ -16,6 +16,7 @@
 #include "hss_tree.h"
 
 #include <algorithm>
+#include <climits>
 #include <chrono>
 #include <cstring>
 #include <memory>
@@ -337,10 +338,13 @@ struct Job {
       HSS_TRY(h->store.alloc_t(&g.permc, std::max(L.mc, 1), s));
       HSS_TRY(h->store.alloc_t(&g.Er, std::max<size_t>((size_t)L.mr * std::min(L.mr, d), 1), s));
       HSS_TRY(h->store.alloc_t(&g.Ec, std::max<size_t>((size_t)L.mc * std::min(L.mc, d), 1), s));
+      // a side whose rank exceeds d - p fails the node (d < m): its
+      // generator would be discarded, so the ID skips it
+      const int p = h->opts.oversample_p;
       IdItem a{L.Yr, L.mr, d, ld, g.permr, g.Er, nullptr, nullptr, nullptr,
-               h->opts.rtol, h->opts.atol};
+               h->opts.rtol, h->opts.atol, d < L.mr ? d - p : INT32_MAX};
       IdItem b{L.Yc, L.mc, d, ld, g.permc, g.Ec, nullptr, nullptr, nullptr,
-               h->opts.rtol, h->opts.atol};
+               h->opts.rtol, h->opts.atol, d < L.mc ? d - p : INT32_MAX};
       rd.ids.push_back(a);
       rd.ids.push_back(b);
     }
@@ -357,7 +361,14 @@ struct Job {
       Loc& L = loc[q];
       NodeGen& g = h->gen[L.id];
       int kr = ks[2 * q], kc = ks[2 * q + 1];
-      h->info.flops_id += 4.0 * d * (double)L.mr * kr + 4.0 * d * (double)L.mc * kc;
+      // FP64 work of the two truncated CPQRs: each of the k steps takes the
+      // dot product and the update of every remaining column over the
+      // remaining rows, sum_{i<k} 4 (d - i) (m - i)
+      auto cpqr_flops = [](double dd, double mm, double kk) {
+        return 4.0 * (kk * dd * mm - (dd + mm) * kk * (kk - 1.0) / 2.0 +
+                      (kk - 1.0) * kk * (2.0 * kk - 1.0) / 6.0);
+      };
+      h->info.flops_id += cpqr_flops(d, L.mr, kr) + cpqr_flops(d, L.mc, kc);
       // adaptive test (Section 3.2): fail iff d < m and k > d - p on either side
       bool failr = d < L.mr && kr > d - p;
       bool failc = d < L.mc && kc > d - p;
@@ -555,6 +566,7 @@ struct Driver {
       cudaEventDestroy(e1);
       for (Job<T>* j : lev) {
         j->h->info.ms_id += ms;
+        j->h->info.id_launches += 1;
         j->h->info.ms_host_id_launch += th1 - th0;
         j->h->info.ms_host_wait += th2 - th1;
         j->h->info.bytes_d2h += (int64_t)(2 * j->nfresh * sizeof(int32_t));

@@ -261,12 +261,18 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     if constexpr (GRP) {
       __syncthreads();
       if (tid == 0) {
+        // arrive after a device-wide fence (the CTA's writes, ordered before
+        // by the block barrier, become visible first), then poll with
+        // acquire loads; the abort flag and the clock are looked at every
+        // 16th poll
         __threadfence();
         atomicAdd(ga.ctr + item, 1u);
         const unsigned target = (++nsync) * static_cast<unsigned>(C);
         const long long t0 = clock64();
         int st = 0;
+        unsigned polls = 0;
         while (ld_acquire_gpu(ga.ctr + item) < target) {
+          if ((++polls & 15u) != 0u) continue;
           if (*reinterpret_cast<volatile int*>(ga.abort)) {
             st = 1;
             break;
@@ -372,14 +378,41 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
       double* w = col(jl);
       if (r > 0 && pend[jl]) {
         // the candidate's pending update of step r - 1, so that its residual
-        // (and the pivot column the peers copy) is current
+        // (and the pivot column the peers copy) is current; the sum of
+        // squares below row r rides along (entry c on lane c mod 32, in
+        // increasing c, then team_sum's butterfly: team_sum's bits)
         const double a = -dprev[jl];
         const double* up = vbuf + ((r - 1) & 1) * d;
-        for (int c = r - 1 + lane; c < d; c += 32) w[c] = fma(a, up[c - (r - 1)], w[c]);
+        double acc = 0.0;
+        // eight 32-row chunks at a time: all their loads are issued before
+        // the first store, so the loads of the column (global memory for the
+        // large sides) are in flight together instead of one after another
+        constexpr int U = 8;
+        for (int base = ((r - 1) / 32) * 32; base < d; base += 32 * U) {
+          double x[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int c = base + 32 * u + lane;
+            x[u] = (c >= r - 1 && c < d) ? w[c] : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int c = base + 32 * u + lane;
+            if (c >= r - 1 && c < d) {
+              x[u] = fma(a, up[c - (r - 1)], x[u]);
+              w[c] = x[u];
+              if (c >= r + 1) acc = fma(x[u], x[u], acc);
+            }
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc = acc + __shfl_xor_sync(0xffffffffu, acc, o);
+        st = acc;
         __syncwarp();
         if (lane == 0) pend[jl] = 0;
+      } else {
+        st = team_sum<32>(r + 1, d, lane, [&](int c, double a) { return fma(w[c], w[c], a); });
       }
-      st = team_sum<32>(r + 1, d, lane, [&](int c, double a) { return fma(w[c], w[c], a); });
       alpha = r < d ? w[r] : 0.0;
     }
     if constexpr (GRP) {
@@ -489,8 +522,18 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
         const double* src = cg::this_cluster().map_shared_rank(Wsm + (size_t)(p / C) * ldw, owner);
         for (int c = i + tid - 64; c < d; c += ID_THREADS - 64) vloc[c - i] = src[c];
       } else {
-        const double* src = it.work + (size_t)p * d;   // written by another CTA: read from L2
-        for (int c = i + tid - 64; c < d; c += ID_THREADS - 64) vloc[c - i] = __ldcg(src + c);
+        // written by another CTA: read from L2, eight loads in flight per
+        // thread before the stores
+        const double* src = it.work + (size_t)p * d;
+        constexpr int U = 8, NT = ID_THREADS - 64;
+        for (int c0 = i + tid - 64; c0 < d; c0 += NT * U) {
+          double x[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) x[u] = c0 + NT * u < d ? __ldcg(src + c0 + NT * u) : 0.0;
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (c0 + NT * u < d) vloc[c0 + NT * u - i] = x[u];
+        }
       }
     }
     __syncthreads();
@@ -550,6 +593,7 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
           double* wr = col(jr);
           if (pend[jr]) {   // the exact norm needs the updated column
             const double a = -dprev[jr];
+#pragma unroll 8
             for (int c = i + lane; c < d; c += 32) wr[c] = fma(a, vloc[c - i], wr[c]);
             __syncwarp();
             if (lane == 0) pend[jr] = 0;
@@ -592,6 +636,14 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     }
   }
 
+  if (k > it.fail_above) {
+    // the caller discards this side (its node fails the adaptive test): no
+    // generator; the barrier keeps every CTA's shared memory alive until the
+    // cluster's last reads and pushes of the loop are done
+    if (crank == 0 && tid == 0) *it.k = k;
+    sync_all();
+    return;
+  }
   // the update of step k - 1 is still pending on the remaining columns
   if (k > 0) {
     const double* ul = vbuf + ((k - 1) & 1) * d;

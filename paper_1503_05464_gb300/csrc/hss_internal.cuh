@@ -220,6 +220,9 @@ struct IdItem {
   double* norms;    // 2 * m doubles of scratch
   double rtol;      // stop at the first |R_ii| <= max(rtol |R_11|, atol)
   double atol;
+  // rank above which the caller discards the result (a node failing the
+  // adaptive test, k > d - p): only k is written then, no generator
+  int32_t fail_above;
 };
 // items_dev: device copy of `host_items` (the host copy sizes the launch).
 // Each item's norms scratch must hold 2*m doubles and its work m*d doubles.

@@ -52,7 +52,7 @@ class HssInfo(ctypes.Structure):
                 ("flops_id", ctypes.c_double), ("factored", ctypes.c_int32),
                 ("launches", ctypes.c_int64), ("bytes_d2h", ctypes.c_int64),
                 ("ms_host_id_launch", ctypes.c_double), ("ms_host_wait", ctypes.c_double),
-                ("ms_host_sample", ctypes.c_double)]
+                ("ms_host_sample", ctypes.c_double), ("id_launches", ctypes.c_int64)]
 
 
 _lib = None

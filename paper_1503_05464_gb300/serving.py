@@ -145,9 +145,16 @@ class Server:
         def now():
             return time.perf_counter() - t0
 
-        worker = threading.Thread(target=self._solve_thread,
-                                  args=(finished, st, lock, acct, now, errors), daemon=True)
-        worker.start()
+        due = []                              # heap of (time, seq, request, nrhs)
+        factor_done = threading.Event()
+        workers = [threading.Thread(target=self._factor_thread,
+                                    args=(finished, due, lock, acct, now, errors, factor_done),
+                                    daemon=True),
+                   threading.Thread(target=self._solve_thread,
+                                    args=(due, st, lock, acct, now, errors, factor_done),
+                                    daemon=True)]
+        for w in workers:
+            w.start()
         try:
             while pending or inflight:
                 t = now()
@@ -191,52 +198,68 @@ class Server:
                     finished.put(r)
         finally:
             finished.put(None)                # no more compressions
-            worker.join()
+            for w in workers:
+                w.join()
             batch.close()
         if errors:
             raise errors[0]
         st.wall_s = now()
         return st
 
-    def _solve_thread(self, finished, st, lock, acct, now, errors):
-        """Factors finished compressions and serves due right-hand sides on
-        its own stream; all requests of one pass share one launch per level."""
+    def _factor_thread(self, finished, due, lock, acct, now, errors, factor_done):
+        """Factors the finished compressions on its own stream, all those
+        waiting at once (one launch per level round), and schedules their
+        right-hand sides."""
         stream = torch.cuda.Stream()
-        due = []                              # heap of (time, seq, request, nrhs)
         seq = 0
         closing = False
         try:
+            while not closing:
+                fresh = []
+                r = finished.get()                # wait for the next compression
+                while True:
+                    if r is None:
+                        closing = True
+                    else:
+                        fresh.append(r)
+                    try:
+                        r = finished.get_nowait()
+                    except queue.Empty:
+                        break
+                if not fresh:
+                    continue
+                sts = H.hss_factor_batched([q.handle for q in fresh], stream=stream)
+                for q, status in zip(fresh, sts):
+                    if status != H.HSS_OK:
+                        raise H.HssError(status, f"request {q.rid}: factorization failed")
+                    info = H.hss_info(q.handle)
+                    q.ranks = max(info["max_rank_r"], info["max_rank_c"])
+                    q.resident = info["bytes_hss"] + info["bytes_ulv"]
+                    q.solves_left = len(q.solves)
+                    t = now()
+                    with lock:
+                        acct["used"] += q.resident - q.reserved
+                        for off, nrhs in q.solves:
+                            heapq.heappush(due, (t + off, seq, q, nrhs))
+                            seq += 1
+        except Exception as e:                # reported by the admitting thread
+            errors.append(e)
+        finally:
+            factor_done.set()
+
+    def _solve_thread(self, due, st, lock, acct, now, errors, factor_done):
+        """Serves every due right-hand side on its own stream, all those due
+        at once (one launch per sweep round), and releases finished requests."""
+        stream = torch.cuda.Stream()
+        try:
             with torch.cuda.stream(stream):
                 while True:
-                    fresh = []
-                    while True:
-                        try:
-                            r = finished.get_nowait()
-                        except queue.Empty:
-                            break
-                        if r is None:
-                            closing = True
-                        else:
-                            fresh.append(r)
-                    if fresh:
-                        sts = H.hss_factor_batched([r.handle for r in fresh], stream=stream)
-                        for r, status in zip(fresh, sts):
-                            if status != H.HSS_OK:
-                                raise H.HssError(status, f"request {r.rid}: factorization failed")
-                            info = H.hss_info(r.handle)
-                            r.ranks = max(info["max_rank_r"], info["max_rank_c"])
-                            r.resident = info["bytes_hss"] + info["bytes_ulv"]
-                            with lock:
-                                acct["used"] += r.resident - r.reserved
-                            t = now()
-                            r.solves_left = len(r.solves)
-                            for off, nrhs in r.solves:
-                                heapq.heappush(due, (t + off, seq, r, nrhs))
-                                seq += 1
                     t = now()
                     batchq = []
-                    while due and due[0][0] <= t:
-                        batchq.append(heapq.heappop(due))
+                    with lock:
+                        while due and due[0][0] <= t:
+                            batchq.append(heapq.heappop(due))
+                        nxt = due[0][0] if due else None
                     if batchq:
                         Bs = []
                         for _, _, r, nrhs in batchq:
@@ -266,9 +289,12 @@ class Server:
                                     r.handle = None
                         del Xs, Bs
                         continue
-                    if closing and not due and finished.empty():
-                        return
-                    nxt = due[0][0] - now() if due else 0.001
-                    time.sleep(max(0.0, min(nxt, 0.001)))
+                    if nxt is None and factor_done.is_set():
+                        with lock:
+                            if not due:
+                                return
+                        continue
+                    wait = (nxt - now()) if nxt is not None else 0.001
+                    time.sleep(max(0.0, min(wait, 0.001)))
         except Exception as e:                # reported by the admitting thread
             errors.append(e)
