@@ -376,43 +376,25 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     if (v != LLONG_MIN) {
       const int jl = (j - crank) / C;
       double* w = col(jl);
-      if (r > 0 && pend[jl]) {
-        // the candidate's pending update of step r - 1, so that its residual
-        // (and the pivot column the peers copy) is current; the sum of
-        // squares below row r rides along (entry c on lane c mod 32, in
-        // increasing c, then team_sum's butterfly: team_sum's bits)
-        const double a = -dprev[jl];
-        const double* up = vbuf + ((r - 1) & 1) * d;
-        double acc = 0.0;
-        // eight 32-row chunks at a time: all their loads are issued before
-        // the first store, so the loads of the column (global memory for the
-        // large sides) are in flight together instead of one after another
-        constexpr int U = 8;
-        for (int base = ((r - 1) / 32) * 32; base < d; base += 32 * U) {
-          double x[U];
+      // its pending update, if any, has been applied by the whole CTA;
+      // sum of squares below row r: entry c goes to partial (c / 32) mod 4
+      // of lane c mod 32, in increasing c (four independent chains, loads
+      // four chunks ahead), then ((p0 + p1) + (p2 + p3)) and a butterfly
+      // over the lanes: a fixed order, computed by the owner alone
+      double pa[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int base = ((r + 1) / 128) * 128; base < d; base += 128) {
+        double x[4];
 #pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int c = base + 32 * u + lane;
-            x[u] = (c >= r - 1 && c < d) ? w[c] : 0.0;
-          }
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int c = base + 32 * u + lane;
-            if (c >= r - 1 && c < d) {
-              x[u] = fma(a, up[c - (r - 1)], x[u]);
-              w[c] = x[u];
-              if (c >= r + 1) acc = fma(x[u], x[u], acc);
-            }
-          }
+        for (int u = 0; u < 4; ++u) {
+          const int c = base + 32 * u + lane;
+          x[u] = (c >= r + 1 && c < d) ? w[c] : 0.0;
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc = acc + __shfl_xor_sync(0xffffffffu, acc, o);
-        st = acc;
-        __syncwarp();
-        if (lane == 0) pend[jl] = 0;
-      } else {
-        st = team_sum<32>(r + 1, d, lane, [&](int c, double a) { return fma(w[c], w[c], a); });
+        for (int u = 0; u < 4; ++u) pa[u] = fma(x[u], x[u], pa[u]);
       }
+      st = (pa[0] + pa[1]) + (pa[2] + pa[3]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) st = st + __shfl_xor_sync(0xffffffffu, st, o);
       alpha = r < d ? w[r] : 0.0;
     }
     if constexpr (GRP) {
@@ -618,21 +600,36 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
         }
       }
       warp_argmax_bits(cv, cj);
-      if (nwd == 1) {
-        push_candidate(slot ^ 1, cv, cj, i + 1);
-      } else if (lane == 0) {
+      if (lane == 0) {
         redb[warp] = cv;
         redi[warp] = cj;
       }
     }
-    if (nwd > 1) {
-      __syncthreads();
-      if (warp == 0) {
-        long long cv = lane < nwd ? redb[lane] : LLONG_MIN;
-        int cj = lane < nwd ? redi[lane] : INT_MAX;
-        warp_argmax_bits(cv, cj);
-        push_candidate(slot ^ 1, cv, cj, i + 1);
+    __syncthreads();
+    {
+      // the CTA's candidate (the same total order as the warps' arg-max),
+      // known to every thread; the whole CTA applies its pending update of
+      // step i, so all its rows' loads are in flight at once, then one warp
+      // sums its residual and pushes it
+      long long cv = LLONG_MIN;
+      int cj = INT_MAX;
+      for (int w = 0; w < nwd; ++w)
+        if (redb[w] > cv || (redb[w] == cv && redi[w] < cj)) {
+          cv = redb[w];
+          cj = redi[w];
+        }
+      if (cv != LLONG_MIN) {
+        const int jl = (cj - crank) / C;
+        if (pend[jl]) {
+          double* w = col(jl);
+          const double a = -dprev[jl];
+          for (int c = i + tid; c < d; c += ID_THREADS) w[c] = fma(a, vloc[c - i], w[c]);
+          __syncthreads();
+          if (tid == 0) pend[jl] = 0;
+          __syncthreads();
+        }
       }
+      if (warp == 0) push_candidate(slot ^ 1, cv, cj, i + 1);
     }
   }
 
@@ -750,6 +747,15 @@ std::array<IdKernel, 6> group_kernels2() {
   return {id_cpqr_cluster_kernel<4, true, 2>, id_cpqr_cluster_kernel<4, true, 2>,
           id_cpqr_cluster_kernel<4, true, 2>, id_cpqr_cluster_kernel<8, true, 2>,
           id_cpqr_cluster_kernel<16, true, 2>, id_cpqr_cluster_kernel<32, true, 2>};
+}
+
+// cluster mode with two CTAs per SM, for launches of more CTAs than SMs
+// (the leaf levels): one wave instead of two, and the same overlap of one
+// CTA's serial part with the other's FP64 work
+std::array<IdKernel, 6> kernels2() {
+  return {id_cpqr_cluster_kernel<4, false, 2>, id_cpqr_cluster_kernel<4, false, 2>,
+          id_cpqr_cluster_kernel<4, false, 2>, id_cpqr_cluster_kernel<8, false, 2>,
+          id_cpqr_cluster_kernel<16, false, 2>, id_cpqr_cluster_kernel<32, false, 2>};
 }
 
 // Measuring tuner of the team size (threads per column) of the ID launches.
@@ -963,7 +969,10 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
     if (dev >= 0 && dev < 64 && !done[dev]) {
       int optin = 0;
       HSS_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-      for (auto fn : kernels()) {
+      std::vector<IdKernel> ck;
+      for (auto fn : kernels()) ck.push_back(fn);
+      for (auto fn : kernels2()) ck.push_back(fn);
+      for (auto fn : ck) {
         cudaFuncAttributes fa;
         HSS_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
         HSS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1142,13 +1151,24 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
     ga = GroupArgs{};
   }
   if (!done) {
+    // more CTAs than SMs, columns in global memory: two CTAs per SM when
+    // they fit (registers, shared memory)
+    bool two = false;
+    if ((long)count * C > sms && !w_in_smem) {
+      int nb = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernels2()[5], ID_THREADS, smem) ==
+              cudaSuccess &&
+          nb >= 2)
+        two = true;
+      cudaGetLastError();
+    }
     TeamTuner::Trial* trial = nullptr;
     const int ti = TeamTuner::get().choose(
-        TeamTuner::Key{dev_ordinal, 0, w_in_smem, ilog2(max_m), ilog2(d), ilog2(count)},
+        TeamTuner::Key{dev_ordinal, two ? 3 : 0, w_in_smem, ilog2(max_m), ilog2(d), ilog2(count)},
         team_index(C, w_in_smem == 0), w_in_smem ? 0 : 2, units, &trial);
     if (trial) cudaEventRecord(trial->e0, s);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kernels()[ti], items_dev, f64 ? 1 : 0,
-                                       w_in_smem, r1, (const int64_t*)offd, ga);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, (two ? kernels2() : kernels())[ti], items_dev,
+                                       f64 ? 1 : 0, w_in_smem, r1, (const int64_t*)offd, ga);
     if (trial) {
       if (e == cudaSuccess) cudaEventRecord(trial->e1, s);
       TeamTuner::get().launched(trial, e == cudaSuccess);
