@@ -475,7 +475,10 @@ def run_serving(P, dev, stream, wl, count, load=None, warm=True):
     rate = load / mean_service
     reqs = S.poisson_requests(count, rate, wl["ks"], seed=wl["seed"], max_solves=3,
                               nrhs_range=(1, 64))
-    srv = S.Server(make, opts, budget_bytes=int(wl["budget"]), stream=stream)
+    # requests of order >= 15000 compress in a lane of their own (the full
+    # size mix); the bounded default stream (n <= 5041) has one lane
+    split = 15000 if max(wl["ks"]) ** 2 >= 15000 else None
+    srv = S.Server(make, opts, budget_bytes=int(wl["budget"]), stream=stream, lane_split_n=split)
     l0 = P.hss.hss_kernel_launches()
     st = srv.run(reqs)
     summ = st.summary()
@@ -483,7 +486,7 @@ def run_serving(P, dev, stream, wl, count, load=None, warm=True):
                  "service_s_alone": {str(k * k): v for k, v in service.items()},
                  "launches": P.hss.hss_kernel_launches() - l0,
                  "sizes": [k * k for k in wl["ks"]], "rtol": wl["rtol"],
-                 "budget_gb": wl["budget"] / 1e9})
+                 "budget_gb": wl["budget"] / 1e9, "lane_split_n": split})
     srv.templates.clear()
     torch.cuda.empty_cache()
     return summ

@@ -301,9 +301,11 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   const int mloc = (m - crank + C - 1) / C;       // columns crank, crank+C, ...
   const int mloc_max = (m + C - 1) / C;
   // reflectors of steps i (vbuf + (i & 1) d) and i - 1: the update of a step
-  // is applied in the same pass as the next step's dot product
-  double* vbuf = smem;                            // 2 d
-  double* nrm = vbuf + 2 * d;                     // mloc_max
+  // is applied in the same pass as the next step's dot product; after the
+  // elimination the same 3 d doubles hold R1's diagonal (d) and two staged
+  // R1 columns of the back substitution (colbuf, 2 d)
+  double* vbuf = smem;                            // 3 d
+  double* nrm = vbuf + 3 * d;                     // mloc_max
   double* lim = nrm + mloc_max;                   // mloc_max: tol3z * (norm at last recompute)^2
   double* rdiag = lim + mloc_max;                 // mloc_max: R_ii of the pivot columns
   double* dprev = rdiag + mloc_max;               // mloc_max: tau (u_i . w), update pending
@@ -317,8 +319,8 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
   int* alist = pstep + ((mloc_max + 1) & ~1);
   int* apos = alist + ((mloc_max + 1) & ~1);
   int* pend = apos + ((mloc_max + 1) & ~1);       // 1: the column's update by dprev is pending
-  double* colbuf = reinterpret_cast<double*>(pend + ((mloc_max + 1) & ~1));   // 2 d: R1 columns
-  double* Wsm = colbuf + 2 * d;
+  double* colbuf = vbuf + d;                      // 2 d, after the elimination only
+  double* Wsm = reinterpret_cast<double*>(pend + ((mloc_max + 1) & ~1));
   // odd column stride in shared memory: a thread per column reads without
   // bank conflicts
   const int ldw = d | 1;
@@ -930,9 +932,12 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
   const int d = std::max(max_d, 1);
   auto need = [&](int c) {
     int mloc = (max_m + c - 1) / c;
-    return sizeof(double) * (4 * (size_t)d + 4 * (size_t)mloc) +
+    return sizeof(double) * (3 * (size_t)d + 4 * (size_t)mloc) +
            4 * sizeof(int) * (size_t)((mloc + 1) & ~1);
   };
+  // a large side among many items: more CTAs per item until its share of the
+  // per-column arrays fits in shared memory
+  while (C < 16 && need(C) > 227 * 1024 - 2048) C *= 2;
   size_t base = need(C);
   size_t wbytes = sizeof(double) * (size_t)((max_m + C - 1) / C) * (d | 1);
   int w_in_smem = base + wbytes <= ID_SMEM_CAP ? 1 : 0;
@@ -1107,6 +1112,12 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
     ga.abort = reinterpret_cast<int*>(ga.ctr + count);
     ga.err = ga.abort + 1;
     HSS_CUDA_TRY(cudaMemsetAsync(ga.ctr, 0, ctl_bytes, s));
+    // one spread-out launch at a time in the process: its CTAs wait for one
+    // another, so two of them sharing the GPU (two threads, two streams)
+    // could each hold SMs the other's waiting CTAs need; the lock is held
+    // until this launch has completed (the stream is synchronized below)
+    static std::mutex coop_mu;
+    std::lock_guard<std::mutex> coop_lock(coop_mu);
     cudaLaunchConfig_t gcfg = {};
     gcfg.gridDim = dim3((unsigned)(count * gsz), 1, 1);
     gcfg.blockDim = dim3(ID_THREADS, 1, 1);

@@ -22,7 +22,8 @@ using namespace hss;
 namespace hss {
 
 size_t ulv_big_min_m();
-Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaStream_t s);
+Err ulv_factor_big_multi(const std::vector<std::pair<hss_s*, int>>& items,
+                         const std::vector<int32_t*>& status, cudaStream_t s);
 Err ulv_solve_up_big(hss_s* h, const std::vector<int>& ids, const std::vector<UlvBufs>& bufs,
                      const void* B, int64_t ldb, int nr, cudaStream_t s);
 Err ulv_solve_down_big(hss_s* h, const std::vector<DownBig>& kids, const std::vector<UlvBufs>& bufs,
@@ -629,6 +630,8 @@ void factor_many(int count, hss_t* hs, cudaStream_t s, hss_status* st) {
   const int f64 = (!live.empty() && hs[live[0]]->dtype == HSS_F64) ? 1 : 0;
   for (int r = 0; r < rounds && e.st == HSS_OK; ++r) {
     std::vector<std::pair<int, int>> small;   // (handle, node)
+    std::vector<std::pair<hss_s*, int>> big;  // large nodes of every handle
+    std::vector<int32_t*> big_status;
     size_t scratch = 0;
     int maxm = 1;
     for (int q : live) {
@@ -636,22 +639,20 @@ void factor_many(int count, hss_t* hs, cudaStream_t s, hss_status* st) {
       hss_s* h = hs[q];
       const int depth = h->tree.maxdepth - r;
       if (depth < 0) continue;
-      std::vector<int> big;
       for (int id : h->tree.levels[depth]) {
         if ((size_t)h->ulv.nodes[id].m >= ulv_big_min_m()) {
-          big.push_back(id);
+          big.push_back({h, id});
+          big_status.push_back(status + q);
         } else {
           small.push_back({q, id});
           scratch += fac_scratch(h, id);
           maxm = std::max(maxm, h->ulv.nodes[id].m);
         }
       }
-      Err eb = ulv_factor_big(h, big, status + q, s);
-      if (eb.st) {
-        h->err = eb.msg;
-        st[q] = eb.st;
-      }
     }
+    // the large nodes of all handles share the blocked path's launches
+    e = ulv_factor_big_multi(big, big_status, s);
+    if (e.st) break;
     if (small.empty()) continue;
     double* sc = nullptr;
     e = dalloc_t(&sc, std::max<size_t>(scratch, 1), s);

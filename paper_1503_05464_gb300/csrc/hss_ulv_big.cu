@@ -407,24 +407,32 @@ Err run_gemms(const std::vector<GemmItem<double>>& v, cudaStream_t s, Arena& ar)
 
 size_t ulv_big_min_m() { return 320; }
 
-// Factor the large nodes `ids` of one level (all non-root, or the root alone).
-Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaStream_t s) {
-  if (ids.empty()) return ok();
-  const Tree& tr = h->tree;
-  UlvFactors& F = h->ulv;
-  const bool f64in = h->dtype == HSS_F64;
+// Factor the large nodes `items` ((handle, node) pairs of one level round of
+// any number of handles; status[q] is item q's root-LU status slot).  Roots
+// take the blocked LU one at a time, the other nodes share every launch.
+Err ulv_factor_big_multi(const std::vector<std::pair<hss_s*, int>>& items,
+                         const std::vector<int32_t*>& status, cudaStream_t s) {
+  if (items.empty()) return ok();
   Arena ar{(size_t)8 << 20};
   struct Node {
-    int id, m, k, r, kc, mc, leaf, root;
+    hss_s* h;
+    int id, m, k, r, kc, mc, leaf, root, f64in;
+    int32_t* status;
     double *Dw, *W, *Vh, *Vd, *Bd, *Y, *Y2, *G, *Tall, *Z1, *Z2;
   };
   std::vector<Node> N;
   Err e = ok();
-  for (int id : ids) {
-    const TNode& nd = tr.nodes[id];
+  for (size_t q = 0; q < items.size(); ++q) {
+    hss_s* h = items[q].first;
+    const int id = items[q].second;
+    const TNode& nd = h->tree.nodes[id];
+    UlvFactors& F = h->ulv;
     const UlvNode& u = F.nodes[id];
     const NodeGen& g = h->gen[id];
     Node x{};
+    x.h = h;
+    x.status = status[q];
+    x.f64in = h->dtype == HSS_F64;
     x.id = id;
     x.m = u.m;
     x.root = id == 0;
@@ -464,21 +472,22 @@ Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaS
     std::vector<CopyItem> cp;
     std::vector<GemmItem<double>> gm;
     for (Node& x : N) {
-      const TNode& nd = tr.nodes[x.id];
-      const NodeGen& g = h->gen[x.id];
+      const TNode& nd = x.h->tree.nodes[x.id];
+      const NodeGen& g = x.h->gen[x.id];
+      const UlvFactors& F = x.h->ulv;
       if (x.leaf) {
-        cp.push_back({g.D, x.m, f64in ? 1 : 0, x.Dw, x.m, x.m, x.m, nullptr, 0});
+        cp.push_back({g.D, x.m, x.f64in, x.Dw, x.m, x.m, x.m, nullptr, 0});
         continue;
       }
-      const UlvNode& a = F.nodes[nd.c1];
-      const UlvNode& b = F.nodes[nd.c2];
+      const UlvNode& a = x.h->ulv.nodes[nd.c1];
+      const UlvNode& b = x.h->ulv.nodes[nd.c2];
       const int k1 = a.k, k2 = b.k;
       cp.push_back({a.Dtil, k1, 1, x.Dw, x.m, k1, k1, nullptr, 0});
       cp.push_back({b.Dtil, k2, 1, x.Dw + static_cast<size_t>(k1) * x.m + k1, x.m, k2, k2, nullptr, 0});
       double* b12 = x.Bd;
       double* b21 = x.Bd + static_cast<size_t>(k1) * b.kc;
-      cp.push_back({g.B12, b.kc, f64in ? 1 : 0, b12, b.kc, k1, b.kc, nullptr, 0});
-      cp.push_back({g.B21, a.kc, f64in ? 1 : 0, b21, a.kc, k2, a.kc, nullptr, 0});
+      cp.push_back({g.B12, b.kc, x.f64in, b12, b.kc, k1, b.kc, nullptr, 0});
+      cp.push_back({g.B21, a.kc, x.f64in, b21, a.kc, k2, a.kc, nullptr, 0});
       // B12 Vtb_2^T and B21 Vtb_1^T
       gm.push_back(gemm(x.Dw + k1, x.m, k1, k2, b.kc, b12, b.kc, 0, b.Vtb, b.kc, 1, nullptr, 0, 1.0));
       gm.push_back(gemm(x.Dw + static_cast<size_t>(k1) * x.m, x.m, k2, k1, a.kc, b21, a.kc, 0,
@@ -488,13 +497,13 @@ Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaS
     HSS_TRY(run_gemms(gm, s, ar));
   }
 
-  // ---- root: blocked LU with partial pivoting
-  if (N.size() == 1 && N[0].root) {
-    Node& x = N[0];
+  // ---- roots: blocked LU with partial pivoting, one root at a time
+  for (Node& x : N) {
+    if (!x.root) continue;
     const int m = x.m;
     for (int j0 = 0; j0 < m; j0 += NB) {
       const int nbb = std::min(NB, m - j0);
-      std::vector<LuPanel> lp{{x.Dw, F.root_piv, status, m, j0, nbb}};
+      std::vector<LuPanel> lp{{x.Dw, x.h->ulv.root_piv, x.status, m, j0, nbb}};
       LuPanel* dlp = nullptr;
       HSS_TRY(upload(lp, s, ar, &dlp));
       lu_panel_kernel<<<1, B_THREADS, 0, s>>>(dlp);
@@ -510,6 +519,9 @@ Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaS
                                             a22, m, -1.0)};
       HSS_TRY(run_gemms(gm, s, ar));
     }
+  }
+  N.erase(std::remove_if(N.begin(), N.end(), [](const Node& x) { return x.root != 0; }), N.end());
+  if (N.empty()) {
     ar.release(s);
     return ok();
   }
@@ -521,7 +533,7 @@ Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaS
     std::vector<GemmItem<double>> gm;
     for (Node& x : N) {
       if (x.kc == 0) continue;
-      const NodeGen& g = h->gen[x.id];
+      const NodeGen& g = x.h->gen[x.id];
       HSS_CUDA_TRY(cudaMemsetAsync(x.Vd, 0, sizeof(double) * x.mc * x.kc, s));
       cp.push_back({g.Ec, x.kc, 1, x.Vd, x.kc, x.mc - x.kc, x.kc, g.permc + x.kc, 0});
       ey.push_back({x.Vd, x.kc, g.permc});
@@ -538,14 +550,14 @@ Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaS
     }
     for (Node& x : N) {
       if (x.kc == 0) continue;
-      const TNode& nd = tr.nodes[x.id];
+      const TNode& nd = x.h->tree.nodes[x.id];
       if (x.leaf) {
         HSS_CUDA_TRY(cudaMemcpyAsync(x.Vh, x.Vd, sizeof(double) * x.m * x.kc,
                                      cudaMemcpyDeviceToDevice, s));
         continue;
       }
-      const UlvNode& a = F.nodes[nd.c1];
-      const UlvNode& b = F.nodes[nd.c2];
+      const UlvNode& a = x.h->ulv.nodes[nd.c1];
+      const UlvNode& b = x.h->ulv.nodes[nd.c2];
       gm.push_back(gemm(x.Vh, x.kc, a.k, x.kc, a.kc, a.Vtb, a.kc, 0, x.Vd, x.kc, 0, nullptr, 0, 1.0));
       gm.push_back(gemm(x.Vh + static_cast<size_t>(a.k) * x.kc, x.kc, b.k, x.kc, b.kc, b.Vtb, b.kc,
                         0, x.Vd + static_cast<size_t>(a.kc) * x.kc, x.kc, 0, nullptr, 0, 1.0));
@@ -557,7 +569,7 @@ Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaS
   {
     std::vector<GemmItem<double>> gm;
     for (Node& x : N) {
-      const NodeGen& g = h->gen[x.id];
+      const NodeGen& g = x.h->gen[x.id];
       GemmItem<double> top = gemm(x.W, x.m, x.r, x.m, x.k, g.Er, x.k, 0, x.Dw, x.m, 0, x.Dw, x.m, -1.0);
       top.Z.map = g.permr;
       top.X.map = g.permr + x.k;
@@ -587,7 +599,7 @@ Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaS
     std::vector<GemmItem<double>> gG, gY, gY2, gW;
     for (Node& x : N) {
       if (i0 >= x.r) continue;
-      const UlvNode& u = F.nodes[x.id];
+      const UlvNode& u = x.h->ulv.nodes[x.id];
       const int nbb = std::min(NB, x.r - i0);
       lp.push_back({x.W, u.hv, u.tau, x.m, i0, nbb});
       const double* vp = u.hv + static_cast<size_t>(i0) * x.m + i0;
@@ -620,7 +632,7 @@ Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaS
   {
     std::vector<CopyItem> cp;
     for (Node& x : N) {
-      const UlvNode& u = F.nodes[x.id];
+      const UlvNode& u = x.h->ulv.nodes[x.id];
       cp.push_back({x.W, x.m, 1, u.L, x.r, x.r, x.r, nullptr, 1});
       cp.push_back({x.W + static_cast<size_t>(x.r) * x.m, x.m, 1, u.WbQt, x.r, x.k, x.r, nullptr, 0});
       cp.push_back({x.W + static_cast<size_t>(x.r) * x.m + x.r, x.m, 1, u.Dtil, x.k, x.k, x.k,
@@ -634,7 +646,7 @@ Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaS
     std::vector<GemmItem<double>> g1, g2, g3;
     for (Node& x : N) {
       if (i0 >= x.r || x.kc == 0) continue;
-      const UlvNode& u = F.nodes[x.id];
+      const UlvNode& u = x.h->ulv.nodes[x.id];
       const int nbb = std::min(NB, x.r - i0);
       const double* vp = u.hv + static_cast<size_t>(i0) * x.m + i0;
       const double* T = x.Tall + static_cast<size_t>(i0 / NB) * NB * NB;
@@ -651,7 +663,7 @@ Err ulv_factor_big(hss_s* h, const std::vector<int>& ids, int32_t* status, cudaS
     std::vector<CopyItem> cp;
     for (Node& x : N) {
       if (x.kc == 0) continue;
-      const UlvNode& u = F.nodes[x.id];
+      const UlvNode& u = x.h->ulv.nodes[x.id];
       cp.push_back({x.Vh, x.kc, 1, u.Vtt, x.kc, x.r, x.kc, nullptr, 0});
       cp.push_back({x.Vh + static_cast<size_t>(x.r) * x.kc, x.kc, 1, u.Vtb, x.kc, x.k, x.kc, nullptr, 0});
     }

@@ -114,8 +114,10 @@ class ServeStats:
 
 
 class Server:
-    def __init__(self, make_matrix, opts, budget_bytes, stream=None, keep_handles=False):
+    def __init__(self, make_matrix, opts, budget_bytes, stream=None, keep_handles=False,
+                 lane_split_n=None):
         self.make_matrix = make_matrix          # k -> device template matrix
+        self.lane_split_n = lane_split_n        # order from which requests get their own lane
         self.opts = opts
         self.budget = budget_bytes
         self.stream = stream
@@ -134,55 +136,101 @@ class Server:
         for r in pending:                     # generate inputs before the clock starts
             self._template(r.k)
         torch.cuda.synchronize()
-        batch = H.HssBatch(torch.float32, self.stream)
-        inflight = {}
         lock = threading.Lock()
-        acct = {"used": 0}
-        finished = queue.Queue()              # compressed requests for the solve thread
+        acct = {"used": 0, "inflight": 0}
+        finished = queue.Queue()              # compressed requests for the factor thread
         errors = []
         t0 = time.perf_counter()
 
         def now():
             return time.perf_counter() - t0
 
+        # lanes: requests of order >= lane_split_n compress in a batch of their
+        # own, stepped by its own thread on its own stream, so that the small
+        # requests' rounds do not wait for a large request's level work
+        nlanes = 2 if self.lane_split_n else 1
+        lane_q = [queue.Queue() for _ in range(nlanes)]
+        admitting = threading.Event()
+        admitting.set()
         due = []                              # heap of (time, seq, request, nrhs)
         factor_done = threading.Event()
+        lanes_done = [threading.Event() for _ in range(nlanes)]
+        lanes = [threading.Thread(target=self._lane_thread,
+                                  args=(q, lane_q[q], finished, st, lock, acct, now, errors,
+                                        admitting, lanes_done[q]), daemon=True)
+                 for q in range(nlanes)]
         workers = [threading.Thread(target=self._factor_thread,
                                     args=(finished, due, lock, acct, now, errors, factor_done),
                                     daemon=True),
                    threading.Thread(target=self._solve_thread,
                                     args=(due, st, lock, acct, now, errors, factor_done),
                                     daemon=True)]
-        for w in workers:
+        for w in lanes + workers:
             w.start()
         try:
-            while pending or inflight:
+            while pending:
+                if errors:
+                    raise errors[0]
                 t = now()
                 # admission: arrived requests whose estimate fits the budget
                 while pending and pending[0].arrival <= t:
                     r = pending[0]
                     need = estimate_bytes(r.n, self.opts)
                     with lock:
-                        if acct["used"] + need > self.budget and (inflight or acct["used"] > 0):
+                        if acct["used"] + need > self.budget and (acct["inflight"] or acct["used"] > 0):
                             break
                         acct["used"] += need
+                        acct["inflight"] += 1
                         st.peak_reserved = max(st.peak_reserved, acct["used"])
+                        st.max_inflight = max(st.max_inflight, acct["inflight"])
                     pending.pop(0)
                     r.A = self._template(r.k) * r.scale
+                    torch.cuda.current_stream().synchronize()   # r.A ready for any lane's stream
                     r.reserved = need
                     r.t_admit = now()
+                    lane = 1 if self.lane_split_n and r.n >= self.lane_split_n else 0
+                    lane_q[lane].put(r)
+                wait = (pending[0].arrival - now()) if pending else 0.0
+                time.sleep(max(0.0, min(wait, 0.002)))
+        finally:
+            admitting.clear()                 # no more requests for the lanes
+            for q in lane_q:
+                q.put(None)
+            for w in lanes:
+                w.join()
+            finished.put(None)                # no more compressions
+            for w in workers:
+                w.join()
+        if errors:
+            raise errors[0]
+        st.wall_s = now()
+        return st
+
+    def _lane_thread(self, lane, inbox, finished, st, lock, acct, now, errors, admitting, done):
+        """Compresses the requests of one lane in one incremental batch on
+        its own stream: submits what the admission sent, runs one round of
+        every compression in flight, hands finished ones on."""
+        stream = self.stream if lane == 0 and self.stream is not None else torch.cuda.Stream()
+        batch = H.HssBatch(torch.float32, stream)
+        inflight = {}
+        closing = False
+        try:
+            while True:
+                while True:
+                    try:
+                        r = inbox.get(timeout=0.002) if not inflight and not closing else \
+                            inbox.get_nowait()
+                    except queue.Empty:
+                        break
+                    if r is None:
+                        closing = True
+                        break
                     r.ticket = batch.submit(r.A, self.opts)
                     inflight[r.ticket] = r
-                st.max_inflight = max(st.max_inflight, len(inflight))
-                if errors:
-                    raise errors[0]
                 if not inflight:
-                    if pending:
-                        wait = pending[0].arrival - now()
-                        if wait > 0:
-                            time.sleep(min(wait, 0.002))
+                    if closing:
+                        return
                     continue
-                # one round of every compression in flight
                 batch.step()
                 for ticket in list(inflight):
                     h, status = batch.take(ticket)
@@ -195,16 +243,14 @@ class Server:
                     r.t_compressed = now()
                     st.compress_latency.append(r.t_compressed - r.arrival)
                     r.A = None                # the input is no longer needed
+                    with lock:
+                        acct["inflight"] -= 1
                     finished.put(r)
+        except Exception as e:                # reported by the admitting thread
+            errors.append(e)
         finally:
-            finished.put(None)                # no more compressions
-            for w in workers:
-                w.join()
             batch.close()
-        if errors:
-            raise errors[0]
-        st.wall_s = now()
-        return st
+            done.set()
 
     def _factor_thread(self, finished, due, lock, acct, now, errors, factor_done):
         """Factors the finished compressions on its own stream, all those

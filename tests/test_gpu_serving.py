@@ -20,14 +20,19 @@ def P():
     return pkg
 
 
-def test_served_results_equal_alone_and_solve(P):
+@pytest.mark.parametrize("lane_split_n", [None, 900])
+def test_served_results_equal_alone_and_solve(P, lane_split_n):
+    """One lane, or two (requests of order >= 900 in a batch, stream and
+    thread of their own): each served result equals the same matrix
+    compressed alone."""
     from paper_1503_05464_gb300 import serving as S
     opts = P.hss_default_opts(leaf_size=64, rtol=1e-6, d0=64, d_step=32, seed=5,
                               sample_mode="bf16x3")
     reqs = S.poisson_requests(10, rate=200.0, ks=[20, 30, 40], seed=3, max_solves=2,
                               nrhs_range=(1, 8))
     make = lambda k: W.laplacian_schur(k, dtype=np.float32, device=DEV)
-    srv = S.Server(make, opts, budget_bytes=int(2e9), keep_handles=True)
+    srv = S.Server(make, opts, budget_bytes=int(2e9), keep_handles=True,
+                   lane_split_n=lane_split_n)
     st = srv.run(reqs)
     summ = st.summary()
     assert summ["requests"] == 10 and summ["solves"] == sum(len(r.solves) for r in reqs)
