@@ -84,7 +84,7 @@ GOLDEN_BEM60K = os.path.join(ROOT, "tests", "golden", "bem60k_oracle.json")
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) per FP64 flop of the ID kernel over a whole bem32k
 # compression, from profiles/id_cpqr_dram_bem32k.md
-ID_DRAM_BYTES_PER_FLOP = 0.437
+ID_DRAM_BYTES_PER_FLOP = 0.442
 FP32_SIMT_PEAK_TFLOPS = 69.7
 
 
