@@ -54,7 +54,7 @@ typedef enum { HSS_F32 = 0, HSS_F64 = 1 } hss_dtype;
  * split modes only split A.  For HSS_F64 inputs only NATIVE is accepted. */
 typedef enum {
   HSS_SAMPLE_NATIVE = 0, /* FP32 (or FP64) fused multiply-add, no tensor cores  */
-  HSS_SAMPLE_TF32 = 1,   /* A rounded to TF32, tensor cores, FP32 accumulation */
+  HSS_SAMPLE_TF32 = 1,   /* A rounded to TF32 (nearest), tensor cores, FP32 acc. */
   HSS_SAMPLE_BF16X2 = 2, /* A = hi + lo (two bfloat16 terms), FP32 accumulation */
   HSS_SAMPLE_BF16X3 = 3  /* A = hi + mid + lo (three bfloat16 terms)            */
 } hss_sample_mode;

@@ -27,9 +27,10 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 // Partial sums of both products.  Within the limits above the CUDA-core
 // kernels need at most 16 MiB (16 panels x 2048 x 64 FP64 values) and the
 // tensor-core kernel at most 35.2 MiB (its bfloat16 copy of R plus column and
-// row slabs; largest at n = 1983 with 125 clusters of two CTAs), so 36 MiB
-// holds every accepted call.  The need of each call is still checked before
-// any work is queued.
+// row slabs; largest at n = 1984 with 125 clusters of two CTAs; 35.9 MiB in
+// TF32, whose copy of R is a transposed FP32 one), so 36 MiB holds every
+// call on a GPU of up to 252 SMs.  The need of each call is still checked before any
+// work is queued.
 constexpr size_t NOALLOC_PART_BYTES = (size_t)36 << 20;
 
 static __device__ __align__(256) unsigned char g_noalloc_part[NOALLOC_PART_BYTES];

@@ -214,7 +214,7 @@ Err launch_sample_mma(const float* A, int64_t n, int64_t lda, const float* R, in
                       const int32_t* leaf_of, int mode, float* P, cudaStream_t s);
 
 bool sample_tc_supported(const float* A, int64_t n, int64_t lda, int mode);
-Err sample_tc_need(int64_t n, int64_t ncols, size_t* need);
+Err sample_tc_need(int64_t n, int64_t ncols, int mode, size_t* need);
 Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int64_t ldr,
                      int64_t c0, int64_t ncols, float* Sr, float* Sc, int64_t lds,
                      const int32_t* leaf_of, int mode, SampleScratch* scratch, cudaStream_t s);
@@ -240,7 +240,7 @@ Err sample_scratch_need(const void* A, int64_t n, int64_t lda, int64_t ncols, in
   if (n <= 0 || ncols <= 0) return ok();
   if (!f64 && !legacy_mma_requested() &&
       sample_tc_supported(reinterpret_cast<const float*>(A), n, lda, mode))
-    return sample_tc_need(n, ncols, need);
+    return sample_tc_need(n, ncols, mode, need);
   *need = sample_scratch_bytes(n, ncols, mode, f64);
   return ok();
 }
@@ -252,8 +252,9 @@ Err launch_sample(const T* A, int64_t n, int64_t lda, const T* R, int64_t ldr, i
   int64_t ncols = c1 - c0;
   if (n <= 0 || ncols <= 0) return ok();
   const bool f64 = sizeof(T) == 8;
-  // split-bfloat16 modes run on tcgen05 when A's layout suits TMA (16-byte
-  // aligned rows); HSS_SAMPLE_KERNEL=mma selects the warp-level mma.sync kernel
+  // the TF32 and split-bfloat16 modes run on tcgen05 when A's layout suits
+  // TMA (16-byte aligned rows); HSS_SAMPLE_KERNEL=mma selects the warp-level
+  // mma.sync kernel
   const bool tc = !f64 && !legacy_mma_requested() &&
                   sample_tc_supported(reinterpret_cast<const float*>(A), n, lda, mode);
   size_t need = tc ? 0 : sample_scratch_bytes(n, ncols, mode, f64);

@@ -1,5 +1,5 @@
 // Fused sampling on the 5th-generation tensor cores (tcgen05 + TMA + TMEM)
-// for FP32 inputs in the split-bfloat16 modes:
+// for FP32 inputs in the split-bfloat16 modes and in TF32:
 //   Sr[:, c] = (A - D) R[:, c]  and  Sc[:, c] = (A - D)^T R[:, c]
 // (Section 2.2, step 2; Algorithm 1's leaf samples: D = the leaf diagonal
 // blocks), each tile of A read from HBM once for both products.
@@ -12,10 +12,19 @@
 // p.  For a tile (panel p, columns J):
 //   row product     Sr_p    += A_pJ  R_J      M = 128 rows, N = c, K = 64
 //   column product  Sc_J^T   = R_p^T A_pJ     M = c (<= 128), N = 64, K = 128
-// with A_pJ = hi + mid (+ lo) bfloat16 planes.  Both products read the same
-// shared-memory planes: K-major for the row product, MN-major (transposed)
-// for the column product.  R is bfloat16-exact (its Gaussian entries are
-// rounded to bfloat16 when drawn), so it needs no split.
+// with A_pJ = hi + mid (+ lo) bfloat16 planes (kind::f16).  Both products
+// read the same shared-memory planes: K-major for the row product, MN-major
+// (transposed) for the column product.  R is bfloat16-exact (its Gaussian
+// entries are rounded to bfloat16 when drawn), so it needs no split.
+//
+// TF32 (kind::tf32, template parameter NT = 1; NT = 2 or 3 is the number of
+// bfloat16 planes) reads every shared-memory operand K-major: the row
+// product is taken transposed, Sr_p^T += R_J^T A_pJ^T (M = c, N = 128 panel
+// rows, K = 64), with R_J^T from a transposed copy of R and A_pJ straight
+// from the TMA stage (rounded to TF32 in place); the column product reads a
+// transposed copy of the tile (N = 64, K = 128 panel rows) that the
+// converters write.  R_p^T goes to TMEM from the transposed copy of R in
+// global memory (no shared-memory stage).
 //
 // Pipeline (warp-specialised, mbarrier hand-offs, 576 threads):
 //   warp 0       TMA producer: FP32 half-tiles of A (128 x 32, 128-byte
@@ -23,8 +32,9 @@
 //                R_p (128 rows) per panel segment, bfloat16;
 //   warps 2-9    converters: two threads per row, one per half-tile; apply
 //                the leaf mask (the index range of the row's leaf), split into
-//                the bfloat16 planes (double-buffered, swizzled operand
-//                layout); two warps per scheduler keep the ALUs fed;
+//                the bfloat16 planes or round to TF32 (double-buffered,
+//                swizzled operand layout); two warps per scheduler keep the
+//                ALUs fed;
 //   warp 1       MMA issuer (one thread): tcgen05.mma into TMEM;
 //   warps 10-13  column drain: the column product of each tile (TMEM, three
 //                buffers) is summed over the panel pair through distributed
@@ -42,7 +52,8 @@
 //                the fold reads the previous chain.
 // TMEM columns: [0,128) the row accumulator, [128,256) the running row sum,
 // [256,448) three column accumulators, [448,512) R_p^T, the column
-// product's A operand (the drain
+// product's A operand (TF32: two column accumulators in [256,384) and R_p^T,
+// one element per column, in [384,512)) (the drain
 // warps copy it from shared memory at the start of each panel segment, so
 // the tensor core reads only the planes from shared memory for that
 // product).  When the panel count is odd the last pair's second panel
@@ -52,7 +63,7 @@
 // Numerics: the tensor core's FP32 accumulation runs over at most 24 MMAs
 // (one tile of the column product, one chain of two tiles of the row
 // product; callers with a loose tolerance may ask for chains of up to 16
-// tiles); the chains of a flush group are added in FP32 by the fold warps,
+// tiles, and TF32, whose rounding of A is far larger, always takes them); the chains of a flush group are added in FP32 by the fold warps,
 // and the slabs are summed in the reduce kernel with compensated FP32
 // (Neumaier) summation in a fixed order, so the result is deterministic and
 // independent of what else runs on the GPU.
@@ -78,12 +89,18 @@ constexpr int BM = 128;          // panel rows
 constexpr int BN = 64;           // column tile of A
 constexpr int CMAX = 128;        // sample columns per sweep
 // FP32 half-tile stages: an even number (stage s serves converter group
-// s % 2); two with three bfloat16 planes (shared memory is full), four with two
+// s % 2); two with three bfloat16 planes (shared memory is full), four with
+// two, four in TF32 (a tile's two stages are the row product's operand until
+// its MMAs complete)
 constexpr int ASTAGES_MAX = 4;
 template <int NT>
 constexpr int astages() { return NT == 3 ? 2 : 4; }
+template <int NT>
+constexpr bool is_tf32() { return NT == 1; }
 constexpr int KC = 2;            // CTAs per cluster: panels 2g and 2g+1 reduce their column products
-constexpr int CBUF = 3;          // column accumulators in TMEM
+constexpr int CBUF = 3;          // column accumulators in TMEM (barrier slots)
+template <int NT>
+constexpr int cbuf() { return is_tf32<NT>() ? 2 : CBUF; }
 constexpr int FLUSH_MAX = 16;    // tiles per flush group of the running row sum, at most
 // The row product accumulates in the tensor core over chains of g.chain
 // tiles (2 by default: 24 MMAs with three planes, as many as the column
@@ -96,7 +113,8 @@ constexpr long long WAIT_LIMIT = 1ll << 32;   // clock cycles (about 2 s)
 
 constexpr uint32_t A_HALF_BYTES = BM * 32 * 4;   // 16 KB
 constexpr uint32_t PLANE_BYTES = BM * BN * 2;    // 16 KB
-constexpr uint32_t RJ_BYTES = BN * CMAX * 2;     // 16 KB (two 8 KB boxes)
+constexpr uint32_t RJ_BOX = 8192;                // one box of R_J: 64 rows x 128 bytes
+constexpr uint32_t RJ_BYTES = BN * CMAX * 2;     // 16 KB (two boxes)
 constexpr uint32_t RI_BYTES = BM * CMAX * 2;     // 32 KB (two 16 KB boxes)
 constexpr uint32_t X_BYTES = CMAX * (BN / KC) * 4;   // 16 KB: the partner's half of a column product
 constexpr int XSLOTS = 2;                             // exchange buffers (double buffered)
@@ -104,19 +122,31 @@ constexpr int XSLOTS = 2;                             // exchange buffers (doubl
 // row sum (fold warps only), three column accumulators, and R_p^T (the column
 // product's A operand: lane = sample column, 64 columns of bfloat16 pairs
 // along the panel rows)
-constexpr uint32_t T_ROW = 0, T_RSUM = 128, T_COL = 256, T_RP = 448;
+constexpr uint32_t T_ROW = 0, T_RSUM = 128, T_COL = 256;
+template <int NT>
+constexpr uint32_t t_rp() { return is_tf32<NT>() ? 384 : 448; }
 
 template <int NT>
 struct Layout {
+  // one stage of planes: NT bfloat16 planes, or (TF32) the transposed tile:
+  // four 8 KB chunks of 32 panel rows, each 64 tile columns x 128 bytes
+  static constexpr uint32_t pstage = is_tf32<NT>() ? 2 * PLANE_BYTES : NT * PLANE_BYTES;
+  // one stage of R_J: up to 128 columns of bfloat16 (two boxes), or (TF32)
+  // R_J^T: two 16 KB halves of 32 tile columns x 128 sample columns
+  static constexpr uint32_t rjstage = is_tf32<NT>() ? 2 * RJ_BYTES : RJ_BYTES;
   static constexpr uint32_t a = 0;
   static constexpr uint32_t planes = a + astages<NT>() * A_HALF_BYTES;
-  static constexpr uint32_t rj = planes + 2 * NT * PLANE_BYTES;
-  static constexpr uint32_t ri = rj + 2 * RJ_BYTES;
-  static constexpr uint32_t xb = ri + RI_BYTES;
+  static constexpr uint32_t rj = planes + 2 * pstage;
+  static constexpr uint32_t ri = rj + 2 * rjstage;
+  static constexpr uint32_t xb = ri + (is_tf32<NT>() ? 0 : RI_BYTES);
   static constexpr uint32_t bars = xb + XSLOTS * X_BYTES;
   static constexpr uint32_t total = bars + 512;
   static constexpr uint32_t alloc = total + 1024;   // room to align the base to 1 KB
 };
+
+static_assert(Layout<3>::alloc <= 232448 && Layout<2>::alloc <= 232448 &&
+                  Layout<1>::alloc <= 232448,
+              "a layout exceeds the shared memory of one CTA");
 
 // barrier slots
 enum {
@@ -131,7 +161,9 @@ enum {
 struct TcArgs {
   int n;          // matrix order
   int c;          // sample columns of this sweep (1..128)
-  int ncb;        // 64-column boxes of R per row (1 or 2)
+  int ncb;        // 64-column boxes of R per row (1 or 2; bfloat16 modes)
+  const float* rt;   // TF32: R^T, 128 rows (sample columns) x ldrt, zero-padded
+  int ldrt;          // TF32: row pitch of rt (2 ngp 128 elements)
   int nr;         // N of the row product (c rounded up to 16)
   int ntc;        // column tiles per panel
   int npanel;
@@ -165,6 +197,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                      const __grid_constant__ CUtensorMap tmRI, const TcArgs g) {
   using L = Layout<NT>;
   constexpr int AS = astages<NT>();
+  constexpr int CB = cbuf<NT>();
+  constexpr uint32_t T_RP = t_rp<NT>();
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) &
                                            ~static_cast<uintptr_t>(1023));
@@ -182,7 +216,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (tid == 0) {
     for (int i = 0; i < AS; ++i) {
       mbar_init(bar(B_AFULL + i), 1);
-      mbar_init(bar(B_AEMPTY + i), BM);
+      // released by the converters' reads, or (TF32) by the row product's MMAs
+      mbar_init(bar(B_AEMPTY + i), is_tf32<NT>() ? 1 : BM);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(bar(B_PFULL + i), 2 * BM);
@@ -237,7 +272,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (long long t = tb; t < te; ++t) {
         const int p = KC * static_cast<int>(t / ntc) + crank, J = static_cast<int>(t % ntc);
         const bool first = (t == tb) || J == 0;
-        if (first) {
+        if (!is_tf32<NT>() && first) {
           // the previous segment's R_p has been copied to TMEM
           if (!mbar_wait(bar(B_RSEMPTY), (ri_cnt & 1) ^ 1, abort_flag, g.err, 1, WAIT_LIMIT))
             break;
@@ -260,10 +295,18 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (!ok) break;
         const int r = tl & 1, u = tl >> 1;
         if (!mbar_wait(bar(B_RJEMPTY + r), (u & 1) ^ 1, abort_flag, g.err, 3, WAIT_LIMIT)) break;
-        mbar_expect_tx(bar(B_RJFULL + r), g.ncb * (RJ_BYTES / 2));
-        for (int cb = 0; cb < g.ncb; ++cb)
-          tma_load_2d(su32(sm + L::rj + r * RJ_BYTES + cb * (RJ_BYTES / 2)), &tmRJ, cb * 64,
-                      J * BN, bar(B_RJFULL + r));
+        if constexpr (is_tf32<NT>()) {
+          // R_J^T: tile columns J 64 + 32 h .. + 31 of the 128 rows of R^T
+          mbar_expect_tx(bar(B_RJFULL + r), 2 * A_HALF_BYTES);
+          for (int h = 0; h < 2; ++h)
+            tma_load_2d(su32(sm + L::rj + r * L::rjstage + h * A_HALF_BYTES), &tmRJ,
+                        J * BN + h * 32, 0, bar(B_RJFULL + r));
+        } else {
+          mbar_expect_tx(bar(B_RJFULL + r), g.ncb * RJ_BOX);
+          for (int cb = 0; cb < g.ncb; ++cb)
+            tma_load_2d(su32(sm + L::rj + r * RJ_BYTES + cb * RJ_BOX), &tmRJ, cb * 64, J * BN,
+                        bar(B_RJFULL + r));
+        }
         ++tl;
       }
       if (*abort_flag) {
@@ -283,13 +326,22 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      const uint32_t idr = idesc_bf16(BM, g.nr, 0, 1);    // planes K-major, R_J MN-major
-      const uint32_t idc = idesc_bf16(BM, BN, 0, 1);      // R_p^T from TMEM, planes MN-major
+      // bfloat16: the planes K-major and R_J MN-major (row product), R_p^T
+      // from TMEM and the planes MN-major (column product).  TF32: R_J^T and
+      // the A stages, both K-major (the transposed row product, M = sample
+      // columns, N = panel rows), and R_p^T from TMEM with the transposed
+      // tile K-major (column product).
+      const uint32_t idr = is_tf32<NT>() ? idesc_tf32(BM, BM, 0, 0) : idesc_bf16(BM, g.nr, 0, 1);
+      const uint32_t idc = is_tf32<NT>() ? idesc_tf32(BM, BN, 0, 0) : idesc_bf16(BM, BN, 0, 1);
       // descriptors of stage 0; other stages and K steps add (offset >> 4)
-      // to the start-address field
-      const uint64_t a_row = sdesc(su32(sm + L::planes), 16, 1024);        // plane, K-major
-      const uint64_t b_col = sdesc(su32(sm + L::planes), 8192, 1024);      // plane, MN-major
-      const uint64_t b_row = sdesc(su32(sm + L::rj), RJ_BYTES / 2, 1024);  // R_J, MN-major
+      // to the start-address field.  MN-major blocks of 128 bytes along N
+      // are 8 KB apart (a bfloat16 plane holds one, R_J one per box)
+      const uint64_t a_row = sdesc(su32(sm + L::planes), 16, 1024);   // plane, K-major
+      const uint64_t b_col = is_tf32<NT>() ? sdesc(su32(sm + L::planes), 16, 1024)   // K-major
+                                           : sdesc(su32(sm + L::planes), 8192, 1024);   // MN-major
+      const uint64_t b_row = is_tf32<NT>() ? sdesc(su32(sm + L::rj), 16, 1024)   // R_J^T, K-major
+                                           : sdesc(su32(sm + L::rj), RJ_BOX, 1024);   // R_J, MN-major
+      const uint64_t a_stg = sdesc(su32(sm + L::a), 16, 1024);   // TF32: A stages, K-major
       int tl = 0, seg = 0, ch = 0, since = 0;
       for (long long t = tb; t < te; ++t) {
         const int J = static_cast<int>(t % ntc);
@@ -298,36 +350,62 @@ __global__ void __launch_bounds__(THREADS, 1)
         const bool cend = gend || ((J % gs) % chain) == chain - 1;
         if (first && !mbar_wait(bar(B_RTFULL), seg & 1, abort_flag, g.err, 4, WAIT_LIMIT)) break;
         const int ps = tl & 1, u = tl >> 1;
-        const int cb = tl % CBUF, cu = tl / CBUF;
+        const int cb = tl % CB, cu = tl / CB;
         if (!mbar_wait(bar(B_PFULL + ps), u & 1, abort_flag, g.err, 5, WAIT_LIMIT)) break;
         if (!mbar_wait(bar(B_RJFULL + ps), u & 1, abort_flag, g.err, 6, WAIT_LIMIT)) break;
         if (!mbar_wait(bar(B_CEMPTY + cb), (cu & 1) ^ 1, abort_flag, g.err, 7, WAIT_LIMIT)) break;
         fence_after();
-        const uint64_t poff = (ps * NT * PLANE_BYTES) >> 4;
-        const uint64_t roff = (ps * RJ_BYTES) >> 4;
+        const uint64_t poff = (ps * L::pstage) >> 4;
+        const uint64_t roff = (ps * L::rjstage) >> 4;
         // the column product first: it keeps the tensor core busy while the
         // fold warps read the previous chain's row accumulator
         const uint32_t dc = tbase + T_COL + 64 * cb;
+        if constexpr (is_tf32<NT>()) {
+          // K = 8 panel rows per MMA: eight TMEM columns of R_p^T, 32 bytes
+          // along the rows of one 8 KB chunk of the transposed tile
 #pragma unroll
-        for (int term = 0; term < NT; ++term) {
+          for (int k = 0; k < BM / 8; ++k)
+            mma_tf32_tmem_a(dc, tbase + T_RP + 8 * k,
+                            b_col + poff + (((k >> 2) * 8192 + 32 * (k & 3)) >> 4), idc,
+                            k > 0 ? 1u : 0u);
+        } else {
 #pragma unroll
-          for (int k = 0; k < BM / 16; ++k)
-            mma_bf16_tmem_a(dc, tbase + T_RP + 8 * k,
-                            b_col + poff + ((term * PLANE_BYTES + 2048 * k) >> 4), idc,
-                            (term > 0 || k > 0) ? 1u : 0u);
+          for (int term = 0; term < NT; ++term) {
+#pragma unroll
+            for (int k = 0; k < BM / 16; ++k)
+              mma_bf16_tmem_a(dc, tbase + T_RP + 8 * k,
+                              b_col + poff + ((term * PLANE_BYTES + 2048 * k) >> 4), idc,
+                              (term > 0 || k > 0) ? 1u : 0u);
+          }
         }
         if (since == 0) {
           if (!mbar_wait(bar(B_REMPTY), (ch & 1) ^ 1, abort_flag, g.err, 8, WAIT_LIMIT)) break;
           fence_after();
         }
         const uint32_t dr = tbase + T_ROW;
+        if constexpr (is_tf32<NT>()) {
+          // K = 8 columns of the tile per MMA: 32 bytes along the rows of
+          // one half of R_J^T and of the tile's A stage of that half (the
+          // tile's two stages are adjacent: four stages, two per tile)
+          const uint64_t aoff = (((2 * tl) % AS) * A_HALF_BYTES) >> 4;
 #pragma unroll
-        for (int term = 0; term < NT; ++term) {
+          for (int k = 0; k < BN / 8; ++k) {
+            const uint32_t koff = (k >> 2) * A_HALF_BYTES + 32 * (k & 3);
+            mma_tf32(dr, b_row + roff + (koff >> 4), a_stg + aoff + (koff >> 4), idr,
+                     (since > 0 || k > 0) ? 1u : 0u);
+          }
+          // the tile's A stages go back to the producer when these MMAs are done
+          mma_commit(bar(B_AEMPTY + (2 * tl) % AS));
+          mma_commit(bar(B_AEMPTY + (2 * tl) % AS + 1));
+        } else {
 #pragma unroll
-          for (int k = 0; k < BN / 16; ++k)
-            mma_bf16(dr, a_row + poff + ((term * PLANE_BYTES + 32 * k) >> 4),
-                     b_row + roff + ((2048 * k) >> 4), idr,
-                     (since > 0 || term > 0 || k > 0) ? 1u : 0u);
+          for (int term = 0; term < NT; ++term) {
+#pragma unroll
+            for (int k = 0; k < BN / 16; ++k)
+              mma_bf16(dr, a_row + poff + ((term * PLANE_BYTES + 32 * k) >> 4),
+                       b_row + roff + ((2048 * k) >> 4), idr,
+                       (since > 0 || term > 0 || k > 0) ? 1u : 0u);
+          }
         }
         mma_commit(bar(B_PEMPTY + ps));
         mma_commit(bar(B_RJEMPTY + ps));
@@ -371,7 +449,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int j0 = J * BN;
       const int jb = j0 + h * 32;
       const bool need_mask = mlo < jb + 32 && mhi > jb;
-      uint8_t* pbase = sm + L::planes + ps * NT * PLANE_BYTES;
+      uint8_t* pbase = sm + L::planes + ps * L::pstage;
       const int a_idx = 2 * tl + h;
       const int s = a_idx % AS, ua = a_idx / AS;
       if (!mbar_wait(bar(B_AFULL + s), ua & 1, abort_flag, g.err, 12, WAIT_LIMIT)) break;
@@ -388,9 +466,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       // the stage goes back to the producer as soon as it is read: the fence
       // orders these shared-memory reads before the next TMA copy into the
       // stage, which the arrival releases (without it a late read could return
-      // the next copy's data)
-      fence_proxy_async();
-      mbar_arrive(bar(B_AEMPTY + s));
+      // the next copy's data).  In TF32 the stage is an operand of the row
+      // product and the MMAs release it.
+      if constexpr (!is_tf32<NT>()) {
+        fence_proxy_async();
+        mbar_arrive(bar(B_AEMPTY + s));
+      }
       // the plane buffer of this tile: free once the MMAs two tiles back are done
       if (!mbar_wait(bar(B_PEMPTY + ps), (u & 1) ^ 1, abort_flag, g.err, 11, WAIT_LIMIT)) break;
       if (need_mask) {
@@ -400,31 +481,51 @@ __global__ void __launch_bounds__(THREADS, 1)
           if (j >= mlo && j < mhi) v[e] = 0.f;
         }
       }
+      if constexpr (is_tf32<NT>()) {
+        // the half-tile rounded to TF32, in place (the row product's operand:
+        // rows = panel rows, K = tile columns), and transposed into the
+        // plane buffer: entry (row, j) at chunk row / 32, row j, bytes
+        // 4 (row % 32) (a warp's 32 rows fill one 128-byte row: no bank
+        // conflict)
 #pragma unroll
-      for (int qd = 0; qd < 4; ++qd) {
-        uint32_t hw[4], mw[4], lw[4];
+        for (int e = 0; e < 32; ++e) v[e] = to_tf32(v[e]);
+        uint8_t* stage = sm + L::a + s * A_HALF_BYTES;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float x0 = v[8 * qd + 2 * e], x1 = v[8 * qd + 2 * e + 1];
-          const __nv_bfloat162 hv = __floats2bfloat162_rn(x0, x1);
-          const float2 hf = __bfloat1622float2(hv);
-          const float r0 = x0 - hf.x, r1 = x1 - hf.y;
-          const __nv_bfloat162 mv = __floats2bfloat162_rn(r0, r1);
-          hw[e] = *reinterpret_cast<const uint32_t*>(&hv);
-          mw[e] = *reinterpret_cast<const uint32_t*>(&mv);
-          if (NT == 3) {
-            const float2 mf = __bfloat1622float2(mv);
-            const __nv_bfloat162 lv = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
-            lw[e] = *reinterpret_cast<const uint32_t*>(&lv);
+        for (int qd = 0; qd < 8; ++qd)
+          *reinterpret_cast<float4*>(stage + sw128(row, qd * 16)) =
+              make_float4(v[4 * qd], v[4 * qd + 1], v[4 * qd + 2], v[4 * qd + 3]);
+        uint8_t* chunk = pbase + (row >> 5) * 8192;
+        const uint32_t rb = static_cast<uint32_t>(row & 31) * 4;
+#pragma unroll
+        for (int e = 0; e < 32; ++e)
+          *reinterpret_cast<float*>(chunk + sw128(32 * h + e, rb)) = v[e];
+      } else {
+#pragma unroll
+        for (int qd = 0; qd < 4; ++qd) {
+          uint32_t hw[4], mw[4], lw[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float x0 = v[8 * qd + 2 * e], x1 = v[8 * qd + 2 * e + 1];
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(x0, x1);
+            const float2 hf = __bfloat1622float2(hv);
+            const float r0 = x0 - hf.x, r1 = x1 - hf.y;
+            const __nv_bfloat162 mv = __floats2bfloat162_rn(r0, r1);
+            hw[e] = *reinterpret_cast<const uint32_t*>(&hv);
+            mw[e] = *reinterpret_cast<const uint32_t*>(&mv);
+            if (NT == 3) {
+              const float2 mf = __bfloat1622float2(mv);
+              const __nv_bfloat162 lv = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+              lw[e] = *reinterpret_cast<const uint32_t*>(&lv);
+            }
           }
+          const uint32_t off = sw128(row, h * 64 + qd * 16);
+          *reinterpret_cast<uint4*>(pbase + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(pbase + PLANE_BYTES + off) =
+              make_uint4(mw[0], mw[1], mw[2], mw[3]);
+          if (NT == 3)
+            *reinterpret_cast<uint4*>(pbase + 2 * PLANE_BYTES + off) =
+                make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
-        const uint32_t off = sw128(row, h * 64 + qd * 16);
-        *reinterpret_cast<uint4*>(pbase + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4*>(pbase + PLANE_BYTES + off) =
-            make_uint4(mw[0], mw[1], mw[2], mw[3]);
-        if (NT == 3)
-          *reinterpret_cast<uint4*>(pbase + 2 * PLANE_BYTES + off) =
-              make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
       // the plane writes, before the tensor core's reads that the arrival releases
       fence_proxy_async();
@@ -453,7 +554,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int nt = static_cast<int>(te - tb);
     int rseg = 0;
     for (int i = 0; i < nt; ++i) {
-      const int cb = i % CBUF, cu = i / CBUF;
+      const int cb = i % CB, cu = i / CB;
       const int xs = i % XSLOTS, xu = i / XSLOTS;
       const int J = static_cast<int>((tb + i) % ntc);
       if (i == 0 || J == 0) {
@@ -462,14 +563,36 @@ __global__ void __launch_bounds__(THREADS, 1)
         // once the previous segment's MMAs are done with TMEM
         if (elect) {
           const bool ok =
-              mbar_wait(bar(B_RIFULL), rseg & 1, abort_flag, g.err, 19, WAIT_LIMIT) &&
+              (is_tf32<NT>() ||
+               mbar_wait(bar(B_RIFULL), rseg & 1, abort_flag, g.err, 19, WAIT_LIMIT)) &&
               mbar_wait(bar(B_RIEMPTY), (rseg & 1) ^ 1, abort_flag, g.err, 20, WAIT_LIMIT);
           dstop[2] = ok ? 0 : 1;
         }
         named_sync(1, 128);
         if (dstop[2]) break;
         fence_after();
-        {
+        if constexpr (is_tf32<NT>()) {
+          // lane e: R^T[e][p 128 + r] for the 128 panel rows r, one per
+          // column, from global memory (R^T is zero-padded to 2 ngp 128
+          // columns, so the rows of a pair's phantom last panel exist)
+          const int p = KC * static_cast<int>((tb + i) / ntc) + crank;
+          const float4* src = reinterpret_cast<const float4*>(
+              g.rt + static_cast<size_t>(e) * g.ldrt + static_cast<size_t>(p) * BM);
+#pragma unroll
+          for (int q4 = 0; q4 < 4; ++q4) {
+            float wv[32];
+#pragma unroll
+            for (int x4 = 0; x4 < 8; ++x4) {
+              const float4 f = __ldg(src + q4 * 8 + x4);
+              wv[4 * x4] = f.x;
+              wv[4 * x4 + 1] = f.y;
+              wv[4 * x4 + 2] = f.z;
+              wv[4 * x4 + 3] = f.w;
+            }
+            tmem_st32(tbase + loff + T_RP + 32 * q4, wv);
+          }
+          tmem_wait_st();
+        } else {
           // lane e: R_p[r][e] for the 128 panel rows r, two per 32-bit column
           const uint8_t* rbox = sm + L::ri + (e >> 6) * (RI_BYTES / 2);
           const uint32_t eb = static_cast<uint32_t>(e & 63) * 2;
@@ -536,7 +659,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int e = (warp & 3) * 32 + lane;       // TMEM lane: sample column / panel row
     const uint32_t loff = static_cast<uint32_t>((warp & 3) * 32) << 16;
     const int c = g.c;
-    const int nch = (c + 31) / 32;
+    // 32-column chunks of the row accumulator: sample columns, or (TF32,
+    // the transposed row product: lane = sample column) panel rows
+    const int nch = is_tf32<NT>() ? BM / 32 : (c + 31) / 32;
     const bool elect = warp == 14 && lane == 0;
     constexpr int HB = BN / KC;
     const uint32_t own = static_cast<uint32_t>(crank * HB);
@@ -552,7 +677,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const bool cend = gend || ((J % gs) % chain) == chain - 1;
       if (jfirst < 0) jfirst = J;
       // ---- tile i's column sums
-      const int cb = i % CBUF, cu = i / CBUF;
+      const int cb = i % CB, cu = i / CB;
       const int xs = i % XSLOTS, xu = i / XSLOTS;
       if (elect) {
         // this CTA's column product of the tile is in TMEM (the buffer cannot
@@ -649,10 +774,21 @@ __global__ void __launch_bounds__(THREADS, 1)
           float a[32];
           tmem_ld32(tbase + loff + T_RSUM + 32 * q, a);
           tmem_wait_ld();
+          if constexpr (is_tf32<NT>()) {
+            // lane e holds sample column e of panel rows 32 q .. 32 q + 31
+            if (e < c) {
+              float* d = dst - e + static_cast<size_t>(e) * BM + 32 * q;
 #pragma unroll
-          for (int x = 0; x < 32; ++x) {
-            const int cc = 32 * q + x;
-            if (cc < c) dst[static_cast<size_t>(cc) * BM] = a[x];
+              for (int x4 = 0; x4 < 8; ++x4)
+                *reinterpret_cast<float4*>(d + 4 * x4) =
+                    make_float4(a[4 * x4], a[4 * x4 + 1], a[4 * x4 + 2], a[4 * x4 + 3]);
+            }
+          } else {
+#pragma unroll
+            for (int x = 0; x < 32; ++x) {
+              const int cc = 32 * q + x;
+              if (cc < c) dst[static_cast<size_t>(cc) * BM] = a[x];
+            }
           }
         }
       }
@@ -774,6 +910,17 @@ __global__ void r_to_bf16_kernel(const float* __restrict__ R, long long ldr, int
   R16[idx] = __float2bfloat16_rn(cc < c ? R[static_cast<size_t>(i) * ldr + cc] : 0.f);
 }
 
+// TF32: Rt[cc, i] = R[i, c0 + cc] for cc < c and i < n, zero elsewhere in
+// the CMAX x ldrt array (R^T, the operand of the transposed row product and
+// the source of R_p^T)
+__global__ void r_transpose_kernel(const float* __restrict__ R, long long ldr, int n, int c,
+                                   int ldrt, float* Rt) {
+  const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= static_cast<long long>(CMAX) * ldrt) return;
+  const int cc = static_cast<int>(idx / ldrt), i = static_cast<int>(idx % ldrt);
+  Rt[idx] = (cc < c && i < n) ? R[static_cast<size_t>(i) * ldr + cc] : 0.f;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -806,7 +953,7 @@ Err make_map(CUtensorMap* m, CUtensorMapDataType dt, const void* base, uint64_t 
 struct DevInfo {
   int sms = 0;
   int clusters = 0;   // clusters of KC CTAs that fit at once
-  bool attr3 = false, attr2 = false;
+  bool attr3 = false, attr2 = false, attr1 = false;
 };
 
 DevInfo& dev_info(int dev) {
@@ -842,11 +989,19 @@ TcPlan plan(int64_t n, int clusters) {
 
 }  // namespace
 
-size_t sample_tc_scratch_bytes(int64_t n, int64_t ncols, int clusters) {
+// bytes of the copy of R a sweep uses: bfloat16 (n x cpad), or for TF32
+// R^T (CMAX rows of 2 ngp 128 FP32 entries)
+static size_t rcopy_bytes(int64_t n, int64_t cpad, const TcPlan& pl, int mode) {
+  if (mode == HSS_SAMPLE_TF32)
+    return align256(static_cast<size_t>(CMAX) * (2 * static_cast<size_t>(pl.ngp) * BM) * 4);
+  return align256(static_cast<size_t>(n) * cpad * 2);
+}
+
+size_t sample_tc_scratch_bytes(int64_t n, int64_t ncols, int clusters, int mode) {
   const TcPlan pl = plan(n, clusters);
   const int64_t c = ncols < CMAX ? ncols : CMAX;
   const int64_t cpad = (c + 63) / 64 * 64;
-  return align256(static_cast<size_t>(n) * cpad * 2) +
+  return rcopy_bytes(n, cpad, pl, mode) +
          align256(static_cast<size_t>(pl.ngp) * c * pl.ntc * BN * 4) +
          align256(static_cast<size_t>(pl.npanel) * pl.ngroups * 2 * c * BM * 4) +
          2 * align256(static_cast<size_t>(n) * 4) +
@@ -854,7 +1009,8 @@ size_t sample_tc_scratch_bytes(int64_t n, int64_t ncols, int clusters) {
 }
 
 bool sample_tc_supported(const float* A, int64_t n, int64_t lda, int mode) {
-  return (mode == HSS_SAMPLE_BF16X2 || mode == HSS_SAMPLE_BF16X3) && n >= 1 &&
+  return (mode == HSS_SAMPLE_TF32 || mode == HSS_SAMPLE_BF16X2 || mode == HSS_SAMPLE_BF16X3) &&
+         n >= 1 &&
          n <= (int64_t)1 << 30 && lda % 4 == 0 &&
          (reinterpret_cast<uintptr_t>(A) & 15) == 0;
 }
@@ -874,8 +1030,15 @@ static Err query_clusters(DevInfo& di, const cudaLaunchConfig_t& cfg) {
                                       (int)Layout<2>::alloc));
     di.attr2 = true;
   }
+  if (!di.attr1) {
+    HSS_CUDA_TRY(cudaFuncSetAttribute(sample_tc_kernel<1>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)Layout<1>::alloc));
+    di.attr1 = true;
+  }
   if (di.clusters == 0) {
-    // the larger (three-plane) layout decides how many clusters fit at once
+    // the three-plane layout decides how many clusters fit at once (every
+    // layout runs one CTA per SM)
     cudaLaunchConfig_t q = cfg;
     q.gridDim = dim3(static_cast<unsigned>(di.sms / KC * KC), 1, 1);
     q.dynamicSmemBytes = Layout<3>::alloc;
@@ -901,14 +1064,14 @@ static cudaLaunchConfig_t base_config(cudaLaunchAttribute* attr) {
   return cfg;
 }
 
-Err sample_tc_need(int64_t n, int64_t ncols, size_t* need) {
+Err sample_tc_need(int64_t n, int64_t ncols, int mode, size_t* need) {
   int dev = 0;
   HSS_CUDA_TRY(cudaGetDevice(&dev));
   DevInfo& di = dev_info(dev);
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = base_config(attr);
   HSS_TRY(query_clusters(di, cfg));
-  *need = sample_tc_scratch_bytes(n, ncols, di.clusters);
+  *need = sample_tc_scratch_bytes(n, ncols, di.clusters, mode);
   return ok();
 }
 
@@ -918,15 +1081,15 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
   int dev = 0;
   HSS_CUDA_TRY(cudaGetDevice(&dev));
   DevInfo& di = dev_info(dev);
-  const bool three = mode == HSS_SAMPLE_BF16X3;
-  const uint32_t smem = three ? Layout<3>::alloc : Layout<2>::alloc;
+  const bool three = mode == HSS_SAMPLE_BF16X3, tf32 = mode == HSS_SAMPLE_TF32;
+  const uint32_t smem = three ? Layout<3>::alloc : tf32 ? Layout<1>::alloc : Layout<2>::alloc;
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = base_config(attr);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   HSS_TRY(query_clusters(di, cfg));
   const TcPlan pl = plan(n, di.clusters);
-  const size_t need = sample_tc_scratch_bytes(n, ncols, di.clusters);
+  const size_t need = sample_tc_scratch_bytes(n, ncols, di.clusters, mode);
   if (scratch->bytes < need && scratch->fixed)
     return fail(HSS_ERR_INVALID,
                 "sample_tc: the fixed scratch is smaller than this call needs");
@@ -946,7 +1109,9 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     const int cpad = (c + 63) / 64 * 64;
     uint8_t* base = static_cast<uint8_t*>(scratch->part);
     __nv_bfloat16* R16 = reinterpret_cast<__nv_bfloat16*>(base);
-    base += align256(static_cast<size_t>(n) * cpad * 2);
+    float* Rt = reinterpret_cast<float*>(base);
+    const int ldrt = 2 * pl.ngp * BM;
+    base += rcopy_bytes(n, cpad, pl, mode);
     float* scp = reinterpret_cast<float*>(base);
     base += align256(static_cast<size_t>(pl.ngp) * c * pl.ntc * BN * 4);
     float* srp = reinterpret_cast<float*>(base);
@@ -964,19 +1129,31 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
       HSS_TRY(check_launch("leaf_bounds_kernel"));
     }
 
-    const long long nconv = static_cast<long long>(n) * cpad;
-    r_to_bf16_kernel<<<static_cast<unsigned>((nconv + 255) / 256), 256, 0, s>>>(
-        R + c0 + done, ldr, static_cast<int>(n), c, cpad, R16);
-    HSS_TRY(check_launch("r_to_bf16_kernel"));
-
     CUtensorMap tmA, tmRJ, tmRI;
     HSS_TRY(make_map(&tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, n, n, lda * 4, 32, BM));
-    HSS_TRY(make_map(&tmRJ, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, R16, cpad, n, cpad * 2, 64, BN));
-    HSS_TRY(make_map(&tmRI, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, R16, cpad, n, cpad * 2, 64, BM));
+    if (tf32) {
+      const long long nt = static_cast<long long>(CMAX) * ldrt;
+      r_transpose_kernel<<<static_cast<unsigned>((nt + 255) / 256), 256, 0, s>>>(
+          R + c0 + done, ldr, static_cast<int>(n), c, ldrt, Rt);
+      HSS_TRY(check_launch("r_transpose_kernel"));
+      // R_J^T boxes: 32 entries of each of the CMAX rows (128 bytes, swizzled)
+      HSS_TRY(make_map(&tmRJ, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Rt, ldrt, CMAX, ldrt * 4, 32,
+                       CMAX));
+      tmRI = tmRJ;   // R_p^T comes from global memory
+    } else {
+      const long long nconv = static_cast<long long>(n) * cpad;
+      r_to_bf16_kernel<<<static_cast<unsigned>((nconv + 255) / 256), 256, 0, s>>>(
+          R + c0 + done, ldr, static_cast<int>(n), c, cpad, R16);
+      HSS_TRY(check_launch("r_to_bf16_kernel"));
+      HSS_TRY(make_map(&tmRJ, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, R16, cpad, n, cpad * 2, 64, BN));
+      HSS_TRY(make_map(&tmRI, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, R16, cpad, n, cpad * 2, 64, BM));
+    }
     TcArgs g;
     g.n = static_cast<int>(n);
     g.c = c;
     g.ncb = cpad / 64;
+    g.rt = tf32 ? Rt : nullptr;
+    g.ldrt = ldrt;
     g.nr = (c + 15) / 16 * 16;
     g.ntc = pl.ntc;
     g.npanel = pl.npanel;
@@ -984,7 +1161,9 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     g.T = pl.T;
     g.Q = pl.Q;
     g.gs = pl.gs;
-    g.chain = std::max(1, std::min(scratch->row_chain, pl.gs));
+    // TF32's rounding of A (2^-11) is far above the accumulation error of
+    // the longest chain, so it always takes whole flush groups
+    g.chain = tf32 ? pl.gs : std::max(1, std::min(scratch->row_chain, pl.gs));
     g.ngroups = pl.ngroups;
     g.leaf_of = leaf_of;
     g.leaf_lo = leaf_lo;
@@ -994,8 +1173,9 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     g.sr_part = srp;
     g.err = err;
     HSS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-    cudaError_t le = three ? cudaLaunchKernelEx(&cfg, sample_tc_kernel<3>, tmA, tmRJ, tmRI, g)
-                           : cudaLaunchKernelEx(&cfg, sample_tc_kernel<2>, tmA, tmRJ, tmRI, g);
+    cudaError_t le = three  ? cudaLaunchKernelEx(&cfg, sample_tc_kernel<3>, tmA, tmRJ, tmRI, g)
+                     : tf32 ? cudaLaunchKernelEx(&cfg, sample_tc_kernel<1>, tmA, tmRJ, tmRI, g)
+                            : cudaLaunchKernelEx(&cfg, sample_tc_kernel<2>, tmA, tmRJ, tmRI, g);
     if (le != cudaSuccess) {
       cudaGetLastError();
       return fail(HSS_ERR_CUDA, std::string("sample_tc_kernel launch: ") + cudaGetErrorString(le));

@@ -203,6 +203,31 @@ __device__ __forceinline__ void mma_bf16_tmem_a(uint32_t d, uint32_t a_tmem, uin
       "%3, p; }" ::"r"(d),
       "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
 }
+// D[tmem] (+)= A[smem] * B[smem], TF32 operands (32-bit containers), FP32
+// accumulation; K = 8 per instruction
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, "
+      "%3, p; }" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+// the same with A read from tensor memory: row m of A is TMEM lane m, column
+// k holds element k
+__device__ __forceinline__ void mma_tf32_tmem_a(uint32_t d, uint32_t a_tmem, uint64_t b,
+                                                uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, "
+      "%3, p; }" ::"r"(d),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
+}
+// FP32 -> TF32, round to nearest (ties away from zero); the low 13 bits of
+// the result are zero
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
 // arrive once on `bar` when every tcgen05 operation issued so far by this
 // thread has completed
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -212,7 +237,7 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 }
 
 // Matrix descriptor of a 128-byte swizzled operand at shared address `saddr`:
-// `lbo` = byte distance between 64-element blocks along M/N (MN-major), `sbo`
+// `lbo` = byte distance between 128-byte blocks along M/N (MN-major), `sbo`
 // = byte distance between 8-row groups (1024 for packed atoms).
 __host__ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
@@ -230,6 +255,20 @@ __host__ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N, int a_mn, 
   d |= 1u << 4;    // D: F32
   d |= 1u << 7;    // A: BF16
   d |= 1u << 10;   // B: BF16
+  d |= static_cast<uint32_t>(a_mn) << 15;
+  d |= static_cast<uint32_t>(b_mn) << 16;
+  d |= static_cast<uint32_t>(N >> 3) << 17;
+  d |= static_cast<uint32_t>(M >> 4) << 24;
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: TF32 A and B, FP32 D (the same fields
+// as kind::f16 with the TF32 operand format)
+__host__ __device__ __forceinline__ uint32_t idesc_tf32(int M, int N, int a_mn, int b_mn) {
+  uint32_t d = 0;
+  d |= 1u << 4;    // D: F32
+  d |= 2u << 7;    // A: TF32
+  d |= 2u << 10;   // B: TF32
   d |= static_cast<uint32_t>(a_mn) << 15;
   d |= static_cast<uint32_t>(b_mn) << 16;
   d |= static_cast<uint32_t>(N >> 3) << 17;

@@ -181,7 +181,7 @@ def test_tensor_core_sampling_accuracy_on_schur_complement(P):
     assert er <= 6e-7 and ec <= 6e-7, (er, ec)
 
 
-@pytest.mark.parametrize("mode", ["bf16x2", "bf16x3"])
+@pytest.mark.parametrize("mode", ["tf32", "bf16x2", "bf16x3"])
 def test_tensor_core_sampling_repeats_identically(P, mode):
     # many CTAs, a ragged tail and a masked leaf diagonal: every repeat must
     # give the same bits (a hand-off race in the staging pipeline shows up as
@@ -420,6 +420,39 @@ def test_compress_gaussian_kernel_fp32_reduced(P, mode):
     _ranks_close(P, h, ho)
     H = _dense_from_gpu(P, h, n, torch.float32)
     assert _rel(H, A32) <= _err_bound(A32, ho, rtol)
+    P.hss_factor(h)
+    b = np.random.default_rng(4).standard_normal((n, 8))
+    xs = P.hss_solve(h, torch.tensor(b, dtype=torch.float32, device=DEV)).cpu().numpy()
+    O.ulv_factor(ho)
+    xo = O.ulv_solve(ho, b)
+    assert _rel(A32 @ xs, b) <= 10 * max(_rel(A32 @ xo, b), 1e-6)
+
+
+def test_compress_gaussian_kernel_tf32(P):
+    """TF32 sampling (A rounded to TF32, 2^-11, on kind::tf32) at rtol 1e-4,
+    the tolerance class where it converges: the samples' rounding adds
+    rank, never removes it (every node's rank at least the oracle's - 2,
+    the largest within twice the oracle's), the reconstruction stays within
+    the oracle's bound plus one TF32 rounding unit, and the ULV solve
+    within 10x the oracle's residual."""
+    n, leaf, rtol = 4000, 256, 1e-4
+    pts = W.points_unit_cube(n, 1002)
+    pts = pts[W.rcb_order(pts, leaf)]
+    At = W.gaussian_kernel(pts, 0.2, 1.0, dtype=np.float32, device=DEV)
+    A32 = At.cpu().numpy().astype(np.float64)
+    h = P.hss_compress(At, leaf_size=leaf, rtol=rtol, d0=128, d_step=64, seed=1003,
+                       sample_mode="tf32")
+    ho = O.compress(A32, rtol, leaf_size=leaf, d0=128, d_step=64, seed=1003)
+    ranks = P.hss_node_ranks(h)
+    ro = ho.ranks()
+    for i, (lo, hi, kr, kc) in enumerate(ranks[1:], start=1):
+        assert (lo, hi) == (ho.nodes[i].lo, ho.nodes[i].hi)
+        assert kr >= ro[i][0] - 2 and kc >= ro[i][1] - 2, (i, kr, kc, ro[i])
+    mx = max(max(kr, kc) for (_, _, kr, kc) in ranks[1:])
+    mo = max(max(a, b) for (a, b) in ro[1:])
+    assert mx <= 2 * mo, (mx, mo)
+    H = _dense_from_gpu(P, h, n, torch.float32)
+    assert _rel(H, A32) <= _err_bound(A32, ho, rtol) + 2.0 ** -11
     P.hss_factor(h)
     b = np.random.default_rng(4).standard_normal((n, 8))
     xs = P.hss_solve(h, torch.tensor(b, dtype=torch.float32, device=DEV)).cpu().numpy()
