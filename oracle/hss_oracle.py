@@ -34,6 +34,9 @@ Readings taken where the paper is silent:
   samples with all d columns and retries the ID.
 * Root: no ID; B12/B21 are gathered and the ULV root is LU with partial
   pivoting.
+* Symmetric matrices (optional): with A = A^T and one R for both samples,
+  S^c = A^T R = A R = S^r, so every column-side quantity repeats the row
+  side: the column ID is the row ID (V = U, I^c = I^r) and R^c_tau = R^r_tau.
 
 Pins for every function here live in tests/test_oracle.py.
 """
@@ -255,10 +258,13 @@ class RankCapError(RuntimeError):
 
 
 def compress(A, rtol, atol=0.0, leaf_size=128, d0=64, d_step=32, d_max=None,
-             oversample_p=10, seed=0, tree=None) -> HSS:
+             oversample_p=10, seed=0, tree=None, symmetric=False) -> HSS:
     """Randomized HSS compression, Algorithm 1 with Algorithm 5's adaptivity.
 
     A is upcast to FP64 as given (the stored values are the matrix).
+    symmetric=True takes A = A^T (not checked): S^c is S^r (Section 2.2's
+    samples with one R), the column side of every node is its row side
+    (idc is idr, Sc/Rc/Ic are Sr/Rr/Ir); B12 and B21 are still read from A.
     """
     A = np.asarray(A, dtype=np.float64)
     n = A.shape[0]
@@ -271,7 +277,7 @@ def compress(A, rtol, atol=0.0, leaf_size=128, d0=64, d_step=32, d_max=None,
     d = min(d0, d_max)
     R = gaussian_bf16(seed, n, 0, d)
     Sr = A @ R
-    Sc = A.T @ R
+    Sc = Sr if symmetric else A.T @ R
     maxdepth = max(nd.depth for nd in nodes)
     passes = 0
     for nd in nodes:
@@ -282,7 +288,8 @@ def compress(A, rtol, atol=0.0, leaf_size=128, d0=64, d_step=32, d_max=None,
         for depth in range(maxdepth, 0, -1):
             for nd in nodes:
                 if nd.depth == depth:
-                    _process_node(A, R, Sr, Sc, nodes, data, nd, d, rtol, atol, oversample_p)
+                    _process_node(A, R, Sr, Sc, nodes, data, nd, d, rtol, atol, oversample_p,
+                                  symmetric)
         root = nodes[0]
         if root.is_leaf or all(data[c].state == COMPRESSED for c in root.children):
             if not root.is_leaf:
@@ -297,7 +304,7 @@ def compress(A, rtol, atol=0.0, leaf_size=128, d0=64, d_step=32, d_max=None,
         Rn = gaussian_bf16(seed, n, d, dn)
         R = np.hstack([R, Rn])
         Sr = np.hstack([Sr, A @ Rn])
-        Sc = np.hstack([Sc, A.T @ Rn])
+        Sc = Sr if symmetric else np.hstack([Sc, A.T @ Rn])
         d = dn
     return HSS(n, nodes, data, d, passes, rtol)
 
@@ -327,8 +334,9 @@ def _fails(k, d, m, p):
     return d < m and k > d - p
 
 
-def _process_node(A, R, Sr, Sc, nodes, data, nd, d, rtol, atol, p):
-    """Process one node in one pass (Algorithm 5 in level-synchronous form)."""
+def _process_node(A, R, Sr, Sc, nodes, data, nd, d, rtol, atol, p, symmetric=False):
+    """Process one node in one pass (Algorithm 5 in level-synchronous form).
+    symmetric: the column side is the row side (see compress)."""
     me = data[nd.id]
     if not nd.is_leaf and any(data[c].state != COMPRESSED for c in nd.children):
         me.state = UNTOUCHED
@@ -343,9 +351,12 @@ def _process_node(A, R, Sr, Sc, nodes, data, nd, d, rtol, atol, p):
         cols = slice(me.ncols, d)
         srl, scl, rin_r, rin_c = _local_samples(A, R, Sr, Sc, nodes, data, nd, cols)
         me.Sr = np.hstack([me.Sr, srl[me.idr.J]])
-        me.Sc = np.hstack([me.Sc, scl[me.idc.J]])
         me.Rr = np.hstack([me.Rr, me.V.T @ rin_r])
-        me.Rc = np.hstack([me.Rc, me.U.T @ rin_c])
+        if symmetric:
+            me.Sc, me.Rc = me.Sr, me.Rr
+        else:
+            me.Sc = np.hstack([me.Sc, scl[me.idc.J]])
+            me.Rc = np.hstack([me.Rc, me.U.T @ rin_c])
         me.ncols = d
         return
     cols = slice(0, d)
@@ -355,22 +366,31 @@ def _process_node(A, R, Sr, Sc, nodes, data, nd, d, rtol, atol, p):
     if _fails(idr.k, d, m, p):
         me.state = PARTIALLY
         return
-    idc = interpolative_decomposition(scl.T, rtol, atol)
-    if _fails(idc.k, d, scl.shape[0], p):
-        me.state = PARTIALLY
-        return
+    if symmetric:
+        idc = idr
+    else:
+        idc = interpolative_decomposition(scl.T, rtol, atol)
+        if _fails(idc.k, d, scl.shape[0], p):
+            me.state = PARTIALLY
+            return
     me.idr, me.idc = idr, idc
     me.Sr = srl[idr.J]
-    me.Sc = scl[idc.J]
     me.Rr = me.V.T @ rin_r
-    me.Rc = me.U.T @ rin_c
     if nd.is_leaf:
         idx = np.arange(nd.lo, nd.hi)
-        me.Ir, me.Ic = idx[idr.J], idx[idc.J]
+        me.Ir = idx[idr.J]
     else:
         c1, c2 = (data[c] for c in nd.children)
         me.Ir = np.concatenate([c1.Ir, c2.Ir])[idr.J]
-        me.Ic = np.concatenate([c1.Ic, c2.Ic])[idc.J]
+    if symmetric:
+        me.Sc, me.Rc, me.Ic = me.Sr, me.Rr, me.Ir
+    else:
+        me.Sc = scl[idc.J]
+        me.Rc = me.U.T @ rin_c
+        if nd.is_leaf:
+            me.Ic = np.arange(nd.lo, nd.hi)[idc.J]
+        else:
+            me.Ic = np.concatenate([c1.Ic, c2.Ic])[idc.J]
     me.ncols = d
     me.d_compressed = d
     me.state = COMPRESSED

@@ -404,3 +404,47 @@ def test_comb_tree_compression_invariants():
         sv = np.linalg.svd(A[nd.lo:nd.hi][:, rest], compute_uv=False)
         kr = h.data[nd.id].idr.k
         assert kr >= int(np.sum(sv > 1e-7 * sv[0]))
+
+
+def test_symmetric_compression_repeats_the_row_side():
+    """symmetric=True on a symmetric matrix (Gaussian kernel, with adaptive
+    restarts): the column side is the row side (same ID, V = U, I^c = I^r),
+    so the reconstruction is symmetric to rounding; the ranks, passes and
+    error match the general compression of the same matrix, whose column
+    samples A^T R equal A R in exact arithmetic (Section 2.2 with one R)."""
+    n, leaf, rtol = 800, 50, 1e-6
+    pts = W.points_unit_cube(n, 7)
+    pts = pts[W.rcb_order(pts, leaf)]
+    A = W.gaussian_kernel(pts, 0.2, 1.0, dtype=np.float64).numpy()
+    assert np.array_equal(A, A.T)
+    g = O.compress(A, rtol, leaf_size=leaf, d0=16, d_step=16, seed=3)
+    sy = O.compress(A, rtol, leaf_size=leaf, d0=16, d_step=16, seed=3, symmetric=True)
+    assert sy.passes > 1 and abs(sy.passes - g.passes) <= 1
+    for nd in sy.nodes[1:]:
+        me = sy.data[nd.id]
+        assert me.idc is me.idr and np.array_equal(me.Ic, me.Ir)
+        kr, kc = g.ranks()[nd.id]
+        assert abs(me.idr.k - kr) <= 1 and abs(me.idr.k - kc) <= 1
+    H = O.to_dense(sy)
+    assert np.linalg.norm(H - H.T) <= 1e-13 * np.linalg.norm(H)
+    e_gen = np.linalg.norm(O.to_dense(g) - A) / np.linalg.norm(A)
+    e_sym = np.linalg.norm(H - A) / np.linalg.norm(A)
+    assert e_sym <= 2 * max(rtol, e_gen)
+
+
+def test_symmetric_flag_on_an_unsymmetric_matrix_misses_it():
+    """The flag is a promise, not a check: on a matrix whose off-diagonal
+    blocks have column spaces unlike their row spaces (T + X Y^T, X and Y
+    independent), the symmetric path's V = U cannot hold the row spaces and
+    the compression misses A, while the general path meets its tolerance."""
+    n, leaf = 400, 50
+    rng = np.random.default_rng(8)
+    i = np.arange(n)
+    A = 1.0 / (1.0 + np.abs(i[:, None] - i[None, :]))
+    K = rng.standard_normal((n, 6)) @ rng.standard_normal((6, n))
+    A = A + K / np.linalg.norm(K) * np.linalg.norm(A)
+    sy = O.compress(A, 1e-8, leaf_size=leaf, d0=32, d_step=16, seed=2, symmetric=True)
+    g = O.compress(A, 1e-8, leaf_size=leaf, d0=32, d_step=16, seed=2)
+    nA = np.linalg.norm(A)
+    assert np.linalg.norm(O.to_dense(g) - A) <= 1e-6 * nA
+    assert np.linalg.norm(O.to_dense(sy) - A) >= 0.1 * nA
