@@ -183,8 +183,9 @@ def run_ours(args, wl):
 
     A = make_matrix(wl, dev).contiguous()
     torch.cuda.synchronize()
-    opts = P.hss_default_opts(leaf_size=wl["leaf"], rtol=wl["rtol"], d0=wl["d0"],
-                              d_step=wl["step"], seed=wl["seed"] + 1, sample_mode=args.mode)
+    okw = dict(leaf_size=wl["leaf"], rtol=wl["rtol"], d0=wl["d0"], d_step=wl["step"],
+               seed=wl["seed"] + 1, sample_mode=args.mode)
+    opts = P.hss_default_opts(symmetric=args.symmetric, **okw)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -248,7 +249,13 @@ def run_ours(args, wl):
             "note": "e_oracle exceeds 2 rtol: the paper's ID stopping test is local "
                     "and relative, the oracle itself ends at this error"})
     h_chk.close()
-    del AG, HG, G
+    del HG
+    sym_extra = None
+    if not args.no_extras and not args.symmetric:
+        # the symmetric form of the same compression (every single-matrix
+        # workload here is symmetric to the bit): one ID per node, V = U
+        sym_extra = run_symmetric(P, A, okw, stream, max(1, min(args.steps, 3)), G, AG, gold)
+    del AG, G
 
     # end to end through the public API from pinned host memory
     A_host = A.cpu().pin_memory()
@@ -331,6 +338,7 @@ def run_ours(args, wl):
         "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "leaf": wl["leaf"], "rtol": wl["rtol"],
                    "d0": wl["d0"], "d_step": wl["step"], "sample_mode": args.mode,
+                   "symmetric": bool(args.symmetric),
                    "family": wl["family"], "l2": "input larger than L2 (no flush needed)"},
         "roofline": roof,
         "phases": phases,
@@ -349,6 +357,8 @@ def run_ours(args, wl):
     clocks = clk.summary()
     if clocks:
         out["clocks"] = clocks
+    if sym_extra is not None:
+        out["symmetric"] = sym_extra
     if not args.no_extras:
         # the batched and served forms, each beside the plain one-at-a-time method
         out["batching"] = run_batching(P, dev, stream, count=64, seed=WORKLOADS["batch512"]["seed"])
@@ -362,6 +372,47 @@ def run_ours(args, wl):
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_symmetric(P, A, okw, stream, steps, G, AG, gold):
+    """The symmetric compression (hss_opts.symmetric) of the same matrix:
+    seconds per compression (CUDA events, one warm-up), its ID time and
+    flops, and its accuracy with the main line's probes (and, with a golden,
+    its ranks against the general oracle's)."""
+    import torch
+    o = P.hss_default_opts(symmetric=True, **okw)
+    P.hss_compress(A, o, stream=stream).close()
+    torch.cuda.synchronize()
+    infos = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        h = P.hss_compress(A, o, stream=stream)
+        infos.append(P.hss_info(h))
+        h.close()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    h = P.hss_compress(A, o, stream=stream)
+    HG = P.hss_matvec(h, G.to(A.dtype)).double()
+    err = float(torch.linalg.norm(AG - HG) / torch.linalg.norm(AG))
+    info = P.hss_info(h)
+    res = {"value": e0.elapsed_time(e1) / 1e3 / steps, "unit": "s", "steps": steps,
+           "id_ms": statistics.mean(i["ms_id"] for i in infos),
+           "sampling_ms": statistics.mean(i["ms_sample"] for i in infos),
+           "flops_id": info["flops_id"], "passes": info["passes"], "d_final": info["d_final"],
+           "max_rank": max(info["max_rank_r"], info["max_rank_c"]), "probe_rel_err": err,
+           "bytes_hss": info["bytes_hss"]}
+    if gold is not None:
+        ranks = P.hss_node_ranks(h)
+        diffs = [max(abs(kr - nd["kr"]), abs(kc - nd["kc"]))
+                 for (lo, hi, kr, kc), nd in zip(ranks[1:], gold["nodes"][1:])]
+        res.update({"e_oracle_general": gold["probe_rel_err"],
+                    "bound": 2 * max(okw["rtol"], gold["probe_rel_err"]),
+                    "ranks_within_2_of_general_oracle_frac": sum(x <= 2 for x in diffs) / len(diffs),
+                    "max_rank_diff_vs_general_oracle": max(diffs)})
+    h.close()
+    return res
 
 
 def _event_time(stream, fn):
@@ -557,11 +608,13 @@ def load_golden(workload, A=None):
 _SAMPLE_CACHE = {}
 
 
-def bounded_oracle_sample(workload, wl):
+def bounded_oracle_sample(workload, wl, symmetric=False):
     """(seconds of one oracle compression of the bounded sample, scale to the
     full workload, description) -- bem60k: the same family, leaf, tolerance
     and schedule at n = 12000, scaled by the full/sample time ratio measured
-    with the golden; other workloads: one full compression (scale 1)."""
+    with the golden; other workloads: one full compression (scale 1).
+    symmetric: the oracle's symmetric compression (the scale stays the
+    general compression's ratio)."""
     from oracle import hss_oracle as O
     gold = load_golden(workload)
     if gold is not None:
@@ -573,7 +626,7 @@ def bounded_oracle_sample(workload, wl):
         A64 = _SAMPLE_CACHE[key]
         t0 = time.perf_counter()
         O.compress(A64, wl["rtol"], leaf_size=wl["leaf"], d0=wl["d0"], d_step=wl["step"],
-                   seed=wl["seed"] + 1)
+                   seed=wl["seed"] + 1, symmetric=symmetric)
         t = time.perf_counter() - t0
         ratio = gold["oracle_s"] / gold["sample_s"]
         host = gold["host"]
@@ -585,9 +638,10 @@ def bounded_oracle_sample(workload, wl):
     A64 = make_matrix(wl, "cpu").numpy().astype(np.float64)
     t0 = time.perf_counter()
     O.compress(A64, wl["rtol"], leaf_size=wl["leaf"], d0=wl["d0"], d_step=wl["step"],
-               seed=wl["seed"] + 1)
+               seed=wl["seed"] + 1, symmetric=symmetric)
     t = time.perf_counter() - t0
-    return t, 1.0, f"one full FP64 oracle compression of {wl['family']} n={wl['n']}"
+    return t, 1.0, (f"one full FP64 oracle {'symmetric ' if symmetric else ''}compression of "
+                    f"{wl['family']} n={wl['n']}")
 
 
 def cpu_baseline(workload, wl, A):
@@ -642,7 +696,7 @@ def run_reference(args, wl):
     times = []
     ratio, desc = 1.0, ""
     for i in range(args.warmup + args.steps):
-        t, ratio, desc = bounded_oracle_sample(args.workload, wl)
+        t, ratio, desc = bounded_oracle_sample(args.workload, wl, args.symmetric)
         if i >= args.warmup:
             times.append(t * ratio)
     v = sum(times) / len(times)
@@ -652,7 +706,8 @@ def run_reference(args, wl):
            "impl": "reference",
            "config": {"workload": args.workload, "n": wl["n"], "leaf": wl["leaf"],
                       "rtol": wl["rtol"], "d0": wl["d0"], "d_step": wl["step"],
-                      "sample_mode": "f64 (oracle)", "family": wl["family"]},
+                      "sample_mode": "f64 (oracle)", "symmetric": bool(args.symmetric),
+                      "family": wl["family"]},
            "cpu_baseline": {"value": v, "unit": "s", "cores": _threads(), "kind": "oracle",
                             "sample": desc + " (per step)"},
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -669,6 +724,8 @@ def main():
                     help="sampling arithmetic (default: bf16x3 for FP32 inputs, native for FP64)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--symmetric", action="store_true",
+                    help="compress with hss_opts.symmetric (A = A^T): one ID per node, V = U")
     ap.add_argument("--no-extras", action="store_true",
                     help="leave the batching and serving objects out of the default line")
     ap.add_argument("--requests", type=int, default=None,

@@ -81,6 +81,11 @@ typedef struct {
    * INVALID if a split is out of range or the count does not match. */
   const int64_t* tree;
   int32_t tree_nodes;
+  /* 1: the caller guarantees A = A^T (not checked).  One R serves both
+   * samples (Section 2.2), so S^c = A^T R = S^r: the column side of every
+   * node repeats its row side -- one ID per node instead of two, V = U,
+   * I^c = I^r; B12 and B21 are still read from A.  0: general A. */
+  int32_t symmetric;
 } hss_opts;
 
 /* Statistics of a handle (Table 3's columns: max rank, factor sizes, time). */

@@ -124,6 +124,7 @@ hss_status hss_default_opts(hss_opts* o) {
   o->seed = 0;
   o->tree = nullptr;
   o->tree_nodes = 0;
+  o->symmetric = 0;
   return HSS_OK;
 }
 

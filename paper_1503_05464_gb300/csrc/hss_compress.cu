@@ -74,6 +74,10 @@ struct Job {
   };
   std::vector<Loc> loc;
   size_t nfresh = 0;
+  // A = A^T (hss_opts.symmetric): the column side of every node is its row
+  // side (S^c = S^r with one R), so its buffers alias the row side's and
+  // only the row side is computed
+  bool sym() const { return h->opts.symmetric != 0; }
   size_t id_first = 0;   // index of this job's first item in the round's ID table
 
   Job(hss_s* h_, const T* A_, int64_t lda_, cudaStream_t s_) : h(h_), A(A_), lda(lda_), s(s_) {}
@@ -128,9 +132,14 @@ struct Job {
     }
     for (NodeGen& g : h->gen) {
       HSS_TRY(regrow(reinterpret_cast<T**>(&g.Sr), g.kr, old, nc, g.ncols, true, copies));
-      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Sc), g.kc, old, nc, g.ncols, true, copies));
       HSS_TRY(regrow(reinterpret_cast<T**>(&g.Rr), g.kc, old, nc, g.ncols, true, copies));
-      HSS_TRY(regrow(reinterpret_cast<T**>(&g.Rc), g.kr, old, nc, g.ncols, true, copies));
+      if (sym()) {
+        g.Sc = g.Sr;
+        g.Rc = g.Rr;
+      } else {
+        HSS_TRY(regrow(reinterpret_cast<T**>(&g.Sc), g.kc, old, nc, g.ncols, true, copies));
+        HSS_TRY(regrow(reinterpret_cast<T**>(&g.Rc), g.kr, old, nc, g.ncols, true, copies));
+      }
     }
     HSS_TRY(launch_copy_batched<T>(copies, s, nullptr));
     for (T* p : old_global) dfree(p, s);
@@ -281,7 +290,7 @@ struct Job {
       Loc L{id, nullptr, nullptr, 0, 0, nullptr, nullptr};
       if (nd.c1 < 0) {   // leaf: the masked sample itself
         L.Yr = Sr + (int64_t)nd.lo * ld;
-        L.Yc = Sc + (int64_t)nd.lo * ld;
+        L.Yc = sym() ? L.Yr : Sc + (int64_t)nd.lo * ld;
         L.mr = L.mc = nd.hi - nd.lo;
       } else {
         NodeGen& g = h->gen[id];
@@ -290,9 +299,9 @@ struct Job {
         L.mr = a.kr + b.kr;
         L.mc = a.kc + b.kc;
         HSS_TRY(lvl->alloc_t(&L.own_r, (size_t)std::max(L.mr, 1) * ld, s));
-        HSS_TRY(lvl->alloc_t(&L.own_c, (size_t)std::max(L.mc, 1) * ld, s));
+        if (!sym()) HSS_TRY(lvl->alloc_t(&L.own_c, (size_t)std::max(L.mc, 1) * ld, s));
         L.Yr = L.own_r;
-        L.Yc = L.own_c;
+        L.Yc = sym() ? L.own_r : L.own_c;
         auto item = [&](T* out, int rows, const T* X, const void* M, int64_t ldm, int trans,
                         int inner, const T* Z) {
           GemmItem<T> it{};
@@ -318,9 +327,11 @@ struct Job {
         item(L.own_r + (int64_t)a.kr * ld, b.kr, (const T*)b.Sr, g.B21, a.kc, 0, a.kc,
              (const T*)a.Rr);
         // S^c_loc = [S^c_1 - B21^T R^c_2 ; S^c_2 - B12^T R^c_1]
-        item(L.own_c, a.kc, (const T*)a.Sc, g.B21, a.kc, 1, b.kr, (const T*)b.Rc);
-        item(L.own_c + (int64_t)a.kc * ld, b.kc, (const T*)b.Sc, g.B12, b.kc, 1, a.kr,
-             (const T*)a.Rc);
+        if (!sym()) {
+          item(L.own_c, a.kc, (const T*)a.Sc, g.B21, a.kc, 1, b.kr, (const T*)b.Rc);
+          item(L.own_c + (int64_t)a.kc * ld, b.kc, (const T*)b.Sc, g.B12, b.kc, 1, a.kr,
+               (const T*)a.Rc);
+        }
       }
       loc.push_back(L);
       return ok();
@@ -335,9 +346,14 @@ struct Job {
       NodeGen& g = h->gen[L.id];
       g.free_id();
       HSS_TRY(h->store.alloc_t(&g.permr, std::max(L.mr, 1), s));
-      HSS_TRY(h->store.alloc_t(&g.permc, std::max(L.mc, 1), s));
       HSS_TRY(h->store.alloc_t(&g.Er, std::max<size_t>((size_t)L.mr * std::min(L.mr, d), 1), s));
-      HSS_TRY(h->store.alloc_t(&g.Ec, std::max<size_t>((size_t)L.mc * std::min(L.mc, d), 1), s));
+      if (sym()) {   // V = U: the column ID is the row ID
+        g.permc = g.permr;
+        g.Ec = g.Er;
+      } else {
+        HSS_TRY(h->store.alloc_t(&g.permc, std::max(L.mc, 1), s));
+        HSS_TRY(h->store.alloc_t(&g.Ec, std::max<size_t>((size_t)L.mc * std::min(L.mc, d), 1), s));
+      }
       // a side whose rank exceeds d - p fails the node (d < m): its
       // generator would be discarded, so the ID skips it
       const int p = h->opts.oversample_p;
@@ -346,7 +362,7 @@ struct Job {
       IdItem b{L.Yc, L.mc, d, ld, g.permc, g.Ec, nullptr, nullptr, nullptr,
                h->opts.rtol, h->opts.atol, d < L.mc ? d - p : INT32_MAX};
       rd.ids.push_back(a);
-      rd.ids.push_back(b);
+      if (!sym()) rd.ids.push_back(b);
     }
     return ok();
   }
@@ -360,7 +376,8 @@ struct Job {
     for (size_t q = 0; q < nfresh; ++q) {
       Loc& L = loc[q];
       NodeGen& g = h->gen[L.id];
-      int kr = ks[2 * q], kc = ks[2 * q + 1];
+      // one ID per node when symmetric (its column side is its row side)
+      const int kr = sym() ? ks[q] : ks[2 * q], kc = sym() ? kr : ks[2 * q + 1];
       // FP64 work of the two truncated CPQRs: each of the k steps takes the
       // dot product and the update of every remaining column over the
       // remaining rows, sum_{i<k} 4 (d - i) (m - i)
@@ -368,7 +385,7 @@ struct Job {
         return 4.0 * (kk * dd * mm - (dd + mm) * kk * (kk - 1.0) / 2.0 +
                       (kk - 1.0) * kk * (2.0 * kk - 1.0) / 6.0);
       };
-      h->info.flops_id += cpqr_flops(d, L.mr, kr) + cpqr_flops(d, L.mc, kc);
+      h->info.flops_id += cpqr_flops(d, L.mr, kr) + (sym() ? 0.0 : cpqr_flops(d, L.mc, kc));
       // adaptive test (Section 3.2): fail iff d < m and k > d - p on either side
       bool failr = d < L.mr && kr > d - p;
       bool failc = d < L.mc && kc > d - p;
@@ -394,11 +411,17 @@ struct Job {
       int c0 = is_fresh ? 0 : g.ncols;
       if (is_fresh) {
         HSS_TRY(tmp.alloc(&g.Sr, sizeof(T) * std::max(g.kr, 1) * ld, s));
-        HSS_TRY(tmp.alloc(&g.Sc, sizeof(T) * std::max(g.kc, 1) * ld, s));
         HSS_TRY(tmp.alloc(&g.Rr, sizeof(T) * std::max(g.kc, 1) * ld, s));
-        HSS_TRY(tmp.alloc(&g.Rc, sizeof(T) * std::max(g.kr, 1) * ld, s));
         HSS_TRY(h->store.alloc_t(&g.Ir, std::max(g.kr, 1), s));
-        HSS_TRY(h->store.alloc_t(&g.Ic, std::max(g.kc, 1), s));
+        if (sym()) {
+          g.Sc = g.Sr;
+          g.Rc = g.Rr;
+          g.Ic = g.Ir;
+        } else {
+          HSS_TRY(tmp.alloc(&g.Sc, sizeof(T) * std::max(g.kc, 1) * ld, s));
+          HSS_TRY(tmp.alloc(&g.Rc, sizeof(T) * std::max(g.kr, 1) * ld, s));
+          HSS_TRY(h->store.alloc_t(&g.Ic, std::max(g.kc, 1), s));
+        }
       }
       // S^r_tau = S^r_loc(J^r, :), S^c_tau = S^c_loc(J^c, :)
       GemmItem<T> it{};
@@ -413,11 +436,13 @@ struct Job {
       it.X.ld0 = ld;
       it.X.map = g.permr;
       rd.updates.push_back(it);
-      it.out = (T*)g.Sc;
-      it.rows = g.kc;
-      it.X.p0 = L.Yc;
-      it.X.map = g.permc;
-      rd.updates.push_back(it);
+      if (!sym()) {
+        it.out = (T*)g.Sc;
+        it.rows = g.kc;
+        it.X.p0 = L.Yc;
+        it.X.map = g.permc;
+        rd.updates.push_back(it);
+      }
       // R^r_tau = V^T R_in^r (V from the column ID), R^c_tau = U^T R_in^c
       RowSrc<T> rin_r, rin_c;
       if (nd.c1 < 0) {
@@ -459,16 +484,16 @@ struct Job {
         rd.updates.push_back(b);
       };
       basis((T*)g.Rr, g.kc, g.mc, g.permc, g.Ec, rin_r);
-      basis((T*)g.Rc, g.kr, g.mr, g.permr, g.Er, rin_c);
+      if (!sym()) basis((T*)g.Rc, g.kr, g.mr, g.permr, g.Er, rin_c);
       if (is_fresh) {   // skeleton index sets I^r = I(J^r), I^c = I(J^c)
         if (nd.c1 < 0) {
           rd.index.push_back({g.Ir, g.permr, nullptr, nullptr, 0, nd.lo, g.kr});
-          rd.index.push_back({g.Ic, g.permc, nullptr, nullptr, 0, nd.lo, g.kc});
+          if (!sym()) rd.index.push_back({g.Ic, g.permc, nullptr, nullptr, 0, nd.lo, g.kc});
         } else {
           NodeGen& a = h->gen[nd.c1];
           NodeGen& b = h->gen[nd.c2];
           rd.index.push_back({g.Ir, g.permr, a.Ir, b.Ir, a.kr, 0, g.kr});
-          rd.index.push_back({g.Ic, g.permc, a.Ic, b.Ic, a.kc, 0, g.kc});
+          if (!sym()) rd.index.push_back({g.Ic, g.permc, a.Ic, b.Ic, a.kc, 0, g.kc});
         }
       }
     }
@@ -607,7 +632,8 @@ static hss_status validate_opts(const void* A, int64_t n, int64_t lda, hss_dtype
   if (o->d_max <= 0 || o->d_max > n) o->d_max = (int32_t)std::min<int64_t>(n, INT32_MAX);
   if (o->leaf_size < 1 || o->d0 < 1 || o->d_step < 1 || o->oversample_p < 0 ||
       !(o->rtol >= 0.0) || !(o->atol >= 0.0) || o->sample_mode < 0 || o->sample_mode > 3 ||
-      (dtype == HSS_F64 && o->sample_mode != HSS_SAMPLE_NATIVE) || n > INT32_MAX) {
+      (dtype == HSS_F64 && o->sample_mode != HSS_SAMPLE_NATIVE) || n > INT32_MAX ||
+      (o->symmetric != 0 && o->symmetric != 1)) {
     *msg = "bad options";
     return HSS_ERR_INVALID;
   }

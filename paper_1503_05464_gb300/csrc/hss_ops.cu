@@ -93,8 +93,12 @@ Err finalize_generators(hss_s* h, cudaStream_t s) {
     HSS_TRY(h->store.alloc_t(&g.iperm_r, std::max(g.mr, 1), s));
     inv.push_back({g.iperm_r, g.permr, g.mr});
     int64_t esz = h->dtype == HSS_F64 ? 8 : 4;
-    h->info.bytes_hss += 8 * ((int64_t)(g.mr - g.kr) * g.kr + (int64_t)(g.mc - g.kc) * g.kc) +
-                         4 * ((int64_t)g.mr + g.mc);
+    // a symmetric handle's column generator is its row generator (one copy)
+    if (h->opts.symmetric)
+      h->info.bytes_hss += 8 * (int64_t)(g.mr - g.kr) * g.kr + 4 * (int64_t)g.mr;
+    else
+      h->info.bytes_hss += 8 * ((int64_t)(g.mr - g.kr) * g.kr + (int64_t)(g.mc - g.kc) * g.kc) +
+                           4 * ((int64_t)g.mr + g.mc);
     const TNode& nd = h->tree.nodes[i];
     if (nd.c1 >= 0) {
       const NodeGen& a = h->gen[nd.c1];

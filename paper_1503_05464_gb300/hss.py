@@ -38,7 +38,8 @@ class HssOpts(ctypes.Structure):
                 ("atol", ctypes.c_double), ("d0", ctypes.c_int32), ("d_step", ctypes.c_int32),
                 ("d_max", ctypes.c_int32), ("oversample_p", ctypes.c_int32),
                 ("sample_mode", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("tree", ctypes.POINTER(ctypes.c_int64)), ("tree_nodes", ctypes.c_int32)]
+                ("tree", ctypes.POINTER(ctypes.c_int64)), ("tree_nodes", ctypes.c_int32),
+                ("symmetric", ctypes.c_int32)]
 
 
 class HssInfo(ctypes.Structure):
@@ -145,7 +146,7 @@ def _require_cuda(*ts):
 def hss_default_opts(**kw) -> HssOpts:
     """hss_opts with the library defaults, then the keyword fields.  tree: a
     list of split points, one per node in breadth-first order (-1 = leaf),
-    the format of hss_opts.tree."""
+    the format of hss_opts.tree.  symmetric: True when A = A^T."""
     o = HssOpts()
     _check(load().hss_default_opts(ctypes.byref(o)))
     for k, v in kw.items():
@@ -160,6 +161,8 @@ def hss_default_opts(**kw) -> HssOpts:
             o.tree = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int64))
             o.tree_nodes = len(v)
             continue
+        if k == "symmetric":
+            v = int(bool(v))
         setattr(o, k, v)
     return o
 

@@ -60,6 +60,22 @@ def test_batched_equals_alone(P, mode):
         _same(P, h, alone, A.shape[0], A.dtype)
 
 
+def test_batched_symmetric_and_general_mixed_equal_alone(P):
+    # symmetric matrices, every other one compressed with symmetric=True:
+    # each handle comes out as it does alone, whatever shares its launches
+    mats = _mats_f32()
+    opts = [P.hss_default_opts(leaf_size=128, rtol=1e-5, d0=64, d_step=32, seed=9,
+                               sample_mode="bf16x3", symmetric=(i % 2 == 0))
+            for i in range(len(mats))]
+    hs, sts = P.hss_compress_batched(mats, opts)
+    assert sts == [0] * len(mats)
+    for A, h, o in zip(mats, hs, opts):
+        alone = P.hss_compress(A, o)
+        _same(P, h, alone, A.shape[0], A.dtype)
+        if o.symmetric:
+            assert all(kr == kc for (_, _, kr, kc) in P.hss_node_ranks(h)[1:])
+
+
 def test_batched_fp64_matches_oracle(P):
     mats = _mats_f64()
     kw = dict(leaf_size=64, rtol=1e-8, d0=48, d_step=16, seed=4)

@@ -449,7 +449,7 @@ def test_compress_gaussian_kernel_tf32(P):
         assert (lo, hi) == (ho.nodes[i].lo, ho.nodes[i].hi)
         assert kr >= ro[i][0] - 2 and kc >= ro[i][1] - 2, (i, kr, kc, ro[i])
     mx = max(max(kr, kc) for (_, _, kr, kc) in ranks[1:])
-    mo = max(max(a, b) for (a, b) in ro[1:])
+    mo = max(max(a, b) for (a, b) in ro.values())
     assert mx <= 2 * mo, (mx, mo)
     H = _dense_from_gpu(P, h, n, torch.float32)
     assert _rel(H, A32) <= _err_bound(A32, ho, rtol) + 2.0 ** -11
@@ -459,6 +459,45 @@ def test_compress_gaussian_kernel_tf32(P):
     O.ulv_factor(ho)
     xo = O.ulv_solve(ho, b)
     assert _rel(A32 @ xs, b) <= 10 * max(_rel(A32 @ xo, b), 1e-6)
+
+
+@pytest.mark.parametrize("dtype,mode", [(torch.float64, "native"), (torch.float32, "bf16x3")])
+def test_compress_symmetric_matches_oracle(P, dtype, mode):
+    """symmetric=True on a symmetric matrix (Gaussian kernel, adaptive
+    restarts): one ID per node and V = U, as the oracle's symmetric
+    compression (Section 2.2 with one R: S^c = S^r).  Ranks match the
+    oracle's (FP64: +-2; BF16x3: the FP32-class check) with k^c = k^r, the
+    reconstruction is symmetric to rounding and within the oracle's bound,
+    the ID work is half the general compression's, and the ULV solve is
+    within 10x the oracle's residual."""
+    n, leaf, rtol = 3000, 128, 1e-6
+    f64 = dtype == torch.float64
+    pts = W.points_unit_cube(n, 1012)
+    pts = pts[W.rcb_order(pts, leaf)]
+    At = W.gaussian_kernel(pts, 0.2, 1.0, dtype=np.float64 if f64 else np.float32, device=DEV)
+    A = At.cpu().numpy().astype(np.float64)
+    kw = dict(leaf_size=leaf, rtol=rtol, d0=64, d_step=32, seed=1013, sample_mode=mode)
+    h = P.hss_compress(At, symmetric=True, **kw)
+    hg = P.hss_compress(At, **kw)
+    ho = O.compress(A, rtol, leaf_size=leaf, d0=64, d_step=32, seed=1013, symmetric=True)
+    ranks = P.hss_node_ranks(h)
+    assert all(kr == kc for (_, _, kr, kc) in ranks[1:])
+    if f64:
+        _ranks_close(P, h, ho)
+    else:
+        _ranks_close_fp32(P, h, ho)
+    assert P.hss_info(h)["passes"] == ho.passes or not f64
+    fs, fg = P.hss_info(h)["flops_id"], P.hss_info(hg)["flops_id"]
+    assert 0.3 * fg <= fs <= 0.6 * fg, (fs, fg)
+    H = _dense_from_gpu(P, h, n, dtype)
+    assert np.linalg.norm(H - H.T) <= (1e-12 if f64 else 1e-5) * np.linalg.norm(H)
+    assert _rel(H, A) <= _err_bound(A, ho, rtol)
+    P.hss_factor(h)
+    b = np.random.default_rng(5).standard_normal((n, 4))
+    xs = P.hss_solve(h, torch.tensor(b, dtype=dtype, device=DEV)).cpu().numpy()
+    O.ulv_factor(ho)
+    xo = O.ulv_solve(ho, b)
+    assert _rel(A @ xs, b) <= 10 * max(_rel(A @ xo, b), 1e-6 if not f64 else 1e-13)
 
 
 @pytest.mark.parametrize("mode", ["bf16x2", "bf16x3"])
