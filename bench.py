@@ -82,8 +82,10 @@ GOLDEN_BEM60K = os.path.join(ROOT, "tests", "golden", "bem60k_oracle.json")
 # on the same part: 1.20); FP32 FMA: 152 SMs x 128 lanes x 2 flops at the
 # probed ~1.79 GHz under load (own probe: 69.7 TFLOP/s)
 FP64_PEAK_TFLOPS = 1.25
-# DRAM bytes (read + write) per FP64 flop of the ID kernel over a whole bem32k
-# compression, from profiles/id_cpqr_dram_bem32k.md
+# DRAM bytes (read + write) of the ID kernel over a whole bem32k compression
+# per FP64 flop of its CPQR steps (the flops_id count of that capture, which
+# did not yet include the T = R1^-1 R2 solve), from
+# profiles/id_cpqr_dram_bem32k.md
 ID_DRAM_BYTES_PER_FLOP = 0.442
 FP32_SIMT_PEAK_TFLOPS = 69.7
 
@@ -297,8 +299,10 @@ def run_ours(args, wl):
     else:
         unit_peak, bound = peaks.get("bf16_tflops", 1972.8), "tensor"
     cols = [wl["d0"]] + [wl["step"]] * (info["passes"] - 1)
-    roof_ms = sum(max(terms * 4.0 * n * n * c / (unit_peak * 1e12), n * n * esz / (hbm * 1e9))
-                  for c in cols) * 1e3
+    # (2 n^2 c per product; the symmetric path forms the row product only)
+    prods = 1 if args.symmetric else 2
+    roof_ms = sum(max(terms * 2.0 * prods * n * n * c / (unit_peak * 1e12),
+                      n * n * esz / (hbm * 1e9)) for c in cols) * 1e3
     samp_tflops = terms * info["flops_sample"] / (s_ms * 1e-3) / 1e12 if s_ms > 0 else 0.0
     samp_gbs = info["passes"] * n * n * esz / (s_ms * 1e-3) / 1e9 if s_ms > 0 else 0.0
     phases = {
@@ -307,7 +311,8 @@ def run_ours(args, wl):
                          "frac": id_tflops / FP64_PEAK_TFLOPS,
                          "peak_source": "GB300 nominal dense FP64 (own FMA probe: 1.20)",
                          "flops": info["flops_id"], "launches": info["id_launches"],
-                         "flops_is": "sum over node sides of sum_{i<k} 4 (d-i)(m-i)"},
+                         "flops_is": "sum over node sides of sum_{i<k} 4 (d-i)(m-i) (CPQR) "
+                                     "+ (m-k) k^2 (T = R1^-1 R2, sides that pass)"},
         "fused_sampling": {"ms": s_ms, "bound": bound, "achieved": samp_tflops,
                            "peak": unit_peak, "unit": "TFLOP/s", "roofline_ms": roof_ms,
                            "frac": roof_ms / s_ms if s_ms > 0 else 0.0,
@@ -327,7 +332,8 @@ def run_ours(args, wl):
         # DRAM bytes per FP64 flop of the ID launches, measured by ncu over a
         # whole bem32k compression (profiles/id_cpqr_dram_bem32k.md), times
         # this compression's flops per ID launch
-        roof["traffic"] = ID_DRAM_BYTES_PER_FLOP * info["flops_id"] / info["id_launches"]
+        roof["traffic"] = (ID_DRAM_BYTES_PER_FLOP * (info["flops_id"] - info["flops_id_solve"]) /
+                           info["id_launches"])
         roof["traffic_unit"] = "bytes per launch (scaled from the bem32k capture)"
     value = ms / 1e3 / (args.steps * world) if world > 1 else ms / 1e3 / args.steps
     out = {

@@ -103,7 +103,9 @@ typedef struct {
   double ms_levels;                 /* host wall time of the level loop        */
   double flops_sample;              /* 4 n^2 d summed over passes              */
   double flops_id;                  /* FP64 flops of the IDs: sum over node sides
-                                       of sum_{i<k} 4 (d - i)(m - i)            */
+                                       of sum_{i<k} 4 (d - i)(m - i) (the CPQR),
+                                       plus (m - k) k^2 (T = R1^{-1} R2) where
+                                       the side passes the adaptive test      */
   int32_t factored;                 /* 1 after hss_factor                      */
   int64_t launches;                 /* kernels launched by hss_compress        */
   int64_t bytes_d2h;                /* bytes read back to the host (ranks)     */
@@ -111,11 +113,12 @@ typedef struct {
   double ms_host_wait;              /* host time blocked on the rank readback  */
   double ms_host_sample;            /* host wall time of the sampling passes   */
   int64_t id_launches;              /* ID kernel launches of hss_compress      */
+  double flops_id_solve;            /* the T = R1^{-1} R2 part of flops_id     */
 } hss_info_t;
 
 /* Fills *opts with defaults: leaf_size 128, rtol 1e-6, atol 0, d0 64,
  * d_step 32, d_max 0 (= n), oversample_p 10, NATIVE sampling, seed 0,
- * tree NULL (bisection). */
+ * tree NULL (bisection), symmetric 0. */
 hss_status hss_default_opts(hss_opts* opts);
 
 /*
@@ -284,6 +287,9 @@ hss_status hss_random_gaussian(uint64_t seed, int64_t n, int64_t c0, int64_t c1,
  * mask, Sr(I_t, :) is Algorithm 1's S^r_loc = S^r(I_t,:) - D_t R(I_t,:).
  *   A  device n x n row-major (lda);  R, Sr, Sc device n x ld row-major with
  *   ldr / lds >= c1.  mode: hss_sample_mode (NATIVE only for HSS_F64).
+ *   Sc may be NULL: only Sr is formed (a symmetric A, whose S^c is S^r; the
+ *   tensor-core kernel then skips the column product), with the same bits
+ *   in Sr as when Sc is given.
  * The split-BF16 modes on the tensor cores accumulate in FP32 over at most
  * 24 MMAs at a time and sum those partial results in FP32 on the CUDA cores.
  * Errors: INVALID, OOM (scratch for the partial sums), CUDA, TIMEOUT (a

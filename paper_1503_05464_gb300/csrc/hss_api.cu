@@ -217,7 +217,7 @@ hss_status hss_sample(const void* A, int64_t n, int64_t lda, hss_dtype dtype, co
                       int64_t ldr, int64_t c0, int64_t c1, void* Sr, void* Sc, int64_t lds,
                       const int64_t* leaf_starts, int32_t nleaf, int32_t mode, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  if (!A || !R || !Sr || !Sc || n < 1 || lda < n || c0 < 0 || c1 < c0 || ldr < c1 || lds < c1 ||
+  if (!A || !R || !Sr || n < 1 || lda < n || c0 < 0 || c1 < c0 || ldr < c1 || lds < c1 ||
       nleaf < 0 || mode < 0 || mode > 3 || (dtype == HSS_F64 && mode != 0) ||
       (nleaf > 0 && !leaf_starts))
     return set_err(nullptr, fail(HSS_ERR_INVALID, "hss_sample: bad arguments"));

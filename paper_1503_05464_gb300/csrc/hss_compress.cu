@@ -127,6 +127,7 @@ struct Job {
     int old = h->dcap, cols = h->d;
     std::vector<Copy2D<T>> copies;
     for (T** g : {&R, &Sr, &Sc}) {
+      if (g == &Sc && sym()) continue;   // no column samples: S^c = S^r
       if (*g) HSS_TRY(regrow(g, n(), old, nc, cols, false, copies));
       else HSS_TRY(dalloc_t(g, (size_t)n() * nc, s));
     }
@@ -157,10 +158,12 @@ struct Job {
     // n = 10000), two-tile chains 3.6e-7: the long ones only where rtol is
     // at least 60 times above that
     scratch.row_chain = h->opts.rtol >= 1e-4 ? 16 : 2;
-    HSS_TRY(launch_sample<T>(A, n(), lda, R, h->dcap, c0, c1, Sr, Sc, h->dcap, leaf_of,
+    // symmetric: the row product only (S^c = S^r)
+    HSS_TRY(launch_sample<T>(A, n(), lda, R, h->dcap, c0, c1, Sr, sym() ? nullptr : Sc, h->dcap,
+                             leaf_of,
                              h->opts.sample_mode, &scratch, s, timing ? &ms : nullptr));
     ms_sample += ms;
-    h->info.flops_sample += 4.0 * (double)n() * (double)n() * (double)(c1 - c0);
+    h->info.flops_sample += (sym() ? 2.0 : 4.0) * (double)n() * (double)n() * (double)(c1 - c0);
     h->info.ms_host_sample += now_ms() - t0;
     return ok();
   }
@@ -385,10 +388,18 @@ struct Job {
         return 4.0 * (kk * dd * mm - (dd + mm) * kk * (kk - 1.0) / 2.0 +
                       (kk - 1.0) * kk * (2.0 * kk - 1.0) / 6.0);
       };
-      h->info.flops_id += cpqr_flops(d, L.mr, kr) + (sym() ? 0.0 : cpqr_flops(d, L.mc, kc));
       // adaptive test (Section 3.2): fail iff d < m and k > d - p on either side
       bool failr = d < L.mr && kr > d - p;
       bool failc = d < L.mc && kc > d - p;
+      // and of T = R1^{-1} R2 (Section 2.2's ID) for a side that passes its
+      // own test: per remaining column k divisions and k (k - 1) / 2
+      // multiply-adds, (m - k) k^2 flops
+      auto solve_flops = [](double mm, double kk, bool failed) {
+        return failed ? 0.0 : (mm - kk) * kk * kk;
+      };
+      const double fs = solve_flops(L.mr, kr, failr) + (sym() ? 0.0 : solve_flops(L.mc, kc, failc));
+      h->info.flops_id += cpqr_flops(d, L.mr, kr) + (sym() ? 0.0 : cpqr_flops(d, L.mc, kc)) + fs;
+      h->info.flops_id_solve += fs;
       if (failr || failc) {
         g.state = NODE_PARTIALLY;
         g.free_id();

@@ -293,10 +293,12 @@ Err launch_sample(const T* A, int64_t n, int64_t lda, const T* R, int64_t ldr, i
     sample_simt_kernel<T><<<npanel * nchunk, S_THREADS, smem, s>>>(
         A, n, lda, R, ldr, c0, ncols, nchunk, Sr, lds, leaf_of, P);
     HSS_TRY(check_launch("sample_simt_kernel"));
-    int64_t total = (int64_t)nchunk * n * (S_DC / 4);
-    reduce_partials_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-        P, n, npanel, nchunk, c0, ncols, Sc, lds);
-    HSS_TRY(check_launch("reduce_partials_kernel"));
+    if (Sc != nullptr) {   // (nullptr: the row samples only)
+      int64_t total = (int64_t)nchunk * n * (S_DC / 4);
+      reduce_partials_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+          P, n, npanel, nchunk, c0, ncols, Sc, lds);
+      HSS_TRY(check_launch("reduce_partials_kernel"));
+    }
   }
   if (ms_out) {
     HSS_CUDA_TRY(cudaEventRecord(e1, s));

@@ -406,6 +406,7 @@ Err launch_sample_mma(const float* A, int64_t n, int64_t lda, const float* R, in
       return fail(HSS_ERR_INVALID, "launch_sample_mma: mode must be TF32, BF16X2 or BF16X3");
   }
   if (e.st) return e;
+  if (Sc == nullptr) return ok();   // the row samples only
   return launch_reduce_partials(P, n, npanel, nchunk, c0, ncols, Sc, lds, s);
 }
 

@@ -164,6 +164,7 @@ struct TcArgs {
   int ncb;        // 64-column boxes of R per row (1 or 2; bfloat16 modes)
   const float* rt;   // TF32: R^T, 128 rows (sample columns) x ldrt, zero-padded
   int ldrt;          // TF32: row pitch of rt (2 ngp 128 elements)
+  int rows_only;     // 1: the row product only (no column product, R_p, exchange)
   int nr;         // N of the row product (c rounded up to 16)
   int ntc;        // column tiles per panel
   int npanel;
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (long long t = tb; t < te; ++t) {
         const int p = KC * static_cast<int>(t / ntc) + crank, J = static_cast<int>(t % ntc);
         const bool first = (t == tb) || J == 0;
-        if (!is_tf32<NT>() && first) {
+        if (!is_tf32<NT>() && !g.rows_only && first) {
           // the previous segment's R_p has been copied to TMEM
           if (!mbar_wait(bar(B_RSEMPTY), (ri_cnt & 1) ^ 1, abort_flag, g.err, 1, WAIT_LIMIT))
             break;
@@ -348,19 +349,24 @@ __global__ void __launch_bounds__(THREADS, 1)
         const bool first = (t == tb) || J == 0, last = (t == te - 1) || J == ntc - 1;
         const bool gend = last || (J % gs) == gs - 1;
         const bool cend = gend || ((J % gs) % chain) == chain - 1;
-        if (first && !mbar_wait(bar(B_RTFULL), seg & 1, abort_flag, g.err, 4, WAIT_LIMIT)) break;
+        const bool col = !g.rows_only;
+        if (col && first && !mbar_wait(bar(B_RTFULL), seg & 1, abort_flag, g.err, 4, WAIT_LIMIT))
+          break;
         const int ps = tl & 1, u = tl >> 1;
         const int cb = tl % CB, cu = tl / CB;
         if (!mbar_wait(bar(B_PFULL + ps), u & 1, abort_flag, g.err, 5, WAIT_LIMIT)) break;
         if (!mbar_wait(bar(B_RJFULL + ps), u & 1, abort_flag, g.err, 6, WAIT_LIMIT)) break;
-        if (!mbar_wait(bar(B_CEMPTY + cb), (cu & 1) ^ 1, abort_flag, g.err, 7, WAIT_LIMIT)) break;
+        if (col && !mbar_wait(bar(B_CEMPTY + cb), (cu & 1) ^ 1, abort_flag, g.err, 7, WAIT_LIMIT))
+          break;
         fence_after();
         const uint64_t poff = (ps * L::pstage) >> 4;
         const uint64_t roff = (ps * L::rjstage) >> 4;
         // the column product first: it keeps the tensor core busy while the
         // fold warps read the previous chain's row accumulator
         const uint32_t dc = tbase + T_COL + 64 * cb;
-        if constexpr (is_tf32<NT>()) {
+        if (!col) {
+          // row samples only
+        } else if constexpr (is_tf32<NT>()) {
           // K = 8 panel rows per MMA: eight TMEM columns of R_p^T, 32 bytes
           // along the rows of one 8 KB chunk of the transposed tile
 #pragma unroll
@@ -409,14 +415,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         mma_commit(bar(B_PEMPTY + ps));
         mma_commit(bar(B_RJEMPTY + ps));
-        mma_commit(bar(B_CFULL + cb));
+        if (col) mma_commit(bar(B_CFULL + cb));
         ++since;
         if (cend) {   // the row accumulator holds the chain's sum
           mma_commit(bar(B_RFULL));
           ++ch;
           since = 0;
         }
-        if (last) {
+        if (col && last) {
           mma_commit(bar(B_RIEMPTY));
           ++seg;
         }
@@ -551,7 +557,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t xpeer = mapa(su32(sm + L::xb), peer);          // slot x at + x X_BYTES
     const uint32_t xfull_peer = mapa(bar(B_XFULL), peer);          // slot x at + 8 x
     const uint32_t xrow = static_cast<uint32_t>(e) * (HB * 4);   // this thread's row of a slot
-    const int nt = static_cast<int>(te - tb);
+    // (no column product: nothing to drain)
+    const int nt = g.rows_only ? 0 : static_cast<int>(te - tb);
     int rseg = 0;
     for (int i = 0; i < nt; ++i) {
       const int cb = i % CB, cu = i / CB;
@@ -676,53 +683,55 @@ __global__ void __launch_bounds__(THREADS, 1)
       const bool gend = last || (J % gs) == gs - 1;
       const bool cend = gend || ((J % gs) % chain) == chain - 1;
       if (jfirst < 0) jfirst = J;
-      // ---- tile i's column sums
-      const int cb = i % CB, cu = i / CB;
-      const int xs = i % XSLOTS, xu = i / XSLOTS;
-      if (elect) {
-        // this CTA's column product of the tile is in TMEM (the buffer cannot
-        // move on to a later tile before this group has read it), and the
-        // partner's half has arrived
-        mbar_expect_tx(bar(B_XFULL + xs), static_cast<uint32_t>(c) * (HB * 4));
-        const bool ok =
-            mbar_wait(bar(B_CFULL + cb), cu & 1, abort_flag, g.err, 18, WAIT_LIMIT) &&
-            mbar_wait(bar(B_XFULL + xs), xu & 1, abort_flag, g.err, 16, WAIT_LIMIT);
-        fstop[2] = ok ? 0 : 1;
-      }
-      named_sync(2, 128);
-      if (fstop[2]) break;
-      // the partner's half into registers, and the slot back to the partner
-      float r[HB];
-      {
-        const uint8_t* xslot = sm + L::xb + xs * X_BYTES + xrow;
-#pragma unroll
-        for (int q4 = 0; q4 < HB / 4; ++q4) {
-          const float4 x = *reinterpret_cast<const float4*>(xslot + ((q4 ^ (e & 7)) << 4));
-          r[4 * q4] = x.x;
-          r[4 * q4 + 1] = x.y;
-          r[4 * q4 + 2] = x.z;
-          r[4 * q4 + 3] = x.w;
+      // ---- tile i's column sums (none when only the row product runs)
+      if (!g.rows_only) {
+        const int cb = i % CB, cu = i / CB;
+        const int xs = i % XSLOTS, xu = i / XSLOTS;
+        if (elect) {
+          // this CTA's column product of the tile is in TMEM (the buffer cannot
+          // move on to a later tile before this group has read it), and the
+          // partner's half has arrived
+          mbar_expect_tx(bar(B_XFULL + xs), static_cast<uint32_t>(c) * (HB * 4));
+          const bool ok =
+              mbar_wait(bar(B_CFULL + cb), cu & 1, abort_flag, g.err, 18, WAIT_LIMIT) &&
+              mbar_wait(bar(B_XFULL + xs), xu & 1, abort_flag, g.err, 16, WAIT_LIMIT);
+          fstop[2] = ok ? 0 : 1;
         }
-      }
-      named_sync(2, 128);
-      if (elect) mbar_arrive_remote(xempty_peer + 8 * xs);
-      fence_after();
-      {
-        float m[HB];
-        tmem_ld32(tbase + loff + T_COL + 64 * cb + own, m);
-        tmem_wait_ld();
-        fence_before();
-        mbar_arrive(bar(B_CEMPTY + cb));
-        if (e < c) {
-          // the pair's sum for columns j = J 64 + own .. + 31 and sample
-          // column e: Sc_part[pg][j][e], so that a warp stores one whole
-          // 128-byte row per instruction (rows are padded to whole tiles;
-          // past n the TMA fill is zero, so the pad holds zeros, which the
-          // reduction never reads)
-          float* dst = g.sc_part +
-                       (static_cast<size_t>(pg) * g.npad + static_cast<size_t>(J) * BN + own) * c + e;
+        named_sync(2, 128);
+        if (fstop[2]) break;
+        // the partner's half into registers, and the slot back to the partner
+        float r[HB];
+        {
+          const uint8_t* xslot = sm + L::xb + xs * X_BYTES + xrow;
 #pragma unroll
-          for (int x = 0; x < HB; ++x) dst[static_cast<size_t>(x) * c] = m[x] + r[x];
+          for (int q4 = 0; q4 < HB / 4; ++q4) {
+            const float4 x = *reinterpret_cast<const float4*>(xslot + ((q4 ^ (e & 7)) << 4));
+            r[4 * q4] = x.x;
+            r[4 * q4 + 1] = x.y;
+            r[4 * q4 + 2] = x.z;
+            r[4 * q4 + 3] = x.w;
+          }
+        }
+        named_sync(2, 128);
+        if (elect) mbar_arrive_remote(xempty_peer + 8 * xs);
+        fence_after();
+        {
+          float m[HB];
+          tmem_ld32(tbase + loff + T_COL + 64 * cb + own, m);
+          tmem_wait_ld();
+          fence_before();
+          mbar_arrive(bar(B_CEMPTY + cb));
+          if (e < c) {
+            // the pair's sum for columns j = J 64 + own .. + 31 and sample
+            // column e: Sc_part[pg][j][e], so that a warp stores one whole
+            // 128-byte row per instruction (rows are padded to whole tiles;
+            // past n the TMA fill is zero, so the pad holds zeros, which the
+            // reduction never reads)
+            float* dst = g.sc_part +
+                         (static_cast<size_t>(pg) * g.npad + static_cast<size_t>(J) * BN + own) * c + e;
+#pragma unroll
+            for (int x = 0; x < HB; ++x) dst[static_cast<size_t>(x) * c] = m[x] + r[x];
+          }
         }
       }
       if (!cend) continue;
@@ -839,7 +848,8 @@ __global__ void sample_tc_reduce_kernel(const float* __restrict__ sc_part,
                                         float* Sc, long long lds) {
   const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int cv = c / V;
-  const long long ncv = static_cast<long long>(n) * cv;
+  // Sc == nullptr: the row samples only
+  const long long ncv = Sc != nullptr ? static_cast<long long>(n) * cv : 0;
   if (idx < ncv) {
     const int j = static_cast<int>(idx / cv), cc = static_cast<int>(idx % cv) * V;
     const float* src = sc_part + static_cast<size_t>(j) * c + cc;
@@ -1154,6 +1164,7 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     g.ncb = cpad / 64;
     g.rt = tf32 ? Rt : nullptr;
     g.ldrt = ldrt;
+    g.rows_only = Sc == nullptr ? 1 : 0;
     g.nr = (c + 15) / 16 * 16;
     g.ntc = pl.ntc;
     g.npanel = pl.npanel;
@@ -1189,16 +1200,17 @@ Err launch_sample_tc(const float* A, int64_t n, int64_t lda, const float* R, int
     }
     const long long nrow = static_cast<long long>(pl.npanel) * c * BM;
     const int npad = pl.ntc * BN;
+    float* scout = Sc != nullptr ? Sc + c0 + done : nullptr;
     if (c % 4 == 0) {
-      const long long nred = static_cast<long long>(n) * (c / 4) + nrow;
+      const long long nred = (scout ? static_cast<long long>(n) * (c / 4) : 0) + nrow;
       sample_tc_reduce_kernel<4><<<static_cast<unsigned>((nred + 255) / 256), 256, 0, s>>>(
           scp, srp, side1, static_cast<int>(n), npad, c, pl.npanel, pl.ngp, pl.ngroups,
-          Sr + c0 + done, Sc + c0 + done, lds);
+          Sr + c0 + done, scout, lds);
     } else {
-      const long long nred = static_cast<long long>(n) * c + nrow;
+      const long long nred = (scout ? static_cast<long long>(n) * c : 0) + nrow;
       sample_tc_reduce_kernel<1><<<static_cast<unsigned>((nred + 255) / 256), 256, 0, s>>>(
           scp, srp, side1, static_cast<int>(n), npad, c, pl.npanel, pl.ngp, pl.ngroups,
-          Sr + c0 + done, Sc + c0 + done, lds);
+          Sr + c0 + done, scout, lds);
     }
     HSS_TRY(check_launch("sample_tc_reduce_kernel"));
     int herr = 0;

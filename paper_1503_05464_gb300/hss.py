@@ -53,7 +53,8 @@ class HssInfo(ctypes.Structure):
                 ("flops_id", ctypes.c_double), ("factored", ctypes.c_int32),
                 ("launches", ctypes.c_int64), ("bytes_d2h", ctypes.c_int64),
                 ("ms_host_id_launch", ctypes.c_double), ("ms_host_wait", ctypes.c_double),
-                ("ms_host_sample", ctypes.c_double), ("id_launches", ctypes.c_int64)]
+                ("ms_host_sample", ctypes.c_double), ("id_launches", ctypes.c_int64),
+                ("flops_id_solve", ctypes.c_double)]
 
 
 _lib = None
@@ -399,9 +400,10 @@ def hss_random_gaussian(seed: int, n: int, c0: int, c1: int, R: torch.Tensor, st
 
 
 def hss_sample(A, R, c0, c1, Sr, Sc, leaf_starts=None, mode="native", stream=None):
-    """Fused sampling of columns [c0, c1): Sr = (A-D) R, Sc = (A-D)^T R."""
-    _require_cuda(A, R, Sr, Sc)
-    if Sr.stride(0) != Sc.stride(0):
+    """Fused sampling of columns [c0, c1): Sr = (A-D) R, Sc = (A-D)^T R
+    (Sc None: the row samples only)."""
+    _require_cuda(A, R, Sr, *([Sc] if Sc is not None else []))
+    if Sc is not None and Sr.stride(0) != Sc.stride(0):
         raise ValueError("Sr and Sc must share a leading dimension")
     if isinstance(mode, str):
         mode = SAMPLE_MODES[mode]
@@ -412,7 +414,8 @@ def hss_sample(A, R, c0, c1, Sr, Sc, leaf_starts=None, mode="native", stream=Non
         ls, nleaf = ctypes.cast(arr, ctypes.c_void_p), len(leaf_starts) - 1
     _check(load().hss_sample(ctypes.c_void_p(A.data_ptr()), A.shape[0], A.stride(0), _dtype(A),
                              ctypes.c_void_p(R.data_ptr()), R.stride(0), c0, c1,
-                             ctypes.c_void_p(Sr.data_ptr()), ctypes.c_void_p(Sc.data_ptr()),
+                             ctypes.c_void_p(Sr.data_ptr()),
+                             ctypes.c_void_p(Sc.data_ptr() if Sc is not None else None),
                              Sr.stride(0), ls, nleaf, mode, _stream(stream)))
 
 

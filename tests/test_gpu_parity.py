@@ -203,6 +203,25 @@ def test_tensor_core_sampling_repeats_identically(P, mode):
             assert torch.equal(Sr, ref[0]) and torch.equal(Sc, ref[1])
 
 
+@pytest.mark.parametrize("mode", ["native", "tf32", "bf16x2", "bf16x3"])
+def test_row_samples_alone_equal_the_row_part(P, mode):
+    # Sc = None forms S^r only (the symmetric path; the tensor-core kernel
+    # skips the column product): the same bits as the row part of a full call
+    n, c = 4100, 96
+    rng = np.random.default_rng(12)
+    At = torch.tensor(rng.standard_normal((n, n)), dtype=torch.float32, device=DEV)
+    R = torch.zeros((n, c), device=DEV)
+    P.hss_random_gaussian(6, n, 0, c, R)
+    starts = list(range(0, n, 300)) + [n]
+    Sr = torch.empty((n, c), device=DEV)
+    Sc = torch.empty((n, c), device=DEV)
+    P.hss_sample(At, R, 0, c, Sr, Sc, leaf_starts=starts, mode=mode)
+    Sr1 = torch.full((n, c), 5.0, device=DEV)
+    P.hss_sample(At, R, 0, c, Sr1, None, leaf_starts=starts, mode=mode)
+    torch.cuda.synchronize()
+    assert torch.equal(Sr, Sr1)
+
+
 @pytest.mark.parametrize("mode", ["native", "bf16x3"])
 def test_sampling_is_deterministic(P, mode):
     n = 900
