@@ -73,6 +73,18 @@ WORKLOADS = {
     "batch512": dict(family="mixed_batch", count=512, seed=1004, dtype="f32", nrhs=16),
     "serve": dict(family="laplacian_schur", ks=[45, 71, 100, 141, 200], rtol=1e-6, leaf=256,
                   d0=128, step=64, dtype="f32", seed=1005, budget=150e9, load=0.8),
+    # the paper's Table 3 Toeplitz rows: SimpleToeplitz and QChemToeplitz
+    # (grid spacing 1), n = 80000, FP64, eps = 1e-8, 1e-6, 1e-4, 1e-2
+    "table3": dict(family="table3", n=80000, leaf=128, d0=64, step=32, dtype="f64", seed=1006,
+                   eps=[1e-8, 1e-6, 1e-4, 1e-2]),
+}
+# Table 3's printed values for those rows (max rank, HSS factors MB, ULV
+# factors MB), beside which the table3 workload reports its own
+TABLE3_PAPER = {
+    "SimpleToeplitz": {1e-8: (2, 14.6, 37.2), 1e-6: (2, 14.2, 37.0), 1e-4: (3, 13.3, 36.3),
+                       1e-2: (3, 13.2, 36.2)},
+    "QChemToeplitz": {1e-8: (169, 55.1, 152.7), 1e-6: (147, 42.1, 110.0),
+                      1e-4: (120, 33.3, 83.6), 1e-2: (30, 18.1, 42.7)},
 }
 
 METRIC = "HSS compress s"
@@ -180,7 +192,7 @@ def run_ours(args, wl):
     import __graft_entry__ as g
     g.build()
     import paper_1503_05464_gb300 as P
-    if wl["family"] in ("mixed_batch", "laplacian_schur"):
+    if wl["family"] in ("mixed_batch", "laplacian_schur", "table3"):
         return run_aux(args, wl, P, dev, rank, world)
 
     A = make_matrix(wl, dev).contiguous()
@@ -549,6 +561,49 @@ def run_serving(P, dev, stream, wl, count, load=None, warm=True):
     return summ
 
 
+def run_table3(P, dev, stream, wl):
+    """The paper's Table 3 Toeplitz rows at n = 80000 (FP64): per matrix and
+    eps, one compression after a warm-up of the first eps (CUDA events), the
+    max rank, HSS and ULV factor sizes, factorization time and the solve's
+    relative residual with one right-hand side, beside the printed values
+    (the paper's leaf size is not given; leaf 128 here)."""
+    import torch
+    import workloads as W
+    n = wl["n"]
+    rows = []
+    total = 0.0
+    for name, make in (("SimpleToeplitz", lambda: W.simple_toeplitz(n, np.float64, dev)),
+                       ("QChemToeplitz", lambda: W.qchem_toeplitz(n, 1.0, np.float64, dev))):
+        A = make().contiguous()
+        b = torch.randn(n, 1, dtype=torch.float64, device=dev,
+                        generator=torch.Generator(device=dev).manual_seed(wl["seed"]))
+        for q, eps in enumerate(wl["eps"]):
+            o = P.hss_default_opts(leaf_size=wl["leaf"], rtol=eps, d0=wl["d0"], d_step=wl["step"],
+                                   seed=wl["seed"] + 1)
+            if q == 0:
+                P.hss_compress(A, o, stream=stream).close()
+            t, h = _event_time(stream, lambda: P.hss_compress(A, o, stream=stream))
+            tf, _ = _event_time(stream, lambda: P.hss_factor(h, stream))
+            x = P.hss_solve(h, b)
+            r = float(torch.linalg.norm(A @ x - b) / torch.linalg.norm(b))
+            info = P.hss_info(h)
+            pr, pmb, pulv = TABLE3_PAPER[name][eps]
+            rows.append({"matrix": name, "eps": eps,
+                         "max_rank": max(info["max_rank_r"], info["max_rank_c"]),
+                         "paper_max_rank": pr, "hss_mb": info["bytes_hss"] / 1e6,
+                         "paper_hss_mb": pmb, "ulv_mb": info["bytes_ulv"] / 1e6,
+                         "paper_ulv_mb": pulv, "compress_s": t, "factor_s": tf,
+                         "passes": info["passes"], "solve_rel_residual": r})
+            total += t
+            h.close()
+        del A
+        torch.cuda.empty_cache()
+    return {"rows": rows, "n": n, "leaf": wl["leaf"], "compress_s_total": total,
+            "mean_compress_s": total / len(rows),
+            "note": "QChemToeplitz with grid spacing 1 (the ranks do not depend on it: it "
+                    "scales every off-diagonal entry alike); FP64 SIMT sampling"}
+
+
 def run_aux(args, wl, P, dev, rank, world):
     """The batch512 and serve workloads (each rank runs its own replica)."""
     import torch
@@ -561,6 +616,10 @@ def run_aux(args, wl, P, dev, rank, world):
             res = run_batching(P, dev, stream, count=wl["count"], seed=wl["seed"], nrhs=wl["nrhs"])
             value, key = res["batched_s_per_matrix"], "batching"
             ms = res["batched_s"] * 1e3
+        elif wl["family"] == "table3":
+            res = run_table3(P, dev, stream, wl)
+            value, key = res["mean_compress_s"], "table3"
+            ms = res["compress_s_total"] * 1e3
         else:
             res = run_serving(P, dev, stream, wl, count=args.requests or 2000)
             value, key = res["request_p50_s"], "serving"
@@ -572,10 +631,12 @@ def run_aux(args, wl, P, dev, rank, world):
     out = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": 1,
            "warmup": 1, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64-id", "data": "synthetic",
-           "config": {"workload": args.workload, "sample_mode": "bf16x3",
-                      "value_is": ("batched seconds per matrix (compress + factor + solve)"
-                                   if key == "batching" else
-                                   "p50 request latency, arrival to first solution")},
+           "config": {"workload": args.workload,
+                      "sample_mode": "native (f64)" if key == "table3" else "bf16x3",
+                      "value_is": {"batching": "batched seconds per matrix (compress + factor "
+                                               "+ solve)",
+                                   "serving": "p50 request latency, arrival to first solution",
+                                   "table3": "mean seconds per compression over the 8 runs"}[key]},
            key: res}
     clocks = clk.summary()
     if clocks:
@@ -667,6 +728,13 @@ def run_reference_aux(args, wl, O):
         items = [(W.build_matrix(sp, np.float32, "cpu").numpy().astype(np.float64),
                   sp["rtol"], sp["leaf"], sp["d0"], sp["step"], wl["nrhs"]) for sp in specs]
         sample = "compress + factor + 16-RHS solve of 2 matrices of the batch mix per step"
+    elif wl["family"] == "table3":
+        # the FP64 n = 80000 matrices take 51 GB each: the oracle runs both
+        # Toeplitz matrices at n = 4000 (eps 1e-6), unscaled
+        items = [(W.simple_toeplitz(4000).numpy(), 1e-6, wl["leaf"], wl["d0"], wl["step"], 1),
+                 (W.qchem_toeplitz(4000).numpy(), 1e-6, wl["leaf"], wl["d0"], wl["step"], 1)]
+        sample = ("compress + factor + 1-RHS solve of SimpleToeplitz and QChemToeplitz at "
+                  "n=4000, eps 1e-6 (not scaled to n=80000)")
     else:
         items = [(W.laplacian_schur(k, dtype=np.float32).numpy().astype(np.float64), wl["rtol"],
                   wl["leaf"], wl["d0"], wl["step"], 8) for k in wl["ks"][:2]]
@@ -697,7 +765,7 @@ def run_reference(args, wl):
         return
     import workloads  # noqa: F401
     from oracle import hss_oracle as O
-    if wl["family"] in ("mixed_batch", "laplacian_schur"):
+    if wl["family"] in ("mixed_batch", "laplacian_schur", "table3"):
         return run_reference_aux(args, wl, O)
     times = []
     ratio, desc = 1.0, ""

@@ -813,6 +813,35 @@ def test_full_size_bem60k_matches_oracle_golden(P):
 
 
 # ------------------------------------------------ ULV of large nodes (blocked path)
+def test_full_size_simple_toeplitz_matches_paper_table3(P):
+    """Table 3 (SimpleToeplitz, a_ii = n^2, a_ij = i - j, n = 80,000, double
+    precision): max HSS rank 2 at eps = 1e-8 and 1e-6 (the stored values,
+    tests/golden/simple_toeplitz_table3.txt); the ULV solve of this
+    diagonally dominant system to a relative residual of 1e-12."""
+    n = 80000
+    rows = []
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "simple_toeplitz_table3.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#") and not line.startswith("eps"):
+                eps, rank = line.split()
+                rows.append((float(eps), int(rank)))
+    assert rows
+    A = W.simple_toeplitz(n, dtype=np.float64, device=DEV)
+    b = torch.randn(n, 1, dtype=torch.float64, device=DEV,
+                    generator=torch.Generator(device=DEV).manual_seed(3))
+    for eps, want in rows:
+        h = P.hss_compress(A, leaf_size=128, rtol=eps, d0=64, d_step=32, seed=1007)
+        info = P.hss_info(h)
+        assert max(info["max_rank_r"], info["max_rank_c"]) == want, (eps, info["max_rank_r"])
+        P.hss_factor(h)
+        x = P.hss_solve(h, b)
+        assert float(torch.linalg.norm(A @ x - b) / torch.linalg.norm(b)) <= 1e-12
+        h.close()
+    del A
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_ulv_large_nodes_match_dense_solve(P, dtype):
     """Leaves of 512 and ranks of 200 put every node (and the root LU) on the

@@ -9,6 +9,8 @@ Matrix families (stand-ins for the paper's application matrices, Section 4.1):
 
 * ``toeplitz_inv_distance``  a_ij = 1/(1+|i-j|), a_ii = 10.
 * ``simple_toeplitz``        the paper's SimpleToeplitz: a_ii = n^2, a_ij = i-j.
+* ``qchem_toeplitz``         the paper's QChemToeplitz kinetic-energy matrix:
+                             a_ii = pi^2/6, a_ij = (-1)^(i-j) / ((i-j)^2 h^2).
 * ``gaussian_kernel``        K_ij = exp(-|x_i-x_j|^2/(2h^2)) + lambda*delta_ij on
                              points uniform in the unit cube.
 * ``bem_like``               a_ij = 1/(4*pi*|x_i-x_j|), a_ii = sqrt(n) on points
@@ -111,6 +113,26 @@ def simple_toeplitz(n: int, dtype=np.float64, device="cpu"):
     a = i[:, None] - i[None, :]
     a.diagonal().fill_(float(n) * n)
     return a.to(_tdtype(dtype))
+
+
+def qchem_toeplitz(n: int, spacing: float = 1.0, dtype=np.float64, device="cpu", chunk=2048):
+    """The paper's QChemToeplitz matrix (Section 4.1, a kinetic-energy matrix
+    from quantum chemistry): a_ii = pi^2/6, a_ij = (-1)^(i-j) / ((i-j)^2 h^2)
+    with grid spacing h (row blocks of `chunk`; every operation exact or
+    correctly rounded, so the bits are the same on the CPU and the GPU)."""
+    dev = _dev(device)
+    out = torch.empty((n, n), dtype=_tdtype(dtype), device=dev)
+    j = torch.arange(n, device=dev, dtype=torch.float64)
+    h2 = float(spacing) * float(spacing)
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        k = torch.arange(r0, r1, device=dev, dtype=torch.float64)[:, None] - j[None, :]
+        sgn = 1.0 - 2.0 * torch.remainder(k, 2.0)
+        blk = sgn / ((k * k) * h2)
+        idx = torch.arange(r0, r1, device=dev)
+        blk[idx - r0, idx] = math.pi ** 2 / 6.0
+        out[r0:r1] = blk.to(out.dtype)
+    return out
 
 
 def _tdtype(dtype):
