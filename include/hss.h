@@ -138,6 +138,40 @@ hss_status hss_compress(const void* A, int64_t n, int64_t lda, hss_dtype dtype,
                         const hss_opts* opts, void* stream, hss_t* out);
 
 /*
+ * Matrix-free access to A: the randomized compression needs only products
+ * of A and A^T with random blocks and selected entries of A (Section 2.2;
+ * A "does not need to be explicitly formed").  Both callbacks run on the
+ * thread that called hss_compress_matfree, queue their device work on
+ * `stream` (the compression's stream) and return 0 on success.  Every
+ * buffer they receive is device memory of the library, valid until the work
+ * they queue has completed; elements have the handle's dtype.
+ */
+typedef struct {
+  /* Sr[:, 0:c] = A R and, when Sc is not NULL, Sc[:, 0:c] = A^T R for the
+   * n x c block R (all rows; no leaf masking).  R, Sr, Sc row-major with
+   * leading dimensions ldr, lds. */
+  int (*sample)(void* ctx, int64_t c, const void* R, int64_t ldr, void* Sr, void* Sc,
+                int64_t lds, void* stream);
+  /* out[i * ldo + j] = A(rows[i], cols[j]) for i < nr, j < nc (rows, cols:
+   * int32 indices in [0, n)). */
+  int (*extract)(void* ctx, const int32_t* rows, int64_t nr, const int32_t* cols, int64_t nc,
+                 void* out, int64_t ldo, void* stream);
+  void* ctx;
+} hss_matfree;
+
+/*
+ * hss_compress_matfree -- hss_compress for a matrix given only through
+ * `ops` (host struct, read during the call).  The leaf blocks D and the
+ * generators B are extracted; the leaf samples are formed after the
+ * products as S(I_t,:) - D_t R(I_t,:) (Algorithm 1 as printed), and
+ * hss_opts.sample_mode is not used (the callback's arithmetic is).
+ * Errors: as hss_compress, plus INVALID when a callback returns non-zero
+ * (no handle).  Synchronizes `stream`.
+ */
+hss_status hss_compress_matfree(int64_t n, hss_dtype dtype, const hss_matfree* ops,
+                                const hss_opts* opts, void* stream, hss_t* out);
+
+/*
  * hss_matvec -- B = H X with the compressed form (Algorithm 2).
  *   X  device, n x nrhs row-major, ldx >= nrhs, the handle's dtype.
  *   B  device, n x nrhs row-major, ldb >= nrhs; must not overlap X.

@@ -79,11 +79,33 @@ struct Job {
   // only the row side is computed
   bool sym() const { return h->opts.symmetric != 0; }
   size_t id_first = 0;   // index of this job's first item in the round's ID table
+  // matrix-free (hss_compress_matfree): A is null, the caller's callbacks
+  // give the products and the entries; idx = 0, 1, ..., n - 1 on the device
+  const hss_matfree* mf = nullptr;
+  int32_t* idx = nullptr;
+
+  // out[i][j] = A(rows[i], cols[j]) through the caller's extract callback
+  Err mf_extract(const int32_t* rows, int nr, const int32_t* cols, int nc, T* out, int64_t ldo) {
+    if (nr <= 0 || nc <= 0) return ok();
+    if (mf->extract(mf->ctx, rows, nr, cols, nc, out, ldo, s) != 0)
+      return fail(HSS_ERR_INVALID, "hss_compress_matfree: the extract callback failed");
+    return ok();
+  }
+  // gathers of B blocks: from A, or through the callback
+  Err add_gather(std::vector<GatherItem<T>>& to, const GatherItem<T>& it) {
+    if (!mf) {
+      to.push_back(it);
+      return ok();
+    }
+    return mf_extract(it.rows, it.nr, it.cols, it.nc, it.out, it.nc);
+  }
 
   Job(hss_s* h_, const T* A_, int64_t lda_, cudaStream_t s_) : h(h_), A(A_), lda(lda_), s(s_) {}
   ~Job() { release(); }
 
   void release() {
+    dfree(idx, s);
+    idx = nullptr;
     dfree(R, s);
     dfree(Sr, s);
     dfree(Sc, s);
@@ -159,12 +181,64 @@ struct Job {
     // at least 60 times above that
     scratch.row_chain = h->opts.rtol >= 1e-4 ? 16 : 2;
     // symmetric: the row product only (S^c = S^r)
-    HSS_TRY(launch_sample<T>(A, n(), lda, R, h->dcap, c0, c1, Sr, sym() ? nullptr : Sc, h->dcap,
-                             leaf_of,
-                             h->opts.sample_mode, &scratch, s, timing ? &ms : nullptr));
+    if (mf) HSS_TRY(sample_matfree(c0, c1, timing ? &ms : nullptr));
+    else
+      HSS_TRY(launch_sample<T>(A, n(), lda, R, h->dcap, c0, c1, Sr, sym() ? nullptr : Sc,
+                               h->dcap, leaf_of, h->opts.sample_mode, &scratch, s,
+                               timing ? &ms : nullptr));
     ms_sample += ms;
     h->info.flops_sample += (sym() ? 2.0 : 4.0) * (double)n() * (double)n() * (double)(c1 - c0);
     h->info.ms_host_sample += now_ms() - t0;
+    return ok();
+  }
+
+  // Matrix-free sampling of columns [c0, c1): the caller's products, then
+  // Algorithm 1's leaf samples S(I_t,:) - D_t R(I_t,:) (S^c: D_t^T) by one
+  // batched GEMM over the leaves.
+  Err sample_matfree(int c0, int c1, float* ms_out) {
+    const int ld = h->dcap;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms_out) {
+      HSS_CUDA_TRY(cudaEventCreate(&e0));
+      HSS_CUDA_TRY(cudaEventCreate(&e1));
+      HSS_CUDA_TRY(cudaEventRecord(e0, s));
+    }
+    if (mf->sample(mf->ctx, c1 - c0, R + c0, ld, Sr + c0, sym() ? nullptr : Sc + c0, ld, s) != 0)
+      return fail(HSS_ERR_INVALID, "hss_compress_matfree: the sample callback failed");
+    std::vector<GemmItem<T>> items;
+    for (size_t i = 0; i < h->tree.nodes.size(); ++i) {
+      const TNode& nd = h->tree.nodes[i];
+      if (nd.c1 >= 0) continue;
+      const int m = nd.hi - nd.lo;
+      for (int side = 0; side < (sym() ? 1 : 2); ++side) {
+        T* S = (side == 0 ? Sr : Sc) + (int64_t)nd.lo * ld;
+        GemmItem<T> it{};
+        it.out = S;
+        it.ldo = ld;
+        it.rows = m;
+        it.inner = m;
+        it.c0 = c0;
+        it.c1 = c1;
+        it.X.p0 = S;
+        it.X.ld0 = ld;
+        it.Z.p0 = R + (int64_t)nd.lo * ld;
+        it.Z.ld0 = ld;
+        it.M = h->gen[i].D;
+        it.ldm = m;
+        it.m_trans = side;   // D_t, or D_t^T for the column samples
+        it.m_is_f64 = 0;
+        it.sign = T(-1);
+        items.push_back(it);
+      }
+    }
+    HSS_TRY(launch_gemm_batched<T>(items, s, nullptr, 0, lvl ? lvl : nullptr));
+    if (ms_out) {
+      HSS_CUDA_TRY(cudaEventRecord(e1, s));
+      HSS_CUDA_TRY(cudaEventSynchronize(e1));
+      HSS_CUDA_TRY(cudaEventElapsedTime(ms_out, e0, e1));
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
     return ok();
   }
 
@@ -187,6 +261,13 @@ struct Job {
       HSS_CUDA_TRY(cudaMemcpyAsync(leaf_of, lof.data(), N * sizeof(int32_t),
                                    cudaMemcpyHostToDevice, s));
     }
+    if (mf) {   // the index list 0, 1, ..., n - 1 that extraction reads from
+      std::vector<int32_t> hv(N);
+      for (int64_t i = 0; i < N; ++i) hv[i] = (int32_t)i;
+      HSS_TRY(dalloc_t(&idx, N, s));
+      HSS_CUDA_TRY(cudaMemcpyAsync(idx, hv.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      HSS_CUDA_TRY(cudaStreamSynchronize(s));
+    }
     std::vector<Copy2D<T>> dcopies;
     for (size_t i = 0; i < tr.nodes.size(); ++i) {   // D_tau = A(I_tau, I_tau)
       const TNode& nd = tr.nodes[i];
@@ -194,7 +275,10 @@ struct Job {
       int m = nd.hi - nd.lo;
       NodeGen& g = h->gen[i];
       HSS_TRY(h->store.alloc(&g.D, sizeof(T) * m * m, s));
-      dcopies.push_back({reinterpret_cast<T*>(g.D), A + (int64_t)nd.lo * lda + nd.lo, m, lda, m, m});
+      if (mf)
+        HSS_TRY(mf_extract(idx + nd.lo, m, idx + nd.lo, m, reinterpret_cast<T*>(g.D), m));
+      else
+        dcopies.push_back({reinterpret_cast<T*>(g.D), A + (int64_t)nd.lo * lda + nd.lo, m, lda, m, m});
       h->info.bytes_hss += sizeof(T) * (int64_t)m * m;
     }
     HSS_TRY(launch_copy_batched<T>(dcopies, s, nullptr));
@@ -231,10 +315,10 @@ struct Job {
       NodeGen& g0 = h->gen[0];
       HSS_TRY(h->store.alloc(&g0.B12, sizeof(T) * g1.kr * g2.kc, s));
       HSS_TRY(h->store.alloc(&g0.B21, sizeof(T) * g2.kr * g1.kc, s));
-      std::vector<GatherItem<T>> gi = {
-          {reinterpret_cast<T*>(g0.B12), g1.Ir, g2.Ic, g1.kr, g2.kc, A, lda},
-          {reinterpret_cast<T*>(g0.B21), g2.Ir, g1.Ic, g2.kr, g1.kc, A, lda}};
-      HSS_TRY(launch_gather_batched<T>(A, lda, gi, s, nullptr, 0, lvl));
+      std::vector<GatherItem<T>> gi;
+      HSS_TRY(add_gather(gi, {reinterpret_cast<T*>(g0.B12), g1.Ir, g2.Ic, g1.kr, g2.kc, A, lda}));
+      HSS_TRY(add_gather(gi, {reinterpret_cast<T*>(g0.B21), g2.Ir, g1.Ic, g2.kr, g1.kc, A, lda}));
+      if (!gi.empty()) HSS_TRY(launch_gather_batched<T>(A, lda, gi, s, nullptr, 0, lvl));
       h->info.bytes_hss += sizeof(T) * ((int64_t)g1.kr * g2.kc + (int64_t)g2.kr * g1.kc);
       g0.state = NODE_COMPRESSED;
       return finish();
@@ -284,8 +368,8 @@ struct Job {
       NodeGen& b = h->gen[nd.c2];
       HSS_TRY(h->store.alloc(&g.B12, sizeof(T) * a.kr * b.kc, s));
       HSS_TRY(h->store.alloc(&g.B21, sizeof(T) * b.kr * a.kc, s));
-      rd.gathers.push_back({reinterpret_cast<T*>(g.B12), a.Ir, b.Ic, a.kr, b.kc, A, lda});
-      rd.gathers.push_back({reinterpret_cast<T*>(g.B21), b.Ir, a.Ic, b.kr, a.kc, A, lda});
+      HSS_TRY(add_gather(rd.gathers, {reinterpret_cast<T*>(g.B12), a.Ir, b.Ic, a.kr, b.kc, A, lda}));
+      HSS_TRY(add_gather(rd.gathers, {reinterpret_cast<T*>(g.B21), b.Ir, a.Ic, b.kr, a.kc, A, lda}));
     }
     // local samples Y^r, Y^c (m x ld row-major; row j = column j of the ID input)
     auto make_loc = [&](int id, int c0) -> Err {
@@ -633,8 +717,9 @@ template struct Driver<double>;
 using namespace hss;
 
 static hss_status validate_opts(const void* A, int64_t n, int64_t lda, hss_dtype dtype,
-                                const hss_opts* opts, hss_opts* o, std::string* msg) {
-  if (!A || n < 1 || lda < n || (dtype != HSS_F32 && dtype != HSS_F64)) {
+                                const hss_opts* opts, hss_opts* o, std::string* msg,
+                                bool matfree = false) {
+  if ((!matfree && (!A || lda < n)) || n < 1 || (dtype != HSS_F32 && dtype != HSS_F64)) {
     *msg = "bad A, n, lda or dtype";
     return HSS_ERR_INVALID;
   }
@@ -814,14 +899,18 @@ void hss_batch_destroy(hss_batch_t b) {
   delete b;
 }
 
-hss_status hss_compress(const void* A, int64_t n, int64_t lda, hss_dtype dtype,
-                        const hss_opts* opts, void* stream, hss_t* out) {
+// One compression, from A or (mf not null) through the caller's callbacks.
+static hss_status compress_one(const void* A, int64_t n, int64_t lda, hss_dtype dtype,
+                               const hss_matfree* mf, const hss_opts* opts, void* stream,
+                               hss_t* out) {
   if (out) *out = nullptr;
   hss_opts o;
   std::string msg;
-  hss_status st = out ? validate_opts(A, n, lda, dtype, opts, &o, &msg) : HSS_ERR_INVALID;
+  const char* who = mf ? "hss_compress_matfree: " : "hss_compress: ";
+  hss_status st = out ? validate_opts(A, n, lda, dtype, opts, &o, &msg, mf != nullptr)
+                      : HSS_ERR_INVALID;
   if (st != HSS_OK) {
-    set_thread_error("hss_compress: " + (out ? msg : std::string("out is NULL")));
+    set_thread_error(who + (out ? msg : std::string("out is NULL")));
     return st;
   }
   const double t0 = now_ms();
@@ -843,10 +932,12 @@ hss_status hss_compress(const void* A, int64_t n, int64_t lda, hss_dtype dtype,
   };
   if (dtype == HSS_F32) {
     Job<float> jb(h.get(), (const float*)A, lda, h->stream);
+    jb.mf = mf;
     Driver<float> drv(h->stream);
     run(&jb, &drv);
   } else {
     Job<double> jb(h.get(), (const double*)A, lda, h->stream);
+    jb.mf = mf;
     Driver<double> drv(h->stream);
     run(&jb, &drv);
   }
@@ -864,6 +955,22 @@ hss_status hss_compress(const void* A, int64_t n, int64_t lda, hss_dtype dtype,
   }
   set_thread_error(e.msg);
   return e.st;
+}
+
+hss_status hss_compress(const void* A, int64_t n, int64_t lda, hss_dtype dtype,
+                        const hss_opts* opts, void* stream, hss_t* out) {
+  return compress_one(A, n, lda, dtype, nullptr, opts, stream, out);
+}
+
+hss_status hss_compress_matfree(int64_t n, hss_dtype dtype, const hss_matfree* ops,
+                                const hss_opts* opts, void* stream, hss_t* out) {
+  if (!ops || !ops->sample || !ops->extract) {
+    if (out) *out = nullptr;
+    set_thread_error("hss_compress_matfree: ops and both callbacks are required");
+    return HSS_ERR_INVALID;
+  }
+  const hss_matfree copy = *ops;
+  return compress_one(nullptr, n, n, dtype, &copy, opts, stream, out);
 }
 
 hss_status hss_compress_batched(int32_t count, const void* const* A, const int64_t* n,

@@ -57,6 +57,19 @@ class HssInfo(ctypes.Structure):
                 ("flops_id_solve", ctypes.c_double)]
 
 
+# hss_matfree (include/hss.h): the caller's products and entries of A
+SAMPLE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                             ctypes.c_void_p)
+EXTRACT_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                              ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                              ctypes.c_void_p)
+
+
+class HssMatfree(ctypes.Structure):
+    _fields_ = [("sample", SAMPLE_FN), ("extract", EXTRACT_FN), ("ctx", ctypes.c_void_p)]
+
+
 _lib = None
 EXPORTS = ["hss_default_opts", "hss_compress", "hss_matvec", "hss_factor", "hss_solve",
            "hss_info", "hss_node_ranks", "hss_destroy", "hss_last_error",
@@ -64,7 +77,7 @@ EXPORTS = ["hss_default_opts", "hss_compress", "hss_matvec", "hss_factor", "hss_
            "hss_pool_bytes", "hss_set_fault", "hss_tuner_stats",
            "hss_batch_create", "hss_batch_submit", "hss_batch_step", "hss_batch_take",
            "hss_batch_last_error", "hss_batch_destroy", "hss_compress_batched",
-           "hss_factor_batched", "hss_solve_batched"]
+           "hss_factor_batched", "hss_solve_batched", "hss_compress_matfree"]
 
 
 def load(path: str = LIB_PATH):
@@ -107,6 +120,8 @@ def load(path: str = LIB_PATH):
     L.hss_compress_batched.argtypes = [i32, vp, vp, vp, i32, ctypes.POINTER(HssOpts), i32, vp,
                                        vp, vp]
     L.hss_factor_batched.argtypes = [i32, vp, vp, vp]
+    L.hss_compress_matfree.argtypes = [i64, i32, ctypes.POINTER(HssMatfree),
+                                       ctypes.POINTER(HssOpts), vp, ctypes.POINTER(vp)]
     L.hss_solve_batched.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("hss_destroy", "hss_last_error", "hss_kernel_launches",
@@ -471,3 +486,74 @@ def hss_id_batched(Ys, rtol, atol=0.0, stream=None):
         mm = y.shape[0]
         out.append((kk, p[:mm], e[: (mm - kk) * kk].view(mm - kk, kk)))
     return out
+
+
+class _DeviceArray:
+    """A device buffer of the library seen through the CUDA array interface
+    (torch.as_tensor wraps it without a copy)."""
+
+    def __init__(self, ptr, shape, strides, typestr, itemsize):
+        self.__cuda_array_interface__ = {
+            "shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+            "strides": tuple(x * itemsize for x in strides), "version": 3}
+
+
+def _device_view(ptr, rows, cols, ld, dtype):
+    typestr, size = {torch.float32: ("<f4", 4), torch.float64: ("<f8", 8),
+                     torch.int32: ("<i4", 4)}[dtype]
+    shape = (rows,) if cols is None else (rows, cols)
+    strides = (1,) if cols is None else (ld, 1)
+    return torch.as_tensor(_DeviceArray(ptr, shape, strides, typestr, size), device="cuda")
+
+
+def hss_compress_matfree(n: int, sample, extract, dtype=torch.float32,
+                         opts: HssOpts | None = None, stream=None, **kw) -> HSS:
+    """Matrix-free compression (hss_compress_matfree).  sample(R, Sr, Sc)
+    must write Sr = A R and, when Sc is not None, Sc = A^T R (torch views of
+    the library's n x c device buffers); extract(rows, cols, out) must write
+    out[i, j] = A[rows[i], cols[j]] (int32 index tensors, an nr x nc view).
+    Both run with the compression's stream as torch's current stream."""
+    if opts is None:
+        opts = hss_default_opts(**kw)
+    failure = []
+    tstream = stream if stream is not None else torch.cuda.current_stream()
+    sp = _stream(tstream)
+
+    def _sample(ctx, c, r, ldr, sr, sc, lds, st):
+        try:
+            with torch.cuda.stream(tstream):
+                R = _device_view(r, n, c, ldr, dtype)
+                Sr = _device_view(sr, n, c, lds, dtype)
+                Sc = _device_view(sc, n, c, lds, dtype) if sc else None
+                sample(R, Sr, Sc)
+            return 0
+        except Exception as e:   # reported after the call returns
+            failure.append(e)
+            return 1
+
+    def _extract(ctx, rows, nr, cols, nc, out, ldo, st):
+        try:
+            with torch.cuda.stream(tstream):
+                rw = _device_view(rows, nr, None, 1, torch.int32)
+                cl = _device_view(cols, nc, None, 1, torch.int32)
+                extract(rw, cl, _device_view(out, nr, nc, ldo, dtype))
+            return 0
+        except Exception as e:
+            failure.append(e)
+            return 1
+
+    ops = HssMatfree(SAMPLE_FN(_sample), EXTRACT_FN(_extract), None)
+    out = ctypes.c_void_p()
+    st = load().hss_compress_matfree(n, HSS_F64 if dtype == torch.float64 else HSS_F32,
+                                     ctypes.byref(ops), ctypes.byref(opts), sp,
+                                     ctypes.byref(out))
+    if failure:
+        if out.value:
+            load().hss_destroy(out)
+        raise failure[0]
+    if st == HSS_ERR_RANK_CAP and out.value:
+        msg = load().hss_last_error(out).decode()
+        load().hss_destroy(out)
+        raise HssError(st, msg)
+    _check(st)
+    return HSS(out.value, n, dtype)

@@ -1,0 +1,155 @@
+"""Matrix-free compression (hss_compress_matfree): the randomized method needs
+only products of A and A^T with random blocks and selected entries of A
+(Section 2.2).  Checked against the oracle and the dense path on stored
+matrices, and on Toeplitz matrices too large to store, whose products come
+from an FFT and whose entries from the formula (Section 4.1, Table 3)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import hss_oracle as O  # noqa: E402
+import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1503_05464_gb300 as pkg
+    assert torch.cuda.is_available(), "the GPU tests need a CUDA device"
+    return pkg
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _dense_ops(A):
+    """Callbacks backed by a stored matrix (torch matmul, no TF32)."""
+    def sample(R, Sr, Sc):
+        Sr.copy_(A @ R)
+        if Sc is not None:
+            Sc.copy_(A.T @ R)
+
+    def extract(rows, cols, out):
+        out.copy_(A[rows.long()][:, cols.long()])
+    return sample, extract
+
+
+def test_matfree_known_ranks_exact(P):
+    """An unsymmetric matrix of random HSS generators with prescribed ranks
+    (FP64, rtol 1e-12): the matrix-free compression finds exactly those
+    ranks, like the dense path, and reconstructs A to 1e-10."""
+    A, true_ranks = W.random_hss(2048, 64, 10, seed=5, diag_shift=10.0)
+    At = torch.tensor(A, device=DEV)
+    sample, extract = _dense_ops(At)
+    kw = dict(leaf_size=64, rtol=1e-12, d0=24, d_step=16, seed=3)
+    h = P.hss_compress_matfree(2048, sample, extract, dtype=torch.float64, **kw)
+    hd = P.hss_compress(At, **kw)
+    ranks = P.hss_node_ranks(h)
+    assert ranks == P.hss_node_ranks(hd)
+    for i, (lo, hi, kr, kc) in enumerate(ranks):
+        if i:
+            assert (kr, kc) == (true_ranks[(lo, hi)],) * 2
+    H = P.hss_matvec(h, torch.eye(2048, dtype=torch.float64, device=DEV)).cpu().numpy()
+    assert _rel(H, A) <= 1e-10
+
+
+def test_matfree_gaussian_kernel_matches_oracle(P):
+    """Config-2 family at n = 4000 (FP32 storage, rtol 1e-4): ranks against
+    the FP64 oracle (the FP32-class check), reconstruction within the
+    oracle's bound, ULV solve within 10x the oracle's residual."""
+    n, leaf, rtol = 4000, 256, 1e-4
+    pts = W.points_unit_cube(n, 1002)
+    pts = pts[W.rcb_order(pts, leaf)]
+    At = W.gaussian_kernel(pts, 0.2, 1.0, dtype=np.float32, device=DEV)
+    A = At.cpu().numpy().astype(np.float64)
+    sample, extract = _dense_ops(At)
+    h = P.hss_compress_matfree(n, sample, extract, dtype=torch.float32, leaf_size=leaf,
+                               rtol=rtol, d0=128, d_step=64, seed=1003)
+    ho = O.compress(A, rtol, leaf_size=leaf, d0=128, d_step=64, seed=1003)
+    ranks = P.hss_node_ranks(h)
+    ro = ho.ranks()
+    for i, (lo, hi, kr, kc) in enumerate(ranks[1:], start=1):
+        assert (lo, hi) == (ho.nodes[i].lo, ho.nodes[i].hi)
+        assert abs(kr - ro[i][0]) <= max(3, 0.05 * ro[i][0])
+        assert abs(kc - ro[i][1]) <= max(3, 0.05 * ro[i][1])
+    H = P.hss_matvec(h, torch.eye(n, device=DEV)).cpu().numpy().astype(np.float64)
+    e_or = _rel(O.to_dense(ho), A)
+    assert _rel(H, A) <= 2 * max(rtol, e_or)
+    P.hss_factor(h)
+    b = np.random.default_rng(4).standard_normal((n, 4))
+    xs = P.hss_solve(h, torch.tensor(b, dtype=torch.float32, device=DEV)).cpu().numpy()
+    O.ulv_factor(ho)
+    xo = O.ulv_solve(ho, b)
+    assert _rel(A @ xs, b) <= 10 * max(_rel(A @ xo, b), 1e-6)
+
+
+def test_matfree_simple_toeplitz_beyond_storage(P):
+    """SimpleToeplitz at n = 200,000 (320 GB if stored in FP64): products by
+    FFT, entries by formula.  Max rank 2 at eps = 1e-8 (Table 3's value at
+    n = 80,000; the off-diagonal blocks have rank 2 at any n), the HSS
+    product matches the FFT product to 1e-10 and the ULV solve leaves a
+    relative residual of 1e-10."""
+    n = 200000
+    T = W.ToeplitzOperator(n, W.simple_toeplitz_symbol(n), DEV)
+    h = P.hss_compress_matfree(n, T.sample, T.extract, dtype=torch.float64, leaf_size=128,
+                               rtol=1e-8, d0=16, d_step=16, seed=11)
+    info = P.hss_info(h)
+    assert max(info["max_rank_r"], info["max_rank_c"]) == 2
+    x = torch.randn(n, 2, dtype=torch.float64, device=DEV,
+                    generator=torch.Generator(device=DEV).manual_seed(1))
+    ax = T.matmul(x)
+    assert float(torch.linalg.norm(P.hss_matvec(h, x) - ax) / torch.linalg.norm(ax)) <= 1e-10
+    P.hss_factor(h)
+    y = P.hss_solve(h, ax)
+    assert float(torch.linalg.norm(T.matmul(y) - ax) / torch.linalg.norm(ax)) <= 1e-10
+
+
+@pytest.mark.parametrize("symmetric", [False, True])
+def test_matfree_qchem_toeplitz_beyond_storage(P, symmetric):
+    """QChemToeplitz at n = 200,000 (eps 1e-6), general and symmetric: the
+    HSS product matches the FFT product within 10 eps (the FP64 oracle at
+    n = 4000, leaf 128: 7.5e-7), and the max rank stays small (the oracle:
+    21 at n = 2000, 27 at n = 4000; Section 4.1 says it grows slowly with
+    n)."""
+    n, rtol = 200000, 1e-6
+    T = W.ToeplitzOperator(n, W.qchem_toeplitz_symbol(1.0), DEV)
+    h = P.hss_compress_matfree(n, T.sample, T.extract, dtype=torch.float64, leaf_size=128,
+                               rtol=rtol, d0=64, d_step=32, seed=12, symmetric=symmetric)
+    info = P.hss_info(h)
+    mr = max(info["max_rank_r"], info["max_rank_c"])
+    assert 1 <= mr <= 200, mr
+    x = torch.randn(n, 2, dtype=torch.float64, device=DEV,
+                    generator=torch.Generator(device=DEV).manual_seed(2))
+    ax = T.matmul(x)
+    assert float(torch.linalg.norm(P.hss_matvec(h, x) - ax) / torch.linalg.norm(ax)) <= 10 * rtol
+    if symmetric:
+        assert all(kr == kc for (_, _, kr, kc) in P.hss_node_ranks(h)[1:])
+
+
+def test_matfree_callback_failure_is_reported(P):
+    """A callback that raises: the call fails with that exception, no handle
+    is left and the library's pool returns to its bytes in use."""
+    n = 1000
+    At = W.toeplitz_inv_distance(n, dtype=np.float64, device=DEV)
+    sample, extract = _dense_ops(At)
+    calls = {"n": 0}
+
+    def bad_sample(R, Sr, Sc):
+        calls["n"] += 1
+        if calls["n"] >= 2:
+            raise ValueError("planted failure")
+        sample(R, Sr, Sc)
+
+    torch.cuda.synchronize()
+    used0, _ = P.hss.hss_pool_bytes()
+    with pytest.raises(ValueError, match="planted failure"):
+        P.hss_compress_matfree(n, bad_sample, extract, dtype=torch.float64, leaf_size=64,
+                               rtol=1e-10, d0=8, d_step=8, seed=1)
+    torch.cuda.synchronize()
+    assert P.hss.hss_pool_bytes()[0] == used0

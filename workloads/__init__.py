@@ -11,6 +11,8 @@ Matrix families (stand-ins for the paper's application matrices, Section 4.1):
 * ``simple_toeplitz``        the paper's SimpleToeplitz: a_ii = n^2, a_ij = i-j.
 * ``qchem_toeplitz``         the paper's QChemToeplitz kinetic-energy matrix:
                              a_ii = pi^2/6, a_ij = (-1)^(i-j) / ((i-j)^2 h^2).
+* ``ToeplitzOperator``       either Toeplitz matrix without storage: FFT
+                             products and entries by formula (matrix-free).
 * ``gaussian_kernel``        K_ij = exp(-|x_i-x_j|^2/(2h^2)) + lambda*delta_ij on
                              points uniform in the unit cube.
 * ``bem_like``               a_ij = 1/(4*pi*|x_i-x_j|), a_ii = sqrt(n) on points
@@ -133,6 +135,56 @@ def qchem_toeplitz(n: int, spacing: float = 1.0, dtype=np.float64, device="cpu",
         blk[idx - r0, idx] = math.pi ** 2 / 6.0
         out[r0:r1] = blk.to(out.dtype)
     return out
+
+
+def simple_toeplitz_symbol(n: int):
+    """t(k) of SimpleToeplitz (a_ij = t(i - j)): n^2 at k = 0, else k."""
+    return lambda k: torch.where(k == 0, torch.full_like(k, float(n) * n), k)
+
+
+def qchem_toeplitz_symbol(spacing: float = 1.0):
+    """t(k) of QChemToeplitz: pi^2/6 at k = 0, else (-1)^k / (k^2 h^2)."""
+    h2 = float(spacing) * float(spacing)
+
+    def t(k):
+        sgn = 1.0 - 2.0 * torch.remainder(k, 2.0)
+        return torch.where(k == 0, torch.full_like(k, math.pi ** 2 / 6.0),
+                           sgn / (torch.where(k == 0, torch.ones_like(k), k * k) * h2))
+    return t
+
+
+class ToeplitzOperator:
+    """An n x n Toeplitz matrix a_ij = t(i - j) that is never stored (FP64,
+    on the device): products with A and A^T through a circulant embedding
+    of length 2n (FFT), entries from t.  `sample` and `extract` have the
+    form of the matrix-free callbacks of hss_compress_matfree."""
+
+    def __init__(self, n, t, device="cuda"):
+        self.n, self.t, self.dev = n, t, _dev(device)
+        k = torch.arange(n, dtype=torch.float64, device=self.dev)
+        col, row = t(k), t(-k)               # first column t(i), first row t(-j)
+        c = torch.cat([col, col.new_zeros(1), row[1:].flip(0)])
+        ct = torch.cat([row, row.new_zeros(1), col[1:].flip(0)])
+        self.fc, self.fct = torch.fft.rfft(c), torch.fft.rfft(ct)
+
+    def _mul(self, f, X):
+        n = self.n
+        Xp = torch.zeros((2 * n, X.shape[1]), dtype=torch.float64, device=self.dev)
+        Xp[:n] = X
+        return torch.fft.irfft(f[:, None] * torch.fft.rfft(Xp, dim=0), n=2 * n, dim=0)[:n]
+
+    def matmul(self, X):
+        """A X for an n x k FP64 device block."""
+        return self._mul(self.fc, X)
+
+    def sample(self, R, Sr, Sc):
+        Sr.copy_(self._mul(self.fc, R))
+        if Sc is not None:
+            Sc.copy_(self._mul(self.fct, R))
+
+    def extract(self, rows, cols, out):
+        k = rows.double()[:, None] - cols.double()[None, :]
+        out.copy_(self.t(k))
 
 
 def _tdtype(dtype):
