@@ -174,8 +174,8 @@ class ToeplitzOperator:
         return torch.fft.irfft(f[:, None] * torch.fft.rfft(Xp, dim=0), n=2 * n, dim=0)[:n]
 
     def matmul(self, X):
-        """A X for an n x k FP64 device block."""
-        return self._mul(self.fc, X)
+        """A X for an n x k FP64 device block (row-major result)."""
+        return self._mul(self.fc, X).contiguous()
 
     def sample(self, R, Sr, Sc):
         Sr.copy_(self._mul(self.fc, R))
