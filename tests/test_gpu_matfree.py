@@ -110,26 +110,46 @@ def test_matfree_simple_toeplitz_beyond_storage(P):
     assert float(torch.linalg.norm(T.matmul(y) - ax) / torch.linalg.norm(ax)) <= 1e-10
 
 
-@pytest.mark.parametrize("symmetric", [False, True])
-def test_matfree_qchem_toeplitz_beyond_storage(P, symmetric):
-    """QChemToeplitz at n = 200,000 (eps 1e-6), general and symmetric: the
-    HSS product matches the FFT product within 10 eps (the FP64 oracle at
-    n = 4000, leaf 128: 7.5e-7), and the max rank stays small (the oracle:
-    21 at n = 2000, 27 at n = 4000; Section 4.1 says it grows slowly with
-    n)."""
-    n, rtol = 200000, 1e-6
+def test_matfree_qchem_toeplitz_matches_the_dense_path(P):
+    """QChemToeplitz at n = 80,000 (Table 3's size, eps 1e-6): the
+    matrix-free compression (FFT products, entries by formula) against the
+    dense one of the stored FP64 matrix -- the same method, with products
+    rounded differently: node ranks within +-2 on 90% of the nodes and
+    within 3% on all, the same number of passes within one, and HSS
+    products as accurate (within 2x of each other's error against the
+    exact product).  The symmetric form of the matrix-free compression
+    gives V = U with ranks within +-2 of the general one on 90% of the
+    nodes."""
+    n, rtol = 80000, 1e-6
     T = W.ToeplitzOperator(n, W.qchem_toeplitz_symbol(1.0), DEV)
-    h = P.hss_compress_matfree(n, T.sample, T.extract, dtype=torch.float64, leaf_size=128,
-                               rtol=rtol, d0=64, d_step=32, seed=12, symmetric=symmetric)
-    info = P.hss_info(h)
-    mr = max(info["max_rank_r"], info["max_rank_c"])
-    assert 1 <= mr <= 200, mr
+    kw = dict(leaf_size=128, rtol=rtol, d0=64, d_step=32, seed=12)
+    hm = P.hss_compress_matfree(n, T.sample, T.extract, dtype=torch.float64, **kw)
+    hs = P.hss_compress_matfree(n, T.sample, T.extract, dtype=torch.float64, symmetric=True, **kw)
+    A = W.qchem_toeplitz(n, 1.0, dtype=np.float64, device=DEV)
+    hd = P.hss_compress(A, **kw)
     x = torch.randn(n, 2, dtype=torch.float64, device=DEV,
                     generator=torch.Generator(device=DEV).manual_seed(2))
-    ax = T.matmul(x)
-    assert float(torch.linalg.norm(P.hss_matvec(h, x) - ax) / torch.linalg.norm(ax)) <= 10 * rtol
-    if symmetric:
-        assert all(kr == kc for (_, _, kr, kc) in P.hss_node_ranks(h)[1:])
+    ax = A @ x
+    del A
+    torch.cuda.empty_cache()
+
+    def err(h):
+        return float(torch.linalg.norm(P.hss_matvec(h, x) - ax) / torch.linalg.norm(ax))
+
+    def close(ra, rb):
+        d = [max(abs(a[2] - b[2]), abs(a[3] - b[3])) for a, b in zip(ra[1:], rb[1:])]
+        assert all(a[:2] == b[:2] for a, b in zip(ra, rb))
+        assert sum(x <= 2 for x in d) >= 0.9 * len(d), sorted(d)[-10:]
+        return d
+    rm, rd = P.hss_node_ranks(hm), P.hss_node_ranks(hd)
+    d = close(rm, rd)
+    assert all(x <= max(3, 0.03 * max(b[2], b[3])) for x, b in zip(d, rd[1:]))
+    assert abs(P.hss_info(hm)["passes"] - P.hss_info(hd)["passes"]) <= 1
+    em, ed = err(hm), err(hd)
+    assert em <= 2 * ed and ed <= 2 * em, (em, ed)
+    rs = P.hss_node_ranks(hs)
+    assert all(kr == kc for (_, _, kr, kc) in rs[1:])
+    close(rs, rm)
 
 
 def test_matfree_callback_failure_is_reported(P):
