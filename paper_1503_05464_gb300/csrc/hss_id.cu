@@ -52,6 +52,7 @@
 #include <cstdlib>
 #include <map>
 #include <mutex>
+#include <cstddef>
 #include <tuple>
 
 namespace cg = cooperative_groups;
@@ -192,13 +193,15 @@ __device__ __forceinline__ double team_update_dot(int i, int d, int member, bool
 // A CTA's pivot candidate as its peers receive it: with the column's exact
 // residual (entry alpha at the next pivot row, sum st of the squares below
 // it) every CTA can form the reflector without waiting for the column.
-struct Cand {
+struct alignas(16) Cand {
   long long v;    // bit pattern of its largest active residual norm (LLONG_MIN: none)
   int j;          // its global column index
   int pad;
   double st;      // sum of x_c^2 below the next pivot row
   double alpha;   // x at the next pivot row
 };
+// (v, j) are read together as one 16-byte load
+static_assert(offsetof(Cand, j) == 8 && sizeof(Cand) == 32, "Cand layout");
 
 // A node side spread over more CTAs than a cluster holds (a "group"): the
 // group's CTAs meet at a barrier in global memory (a counter per item) and
@@ -448,13 +451,29 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     const Cand* gc = nullptr;
     if constexpr (GRP) {
       gc = ga.cand + (static_cast<size_t>(item) * 2 + slot) * C;
-      for (int r = lane; r < C; r += 32) {
-        const long long v = __ldcg(&gc[r].v);
-        const int j = __ldcg(&gc[r].j);
-        if (v > bv || (v == bv && j < p)) {
-          bv = v;
-          p = j;
+      // every candidate's (v, j) is loaded before any is compared: one round
+      // trip to L2 for up to 320 CTAs instead of one per 32
+      constexpr int U = 10;
+      for (int r0 = lane; r0 < C; r0 += 32 * U) {
+        long long vv[U];
+        int jj[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int r = r0 + 32 * u;
+          vv[u] = LLONG_MIN;
+          jj[u] = INT_MAX;
+          if (r < C) {
+            const longlong2 x = __ldcg(reinterpret_cast<const longlong2*>(&gc[r]));
+            vv[u] = x.x;
+            jj[u] = static_cast<int>(x.y & 0xffffffffll);
+          }
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (vv[u] > bv || (vv[u] == bv && jj[u] < p)) {
+            bv = vv[u];
+            p = jj[u];
+          }
       }
     } else if (lane < C) {
       bv = cands[slot][lane].v;
@@ -791,8 +810,11 @@ class TeamTuner {
     return t;
   }
   // team index for this launch; *trial receives events to record around it
-  // (nullptr when the class has settled)
-  int choose(const Key& k, int model_ti, int min_ti, double units, Trial** trial) {
+  // (nullptr when the class has settled).  half_group: the launch may also
+  // run with half as many CTAs per item (a spread-out launch whose CTAs own
+  // few columns each): that candidate is the model's team index + 8.
+  int choose(const Key& k, int model_ti, int min_ti, double units, Trial** trial,
+             bool half_group = false) {
     std::lock_guard<std::mutex> lock(mu_);
     harvest();
     *trial = nullptr;
@@ -801,6 +823,7 @@ class TeamTuner {
     if (c.cand.empty()) {
       for (int t : {model_ti, model_ti - 1, model_ti + 1})
         if (t >= min_ti && t <= 5) c.cand.push_back(t);
+      if (half_group) c.cand.push_back(model_ti + 8);
       c.sum.assign(c.cand.size(), 0.0);
       c.cnt.assign(c.cand.size(), 0);
       c.issued.assign(c.cand.size(), 0);
@@ -1097,6 +1120,18 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
   Err res;
   bool done = false;
   if (gsz > 0) {
+    // the tuner may also try half as many CTAs per item when each owns few
+    // columns (the per-step serial part -- barrier, candidates, reflector --
+    // then weighs less against the columns' work); results do not depend on
+    // the choice
+    TeamTuner::Trial* trial = nullptr;
+    const bool half_ok = (max_m + gsz - 1) / gsz < 32 && gsz >= 4 &&
+                         need(gsz / 2) <= 227 * 1024 - 2048;
+    const int choice = TeamTuner::get().choose(
+        TeamTuner::Key{dev_ordinal, two_per_sm ? 2 : 1, 0, ilog2(max_m), ilog2(d), ilog2(count)},
+        team_index(gsz, true), 2, units, &trial, half_ok);
+    const int ti = choice & 7;
+    if (choice >> 3) gsz /= 2;
     const size_t gsmem = need(gsz);
     // candidates [count][2][gsz], then the counters, the abort flag and the
     // error code (zeroed together)
@@ -1128,10 +1163,6 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
     gattr[0].val.cooperative = 1;
     gcfg.attrs = gattr;
     gcfg.numAttrs = 1;
-    TeamTuner::Trial* trial = nullptr;
-    const int ti = TeamTuner::get().choose(
-        TeamTuner::Key{dev_ordinal, two_per_sm ? 2 : 1, 0, ilog2(max_m), ilog2(d), ilog2(count)},
-        team_index(gsz, true), 2, units, &trial);
     if (trial) cudaEventRecord(trial->e0, s);
     cudaError_t e = cudaLaunchKernelEx(&gcfg, (two_per_sm ? group_kernels2() : group_kernels())[ti],
                                        items_dev,
