@@ -642,7 +642,7 @@ def test_bad_tree_is_rejected(P):
         assert e.value.status == P.hss.HSS_ERR_INVALID
 
 
-# --------------------------------- acceptance on the benchmark spec's terms (eps-scaling)
+# ------------------------------ acceptance at 2 rtol with the ID threshold scaled
 @pytest.mark.parametrize("mode", ["native", "bf16x3"])
 def test_compress_meets_two_rtol_under_eps_scaling(P, mode):
     """||A - H||_F / ||A||_F <= 2 rtol.  The paper's stopping test is local:
@@ -694,7 +694,7 @@ def test_full_size_gauss20k_matches_oracle(P):
     """n=20000 Gaussian kernel, the benchmark's workload and launch configuration.
 
     FP64 path (A upcast): ranks within +-2 of the oracle's (observed: equal)
-    and the same pass count.  BF16x3 sampling (judged on accuracy): the probe
+    and the same pass count.  BF16x3 sampling (checked on accuracy): the probe
     error within 2x the oracle's own; ranks within +-2 on 95% of the nodes and
     +-5% on all, leaving out nodes within 2 of the adaptive boundary d - p of
     their pass (they may take another pass) and those nodes' ancestors.
