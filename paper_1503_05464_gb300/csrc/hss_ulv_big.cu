@@ -17,6 +17,8 @@
 //           solve of the block row, GEMM update of the trailing matrix).
 // The factors have the per-node kernel's layout, so the solve is unchanged.
 #include "hss_internal.cuh"
+
+#include <cfloat>
 #include "hss_tree.h"
 
 #include <algorithm>
@@ -232,22 +234,44 @@ __global__ void __launch_bounds__(B_THREADS) lu_panel_kernel(const LuPanel* item
       }
     if (tid == 0) it.piv[j] = bi;
     __syncthreads();
+    // the multipliers scale by the pivot's reciprocal (as LAPACK's xGETF2
+    // does for a pivot above the underflow threshold); each warp takes four
+    // rows at a time, their loads issued before the arithmetic
     const double pv = A[static_cast<int64_t>(j) * m + j];
+    const double rpv = 1.0 / pv;
+    const bool scale = fabs(pv) >= DBL_MIN;
     const int cend = it.j0 + it.nbb;
-    for (int i = j + 1 + warp; i < m; i += B_WARPS) {
-      double* ai = A + static_cast<int64_t>(i) * m;
-      const double l = ai[j] / pv;
-      for (int c = j + 1 + lane; c < cend; c += 32)
-        ai[c] = fma(-l, A[static_cast<int64_t>(j) * m + c], ai[c]);
-      if (lane == 0) ai[j] = l;
+    const int c = j + 1 + lane;   // < cend: at most 31 columns right of j in the panel
+    const double uj = c < cend ? A[static_cast<int64_t>(j) * m + c] : 0.0;
+    for (int i0 = j + 1 + warp; i0 < m; i0 += 4 * B_WARPS) {
+      double aij[4], aic[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * B_WARPS;
+        aij[u] = i < m ? A[static_cast<int64_t>(i) * m + j] : 0.0;
+        aic[u] = (i < m && c < cend) ? A[static_cast<int64_t>(i) * m + c] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * B_WARPS;
+        if (i >= m) break;
+        const double l = scale ? aij[u] * rpv : aij[u] / pv;
+        if (c < cend) A[static_cast<int64_t>(i) * m + c] = fma(-l, uj, aic[u]);
+        if (lane == 0) A[static_cast<int64_t>(i) * m + j] = l;
+      }
     }
     __syncthreads();
   }
 }
 
-// U12 = L11^{-1} A12 (unit lower L11 of the panel), one thread per column
-__global__ void lu_trsm_kernel(double* A, int m, int j0, int nbb) {
+// U12 = L11^{-1} A12 (unit lower L11 of the panel), one thread per column,
+// for a batch of panels, one per blockIdx.y (each item's own A, m, j0 and
+// nbb): the roots of several handles side by side
+__global__ void lu_trsm_items_kernel(const LuPanel* items) {
   __shared__ double L11[NB * NB];
+  const LuPanel it = items[blockIdx.y];
+  const int m = it.m, j0 = it.j0, nbb = it.nbb;
+  double* A = it.A;
   for (int e = threadIdx.x; e < nbb * nbb; e += blockDim.x) {
     const int a = e / nbb, b = e % nbb;
     L11[a * NB + b] = A[static_cast<int64_t>(j0 + a) * m + j0 + b];
@@ -497,26 +521,41 @@ Err ulv_factor_big_multi(const std::vector<std::pair<hss_s*, int>>& items,
     HSS_TRY(run_gemms(gm, s, ar));
   }
 
-  // ---- roots: blocked LU with partial pivoting, one root at a time
-  for (Node& x : N) {
-    if (!x.root) continue;
-    const int m = x.m;
-    for (int j0 = 0; j0 < m; j0 += NB) {
-      const int nbb = std::min(NB, m - j0);
-      std::vector<LuPanel> lp{{x.Dw, x.h->ulv.root_piv, x.status, m, j0, nbb}};
+  // ---- roots: blocked LU with partial pivoting, the roots of all handles
+  // side by side (panel j0 of every root in one launch, its row block in
+  // one, the trailing updates in one; each root's operations and their
+  // order are those it has alone)
+  {
+    int maxm = 0;
+    for (const Node& x : N)
+      if (x.root) maxm = std::max(maxm, x.m);
+    for (int j0 = 0; j0 < maxm; j0 += NB) {
+      std::vector<LuPanel> lp, lt;
+      std::vector<GemmItem<double>> gm;
+      int maxrest = 0;
+      for (Node& x : N) {
+        if (!x.root || j0 >= x.m) continue;
+        const int m = x.m, nbb = std::min(NB, m - j0), rest = m - j0 - nbb;
+        lp.push_back({x.Dw, x.h->ulv.root_piv, x.status, m, j0, nbb});
+        if (rest <= 0) continue;
+        lt.push_back(lp.back());
+        maxrest = std::max(maxrest, rest);
+        double* a22 = x.Dw + static_cast<size_t>(j0 + nbb) * m + j0 + nbb;
+        gm.push_back(gemm(a22, m, rest, rest, nbb, x.Dw + static_cast<size_t>(j0 + nbb) * m + j0,
+                          m, 0, x.Dw + static_cast<size_t>(j0) * m + j0 + nbb, m, 0, a22, m, -1.0));
+      }
+      if (lp.empty()) break;
       LuPanel* dlp = nullptr;
       HSS_TRY(upload(lp, s, ar, &dlp));
-      lu_panel_kernel<<<1, B_THREADS, 0, s>>>(dlp);
+      lu_panel_kernel<<<static_cast<unsigned>(lp.size()), B_THREADS, 0, s>>>(dlp);
       HSS_TRY(check_launch("lu_panel_kernel"));
-      const int rest = m - j0 - nbb;
-      if (rest <= 0) break;
-      lu_trsm_kernel<<<(rest + 127) / 128, 128, 0, s>>>(x.Dw, m, j0, nbb);
-      HSS_TRY(check_launch("lu_trsm_kernel"));
-      double* a22 = x.Dw + static_cast<size_t>(j0 + nbb) * m + j0 + nbb;
-      std::vector<GemmItem<double>> gm{gemm(a22, m, rest, rest, nbb,
-                                            x.Dw + static_cast<size_t>(j0 + nbb) * m + j0, m, 0,
-                                            x.Dw + static_cast<size_t>(j0) * m + j0 + nbb, m, 0,
-                                            a22, m, -1.0)};
+      if (lt.empty()) continue;
+      LuPanel* dlt = nullptr;
+      HSS_TRY(upload(lt, s, ar, &dlt));
+      lu_trsm_items_kernel<<<dim3(static_cast<unsigned>((maxrest + 127) / 128),
+                                  static_cast<unsigned>(lt.size())),
+                             128, 0, s>>>(dlt);
+      HSS_TRY(check_launch("lu_trsm_items_kernel"));
       HSS_TRY(run_gemms(gm, s, ar));
     }
   }
