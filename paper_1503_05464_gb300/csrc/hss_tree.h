@@ -110,6 +110,26 @@ struct DownBig {
   int child;
   const double* xp;
 };
+// one handle's share of a level of the blocked (large-node) solve: the
+// upward sweep's nodes `ids`, or the downward sweep's large children `kids`
+struct UpBigWork {
+  hss_s* h;
+  std::vector<int> ids;
+  const std::vector<UlvBufs>* bufs;
+  const void* B;
+  int64_t ldb;
+  int nr;
+  hss_status* status;
+};
+struct DownBigWork {
+  hss_s* h;
+  std::vector<DownBig> kids;
+  const std::vector<UlvBufs>* bufs;
+  int nr;
+  void* X;
+  int64_t ldx;
+  hss_status* status;
+};
 void fill_info(hss_s* h);
 
 }  // namespace hss

@@ -24,10 +24,8 @@ namespace hss {
 size_t ulv_big_min_m();
 Err ulv_factor_big_multi(const std::vector<std::pair<hss_s*, int>>& items,
                          const std::vector<int32_t*>& status, cudaStream_t s);
-Err ulv_solve_up_big(hss_s* h, const std::vector<int>& ids, const std::vector<UlvBufs>& bufs,
-                     const void* B, int64_t ldb, int nr, cudaStream_t s);
-Err ulv_solve_down_big(hss_s* h, const std::vector<DownBig>& kids, const std::vector<UlvBufs>& bufs,
-                       int nr, void* X, int64_t ldx, cudaStream_t s);
+Err ulv_solve_up_big_multi(const std::vector<UpBigWork>& work, cudaStream_t s);
+Err ulv_solve_down_big_multi(const std::vector<DownBigWork>& work, cudaStream_t s);
 
 namespace {
 
@@ -844,8 +842,8 @@ SolItem up_item(const SolveJob& j, int id) {
 
 // Solves every job: the upward sweep takes depth maxdepth - r of every
 // handle in round r, the downward sweep depth r; the small nodes of all
-// handles share one launch per round, the large ones take the blocked path
-// handle by handle.  Per node the arithmetic is that of a single solve.
+// handles share one launch per round, the large ones the blocked path's
+// launches of that round.  Per node the arithmetic is that of a single solve.
 void solve_many(std::vector<SolveJob>& jobs, cudaStream_t s) {
   int rounds = 0;
   const int f64 = (!jobs.empty() && jobs[0].h->dtype == HSS_F64) ? 1 : 0;
@@ -868,8 +866,17 @@ void solve_many(std::vector<SolveJob>& jobs, cudaStream_t s) {
       }
   };
   Err e;
+  // a failure of a shared big-path launch fails every handle that had work in it
+  auto fail_work = [](auto& work, const Err& eb) {
+    for (auto& w : work)
+      if (*w.status == HSS_OK) {
+        w.h->err = eb.msg;
+        *w.status = eb.st;
+      }
+  };
   for (int r = 0; r < rounds && e.st == HSS_OK; ++r) {
     std::vector<SolItem> items;
+    std::vector<UpBigWork> bigw;
     for (SolveJob& j : jobs) {
       if (*j.st != HSS_OK) continue;
       const int depth = j.h->tree.maxdepth - r;
@@ -879,12 +886,10 @@ void solve_many(std::vector<SolveJob>& jobs, cudaStream_t s) {
         if (is_big(j.h, id)) big.push_back(id);
         else items.push_back(up_item(j, id));
       }
-      Err eb = ulv_solve_up_big(j.h, big, j.bufs, j.B, j.ldb, j.nr, s);
-      if (eb.st) {
-        j.h->err = eb.msg;
-        *j.st = eb.st;
-      }
+      if (!big.empty()) bigw.push_back({j.h, big, &j.bufs, j.B, j.ldb, j.nr, j.st});
     }
+    Err eb = ulv_solve_up_big_multi(bigw, s);
+    if (eb.st) fail_work(bigw, eb);
     if (items.empty()) continue;
     SolItem* dev = nullptr;
     e = upload_and_launch(items, s, &dev);
@@ -904,6 +909,7 @@ void solve_many(std::vector<SolveJob>& jobs, cudaStream_t s) {
   }
   for (int r = 0; r < rounds && e.st == HSS_OK; ++r) {
     std::vector<DownItem> items;
+    std::vector<DownBigWork> bigw;
     for (SolveJob& j : jobs) {
       if (*j.st != HSS_OK) continue;
       const hss_s* h = j.h;
@@ -940,12 +946,10 @@ void solve_many(std::vector<SolveJob>& jobs, cudaStream_t s) {
           items.push_back(it);
         }
       }
-      Err eb = ulv_solve_down_big(j.h, bigkids, j.bufs, j.nr, j.X, j.ldx, s);
-      if (eb.st) {
-        j.h->err = eb.msg;
-        *j.st = eb.st;
-      }
+      if (!bigkids.empty()) bigw.push_back({j.h, bigkids, &j.bufs, j.nr, j.X, j.ldx, j.st});
     }
+    Err eb = ulv_solve_down_big_multi(bigw, s);
+    if (eb.st) fail_work(bigw, eb);
     if (items.empty()) continue;
     DownItem* dev = nullptr;
     e = upload_and_launch(items, s, &dev);

@@ -758,88 +758,111 @@ Err blocked_trsm(const std::vector<TriItem>& base, const std::vector<int>& ord, 
 
 }  // namespace
 
-// Upward sweep of the solve (Algorithm 4) for the large nodes `ids` of one
-// level; buffers of every node are given by `bufs`.
-Err ulv_solve_up_big(hss_s* h, const std::vector<int>& ids, const std::vector<UlvBufs>& bufs,
-                     const void* B, int64_t ldb, int nr, cudaStream_t s) {
-  if (ids.empty()) return ok();
-  const Tree& tr = h->tree;
-  const UlvFactors& F = h->ulv;
-  const int f64 = h->dtype == HSS_F64;
-  const size_t esz = f64 ? 8 : 4;
+// Upward sweep of the solve (Algorithm 4) for the large nodes of one level of
+// every handle in `work` (each entry: one handle's nodes and buffers), all
+// handles sharing each launch; per node the operations are those of a
+// single solve.
+Err ulv_solve_up_big_multi(const std::vector<UpBigWork>& work, cudaStream_t s) {
+  bool any = false;
+  for (const UpBigWork& w : work) any = any || !w.ids.empty();
+  if (!any) return ok();
   Arena ar{(size_t)4 << 20};
   // b: leaf rows of B, or the children's contributions
   {
     std::vector<CopyItem> cp;
     std::vector<GemmItem<double>> g1, g2;
-    for (int id : ids) {
-      const TNode& nd = tr.nodes[id];
-      const UlvNode& u = F.nodes[id];
-      const UlvBufs& me = bufs[id];
-      if (nd.c1 < 0) {
-        cp.push_back({static_cast<const char*>(B) + static_cast<size_t>(nd.lo) * ldb * esz, ldb, f64,
-                      me.b, nr, u.m, nr, nullptr, 0});
-        continue;
+    for (const UpBigWork& w : work) {
+      const hss_s* h = w.h;
+      const Tree& tr = h->tree;
+      const UlvFactors& F = h->ulv;
+      const std::vector<UlvBufs>& bufs = *w.bufs;
+      const int f64 = h->dtype == HSS_F64;
+      const size_t esz = f64 ? 8 : 4;
+      const int nr = w.nr;
+      for (int id : w.ids) {
+        const TNode& nd = tr.nodes[id];
+        const UlvNode& u = F.nodes[id];
+        const UlvBufs& me = bufs[id];
+        if (nd.c1 < 0) {
+          cp.push_back({static_cast<const char*>(w.B) + static_cast<size_t>(nd.lo) * w.ldb * esz,
+                        w.ldb, f64, me.b, nr, u.m, nr, nullptr, 0});
+          continue;
+        }
+        const NodeGen& g = h->gen[id];
+        const UlvNode& a = F.nodes[nd.c1];
+        const UlvNode& b = F.nodes[nd.c2];
+        const UlvBufs& ba = bufs[nd.c1];
+        const UlvBufs& bb = bufs[nd.c2];
+        const int ra = a.m - a.k, rb = b.m - b.k;
+        double* top = me.b;
+        double* bot = me.b + static_cast<size_t>(a.k) * nr;
+        g1.push_back(gemm(top, nr, a.k, nr, ra, a.WbQt, ra, 0, ba.y, nr, 0, ba.btb, nr, -1.0));
+        GemmItem<double> b21 =
+            gemm(bot, nr, b.k, nr, a.kc, nullptr, a.kc, 0, ba.z, nr, 0, bb.btb, nr, -1.0);
+        b21.M = g.B21;
+        b21.m_is_f64 = f64 ? 1 : 2;
+        g1.push_back(b21);
+        GemmItem<double> b12 =
+            gemm(top, nr, a.k, nr, b.kc, nullptr, b.kc, 0, bb.z, nr, 0, top, nr, -1.0);
+        b12.M = g.B12;
+        b12.m_is_f64 = f64 ? 1 : 2;
+        g2.push_back(b12);
+        g2.push_back(gemm(bot, nr, b.k, nr, rb, b.WbQt, rb, 0, bb.y, nr, 0, bot, nr, -1.0));
       }
-      const NodeGen& g = h->gen[id];
-      const UlvNode& a = F.nodes[nd.c1];
-      const UlvNode& b = F.nodes[nd.c2];
-      const UlvBufs& ba = bufs[nd.c1];
-      const UlvBufs& bb = bufs[nd.c2];
-      const int ra = a.m - a.k, rb = b.m - b.k;
-      double* top = me.b;
-      double* bot = me.b + static_cast<size_t>(a.k) * nr;
-      g1.push_back(gemm(top, nr, a.k, nr, ra, a.WbQt, ra, 0, ba.y, nr, 0, ba.btb, nr, -1.0));
-      GemmItem<double> b21 = gemm(bot, nr, b.k, nr, a.kc, nullptr, a.kc, 0, ba.z, nr, 0, bb.btb, nr, -1.0);
-      b21.M = g.B21;
-      b21.m_is_f64 = f64 ? 1 : 2;
-      g1.push_back(b21);
-      GemmItem<double> b12 = gemm(top, nr, a.k, nr, b.kc, nullptr, b.kc, 0, bb.z, nr, 0, top, nr, -1.0);
-      b12.M = g.B12;
-      b12.m_is_f64 = f64 ? 1 : 2;
-      g2.push_back(b12);
-      g2.push_back(gemm(bot, nr, b.k, nr, rb, b.WbQt, rb, 0, bb.y, nr, 0, bot, nr, -1.0));
     }
     HSS_TRY(launch_copies(cp, s, ar));
     HSS_TRY(run_gemms(g1, s, ar));
     HSS_TRY(run_gemms(g2, s, ar));
   }
-  // root: x = U^{-1} L^{-1} P b
-  if (ids.size() == 1 && ids[0] == 0) {
-    const UlvBufs& me = bufs[0];
-    const int m = F.root_m;
-    HSS_CUDA_TRY(cudaMemcpyAsync(me.x, me.b, sizeof(double) * m * nr, cudaMemcpyDeviceToDevice, s));
-    apply_piv_kernel<<<(nr + 127) / 128, 128, 0, s>>>(me.x, F.root_piv, m, nr);
-    HSS_TRY(check_launch("apply_piv_kernel"));
-    std::vector<TriItem> base{{F.root_lu, m, me.x, nr, 0, 0, 0, 1}};
-    std::vector<int> ord{m};
-    HSS_TRY(blocked_trsm(base, ord, false, s, ar));
-    base[0].upper = 1;
-    base[0].unit = 0;
-    HSS_TRY(blocked_trsm(base, ord, true, s, ar));
-    ar.release(s);
-    return ok();
+  // roots: x = U^{-1} L^{-1} P b, every root's blocks in shared launches
+  {
+    std::vector<TriItem> base;
+    std::vector<int> ord;
+    for (const UpBigWork& w : work) {
+      if (!(w.ids.size() == 1 && w.ids[0] == 0)) continue;
+      const UlvFactors& F = w.h->ulv;
+      const UlvBufs& me = (*w.bufs)[0];
+      const int m = F.root_m, nr = w.nr;
+      HSS_CUDA_TRY(cudaMemcpyAsync(me.x, me.b, sizeof(double) * m * nr, cudaMemcpyDeviceToDevice, s));
+      apply_piv_kernel<<<(nr + 127) / 128, 128, 0, s>>>(me.x, F.root_piv, m, nr);
+      HSS_TRY(check_launch("apply_piv_kernel"));
+      base.push_back({F.root_lu, m, me.x, nr, 0, 0, 0, 1});
+      ord.push_back(m);
+    }
+    if (!base.empty()) {
+      HSS_TRY(blocked_trsm(base, ord, false, s, ar));
+      for (TriItem& t : base) {
+        t.upper = 1;
+        t.unit = 0;
+      }
+      HSS_TRY(blocked_trsm(base, ord, true, s, ar));
+    }
   }
   // btilde = Omega b; y = L^{-1} btilde_t; z = Vtt^T y (+ V^T [z1; z2])
   {
     std::vector<GemmItem<double>> gm;
     std::vector<TriItem> base;
     std::vector<int> ord;
-    for (int id : ids) {
-      const UlvNode& u = F.nodes[id];
-      const NodeGen& g = h->gen[id];
-      const UlvBufs& me = bufs[id];
-      const int r = u.m - u.k;
-      GemmItem<double> top = gemm(me.y, nr, r, nr, u.k, g.Er, u.k, 0, me.b, nr, 0, me.b, nr, -1.0);
-      top.Z.map = g.permr;
-      top.X.map = g.permr + u.k;
-      gm.push_back(top);
-      GemmItem<double> bot = gemm(me.btb, nr, u.k, nr, 0, nullptr, 1, 0, nullptr, 1, 0, me.b, nr, 1.0);
-      bot.X.map = g.permr;
-      gm.push_back(bot);
-      if (r > 0) {
-        base.push_back({u.L, r, me.y, nr, 0, 0, 0, 0});
-        ord.push_back(r);
+    for (const UpBigWork& w : work) {
+      if (w.ids.size() == 1 && w.ids[0] == 0) continue;
+      const UlvFactors& F = w.h->ulv;
+      const int nr = w.nr;
+      for (int id : w.ids) {
+        const UlvNode& u = F.nodes[id];
+        const NodeGen& g = w.h->gen[id];
+        const UlvBufs& me = (*w.bufs)[id];
+        const int r = u.m - u.k;
+        GemmItem<double> top = gemm(me.y, nr, r, nr, u.k, g.Er, u.k, 0, me.b, nr, 0, me.b, nr, -1.0);
+        top.Z.map = g.permr;
+        top.X.map = g.permr + u.k;
+        gm.push_back(top);
+        GemmItem<double> bot = gemm(me.btb, nr, u.k, nr, 0, nullptr, 1, 0, nullptr, 1, 0, me.b, nr, 1.0);
+        bot.X.map = g.permr;
+        gm.push_back(bot);
+        if (r > 0) {
+          base.push_back({u.L, r, me.y, nr, 0, 0, 0, 0});
+          ord.push_back(r);
+        }
       }
     }
     HSS_TRY(run_gemms(gm, s, ar));
@@ -847,33 +870,40 @@ Err ulv_solve_up_big(hss_s* h, const std::vector<int>& ids, const std::vector<Ul
   }
   {
     std::vector<GemmItem<double>> g1, g2;
-    for (int id : ids) {
-      const TNode& nd = tr.nodes[id];
-      const UlvNode& u = F.nodes[id];
-      const NodeGen& g = h->gen[id];
-      const UlvBufs& me = bufs[id];
-      const int r = u.m - u.k;
-      if (u.kc == 0) continue;
-      GemmItem<double> z = gemm(me.z, nr, u.kc, nr, r, u.Vtt, u.kc, 1, me.y, nr, 0, nullptr, 0, 1.0);
-      if (nd.c1 >= 0) {
-        const UlvNode& a = F.nodes[nd.c1];
-        z.X.p0 = bufs[nd.c1].z;
-        z.X.ld0 = nr;
-        z.X.p1 = bufs[nd.c2].z;
-        z.X.ld1 = nr;
-        z.X.split = a.kc;
-        z.X.map = g.permc;
-        GemmItem<double> ez = gemm(me.z, nr, u.kc, nr, g.mc - u.kc, g.Ec, u.kc, 1, nullptr, nr, 0,
-                                   me.z, nr, 1.0);
-        ez.Z.p0 = bufs[nd.c1].z;
-        ez.Z.ld0 = nr;
-        ez.Z.p1 = bufs[nd.c2].z;
-        ez.Z.ld1 = nr;
-        ez.Z.split = a.kc;
-        ez.Z.map = g.permc + u.kc;
-        g2.push_back(ez);
+    for (const UpBigWork& w : work) {
+      if (w.ids.size() == 1 && w.ids[0] == 0) continue;
+      const Tree& tr = w.h->tree;
+      const UlvFactors& F = w.h->ulv;
+      const std::vector<UlvBufs>& bufs = *w.bufs;
+      const int nr = w.nr;
+      for (int id : w.ids) {
+        const TNode& nd = tr.nodes[id];
+        const UlvNode& u = F.nodes[id];
+        const NodeGen& g = w.h->gen[id];
+        const UlvBufs& me = bufs[id];
+        const int r = u.m - u.k;
+        if (u.kc == 0) continue;
+        GemmItem<double> z = gemm(me.z, nr, u.kc, nr, r, u.Vtt, u.kc, 1, me.y, nr, 0, nullptr, 0, 1.0);
+        if (nd.c1 >= 0) {
+          const UlvNode& a = F.nodes[nd.c1];
+          z.X.p0 = bufs[nd.c1].z;
+          z.X.ld0 = nr;
+          z.X.p1 = bufs[nd.c2].z;
+          z.X.ld1 = nr;
+          z.X.split = a.kc;
+          z.X.map = g.permc;
+          GemmItem<double> ez = gemm(me.z, nr, u.kc, nr, g.mc - u.kc, g.Ec, u.kc, 1, nullptr, nr,
+                                     0, me.z, nr, 1.0);
+          ez.Z.p0 = bufs[nd.c1].z;
+          ez.Z.ld0 = nr;
+          ez.Z.p1 = bufs[nd.c2].z;
+          ez.Z.ld1 = nr;
+          ez.Z.split = a.kc;
+          ez.Z.map = g.permc + u.kc;
+          g2.push_back(ez);
+        }
+        g1.push_back(z);
       }
-      g1.push_back(z);
     }
     HSS_TRY(run_gemms(g1, s, ar));
     HSS_TRY(run_gemms(g2, s, ar));
@@ -882,37 +912,39 @@ Err ulv_solve_up_big(hss_s* h, const std::vector<int>& ids, const std::vector<Ul
   return ok();
 }
 
-// Downward sweep for large children: v = [y; x_parent part], v <- Q^T v with
-// Q^T = H_0 H_1 ... H_{r-1} applied panel by panel from the last, then the
-// leaves' rows of X.
-Err ulv_solve_down_big(hss_s* h, const std::vector<DownBig>& kids, const std::vector<UlvBufs>& bufs,
-                       int nr, void* X, int64_t ldx, cudaStream_t s) {
+// Downward sweep for the large children of one level of every handle in
+// `work`: v = [y; x_parent part], v <- Q^T v with Q^T = H_0 H_1 ... H_{r-1}
+// applied panel by panel from the last, then the leaves' rows of X.
+Err ulv_solve_down_big_multi(const std::vector<DownBigWork>& work, cudaStream_t s) {
+  struct Kid {
+    const DownBigWork* w;
+    const DownBig* d;
+    double *z1, *z2;
+  };
+  std::vector<Kid> kids;
+  for (const DownBigWork& w : work)
+    for (const DownBig& d : w.kids) kids.push_back({&w, &d, nullptr, nullptr});
   if (kids.empty()) return ok();
-  const Tree& tr = h->tree;
-  const UlvFactors& F = h->ulv;
-  const int f64 = h->dtype == HSS_F64;
   Arena ar{(size_t)4 << 20};
   int maxr = 0;
-  std::vector<double*> z1(kids.size()), z2(kids.size());
-  for (size_t t = 0; t < kids.size(); ++t) {
-    const DownBig& d = kids[t];
-    const UlvNode& u = F.nodes[d.child];
-    const UlvBufs& me = bufs[d.child];
-    const int r = u.m - u.k;
+  for (Kid& k : kids) {
+    const UlvNode& u = k.w->h->ulv.nodes[k.d->child];
+    const UlvBufs& me = (*k.w->bufs)[k.d->child];
+    const int r = u.m - u.k, nr = k.w->nr;
     maxr = std::max(maxr, r);
     HSS_CUDA_TRY(cudaMemcpyAsync(me.x, me.y, sizeof(double) * r * nr, cudaMemcpyDeviceToDevice, s));
-    HSS_CUDA_TRY(cudaMemcpyAsync(me.x + static_cast<size_t>(r) * nr, d.xp,
+    HSS_CUDA_TRY(cudaMemcpyAsync(me.x + static_cast<size_t>(r) * nr, k.d->xp,
                                  sizeof(double) * u.k * nr, cudaMemcpyDeviceToDevice, s));
-    HSS_TRY(ar.alloc_t(&z1[t], static_cast<size_t>(NB) * nr, s));
-    HSS_TRY(ar.alloc_t(&z2[t], static_cast<size_t>(NB) * nr, s));
+    HSS_TRY(ar.alloc_t(&k.z1, static_cast<size_t>(NB) * nr, s));
+    HSS_TRY(ar.alloc_t(&k.z2, static_cast<size_t>(NB) * nr, s));
   }
   const int npmax = (maxr + NB - 1) / NB;
   for (int q = 0; q < npmax; ++q) {
     std::vector<GemmItem<double>> g1, g2, g3;
-    for (size_t t = 0; t < kids.size(); ++t) {
-      const UlvNode& u = F.nodes[kids[t].child];
-      const UlvBufs& me = bufs[kids[t].child];
-      const int r = u.m - u.k, m = u.m;
+    for (Kid& k : kids) {
+      const UlvNode& u = k.w->h->ulv.nodes[k.d->child];
+      const UlvBufs& me = (*k.w->bufs)[k.d->child];
+      const int r = u.m - u.k, m = u.m, nr = k.w->nr;
       const int np = (r + NB - 1) / NB;
       if (q >= np) continue;
       const int p = np - 1 - q;
@@ -920,21 +952,23 @@ Err ulv_solve_down_big(hss_s* h, const std::vector<DownBig>& kids, const std::ve
       const double* vp = u.hv + static_cast<size_t>(i0) * m + i0;
       const double* T = u.T + static_cast<size_t>(p) * NB * NB;
       double* v = me.x + static_cast<size_t>(i0) * nr;
-      g1.push_back(gemm(z1[t], nr, nbb, nr, m - i0, vp, m, 0, v, nr, 0, nullptr, 0, 1.0));
-      g2.push_back(gemm(z2[t], nr, nbb, nr, nbb, T, NB, 0, z1[t], nr, 0, nullptr, 0, 1.0));
-      g3.push_back(gemm(v, nr, m - i0, nr, nbb, vp, m, 1, z2[t], nr, 0, v, nr, -1.0));
+      g1.push_back(gemm(k.z1, nr, nbb, nr, m - i0, vp, m, 0, v, nr, 0, nullptr, 0, 1.0));
+      g2.push_back(gemm(k.z2, nr, nbb, nr, nbb, T, NB, 0, k.z1, nr, 0, nullptr, 0, 1.0));
+      g3.push_back(gemm(v, nr, m - i0, nr, nbb, vp, m, 1, k.z2, nr, 0, v, nr, -1.0));
     }
     HSS_TRY(run_gemms(g1, s, ar));
     HSS_TRY(run_gemms(g2, s, ar));
     HSS_TRY(run_gemms(g3, s, ar));
   }
-  for (const DownBig& d : kids) {
-    const TNode& cn = tr.nodes[d.child];
+  for (Kid& k : kids) {
+    const TNode& cn = k.w->h->tree.nodes[k.d->child];
     if (cn.c1 >= 0) continue;
-    const UlvNode& u = F.nodes[d.child];
+    const UlvNode& u = k.w->h->ulv.nodes[k.d->child];
+    const int nr = k.w->nr;
     const int64_t total = static_cast<int64_t>(u.m) * nr;
     store_rows_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, s>>>(
-        bufs[d.child].x, u.m, nr, X, ldx, cn.lo, f64);
+        (*k.w->bufs)[k.d->child].x, u.m, nr, k.w->X, k.w->ldx, cn.lo,
+        k.w->h->dtype == HSS_F64 ? 1 : 0);
     HSS_TRY(check_launch("store_rows_kernel"));
   }
   ar.release(s);
