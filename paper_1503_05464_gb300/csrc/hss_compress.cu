@@ -83,6 +83,11 @@ struct Job {
   // give the products and the entries; idx = 0, 1, ..., n - 1 on the device
   const hss_matfree* mf = nullptr;
   int32_t* idx = nullptr;
+  // an FP32 A whose rows are not 16-byte aligned cannot be read by TMA: the
+  // tensor-core sampling then reads a copy with a padded leading dimension
+  // (made once, at the first pass)
+  T* apad = nullptr;
+  int64_t ldpad = 0;
 
   // out[i][j] = A(rows[i], cols[j]) through the caller's extract callback
   Err mf_extract(const int32_t* rows, int nr, const int32_t* cols, int nc, T* out, int64_t ldo) {
@@ -106,6 +111,8 @@ struct Job {
   void release() {
     dfree(idx, s);
     idx = nullptr;
+    dfree(apad, s);
+    apad = nullptr;
     dfree(R, s);
     dfree(Sr, s);
     dfree(Sc, s);
@@ -183,9 +190,9 @@ struct Job {
     // symmetric: the row product only (S^c = S^r)
     if (mf) HSS_TRY(sample_matfree(c0, c1, timing ? &ms : nullptr));
     else
-      HSS_TRY(launch_sample<T>(A, n(), lda, R, h->dcap, c0, c1, Sr, sym() ? nullptr : Sc,
-                               h->dcap, leaf_of, h->opts.sample_mode, &scratch, s,
-                               timing ? &ms : nullptr));
+      HSS_TRY(launch_sample<T>(apad ? apad : A, n(), apad ? ldpad : lda, R, h->dcap, c0, c1, Sr,
+                               sym() ? nullptr : Sc, h->dcap, leaf_of, h->opts.sample_mode,
+                               &scratch, s, timing ? &ms : nullptr));
     ms_sample += ms;
     h->info.flops_sample += (sym() ? 2.0 : 4.0) * (double)n() * (double)n() * (double)(c1 - c0);
     h->info.ms_host_sample += now_ms() - t0;
@@ -286,6 +293,13 @@ struct Job {
       h->gen[0].state = NODE_COMPRESSED;
       h->passes = 1;
       return finish();
+    }
+    if (!mf && sizeof(T) == 4 && h->opts.sample_mode != HSS_SAMPLE_NATIVE &&
+        (lda % 4 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0)) {
+      ldpad = (N + 3) / 4 * 4;
+      HSS_TRY(dalloc_t(&apad, (size_t)N * ldpad, s));
+      HSS_CUDA_TRY(cudaMemcpy2DAsync(apad, ldpad * sizeof(T), A, lda * sizeof(T), N * sizeof(T),
+                                     N, cudaMemcpyDeviceToDevice, s));
     }
     h->d = 0;
     h->dcap = 0;

@@ -74,10 +74,14 @@ def poisson_requests(count, rate, ks, seed, max_solves=3, nrhs_range=(1, 64)):
 
 
 def estimate_bytes(n, opts, esz=4):
-    """Peak device memory of one compression: the matrix, the samples, the
-    column-sample partial slab of one pass, and the resident form."""
+    """Peak device memory of one compression: the matrix (twice when its rows
+    are not 16-byte aligned: the tensor-core sampling reads a padded copy),
+    the samples, the column-sample partial slab of one pass, and the
+    resident form."""
     d = max(opts.d0, 64) * 4
     a = n * n * esz
+    if esz == 4 and n % 4 != 0 and opts.sample_mode != 0:
+        a += n * ((n + 3) // 4 * 4) * esz
     samples = 3 * n * d * esz
     slab = ((n + 127) // 128) * ((opts.d0 + 63) // 64) * n * 64 * esz
     return a + samples + slab
