@@ -645,7 +645,9 @@ def run_aux(args, wl, P, dev, rank, world):
             value, key = res["mean_compress_s"], "table3"
             ms = res["compress_s_total"] * 1e3
         else:
-            res = run_serving(P, dev, stream, wl, count=args.requests or 2000)
+            if args.bounded:   # the two smallest request sizes
+                wl = dict(wl, ks=wl["ks"][:2])
+            res = run_serving(P, dev, stream, wl, count=args.requests or 2000, load=args.load)
             value, key = res["request_p50_s"], "serving"
             ms = res["wall_s"] * 1e3
     if world > 1:
@@ -826,6 +828,11 @@ def main():
                     help="compress with hss_opts.symmetric (A = A^T): one ID per node, V = U")
     ap.add_argument("--no-extras", action="store_true",
                     help="leave the batching and serving objects out of the default line")
+    ap.add_argument("--load", type=float, default=None,
+                    help="serve: arrival rate as a multiple of the measured service rate "
+                         "(default 0.8; 2.0 is the overload run)")
+    ap.add_argument("--bounded", action="store_true",
+                    help="serve: only the two smallest request sizes (n = 2025, 5041)")
     ap.add_argument("--requests", type=int, default=None,
                     help="length of the served request stream")
     args = ap.parse_args()
