@@ -322,7 +322,8 @@ def run_ours(args, wl):
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": id_tflops / FP64_PEAK_TFLOPS,
                          "peak_source": "GB300 nominal dense FP64 (own FMA probe: 1.20)",
-                         "flops": info["flops_id"], "launches": info["id_launches"],
+                         "flops": info["flops_id"], "flops_solve": info["flops_id_solve"],
+                         "launches": info["id_launches"],
                          "flops_is": "sum over node sides of sum_{i<k} 4 (d-i)(m-i) (CPQR) "
                                      "+ (m-k) k^2 (T = R1^-1 R2, sides that pass)"},
         "fused_sampling": {"ms": s_ms, "bound": bound, "achieved": samp_tflops,
