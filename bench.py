@@ -95,10 +95,9 @@ GOLDEN_BEM60K = os.path.join(ROOT, "tests", "golden", "bem60k_oracle.json")
 # probed ~1.79 GHz under load (own probe: 69.7 TFLOP/s)
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) of the ID kernel over a whole bem32k compression
-# per FP64 flop of its CPQR steps (the flops_id count of that capture, which
-# did not yet include the T = R1^-1 R2 solve), from
+# per FP64 flop of its CPQR steps (flops_id - flops_id_solve), from
 # profiles/id_cpqr_dram_bem32k.md
-ID_DRAM_BYTES_PER_FLOP = 0.442
+ID_DRAM_BYTES_PER_FLOP = 0.447
 FP32_SIMT_PEAK_TFLOPS = 69.7
 
 
