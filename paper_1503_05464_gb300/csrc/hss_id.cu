@@ -813,8 +813,10 @@ class TeamTuner {
   // (nullptr when the class has settled).  half_group: the launch may also
   // run with half as many CTAs per item (a spread-out launch whose CTAs own
   // few columns each): that candidate is the model's team index + 8.
+  // double_cluster: a cluster launch may also run with clusters twice as
+  // large: the model's team index + 16.
   int choose(const Key& k, int model_ti, int min_ti, double units, Trial** trial,
-             bool half_group = false) {
+             bool half_group = false, bool double_cluster = false) {
     std::lock_guard<std::mutex> lock(mu_);
     harvest();
     *trial = nullptr;
@@ -824,6 +826,7 @@ class TeamTuner {
       for (int t : {model_ti, model_ti - 1, model_ti + 1})
         if (t >= min_ti && t <= 5) c.cand.push_back(t);
       if (half_group) c.cand.push_back(model_ti + 8);
+      if (double_cluster) c.cand.push_back(model_ti + 16);
       c.sum.assign(c.cand.size(), 0.0);
       c.cnt.assign(c.cand.size(), 0);
       c.issued.assign(c.cand.size(), 0);
@@ -1195,19 +1198,50 @@ Err launch_id_batched(const IdItem* items_dev, const std::vector<IdItem>& h, boo
   if (!done) {
     // more CTAs than SMs, columns in global memory: two CTAs per SM when
     // they fit (registers, shared memory)
-    bool two = false;
-    if ((long)count * C > sms && !w_in_smem) {
+    auto two_fit = [&](int c, size_t sm_bytes, int in_smem) {
+      if ((long)count * c <= sms || in_smem) return false;
       int nb = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernels2()[5], ID_THREADS, smem) ==
-              cudaSuccess &&
-          nb >= 2)
-        two = true;
+      const bool ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                          &nb, kernels2()[5], ID_THREADS, sm_bytes) == cudaSuccess && nb >= 2;
       cudaGetLastError();
+      return ok;
+    };
+    bool two = two_fit(C, smem, w_in_smem);
+    // the tuner may also try clusters twice as large when the launch leaves
+    // SMs with fewer than two CTAs and the columns are in global memory
+    // (more warps per SM to hide the columns' memory latency, a cluster
+    // barrier per step in exchange); results do not depend on the choice
+    const int C2 = 2 * C;
+    const size_t smem2 = need(C2);
+    bool dbl_ok = !w_in_smem && C2 <= 16 && (long)count * C < 2L * sms && max_m / C2 >= 16 &&
+                  smem2 <= 227 * 1024 - 2048;
+    if (dbl_ok) {
+      cudaLaunchConfig_t c2 = cfg;
+      cudaLaunchAttribute a2[1];
+      a2[0] = attr[0];
+      a2[0].val.clusterDim.x = C2;
+      c2.attrs = a2;
+      c2.gridDim = dim3((unsigned)(count * C2), 1, 1);
+      c2.dynamicSmemBytes = smem2;
+      int ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, id_cpqr_cluster_kernel<1, false>, &c2) != cudaSuccess)
+        ncl = 0;
+      cudaGetLastError();
+      dbl_ok = ncl > 0;
     }
     TeamTuner::Trial* trial = nullptr;
-    const int ti = TeamTuner::get().choose(
+    const int choice = TeamTuner::get().choose(
         TeamTuner::Key{dev_ordinal, two ? 3 : 0, w_in_smem, ilog2(max_m), ilog2(d), ilog2(count)},
-        team_index(C, w_in_smem == 0), w_in_smem ? 0 : 2, units, &trial);
+        team_index(C, w_in_smem == 0), w_in_smem ? 0 : 2, units, &trial, false, dbl_ok);
+    const int ti = choice & 7;
+    if (choice & 16) {   // clusters of C2: the columns stay in global memory
+      C = C2;
+      smem = smem2;
+      attr[0].val.clusterDim.x = C;
+      cfg.gridDim = dim3((unsigned)(count * C), 1, 1);
+      cfg.dynamicSmemBytes = smem;
+      two = two_fit(C, smem, 0);
+    }
     if (trial) cudaEventRecord(trial->e0, s);
     cudaError_t e = cudaLaunchKernelEx(&cfg, (two ? kernels2() : kernels())[ti], items_dev,
                                        f64 ? 1 : 0, w_in_smem, r1, (const int64_t*)offd, ga);
