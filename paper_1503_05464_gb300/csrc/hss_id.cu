@@ -200,8 +200,10 @@ struct alignas(16) Cand {
   double st;      // sum of x_c^2 below the next pivot row
   double alpha;   // x at the next pivot row
 };
-// (v, j) are read together as one 16-byte load
-static_assert(offsetof(Cand, j) == 8 && sizeof(Cand) == 32, "Cand layout");
+// (v, j) and (st, alpha) are read as two 16-byte loads
+static_assert(offsetof(Cand, j) == 8 && offsetof(Cand, st) == 16 &&
+                  offsetof(Cand, alpha) == 24 && sizeof(Cand) == 32,
+              "Cand layout");
 
 // A node side spread over more CTAs than a cluster holds (a "group"): the
 // group's CTAs meet at a barrier in global memory (a counter per item) and
@@ -448,24 +450,31 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
     // on the pivot without a block barrier
     long long bv = LLONG_MIN;
     int p = INT_MAX;
+    double wst = 0.0, wal = 0.0;   // the best candidate's residual (group mode)
     const Cand* gc = nullptr;
     if constexpr (GRP) {
       gc = ga.cand + (static_cast<size_t>(item) * 2 + slot) * C;
-      // every candidate's (v, j) is loaded before any is compared: one round
-      // trip to L2 for up to 320 CTAs instead of one per 32
+      // every candidate (v, j and its residual st, alpha) is loaded before
+      // any is compared: one round trip to L2 for up to 320 CTAs instead of
+      // one per 32, and none more for the winner's residual
       constexpr int U = 10;
       for (int r0 = lane; r0 < C; r0 += 32 * U) {
         long long vv[U];
         int jj[U];
+        double ss[U], aa[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int r = r0 + 32 * u;
           vv[u] = LLONG_MIN;
           jj[u] = INT_MAX;
+          ss[u] = aa[u] = 0.0;
           if (r < C) {
             const longlong2 x = __ldcg(reinterpret_cast<const longlong2*>(&gc[r]));
+            const double2 y = __ldcg(reinterpret_cast<const double2*>(&gc[r]) + 1);
             vv[u] = x.x;
             jj[u] = static_cast<int>(x.y & 0xffffffffll);
+            ss[u] = y.x;
+            aa[u] = y.y;
           }
         }
 #pragma unroll
@@ -473,13 +482,23 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
           if (vv[u] > bv || (vv[u] == bv && jj[u] < p)) {
             bv = vv[u];
             p = jj[u];
+            wst = ss[u];
+            wal = aa[u];
           }
       }
     } else if (lane < C) {
       bv = cands[slot][lane].v;
       p = cands[slot][lane].j;
     }
+    const int mine = p;   // this lane's best before the warp's reduction
     warp_argmax_bits(bv, p);
+    if constexpr (GRP) {
+      // the winner's residual from the lane that loaded it
+      const unsigned has = __ballot_sync(0xffffffffu, mine == p);
+      const int src = __ffs(has) - 1;
+      wst = __shfl_sync(0xffffffffu, wst, src);
+      wal = __shfl_sync(0xffffffffu, wal, src);
+    }
     const int owner = p % C;
     if (tid == 0 || tid == 32) {
       // the reflector from the owner's pushed residual, the same arithmetic on
@@ -487,8 +506,8 @@ id_cpqr_cluster_kernel(const IdItem* __restrict__ items, int f64in,
       // by side while the other warps copy the pivot column
       double st, alpha;
       if constexpr (GRP) {
-        st = __ldcg(&gc[owner].st);
-        alpha = __ldcg(&gc[owner].alpha);
+        st = wst;
+        alpha = wal;
       } else {
         st = cands[slot][owner].st;
         alpha = cands[slot][owner].alpha;
