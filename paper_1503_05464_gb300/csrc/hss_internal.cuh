@@ -263,6 +263,24 @@ struct GemmItem {
 template <typename T>
 Err launch_gemm_batched(const std::vector<GemmItem<T>>& items, cudaStream_t s,
                         void* scratch_dev, size_t scratch_bytes, Arena* scratch = nullptr);
+// A sequence of batched GEMM launches whose items are all known before the
+// first runs (each phase may read what the earlier ones write): the item
+// tables of every phase go to the device in one copy, then one launch per
+// phase, in order.
+template <typename T>
+class GemmPlan {
+ public:
+  void add(const std::vector<GemmItem<T>>& items);
+  Err run(cudaStream_t s);
+
+ private:
+  struct Phase {
+    size_t items_off, starts_off;
+    int n, tiles;
+  };
+  std::vector<char> host_;
+  std::vector<Phase> phases_;
+};
 
 // ------------------------------------------------------------- gathers
 // out[j][l] = A[rows[j]][cols[l]] for a batch of blocks (each item names its A;

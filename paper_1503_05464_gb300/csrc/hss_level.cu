@@ -11,6 +11,8 @@
 //    an ID basis, B_{nu1,nu2} = A(I^r_nu1, I^c_nu2)).
 #include "hss_internal.cuh"
 
+#include <cstring>
+
 #include <algorithm>
 
 namespace hss {
@@ -376,6 +378,55 @@ Err launch_index_compose(int32_t* out, const int32_t* base, const int32_t* idx, 
   index_compose_kernel<<<(count + 255) / 256, 256, 0, s>>>(out, base, idx, count);
   return check_launch("index_compose_kernel");
 }
+
+template <typename T>
+void GemmPlan<T>::add(const std::vector<GemmItem<T>>& items) {
+  std::vector<GemmItem<T>> live;
+  std::vector<int> starts;
+  int tiles = 0;
+  for (const auto& it : items) {
+    if (it.rows <= 0 || it.c1 <= it.c0) continue;
+    const int tr = (it.rows + G_TM - 1) / G_TM, tc = (it.c1 - it.c0 + G_TN - 1) / G_TN;
+    live.push_back(it);
+    starts.push_back(tiles);
+    tiles += tr * tc;
+  }
+  if (live.empty()) return;
+  auto append = [&](const void* p, size_t bytes) {
+    const size_t off = (host_.size() + 255) & ~size_t(255);
+    host_.resize(off + bytes);
+    std::memcpy(host_.data() + off, p, bytes);
+    return off;
+  };
+  Phase ph;
+  ph.items_off = append(live.data(), live.size() * sizeof(GemmItem<T>));
+  ph.starts_off = append(starts.data(), starts.size() * sizeof(int));
+  ph.n = static_cast<int>(live.size());
+  ph.tiles = tiles;
+  phases_.push_back(ph);
+}
+
+template <typename T>
+Err GemmPlan<T>::run(cudaStream_t s) {
+  if (phases_.empty()) return ok();
+  char* buf = nullptr;
+  HSS_TRY(dalloc(reinterpret_cast<void**>(&buf), host_.size(), s));
+  // one copy from pageable memory: it is staged before the call returns
+  HSS_CUDA_TRY(cudaMemcpyAsync(buf, host_.data(), host_.size(), cudaMemcpyHostToDevice, s));
+  Err e;
+  for (const Phase& ph : phases_) {
+    gemm_batched_kernel<T><<<ph.tiles, G_THREADS, 0, s>>>(
+        reinterpret_cast<const GemmItem<T>*>(buf + ph.items_off),
+        reinterpret_cast<const int*>(buf + ph.starts_off), ph.n);
+    e = check_launch("gemm_batched_kernel");
+    if (e.st) break;
+  }
+  dfree(buf, s);
+  return e;
+}
+
+template class GemmPlan<float>;
+template class GemmPlan<double>;
 
 template Err launch_gemm_batched<float>(const std::vector<GemmItem<float>>&, cudaStream_t, void*,
                                         size_t, Arena*);

@@ -168,10 +168,14 @@ static Err matvec_impl(hss_s* h, const T* X, int64_t ldx, int nrhs, T* B, int64_
   auto EZ = [&](int i) { return buf + oe[i]; };
   Err err = ok();
   std::vector<GemmItem<T>> items;
+  // every level's items are known up front (they depend on the tree and the
+  // buffers, not on the data): one upload of all item tables, then one
+  // launch per phase in this order
+  GemmPlan<T> plan;
   auto run = [&]() -> Err {
-    Err e = launch_gemm_batched<T>(items, s, nullptr, 0);
+    plan.add(items);
     items.clear();
-    return e;
+    return ok();
   };
   // upward sweep: y_tau = V_tau^T x(I_tau) or V_tau^T [y_c1; y_c2]
   for (int depth = tr.maxdepth; depth >= 1 && err.st == HSS_OK; --depth) {
@@ -294,6 +298,7 @@ static Err matvec_impl(hss_s* h, const T* X, int64_t ldx, int nrhs, T* B, int64_
     }
     err = run();
   }
+  if (err.st == HSS_OK) err = plan.run(s);
   dfree(buf, s);
   return err;
 }
