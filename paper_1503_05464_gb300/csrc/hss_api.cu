@@ -96,6 +96,60 @@ void dfree(void* p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
 }
 
+namespace {
+// Eight pinned blocks per host thread, used in turn.  A block is written
+// again only after the event recorded behind its last copy has passed, so a
+// thread may queue up to eight uploads ahead of the device.
+struct UploadSlot {
+  char* buf = nullptr;
+  size_t cap = 0;
+  cudaEvent_t ev = nullptr;
+};
+struct UploadRing {
+  UploadSlot slot[8];
+  int next = 0;
+  int dev = -1;
+  void drop() {
+    for (UploadSlot& u : slot) {
+      if (u.ev) {
+        cudaEventSynchronize(u.ev);
+        cudaEventDestroy(u.ev);
+      }
+      if (u.buf) cudaFreeHost(u.buf);
+      u = UploadSlot{};
+    }
+  }
+  ~UploadRing() { drop(); }
+};
+}  // namespace
+
+Err upload_async(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return ok();
+  static thread_local UploadRing ring;
+  int dev = 0;
+  HSS_CUDA_TRY(cudaGetDevice(&dev));
+  if (ring.dev != dev) {   // events and pinned blocks belong to one device
+    ring.drop();
+    ring.dev = dev;
+  }
+  UploadSlot& u = ring.slot[ring.next];
+  ring.next = (ring.next + 1) % 8;
+  if (u.ev) HSS_CUDA_TRY(cudaEventSynchronize(u.ev));
+  else HSS_CUDA_TRY(cudaEventCreateWithFlags(&u.ev, cudaEventDisableTiming));
+  if (u.cap < bytes) {
+    if (u.buf) cudaFreeHost(u.buf);
+    u.buf = nullptr;
+    u.cap = 0;
+    const size_t cap = std::max(bytes + (bytes >> 2), (size_t)256 << 10);
+    HSS_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&u.buf), cap));
+    u.cap = cap;
+  }
+  std::memcpy(u.buf, src, bytes);
+  HSS_CUDA_TRY(cudaMemcpyAsync(dst, u.buf, bytes, cudaMemcpyHostToDevice, s));
+  HSS_CUDA_TRY(cudaEventRecord(u.ev, s));
+  return ok();
+}
+
 }  // namespace hss
 
 using namespace hss;

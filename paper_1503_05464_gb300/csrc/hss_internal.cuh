@@ -51,6 +51,11 @@ int64_t fault_wait_limit();
 Err dalloc(void** p, size_t bytes, cudaStream_t s);
 void dfree(void* p, cudaStream_t s);
 
+// Host->device copy of a small table without waiting for the stream (a copy
+// from pageable memory would synchronize it first): the bytes are staged in a
+// pinned block of the calling thread, which the function returns at once.
+Err upload_async(void* dst, const void* src, size_t bytes, cudaStream_t s);
+
 template <typename T>
 inline Err dalloc_t(T** p, size_t count, cudaStream_t s) {
   return dalloc(reinterpret_cast<void**>(p), count * sizeof(T), s);
@@ -164,8 +169,7 @@ class Arena {
   PinnedStage* stage = nullptr;
   Err upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
     if (stage) return stage->put(dst, src, bytes, s);
-    HSS_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
-    return ok();
+    return upload_async(dst, src, bytes, s);
   }
 
  private:
@@ -276,7 +280,7 @@ class GemmPlan {
  private:
   struct Phase {
     size_t items_off, starts_off;
-    int n, tiles;
+    int n, tiles, nc;
   };
   std::vector<char> host_;
   std::vector<Phase> phases_;

@@ -108,6 +108,183 @@ gemm_batched_kernel(const GemmItem<T>* __restrict__ items, const int* __restrict
   }
 }
 
+// Narrow variant for items with few columns (the products of Algorithm 2 and
+// the ULV sweeps, one column per right-hand side): a 64 x 64 tile would spend
+// most of its FP64 FMAs on padding columns.  A block covers 32 rows of one
+// item and NC columns.  Its slice of Z goes to shared memory first, in chunks
+// of N_ZVALS values, with every thread's loads independent (the row maps of Z
+// make each load depend on an index load); the loops over M then issue
+// coalesced loads with no index chains.
+//  * m_trans: lane = row, the 8 warps take the inner indices l = w (mod 8);
+//    the partial sums meet in shared memory in warp order.
+//  * otherwise: warp w owns rows 4w .. 4w+3, lanes take l = lane (mod 32);
+//    the partial sums meet by a butterfly of shuffles.
+// Each thread adds its terms in increasing l whatever the chunk length (a
+// multiple of 32), so a column's result does not depend on NC and results
+// repeat bit for bit.  tile_map holds (item, tile of the item) per block.
+constexpr int N_ROWS = 32, N_THREADS = 256, N_ZVALS = 4096;
+
+template <typename T>
+__device__ __forceinline__ T z_at(const GemmItem<T>& it, int l, int c) {
+  return it.z_trans ? src_row(it.Z, c)[l] : src_row(it.Z, l)[c];
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(N_THREADS)
+gemm_narrow_kernel(const GemmItem<T>* __restrict__ items, const int2* __restrict__ tile_map) {
+  constexpr int LCH = N_ZVALS / NC;   // inner indices per chunk
+  static_assert(LCH % 32 == 0, "chunks keep every thread's inner indices in order");
+  static_assert(sizeof(T) * N_ZVALS >= sizeof(T) * (N_THREADS / 32) * N_ROWS * NC,
+                "the reduction reuses the staging buffer");
+  __shared__ T zs[N_ZVALS];
+  const int2 tm = tile_map[blockIdx.x];
+  const GemmItem<T> it = items[tm.x];
+  const int tiles_c = (it.c1 - it.c0 + NC - 1) / NC;
+  const int tr = tm.y / tiles_c, tc = tm.y - tr * tiles_c;
+  const int j0 = tr * N_ROWS, cb = it.c0 + tc * NC;
+  const int nc = min(NC, it.c1 - cb);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  T acc[4][NC];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[r][c] = T(0);
+  const int jt = j0 + lane;    // m_trans: this thread's row
+  const int jr = j0 + 4 * w;   // otherwise: this warp's first row
+  for (int l0 = 0; l0 < it.inner; l0 += LCH) {
+    const int lc = min(LCH, it.inner - l0);
+    __syncthreads();
+    for (int e = tid; e < lc * NC; e += N_THREADS) {
+      const int l = e / NC, c = e - l * NC;
+      zs[e] = c < nc ? z_at(it, l0 + l, cb + c) : T(0);
+    }
+    __syncthreads();
+    if (it.m_trans) {
+      if (jt < it.rows) {
+#pragma unroll 4
+        for (int l = w; l < lc; l += N_THREADS / 32) {
+          const T m = mat_at(it, jt, l0 + l);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[0][c] = fma(m, zs[l * NC + c], acc[0][c]);
+        }
+      }
+    } else {
+#pragma unroll 2
+      for (int l = lane; l < lc; l += 32) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const T m = jr + r < it.rows ? mat_at(it, jr + r, l0 + l) : T(0);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[r][c] = fma(m, zs[l * NC + c], acc[r][c]);
+        }
+      }
+    }
+  }
+  if (it.m_trans) {
+    __syncthreads();   // zs becomes red[w][lane][c]
+#pragma unroll
+    for (int c = 0; c < NC; ++c) zs[(w * N_ROWS + lane) * NC + c] = acc[0][c];
+    __syncthreads();
+    if (w == 0 && jt < it.rows) {
+      const T* xr = it.X.p0 ? src_row(it.X, jt) : nullptr;
+      T* o = it.out + (int64_t)jt * it.ldo;
+      for (int c = 0; c < nc; ++c) {
+        T v = zs[lane * NC + c];
+#pragma unroll
+        for (int q = 1; q < N_THREADS / 32; ++q) v += zs[(q * N_ROWS + lane) * NC + c];
+        v = it.sign * v;
+        if (xr) v += xr[cb + c];
+        o[cb + c] = v;
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T v = acc[r][c];
+#pragma unroll
+      for (int sh = 16; sh >= 1; sh >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
+      acc[r][c] = v;
+    }
+  // lane r (< 4) writes row jr + r
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int j = jr + r;
+    if (lane != r || j >= it.rows) continue;
+    const T* xr = it.X.p0 ? src_row(it.X, j) : nullptr;
+    T* o = it.out + (int64_t)j * it.ldo;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (c >= nc) break;
+      T v = it.sign * acc[r][c];
+      if (xr) v += xr[cb + c];
+      o[cb + c] = v;
+    }
+  }
+}
+
+// Launch shape of one batched GEMM: the 64 x 64 tile kernel (nc = 0), or the
+// narrow kernel with nc columns per block.
+struct GemmShape {
+  int nc;
+  int tiles(int rows, int ncol) const {
+    return nc ? ((rows + N_ROWS - 1) / N_ROWS) * ((ncol + nc - 1) / nc)
+              : ((rows + G_TM - 1) / G_TM) * ((ncol + G_TN - 1) / G_TN);
+  }
+};
+
+// Items with at most 32 columns go to the narrow kernel, the others to the
+// tile kernel.  The choice is per item and a column's sums do not depend on
+// nc, so an item's result is the same whatever shares its launch.
+constexpr int NARROW_MAX = 32;
+
+template <typename T>
+struct GemmGroup {
+  GemmShape shape{0};
+  std::vector<GemmItem<T>> live;
+  std::vector<int> starts;   // tile kernel: first block of each item; narrow: (item, tile) pairs
+  int tiles = 0;
+};
+
+template <typename T>
+void split_gemm(const std::vector<GemmItem<T>>& items, GemmGroup<T> g[2]) {
+  int mc = 0;
+  for (const auto& it : items)
+    if (it.rows > 0 && it.c1 > it.c0 && it.c1 - it.c0 <= NARROW_MAX) mc = std::max(mc, it.c1 - it.c0);
+  g[0].shape.nc = 0;
+  g[1].shape.nc = mc <= 1 ? 1 : mc == 2 ? 2 : mc <= 4 ? 4 : 8;
+  for (const auto& it : items) {
+    if (it.rows <= 0 || it.c1 <= it.c0) continue;
+    GemmGroup<T>& q = g[it.c1 - it.c0 <= NARROW_MAX ? 1 : 0];
+    const int t = q.shape.tiles(it.rows, it.c1 - it.c0);
+    if (q.shape.nc) {   // (item, tile of the item) per block
+      for (int k = 0; k < t; ++k) {
+        q.starts.push_back(static_cast<int>(q.live.size()));
+        q.starts.push_back(k);
+      }
+    } else {            // first block of each item
+      q.starts.push_back(q.tiles);
+    }
+    q.live.push_back(it);
+    q.tiles += t;
+  }
+}
+
+template <typename T>
+void launch_gemm_shape(GemmShape g, int tiles, const GemmItem<T>* items, const int* starts, int n,
+                       cudaStream_t s) {
+  const int2* map = reinterpret_cast<const int2*>(starts);
+  switch (g.nc) {
+    case 0: gemm_batched_kernel<T><<<tiles, G_THREADS, 0, s>>>(items, starts, n); break;
+    case 1: gemm_narrow_kernel<T, 1><<<tiles, N_THREADS, 0, s>>>(items, map); break;
+    case 2: gemm_narrow_kernel<T, 2><<<tiles, N_THREADS, 0, s>>>(items, map); break;
+    case 4: gemm_narrow_kernel<T, 4><<<tiles, N_THREADS, 0, s>>>(items, map); break;
+    default: gemm_narrow_kernel<T, 8><<<tiles, N_THREADS, 0, s>>>(items, map); break;
+  }
+}
+
 template <typename T>
 __global__ void gather_batched_kernel(const T* __restrict__ A, int64_t lda,
                                       const GatherItem<T>* __restrict__ items,
@@ -197,9 +374,8 @@ Err upload_table(const std::vector<I>& items, const std::vector<int64_t>& starts
     return ok();
   }
   HSS_TRY(dalloc(buf, *off + starts.size() * sizeof(int64_t), s));
-  HSS_CUDA_TRY(cudaMemcpyAsync(*buf, items.data(), bi, cudaMemcpyHostToDevice, s));
-  HSS_CUDA_TRY(cudaMemcpyAsync((char*)*buf + *off, starts.data(), starts.size() * sizeof(int64_t),
-                               cudaMemcpyHostToDevice, s));
+  HSS_TRY(upload_async(*buf, items.data(), bi, s));
+  HSS_TRY(upload_async((char*)*buf + *off, starts.data(), starts.size() * sizeof(int64_t), s));
   return ok();
 }
 
@@ -252,43 +428,40 @@ Err launch_invert_batched(const std::vector<InvItem>& items, cudaStream_t s, Are
 template <typename T>
 Err launch_gemm_batched(const std::vector<GemmItem<T>>& items, cudaStream_t s,
                         void* scratch_dev, size_t scratch_bytes, Arena* scratch) {
-  std::vector<GemmItem<T>> live;
-  std::vector<int> starts;
-  int tiles = 0;
-  for (const auto& it : items) {
-    if (it.rows <= 0 || it.c1 <= it.c0) continue;
-    int tr = (it.rows + G_TM - 1) / G_TM, tc = (it.c1 - it.c0 + G_TN - 1) / G_TN;
-    live.push_back(it);
-    starts.push_back(tiles);
-    tiles += tr * tc;
-  }
-  if (live.empty()) return ok();
-  size_t bi = live.size() * sizeof(GemmItem<T>);
-  size_t bs = starts.size() * sizeof(int);
-  size_t off = (bi + 255) & ~size_t(255);
-  void* buf = scratch_dev;
-  bool own = false;
-  if (!buf || scratch_bytes < off + bs) {
-    if (scratch) {
-      HSS_TRY(scratch->alloc(&buf, off + bs, s));
-    } else {
-      HSS_TRY(dalloc(&buf, off + bs, s));
-      own = true;
+  GemmGroup<T> grp[2];
+  split_gemm(items, grp);
+  for (const GemmGroup<T>& g : grp) {
+    if (g.live.empty()) continue;
+    size_t bi = g.live.size() * sizeof(GemmItem<T>);
+    size_t bs = g.starts.size() * sizeof(int);
+    size_t off = (bi + 255) & ~size_t(255);
+    void* buf = scratch_dev;
+    bool own = false;
+    if (!buf || scratch_bytes < off + bs) {
+      if (scratch) {
+        HSS_TRY(scratch->alloc(&buf, off + bs, s));
+      } else {
+        HSS_TRY(dalloc(&buf, off + bs, s));
+        own = true;
+      }
     }
+    if (scratch) {
+      HSS_TRY(scratch->upload(buf, g.live.data(), bi, s));
+      HSS_TRY(scratch->upload((char*)buf + off, g.starts.data(), bs, s));
+    } else {
+      HSS_TRY(upload_async(buf, g.live.data(), bi, s));
+      HSS_TRY(upload_async((char*)buf + off, g.starts.data(), bs, s));
+    }
+    launch_gemm_shape<T>(g.shape, g.tiles, reinterpret_cast<const GemmItem<T>*>(buf),
+                         reinterpret_cast<const int*>((char*)buf + off), (int)g.live.size(), s);
+    Err e = check_launch(g.shape.nc ? "gemm_narrow_kernel" : "gemm_batched_kernel");
+    if (own) dfree(buf, s);
+    if (e.st) return e;
+    // a caller-provided scratch buffer is reused by the second group: the
+    // launches are stream-ordered, the upload of the second table follows
+    // the first launch
   }
-  if (scratch) {
-    HSS_TRY(scratch->upload(buf, live.data(), bi, s));
-    HSS_TRY(scratch->upload((char*)buf + off, starts.data(), bs, s));
-  } else {
-    HSS_CUDA_TRY(cudaMemcpyAsync(buf, live.data(), bi, cudaMemcpyHostToDevice, s));
-    HSS_CUDA_TRY(cudaMemcpyAsync((char*)buf + off, starts.data(), bs, cudaMemcpyHostToDevice, s));
-  }
-  gemm_batched_kernel<T><<<tiles, G_THREADS, 0, s>>>(
-      reinterpret_cast<const GemmItem<T>*>(buf), reinterpret_cast<const int*>((char*)buf + off),
-      (int)live.size());
-  Err e = check_launch("gemm_batched_kernel");
-  if (own) dfree(buf, s);
-  return e;
+  return ok();
 }
 
 template <typename T>
@@ -322,8 +495,8 @@ Err launch_gather_batched(const T* A, int64_t lda, const std::vector<GatherItem<
     HSS_TRY(scratch->upload(buf, live.data(), bi, s));
     HSS_TRY(scratch->upload((char*)buf + off, starts.data(), bs, s));
   } else {
-    HSS_CUDA_TRY(cudaMemcpyAsync(buf, live.data(), bi, cudaMemcpyHostToDevice, s));
-    HSS_CUDA_TRY(cudaMemcpyAsync((char*)buf + off, starts.data(), bs, cudaMemcpyHostToDevice, s));
+    HSS_TRY(upload_async(buf, live.data(), bi, s));
+    HSS_TRY(upload_async((char*)buf + off, starts.data(), bs, s));
   }
   gather_batched_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
       A, lda, reinterpret_cast<const GatherItem<T>*>(buf),
@@ -357,8 +530,8 @@ Err launch_copy_batched(const std::vector<Copy2D<T>>& items, cudaStream_t s, Are
   } else {
     HSS_TRY(dalloc(&buf, off + bs, s));
     own = true;
-    HSS_CUDA_TRY(cudaMemcpyAsync(buf, live.data(), bi, cudaMemcpyHostToDevice, s));
-    HSS_CUDA_TRY(cudaMemcpyAsync((char*)buf + off, starts.data(), bs, cudaMemcpyHostToDevice, s));
+    HSS_TRY(upload_async(buf, live.data(), bi, s));
+    HSS_TRY(upload_async((char*)buf + off, starts.data(), bs, s));
   }
   copy_batched_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
       reinterpret_cast<const Copy2D<T>*>(buf), reinterpret_cast<const int64_t*>((char*)buf + off),
@@ -381,29 +554,24 @@ Err launch_index_compose(int32_t* out, const int32_t* base, const int32_t* idx, 
 
 template <typename T>
 void GemmPlan<T>::add(const std::vector<GemmItem<T>>& items) {
-  std::vector<GemmItem<T>> live;
-  std::vector<int> starts;
-  int tiles = 0;
-  for (const auto& it : items) {
-    if (it.rows <= 0 || it.c1 <= it.c0) continue;
-    const int tr = (it.rows + G_TM - 1) / G_TM, tc = (it.c1 - it.c0 + G_TN - 1) / G_TN;
-    live.push_back(it);
-    starts.push_back(tiles);
-    tiles += tr * tc;
-  }
-  if (live.empty()) return;
+  GemmGroup<T> grp[2];
+  split_gemm(items, grp);
   auto append = [&](const void* p, size_t bytes) {
     const size_t off = (host_.size() + 255) & ~size_t(255);
     host_.resize(off + bytes);
     std::memcpy(host_.data() + off, p, bytes);
     return off;
   };
-  Phase ph;
-  ph.items_off = append(live.data(), live.size() * sizeof(GemmItem<T>));
-  ph.starts_off = append(starts.data(), starts.size() * sizeof(int));
-  ph.n = static_cast<int>(live.size());
-  ph.tiles = tiles;
-  phases_.push_back(ph);
+  for (const GemmGroup<T>& g : grp) {
+    if (g.live.empty()) continue;
+    Phase ph;
+    ph.items_off = append(g.live.data(), g.live.size() * sizeof(GemmItem<T>));
+    ph.starts_off = append(g.starts.data(), g.starts.size() * sizeof(int));
+    ph.n = static_cast<int>(g.live.size());
+    ph.tiles = g.tiles;
+    ph.nc = g.shape.nc;
+    phases_.push_back(ph);
+  }
 }
 
 template <typename T>
@@ -411,14 +579,13 @@ Err GemmPlan<T>::run(cudaStream_t s) {
   if (phases_.empty()) return ok();
   char* buf = nullptr;
   HSS_TRY(dalloc(reinterpret_cast<void**>(&buf), host_.size(), s));
-  // one copy from pageable memory: it is staged before the call returns
-  HSS_CUDA_TRY(cudaMemcpyAsync(buf, host_.data(), host_.size(), cudaMemcpyHostToDevice, s));
+  HSS_TRY(upload_async(buf, host_.data(), host_.size(), s));
   Err e;
   for (const Phase& ph : phases_) {
-    gemm_batched_kernel<T><<<ph.tiles, G_THREADS, 0, s>>>(
-        reinterpret_cast<const GemmItem<T>*>(buf + ph.items_off),
-        reinterpret_cast<const int*>(buf + ph.starts_off), ph.n);
-    e = check_launch("gemm_batched_kernel");
+    launch_gemm_shape<T>(GemmShape{ph.nc}, ph.tiles,
+                         reinterpret_cast<const GemmItem<T>*>(buf + ph.items_off),
+                         reinterpret_cast<const int*>(buf + ph.starts_off), ph.n, s);
+    e = check_launch(ph.nc ? "gemm_narrow_kernel" : "gemm_batched_kernel");
     if (e.st) break;
   }
   dfree(buf, s);

@@ -53,6 +53,76 @@ __device__ __forceinline__ double ld_any(const void* p, int64_t i, int f64) {
   return f64 ? reinterpret_cast<const double*>(p)[i] : (double)reinterpret_cast<const float*>(p)[i];
 }
 
+// The solve kernels keep one right-hand side per warp in shared memory
+// (U_MAXM values: the small-node path takes nodes of fewer than 320 rows)
+// and stream the rows of their triangular factors or reflectors through
+// shared memory U_RB rows at a time, loaded by the whole block with
+// independent coalesced loads.  Each row's dot product is split over the
+// lanes (lane q takes the entries q mod 32) and summed by a butterfly, so the
+// result of a column depends neither on nrhs nor on what shares the launch.
+constexpr int U_MAXM = 320, U_RB = 8;
+
+struct SolveSmem {
+  double rows[U_RB][U_MAXM];   // rows [i0, i0 + U_RB) of the streamed matrix
+  double col[U_WARPS][U_MAXM]; // warp w's right-hand side
+};
+
+// rows[t][q] = A[(i0 + t) * ld + q] for t < i1 - i0, q0 <= q < q1; whole block
+__device__ __forceinline__ void stage_rows(SolveSmem& sm, const double* A, int64_t ld, int i0,
+                                           int i1, int q0, int q1) {
+  const int w = q1 - q0;
+  for (int e = threadIdx.x; e < (i1 - i0) * w; e += U_THREADS) {
+    const int t = e / w, q = q0 + (e - t * w);
+    sm.rows[t][q] = A[(int64_t)(i0 + t) * ld + q];
+  }
+}
+
+// x = T^{-1} x on a warp's column x[0..m) with T lower triangular (row-major,
+// ld), unit diagonal or not: rows in increasing order.  Every warp of the
+// block calls it (the staging is block-wide); `active` says whether this
+// warp holds a column.
+__device__ void warp_lower_solve(SolveSmem& sm, double* x, const double* T, int64_t ld, int m,
+                                 bool unit, bool active) {
+  const int lane = threadIdx.x & 31;
+  for (int i0 = 0; i0 < m; i0 += U_RB) {
+    const int i1 = min(m, i0 + U_RB);
+    __syncthreads();
+    stage_rows(sm, T, ld, i0, i1, 0, i1);
+    __syncthreads();
+    if (!active) continue;
+    for (int i = i0; i < i1; ++i) {
+      const double* t = sm.rows[i - i0];
+      double p = 0.0;
+      for (int j = lane; j < i; j += 32) p = fma(t[j], x[j], p);
+      p = wsum(p);
+      if (lane == 0) x[i] = unit ? x[i] - p : (x[i] - p) / t[i];
+      __syncwarp();
+    }
+  }
+}
+
+// x = T^{-1} x with T upper triangular (non-unit diagonal): rows in
+// decreasing order.
+__device__ void warp_upper_solve(SolveSmem& sm, double* x, const double* T, int64_t ld, int m,
+                                 bool active) {
+  const int lane = threadIdx.x & 31;
+  for (int i1 = m; i1 > 0; i1 -= U_RB) {
+    const int i0 = max(0, i1 - U_RB);
+    __syncthreads();
+    stage_rows(sm, T, ld, i0, i1, i0, m);
+    __syncthreads();
+    if (!active) continue;
+    for (int i = i1 - 1; i >= i0; --i) {
+      const double* t = sm.rows[i - i0];
+      double p = 0.0;
+      for (int j = i + 1 + lane; j < m; j += 32) p = fma(t[j], x[j], p);
+      p = wsum(p);
+      if (lane == 0) x[i] = (x[i] - p) / t[i];
+      __syncwarp();
+    }
+  }
+}
+
 struct FacItem {
   int m, k, kc, mc, leaf, root;
   const void* D;          // leaf block (input dtype), ld m
@@ -339,27 +409,33 @@ __global__ void __launch_bounds__(U_THREADS) ulv_solve_up_kernel(const SolItem* 
     b[e] = v;
   }
   __syncthreads();
-  if (it.root) {
-    for (int c = tid; c < nr; c += U_THREADS) {
-      double* x = it.x;
-      for (int i = 0; i < m; ++i) x[(int64_t)i * nr + c] = b[(int64_t)i * nr + c];
-      for (int i = 0; i < m; ++i) {
-        int p = it.piv[i];
-        if (p != i) {
-          double t = x[(int64_t)i * nr + c];
-          x[(int64_t)i * nr + c] = x[(int64_t)p * nr + c];
-          x[(int64_t)p * nr + c] = t;
-        }
+  __shared__ SolveSmem sm;
+  const int w = tid >> 5, lane = tid & 31;
+  double* xw = sm.col[w];
+  if (it.root) {   // x = U^{-1} L^{-1} P b with the root's LU (m < U_MAXM)
+    if (m > U_MAXM) return;
+    for (int c0 = 0; c0 < nr; c0 += U_WARPS) {
+      const int c = c0 + w;
+      const bool active = c < nr;
+      if (active) {
+        for (int i = lane; i < m; i += 32) xw[i] = b[(int64_t)i * nr + c];
+        __syncwarp();
+        if (lane == 0)
+          for (int i = 0; i < m; ++i) {
+            const int p = it.piv[i];
+            if (p != i) {
+              const double t = xw[i];
+              xw[i] = xw[p];
+              xw[p] = t;
+            }
+          }
+        __syncwarp();
       }
-      for (int i = 0; i < m; ++i) {
-        double v = x[(int64_t)i * nr + c];
-        for (int j = 0; j < i; ++j) v = fma(-it.lu[(int64_t)i * m + j], x[(int64_t)j * nr + c], v);
-        x[(int64_t)i * nr + c] = v;
-      }
-      for (int i = m - 1; i >= 0; --i) {
-        double v = x[(int64_t)i * nr + c];
-        for (int j = i + 1; j < m; ++j) v = fma(-it.lu[(int64_t)i * m + j], x[(int64_t)j * nr + c], v);
-        x[(int64_t)i * nr + c] = v / it.lu[(int64_t)i * m + i];
+      warp_lower_solve(sm, xw, it.lu, m, m, true, active);
+      warp_upper_solve(sm, xw, it.lu, m, m, active);
+      if (active) {
+        __syncwarp();
+        for (int i = lane; i < m; i += 32) it.x[(int64_t)i * nr + c] = xw[i];
       }
     }
     return;
@@ -377,11 +453,19 @@ __global__ void __launch_bounds__(U_THREADS) ulv_solve_up_kernel(const SolItem* 
   }
   __syncthreads();
   // y = L^{-1} btilde_t
-  for (int c = tid; c < nr; c += U_THREADS) {
-    for (int i = 0; i < r; ++i) {
-      double v = it.y[(int64_t)i * nr + c];
-      for (int j = 0; j < i; ++j) v = fma(-it.L[(int64_t)i * r + j], it.y[(int64_t)j * nr + c], v);
-      it.y[(int64_t)i * nr + c] = v / it.L[(int64_t)i * r + i];
+  if (r <= U_MAXM) {
+    for (int c0 = 0; c0 < nr; c0 += U_WARPS) {
+      const int c = c0 + w;
+      const bool active = c < nr;
+      if (active) {
+        for (int i = lane; i < r; i += 32) xw[i] = it.y[(int64_t)i * nr + c];
+        __syncwarp();
+      }
+      warp_lower_solve(sm, xw, it.L, r, r, false, active);
+      if (active) {
+        __syncwarp();
+        for (int i = lane; i < r; i += 32) it.y[(int64_t)i * nr + c] = xw[i];
+      }
     }
   }
   __syncthreads();
@@ -415,23 +499,44 @@ struct DownItem {
 __global__ void __launch_bounds__(U_THREADS) ulv_solve_down_kernel(const DownItem* items, int f64) {
   const DownItem it = items[blockIdx.x];
   const int m = it.m, r = it.r, nr = it.nrhs;
-  for (int c = threadIdx.x; c < nr; c += U_THREADS) {
-    double* v = it.x;   // m x nrhs scratch (also for leaves)
-    for (int i = 0; i < m; ++i)
-      v[(int64_t)i * nr + c] = i < r ? it.y[(int64_t)i * nr + c] : it.xp[(int64_t)(i - r) * nr + c];
-    for (int i = r - 1; i >= 0; --i) {   // Q^T = H_0 H_1 ... H_{r-1}
-      const double* h = it.hv + (int64_t)i * m;
-      double dot = 0.0;
-      for (int q = i; q < m; ++q) dot = fma(h[q], v[(int64_t)q * nr + c], dot);
-      dot *= it.tau[i];
-      for (int q = i; q < m; ++q) v[(int64_t)q * nr + c] = fma(-dot, h[q], v[(int64_t)q * nr + c]);
+  if (m > U_MAXM) return;
+  __shared__ SolveSmem sm;
+  __shared__ double taus[U_RB];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* v = sm.col[w];
+  for (int c0 = 0; c0 < nr; c0 += U_WARPS) {
+    const int c = c0 + w;
+    const bool active = c < nr;
+    if (active)
+      for (int i = lane; i < m; i += 32)
+        v[i] = i < r ? it.y[(int64_t)i * nr + c] : it.xp[(int64_t)(i - r) * nr + c];
+    // Q^T = H_0 H_1 ... H_{r-1}: reflectors r-1 down to 0, U_RB at a time
+    for (int i1 = r; i1 > 0; i1 -= U_RB) {
+      const int i0 = max(0, i1 - U_RB);
+      __syncthreads();
+      stage_rows(sm, it.hv, m, i0, i1, i0, m);
+      if (threadIdx.x < i1 - i0) taus[threadIdx.x] = it.tau[i0 + threadIdx.x];
+      __syncthreads();
+      if (!active) continue;
+      for (int i = i1 - 1; i >= i0; --i) {
+        const double* h = sm.rows[i - i0];
+        double dot = 0.0;
+        for (int q = i + lane; q < m; q += 32) dot = fma(h[q], v[q], dot);
+        dot = wsum(dot) * taus[i - i0];
+        for (int q = i + lane; q < m; q += 32) v[q] = fma(-dot, h[q], v[q]);
+        __syncwarp();
+      }
     }
-    if (it.leaf) {
-      for (int i = 0; i < m; ++i) {
-        double val = v[(int64_t)i * nr + c];
-        int64_t o = (int64_t)(it.lo + i) * it.ldx + c;
+    if (!active) continue;
+    __syncwarp();
+    for (int i = lane; i < m; i += 32) {
+      const double val = v[i];
+      if (it.leaf) {
+        const int64_t o = (int64_t)(it.lo + i) * it.ldx + c;
         if (f64) reinterpret_cast<double*>(it.Xout)[o] = val;
         else reinterpret_cast<float*>(it.Xout)[o] = (float)val;
+      } else {
+        it.x[(int64_t)i * nr + c] = val;
       }
     }
   }
@@ -448,8 +553,7 @@ __global__ void copy_out_kernel(const double* x, int m, int nr, void* X, int64_t
 template <typename TI>
 Err upload_and_launch(const std::vector<TI>& items, cudaStream_t s, TI** dev) {
   HSS_TRY(dalloc_t(dev, std::max<size_t>(items.size(), 1), s));
-  HSS_CUDA_TRY(cudaMemcpyAsync(*dev, items.data(), items.size() * sizeof(TI),
-                               cudaMemcpyHostToDevice, s));
+  HSS_TRY(upload_async(*dev, items.data(), items.size() * sizeof(TI), s));
   return ok();
 }
 

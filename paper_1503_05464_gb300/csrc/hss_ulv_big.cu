@@ -357,6 +357,129 @@ __global__ void apply_piv_kernel(double* x, const int32_t* piv, int m, int nr) {
   }
 }
 
+// One-launch triangular solves for few right-hand sides: the blocked solve
+// takes two launches per NB rows, each busy on one column per thread.  Here
+// a block takes one matrix and W_COLS columns (one per warp, held in shared
+// memory) and streams the rows of T through shared memory W_RB at a time.
+// For a chunk of rows the terms of the columns already solved go to the
+// lanes (lane q takes the entries q mod 32, W_RB independent sums), are
+// summed by a butterfly, and lane 0 finishes the chunk's small triangle in
+// order.  Optionally: row interchanges first (factorization order), and an
+// upper solve after the lower one with the same matrix (the root's LU).
+// A column's arithmetic depends only on its matrix, never on nr or on what
+// shares the launch.
+constexpr int W_COLS = 4, W_RB = 8, W_THREADS = 32 * W_COLS;
+constexpr int W_MAXM = 2400;   // (W_RB + W_COLS) * 2400 * 8 bytes = 225 KiB of shared memory
+constexpr int W_MAXNR = 64;
+
+struct WTrsmItem {
+  const double* T;        // m x m (ld ldt): lower triangle, then (upper) its upper triangle
+  int64_t ldt;
+  double* X;              // m x nr, ld nr, in place
+  const int32_t* piv;     // null: no interchanges
+  int m, nr, lower_unit, upper;
+};
+
+__global__ void __launch_bounds__(W_THREADS)
+warp_trsm_kernel(const WTrsmItem* __restrict__ items, const int2* __restrict__ map) {
+  extern __shared__ double wsm[];
+  const int2 tm = map[blockIdx.x];
+  const WTrsmItem it = items[tm.x];
+  const int m = it.m, nr = it.nr;
+  double* rows = wsm;                       // [W_RB][m]
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* x = wsm + (size_t)W_RB * m + (size_t)w * m;   // this warp's column
+  const int c = tm.y * W_COLS + w;
+  const bool active = c < nr;
+  if (active) {
+    for (int i = lane; i < m; i += 32) x[i] = it.X[(int64_t)i * nr + c];
+    __syncwarp();
+    if (it.piv && lane == 0)
+      for (int i = 0; i < m; ++i) {
+        const int p = it.piv[i];
+        if (p != i) {
+          const double t = x[i];
+          x[i] = x[p];
+          x[p] = t;
+        }
+      }
+    __syncwarp();
+  }
+  auto stage = [&](int i0, int i1, int q0, int q1) {
+    const int wd = q1 - q0;
+    for (int e = threadIdx.x; e < (i1 - i0) * wd; e += W_THREADS) {
+      const int t = e / wd, q = q0 + (e - t * wd);
+      rows[(size_t)t * m + q] = it.T[(int64_t)(i0 + t) * it.ldt + q];
+    }
+  };
+  // lower: x = L^{-1} x, rows in increasing order
+  for (int i0 = 0; i0 < m; i0 += W_RB) {
+    const int i1 = min(m, i0 + W_RB), nb = i1 - i0;
+    __syncthreads();
+    stage(i0, i1, 0, i1);
+    __syncthreads();
+    if (!active) continue;
+    double p[W_RB];
+#pragma unroll
+    for (int t = 0; t < W_RB; ++t) p[t] = 0.0;
+    for (int j = lane; j < i0; j += 32) {
+      const double xj = x[j];
+#pragma unroll
+      for (int t = 0; t < W_RB; ++t)
+        if (t < nb) p[t] = fma(rows[(size_t)t * m + j], xj, p[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < W_RB; ++t) p[t] = wsum_b(p[t]);
+    if (lane == 0) {
+#pragma unroll
+      for (int t = 0; t < W_RB; ++t) {
+        if (t >= nb) break;
+        const int i = i0 + t;
+        const double* row = rows + (size_t)t * m;
+        double v = x[i] - p[t];
+        for (int j = i0; j < i; ++j) v = fma(-row[j], x[j], v);
+        x[i] = it.lower_unit ? v : v / row[i];
+      }
+    }
+    __syncwarp();
+  }
+  // upper: x = U^{-1} x, rows in decreasing order
+  if (it.upper)
+    for (int i1 = m; i1 > 0; i1 -= W_RB) {
+      const int i0 = max(0, i1 - W_RB), nb = i1 - i0;
+      __syncthreads();
+      stage(i0, i1, i0, m);
+      __syncthreads();
+      if (!active) continue;
+      double p[W_RB];
+#pragma unroll
+      for (int t = 0; t < W_RB; ++t) p[t] = 0.0;
+      for (int j = i1 + lane; j < m; j += 32) {
+        const double xj = x[j];
+#pragma unroll
+        for (int t = 0; t < W_RB; ++t)
+          if (t < nb) p[t] = fma(rows[(size_t)t * m + j], xj, p[t]);
+      }
+#pragma unroll
+      for (int t = 0; t < W_RB; ++t) p[t] = wsum_b(p[t]);
+      if (lane == 0) {
+#pragma unroll
+        for (int t = W_RB - 1; t >= 0; --t) {
+          if (t >= nb) continue;
+          const int i = i0 + t;
+          const double* row = rows + (size_t)t * m;
+          double v = x[i] - p[t];
+          for (int j = i + 1; j < i1; ++j) v = fma(-row[j], x[j], v);
+          x[i] = v / row[i];
+        }
+      }
+      __syncwarp();
+    }
+  if (!active) return;
+  __syncwarp();
+  for (int i = lane; i < m; i += 32) it.X[(int64_t)i * nr + c] = x[i];
+}
+
 // X[lo + i][c] = v[i][c] in the output dtype
 __global__ void store_rows_kernel(const double* v, int m, int nr, void* X, int64_t ldx, int lo,
                                   int f64) {
@@ -756,6 +879,29 @@ Err blocked_trsm(const std::vector<TriItem>& base, const std::vector<int>& ord, 
   return ok();
 }
 
+bool warp_trsm_fits(int m, int nr) { return m <= W_MAXM && nr <= W_MAXNR; }
+
+// one launch for every item (all of them warp_trsm_fits)
+Err warp_trsm(const std::vector<WTrsmItem>& items, cudaStream_t s, Arena& ar) {
+  if (items.empty()) return ok();
+  std::vector<int2> map;
+  int maxm = 0;
+  for (size_t q = 0; q < items.size(); ++q) {
+    maxm = std::max(maxm, items[q].m);
+    for (int g = 0; g * W_COLS < items[q].nr; ++g) map.push_back(make_int2((int)q, g));
+  }
+  if (map.empty() || maxm == 0) return ok();
+  const size_t smem = sizeof(double) * (size_t)(W_RB + W_COLS) * maxm;
+  HSS_CUDA_TRY(cudaFuncSetAttribute(warp_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  WTrsmItem* di = nullptr;
+  int2* dm = nullptr;
+  HSS_TRY(upload(items, s, ar, &di));
+  HSS_TRY(upload(map, s, ar, &dm));
+  warp_trsm_kernel<<<(unsigned)map.size(), W_THREADS, smem, s>>>(di, dm);
+  return check_launch("warp_trsm_kernel");
+}
+
 }  // namespace
 
 // Upward sweep of the solve (Algorithm 4) for the large nodes of one level of
@@ -814,21 +960,28 @@ Err ulv_solve_up_big_multi(const std::vector<UpBigWork>& work, cudaStream_t s) {
     HSS_TRY(run_gemms(g1, s, ar));
     HSS_TRY(run_gemms(g2, s, ar));
   }
-  // roots: x = U^{-1} L^{-1} P b, every root's blocks in shared launches
+  // roots: x = U^{-1} L^{-1} P b, every root in shared launches (one launch
+  // for all roots with few columns, the blocked solve for the others)
   {
     std::vector<TriItem> base;
     std::vector<int> ord;
+    std::vector<WTrsmItem> wt;
     for (const UpBigWork& w : work) {
       if (!(w.ids.size() == 1 && w.ids[0] == 0)) continue;
       const UlvFactors& F = w.h->ulv;
       const UlvBufs& me = (*w.bufs)[0];
       const int m = F.root_m, nr = w.nr;
       HSS_CUDA_TRY(cudaMemcpyAsync(me.x, me.b, sizeof(double) * m * nr, cudaMemcpyDeviceToDevice, s));
+      if (warp_trsm_fits(m, nr)) {
+        wt.push_back({F.root_lu, m, me.x, F.root_piv, m, nr, 1, 1});
+        continue;
+      }
       apply_piv_kernel<<<(nr + 127) / 128, 128, 0, s>>>(me.x, F.root_piv, m, nr);
       HSS_TRY(check_launch("apply_piv_kernel"));
       base.push_back({F.root_lu, m, me.x, nr, 0, 0, 0, 1});
       ord.push_back(m);
     }
+    HSS_TRY(warp_trsm(wt, s, ar));
     if (!base.empty()) {
       HSS_TRY(blocked_trsm(base, ord, false, s, ar));
       for (TriItem& t : base) {
@@ -843,6 +996,7 @@ Err ulv_solve_up_big_multi(const std::vector<UpBigWork>& work, cudaStream_t s) {
     std::vector<GemmItem<double>> gm;
     std::vector<TriItem> base;
     std::vector<int> ord;
+    std::vector<WTrsmItem> wt;
     for (const UpBigWork& w : work) {
       if (w.ids.size() == 1 && w.ids[0] == 0) continue;
       const UlvFactors& F = w.h->ulv;
@@ -859,13 +1013,16 @@ Err ulv_solve_up_big_multi(const std::vector<UpBigWork>& work, cudaStream_t s) {
         GemmItem<double> bot = gemm(me.btb, nr, u.k, nr, 0, nullptr, 1, 0, nullptr, 1, 0, me.b, nr, 1.0);
         bot.X.map = g.permr;
         gm.push_back(bot);
-        if (r > 0) {
+        if (r > 0 && warp_trsm_fits(r, nr)) {
+          wt.push_back({u.L, r, me.y, nullptr, r, nr, 0, 0});
+        } else if (r > 0) {
           base.push_back({u.L, r, me.y, nr, 0, 0, 0, 0});
           ord.push_back(r);
         }
       }
     }
     HSS_TRY(run_gemms(gm, s, ar));
+    HSS_TRY(warp_trsm(wt, s, ar));
     HSS_TRY(blocked_trsm(base, ord, false, s, ar));
   }
   {

@@ -543,6 +543,33 @@ def test_compress_uneven_tree_split_modes(P, mode):
         assert abs(ranks[i][2] - ro[i][0]) <= 2 + (2 if mode == "bf16x2" else 0), (i, ranks[i], ro[i])
 
 
+# ------------------------------------------------------------ Algorithm 2 widths
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_matvec_column_counts(P, dtype):
+    """Algorithm 2 at 1 to 70 right-hand sides.  Up to 32 columns the level
+    products run on the narrow kernel, wider ones on 64 x 64 tiles; in both a
+    column's sums do not depend on the other columns, so a column of a wide
+    call equals the call on that column alone (on the same kernel), and every
+    width matches the dense product."""
+    A = torch.tensor(W.random_hss(2000, 128, 12, seed=5, diag_shift=10.0)[0], device=DEV).to(dtype)
+    f64 = dtype == torch.float64
+    h = P.hss_compress(A, leaf_size=128, rtol=1e-10 if f64 else 1e-5, d0=64, d_step=32, seed=3)
+    g = torch.Generator(device=DEV).manual_seed(12)
+    X = torch.randn(2000, 70, dtype=torch.float64, device=DEV, generator=g).to(dtype)
+    tol = 1e-9 if f64 else 1e-4
+    outs = {}
+    for k in (1, 2, 3, 5, 8, 17, 32, 33, 40, 70):
+        Y = P.hss_matvec(h, X[:, :k].contiguous())
+        ref = A.double() @ X[:, :k].double()
+        assert float(torch.linalg.norm(Y.double() - ref) / torch.linalg.norm(ref)) <= tol, k
+        outs[k] = Y
+    for k in (2, 3, 5, 8, 17, 32):        # narrow kernel
+        assert torch.equal(outs[k][:, :1], outs[1]), k
+        assert torch.equal(outs[32][:, :k], outs[k]), k
+    for k in (33, 40):                    # tile kernel
+        assert torch.equal(outs[70][:, :k], outs[k]), k
+
+
 # ------------------------------------------------------------ edge cases
 def test_single_node_tree(P):
     n = 100
@@ -550,7 +577,11 @@ def test_single_node_tree(P):
     At = torch.tensor(A, device=DEV)
     h = P.hss_compress(At, leaf_size=128)
     x = torch.randn(n, 2, dtype=torch.float64, device=DEV)
-    np.testing.assert_allclose(P.hss_matvec(h, x).cpu().numpy(), A @ x.cpu().numpy(), rtol=1e-12)
+    xn = x.cpu().numpy()
+    # H = D exactly; the product differs from numpy's only by the order of its
+    # sums: the FP64 dot-product bound |err| <= n u |A| |x| per entry
+    bound = n * np.finfo(np.float64).eps * (np.abs(A) @ np.abs(xn))
+    assert np.all(np.abs(P.hss_matvec(h, x).cpu().numpy() - A @ xn) <= bound)
     P.hss_factor(h)
     xs = P.hss_solve(h, x).cpu().numpy()
     np.testing.assert_allclose(A @ xs, x.cpu().numpy(), atol=1e-10)
@@ -862,6 +893,16 @@ def test_ulv_large_nodes_match_dense_solve(P, dtype):
     xd = np.linalg.solve(A64, b)
     if dtype == torch.float64:
         np.testing.assert_allclose(xs, xd, rtol=0, atol=1e-8 * np.abs(xd).max())
+        # up to 64 right-hand sides the large nodes' triangular solves take one
+        # launch (a column per warp); more take the blocked solve.  Both end at
+        # the compression error (1e-12) times this matrix's conditioning: the
+        # blocked solve's 70 columns were measured 1.4e-8 of max |x| from the
+        # dense solve
+        b70 = np.random.default_rng(6).standard_normal((n, 70))
+        x70 = P.hss_solve(h, torch.tensor(b70, device=DEV)).cpu().numpy()
+        xd70 = np.linalg.solve(A64, b70)
+        np.testing.assert_allclose(x70, xd70, rtol=0, atol=1e-7 * np.abs(xd70).max())
+        assert _rel(A64 @ x70, b70) <= 100 * _rel(A64 @ xs, b) + 1e-12
     else:
         ho = O.compress(A64, rtol, leaf_size=leaf, d0=256, d_step=128, seed=8)
         O.ulv_factor(ho)
