@@ -77,49 +77,80 @@ __device__ __forceinline__ void stage_rows(SolveSmem& sm, const double* A, int64
   }
 }
 
-// x = T^{-1} x on a warp's column x[0..m) with T lower triangular (row-major,
-// ld), unit diagonal or not: rows in increasing order.  Every warp of the
-// block calls it (the staging is block-wide); `active` says whether this
-// warp holds a column.
-__device__ void warp_lower_solve(SolveSmem& sm, double* x, const double* T, int64_t ld, int m,
-                                 bool unit, bool active) {
+// Sums p[0..7] over the 32 lanes; lanes u and u + 8k return the sum of p[u].
+__device__ __forceinline__ double reduce_scatter8(double (&p)[U_RB]) {
   const int lane = threadIdx.x & 31;
-  for (int i0 = 0; i0 < m; i0 += U_RB) {
-    const int i1 = min(m, i0 + U_RB);
-    __syncthreads();
-    stage_rows(sm, T, ld, i0, i1, 0, i1);
-    __syncthreads();
-    if (!active) continue;
-    for (int i = i0; i < i1; ++i) {
-      const double* t = sm.rows[i - i0];
-      double p = 0.0;
-      for (int j = lane; j < i; j += 32) p = fma(t[j], x[j], p);
-      p = wsum(p);
-      if (lane == 0) x[i] = unit ? x[i] - p : (x[i] - p) / t[i];
-      __syncwarp();
+#pragma unroll
+  for (int h = U_RB / 2; h >= 1; h >>= 1) {
+    const bool hi = (lane & h) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const double mine = hi ? p[h + k] : p[k];
+      const double oth = hi ? p[k] : p[h + k];
+      p[k] = mine + __shfl_xor_sync(0xffffffffu, oth, h);
     }
   }
+  p[0] += __shfl_xor_sync(0xffffffffu, p[0], 8);
+  p[0] += __shfl_xor_sync(0xffffffffu, p[0], 16);
+  return p[0];
 }
 
-// x = T^{-1} x with T upper triangular (non-unit diagonal): rows in
-// decreasing order.
-__device__ void warp_upper_solve(SolveSmem& sm, double* x, const double* T, int64_t ld, int m,
-                                 bool active) {
+// x = T^{-1} x on a warp's column x[0..m) with T triangular (row-major, ld):
+// lower (unit diagonal or not, rows in increasing order) or upper (rows in
+// decreasing order).  Chunks of U_RB rows: the terms of the rows already
+// solved are split over the lanes (U_RB sums per lane) and reduce-scattered,
+// so that lane u holds row u of the chunk; the chunk's diagonal block is then
+// solved by a column sweep (lane t's value is final at step t, times the
+// reciprocal of the diagonal, and is broadcast to the later rows).  Every
+// warp of the block calls it (the staging is block-wide); `active` says
+// whether this warp holds a column.
+__device__ void warp_tri_solve(SolveSmem& sm, double* x, const double* T, int64_t ld, int m,
+                               bool upper, bool unit, bool active) {
   const int lane = threadIdx.x & 31;
-  for (int i1 = m; i1 > 0; i1 -= U_RB) {
-    const int i0 = max(0, i1 - U_RB);
+  const int nch = (m + U_RB - 1) / U_RB;
+  for (int ch = 0; ch < nch; ++ch) {
+    const int i0 = upper ? max(0, m - (ch + 1) * U_RB) : ch * U_RB;
+    const int i1 = upper ? m - ch * U_RB : min(m, i0 + U_RB);
+    const int nb = i1 - i0;
     __syncthreads();
-    stage_rows(sm, T, ld, i0, i1, i0, m);
+    if (upper) stage_rows(sm, T, ld, i0, i1, i0, m);
+    else stage_rows(sm, T, ld, i0, i1, 0, i1);
     __syncthreads();
     if (!active) continue;
-    for (int i = i1 - 1; i >= i0; --i) {
-      const double* t = sm.rows[i - i0];
-      double p = 0.0;
-      for (int j = i + 1 + lane; j < m; j += 32) p = fma(t[j], x[j], p);
-      p = wsum(p);
-      if (lane == 0) x[i] = (x[i] - p) / t[i];
-      __syncwarp();
+    double p[U_RB];
+#pragma unroll
+    for (int t = 0; t < U_RB; ++t) p[t] = 0.0;
+    const int ja = upper ? i1 : 0, jb = upper ? m : i0;
+    for (int j = ja + lane; j < jb; j += 32) {
+      const double xj = x[j];
+#pragma unroll
+      for (int t = 0; t < U_RB; ++t)
+        if (t < nb) p[t] = fma(sm.rows[t][j], xj, p[t]);
     }
+    const int u = lane & (U_RB - 1);
+    const double sum = reduce_scatter8(p);
+    double v = 0.0, rd = 1.0;
+    if (u < nb) {
+      v = x[i0 + u] - sum;
+      if (!unit) rd = 1.0 / sm.rows[u][i0 + u];
+    }
+    double xf = 0.0;
+    if (!upper) {
+      for (int t = 0; t < nb; ++t) {
+        const double xt = __shfl_sync(0xffffffffu, v * rd, t);
+        if (u == t) xf = xt;
+        if (u > t && u < nb) v = fma(-sm.rows[u][i0 + t], xt, v);
+      }
+    } else {
+      for (int t = nb - 1; t >= 0; --t) {
+        const double xt = __shfl_sync(0xffffffffu, v * rd, t);
+        if (u == t) xf = xt;
+        if (u < t) v = fma(-sm.rows[u][i0 + t], xt, v);
+      }
+    }
+    __syncwarp();
+    if (lane < nb) x[i0 + lane] = xf;
+    __syncwarp();
   }
 }
 
@@ -431,8 +462,8 @@ __global__ void __launch_bounds__(U_THREADS) ulv_solve_up_kernel(const SolItem* 
           }
         __syncwarp();
       }
-      warp_lower_solve(sm, xw, it.lu, m, m, true, active);
-      warp_upper_solve(sm, xw, it.lu, m, m, active);
+      warp_tri_solve(sm, xw, it.lu, m, m, false, true, active);
+      warp_tri_solve(sm, xw, it.lu, m, m, true, false, active);
       if (active) {
         __syncwarp();
         for (int i = lane; i < m; i += 32) it.x[(int64_t)i * nr + c] = xw[i];
@@ -461,7 +492,7 @@ __global__ void __launch_bounds__(U_THREADS) ulv_solve_up_kernel(const SolItem* 
         for (int i = lane; i < r; i += 32) xw[i] = it.y[(int64_t)i * nr + c];
         __syncwarp();
       }
-      warp_lower_solve(sm, xw, it.L, r, r, false, active);
+      warp_tri_solve(sm, xw, it.L, r, r, false, false, active);
       if (active) {
         __syncwarp();
         for (int i = lane; i < r; i += 32) it.y[(int64_t)i * nr + c] = xw[i];

@@ -357,19 +357,26 @@ __global__ void apply_piv_kernel(double* x, const int32_t* piv, int m, int nr) {
   }
 }
 
-// One-launch triangular solves for few right-hand sides: the blocked solve
-// takes two launches per NB rows, each busy on one column per thread.  Here
-// a block takes one matrix and W_COLS columns (one per warp, held in shared
-// memory) and streams the rows of T through shared memory W_RB at a time.
-// For a chunk of rows the terms of the columns already solved go to the
-// lanes (lane q takes the entries q mod 32, W_RB independent sums), are
-// summed by a butterfly, and lane 0 finishes the chunk's small triangle in
-// order.  Optionally: row interchanges first (factorization order), and an
-// upper solve after the lower one with the same matrix (the root's LU).
-// A column's arithmetic depends only on its matrix, never on nr or on what
+// One-launch triangular solves for few right-hand sides.  The blocked solve
+// takes two launches per NB rows and runs each diagonal block on one thread
+// per column; FP64 dependence chains on one lane are slow on this GPU.  Here
+// a block of T_THREADS takes one (matrix, column) pair, keeps the column in
+// shared memory and walks it in chunks of T_RB rows:
+//   1. the terms of the rows already solved: thread q takes the entries
+//      q mod T_THREADS of the chunk's T_RB rows (independent coalesced loads
+//      from global memory, T_RB sums per thread);
+//   2. a reduce-scatter butterfly leaves lane u of every warp with its warp's
+//      sum for row u, and warp 0 adds the warps' sums in warp order;
+//   3. warp 0 solves the chunk's diagonal block by a column sweep: lane u
+//      holds row u; at step t lane t's value is final (times the reciprocal
+//      of the diagonal), is broadcast, and the later rows subtract their
+//      multiple of it.
+// Optionally: row interchanges first (factorization order), and an upper
+// solve after the lower one with the same matrix (the root's LU).  A
+// column's arithmetic depends only on its matrix, never on nr or on what
 // shares the launch.
-constexpr int W_COLS = 4, W_RB = 8, W_THREADS = 32 * W_COLS;
-constexpr int W_MAXM = 2400;   // (W_RB + W_COLS) * 2400 * 8 bytes = 225 KiB of shared memory
+constexpr int T_RB = 32, T_THREADS = 128, T_WARPS = T_THREADS / 32;
+constexpr int W_MAXM = 4096;   // the column in shared memory: 32 KiB
 constexpr int W_MAXNR = 64;
 
 struct WTrsmItem {
@@ -380,104 +387,98 @@ struct WTrsmItem {
   int m, nr, lower_unit, upper;
 };
 
-__global__ void __launch_bounds__(W_THREADS)
-warp_trsm_kernel(const WTrsmItem* __restrict__ items, const int2* __restrict__ map) {
-  extern __shared__ double wsm[];
+// sums p[0..31] over the 32 lanes; lane u returns the sum of p[u]
+__device__ __forceinline__ double reduce_scatter32(double (&p)[T_RB]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool hi = (lane & h) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const double mine = hi ? p[h + k] : p[k];
+      const double oth = hi ? p[k] : p[h + k];
+      p[k] = mine + __shfl_xor_sync(0xffffffffu, oth, h);
+    }
+  }
+  return p[0];
+}
+
+__global__ void __launch_bounds__(T_THREADS)
+block_trsm_kernel(const WTrsmItem* __restrict__ items, const int2* __restrict__ map) {
+  __shared__ double x[W_MAXM];
+  __shared__ double tb[T_RB][T_RB + 1];
+  __shared__ double red[T_WARPS][T_RB];
   const int2 tm = map[blockIdx.x];
   const WTrsmItem it = items[tm.x];
-  const int m = it.m, nr = it.nr;
-  double* rows = wsm;                       // [W_RB][m]
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* x = wsm + (size_t)W_RB * m + (size_t)w * m;   // this warp's column
-  const int c = tm.y * W_COLS + w;
-  const bool active = c < nr;
-  if (active) {
-    for (int i = lane; i < m; i += 32) x[i] = it.X[(int64_t)i * nr + c];
-    __syncwarp();
-    if (it.piv && lane == 0)
-      for (int i = 0; i < m; ++i) {
-        const int p = it.piv[i];
-        if (p != i) {
-          const double t = x[i];
-          x[i] = x[p];
-          x[p] = t;
-        }
-      }
-    __syncwarp();
-  }
-  auto stage = [&](int i0, int i1, int q0, int q1) {
-    const int wd = q1 - q0;
-    for (int e = threadIdx.x; e < (i1 - i0) * wd; e += W_THREADS) {
-      const int t = e / wd, q = q0 + (e - t * wd);
-      rows[(size_t)t * m + q] = it.T[(int64_t)(i0 + t) * it.ldt + q];
-    }
-  };
-  // lower: x = L^{-1} x, rows in increasing order
-  for (int i0 = 0; i0 < m; i0 += W_RB) {
-    const int i1 = min(m, i0 + W_RB), nb = i1 - i0;
-    __syncthreads();
-    stage(i0, i1, 0, i1);
-    __syncthreads();
-    if (!active) continue;
-    double p[W_RB];
-#pragma unroll
-    for (int t = 0; t < W_RB; ++t) p[t] = 0.0;
-    for (int j = lane; j < i0; j += 32) {
-      const double xj = x[j];
-#pragma unroll
-      for (int t = 0; t < W_RB; ++t)
-        if (t < nb) p[t] = fma(rows[(size_t)t * m + j], xj, p[t]);
-    }
-#pragma unroll
-    for (int t = 0; t < W_RB; ++t) p[t] = wsum_b(p[t]);
-    if (lane == 0) {
-#pragma unroll
-      for (int t = 0; t < W_RB; ++t) {
-        if (t >= nb) break;
-        const int i = i0 + t;
-        const double* row = rows + (size_t)t * m;
-        double v = x[i] - p[t];
-        for (int j = i0; j < i; ++j) v = fma(-row[j], x[j], v);
-        x[i] = it.lower_unit ? v : v / row[i];
+  const int m = it.m, nr = it.nr, c = tm.y;
+  if (m > W_MAXM) return;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < m; i += T_THREADS) x[i] = it.X[(int64_t)i * nr + c];
+  __syncthreads();
+  if (it.piv && tid == 0)
+    for (int i = 0; i < m; ++i) {
+      const int p = it.piv[i];
+      if (p != i) {
+        const double t = x[i];
+        x[i] = x[p];
+        x[p] = t;
       }
     }
-    __syncwarp();
-  }
-  // upper: x = U^{-1} x, rows in decreasing order
-  if (it.upper)
-    for (int i1 = m; i1 > 0; i1 -= W_RB) {
-      const int i0 = max(0, i1 - W_RB), nb = i1 - i0;
-      __syncthreads();
-      stage(i0, i1, i0, m);
-      __syncthreads();
-      if (!active) continue;
-      double p[W_RB];
+  __syncthreads();
+  for (int pass = 0; pass < (it.upper ? 2 : 1); ++pass) {
+    const bool up = pass == 1, unit = !up && it.lower_unit;
+    const int nch = (m + T_RB - 1) / T_RB;
+    for (int ch = 0; ch < nch; ++ch) {
+      // lower: chunks from the top; upper: from the bottom
+      const int i0 = up ? max(0, m - (ch + 1) * T_RB) : ch * T_RB;
+      const int i1 = up ? m - ch * T_RB : min(m, i0 + T_RB);
+      const int nb = i1 - i0;
+      for (int e = tid; e < nb * nb; e += T_THREADS) {
+        const int u = e / nb, t = e - u * nb;
+        tb[u][t] = it.T[(int64_t)(i0 + u) * it.ldt + i0 + t];
+      }
+      double p[T_RB];
 #pragma unroll
-      for (int t = 0; t < W_RB; ++t) p[t] = 0.0;
-      for (int j = i1 + lane; j < m; j += 32) {
+      for (int u = 0; u < T_RB; ++u) p[u] = 0.0;
+      const int ja = up ? i1 : 0, jb = up ? m : i0;
+      for (int j = ja + tid; j < jb; j += T_THREADS) {
         const double xj = x[j];
+        const double* col = it.T + (int64_t)i0 * it.ldt + j;
 #pragma unroll
-        for (int t = 0; t < W_RB; ++t)
-          if (t < nb) p[t] = fma(rows[(size_t)t * m + j], xj, p[t]);
+        for (int u = 0; u < T_RB; ++u)
+          if (u < nb) p[u] = fma(col[(int64_t)u * it.ldt], xj, p[u]);
       }
+      red[w][lane] = reduce_scatter32(p);
+      __syncthreads();
+      if (w == 0) {
+        double v = 0.0, rd = 1.0;
+        if (lane < nb) {
+          double sum = red[0][lane];
 #pragma unroll
-      for (int t = 0; t < W_RB; ++t) p[t] = wsum_b(p[t]);
-      if (lane == 0) {
-#pragma unroll
-        for (int t = W_RB - 1; t >= 0; --t) {
-          if (t >= nb) continue;
-          const int i = i0 + t;
-          const double* row = rows + (size_t)t * m;
-          double v = x[i] - p[t];
-          for (int j = i + 1; j < i1; ++j) v = fma(-row[j], x[j], v);
-          x[i] = v / row[i];
+          for (int q = 1; q < T_WARPS; ++q) sum += red[q][lane];
+          v = x[i0 + lane] - sum;
+          if (!unit) rd = 1.0 / tb[lane][lane];
         }
+        double xf = 0.0;
+        if (!up) {
+          for (int t = 0; t < nb; ++t) {
+            const double xt = __shfl_sync(0xffffffffu, v * rd, t);
+            if (lane == t) xf = xt;
+            if (lane > t && lane < nb) v = fma(-tb[lane][t], xt, v);
+          }
+        } else {
+          for (int t = nb - 1; t >= 0; --t) {
+            const double xt = __shfl_sync(0xffffffffu, v * rd, t);
+            if (lane == t) xf = xt;
+            if (lane < t) v = fma(-tb[lane][t], xt, v);
+          }
+        }
+        if (lane < nb) x[i0 + lane] = xf;
       }
-      __syncwarp();
+      __syncthreads();
     }
-  if (!active) return;
-  __syncwarp();
-  for (int i = lane; i < m; i += 32) it.X[(int64_t)i * nr + c] = x[i];
+  }
+  for (int i = tid; i < m; i += T_THREADS) it.X[(int64_t)i * nr + c] = x[i];
 }
 
 // X[lo + i][c] = v[i][c] in the output dtype
@@ -881,25 +882,19 @@ Err blocked_trsm(const std::vector<TriItem>& base, const std::vector<int>& ord, 
 
 bool warp_trsm_fits(int m, int nr) { return m <= W_MAXM && nr <= W_MAXNR; }
 
-// one launch for every item (all of them warp_trsm_fits)
+// one launch for every item (all of them warp_trsm_fits): a block per
+// (item, column)
 Err warp_trsm(const std::vector<WTrsmItem>& items, cudaStream_t s, Arena& ar) {
-  if (items.empty()) return ok();
   std::vector<int2> map;
-  int maxm = 0;
-  for (size_t q = 0; q < items.size(); ++q) {
-    maxm = std::max(maxm, items[q].m);
-    for (int g = 0; g * W_COLS < items[q].nr; ++g) map.push_back(make_int2((int)q, g));
-  }
-  if (map.empty() || maxm == 0) return ok();
-  const size_t smem = sizeof(double) * (size_t)(W_RB + W_COLS) * maxm;
-  HSS_CUDA_TRY(cudaFuncSetAttribute(warp_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+  for (size_t q = 0; q < items.size(); ++q)
+    for (int c = 0; c < items[q].nr; ++c) map.push_back(make_int2((int)q, c));
+  if (map.empty()) return ok();
   WTrsmItem* di = nullptr;
   int2* dm = nullptr;
   HSS_TRY(upload(items, s, ar, &di));
   HSS_TRY(upload(map, s, ar, &dm));
-  warp_trsm_kernel<<<(unsigned)map.size(), W_THREADS, smem, s>>>(di, dm);
-  return check_launch("warp_trsm_kernel");
+  block_trsm_kernel<<<(unsigned)map.size(), T_THREADS, 0, s>>>(di, dm);
+  return check_launch("block_trsm_kernel");
 }
 
 }  // namespace
