@@ -77,6 +77,10 @@ WORKLOADS = {
     # (grid spacing 1), n = 80000, FP64, eps = 1e-8, 1e-6, 1e-4, 1e-2
     "table3": dict(family="table3", n=80000, leaf=128, d0=64, step=32, dtype="f64", seed=1006,
                    eps=[1e-8, 1e-6, 1e-4, 1e-2], n_matfree=1000000, power_iters=318),
+    # Algorithms 2 and 4 on a compressed QChemToeplitz (n = 80000, eps 1e-6,
+    # FP64, matrix-free): HSS matvec and ULV solve latency per call
+    "ops80k": dict(family="toeplitz_ops", n=80000, leaf=128, d0=64, step=32, dtype="f64",
+                   seed=1007, rtol=1e-6, nrhs=[1, 16], reps=50),
 }
 # Table 3's printed values for those rows (max rank, HSS factors MB, ULV
 # factors MB), beside which the table3 workload reports its own
@@ -208,7 +212,7 @@ def run_ours(args, wl):
     import __graft_entry__ as g
     g.build()
     import paper_1503_05464_gb300 as P
-    if wl["family"] in ("mixed_batch", "laplacian_schur", "table3"):
+    if wl["family"] in ("mixed_batch", "laplacian_schur", "table3", "toeplitz_ops"):
         return run_aux(args, wl, P, dev, rank, world)
 
     A = make_matrix(wl, dev).contiguous()
@@ -676,6 +680,61 @@ def run_table3(P, dev, stream, wl):
                     "hss_compress_matfree with FFT products (first call includes warm-up)"}
 
 
+def run_ops(P, dev, stream, wl):
+    """HSS matvec (Algorithm 2) and ULV solve (Algorithm 4) of QChemToeplitz
+    compressed matrix-free: per nrhs, milliseconds per call (CUDA events over
+    `reps` calls after three untimed ones), the product's error against the
+    FFT product and the solve's residual.  One more call of each runs inside
+    the NVTX ranges "hss_matvec" and "hss_solve" (for launch lists)."""
+    import torch
+    import workloads as W
+    n = wl["n"]
+    T = W.ToeplitzOperator(n, W.qchem_toeplitz_symbol(1.0), dev)
+    t_c, h = _event_time(stream, lambda: P.hss_compress_matfree(
+        n, T.sample, T.extract, dtype=torch.float64, leaf_size=wl["leaf"], rtol=wl["rtol"],
+        d0=wl["d0"], d_step=wl["step"], seed=wl["seed"]))
+    t_f, _ = _event_time(stream, lambda: P.hss_factor(h, stream))
+    info = P.hss_info(h)
+    out = {"n": n, "rtol": wl["rtol"], "compress_s": t_c, "factor_s": t_f,
+           "max_rank": max(info["max_rank_r"], info["max_rank_c"]), "levels": info["levels"],
+           "hss_mb": info["bytes_hss"] / 1e6, "ulv_mb": info["bytes_ulv"] / 1e6, "per_nrhs": {}}
+    g = torch.Generator(device=dev).manual_seed(wl["seed"] + 1)
+    for k in wl["nrhs"]:
+        x = torch.randn(n, k, dtype=torch.float64, device=dev, generator=g)
+        B = torch.empty_like(x)
+
+        def mv():
+            for _ in range(wl["reps"]):
+                P.hss_matvec(h, x, B, stream=stream)
+
+        def sv():
+            for _ in range(wl["reps"]):
+                P.hss_solve(h, x, stream=stream)
+
+        for _ in range(3):
+            P.hss_matvec(h, x, B, stream=stream)
+            P.hss_solve(h, x, stream=stream)
+        t_mv, _ = _event_time(stream, mv)
+        t_sv, _ = _event_time(stream, sv)
+        torch.cuda.nvtx.range_push("hss_matvec")
+        P.hss_matvec(h, x, B, stream=stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.nvtx.range_push("hss_solve")
+        X = P.hss_solve(h, x, stream=stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        ax = T.matmul(x)
+        out["per_nrhs"][str(k)] = {
+            "matvec_ms": t_mv * 1e3 / wl["reps"], "solve_ms": t_sv * 1e3 / wl["reps"],
+            "matvec_rel_err_vs_fft": float(torch.linalg.norm(B - ax) / torch.linalg.norm(ax)),
+            "solve_rel_residual": float(torch.linalg.norm(T.matmul(X) - x) / torch.linalg.norm(x))}
+    h.close()
+    out["note"] = ("QChemToeplitz is ill-conditioned (cond about 6e9 at this n): the solve's "
+                   "residual follows the compression tolerance times the conditioning")
+    return out
+
+
 def run_aux(args, wl, P, dev, rank, world):
     """The batch512 and serve workloads (each rank runs its own replica)."""
     import torch
@@ -692,6 +751,11 @@ def run_aux(args, wl, P, dev, rank, world):
             res = run_table3(P, dev, stream, wl)
             value, key = res["mean_compress_s"], "table3"
             ms = res["compress_s_total"] * 1e3
+        elif wl["family"] == "toeplitz_ops":
+            res = run_ops(P, dev, stream, wl)
+            one = res["per_nrhs"][str(wl["nrhs"][0])]
+            value, key = one["solve_ms"] / 1e3, "ops"
+            ms = sum(v["matvec_ms"] + v["solve_ms"] for v in res["per_nrhs"].values()) * wl["reps"]
         else:
             if args.bounded:   # the two smallest request sizes
                 wl = dict(wl, ks=wl["ks"][:2])
@@ -703,11 +767,13 @@ def run_aux(args, wl, P, dev, rank, world):
            "warmup": 1, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64-id", "data": "synthetic",
            "config": {"workload": args.workload,
-                      "sample_mode": "native (f64)" if key == "table3" else "bf16x3",
+                      "sample_mode": "native (f64)" if key in ("table3", "ops") else "bf16x3",
                       "value_is": {"batching": "batched seconds per matrix (compress + factor "
                                                "+ solve)",
                                    "serving": "p50 request latency, arrival to first solution",
-                                   "table3": "mean seconds per compression over the 8 runs"}[key]},
+                                   "table3": "mean seconds per compression over the 8 runs",
+                                   "ops": "seconds per 1-RHS ULV solve (Algorithm 4); matvec "
+                                          "and 16-RHS times under 'ops'"}[key]},
            key: res}
     clocks = clk.summary()
     if clocks:
@@ -799,6 +865,10 @@ def run_reference_aux(args, wl, O):
         items = [(W.build_matrix(sp, np.float32, "cpu").numpy().astype(np.float64),
                   sp["rtol"], sp["leaf"], sp["d0"], sp["step"], wl["nrhs"]) for sp in specs]
         sample = "compress + factor + 16-RHS solve of 2 matrices of the batch mix per step"
+    elif wl["family"] == "toeplitz_ops":
+        items = [(W.qchem_toeplitz(4000).numpy(), wl["rtol"], wl["leaf"], wl["d0"], wl["step"], 1)]
+        sample = ("compress + factor + 1-RHS solve of QChemToeplitz at n=4000, eps 1e-6 "
+                  "(not scaled to n=80000)")
     elif wl["family"] == "table3":
         # the FP64 n = 80000 matrices take 51 GB each: the oracle runs both
         # Toeplitz matrices at n = 4000 (eps 1e-6), unscaled
@@ -836,7 +906,7 @@ def run_reference(args, wl):
         return
     import workloads  # noqa: F401
     from oracle import hss_oracle as O
-    if wl["family"] in ("mixed_batch", "laplacian_schur", "table3"):
+    if wl["family"] in ("mixed_batch", "laplacian_schur", "table3", "toeplitz_ops"):
         return run_reference_aux(args, wl, O)
     times = []
     ratio, desc = 1.0, ""
