@@ -264,9 +264,13 @@ struct GemmItem {
   T sign;
   int32_t z_trans;       // 0: Z row l, column c; 1: Z row c, column l (rows of Z are columns)
 };
+// narrow: items of at most 32 columns may take the narrow-column kernel
+// (products with few right-hand sides); otherwise every item takes the
+// 64 x 64 tile kernel.
 template <typename T>
 Err launch_gemm_batched(const std::vector<GemmItem<T>>& items, cudaStream_t s,
-                        void* scratch_dev, size_t scratch_bytes, Arena* scratch = nullptr);
+                        void* scratch_dev, size_t scratch_bytes, Arena* scratch = nullptr,
+                        bool narrow = false);
 // A sequence of batched GEMM launches whose items are all known before the
 // first runs (each phase may read what the earlier ones write): the item
 // tables of every phase go to the device in one copy, then one launch per

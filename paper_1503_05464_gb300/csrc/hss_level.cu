@@ -235,9 +235,11 @@ struct GemmShape {
   }
 };
 
-// Items with at most 32 columns go to the narrow kernel, the others to the
-// tile kernel.  The choice is per item and a column's sums do not depend on
-// nc, so an item's result is the same whatever shares its launch.
+// With `narrow`, items with at most 32 columns go to the narrow kernel, the
+// others to the tile kernel.  The choice is per item and a column's sums do
+// not depend on nc, so an item's result is the same whatever shares its
+// launch.  Compression keeps the tile kernel for every item: its FP32 rank
+// decisions near the tolerance follow the tile kernel's summation order.
 constexpr int NARROW_MAX = 32;
 
 template <typename T>
@@ -249,15 +251,16 @@ struct GemmGroup {
 };
 
 template <typename T>
-void split_gemm(const std::vector<GemmItem<T>>& items, GemmGroup<T> g[2]) {
+void split_gemm(const std::vector<GemmItem<T>>& items, GemmGroup<T> g[2], bool narrow) {
+  const int lim = narrow ? NARROW_MAX : 0;
   int mc = 0;
   for (const auto& it : items)
-    if (it.rows > 0 && it.c1 > it.c0 && it.c1 - it.c0 <= NARROW_MAX) mc = std::max(mc, it.c1 - it.c0);
+    if (it.rows > 0 && it.c1 > it.c0 && it.c1 - it.c0 <= lim) mc = std::max(mc, it.c1 - it.c0);
   g[0].shape.nc = 0;
   g[1].shape.nc = mc <= 1 ? 1 : mc == 2 ? 2 : mc <= 4 ? 4 : 8;
   for (const auto& it : items) {
     if (it.rows <= 0 || it.c1 <= it.c0) continue;
-    GemmGroup<T>& q = g[it.c1 - it.c0 <= NARROW_MAX ? 1 : 0];
+    GemmGroup<T>& q = g[it.c1 - it.c0 <= lim ? 1 : 0];
     const int t = q.shape.tiles(it.rows, it.c1 - it.c0);
     if (q.shape.nc) {   // (item, tile of the item) per block
       for (int k = 0; k < t; ++k) {
@@ -427,9 +430,9 @@ Err launch_invert_batched(const std::vector<InvItem>& items, cudaStream_t s, Are
 
 template <typename T>
 Err launch_gemm_batched(const std::vector<GemmItem<T>>& items, cudaStream_t s,
-                        void* scratch_dev, size_t scratch_bytes, Arena* scratch) {
+                        void* scratch_dev, size_t scratch_bytes, Arena* scratch, bool narrow) {
   GemmGroup<T> grp[2];
-  split_gemm(items, grp);
+  split_gemm(items, grp, narrow);
   for (const GemmGroup<T>& g : grp) {
     if (g.live.empty()) continue;
     size_t bi = g.live.size() * sizeof(GemmItem<T>);
@@ -555,7 +558,7 @@ Err launch_index_compose(int32_t* out, const int32_t* base, const int32_t* idx, 
 template <typename T>
 void GemmPlan<T>::add(const std::vector<GemmItem<T>>& items) {
   GemmGroup<T> grp[2];
-  split_gemm(items, grp);
+  split_gemm(items, grp, true);
   auto append = [&](const void* p, size_t bytes) {
     const size_t off = (host_.size() + 255) & ~size_t(255);
     host_.resize(off + bytes);
@@ -596,9 +599,9 @@ template class GemmPlan<float>;
 template class GemmPlan<double>;
 
 template Err launch_gemm_batched<float>(const std::vector<GemmItem<float>>&, cudaStream_t, void*,
-                                        size_t, Arena*);
+                                        size_t, Arena*, bool);
 template Err launch_gemm_batched<double>(const std::vector<GemmItem<double>>&, cudaStream_t,
-                                         void*, size_t, Arena*);
+                                         void*, size_t, Arena*, bool);
 template Err launch_gather_batched<float>(const float*, int64_t,
                                           const std::vector<GatherItem<float>>&, cudaStream_t,
                                           void*, size_t, Arena*);

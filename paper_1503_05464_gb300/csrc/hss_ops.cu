@@ -147,7 +147,7 @@ static Err matvec_impl(hss_s* h, const T* X, int64_t ldx, int nrhs, T* B, int64_
     it.M = h->gen[0].D;
     it.ldm = h->n;
     it.sign = T(1);
-    return launch_gemm_batched<T>({it}, s, nullptr, 0);
+    return launch_gemm_batched<T>({it}, s, nullptr, 0, nullptr, true);
   }
   // y_tau (kc x nrhs), z_tau (kr x nrhs), Ez_tau ((mr - kr) x nrhs) per non-root node
   std::vector<int64_t> oy(nn, 0), oz(nn, 0), oe(nn, 0);

@@ -548,7 +548,7 @@ Err run_gemms(const std::vector<GemmItem<double>>& v, cudaStream_t s, Arena& ar)
   for (const auto& g : v)
     if (g.rows > 0 && g.c1 > g.c0) live.push_back(g);
   if (live.empty()) return ok();
-  return launch_gemm_batched<double>(live, s, nullptr, 0, &ar);
+  return launch_gemm_batched<double>(live, s, nullptr, 0, &ar, true);
 }
 
 }  // namespace
