@@ -175,7 +175,9 @@ hss_status hss_compress_matfree(int64_t n, hss_dtype dtype, const hss_matfree* o
  * hss_matvec -- B = H X with the compressed form (Algorithm 2).
  *   X  device, n x nrhs row-major, ldx >= nrhs, the handle's dtype.
  *   B  device, n x nrhs row-major, ldb >= nrhs; must not overlap X.
- * Errors: INVALID, OOM, CUDA.  Stream-ordered.
+ * Errors: INVALID, OOM, CUDA.  Stream-ordered: the call returns without
+ * waiting for the device (its small tables go up through pinned blocks of
+ * the calling thread, eight of which may be in flight).
  */
 hss_status hss_matvec(hss_t h, const void* X, int64_t ldx, int64_t nrhs,
                       void* B, int64_t ldb, void* stream);
@@ -191,7 +193,8 @@ hss_status hss_factor(hss_t h, void* stream);
  * hss_solve -- X = H^{-1} B with the ULV factors (Algorithm 4).
  *   B  device, n x nrhs row-major, ldb >= nrhs, the handle's dtype.
  *   X  device, n x nrhs row-major, ldx >= nrhs (may equal B when ldx == ldb).
- * Errors: STATE (no hss_factor yet), INVALID, OOM, CUDA.  Stream-ordered.
+ * Errors: STATE (no hss_factor yet), INVALID, OOM, CUDA.  Stream-ordered,
+ * returning without waiting for the device, as hss_matvec.
  */
 hss_status hss_solve(hss_t h, const void* B, int64_t ldb, int64_t nrhs,
                      void* X, int64_t ldx, void* stream);
