@@ -199,29 +199,42 @@ gemm_narrow_kernel(const GemmItem<T>* __restrict__ items, const int2* __restrict
     }
     return;
   }
+  // The warp's 4 x NC sums, each added over the lanes at levels 16, 8, 4,
+  // 2, 1 (lane L adds lane L ^ h's partial).  The first levels also halve
+  // the values a lane carries (it keeps the half its bit h selects), so the
+  // adds per lane are 4 NC - 1 + the levels left instead of 20 NC; each sum
+  // meets the same partials in the same order as a full butterfly.
+  constexpr int V = 4 * NC, LV = NC == 1 ? 2 : NC == 2 ? 3 : NC == 4 ? 4 : 5;
+  static_assert((1 << LV) == V, "4 NC values per warp");
+  T a[V];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      T v = acc[r][c];
+    for (int c = 0; c < NC; ++c) a[r * NC + c] = acc[r][c];
 #pragma unroll
-      for (int sh = 16; sh >= 1; sh >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
-      acc[r][c] = v;
+  for (int lv = 0; lv < 5; ++lv) {
+    const int h = 16 >> lv;
+    if (lv < LV) {
+      const int half = V >> (lv + 1);
+      const bool hi = (lane & h) != 0;
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const T mine = hi ? a[half + k] : a[k];
+        const T oth = hi ? a[k] : a[half + k];
+        a[k] = mine + __shfl_xor_sync(0xffffffffu, oth, h);
+      }
+    } else {
+      a[0] += __shfl_xor_sync(0xffffffffu, a[0], h);
     }
-  // lane r (< 4) writes row jr + r
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int j = jr + r;
-    if (lane != r || j >= it.rows) continue;
+  }
+  // lane L holds sum number (L >> (5 - LV)); the first lane of each run writes it
+  const int idx = lane >> (5 - LV);
+  const int r = idx / NC, c = idx - r * NC, j = jr + r;
+  if ((lane & ((1 << (5 - LV)) - 1)) == 0 && j < it.rows && c < nc) {
     const T* xr = it.X.p0 ? src_row(it.X, j) : nullptr;
-    T* o = it.out + (int64_t)j * it.ldo;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      if (c >= nc) break;
-      T v = it.sign * acc[r][c];
-      if (xr) v += xr[cb + c];
-      o[cb + c] = v;
-    }
+    T v = it.sign * a[0];
+    if (xr) v += xr[cb + c];
+    it.out[(int64_t)j * it.ldo + cb + c] = v;
   }
 }
 
