@@ -22,12 +22,12 @@ def _json_lines(out):
     return [json.loads(l) for l in out.splitlines() if l.startswith("{")]
 
 
-def _check(line, n_gpus):
+def _check(line, n_gpus, workload="toeplitz2k"):
     assert KEYS <= set(line)
     assert line["impl"] == "reference" and line["n_gpus"] == n_gpus
     assert line["metric"] == "HSS compress s" and line["unit"] == "s"
     assert line["higher_is_better"] is False and line["value"] > 0
-    assert line["config"]["workload"] == "toeplitz2k"
+    assert line["config"]["workload"] == workload
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     e2e = line["e2e"]
@@ -62,3 +62,15 @@ def test_reference_arm_under_torchrun_two_ranks():
     lines = _json_lines(r.stdout)
     assert len(lines) == 1
     _check(lines[0], 2)
+
+
+def test_reference_arm_of_the_matvec_and_solve_workload():
+    """ops80k (HSS matvec and ULV solve of QChemToeplitz): the oracle's
+    compress + factor + solve on a bounded sample, in the same line format."""
+    args = ["--impl", "reference", "--workload", "ops80k", "--steps", "1", "--warmup", "0"]
+    r = subprocess.run([sys.executable, "bench.py", *args], cwd=ROOT, env=_env(),
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = _json_lines(r.stdout)
+    assert len(lines) == 1
+    _check(lines[0], 1, "ops80k")
